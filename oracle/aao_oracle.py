@@ -1,0 +1,457 @@
+"""FP64 CPU oracle for the alpha-circulant preconditioned Crank-Nicolson all-at-once solve
+(arXiv 2401.16113).
+
+TEST INFRASTRUCTURE ONLY. This module is the plain, slow, obviously-correct reference
+that the CUDA path is checked against. Only the test suite, the smoke check and the
+benchmark's CPU-baseline leg may import it; the library never does. It shares no code
+with the CUDA path: numpy/scipy calls (FFT, banded and dense solves, sparse products,
+eigenvalues) serve as library primitives, and every step is written in the order the
+paper states it.
+
+Readings of points the paper leaves open (each one also listed in the design notes):
+  * eigenvalues of the alpha-circulant blocks are obtained numerically from their
+    definition D_l = diag(sqrt(Nt) F Lambda_alpha C_l(:,1)) (Sec. 3.1), with the unitary
+    DFT of the paper (omega = exp(-2 pi i / Nt)); this fixes the pairing of each shifted
+    system with its frequency bin.
+  * Dirichlet data enter f^{k+1/2} through the CN average of the boundary values at
+    t_k and t_{k+1}.
+  * Black-Scholes in S: S_i = i h, h = s_max/(Nx+1), 3-point central differences.
+  * time-dependent coefficients (local volatility): row k of the AaO system uses
+    A(t_{k+1/2}) for both time levels (the form of Eq. 5.8); the preconditioner uses the
+    time mean of those matrices, the direct generalisation of d-bar in Sec. 5.3.
+  * Riesz operator: fractional centred difference with Dirichlet exterior values.
+Parity pins for every function live in tests/test_oracle_*.py.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+import scipy.special as sps
+
+# ----------------------------------------------------------------------------------------
+# Spatial discretisation A (Sec. 2.1: A ~ L by finite differences) and boundary data.
+# ----------------------------------------------------------------------------------------
+
+
+def spatial_grid(p):
+    """Interior nodes: S_i = i h (Black-Scholes), or x_i = -s_max + i h (Riesz), i = 1..Nx."""
+    nx = int(p["nx"])
+    if p["op"] == "riesz":
+        h = 2.0 * p["s_max"] / (nx + 1)
+        return -p["s_max"] + h * np.arange(1, nx + 1), h
+    h = p["s_max"] / (nx + 1)
+    return h * np.arange(1, nx + 1), h
+
+
+def time_grid(p):
+    """t_k = k tau, tau = T/Nt (Sec. 2.1)."""
+    nt = int(p["nt"])
+    tau = p["T"] / nt
+    return tau * np.arange(nt + 1), tau
+
+
+def local_sigma(p, S, t):
+    """sigma(S, t); constant sigma for 'bs'."""
+    if p["op"] == "localvol":
+        return p["sigma"] + p["lv_bump"] * np.exp(-np.log(S / p["K"]) ** 2) * (1.0 + p["lv_tslope"] * t)
+    return p["sigma"] * np.ones_like(S)
+
+
+def bs_matrix(p, t):
+    """Black-Scholes operator u_t = 1/2 sigma^2 S^2 u_SS + r S u_S - r u at time t (sparse
+    Nx x Nx), 3-point central differences on the S grid, Dirichlet nodes removed.
+    Also returns the coefficients of the two Dirichlet nodes in rows 1 and Nx."""
+    S, h = spatial_grid(p)
+    sig = local_sigma(p, S, t)
+    diff = 0.5 * sig ** 2 * S ** 2 / h ** 2
+    conv = 0.5 * p["r"] * S / h
+    lower = diff - conv
+    diag = -2.0 * diff - p["r"]
+    upper = diff + conv
+    A = sp.diags([lower[1:], diag, upper[:-1]], [-1, 0, 1], format="csr")
+    return A, lower[0], upper[-1]
+
+
+def riesz_weights(beta, n):
+    """Fractional centred difference weights g_k = (-1)^k G(b+1) / (G(b/2-k+1) G(b/2+k+1)),
+    k = 0..n-1, from the Gamma-function definition. The Gamma ratios are evaluated as
+    sign * exp(-log|G(a)| - log|G(b)|) so that large k does not overflow; 1/G vanishes at
+    the poles a = 0, -1, -2, ..."""
+    k = np.arange(n, dtype=np.float64)
+    a = beta / 2 - k + 1
+    b = beta / 2 + k + 1
+    pole = (a <= 0) & (a == np.floor(a))
+    a_safe = np.where(pole, 0.5, a)
+    mag = np.exp(sps.gammaln(beta + 1.0) - sps.gammaln(a_safe) - sps.gammaln(b))
+    g = (-1.0) ** k * sps.gammasgn(a_safe) * mag
+    return np.where(pole, 0.0, g)
+
+
+def riesz_matrix(p):
+    """Riesz operator of Eq. 1.2 (second case) in log-price:
+    u_t = kappa d^beta u/d|x|^beta + (r - kappa) u_x - r u, kappa = sigma^2/2, with
+    d^beta/d|x|^beta u(x_i) ~ -h^-beta sum_k g_k u(x_{i-k}) and central u_x.
+    Returns (A, left-exterior coefficient vector, left drift coefficient)."""
+    x, h = spatial_grid(p)
+    nx = x.size
+    kappa = 0.5 * p["sigma"] ** 2
+    g = riesz_weights(p["beta"], nx + 1)
+    A = -kappa * h ** (-p["beta"]) * g[np.abs(np.subtract.outer(np.arange(nx), np.arange(nx)))]
+    drift = (p["r"] - kappa) / (2.0 * h)
+    A[np.arange(nx - 1), np.arange(1, nx)] += drift
+    A[np.arange(1, nx), np.arange(nx - 1)] -= drift
+    A[np.arange(nx), np.arange(nx)] -= p["r"]
+    # exterior nodes j <= 0 all carry the left Dirichlet value: row i (1-based) collects
+    # sum_{m >= i} g_m, with sum_{m >= 1} g_m = -g_0/2 (the weights sum to zero).
+    tail = -0.5 * g[0] - np.concatenate(([0.0], np.cumsum(g[1:nx])))
+    left_ext = -kappa * h ** (-p["beta"]) * tail
+    return A, left_ext, -drift
+
+
+def operator_at(p, t):
+    """A(t) as a dense matrix, plus the coefficients through which the left/right Dirichlet
+    values enter the first/last interior rows. op 'matrix' takes a user matrix p['A']
+    (constant in time, no boundary data) for the spectral pins."""
+    if p["op"] == "matrix":
+        A = np.asarray(p["A"], dtype=np.float64)
+        return A, np.zeros(A.shape[0]), np.zeros(A.shape[0])
+    if p["op"] == "riesz":
+        A, left_ext, left_drift = riesz_matrix(p)
+        cl = left_ext.copy()
+        cl[0] += left_drift
+        return A, cl, np.zeros(A.shape[0])
+    A, lo, up = bs_matrix(p, t)
+    nx = A.shape[0]
+    cl = np.zeros(nx)
+    cr = np.zeros(nx)
+    cl[0] = lo
+    cr[-1] = up
+    return A, cl, cr
+
+
+def boundary_values(p, t):
+    """Dirichlet values (g_L(t), g_R(t)) in time-to-maturity t."""
+    if p["op"] == "matrix":
+        return 0.0, 0.0
+    disc = p["K"] * math.exp(-p["r"] * t)
+    if p["op"] == "riesz":
+        return disc - math.exp(-p["s_max"]), 0.0
+    if p["payoff"] == "put":
+        return disc, 0.0
+    return 0.0, p["s_max"] - disc
+
+
+def payoff(p):
+    """u_0: the option payoff at the interior nodes (Eq. 1.1, u(., 0) = u_0)."""
+    if p["op"] == "matrix":
+        return np.asarray(p.get("u0", np.ones(int(p["nx"]))), dtype=np.float64)
+    x, _ = spatial_grid(p)
+    if p["op"] == "riesz":
+        return np.maximum(p["K"] - np.exp(x), 0.0)
+    if p["payoff"] == "put":
+        return np.maximum(p["K"] - x, 0.0)
+    return np.maximum(x - p["K"], 0.0)
+
+
+def step_operator(p, k):
+    """A_k = A(t_{k+1/2}) used by CN step k -> k+1 (Eq. 2.1; Eq. 5.8 for time-dependent A)."""
+    t, tau = time_grid(p)
+    return operator_at(p, t[k] + 0.5 * tau)
+
+
+def forcing(p, k):
+    """f^{k+1/2}: Dirichlet contribution averaged over t_k and t_{k+1} (CN)."""
+    t, _ = time_grid(p)
+    _, cl, cr = step_operator(p, k)
+    gl0, gr0 = boundary_values(p, t[k])
+    gl1, gr1 = boundary_values(p, t[k + 1])
+    return cl * 0.5 * (gl0 + gl1) + cr * 0.5 * (gr0 + gr1)
+
+
+# ----------------------------------------------------------------------------------------
+# Sequential CN (Eq. 2.1) and the all-at-once system M u = b (Eq. 2.2 / Eq. 5.8).
+# ----------------------------------------------------------------------------------------
+
+
+def _solve(Amat, rhs):
+    """Direct solve of one spatial system: banded LAPACK for sparse tridiagonal matrices,
+    dense LU otherwise."""
+    if sp.issparse(Amat):
+        n = Amat.shape[0]
+        ab = np.zeros((3, n), dtype=np.result_type(Amat.dtype, rhs.dtype))
+        ab[0, 1:] = Amat.diagonal(1)
+        ab[1, :] = Amat.diagonal(0)
+        ab[2, :-1] = Amat.diagonal(-1)
+        return sla.solve_banded((1, 1), ab, rhs)
+    return np.linalg.solve(Amat, rhs)
+
+
+def _eye_like(A):
+    return sp.identity(A.shape[0], format="csr") if sp.issparse(A) else np.eye(A.shape[0])
+
+
+def _dense(A):
+    return A.toarray() if sp.issparse(A) else np.asarray(A)
+
+
+def sequential_cn(p):
+    """Time stepping of Eq. 2.1: (I - tau/2 A_k) u^{k+1} = (I + tau/2 A_k) u^k + tau f^{k+1/2}.
+    Returns U with U[k] = u^{k+1}, k = 0..Nt-1 (the AaO unknown ordering of Eq. 2.2)."""
+    nt = int(p["nt"])
+    _, tau = time_grid(p)
+    u = payoff(p)
+    out = np.empty((nt, u.size))
+    for k in range(nt):
+        A, _, _ = step_operator(p, k)
+        I = _eye_like(A)
+        rhs = (I + 0.5 * tau * A) @ u + tau * forcing(p, k)
+        u = _solve(I - 0.5 * tau * A, rhs)
+        out[k] = u
+    return out
+
+
+def assemble_M(p):
+    """M of Eq. 2.2 (B1 (x) I - B2 (x) A~, A~ = tau A) for constant A; for time-dependent A the
+    form of Eq. 5.8 with A~_k = tau A(t_{k+1/2}) in block row k. Sparse CSR, time-major."""
+    nt, nx = int(p["nt"]), int(p["nx"])
+    _, tau = time_grid(p)
+    I = sp.identity(nx, format="csr")
+    if p["op"] != "localvol":
+        At = sp.csr_matrix(tau * step_operator(p, 0)[0])
+        B1 = sp.diags([np.ones(nt), -np.ones(nt - 1)], [0, -1], shape=(nt, nt))
+        B2 = 0.5 * sp.diags([np.ones(nt), np.ones(nt - 1)], [0, -1], shape=(nt, nt))
+        return (sp.kron(B1, I) - sp.kron(B2, At)).tocsr()
+    blocks = [[None] * nt for _ in range(nt)]
+    for k in range(nt):
+        At = sp.csr_matrix(tau * step_operator(p, k)[0])
+        blocks[k][k] = I - 0.5 * At
+        if k > 0:
+            blocks[k][k - 1] = -(I + 0.5 * At)
+    return sp.bmat(blocks, format="csr")
+
+
+def assemble_b(p):
+    """b = xi + tau f (Eq. 2.2), xi = [(I + A~_0/2) u^0; 0; ...; 0]."""
+    nt, nx = int(p["nt"]), int(p["nx"])
+    _, tau = time_grid(p)
+    b = np.empty((nt, nx))
+    for k in range(nt):
+        b[k] = tau * forcing(p, k)
+    A0, _, _ = step_operator(p, 0)
+    b[0] += payoff(p) + 0.5 * tau * (A0 @ payoff(p))
+    return b.reshape(-1)
+
+
+def matvec(p, x, M=None):
+    """y = M x with the explicit sparse M."""
+    if M is None:
+        M = assemble_M(p)
+    return M @ x
+
+
+# ----------------------------------------------------------------------------------------
+# The preconditioner P_alpha (Eq. 3.1) and its three-step inverse (Eq. 3.2).
+# ----------------------------------------------------------------------------------------
+
+
+def alpha_circulants(nt, alpha):
+    """C1^(alpha) and C2^(alpha) of Sec. 3.1: B1, B2 with corner entries -alpha and alpha/2."""
+    C1 = np.eye(nt) - np.eye(nt, k=-1)
+    C2 = 0.5 * (np.eye(nt) + np.eye(nt, k=-1))
+    C1[0, nt - 1] += -alpha
+    C2[0, nt - 1] += 0.5 * alpha
+    if nt == 1:
+        C1 = np.array([[1.0 - alpha]])
+        C2 = np.array([[0.5 * (1.0 + alpha)]])
+    return C1, C2
+
+
+def mean_operator(p):
+    """A-bar used by the preconditioner: A itself for constant coefficients; the mean of
+    A(t_{k+1/2}) over k for time-dependent ones (generalising d-bar of Sec. 5.3)."""
+    if p["op"] != "localvol":
+        return step_operator(p, 0)[0]
+    nt = int(p["nt"])
+    acc = step_operator(p, 0)[0]
+    for k in range(1, nt):
+        acc = acc + step_operator(p, k)[0]
+    return (acc / nt).tocsr()
+
+
+def dense_P(p, alpha=None):
+    """P_alpha = C1 (x) I_s - C2 (x) A~ (Eq. 3.1), A~ = tau A-bar. Dense; tiny sizes only."""
+    alpha = p["alpha"] if alpha is None else alpha
+    nt, nx = int(p["nt"]), int(p["nx"])
+    _, tau = time_grid(p)
+    C1, C2 = alpha_circulants(nt, alpha)
+    return np.kron(C1, np.eye(nx)) - np.kron(C2, tau * _dense(mean_operator(p)))
+
+
+def dense_M(p):
+    return assemble_M(p).toarray()
+
+
+def precond_dense(p, v, alpha=None):
+    """z = P_alpha^{-1} v by a dense LU solve of Eq. 3.1 (brute force)."""
+    return np.linalg.solve(dense_P(p, alpha), v)
+
+
+def circulant_eigs(nt, alpha):
+    """Lambda_alpha and D_l = diag(sqrt(Nt) F Lambda_alpha C_l(:,1)) (Sec. 3.1), F the unitary
+    DFT with omega = exp(-2 pi i/Nt); sqrt(Nt) F y is numpy's unnormalised forward FFT."""
+    lam = alpha ** (np.arange(nt) / nt)
+    C1, C2 = alpha_circulants(nt, alpha)
+    d1 = np.fft.fft(lam * C1[:, 0])
+    d2 = np.fft.fft(lam * C2[:, 0])
+    return lam, d1, d2
+
+
+def precond_fft(p, v, alpha=None, return_spectrum=False):
+    """z = P_alpha^{-1} v by the three steps of Eq. 3.2:
+    (a) z1 = (V_alpha^{-1} (x) I) v with V_alpha^{-1} = F Lambda_alpha,
+    (b) (lambda_{1,k} I - lambda_{2,k} A~) z2_k = z1_k for every k = 1..Nt,
+    (c) z = (V_alpha (x) I) z2 with V_alpha = Lambda_alpha^{-1} F^*.
+    All Nt shifted systems are solved (the conjugate-pair saving of Remark 1 is not used)."""
+    alpha = p["alpha"] if alpha is None else alpha
+    nt, nx = int(p["nt"]), int(p["nx"])
+    _, tau = time_grid(p)
+    lam, d1, d2 = circulant_eigs(nt, alpha)
+    At = tau * mean_operator(p)
+    V = np.asarray(v, dtype=np.float64).reshape(nt, nx)
+    # step (a): unitary DFT along time of the Lambda-scaled blocks
+    z1 = np.fft.fft(lam[:, None] * V, axis=0) / math.sqrt(nt)
+    # step (b): Nt independent complex-shifted spatial solves
+    z2 = np.empty_like(z1)
+    I = _eye_like(At)
+    for k in range(nt):
+        z2[k] = _solve(d1[k] * I - d2[k] * At, z1[k])
+    # step (c): inverse unitary DFT, then Lambda^{-1}
+    z = (np.fft.ifft(z2, axis=0) * math.sqrt(nt)) / lam[:, None]
+    if return_spectrum:
+        return z, z1, z2
+    return z.real.reshape(-1)
+
+
+# ----------------------------------------------------------------------------------------
+# Right-preconditioned flexible GMRES(m) (Sec. 5: right-preconditioned GMRES, zero initial
+# guess, relative-residual stopping; Its = inner iterations = matrix-vector products).
+# ----------------------------------------------------------------------------------------
+
+
+def fgmres(apply_M, apply_Pinv, b, tol, m, maxit, x0=None):
+    """Flexible right-preconditioned GMRES(m): Arnoldi with classical Gram-Schmidt applied
+    twice, Givens rotations on the Hessenberg matrix, restart after m inner steps; the
+    stopping test uses the true residual ||b - M x|| / ||b|| at every restart.
+    Returns (x, info) with info = dict(its, restarts, rel_res, converged, history)."""
+    b = np.asarray(b, dtype=np.float64)
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
+    bnorm = np.linalg.norm(b)
+    if bnorm == 0.0:
+        return np.zeros_like(b), dict(its=0, restarts=0, rel_res=0.0, converged=True, history=[])
+    r = b - apply_M(x)
+    beta = np.linalg.norm(r)
+    its = 0
+    restarts = 0
+    hist = [beta / bnorm]
+    while True:
+        if beta <= tol * bnorm:
+            return x, dict(its=its, restarts=restarts, rel_res=beta / bnorm, converged=True, history=hist)
+        if its >= maxit:
+            return x, dict(its=its, restarts=restarts, rel_res=beta / bnorm, converged=False, history=hist)
+        Vs = [r / beta]
+        Zs = []
+        H = np.zeros((m + 1, m))
+        g = np.zeros(m + 1)
+        g[0] = beta
+        cs = np.zeros(m)
+        sn = np.zeros(m)
+        jd = 0
+        for j in range(m):
+            z = apply_Pinv(Vs[j])
+            Zs.append(z)
+            w = apply_M(z)
+            its += 1
+            Vm = np.array(Vs)
+            h = Vm @ w
+            w = w - Vm.T @ h
+            h2 = Vm @ w
+            w = w - Vm.T @ h2
+            h = h + h2
+            hn = np.linalg.norm(w)
+            H[: j + 1, j] = h
+            H[j + 1, j] = hn
+            for i in range(j):
+                a, c = H[i, j], H[i + 1, j]
+                H[i, j] = cs[i] * a + sn[i] * c
+                H[i + 1, j] = -sn[i] * a + cs[i] * c
+            rho = math.hypot(H[j, j], H[j + 1, j])
+            cs[j], sn[j] = H[j, j] / rho, H[j + 1, j] / rho
+            H[j, j] = rho
+            H[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            jd = j + 1
+            hist.append(abs(g[j + 1]) / bnorm)
+            if abs(g[j + 1]) <= tol * bnorm or hn == 0.0 or its >= maxit:
+                break
+            Vs.append(w / hn)
+        y = sla.solve_triangular(H[:jd, :jd], g[:jd])
+        x = x + np.array(Zs[:jd]).T @ y
+        r = b - apply_M(x)
+        beta = np.linalg.norm(r)
+        restarts += 1
+        hist.append(beta / bnorm)
+
+
+def solve(p, precond="fft", tol=None, m=None, maxit=200):
+    """AaO solve of Eq. 2.2 by right-preconditioned FGMRES(m) with P_alpha (FP64)."""
+    M = assemble_M(p)
+    b = assemble_b(p)
+    tol = p["tol"] if tol is None else tol
+    m = p["m"] if m is None else m
+    if precond == "fft":
+        Pinv = lambda v: precond_fft(p, v)
+    elif precond == "dense":
+        Pinv = lambda v: precond_dense(p, v)
+    else:
+        Pinv = lambda v: v
+    return fgmres(lambda x: M @ x, Pinv, b, tol, m, maxit)
+
+
+# ----------------------------------------------------------------------------------------
+# Black-Scholes closed form (the PDE check for 'bs'), textbook formula.
+# ----------------------------------------------------------------------------------------
+
+
+def bs_price(S, K, r, sigma, T, kind="put"):
+    S = np.asarray(S, dtype=np.float64)
+    with np.errstate(divide="ignore"):
+        d1 = (np.log(S / K) + (r + 0.5 * sigma ** 2) * T) / (sigma * math.sqrt(T))
+    d2 = d1 - sigma * math.sqrt(T)
+    N = sps.ndtr
+    if kind == "call":
+        return S * N(d1) - K * math.exp(-r * T) * N(d2)
+    return K * math.exp(-r * T) * N(-d2) - S * N(-d1)
+
+
+# ----------------------------------------------------------------------------------------
+# Spectral quantities (Lemma 3.1, Theorem 3.1, Theorem 2.2, Lemma 4.1) on tiny grids.
+# ----------------------------------------------------------------------------------------
+
+
+def preconditioned_eigs(p, alpha=None):
+    """Eigenvalues of P_alpha^{-1} M (dense)."""
+    return np.linalg.eigvals(np.linalg.solve(dense_P(p, alpha), dense_M(p)))
+
+
+def R_matrix(p):
+    """R with P_alpha = M - alpha R (Sec. 4): the only non-zero block is Q2 = I + A~/2 in
+    block position (1, Nt)."""
+    nt, nx = int(p["nt"]), int(p["nx"])
+    _, tau = time_grid(p)
+    R = np.zeros((nt * nx, nt * nx))
+    R[:nx, (nt - 1) * nx:] = np.eye(nx) + 0.5 * tau * _dense(mean_operator(p))
+    return R
