@@ -1,0 +1,149 @@
+/*
+ * aao.h -- C ABI of the GB300 (sm_103a) all-at-once Crank-Nicolson solver with the
+ * generalized block alpha-circulant preconditioner of arXiv 2401.16113.
+ *
+ * Conventions shared by every entry point
+ *  - Space-time vectors are FP64, time-block-major: u[t * nx + i] holds u^{t+1} at the
+ *    interior spatial node i (the ordering of the all-at-once unknown in Sec. 2.2),
+ *    t = 0..nt-1, i = 0..nx-1. Their length is nx * nt.
+ *  - Pointers named *_dev are device pointers owned by the caller; the library never
+ *    frees caller memory. Pointers named *_host are ordinary (pageable or pinned) host
+ *    pointers.
+ *  - Work is issued on the stream given in aao_problem.stream (0 = legacy default stream)
+ *    and is stream-ordered; calls that report statistics synchronise that stream.
+ *  - Every call returns AAO_OK (0) or a negative status; aao_last_error() returns a
+ *    human-readable message for the calling thread's most recent failure.
+ *  - A handle is not thread-safe: serialise calls on one handle.
+ */
+#ifndef AAO_H
+#define AAO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define AAO_OK 0
+#define AAO_EINVAL (-1)        /* invalid argument or unsupported size            */
+#define AAO_ECUDA (-2)         /* a CUDA runtime call failed                      */
+#define AAO_ENOMEM (-3)        /* device allocation failed                        */
+#define AAO_NOT_CONVERGED (-4) /* FGMRES hit maxit before reaching tol            */
+#define AAO_BREAKDOWN (-5)     /* non-finite value or Arnoldi breakdown w/o convergence */
+#define AAO_TIMEOUT (-6)       /* a bounded device-side wait gave up              */
+#define AAO_EUNSUPPORTED (-7)  /* operator / size combination not built           */
+
+/* spatial operator A (Eq. 1.2, discretised by finite differences) */
+#define AAO_OP_BS 0       /* Black-Scholes in S, constant sigma, 3-point central FD      */
+#define AAO_OP_LOCALVOL 1 /* Black-Scholes with sigma(S,t) = sigma + lv_bump *
+                             exp(-ln(S/K)^2) * (1 + lv_tslope * t); row k of the AaO system
+                             uses A(t_{k+1/2}) (the time-dependent form of Eq. 5.8), the
+                             preconditioner the time mean of those matrices (Sec. 5.3)      */
+#define AAO_OP_RIESZ 2    /* Riesz fractional operator in log-price (reserved)           */
+
+#define AAO_PUT 0
+#define AAO_CALL 1
+
+#define AAO_FP64 0  /* preconditioner apply in FP64 complex                           */
+#define AAO_MIXED 1 /* preconditioner apply in FP32 complex inside FP64 FGMRES        */
+
+/*
+ * Problem descriptor (plain old data; copied by aao_create).
+ *  nx, nt      interior spatial nodes (>= 2) and CN steps (power of two, 1..16384)
+ *  op, payoff  AAO_OP_*, AAO_PUT / AAO_CALL
+ *  precision   AAO_FP64 or AAO_MIXED
+ *  T, r, K, sigma   maturity, rate, strike, volatility
+ *  s_max       S-domain [0, s_max]; the grid is S_i = i h, h = s_max / (nx + 1), i = 1..nx,
+ *              with Dirichlet values V(0,t) = K e^{-rt} (put) or 0, V(s_max,t) = 0 (put)
+ *              or s_max - K e^{-rt} (call), t = time to maturity
+ *  alpha       the free parameter of P_alpha (Eq. 3.1), 0 < alpha < 1 (alpha = 1 allowed:
+ *              the classical block-circulant preconditioner P_1)
+ *  stream      cudaStream_t on which all work is issued
+ */
+typedef struct aao_problem {
+  int32_t nx, nt, op, payoff, precision, reserved;
+  double T, r, K, sigma, s_max, lv_bump, lv_tslope, beta, alpha;
+  void* stream;
+} aao_problem;
+
+/* FGMRES outcome. iterations counts inner Arnoldi steps (= preconditioned matrix-vector
+   products, the "Its" of Sec. 5); rel_residual is the true ||b - M x||_2 / ||b||_2 at exit,
+   computed in FP64; ms is wall time of the call including setup of the first cycle. */
+typedef struct aao_stats {
+  int32_t status, iterations, restarts, launches;
+  double rel_residual, est_residual, ms;
+} aao_stats;
+
+typedef struct aao_handle aao_handle;
+
+/* Validate *p, build the operator coefficients, the eigenvalues lambda_{1,k}, lambda_{2,k}
+   (Sec. 3.1, Eq. eigCx), Lambda_alpha, the FFT twiddles and the preconditioner workspace
+   on the device. Ownership: *h owns all of it until aao_destroy. Errors: AAO_EINVAL for
+   bad sizes or parameters, AAO_EUNSUPPORTED for op = AAO_OP_RIESZ or non-power-of-two nt,
+   AAO_ENOMEM / AAO_ECUDA from the device. On error *h is set to NULL. */
+int aao_create(const aao_problem* p, aao_handle** h);
+
+/* Free every device buffer of h (NULL is accepted). */
+int aao_destroy(aao_handle* h);
+
+/* b_dev <- b = xi + tau f of Eq. 2.2: xi = [(I + A~_0/2) u^0; 0; ...], u^0 = payoff, f the
+   Dirichlet data averaged over t_k and t_{k+1}. b_dev: nx*nt doubles, device. */
+int aao_rhs(aao_handle* h, double* b_dev);
+
+/* y_dev <- M x_dev with M = B1 (x) I - B2 (x) A~ (Eq. 2.2; Eq. 5.8 form for AAO_OP_LOCALVOL).
+   x_dev, y_dev: nx*nt doubles, device, must not alias. */
+int aao_matvec(aao_handle* h, const double* x_dev, double* y_dev);
+
+/* z_dev <- P_alpha^{-1} v_dev by the three steps of Eq. 3.2 with the conjugate-pair saving
+   of Remark 1: Lambda_alpha scaling and a real-to-complex FFT along t, nt/2+1 complex-shifted
+   tridiagonal solves (lambda_{1,k} I - lambda_{2,k} A~) z_k = z1_k, then the inverse FFT and
+   Lambda_alpha^{-1}. FP32 complex inside when precision = AAO_MIXED (z is still returned in
+   FP64). v_dev, z_dev: nx*nt doubles, device; may alias. */
+int precond_apply(aao_handle* h, const double* v_dev, double* z_dev);
+
+/* Solve M x = b (Eq. 2.2) by right-preconditioned flexible GMRES(m) with P_alpha
+   (Sec. 5: right preconditioning, relative-residual stop). x_dev holds the initial guess on
+   entry (zero it for the paper's protocol) and the solution on exit. Orthogonalisation is
+   classical Gram-Schmidt applied twice, the least-squares update uses Givens rotations,
+   all in FP64; the true residual is recomputed at every restart. 1 <= m <= 64,
+   maxit >= 1 bounds the total inner iterations. st may be NULL. Returns AAO_OK,
+   AAO_NOT_CONVERGED, AAO_BREAKDOWN or an error. */
+int fgmres_solve(aao_handle* h, const double* b_dev, double* x_dev, double tol, int m, int maxit,
+                 aao_stats* st);
+
+/* As fgmres_solve with host buffers: copies b_host to the device, solves from a zero
+   initial guess, copies the solution to x_host. Both are nx*nt doubles. */
+int fgmres_solve_host(aao_handle* h, const double* b_host, double* x_host, double tol, int m,
+                      int maxit, aao_stats* st);
+
+/* Message of the calling thread's most recent failure ("" if none). */
+const char* aao_last_error(void);
+
+/* Number of kernels this library has launched in this process (monotone counter). */
+uint64_t aao_launch_count(void);
+
+/* Kernel classes for per-kernel device timing (diagnostics; no counterpart in the paper). */
+#define AAO_K_FFT_FWD 0  /* step (a) of Eq. 3.2: scaling + forward FFT along t    */
+#define AAO_K_TRIDIAG 1  /* step (b): shifted tridiagonal solves                  */
+#define AAO_K_FFT_INV 2  /* step (c): inverse FFT along t + unscaling             */
+#define AAO_K_MATVEC 3   /* y = M x and r = b - M x                               */
+#define AAO_K_ARNOLDI 4  /* Gram-Schmidt projections, updates, normalisation      */
+#define AAO_K_OTHER 5    /* reductions, Givens, least squares, solution update    */
+#define AAO_K_COUNT 6
+
+/* Time the kernel classes whose bit (1 << AAO_K_*) is set in mask with CUDA events recorded
+   on the launching stream around each launch, and clear what was accumulated; mask 0 turns
+   timing off (the default). */
+int aao_profile_enable(int mask);
+
+/* For kernel class cls since the last aao_profile_enable: launches timed, their total device
+   milliseconds, and the algorithmic bytes they move (what each launch must read and write
+   once, by its arguments' sizes). Synchronises the recorded events. */
+int aao_profile_read(int cls, int64_t* launches, double* total_ms, double* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AAO_H */

@@ -1,0 +1,212 @@
+"""Thin ctypes binding of libaao.so (include/aao.h): same entry-point names, argument
+marshalling only. Every step of the solver runs in the library's CUDA kernels; nothing
+here computes. The library must have been built (paper_2401_16113_gb300.build.build());
+loading fails loudly otherwise.
+
+Space-time vectors are torch.float64 CUDA tensors of nx*nt elements, time-block-major
+(u[t*nx + i] = u^{t+1}_i); host variants take numpy float64 arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+AAO_OK, AAO_EINVAL, AAO_ECUDA, AAO_ENOMEM = 0, -1, -2, -3
+AAO_NOT_CONVERGED, AAO_BREAKDOWN, AAO_TIMEOUT, AAO_EUNSUPPORTED = -4, -5, -6, -7
+OPS = {"bs": 0, "localvol": 1, "riesz": 2}
+PAYOFFS = {"put": 0, "call": 1}
+PRECISIONS = {"fp64": 0, "mixed": 1}
+STATUS = {0: "ok", -1: "einval", -2: "ecuda", -3: "enomem", -4: "not_converged",
+          -5: "breakdown", -6: "timeout", -7: "unsupported"}
+
+EXPORTS = ["aao_create", "aao_destroy", "aao_rhs", "aao_matvec", "precond_apply",
+           "fgmres_solve", "fgmres_solve_host", "aao_last_error", "aao_launch_count",
+           "aao_profile_enable", "aao_profile_read"]
+
+
+class AaoProblem(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("nt", ctypes.c_int32), ("op", ctypes.c_int32),
+                ("payoff", ctypes.c_int32), ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("T", ctypes.c_double), ("r", ctypes.c_double), ("K", ctypes.c_double),
+                ("sigma", ctypes.c_double), ("s_max", ctypes.c_double), ("lv_bump", ctypes.c_double),
+                ("lv_tslope", ctypes.c_double), ("beta", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("stream", ctypes.c_void_p)]
+
+
+class AaoStats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32), ("restarts", ctypes.c_int32),
+                ("launches", ctypes.c_int32), ("rel_residual", ctypes.c_double),
+                ("est_residual", ctypes.c_double), ("ms", ctypes.c_double)]
+
+    def to_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class AaoError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(path=None):
+    """Load libaao.so (built in-tree). Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libaao.so not built at {path}; run paper_2401_16113_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, dp, ip = ctypes.c_void_p, ctypes.c_double, ctypes.c_int
+    lib.aao_create.argtypes = [ctypes.POINTER(AaoProblem), ctypes.POINTER(vp)]
+    lib.aao_destroy.argtypes = [vp]
+    lib.aao_rhs.argtypes = [vp, vp]
+    lib.aao_matvec.argtypes = [vp, vp, vp]
+    lib.precond_apply.argtypes = [vp, vp, vp]
+    lib.fgmres_solve.argtypes = [vp, vp, vp, dp, ip, ip, ctypes.POINTER(AaoStats)]
+    lib.fgmres_solve_host.argtypes = [vp, vp, vp, dp, ip, ip, ctypes.POINTER(AaoStats)]
+    lib.aao_last_error.restype = ctypes.c_char_p
+    lib.aao_launch_count.restype = ctypes.c_uint64
+    lib.aao_profile_enable.argtypes = [ctypes.c_int]
+    lib.aao_profile_read.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double)]
+    for name in ("aao_create", "aao_destroy", "aao_rhs", "aao_matvec", "precond_apply", "fgmres_solve",
+                 "fgmres_solve_host", "aao_profile_enable", "aao_profile_read"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(code):
+    if code != AAO_OK:
+        raise AaoError(code, load().aao_last_error().decode())
+    return code
+
+
+def make_problem(p, stream=0):
+    s = AaoProblem()
+    s.nx, s.nt = int(p["nx"]), int(p["nt"])
+    s.op, s.payoff, s.precision = OPS[p["op"]], PAYOFFS[p["payoff"]], PRECISIONS[p["precision"]]
+    s.T, s.r, s.K, s.sigma, s.s_max = p["T"], p["r"], p["K"], p["sigma"], p["s_max"]
+    s.lv_bump, s.lv_tslope, s.beta, s.alpha = p["lv_bump"], p["lv_tslope"], p["beta"], p["alpha"]
+    s.stream = int(stream or 0)
+    return s
+
+
+def _stream_of(stream):
+    if stream is not None:
+        return int(stream)
+    import torch
+    return int(torch.cuda.current_stream().cuda_stream)
+
+
+class Handle:
+    """Owns one aao_handle; frees it on close()/garbage collection."""
+
+    def __init__(self, ptr, problem):
+        self.ptr = ptr
+        self.problem = dict(problem)
+        self.n = int(problem["nx"]) * int(problem["nt"])
+
+    def close(self):
+        if self.ptr:
+            load().aao_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _dev(t, n):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+            and t.numel() == n):
+        raise ValueError(f"expected a contiguous float64 CUDA tensor of {n} elements")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def aao_create(p, stream=None):
+    ptr = ctypes.c_void_p()
+    _check(load().aao_create(ctypes.byref(make_problem(p, _stream_of(stream))), ctypes.byref(ptr)))
+    return Handle(ptr, p)
+
+
+def aao_destroy(h):
+    h.close()
+
+
+def aao_rhs(h, b):
+    _check(load().aao_rhs(h.ptr, _dev(b, h.n)))
+
+
+def aao_matvec(h, x, y):
+    _check(load().aao_matvec(h.ptr, _dev(x, h.n), _dev(y, h.n)))
+
+
+def precond_apply(h, v, z):
+    _check(load().precond_apply(h.ptr, _dev(v, h.n), _dev(z, h.n)))
+
+
+def fgmres_solve(h, b, x, tol, m, maxit, raise_on_failure=False):
+    """Returns the aao_stats as a dict (status != 0 reports non-convergence)."""
+    st = AaoStats()
+    code = load().fgmres_solve(h.ptr, _dev(b, h.n), _dev(x, h.n), float(tol), int(m), int(maxit),
+                               ctypes.byref(st))
+    if code in (AAO_OK, AAO_NOT_CONVERGED, AAO_BREAKDOWN) and not raise_on_failure:
+        return st.to_dict()
+    _check(code)
+    return st.to_dict()
+
+
+def fgmres_solve_host(h, b_host, x_host, tol, m, maxit):
+    """Host-buffer variant: b_host, x_host are float64 numpy arrays of nx*nt elements."""
+    for a in (b_host, x_host):
+        if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous and a.size == h.n):
+            raise ValueError(f"expected contiguous float64 numpy arrays of {h.n} elements")
+    st = AaoStats()
+    code = load().fgmres_solve_host(h.ptr, b_host.ctypes.data_as(ctypes.c_void_p),
+                                    x_host.ctypes.data_as(ctypes.c_void_p), float(tol), int(m), int(maxit),
+                                    ctypes.byref(st))
+    if code not in (AAO_OK, AAO_NOT_CONVERGED, AAO_BREAKDOWN):
+        _check(code)
+    return st.to_dict()
+
+
+def aao_launch_count():
+    return int(load().aao_launch_count())
+
+
+KERNEL_CLASSES = {"fft_fwd": 0, "tridiag": 1, "fft_inv": 2, "matvec": 3, "arnoldi": 4, "other": 5}
+
+
+def aao_profile_enable(classes=None):
+    """Time the given kernel classes (names or ids; None = all, [] = off)."""
+    if classes is None:
+        mask = (1 << len(KERNEL_CLASSES)) - 1
+    else:
+        mask = 0
+        for c in classes:
+            mask |= 1 << KERNEL_CLASSES.get(c, c)
+    _check(load().aao_profile_enable(mask))
+
+
+def aao_profile_read(cls):
+    """(launches, total device ms, algorithmic bytes) recorded for a kernel class."""
+    c = KERNEL_CLASSES.get(cls, cls)
+    n, ms, by = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+    _check(load().aao_profile_read(int(c), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)))
+    return int(n.value), float(ms.value), float(by.value)

@@ -1,0 +1,133 @@
+// Internal declarations of the GB300 all-at-once CN solver library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+
+#include "../../include/aao.h"
+
+namespace aao {
+
+// ------------------------------------------------------------------ error plumbing
+void set_error(const std::string& msg);
+extern std::atomic<uint64_t> g_launches;
+
+#define AAO_TRY_CUDA(expr)                                                              \
+  do {                                                                                  \
+    cudaError_t e_ = (expr);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      ::aao::set_error(std::string(#expr) + ": " + cudaGetErrorString(e_));             \
+      return e_ == cudaErrorMemoryAllocation ? AAO_ENOMEM : AAO_ECUDA;                  \
+    }                                                                                   \
+  } while (0)
+
+#define AAO_CHECK_LAUNCH()                                                              \
+  do {                                                                                  \
+    ::aao::g_launches.fetch_add(1, std::memory_order_relaxed);                          \
+    cudaError_t e_ = cudaGetLastError();                                                \
+    if (e_ != cudaSuccess) {                                                            \
+      ::aao::set_error(std::string("kernel launch: ") + cudaGetErrorString(e_));         \
+      return AAO_ECUDA;                                                                 \
+    }                                                                                   \
+  } while (0)
+
+#define AAO_TRY(expr)            \
+  do {                           \
+    int s_ = (expr);             \
+    if (s_ != AAO_OK) return s_; \
+  } while (0)
+
+// ------------------------------------------------------------------ device timing
+// When enabled, every launch inside a ProfScope is bracketed by two CUDA events recorded on
+// the launching stream; aao_profile_read sums their elapsed times per kernel class.
+void prof_begin(int cls, cudaStream_t s);
+void prof_end(int cls, cudaStream_t s, double bytes);
+extern std::atomic<int> g_prof_mask;
+struct ProfScope {
+  int cls;
+  cudaStream_t s;
+  double bytes;
+  bool on;
+  ProfScope(int c, cudaStream_t st, double b = 0.0) : cls(c), s(st), bytes(b) {
+    on = (g_prof_mask.load(std::memory_order_relaxed) >> c) & 1;
+    if (on) prof_begin(cls, s);
+  }
+  ~ProfScope() {
+    if (on) prof_end(cls, s, bytes);
+  }
+};
+
+// ------------------------------------------------------------------ complex helpers
+template <typename R> struct cplx;
+template <> struct cplx<float> { using type = float2; };
+template <> struct cplx<double> { using type = double2; };
+template <typename R> using C_t = typename cplx<R>::type;
+
+template <typename C> __host__ __device__ __forceinline__ C cmk(decltype(C::x) a, decltype(C::x) b) {
+  C c; c.x = a; c.y = b; return c;
+}
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return cmk<C>(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return cmk<C>(a.x - b.x, a.y - b.y); }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  return cmk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename C> __device__ __forceinline__ C cconj(C a) { return cmk<C>(a.x, -a.y); }
+template <typename C> __device__ __forceinline__ C cscale(C a, decltype(C::x) s) { return cmk<C>(a.x * s, a.y * s); }
+// multiply by -i
+template <typename C> __device__ __forceinline__ C cmul_mi(C a) { return cmk<C>(a.y, -a.x); }
+// 1 / z
+template <typename C> __device__ __forceinline__ C cinv(C a) {
+  auto d = a.x * a.x + a.y * a.y;
+  auto s = (decltype(C::x))1 / d;
+  return cmk<C>(a.x * s, -a.y * s);
+}
+
+// ------------------------------------------------------------------ handle
+struct Handle {
+  aao_problem p;
+  cudaStream_t stream = 0;
+  int nx = 0, nt = 0, K = 0, log2n = 0;
+  int pitch = 0;          // row pitch (complex elements) of the half spectrum [K][pitch]
+  double tau = 0.0;
+  size_t n = 0;           // nx * nt
+  bool mixed = false;
+  int coef_rows = 1;      // 1 (constant operator) or nt (time-dependent)
+
+  // matvec coefficients: (1/2) tau A_t, rows of nx (lower, diag, upper), coef_rows rows each.
+  // lower[0] and upper[nx-1] hold the Dirichlet-node coefficients (used by aao_rhs only).
+  double *mL = nullptr, *mD = nullptr, *mU = nullptr;
+  double* gL = nullptr;   // left Dirichlet values at t_0..t_nt
+  double* gR = nullptr;   // right Dirichlet values
+  // preconditioner: tau * Abar diagonals, eigenvalue ratios mu_k = lambda1_k / lambda2_k,
+  // 1/lambda2_k, Lambda_alpha and (Lambda_alpha^{-1} / nt), twiddles exp(-2 pi i m / nt)
+  double *pL = nullptr, *pD = nullptr, *pU = nullptr;
+  float *pLf = nullptr, *pDf = nullptr, *pUf = nullptr;
+  double2 *mu = nullptr, *il2 = nullptr, *tw = nullptr;
+  float2 *muf = nullptr, *il2f = nullptr, *twf = nullptr;
+  double *lam = nullptr, *ilam = nullptr;
+  float *lamf = nullptr, *ilamf = nullptr;
+  void* spec = nullptr;   // half spectrum, K * pitch complex (float2 or double2)
+
+  // FGMRES workspace (grown on demand)
+  int ws_m = 0;
+  double* V = nullptr;    // (m+1) * n
+  void* Z = nullptr;      // m * n (float when mixed, double otherwise)
+  double* w = nullptr;    // n
+  double* scal = nullptr; // small device scalars (see krylov.cu)
+  double* part = nullptr; // block partial sums
+  int part_blocks = 0;
+  double* host_scal = nullptr;  // pinned mirror
+};
+
+// launchers (return AAO_* codes)
+int build_tables(Handle& h);
+int launch_precond(Handle& h, const double* v, void* z, bool z_is_float);
+int launch_matvec(Handle& h, const void* x, bool x_is_float, double* y, const double* b);
+int launch_rhs(Handle& h, double* b);
+int run_fgmres(Handle& h, const double* b, double* x, double tol, int m, int maxit, aao_stats* st);
+void free_handle(Handle& h);
+
+}  // namespace aao

@@ -1,0 +1,214 @@
+// C-ABI entry points (declared in include/aao.h): argument checks, handle lifetime, dispatch.
+#include <math.h>
+#include <stdio.h>
+
+#include <chrono>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "aao_internal.cuh"
+
+namespace aao {
+
+std::atomic<uint64_t> g_launches{0};
+static thread_local std::string t_last_error;
+
+void set_error(const std::string& msg) { t_last_error = msg; }
+
+std::atomic<int> g_prof_mask{0};
+namespace {
+struct ProfState {
+  std::mutex mu;
+  std::vector<cudaEvent_t> pool;                    // free events
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> done[AAO_K_COUNT];
+  double bytes[AAO_K_COUNT] = {};
+  cudaEvent_t open[AAO_K_COUNT] = {};
+};
+ProfState& prof() {
+  static ProfState* st = new ProfState();  // never destroyed: events may outlive static teardown
+  return *st;
+}
+cudaEvent_t take_event(ProfState& st) {
+  if (!st.pool.empty()) {
+    cudaEvent_t e = st.pool.back();
+    st.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+}  // namespace
+
+void prof_begin(int cls, cudaStream_t s) {
+  ProfState& st = prof();
+  std::lock_guard<std::mutex> lk(st.mu);
+  cudaEvent_t e = take_event(st);
+  cudaEventRecord(e, s);
+  st.open[cls] = e;
+}
+
+void prof_end(int cls, cudaStream_t s, double bytes) {
+  ProfState& st = prof();
+  std::lock_guard<std::mutex> lk(st.mu);
+  if (!st.open[cls]) return;
+  st.bytes[cls] += bytes;
+  cudaEvent_t e = take_event(st);
+  cudaEventRecord(e, s);
+  st.done[cls].emplace_back(st.open[cls], e);
+  st.open[cls] = nullptr;
+}
+
+namespace {
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int validate(const aao_problem* p) {
+  if (!p) { set_error("aao_create: null problem"); return AAO_EINVAL; }
+  if (p->nx < 2 || p->nt < 1) { set_error("aao_create: need nx >= 2 and nt >= 1"); return AAO_EINVAL; }
+  if (p->op == AAO_OP_RIESZ) { set_error("aao_create: the Riesz operator is not built in this library"); return AAO_EUNSUPPORTED; }
+  if (p->op != AAO_OP_BS && p->op != AAO_OP_LOCALVOL) { set_error("aao_create: unknown op"); return AAO_EINVAL; }
+  if (p->payoff != AAO_PUT && p->payoff != AAO_CALL) { set_error("aao_create: unknown payoff"); return AAO_EINVAL; }
+  if (p->precision != AAO_FP64 && p->precision != AAO_MIXED) { set_error("aao_create: unknown precision"); return AAO_EINVAL; }
+  if (!is_pow2(p->nt)) { set_error("aao_create: nt must be a power of two"); return AAO_EUNSUPPORTED; }
+  const int nt_max = p->precision == AAO_MIXED ? 16384 : 8192;
+  if (p->nt > nt_max) { set_error("aao_create: nt above the shared-memory FFT limit"); return AAO_EUNSUPPORTED; }
+  if (p->nx > 8191 * 4) { set_error("aao_create: nx above the shared-memory tridiagonal limit"); return AAO_EUNSUPPORTED; }
+  if (!(p->T > 0) || !(p->K > 0) || !(p->sigma > 0) || !(p->s_max > 0) || !(p->r >= 0)) {
+    set_error("aao_create: need T, K, sigma, s_max > 0 and r >= 0");
+    return AAO_EINVAL;
+  }
+  if (!(p->alpha > 0) || !(p->alpha <= 1)) { set_error("aao_create: need 0 < alpha <= 1"); return AAO_EINVAL; }
+  return AAO_OK;
+}
+
+}  // namespace
+}  // namespace aao
+
+struct aao_handle {
+  aao::Handle h;
+};
+
+using namespace aao;
+
+extern "C" {
+
+int aao_create(const aao_problem* p, aao_handle** out) {
+  if (!out) { set_error("aao_create: null handle pointer"); return AAO_EINVAL; }
+  *out = nullptr;
+  AAO_TRY(validate(p));
+  aao_handle* hd = new aao_handle();
+  Handle& h = hd->h;
+  h.p = *p;
+  h.stream = (cudaStream_t)p->stream;
+  h.nx = p->nx;
+  h.nt = p->nt;
+  h.K = p->nt / 2 + 1;
+  int l = 0;
+  while ((1 << l) < p->nt) ++l;
+  h.log2n = l;
+  h.pitch = ((p->nx + 63) / 64) * 64;
+  h.n = (size_t)p->nx * p->nt;
+  h.mixed = p->precision == AAO_MIXED;
+  int s = build_tables(h);
+  if (s != AAO_OK) {
+    free_handle(h);
+    delete hd;
+    return s;
+  }
+  *out = hd;
+  return AAO_OK;
+}
+
+int aao_destroy(aao_handle* hd) {
+  if (!hd) return AAO_OK;
+  cudaStreamSynchronize(hd->h.stream);
+  free_handle(hd->h);
+  delete hd;
+  return AAO_OK;
+}
+
+int aao_rhs(aao_handle* hd, double* b) {
+  if (!hd || !b) { set_error("aao_rhs: null argument"); return AAO_EINVAL; }
+  return launch_rhs(hd->h, b);
+}
+
+int aao_matvec(aao_handle* hd, const double* x, double* y) {
+  if (!hd || !x || !y) { set_error("aao_matvec: null argument"); return AAO_EINVAL; }
+  if (x == y) { set_error("aao_matvec: x and y must not alias"); return AAO_EINVAL; }
+  return launch_matvec(hd->h, x, false, y, nullptr);
+}
+
+int precond_apply(aao_handle* hd, const double* v, double* z) {
+  if (!hd || !v || !z) { set_error("precond_apply: null argument"); return AAO_EINVAL; }
+  return launch_precond(hd->h, v, z, false);
+}
+
+int fgmres_solve(aao_handle* hd, const double* b, double* x, double tol, int m, int maxit, aao_stats* st) {
+  if (!hd || !b || !x) { set_error("fgmres_solve: null argument"); return AAO_EINVAL; }
+  if (m < 1 || m > 64 || maxit < 1 || !(tol > 0)) { set_error("fgmres_solve: need 1 <= m <= 64, maxit >= 1, tol > 0"); return AAO_EINVAL; }
+  return run_fgmres(hd->h, b, x, tol, m, maxit, st);
+}
+
+int fgmres_solve_host(aao_handle* hd, const double* b_host, double* x_host, double tol, int m, int maxit,
+                      aao_stats* st) {
+  if (!hd || !b_host || !x_host) { set_error("fgmres_solve_host: null argument"); return AAO_EINVAL; }
+  if (m < 1 || m > 64 || maxit < 1 || !(tol > 0)) { set_error("fgmres_solve_host: need 1 <= m <= 64, maxit >= 1, tol > 0"); return AAO_EINVAL; }
+  Handle& h = hd->h;
+  const size_t bytes = sizeof(double) * h.n;
+  double *b = nullptr, *x = nullptr;
+  AAO_TRY_CUDA(cudaMallocAsync(&b, bytes, h.stream));
+  AAO_TRY_CUDA(cudaMallocAsync(&x, bytes, h.stream));
+  AAO_TRY_CUDA(cudaMemcpyAsync(b, b_host, bytes, cudaMemcpyHostToDevice, h.stream));
+  AAO_TRY_CUDA(cudaMemsetAsync(x, 0, bytes, h.stream));
+  int s = run_fgmres(h, b, x, tol, m, maxit, st);
+  cudaError_t e = cudaMemcpyAsync(x_host, x, bytes, cudaMemcpyDeviceToHost, h.stream);
+  cudaFreeAsync(b, h.stream);
+  cudaFreeAsync(x, h.stream);
+  cudaError_t e2 = cudaStreamSynchronize(h.stream);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    set_error(std::string("fgmres_solve_host: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    return AAO_ECUDA;
+  }
+  return s;
+}
+
+const char* aao_last_error(void) { return t_last_error.c_str(); }
+
+uint64_t aao_launch_count(void) { return g_launches.load(); }
+
+int aao_profile_enable(int mask) {
+  ProfState& st = prof();
+  std::lock_guard<std::mutex> lk(st.mu);
+  for (int c = 0; c < AAO_K_COUNT; ++c) {
+    for (auto& pr : st.done[c]) {
+      cudaEventSynchronize(pr.second);
+      st.pool.push_back(pr.first);
+      st.pool.push_back(pr.second);
+    }
+    st.done[c].clear();
+    st.bytes[c] = 0.0;
+  }
+  g_prof_mask.store(mask);
+  return AAO_OK;
+}
+
+int aao_profile_read(int cls, int64_t* launches, double* total_ms, double* bytes) {
+  if (cls < 0 || cls >= AAO_K_COUNT || !launches || !total_ms || !bytes) { set_error("aao_profile_read: bad argument"); return AAO_EINVAL; }
+  ProfState& st = prof();
+  std::lock_guard<std::mutex> lk(st.mu);
+  double tot = 0.0;
+  for (auto& pr : st.done[cls]) {
+    AAO_TRY_CUDA(cudaEventSynchronize(pr.second));
+    float ms = 0.f;
+    AAO_TRY_CUDA(cudaEventElapsedTime(&ms, pr.first, pr.second));
+    tot += ms;
+  }
+  *launches = (int64_t)st.done[cls].size();
+  *total_ms = tot;
+  *bytes = st.bytes[cls];
+  return AAO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,83 @@
+"""The C-ABI library builds, loads and exports every entry point include/aao.h declares;
+host-side argument checks reject bad problems before touching a GPU. CPU only."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2401_16113_gb300 import aao, build, workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for hdr in os.listdir(os.path.join(ROOT, "include")):
+        if not hdr.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", hdr)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"^\s*(?:int|const char\*|uint64_t|void)\s+\**\s*([A-Za-z_]\w*)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return aao.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert len(names) >= 9
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(aao.EXPORTS) <= set(names)
+
+
+def test_struct_layout_matches_header():
+    # int32 x 6, double x 9, pointer
+    assert ctypes.sizeof(aao.AaoProblem) == 6 * 4 + 9 * 8 + 8
+    assert aao.AaoProblem.alpha.offset == 24 + 8 * 8
+    assert ctypes.sizeof(aao.AaoStats) == 4 * 4 + 3 * 8
+
+
+def _create(lib, p):
+    h = ctypes.c_void_p()
+    return lib.aao_create(ctypes.byref(aao.make_problem(p)), ctypes.byref(h)), h
+
+
+@pytest.mark.parametrize("bad,code", [
+    (dict(nx=1), aao.AAO_EINVAL),
+    (dict(nt=0), aao.AAO_EINVAL),
+    (dict(nt=96), aao.AAO_EUNSUPPORTED),
+    (dict(alpha=0.0), aao.AAO_EINVAL),
+    (dict(alpha=1.5), aao.AAO_EINVAL),
+    (dict(sigma=-0.1), aao.AAO_EINVAL),
+    (dict(T=0.0), aao.AAO_EINVAL),
+    (dict(op="riesz"), aao.AAO_EUNSUPPORTED),
+    (dict(nt=16384, precision="fp64"), aao.AAO_EUNSUPPORTED),
+])
+def test_create_rejects_bad_problems_on_host(lib, bad, code):
+    rc, h = _create(lib, W.with_(W.bs_put_255x256(), **bad))
+    assert rc == code
+    assert h.value is None
+    assert lib.aao_last_error().decode()
+
+
+def test_null_arguments_rejected(lib):
+    assert lib.aao_create(None, None) == aao.AAO_EINVAL
+    assert lib.aao_matvec(None, None, None) == aao.AAO_EINVAL
+    assert lib.precond_apply(None, None, None) == aao.AAO_EINVAL
+    assert lib.fgmres_solve(None, None, None, 1e-8, 10, 10, None) == aao.AAO_EINVAL
+    assert lib.aao_destroy(None) == aao.AAO_OK
+
+
+def test_product_code_never_references_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2401_16113_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in src and "from oracle" not in src, f

@@ -1,0 +1,233 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on seeded inputs.
+
+Tolerances. FP64 entry points that are pure stencils (rhs, matvec) differ from the oracle
+only in rounding order: 1e-13 relative. The preconditioner apply multiplies rounding errors
+of the time-axis FFT (~u log2 nt) by up to 1/alpha through Lambda_alpha^{-1}; the bound used
+is ||z - z_ref|| <= C u log2(2 nt) / alpha ||z_ref|| with u the unit roundoff of the apply
+(2^-53 FP64, 2^-24 mixed) and C = 20.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import aao_oracle as O
+from paper_2401_16113_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+U64, U32 = 2.0 ** -53, 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def aao():
+    from paper_2401_16113_gb300 import aao as A, build
+    build.build()
+    A.load()
+    assert torch.cuda.is_available()
+    return A
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def relmax(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+BS = W.bs_put_255x256()
+LV = W.localvol_2047x2048("fp64")
+
+SHAPES = [(2, 1), (3, 2), (15, 16), (37, 8), (64, 64), (65, 32), (127, 128), (300, 256), (511, 64)]
+
+
+def problems(nx, nt):
+    return [W.with_(BS, nx=nx, nt=nt), W.with_(BS, nx=nx, nt=nt, payoff="call"),
+            W.with_(LV, nx=nx, nt=nt)]
+
+
+@pytest.mark.parametrize("nx,nt", SHAPES)
+def test_rhs_matches_oracle(aao, nx, nt):
+    for p in problems(nx, nt):
+        h = aao.aao_create(p)
+        b = torch.empty(nx * nt, dtype=torch.float64, device="cuda")
+        aao.aao_rhs(h, b)
+        ref = O.assemble_b(p)
+        assert relmax(host(b), ref) <= 1e-13, p
+        h.close()
+
+
+@pytest.mark.parametrize("nx,nt", SHAPES)
+def test_matvec_matches_oracle(aao, nx, nt):
+    for p in problems(nx, nt):
+        h = aao.aao_create(p)
+        x = W.random_vector(nx * nt, seed=nx + 7 * nt)
+        y = torch.empty(nx * nt, dtype=torch.float64, device="cuda")
+        aao.aao_matvec(h, dev(x), y)
+        ref = O.matvec(p, x)
+        assert relmax(host(y), ref) <= 1e-13, p
+        h.close()
+
+
+def precond_bound(p):
+    u = U32 if p["precision"] == "mixed" else U64
+    return 20.0 * u * math.log2(2 * p["nt"]) / p["alpha"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("alpha", [1e-2, 1e-3])
+@pytest.mark.parametrize("nx,nt", SHAPES)
+def test_precond_matches_oracle(aao, nx, nt, precision, alpha):
+    for p in problems(nx, nt):
+        p = W.with_(p, precision=precision, alpha=alpha)
+        h = aao.aao_create(p)
+        v = W.random_vector(nx * nt, seed=3 * nx + nt)
+        z = torch.empty(nx * nt, dtype=torch.float64, device="cuda")
+        aao.precond_apply(h, dev(v), z)
+        ref = O.precond_fft(p, v)
+        assert rel(host(z), ref) <= precond_bound(p), (p["op"], p["payoff"], rel(host(z), ref))
+        h.close()
+
+
+def test_precond_small_matches_dense_inverse(aao):
+    """Brute force: the dense P_alpha^{-1} of eq. (3.1), independent of any FFT."""
+    for nx, nt in [(5, 4), (7, 8), (9, 16)]:
+        for p in problems(nx, nt):
+            h = aao.aao_create(p)
+            v = W.random_vector(nx * nt, seed=nx * nt)
+            z = torch.empty(nx * nt, dtype=torch.float64, device="cuda")
+            aao.precond_apply(h, dev(v), z)
+            assert rel(host(z), O.precond_dense(p, v)) <= precond_bound(p)
+            h.close()
+
+
+def test_precond_in_place(aao):
+    p = W.with_(BS, nx=63, nt=32)
+    h = aao.aao_create(p)
+    v = W.random_vector(63 * 32, seed=1)
+    t = dev(v)
+    aao.precond_apply(h, t, t)
+    assert rel(host(t), O.precond_fft(p, v)) <= precond_bound(p)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_precond_full_size_localvol(aao, precision):
+    """2047 x 2048 local volatility, the launch configuration of the benchmark."""
+    p = W.with_(LV, precision=precision)
+    h = aao.aao_create(p)
+    v = W.random_vector(W.unknowns(p), seed=11)
+    z = torch.empty(W.unknowns(p), dtype=torch.float64, device="cuda")
+    aao.precond_apply(h, dev(v), z)
+    ref = O.precond_fft(p, v)
+    assert rel(host(z), ref) <= precond_bound(p)
+
+
+def test_fgmres_fp64_bs_put(aao):
+    """Plain FP64 solve of the 255 x 256 put to 1e-10: equals sequential CN and the
+    closed form within the discretisation error."""
+    p = BS
+    h = aao.aao_create(p)
+    n = W.unknowns(p)
+    b = torch.empty(n, dtype=torch.float64, device="cuda")
+    aao.aao_rhs(h, b)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    st = aao.fgmres_solve(h, b, x, 1e-10, 20, 200)
+    assert st["status"] == 0 and st["rel_residual"] <= 1e-10
+    xs = host(x)
+    M, bref = O.assemble_M(p), O.assemble_b(p)
+    assert np.linalg.norm(bref - M @ xs) <= 1.01e-10 * np.linalg.norm(bref)
+    U = O.sequential_cn(p)
+    assert relmax(xs, U.ravel()) <= 1e-8
+    S, _ = O.spatial_grid(p)
+    sel = (S >= 50) & (S <= 150)
+    assert np.abs(xs.reshape(p["nt"], p["nx"])[-1][sel]
+                  - O.bs_price(S[sel], p["K"], p["r"], p["sigma"], p["T"], "put")).max() < 1e-2
+    assert st["iterations"] <= 10
+
+
+def test_fgmres_mixed_localvol_full_size(aao):
+    """Mixed precision 2047 x 2048 local volatility to relative residual 1e-8 (FP64 check)."""
+    p = W.localvol_2047x2048("mixed")
+    h = aao.aao_create(p)
+    n = W.unknowns(p)
+    b = torch.empty(n, dtype=torch.float64, device="cuda")
+    aao.aao_rhs(h, b)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    st = aao.fgmres_solve(h, b, x, 1e-8, 30, 300)
+    assert st["status"] == 0 and st["rel_residual"] <= 1e-8, st
+    xs = host(x)
+    M, bref = O.assemble_M(p), O.assemble_b(p)
+    assert np.linalg.norm(bref - M @ xs) <= 1.01e-8 * np.linalg.norm(bref)
+    U = O.sequential_cn(p)
+    err = np.abs(xs.reshape(p["nt"], p["nx"])[-1] - U[-1]).max() / np.abs(U[-1]).max()
+    print("mixed localvol: its", st["iterations"], "maturity error", err)
+    assert err <= 1e-7
+
+
+def test_fgmres_host_variant_matches_device(aao):
+    p = W.with_(BS, nx=127, nt=128, precision="mixed", alpha=1e-3)
+    h = aao.aao_create(p)
+    n = W.unknowns(p)
+    b = torch.empty(n, dtype=torch.float64, device="cuda")
+    aao.aao_rhs(h, b)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    st = aao.fgmres_solve(h, b, x, 1e-9, 20, 100)
+    bh = host(b).copy()
+    xh = np.zeros(n)
+    st2 = aao.fgmres_solve_host(h, bh, xh, 1e-9, 20, 100)
+    assert st2["iterations"] == st["iterations"]
+    assert np.array_equal(xh, host(x))
+
+
+def test_fgmres_restart_small_m(aao):
+    p = W.with_(BS, nx=63, nt=64)
+    h = aao.aao_create(p)
+    n = W.unknowns(p)
+    b = torch.empty(n, dtype=torch.float64, device="cuda")
+    aao.aao_rhs(h, b)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    st = aao.fgmres_solve(h, b, x, 1e-12, 1, 400)
+    assert st["status"] == 0 and st["restarts"] >= 2
+    ref, _ = O.solve(W.with_(p, tol=1e-12))
+    assert relmax(host(x), ref) <= 1e-9
+
+
+def test_fgmres_maxit_reports_not_converged(aao):
+    p = W.with_(BS, nx=63, nt=64, alpha=1.0)
+    h = aao.aao_create(p)
+    n = W.unknowns(p)
+    b = torch.empty(n, dtype=torch.float64, device="cuda")
+    aao.aao_rhs(h, b)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    st = aao.fgmres_solve(h, b, x, 1e-14, 5, 3)
+    assert st["status"] == aao.AAO_NOT_CONVERGED and st["iterations"] == 3
+
+
+def test_fgmres_zero_rhs(aao):
+    p = W.with_(BS, nx=31, nt=16)
+    h = aao.aao_create(p)
+    b = torch.zeros(31 * 16, dtype=torch.float64, device="cuda")
+    x = torch.ones(31 * 16, dtype=torch.float64, device="cuda")
+    st = aao.fgmres_solve(h, b, x, 1e-10, 10, 10)
+    assert st["status"] == 0 and float(x.abs().max()) == 0.0
+
+
+def test_fgmres_nan_rhs_reports_breakdown(aao):
+    p = W.with_(BS, nx=31, nt=16)
+    h = aao.aao_create(p)
+    b = torch.ones(31 * 16, dtype=torch.float64, device="cuda")
+    b[17] = float("nan")
+    x = torch.zeros(31 * 16, dtype=torch.float64, device="cuda")
+    st = aao.fgmres_solve(h, b, x, 1e-10, 10, 10)
+    assert st["status"] == aao.AAO_BREAKDOWN
