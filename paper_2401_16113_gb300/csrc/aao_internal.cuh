@@ -110,6 +110,7 @@ struct Handle {
   double *lam = nullptr, *ilam = nullptr;
   float *lamf = nullptr, *ilamf = nullptr;
   void* spec = nullptr;   // half spectrum, K * pitch complex (float2 or double2)
+  int fft_p = 0;          // FFT tile: 2*fft_p spatial columns per CTA (0 = heuristic)
 
   // FGMRES workspace (grown on demand)
   int ws_m = 0;
@@ -118,14 +119,17 @@ struct Handle {
   double* w = nullptr;    // n
   double* scal = nullptr; // small device scalars (see krylov.cu)
   double* part = nullptr; // block partial sums
+  unsigned int* counter = nullptr;  // completion counter of the last-block reductions
   int part_blocks = 0;
   double* host_scal = nullptr;  // pinned mirror
 };
 
 // launchers (return AAO_* codes)
 int build_tables(Handle& h);
-int launch_precond(Handle& h, const double* v, void* z, bool z_is_float);
-int launch_matvec(Handle& h, const void* x, bool x_is_float, double* y, const double* b);
+int launch_precond(Handle& h, const double* v, void* z, bool z_is_float, const double* in_scale = nullptr);
+int tune_precond(Handle& h);
+int launch_matvec(Handle& h, const void* x, bool x_is_float, double* y, const double* b, const double* V = nullptr,
+                  int nd = 0, int m = 0);
 int launch_rhs(Handle& h, double* b);
 int run_fgmres(Handle& h, const double* b, double* x, double tol, int m, int maxit, aao_stats* st);
 void free_handle(Handle& h);

@@ -74,7 +74,8 @@ int validate(const aao_problem* p) {
   if (!is_pow2(p->nt)) { set_error("aao_create: nt must be a power of two"); return AAO_EUNSUPPORTED; }
   const int nt_max = p->precision == AAO_MIXED ? 16384 : 8192;
   if (p->nt > nt_max) { set_error("aao_create: nt above the shared-memory FFT limit"); return AAO_EUNSUPPORTED; }
-  if (p->nx > 8191 * 4) { set_error("aao_create: nx above the shared-memory tridiagonal limit"); return AAO_EUNSUPPORTED; }
+  const int nx_max = p->precision == AAO_MIXED ? 8192 : 4096;
+  if (p->nx > nx_max) { set_error("aao_create: nx above the tridiagonal solver's limit (8192 mixed, 4096 FP64)"); return AAO_EUNSUPPORTED; }
   if (!(p->T > 0) || !(p->K > 0) || !(p->sigma > 0) || !(p->s_max > 0) || !(p->r >= 0)) {
     set_error("aao_create: need T, K, sigma, s_max > 0 and r >= 0");
     return AAO_EINVAL;
@@ -112,6 +113,7 @@ int aao_create(const aao_problem* p, aao_handle** out) {
   h.n = (size_t)p->nx * p->nt;
   h.mixed = p->precision == AAO_MIXED;
   int s = build_tables(h);
+  if (s == AAO_OK) s = tune_precond(h);
   if (s != AAO_OK) {
     free_handle(h);
     delete hd;

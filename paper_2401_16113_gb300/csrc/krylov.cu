@@ -5,11 +5,20 @@
 //   k_rhs         b = xi + tau f (Eq. 2.2).
 //   k_matvec      y = M x, block-bidiagonal M = B1 (x) I - B2 (x) A~ (Eq. 2.2; Eq. 5.8 form for
 //                 time-dependent A): y_t = (x_t - x_{t-1}) - (1/2) A~_t (x_t + x_{t-1}), FP64;
-//                 optionally r = b - M x with block partial sums of r.r.
-//   k_mdot / k_update / k_vnext / k_givens / k_lsq / k_xupdate
-//                 right-preconditioned flexible GMRES(m) (Sec. 5): classical Gram-Schmidt
-//                 applied twice, Givens rotations, FP64 throughout. Block partial sums are
-//                 reduced in a fixed order, so results are deterministic.
+//                 fused with the residual norm or with the first Gram-Schmidt projections.
+//   k_update / k_mdot / k_xupdate / k_dot_self
+//                 right-preconditioned flexible GMRES(m) (Sec. 5), FP64.
+//
+// FP64 is 1/64 of the FP32 rate on this part, so the Arnoldi process is arranged to issue as
+// few FP64 instructions as possible:
+//  * the Krylov basis is stored unnormalised (raw vectors V_i with scales sigma_i = 1/||V_i||);
+//    the preconditioner reads sigma_j V_j (the scale is folded into its first kernel) and every
+//    other normalisation into the Hessenberg scalars, so no pass rescales vectors;
+//  * classical Gram-Schmidt runs once; a second pass (CGS2) runs only when cancellation
+//    ||w'|| < kReorthEta ||w|| would lose more than ~1e-11 of orthogonality;
+//  * block partial sums are finished by the last block of the producing kernel, in a fixed
+//    order (deterministic), and the Givens update runs in that block as well;
+//  * FP32 values are widened to FP64 by integer bit assembly, off the FP64 pipe.
 #include <math.h>
 #include <stdio.h>
 
@@ -23,30 +32,44 @@ namespace aao {
 
 namespace {
 
-constexpr int kRedBlocks = 1216;  // 152 SMs x 8: partial-sum blocks of the reductions
+constexpr int kRedBlocks = 1216;   // 152 SMs x 8: blocks of the grid-stride kernels
+constexpr int kPartBlocks = 4096;  // capacity (blocks) of the partial-sum buffer
+constexpr int kPartLd = 16;        // partial sums per block
 constexpr int kThreads = 256;
+constexpr double kReorthEta = 1e-5;
 
 // device scalar slots (offsets into Handle::scal)
 enum : int {
-  S_H1 = 0,        // 128 first-pass projections
-  S_H2 = 128,      // 128 second-pass projections
-  S_NRM2 = 256,    // ||w'||^2
-  S_EST = 257,     // |g_{j+1}|
-  S_HN = 258,      // h_{j+1,j}
-  S_INVHN = 259,   // 1 / h_{j+1,j}
-  S_BETA2 = 260,   // ||r||^2
-  S_INVB = 261,    // 1 / ||r||
-  S_FLAG = 262,    // non-finite detected
-  S_G = 320,       // g (m+1)
-  S_CS = 400,      // cosines (m)
-  S_SN = 480,      // sines (m)
-  S_Y = 560,       // least-squares solution (m)
-  S_HMAT = 640,    // Hessenberg, column-major (m+1) x m, ld 65
-  S_TOTAL = 640 + 65 * 64
+  S_D1 = 0,       // raw first-pass projections V_i . w
+  S_D2 = 128,     // raw second-pass projections
+  S_SIG = 256,    // sigma_i = 1 / ||V_i||, i = 0..m
+  S_WN2 = 330,    // ||w||^2 before orthogonalisation
+  S_WP2 = 331,    // ||w'||^2 after the last pass
+  S_EST = 332,    // |g_{j+1}| (residual estimate)
+  S_HN = 333,     // h_{j+1,j}
+  S_FLAG = 334,   // non-finite value seen
+  S_REORTH = 335, // second pass requested
+  S_BETA2 = 336,  // ||r||^2
+  S_BNORM2 = 337, // ||b||^2
+  S_G = 340,      // g, m+1
+  S_CS = 420,     // Givens cosines, m
+  S_SN = 500,     // Givens sines, m
+  S_HMAT = 580,   // Hessenberg, column-major (m+1) x m, ld 65
+  S_TOTAL = 580 + 65 * 64
 };
 constexpr int kLdH = 65;
 
-template <typename T> __device__ __forceinline__ double ld(const T* p) { return (double)__ldg(p); }
+// exact float -> double by bit assembly (normal numbers and zero; subnormals via hardware)
+__device__ __forceinline__ double widen(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned e = (b >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) return (double)f;
+  const unsigned hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3);
+  return __hiloint2double((int)hi, (int)(b << 29));
+}
+__device__ __forceinline__ double widen(double d) { return d; }
+
+template <typename T> __device__ __forceinline__ double ld(const T* p) { return widen(__ldg(p)); }
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -72,6 +95,39 @@ __device__ __forceinline__ void block_sums(const double (&acc)[CNT], int cnt, do
     out[threadIdx.x] = s;
   }
   __syncthreads();
+}
+
+// After every block wrote its partial sums: true in the block that finishes last.
+__device__ __forceinline__ bool last_block(unsigned int* counter, unsigned int nblocks) {
+  __shared__ bool am_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) am_last = atomicAdd(counter, 1u) == nblocks - 1;
+  __syncthreads();
+  if (am_last) __threadfence();
+  return am_last;
+}
+
+// Executed by the last block: out(q) = sum over blocks b = 0..nblk-1 of part[b*ld + q], in a
+// fixed order; resets the counter for the next kernel.
+template <typename OUT>
+__device__ void finish_sums(const double* part, int nblk, int cnt, OUT out, unsigned int* counter) {
+  __shared__ double red[kThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int q = 0; q < cnt; ++q) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += __ldcg(part + (size_t)b * kPartLd + q);
+    s = warp_sum(s);
+    if (lane == 0) red[warp] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int wv = 0; wv < kThreads / 32; ++wv) t += red[wv];
+      out(q, t);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *counter = 0u;
 }
 
 __global__ void k_build_coef(double* __restrict__ L, double* __restrict__ D, double* __restrict__ U, int nx,
@@ -120,125 +176,127 @@ __global__ void k_rhs(double* __restrict__ b, int nx, int nt, const double* __re
   }
 }
 
-// y = M x  (b == nullptr)   or   y = b - M x with partial sums of y.y  (b != nullptr)
-template <typename IN>
+// y = M x, tiled: warp w of a block owns 32 consecutive spatial columns and walks a chunk of
+// tc time levels, keeping level t-1 in registers; spatial neighbours of s = x_t + x_{t-1} come
+// from lane shuffles (halo columns loaded by lanes 0 and 31). Five FP64 operations per unknown:
+//   y_t,i = (x_t - x_{t-1})_i - [L s_{i-1} + D s_i + U s_{i+1}],  (L, D, U) = tau/2 A_t row i.
+// MODE 0: y = M x.
+// MODE 1: y = b - M x (the restart residual, written as the raw first basis vector); the last
+//         block sets ||r||^2, sigma_0 = 1/||r|| and g = (||r||, 0, ...).
+// MODE 2: y = M x, the first Gram-Schmidt projections d_q = V_q . y (q < nd <= 8) and ||y||^2,
+//         finished by the last block into scal[S_D1 + q] and scal[S_WN2].
+template <typename IN, int MODE>
 __global__ void __launch_bounds__(kThreads) k_matvec(const IN* __restrict__ x, double* __restrict__ y,
-                                                     const double* __restrict__ b, int nx, int nt,
+                                                     const double* __restrict__ b, int nx, int nt, int tc,
                                                      const double* __restrict__ L, const double* __restrict__ D,
                                                      const double* __restrict__ U, int rows,
-                                                     double* __restrict__ part) {
-  const size_t n = (size_t)nx * nt;
-  double acc[1] = {0.0};
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    const int t = (int)(e / nx), i = (int)(e - (size_t)t * nx);
-    const size_t c = (rows == 1) ? (size_t)i : e;
-    const double xc = ld(x + e);
-    const double xl = i > 0 ? ld(x + e - 1) : 0.0;
-    const double xr = i < nx - 1 ? ld(x + e + 1) : 0.0;
-    double pc = 0.0, pl = 0.0, pr = 0.0;
-    if (t > 0) {
-      pc = ld(x + e - nx);
-      pl = i > 0 ? ld(x + e - nx - 1) : 0.0;
-      pr = i < nx - 1 ? ld(x + e - nx + 1) : 0.0;
-    }
-    double v = xc - pc;
-    v = fma(-__ldg(L + c), xl + pl, v);
-    v = fma(-__ldg(D + c), xc + pc, v);
-    v = fma(-__ldg(U + c), xr + pr, v);
-    if (b) {
-      v = __ldg(b + e) - v;
-      acc[0] = fma(v, v, acc[0]);
-    }
-    y[e] = v;
+                                                     const double* __restrict__ V, int nd, size_t vstride,
+                                                     double* __restrict__ part, double* __restrict__ scal,
+                                                     unsigned int* __restrict__ counter, int m) {
+  constexpr int NA = MODE == 2 ? 9 : 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i0 = (blockIdx.x * (kThreads / 32) + warp) * 32;
+  const int i = i0 + lane;
+  const bool act = i < nx;
+  const int t0 = blockIdx.y * tc;
+  const int t1 = min(nt, t0 + tc);
+  double acc[NA];
+#pragma unroll
+  for (int q = 0; q < NA; ++q) acc[q] = 0.0;
+  double xp = 0.0, xpl = 0.0, xpr = 0.0;
+  if (t0 > 0) {
+    const size_t r = (size_t)(t0 - 1) * nx;
+    if (act) xp = ld(x + r + i);
+    if (lane == 0 && i0 > 0 && i0 - 1 < nx) xpl = ld(x + r + i0 - 1);
+    if (lane == 31 && i0 + 32 < nx) xpr = ld(x + r + i0 + 32);
   }
-  if (b) block_sums<1>(acc, 1, part + blockIdx.x);
+  for (int t = t0; t < t1; ++t) {
+    const size_t r = (size_t)t * nx;
+    const double xc = act ? ld(x + r + i) : 0.0;
+    const double s = xc + xp, d = xc - xp;
+    double sl = __shfl_up_sync(0xffffffffu, s, 1);
+    double sr = __shfl_down_sync(0xffffffffu, s, 1);
+    if (lane == 0) {
+      const double xl = (i0 > 0 && i0 - 1 < nx) ? ld(x + r + i0 - 1) : 0.0;
+      sl = xl + xpl;
+      xpl = xl;
+    }
+    if (lane == 31) {
+      const double xr = (i0 + 32 < nx) ? ld(x + r + i0 + 32) : 0.0;
+      sr = xr + xpr;
+      xpr = xr;
+    }
+    if (act) {
+      const size_t c = rows == 1 ? (size_t)i : r + i;
+      double v = fma(-__ldg(L + c), sl, d);
+      v = fma(-__ldg(D + c), s, v);
+      v = fma(-__ldg(U + c), sr, v);
+      if (MODE == 1) {
+        v = __ldg(b + r + i) - v;
+        acc[0] = fma(v, v, acc[0]);
+      }
+      y[r + i] = v;
+      if (MODE == 2) {
+#pragma unroll
+        for (int q = 0; q < NA - 1; ++q)
+          if (q < nd) acc[q] = fma(__ldg(V + (size_t)q * vstride + r + i), v, acc[q]);
+        acc[NA - 1] = fma(v, v, acc[NA - 1]);
+      }
+    }
+    xp = xc;
+  }
+  if constexpr (MODE == 0) return;
+  const unsigned int nblk = gridDim.x * gridDim.y;
+  const unsigned int bid = blockIdx.y * gridDim.x + blockIdx.x;
+  if constexpr (MODE == 2) {
+    double out[NA];
+#pragma unroll
+    for (int q = 0; q < NA; ++q) out[q] = q < nd ? acc[q] : (q == nd ? acc[NA - 1] : 0.0);
+    block_sums<NA>(out, nd + 1, part + (size_t)bid * kPartLd);
+  } else {
+    block_sums<NA>(acc, 1, part + (size_t)bid * kPartLd);
+  }
+  if (!last_block(counter, nblk)) return;
+  if constexpr (MODE == 2) {
+    finish_sums(part, nblk, nd + 1, [&](int q, double v) { scal[q < nd ? S_D1 + q : S_WN2] = v; }, counter);
+  } else {
+    finish_sums(part, nblk, 1, [&](int, double v) {
+      scal[S_BETA2] = v;
+      const double beta = sqrt(v);
+      scal[S_SIG] = beta > 0.0 ? 1.0 / beta : 0.0;
+      scal[S_G] = beta;
+      for (int k = 1; k <= m; ++k) scal[S_G + k] = 0.0;
+      scal[S_FLAG] = isfinite(v) ? 0.0 : 1.0;
+    }, counter);
+  }
 }
 
-// part[blk * nv + i] = sum over the block's elements of V_i . w  (nv <= 8 per launch chunk)
-__global__ void __launch_bounds__(kThreads) k_mdot(const double* __restrict__ V, int nv, size_t n,
+// out[c0 + q] = V_{c0+q} . w for q < nv (chunk of <= 8 basis vectors), finished by the last block
+__global__ void __launch_bounds__(kThreads) k_mdot(const double* __restrict__ V, int c0, int nv, size_t n,
                                                    const double* __restrict__ w, double* __restrict__ part,
-                                                   int part_ld) {
+                                                   double* __restrict__ out, unsigned int* __restrict__ counter) {
   double acc[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+  const double* Vc = V + (size_t)c0 * n;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     const double wv = __ldg(w + e);
 #pragma unroll
     for (int q = 0; q < 8; ++q)
-      if (q < nv) acc[q] = fma(__ldg(V + (size_t)q * n + e), wv, acc[q]);
+      if (q < nv) acc[q] = fma(__ldg(Vc + (size_t)q * n + e), wv, acc[q]);
   }
-  block_sums<8>(acc, nv, part + (size_t)blockIdx.x * part_ld);
+  block_sums<8>(acc, nv, part + (size_t)blockIdx.x * kPartLd);
+  if (!last_block(counter, gridDim.x)) return;
+  finish_sums(part, gridDim.x, nv, [&](int q, double v) { out[c0 + q] = v; }, counter);
 }
 
-// w <- w - sum_i h_i V_i ; part[blk*ld + i] = V_i . w (i < nv, chunked by 8) and part[.. + nv] = w.w
-__global__ void __launch_bounds__(kThreads) k_update(double* __restrict__ w, const double* __restrict__ V,
-                                                     int nv, size_t n, const double* __restrict__ hc,
-                                                     double* __restrict__ part, int part_ld) {
-  __shared__ double hs[128];
-  for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = hc[i];
-  __syncthreads();
-  for (int c0 = 0; c0 <= nv; c0 += 8) {
-    double acc[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) acc[q] = 0.0;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-      double wv;
-      if (c0 == 0) {
-        wv = w[e];
-        for (int i = 0; i < nv; ++i) wv = fma(-hs[i], __ldg(V + (size_t)i * n + e), wv);
-        w[e] = wv;
-      } else {
-        wv = w[e];
-      }
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int i = c0 + q;
-        if (i < nv) acc[q] = fma(__ldg(V + (size_t)i * n + e), wv, acc[q]);
-        else if (i == nv) acc[q] = fma(wv, wv, acc[q]);
-      }
-    }
-    const int cnt = (nv + 1 - c0) < 8 ? (nv + 1 - c0) : 8;
-    block_sums<8>(acc, cnt, part + (size_t)blockIdx.x * part_ld + c0);
-  }
-}
-
-// out[i] = sum_blk part[blk*ld + i], fixed order; one warp per value
-__global__ void k_reduce(const double* __restrict__ part, int nblk, int cnt, int ld, double* __restrict__ out) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (warp >= cnt) return;
-  double s = 0.0;
-  for (int b = lane; b < nblk; b += 32) s += part[(size_t)b * ld + warp];
-  s = warp_sum(s);
-  if (lane == 0) out[warp] = s;
-}
-
-// v_next = (w - sum_i h2_i V_i) / h_{j+1,j}
-__global__ void __launch_bounds__(kThreads) k_vnext(const double* __restrict__ w, const double* __restrict__ V,
-                                                    int nv, size_t n, const double* __restrict__ scal,
-                                                    double* __restrict__ out) {
-  __shared__ double hs[128];
-  for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = scal[S_H2 + i];
-  __syncthreads();
-  const double inv = scal[S_INVHN];
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    double wv = __ldg(w + e);
-    for (int i = 0; i < nv; ++i) wv = fma(-hs[i], __ldg(V + (size_t)i * n + e), wv);
-    out[e] = wv * inv;
-  }
-}
-
-// Hessenberg column j from the two Gram-Schmidt passes, previous rotations, new rotation.
-__global__ void k_givens(double* __restrict__ scal, int j) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// Givens update of Hessenberg column j. w = M z_j with z_j = P^{-1} v_j for the normalised
+// v_j = sigma_j V_j, so h_ij = v_i . w = sigma_i d_i and h_{j+1,j} = ||w'||; one thread.
+__device__ void givens_column(double* __restrict__ scal, int j, const double* d1, const double* d2) {
   double* H = scal + S_HMAT + (size_t)j * kLdH;
-  double h2n = 0.0;
-  for (int i = 0; i <= j; ++i) {
-    const double a = scal[S_H1 + i], c = scal[S_H2 + i];
-    H[i] = a + c;
-    h2n += c * c;
-  }
-  double hn2 = scal[S_NRM2] - h2n;
-  const double hn = hn2 > 0.0 ? sqrt(hn2) : 0.0;
+  for (int i = 0; i <= j; ++i) H[i] = scal[S_SIG + i] * (d1[i] + (d2 ? d2[i] : 0.0));
+  const double wn = sqrt(fmax(scal[S_WP2], 0.0));
+  const double hn = wn;
   H[j + 1] = hn;
   for (int i = 0; i < j; ++i) {
     const double a = H[i], c = H[i + 1];
@@ -256,67 +314,90 @@ __global__ void k_givens(double* __restrict__ scal, int j) {
   scal[S_G + j] = cs * g;
   scal[S_EST] = fabs(sn * g);
   scal[S_HN] = hn;
-  scal[S_INVHN] = hn > 0.0 ? 1.0 / hn : 0.0;
+  scal[S_SIG + j + 1] = wn > 0.0 ? 1.0 / wn : 0.0;
   if (!isfinite(rho) || !isfinite(hn)) scal[S_FLAG] = 1.0;
 }
 
-// y = H(0:jd, 0:jd)^{-1} g(0:jd), upper triangular after the rotations
-__global__ void k_lsq(double* __restrict__ scal, int jd) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  for (int i = jd - 1; i >= 0; --i) {
-    double s = scal[S_G + i];
-    for (int k = i + 1; k < jd; ++k) s -= scal[S_HMAT + (size_t)k * kLdH + i] * scal[S_Y + k];
-    scal[S_Y + i] = s / scal[S_HMAT + (size_t)i * kLdH + i];
+// Gram-Schmidt pass `pass` (1 or 2) on w (the raw vector V_{j+1}, updated in place):
+//   w <- w - sum_{i<=j} sigma_i^2 d_i V_i,  d = scal[S_D1] (pass 1) or scal[S_D2] (pass 2),
+// then ||w||^2 -> scal[S_WP2]. The last block decides: after pass 1 a second pass is requested
+// (scal[S_REORTH] = 1) when ||w'||^2 < eta^2 ||w||^2; otherwise the Givens update of column j runs.
+template <int NV>
+__global__ void __launch_bounds__(kThreads) k_update(double* __restrict__ w, const double* __restrict__ V,
+                                                     int j, size_t n, int pass, double* __restrict__ scal,
+                                                     double* __restrict__ part, unsigned int* __restrict__ counter) {
+  __shared__ double cf[128];
+  const int nv = j + 1;
+  const int off = pass == 1 ? S_D1 : S_D2;
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+    const double si = scal[S_SIG + i];
+    cf[i] = si * si * scal[off + i];
   }
+  __syncthreads();
+  double acc[1] = {0.0};
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    double wv = w[e];
+    if (NV > 0) {
+#pragma unroll
+      for (int q = 0; q < (NV > 0 ? NV : 1); ++q)
+        if (q < nv) wv = fma(-cf[q], __ldg(V + (size_t)q * n + e), wv);
+    } else {
+      for (int q = 0; q < nv; ++q) wv = fma(-cf[q], __ldg(V + (size_t)q * n + e), wv);
+    }
+    w[e] = wv;
+    acc[0] = fma(wv, wv, acc[0]);
+  }
+  block_sums<1>(acc, 1, part + (size_t)blockIdx.x * kPartLd);
+  if (!last_block(counter, gridDim.x)) return;
+  finish_sums(part, gridDim.x, 1, [&](int, double v) {
+    scal[S_WP2] = v;
+    if (pass == 1 && v < kReorthEta * kReorthEta * scal[S_WN2]) {
+      scal[S_REORTH] = 1.0;
+    } else {
+      scal[S_REORTH] = 0.0;
+      givens_column(scal, j, scal + S_D1, pass == 2 ? scal + S_D2 : nullptr);
+    }
+  }, counter);
 }
 
-// x += sum_i y_i Z_i
+// x += sum_{i<jd} y_i Z_i with y = H(0:jd,0:jd)^{-1} g(0:jd) (each block solves the small
+// triangular system itself); Z_i = P^{-1} v_i for the normalised basis vectors v_i
 template <typename ZT>
 __global__ void __launch_bounds__(kThreads) k_xupdate(double* __restrict__ x, const ZT* __restrict__ Z, int jd,
                                                       size_t n, const double* __restrict__ scal) {
   __shared__ double ys[128];
-  for (int i = threadIdx.x; i < jd; i += blockDim.x) ys[i] = scal[S_Y + i];
+  if (threadIdx.x == 0) {
+    for (int i = jd - 1; i >= 0; --i) {
+      double s = scal[S_G + i];
+      for (int k = i + 1; k < jd; ++k) s -= scal[S_HMAT + (size_t)k * kLdH + i] * ys[k];
+      ys[i] = s / scal[S_HMAT + (size_t)i * kLdH + i];
+    }
+  }
   __syncthreads();
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     double v = x[e];
-    for (int i = 0; i < jd; ++i) v = fma(ys[i], (double)__ldg(Z + (size_t)i * n + e), v);
+    for (int i = 0; i < jd; ++i) v = fma(ys[i], ld(Z + (size_t)i * n + e), v);
     x[e] = v;
   }
 }
 
-// v = r / ||r||, starts a cycle: g = (beta, 0, ...)
-__global__ void __launch_bounds__(kThreads) k_start(const double* __restrict__ r, double* __restrict__ v, size_t n,
-                                                    double* __restrict__ scal, int m) {
-  const double beta = sqrt(scal[S_BETA2]);
-  const double inv = beta > 0.0 ? 1.0 / beta : 0.0;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
-    v[e] = r[e] * inv;
-  if (blockIdx.x == 0 && threadIdx.x <= m) scal[S_G + threadIdx.x] = threadIdx.x == 0 ? beta : 0.0;
-  if (blockIdx.x == 0 && threadIdx.x == 0) scal[S_FLAG] = 0.0;
-}
-
-__global__ void __launch_bounds__(kThreads) k_dot_self(const double* __restrict__ v, size_t n, double* part) {
+// scal[slot] = v . v
+__global__ void __launch_bounds__(kThreads) k_dot_self(const double* __restrict__ v, size_t n, double* part,
+                                                       double* __restrict__ scal, int slot,
+                                                       unsigned int* __restrict__ counter) {
   double acc[1] = {0.0};
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     const double a = __ldg(v + e);
     acc[0] = fma(a, a, acc[0]);
   }
-  block_sums<1>(acc, 1, part + blockIdx.x);
+  block_sums<1>(acc, 1, part + (size_t)blockIdx.x * kPartLd);
+  if (!last_block(counter, gridDim.x)) return;
+  finish_sums(part, gridDim.x, 1, [&](int, double s) { scal[slot] = s; }, counter);
 }
 
 int grid_for(size_t n) {
   size_t g = (n + kThreads - 1) / kThreads;
   return (int)(g < (size_t)kRedBlocks ? g : (size_t)kRedBlocks);
-}
-
-int reduce_to(Handle& h, int nblk, int cnt, int ld, double* out) {
-  const int warps = cnt;
-  const int threads = 256;
-  const int blocks = (warps * 32 + threads - 1) / threads;
-  ProfScope ps(AAO_K_OTHER, h.stream, 8.0 * (double)nblk * cnt);
-  k_reduce<<<blocks, threads, 0, h.stream>>>(h.part, nblk, cnt, ld, out);
-  AAO_CHECK_LAUNCH();
-  return AAO_OK;
 }
 
 int ensure_workspace(Handle& h, int m) {
@@ -444,8 +525,10 @@ int build_tables(Handle& h) {
   AAO_TRY_CUDA(cudaMalloc(&h.w, sizeof(double) * h.n));
   AAO_TRY_CUDA(cudaMalloc(&h.scal, sizeof(double) * S_TOTAL));
   AAO_TRY_CUDA(cudaMemsetAsync(h.scal, 0, sizeof(double) * S_TOTAL, h.stream));
+  AAO_TRY_CUDA(cudaMalloc(&h.counter, sizeof(unsigned int) * 4));
+  AAO_TRY_CUDA(cudaMemsetAsync(h.counter, 0, sizeof(unsigned int) * 4, h.stream));
   h.part_blocks = kRedBlocks;
-  AAO_TRY_CUDA(cudaMalloc(&h.part, sizeof(double) * (size_t)kRedBlocks * 136));
+  AAO_TRY_CUDA(cudaMalloc(&h.part, sizeof(double) * (size_t)kPartBlocks * kPartLd));
   AAO_TRY_CUDA(cudaMallocHost(&h.host_scal, sizeof(double) * 8));
   // the temporary gS buffer must outlive the build kernel
   AAO_TRY_CUDA(cudaStreamSynchronize(h.stream));
@@ -455,7 +538,8 @@ int build_tables(Handle& h) {
 
 void free_handle(Handle& h) {
   void* bufs[] = {h.mL, h.mD, h.mU, h.gL, h.gR, h.pL, h.pD, h.pU, h.pLf, h.pDf, h.pUf, h.mu, h.il2, h.tw,
-                  h.muf, h.il2f, h.twf, h.lam, h.ilam, h.lamf, h.ilamf, h.spec, h.V, h.Z, h.w, h.scal, h.part};
+                  h.muf, h.il2f, h.twf, h.lam, h.ilam, h.lamf, h.ilamf, h.spec, h.V, h.Z, h.w, h.scal, h.part,
+                  h.counter};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (h.host_scal) cudaFreeHost(h.host_scal);
@@ -465,19 +549,46 @@ void free_handle(Handle& h) {
 // operator launches
 // ----------------------------------------------------------------------------------------
 
-int launch_matvec(Handle& h, const void* x, bool x_is_float, double* y, const double* b) {
-  const int g = grid_for(h.n);
-  const double nn = (double)h.n;
-  // x once, coefficients (3 per row of the time-dependent operator), y, and b if present
-  const double bytes = nn * (x_is_float ? 4.0 : 8.0) + 3.0 * 8.0 * (double)h.nx * h.coef_rows + nn * 8.0 +
-                       (b ? nn * 8.0 : 0.0);
+namespace {
+
+// time-chunk length: enough blocks to fill the GPU, at most kPartBlocks partial sums
+void matvec_grid(const Handle& h, dim3& grid, int& tc) {
+  const int gx = (h.nx + kThreads - 1) / kThreads;
+  tc = 16;
+  while ((size_t)gx * ((h.nt + tc - 1) / tc) > (size_t)kPartBlocks) tc *= 2;
+  grid = dim3(gx, (h.nt + tc - 1) / tc);
+}
+
+template <typename IN>
+int matvec_t(Handle& h, const IN* x, double* y, const double* b, const double* V, int nd, int m, double bytes) {
+  dim3 grid;
+  int tc;
+  matvec_grid(h, grid, tc);
   ProfScope ps(AAO_K_MATVEC, h.stream, bytes);
-  if (x_is_float)
-    k_matvec<float><<<g, kThreads, 0, h.stream>>>((const float*)x, y, b, h.nx, h.nt, h.mL, h.mD, h.mU, h.coef_rows, h.part);
+  if (V && nd > 0)
+    k_matvec<IN, 2><<<grid, kThreads, 0, h.stream>>>(x, y, nullptr, h.nx, h.nt, tc, h.mL, h.mD, h.mU, h.coef_rows, V,
+                                                     nd, h.n, h.part, h.scal, h.counter, m);
+  else if (b)
+    k_matvec<IN, 1><<<grid, kThreads, 0, h.stream>>>(x, y, b, h.nx, h.nt, tc, h.mL, h.mD, h.mU, h.coef_rows, nullptr,
+                                                     0, h.n, h.part, h.scal, h.counter, m);
   else
-    k_matvec<double><<<g, kThreads, 0, h.stream>>>((const double*)x, y, b, h.nx, h.nt, h.mL, h.mD, h.mU, h.coef_rows, h.part);
+    k_matvec<IN, 0><<<grid, kThreads, 0, h.stream>>>(x, y, nullptr, h.nx, h.nt, tc, h.mL, h.mD, h.mU, h.coef_rows,
+                                                     nullptr, 0, h.n, h.part, h.scal, h.counter, m);
   AAO_CHECK_LAUNCH();
   return AAO_OK;
+}
+
+}  // namespace
+
+// y = M x; with b: y = b - M x (restart residual); with V (nd <= 8): first Gram-Schmidt pass
+int launch_matvec(Handle& h, const void* x, bool x_is_float, double* y, const double* b, const double* V, int nd,
+                  int m) {
+  const double nn = (double)h.n;
+  // x once, coefficients (3 per row of the time-dependent operator), y, b and V_q if present
+  const double bytes = nn * (x_is_float ? 4.0 : 8.0) + 3.0 * 8.0 * (double)h.nx * h.coef_rows + nn * 8.0 +
+                       (b ? nn * 8.0 : 0.0) + (V ? nn * 8.0 * nd : 0.0);
+  if (x_is_float) return matvec_t<float>(h, (const float*)x, y, b, V, nd, m, bytes);
+  return matvec_t<double>(h, (const double*)x, y, b, V, nd, m, bytes);
 }
 
 int launch_rhs(Handle& h, double* b) {
@@ -493,13 +604,39 @@ int launch_rhs(Handle& h, double* b) {
 
 namespace {
 
-int residual(Handle& h, const double* b, const double* x, double* r, double* beta2_host) {
-  AAO_TRY(launch_matvec(h, x, false, r, b));
-  const int g = grid_for(h.n);
-  AAO_TRY(reduce_to(h, g, 1, 1, h.scal + S_BETA2));
-  AAO_TRY_CUDA(cudaMemcpyAsync(h.host_scal, h.scal + S_BETA2, sizeof(double), cudaMemcpyDeviceToHost, h.stream));
+int read_scalars(Handle& h, int first, int count) {
+  AAO_TRY_CUDA(cudaMemcpyAsync(h.host_scal, h.scal + first, sizeof(double) * count, cudaMemcpyDeviceToHost, h.stream));
   AAO_TRY_CUDA(cudaStreamSynchronize(h.stream));
-  *beta2_host = h.host_scal[0];
+  return AAO_OK;
+}
+
+// second-pass projections of w onto V_0..V_{nv-1} into scal[S_D2..]
+int projections(Handle& h, const double* w, int nv, int slot) {
+  const size_t n = h.n;
+  const int g = grid_for(n);
+  for (int c0 = 0; c0 < nv; c0 += 8) {
+    const int cnt = (nv - c0) < 8 ? (nv - c0) : 8;
+    {
+      ProfScope ps(AAO_K_ARNOLDI, h.stream, 8.0 * (double)n * (cnt + 1));
+      k_mdot<<<g, kThreads, 0, h.stream>>>(h.V, c0, cnt, n, w, h.part, h.scal + slot, h.counter);
+    }
+    AAO_CHECK_LAUNCH();
+  }
+  return AAO_OK;
+}
+
+int update(Handle& h, double* w, int j, int pass) {
+  const size_t n = h.n;
+  const int g = grid_for(n);
+  const int nv = j + 1;
+  ProfScope ps(AAO_K_ARNOLDI, h.stream, 8.0 * (double)n * (nv + 2));
+  if (nv <= 4)
+    k_update<4><<<g, kThreads, 0, h.stream>>>(w, h.V, j, n, pass, h.scal, h.part, h.counter);
+  else if (nv <= 8)
+    k_update<8><<<g, kThreads, 0, h.stream>>>(w, h.V, j, n, pass, h.scal, h.part, h.counter);
+  else
+    k_update<0><<<g, kThreads, 0, h.stream>>>(w, h.V, j, n, pass, h.scal, h.part, h.counter);
+  AAO_CHECK_LAUNCH();
   return AAO_OK;
 }
 
@@ -514,12 +651,12 @@ int run_fgmres(Handle& h, const double* b, double* x, double tol, int m, int max
   const size_t zsz = h.mixed ? sizeof(float) : sizeof(double);
   char* Zb = reinterpret_cast<char*>(h.Z);
 
-  // ||b||
-  k_dot_self<<<g, kThreads, 0, h.stream>>>(b, n, h.part);
+  {
+    ProfScope ps(AAO_K_OTHER, h.stream, 8.0 * (double)n);
+    k_dot_self<<<g, kThreads, 0, h.stream>>>(b, n, h.part, h.scal, S_BNORM2, h.counter);
+  }
   AAO_CHECK_LAUNCH();
-  AAO_TRY(reduce_to(h, g, 1, 1, h.scal + S_BETA2));
-  AAO_TRY_CUDA(cudaMemcpyAsync(h.host_scal, h.scal + S_BETA2, sizeof(double), cudaMemcpyDeviceToHost, h.stream));
-  AAO_TRY_CUDA(cudaStreamSynchronize(h.stream));
+  AAO_TRY(read_scalars(h, S_BNORM2, 1));
   const double bnorm = sqrt(h.host_scal[0]);
 
   int its = 0, restarts = 0, status = AAO_OK;
@@ -530,64 +667,56 @@ int run_fgmres(Handle& h, const double* b, double* x, double tol, int m, int max
     status = isfinite(bnorm) ? AAO_OK : AAO_BREAKDOWN;
   } else {
     for (;;) {
-      double beta2 = 0.0;
-      AAO_TRY(residual(h, b, x, h.w, &beta2));
-      const double beta = sqrt(beta2);
+      // restart residual r = b - M x, written as the raw first basis vector V_0
+      AAO_TRY(launch_matvec(h, x, false, h.V, b, nullptr, 0, m));
+      AAO_TRY(read_scalars(h, S_BETA2, 1));
+      const double beta = sqrt(h.host_scal[0]);
       rel = beta / bnorm;
       if (!isfinite(beta)) { status = AAO_BREAKDOWN; break; }
       if (beta <= tol * bnorm) { status = AAO_OK; break; }
       if (its >= maxit) { status = AAO_NOT_CONVERGED; break; }
-      k_start<<<g, kThreads, 0, h.stream>>>(h.w, h.V, n, h.scal, m);
-      AAO_CHECK_LAUNCH();
       int jd = 0;
-      bool stop_cycle = false;
-      for (int j = 0; j < m && !stop_cycle; ++j) {
+      for (int j = 0; j < m; ++j) {
         double* Vj = h.V + (size_t)j * n;
+        double* W = h.V + (size_t)(j + 1) * n;  // raw next basis vector, orthogonalised in place
         void* Zj = Zb + zsz * (size_t)j * n;
-        AAO_TRY(launch_precond(h, Vj, Zj, h.mixed));
-        AAO_TRY(launch_matvec(h, Zj, h.mixed, h.w, nullptr));
+        // z_j = P^{-1} (sigma_j V_j): the scale is applied inside the first FFT kernel
+        AAO_TRY(launch_precond(h, Vj, Zj, h.mixed, h.scal + S_SIG + j));
         const int nv = j + 1;
-        // first Gram-Schmidt pass: projections in chunks of 8 basis vectors
-        for (int c0 = 0; c0 < nv; c0 += 8) {
-          const int cnt = (nv - c0) < 8 ? (nv - c0) : 8;
-          ProfScope ps(AAO_K_ARNOLDI, h.stream, 8.0 * (double)n * (cnt + 1));
-          k_mdot<<<g, kThreads, 0, h.stream>>>(h.V + (size_t)c0 * n, cnt, n, h.w, h.part + c0, 136);
-          AAO_CHECK_LAUNCH();
+        const int nf = nv < 8 ? nv : 8;
+        AAO_TRY(launch_matvec(h, Zj, h.mixed, W, nullptr, h.V, nf, m));
+        if (nv > 8) {
+          for (int c0 = 8; c0 < nv; c0 += 8) {
+            const int cnt = (nv - c0) < 8 ? (nv - c0) : 8;
+            {
+              ProfScope ps(AAO_K_ARNOLDI, h.stream, 8.0 * (double)n * (cnt + 1));
+              k_mdot<<<g, kThreads, 0, h.stream>>>(h.V, c0, cnt, n, W, h.part, h.scal + S_D1, h.counter);
+            }
+            AAO_CHECK_LAUNCH();
+          }
         }
-        AAO_TRY(reduce_to(h, g, nv, 136, h.scal + S_H1));
-        // subtract, second pass projections and ||w'||^2
-        {
-          ProfScope ps(AAO_K_ARNOLDI, h.stream, 8.0 * (double)n * (nv + 2));
-          k_update<<<g, kThreads, 0, h.stream>>>(h.w, h.V, nv, n, h.scal + S_H1, h.part, 136);
+        AAO_TRY(update(h, W, j, 1));
+        AAO_TRY(read_scalars(h, S_EST, 4));  // EST, HN, FLAG, REORTH
+        if (h.host_scal[3] != 0.0) {
+          AAO_TRY(projections(h, W, nv, S_D2));
+          AAO_TRY(update(h, W, j, 2));
+          AAO_TRY(read_scalars(h, S_EST, 4));
         }
-        AAO_CHECK_LAUNCH();
-        AAO_TRY(reduce_to(h, g, nv + 1, 136, h.scal + S_H2));  // S_H2[0..nv) and S_H2[nv] = ||w'||^2
-        // move ||w'||^2 to its slot
-        AAO_TRY_CUDA(cudaMemcpyAsync(h.scal + S_NRM2, h.scal + S_H2 + nv, sizeof(double), cudaMemcpyDeviceToDevice, h.stream));
-        k_givens<<<1, 32, 0, h.stream>>>(h.scal, j);
-        AAO_CHECK_LAUNCH();
-        AAO_TRY_CUDA(cudaMemcpyAsync(h.host_scal, h.scal + S_EST, sizeof(double) * 2, cudaMemcpyDeviceToHost, h.stream));
-        AAO_TRY_CUDA(cudaMemcpyAsync(h.host_scal + 2, h.scal + S_FLAG, sizeof(double), cudaMemcpyDeviceToHost, h.stream));
-        AAO_TRY_CUDA(cudaStreamSynchronize(h.stream));
         est = h.host_scal[0];
         const double hn = h.host_scal[1];
         ++its;
         jd = j + 1;
-        if (h.host_scal[2] != 0.0 || !isfinite(est)) { stop_cycle = true; status = AAO_BREAKDOWN; break; }
-        if (est <= tol * bnorm || hn <= 1e-300 || its >= maxit) { stop_cycle = true; break; }
-        {
-          ProfScope ps(AAO_K_ARNOLDI, h.stream, 8.0 * (double)n * (nv + 2));
-          k_vnext<<<g, kThreads, 0, h.stream>>>(h.w, h.V, nv, n, h.scal, h.V + (size_t)(j + 1) * n);
-        }
-        AAO_CHECK_LAUNCH();
+        if (h.host_scal[2] != 0.0 || !isfinite(est)) { status = AAO_BREAKDOWN; break; }
+        if (est <= tol * bnorm || hn <= 1e-300 || its >= maxit) break;
       }
       if (status == AAO_BREAKDOWN) break;
-      k_lsq<<<1, 32, 0, h.stream>>>(h.scal, jd);
-      AAO_CHECK_LAUNCH();
-      if (h.mixed)
-        k_xupdate<float><<<g, kThreads, 0, h.stream>>>(x, (const float*)h.Z, jd, n, h.scal);
-      else
-        k_xupdate<double><<<g, kThreads, 0, h.stream>>>(x, (const double*)h.Z, jd, n, h.scal);
+      {
+        ProfScope ps(AAO_K_OTHER, h.stream, (double)n * (16.0 + zsz * jd));
+        if (h.mixed)
+          k_xupdate<float><<<g, kThreads, 0, h.stream>>>(x, (const float*)h.Z, jd, n, h.scal);
+        else
+          k_xupdate<double><<<g, kThreads, 0, h.stream>>>(x, (const double*)h.Z, jd, n, h.scal);
+      }
       AAO_CHECK_LAUNCH();
       ++restarts;
     }

@@ -34,26 +34,29 @@ __device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3) {
   a3 = csub(d02, d13);
 }
 
-// One in-place Stockham stage of radix R (4 or 2) over P interleaved columns stored [t][P].
-// Butterfly j (0 <= j < N/R) of column p reads elements j + r N/R, twiddles them by
-// exp(-2 pi i r (j mod Ns) / (Ns R)), and writes (j / Ns) Ns R + (j mod Ns) + r Ns.
-template <typename C, int R>
-__device__ __forceinline__ void stockham_stage(C* __restrict__ data, int N, int P, int Ns,
+// One in-place Stockham stage of radix R = 2^LR (4 or 2) over P = 2^lp interleaved columns
+// stored [t][P]. Butterfly j (0 <= j < N/R) of column p reads elements j + r N/R, twiddles them
+// by exp(-2 pi i r (j mod Ns) / (Ns R)), Ns = 2^lns, and writes (j / Ns) Ns R + (j mod Ns) + r Ns.
+// All index arithmetic is shifts and masks (every size is a power of two).
+template <typename C, int LR>
+__device__ __forceinline__ void stockham_stage(C* __restrict__ data, int log2n, int lp, int lns,
                                                const C* __restrict__ tw) {
+  constexpr int R = 1 << LR;
   constexpr int B = kVals / R;
-  const int nbf = P * (N / R);
-  const int stride_in = N / R;
-  const int tstep = N / (Ns * R);
+  const int nbf = 1 << (lp + log2n - LR);
+  const int stride_in = 1 << (log2n - LR);
+  const int lts = log2n - lns - LR;  // log2 of the twiddle-table step N / (Ns R)
+  const int pm = (1 << lp) - 1, nsm = (1 << lns) - 1;
   C reg[B][R];
 #pragma unroll
   for (int q = 0; q < B; ++q) {
     const int b = threadIdx.x + q * blockDim.x;
     if (b < nbf) {
-      const int p = b % P, j = b / P, k = j % Ns;
+      const int p = b & pm, j = b >> lp, k = j & nsm;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        C a = data[(j + r * stride_in) * P + p];
-        if (r > 0 && k > 0) a = cmul(a, __ldg(&tw[r * k * tstep]));
+        C a = data[((j + r * stride_in) << lp) + p];
+        if (r > 0 && k > 0) a = cmul(a, __ldg(&tw[(r * k) << lts]));
         reg[q][r] = a;
       }
     }
@@ -63,7 +66,7 @@ __device__ __forceinline__ void stockham_stage(C* __restrict__ data, int N, int 
   for (int q = 0; q < B; ++q) {
     const int b = threadIdx.x + q * blockDim.x;
     if (b < nbf) {
-      const int p = b % P, j = b / P, k = j % Ns;
+      const int p = b & pm, j = b >> lp, k = j & nsm;
       if (R == 4) {
         dft4(reg[q][0], reg[q][1], reg[q][2], reg[q][3]);
       } else {
@@ -71,23 +74,23 @@ __device__ __forceinline__ void stockham_stage(C* __restrict__ data, int N, int 
         reg[q][0] = cadd(t0, reg[q][1]);
         reg[q][1] = csub(t0, reg[q][1]);
       }
-      const int base = (j / Ns) * Ns * R + k;
+      const int base = ((j >> lns) << (lns + LR)) + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) data[(base + r * Ns) * P + p] = reg[q][r];
+      for (int r = 0; r < R; ++r) data[((base + (r << lns)) << lp) + p] = reg[q][r];
     }
   }
   __syncthreads();
 }
 
-// Forward DFT (exp(-2 pi i t k / N)) of P columns of length N = 2^log2n in shared memory.
+// Forward DFT (exp(-2 pi i t k / N)) of P = 2^lp columns of length N = 2^log2n in shared memory.
 template <typename C>
-__device__ void smem_fft(C* data, int N, int log2n, int P, const C* tw) {
-  int Ns = 1;
+__device__ void smem_fft(C* data, int log2n, int lp, const C* tw) {
+  int lns = 0;
   for (int s = 0; s < log2n / 2; ++s) {
-    stockham_stage<C, 4>(data, N, P, Ns, tw);
-    Ns *= 4;
+    stockham_stage<C, 2>(data, log2n, lp, lns, tw);
+    lns += 2;
   }
-  if (log2n & 1) stockham_stage<C, 2>(data, N, P, Ns, tw);
+  if (log2n & 1) stockham_stage<C, 1>(data, log2n, lp, lns, tw);
 }
 
 template <typename R> __device__ __forceinline__ R to_r(double v);
@@ -98,25 +101,33 @@ template <> __device__ __forceinline__ double to_r<double>(double v) { return v;
 template <typename R>
 __global__ void __launch_bounds__(sizeof(R) == 8 ? 512 : 1024) k_fft_fwd(const double* __restrict__ v, C_t<R>* __restrict__ spec,
                                                   int nx, int N, int log2n, int P, int pitch,
-                                                  const R* __restrict__ lam, const C_t<R>* __restrict__ tw) {
+                                                  const R* __restrict__ lam, const C_t<R>* __restrict__ tw,
+                                                  const double* __restrict__ in_scale) {
   using C = C_t<R>;
+  const R sc = in_scale ? (R)(*in_scale) : (R)1;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* data = reinterpret_cast<C*>(smraw);
   R* flat = reinterpret_cast<R*>(smraw);
+  // P is a power of two <= 16 and blockDim.x a multiple of 32, so W = 2P divides blockDim.x:
+  // thread owns tile column c and rows t = tr, tr + tstep, ... (independent loads in flight)
   const int W = 2 * P;
   const int x0 = blockIdx.x * W;
-  for (int e = threadIdx.x; e < N * W; e += blockDim.x) {
-    const int t = e / W, c = e - t * W;
-    const int x = x0 + c;
+  const int c = threadIdx.x & (W - 1), tr = threadIdx.x / W, tstep = blockDim.x / W;
+  const int x = x0 + c;
+  const bool ok = x < nx;
+  const double* src = v + x;
+#pragma unroll 8
+  for (int t = tr; t < N; t += tstep) {
     R val = (R)0;
-    if (x < nx) val = to_r<R>(__ldg(&v[(size_t)t * nx + x])) * __ldg(&lam[t]);
-    flat[e] = val;  // complex column c/2, real part for even c, imaginary for odd c
+    if (ok) val = to_r<R>(__ldg(src + (size_t)t * nx)) * (__ldg(&lam[t]) * sc);
+    flat[t * W + c] = val;  // complex column c/2: real part for even c, imaginary for odd c
   }
   __syncthreads();
-  smem_fft(data, N, log2n, P, tw);
+  const int lp = __ffs(P) - 1;
+  smem_fft(data, log2n, lp, tw);
   const int half = N / 2;
   for (int e = threadIdx.x; e < (half + 1) * P; e += blockDim.x) {
-    const int k = e / P, p = e - k * P;
+    const int k = e >> lp, p = e & (P - 1);
     const C zk = data[k * P + p];
     const C zn = data[((N - k) & (N - 1)) * P + p];
     const R h = (R)0.5;
@@ -140,8 +151,9 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 512 : 1024) k_fft_inv(const C
   const int W = 2 * P;
   const int x0 = blockIdx.x * W;
   const int half = N / 2;
+  const int lp = __ffs(P) - 1;
   for (int e = threadIdx.x; e < (half + 1) * P; e += blockDim.x) {
-    const int k = e / P, p = e - k * P;
+    const int k = e >> lp, p = e & (P - 1);
     const int x = x0 + 2 * p;
     const C* in = spec + (size_t)k * pitch + x;
     C A = cmk<C>(0, 0), B = cmk<C>(0, 0);
@@ -156,165 +168,169 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 512 : 1024) k_fft_inv(const C
     }
   }
   __syncthreads();
-  smem_fft(data, N, log2n, P, tw);
-  for (int e = threadIdx.x; e < N * W; e += blockDim.x) {
-    const int t = e / W, c = e - t * W;
-    const int x = x0 + c;
-    if (x < nx) {
+  smem_fft(data, log2n, lp, tw);
+  const int c = threadIdx.x & (W - 1), tr = threadIdx.x / W, tstep = blockDim.x / W;
+  const int x = x0 + c;
+  if (x < nx) {
+    OUT* dst = z + x;
+#pragma unroll 8
+    for (int t = tr; t < N; t += tstep) {
       const C y = data[t * P + (c >> 1)];
       const R val = ((c & 1) ? -y.y : y.x) * __ldg(&ilam[t]);
-      z[(size_t)t * nx + x] = (OUT)val;
+      dst[(size_t)t * nx] = (OUT)val;
     }
   }
 }
 
-// step (b)
-template <typename R>
-__global__ void __launch_bounds__(256) k_tridiag(C_t<R>* __restrict__ spec, int nx, int K, int pitch, int ch,
-                                                 int cs, const R* __restrict__ lo, const R* __restrict__ di,
+// step (b): one CTA per frequency bin k. Row i of (mu_k I - A~), mu_k = lambda_{1,k}/lambda_{2,k},
+// right-hand side z1_k / lambda_{2,k}: a_i = -lo_i, b_i = mu_k - di_i, c_i = -up_i. Thread l owns
+// rows [l ch, (l+1) ch) (padding rows beyond nx are identity rows). A modified Thomas sweep
+// expresses every row of the chunk through the chunk's first and last unknowns (multipliers in
+// registers, right-hand sides in shared memory); the 2T first/last rows form a tridiagonal
+// interface system solved by parallel cyclic reduction in shared memory; back substitution
+// recovers the interior rows.
+template <typename R, int CH>
+__global__ void __launch_bounds__(512) k_tridiag(C_t<R>* __restrict__ spec, int nx, int pitch, int ch, int cs,
+                                                 const R* __restrict__ lo, const R* __restrict__ di,
                                                  const R* __restrict__ up, const C_t<R>* __restrict__ mu,
                                                  const C_t<R>* __restrict__ il2) {
   using C = C_t<R>;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int k = blockIdx.x * (blockDim.x >> 5) + warp;
-  if (k >= K) return;  // the whole warp leaves together; only warp-level sync below
-  const int span = 32 * cs;
-  C* dd = reinterpret_cast<C*>(smraw) + (size_t)warp * 3 * span;
-  C* aa = dd + span;
-  C* cc = aa + span;
+  const int T = blockDim.x, tid = threadIdx.x, k = blockIdx.x;
+  C* dd = reinterpret_cast<C*>(smraw);
+  C* pa = dd + (size_t)T * cs;
+  C* pb = pa + 2 * T;
+  C* pc = pb + 2 * T;
+  C* pd = pc + 2 * T;
   const C muk = mu[k], sk = il2[k];
   C* row = spec + (size_t)k * pitch;
-  const C zero = cmk<C>(0, 0);
-  const int npad = 32 * ch;
-  for (int i = lane; i < npad; i += 32) {
+  const C zero = cmk<C>(0, 0), one = cmk<C>(1, 0);
+  for (int i = tid; i < T * ch; i += T) {
     const int L = i / ch, j = i - L * ch;
     dd[L * cs + j] = (i < nx) ? cmul(row[i], sk) : zero;
   }
-  __syncwarp();
+  __syncthreads();
 
-  // Row i of (mu I - A~): a_i = -lo_i, b_i = mu - di_i, c_i = -up_i; padding rows are identity.
-  auto coef = [&](int i, C& a, C& b, C& c) {
-    if (i < nx) {
-      a = cmk<C>(i > 0 ? -__ldg(&lo[i]) : (R)0, 0);
-      b = cmk<C>(muk.x - __ldg(&di[i]), muk.y);
-      c = cmk<C>(i < nx - 1 ? -__ldg(&up[i]) : (R)0, 0);
-    } else {
-      a = zero; b = cmk<C>(1, 0); c = zero;
+  const int s = tid * ch;
+  C* d_ = dd + tid * cs;
+  C ap[CH], cp[CH];
+  C dprev = zero, A1 = zero, C1 = zero, D1 = zero;
+#pragma unroll
+  for (int j = 0; j < CH; ++j) {
+    if (j < ch) {
+      const int i = s + j;
+      C a = zero, b = one, c = zero;
+      if (i < nx) {
+        a = cmk<C>(i > 0 ? -__ldg(&lo[i]) : (R)0, 0);
+        b = cmk<C>(muk.x - __ldg(&di[i]), muk.y);
+        c = cmk<C>(i < nx - 1 ? -__ldg(&up[i]) : (R)0, 0);
+      }
+      C dj;
+      if (j < 2) {
+        const C ib = cinv(b);
+        ap[j] = cmul(a, ib);
+        cp[j] = cmul(c, ib);
+        dj = cmul(d_[j], ib);
+      } else {
+        const C r = cinv(csub(b, cmul(a, cp[j - 1])));
+        dj = cmul(r, csub(d_[j], cmul(a, dprev)));
+        ap[j] = cscale(cmul(r, cmul(a, ap[j - 1])), (R)-1);
+        cp[j] = cmul(r, c);
+      }
+      d_[j] = dj;
+      dprev = dj;
+      if (j == ch - 1) { A1 = ap[j]; C1 = cp[j]; D1 = dj; }
     }
-  };
-
-  const int s = lane * ch;
-  C* d_ = dd + lane * cs;
-  C* a_ = aa + lane * cs;
-  C* c_ = cc + lane * cs;
-  // forward sweep: rows 0, 1 normalised; rows j >= 2 expressed in terms of x_s and x_{j+1}
-  C ap, cp, dp;
-  for (int j = 0; j < 2; ++j) {
-    C a, b, c;
-    coef(s + j, a, b, c);
-    const C ib = cinv(b);
-    ap = cmul(a, ib); cp = cmul(c, ib); dp = cmul(d_[j], ib);
-    a_[j] = ap; c_[j] = cp; d_[j] = dp;
   }
-  for (int j = 2; j < ch; ++j) {
-    C a, b, c;
-    coef(s + j, a, b, c);
-    const C r = cinv(csub(b, cmul(a, cp)));
-    dp = cmul(r, csub(d_[j], cmul(a, dp)));
-    ap = cscale(cmul(r, cmul(a, ap)), (R)-1);
-    cp = cmul(r, c);
-    a_[j] = ap; c_[j] = cp; d_[j] = dp;
-  }
-  C A0, C0, D0, A1, C1, D1;
-  A1 = a_[ch - 1]; C1 = c_[ch - 1]; D1 = d_[ch - 1];
+  C A0 = ap[0], C0 = cp[0], D0 = d_[0];
   if (ch >= 3) {
-    // backward sweep: rows 1..ch-2 expressed in terms of x_s and x_e
-    C an = a_[ch - 2], cn = c_[ch - 2], dn = d_[ch - 2];
-    for (int j = ch - 3; j >= 1; --j) {
-      const C cj = c_[j];
-      dn = csub(d_[j], cmul(cj, dn));
-      an = csub(a_[j], cmul(cj, an));
-      cn = cscale(cmul(cj, cn), (R)-1);
-      a_[j] = an; c_[j] = cn; d_[j] = dn;
+    C dn = d_[ch - 2];
+#pragma unroll
+    for (int j = CH - 3; j >= 1; --j) {
+      if (j <= ch - 3) {
+        dn = csub(d_[j], cmul(cp[j], dn));
+        ap[j] = csub(ap[j], cmul(cp[j], ap[j + 1]));
+        cp[j] = cscale(cmul(cp[j], cp[j + 1]), (R)-1);
+        d_[j] = dn;
+      }
     }
-    // row 0: eliminate x_1 with row 1
-    const C c0 = c_[0];
-    const C r = cinv(csub(cmk<C>(1, 0), cmul(c0, a_[1])));
-    D0 = cmul(r, csub(d_[0], cmul(c0, d_[1])));
-    A0 = cmul(r, a_[0]);
-    C0 = cscale(cmul(r, cmul(c0, c_[1])), (R)-1);
-  } else {
-    A0 = a_[0]; C0 = c_[0]; D0 = d_[0];
+    const C r = cinv(csub(one, cmul(C0, ap[1])));
+    D0 = cmul(r, csub(D0, cmul(C0, d_[1])));
+    A0 = cmul(r, A0);
+    C0 = cscale(cmul(r, cmul(C0, cp[1])), (R)-1);
   }
-  // parallel cyclic reduction of the 64-row interface system, rows 2*lane (x_s), 2*lane+1 (x_e)
-  C B0 = cmk<C>(1, 0), B1 = cmk<C>(1, 0);
-  auto shfl = [](C v, int src) { return cmk<C>(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src)); };
-  for (int delta = 1; delta < 64; delta <<= 1) {
-    C lA0, lB0, lC0, lD0, hA0, hB0, hC0, hD0;  // neighbours of row 2L
-    C lA1, lB1, lC1, lD1, hA1, hB1, hC1, hD1;  // neighbours of row 2L+1
-    const C one = cmk<C>(1, 0);
-    if (delta == 1) {
-      const int src = lane > 0 ? lane - 1 : 0;
-      lA0 = shfl(A1, src); lB0 = shfl(B1, src); lC0 = shfl(C1, src); lD0 = shfl(D1, src);
-      if (lane == 0) { lA0 = zero; lB0 = one; lC0 = zero; lD0 = zero; }
-      hA0 = A1; hB0 = B1; hC0 = C1; hD0 = D1;
-      lA1 = A0; lB1 = B0; lC1 = C0; lD1 = D0;
-      const int srh = lane < 31 ? lane + 1 : 31;
-      hA1 = shfl(A0, srh); hB1 = shfl(B0, srh); hC1 = shfl(C0, srh); hD1 = shfl(D0, srh);
-      if (lane == 31) { hA1 = zero; hB1 = one; hC1 = zero; hD1 = zero; }
-    } else {
-      const int o = delta >> 1;
-      const int sl = lane >= o ? lane - o : lane, sh = lane + o < 32 ? lane + o : lane;
-      lA0 = shfl(A0, sl); lB0 = shfl(B0, sl); lC0 = shfl(C0, sl); lD0 = shfl(D0, sl);
-      hA0 = shfl(A0, sh); hB0 = shfl(B0, sh); hC0 = shfl(C0, sh); hD0 = shfl(D0, sh);
-      lA1 = shfl(A1, sl); lB1 = shfl(B1, sl); lC1 = shfl(C1, sl); lD1 = shfl(D1, sl);
-      hA1 = shfl(A1, sh); hB1 = shfl(B1, sh); hC1 = shfl(C1, sh); hD1 = shfl(D1, sh);
-      if (lane < o) { lA0 = zero; lB0 = one; lC0 = zero; lD0 = zero; lA1 = zero; lB1 = one; lC1 = zero; lD1 = zero; }
-      if (lane + o >= 32) { hA0 = zero; hB0 = one; hC0 = zero; hD0 = zero; hA1 = zero; hB1 = one; hC1 = zero; hD1 = zero; }
+  // interface system: row 2l couples x_{2l-1}, x_{2l}, x_{2l+1}; row 2l+1 couples x_{2l}..x_{2l+2}
+  const int R2 = 2 * T;
+  pa[2 * tid] = A0; pb[2 * tid] = one; pc[2 * tid] = C0; pd[2 * tid] = D0;
+  pa[2 * tid + 1] = A1; pb[2 * tid + 1] = one; pc[2 * tid + 1] = C1; pd[2 * tid + 1] = D1;
+  __syncthreads();
+  for (int delta = 1; delta < R2; delta <<= 1) {
+    C nA[2], nB[2], nC[2], nD[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int q = 2 * tid + h;
+      C lA = zero, lB = one, lC = zero, lD = zero, hA = zero, hB = one, hC = zero, hD = zero;
+      if (q - delta >= 0) { lA = pa[q - delta]; lB = pb[q - delta]; lC = pc[q - delta]; lD = pd[q - delta]; }
+      if (q + delta < R2) { hA = pa[q + delta]; hB = pb[q + delta]; hC = pc[q + delta]; hD = pd[q + delta]; }
+      const C k1 = cmul(pa[q], cinv(lB)), k2 = cmul(pc[q], cinv(hB));
+      nA[h] = cscale(cmul(lA, k1), (R)-1);
+      nC[h] = cscale(cmul(hC, k2), (R)-1);
+      nB[h] = csub(csub(pb[q], cmul(lC, k1)), cmul(hA, k2));
+      nD[h] = csub(csub(pd[q], cmul(lD, k1)), cmul(hD, k2));
     }
-    {
-      const C k1 = cmul(A0, cinv(lB0)), k2 = cmul(C0, cinv(hB0));
-      const C nA = cscale(cmul(lA0, k1), (R)-1), nC = cscale(cmul(hC0, k2), (R)-1);
-      const C nB = csub(csub(B0, cmul(lC0, k1)), cmul(hA0, k2));
-      const C nD = csub(csub(D0, cmul(lD0, k1)), cmul(hD0, k2));
-      A0 = nA; B0 = nB; C0 = nC; D0 = nD;
+    __syncthreads();
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int q = 2 * tid + h;
+      pa[q] = nA[h]; pb[q] = nB[h]; pc[q] = nC[h]; pd[q] = nD[h];
     }
-    {
-      const C k1 = cmul(A1, cinv(lB1)), k2 = cmul(C1, cinv(hB1));
-      const C nA = cscale(cmul(lA1, k1), (R)-1), nC = cscale(cmul(hC1, k2), (R)-1);
-      const C nB = csub(csub(B1, cmul(lC1, k1)), cmul(hA1, k2));
-      const C nD = csub(csub(D1, cmul(lD1, k1)), cmul(hD1, k2));
-      A1 = nA; B1 = nB; C1 = nC; D1 = nD;
-    }
+    __syncthreads();
   }
-  const C xs = cmul(D0, cinv(B0)), xe = cmul(D1, cinv(B1));
-  // back substitution of the chunk interior
-  for (int j = 1; j < ch - 1; ++j) d_[j] = csub(csub(d_[j], cmul(a_[j], xs)), cmul(c_[j], xe));
+  const C xs = cmul(pd[2 * tid], cinv(pb[2 * tid]));
+  const C xe = cmul(pd[2 * tid + 1], cinv(pb[2 * tid + 1]));
+#pragma unroll
+  for (int j = 1; j < CH - 1; ++j)
+    if (j < ch - 1) d_[j] = csub(csub(d_[j], cmul(ap[j], xs)), cmul(cp[j], xe));
   d_[0] = xs;
   d_[ch - 1] = xe;
-  __syncwarp();
-  for (int i = lane; i < nx; i += 32) {
+  __syncthreads();
+  for (int i = tid; i < nx; i += T) {
     const int L = i / ch, j = i - L * ch;
     row[i] = dd[L * cs + j];
   }
 }
 
-template <typename R>
-int run_precond(Handle& h, const double* v, void* z, bool z_is_float) {
-  using C = C_t<R>;
-  const int N = h.nt, nx = h.nx;
-  const int vmax = (sizeof(R) == 4) ? 16384 : 8192;  // P * N bound from registers / smem
-  int P = nx / 512;
-  if (P < 1) P = 1;
-  if (P > vmax / N) P = vmax / N;
-  if (P < 1) P = 1;
+// threads of the FFT kernels: kVals complex values per thread per stage, a multiple of 32,
+// within the kernels' launch bounds
+int fft_threads(int P, int N, size_t rsize) {
   int threads = (P * N + kVals - 1) / kVals;
   threads = ((threads + 31) / 32) * 32;
   if (threads < 64) threads = 64;
-  const int tmax = sizeof(R) == 8 ? 512 : 1024;  // the kernels' launch bounds
+  const int tmax = rsize == 8 ? 512 : 1024;
   if (threads > tmax) threads = tmax;
-  // also cover the load/post loops comfortably
+  return threads;
+}
+
+// largest power of two P <= 16 with P*N within the register/shared-memory budget
+int max_tile(int N, size_t rsize) {
+  const int vmax = rsize == 4 ? 16384 : 8192;
+  int P = 16;
+  while (P > 1 && P * N > vmax) P >>= 1;
+  return P;
+}
+
+int default_tile(int nx, int N, size_t rsize) {
+  int P = max_tile(N, rsize);
+  while (P > 1 && (nx + 2 * P - 1) / (2 * P) < 2 * 152) P >>= 1;
+  return P;
+}
+
+template <typename R>
+int run_precond(Handle& h, const double* v, void* z, bool z_is_float, const double* in_scale) {
+  using C = C_t<R>;
+  const int N = h.nt, nx = h.nx;
+  const int P = h.fft_p > 0 ? h.fft_p : default_tile(nx, N, sizeof(R));
+  int threads = fft_threads(P, N, sizeof(R));
   const size_t smem = (size_t)P * N * sizeof(C);
   const int grid = (nx + 2 * P - 1) / (2 * P);
   C* spec = reinterpret_cast<C*>(h.spec);
@@ -327,30 +343,30 @@ int run_precond(Handle& h, const double* v, void* z, bool z_is_float) {
   const double nv = (double)nx * N;
   {
     ProfScope ps(AAO_K_FFT_FWD, h.stream, nv * sizeof(double) + nsp);
-    k_fft_fwd<R><<<grid, threads, smem, h.stream>>>(v, spec, nx, N, h.log2n, P, h.pitch, lam, tw);
+    k_fft_fwd<R><<<grid, threads, smem, h.stream>>>(v, spec, nx, N, h.log2n, P, h.pitch, lam, tw, in_scale);
   }
   AAO_CHECK_LAUNCH();
 
-  const int ch = nx <= 64 ? 2 : (nx + 31) / 32;
-  const int cs = (ch & 1) ? ch + 2 : ch + 1;
-  const size_t per_warp = (size_t)3 * 32 * cs * sizeof(C);
-  int wpb = (int)((100 * 1024) / per_warp);
-  if (wpb < 1) wpb = 1;
-  if (wpb > 8) wpb = 8;
-  const size_t smem2 = per_warp * wpb;
-  if (smem2 > 220 * 1024) {
-    set_error("precond_apply: nx too large for the shared-memory tridiagonal solver");
+  // step (b): threads per bin T (multiple of 32, <= 512), chunk ch <= CH rows per thread
+  constexpr int CH = sizeof(R) == 4 ? 16 : 8;
+  int T = 32 * ((nx + 32 * CH - 1) / (32 * CH));
+  if (T > 512) {
+    set_error("precond_apply: nx too large for the tridiagonal solver");
     return AAO_EUNSUPPORTED;
   }
+  int ch = (nx + T - 1) / T;
+  if (ch < 2) ch = 2;
+  const int cs = (ch & 1) ? ch + 2 : ch + 1;  // odd chunk stride: conflict-free shared memory
+  const size_t smem2 = ((size_t)T * cs + 8 * (size_t)T) * sizeof(C);
   const R* lo = (sizeof(R) == 4) ? (const R*)h.pLf : (const R*)h.pL;
   const R* di = (sizeof(R) == 4) ? (const R*)h.pDf : (const R*)h.pD;
   const R* up = (sizeof(R) == 4) ? (const R*)h.pUf : (const R*)h.pU;
   const C* mu = (sizeof(R) == 4) ? (const C*)h.muf : (const C*)h.mu;
   const C* il2 = (sizeof(R) == 4) ? (const C*)h.il2f : (const C*)h.il2;
-  AAO_TRY_CUDA(cudaFuncSetAttribute(k_tridiag<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
+  AAO_TRY_CUDA(cudaFuncSetAttribute(k_tridiag<R, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
   {
     ProfScope ps(AAO_K_TRIDIAG, h.stream, 2.0 * nsp);
-    k_tridiag<R><<<(h.K + wpb - 1) / wpb, 32 * wpb, smem2, h.stream>>>(spec, nx, h.K, h.pitch, ch, cs, lo, di, up, mu, il2);
+    k_tridiag<R, CH><<<h.K, T, smem2, h.stream>>>(spec, nx, h.pitch, ch, cs, lo, di, up, mu, il2);
   }
   AAO_CHECK_LAUNCH();
 
@@ -369,9 +385,49 @@ int run_precond(Handle& h, const double* v, void* z, bool z_is_float) {
 
 }  // namespace
 
-int launch_precond(Handle& h, const double* v, void* z, bool z_is_float) {
-  if (h.mixed) return run_precond<float>(h, v, z, z_is_float);
-  return run_precond<double>(h, v, z, z_is_float);
+int launch_precond(Handle& h, const double* v, void* z, bool z_is_float, const double* in_scale) {
+  if (h.mixed) return run_precond<float>(h, v, z, z_is_float, in_scale);
+  return run_precond<double>(h, v, z, z_is_float, in_scale);
+}
+
+// FFT tile autotuner: time the whole apply for every admissible tile width 2P (P = 1, 2, 4, ...)
+// on this problem's sizes and keep the fastest. Every tile width computes identical results
+// (each column's transform runs the same operations in the same order); only speed differs.
+int tune_precond(Handle& h) {
+  const size_t rs = h.mixed ? 4 : 8;
+  const int pmax = max_tile(h.nt, rs);
+  if (pmax == 1) {
+    h.fft_p = 1;
+    return AAO_OK;
+  }
+  double *v = nullptr, *z = nullptr;
+  AAO_TRY_CUDA(cudaMalloc(&v, sizeof(double) * h.n));
+  AAO_TRY_CUDA(cudaMalloc(&z, sizeof(double) * h.n));
+  AAO_TRY_CUDA(cudaMemsetAsync(v, 0, sizeof(double) * h.n, h.stream));
+  cudaEvent_t e0, e1;
+  AAO_TRY_CUDA(cudaEventCreate(&e0));
+  AAO_TRY_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int bestp = default_tile(h.nx, h.nt, rs);
+  int rc = AAO_OK;
+  for (int P = 1; P <= pmax && rc == AAO_OK; P <<= 1) {
+    h.fft_p = P;
+    rc = launch_precond(h, v, z, h.mixed);
+    if (rc != AAO_OK) break;
+    cudaEventRecord(e0, h.stream);
+    for (int r = 0; r < 3 && rc == AAO_OK; ++r) rc = launch_precond(h, v, z, h.mixed);
+    cudaEventRecord(e1, h.stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) { best = ms; bestp = P; }
+  }
+  h.fft_p = bestp;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(v);
+  cudaFree(z);
+  return rc;
 }
 
 }  // namespace aao
