@@ -117,6 +117,26 @@ int fgmres_solve(aao_handle* h, const double* b_dev, double* x_dev, double tol, 
 int fgmres_solve_host(aao_handle* h, const double* b_host, double* x_host, double tol, int m,
                       int maxit, aao_stats* st);
 
+/* z_dev <- P_alpha^{-1} v_dev, the same computation as precond_apply, for callers that cannot
+   allocate device memory (the paper has no counterpart: this is a deployment variant).
+   Callers inside a CUDA stream capture that must not add allocations, processes with a fixed
+   device-memory budget, or latency-critical paths that cannot afford an allocation's
+   synchronisation cannot call aao_create, which allocates its tables and workspace. This entry
+   point takes the problem descriptor directly and keeps every table and the half spectrum in
+   one static device array of 32 MiB (reserved on each GPU that loads the library until the
+   process exits); it calls no cudaMalloc or cudaFree.
+    - Size limit: the half spectrum plus tables must fit in 32 MiB, roughly
+      (nt/2+1) * 64*ceil(nx/64) * 8 bytes (mixed) or * 16 bytes (FP64) plus O(nt + nx);
+      e.g. nx 2047, nt 2048 fits in mixed precision. Larger problems return AAO_EINVAL
+      with a message; use precond_apply for them.
+    - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+      with that device current; make that first call before any stream capture.
+    - All calls on a device share the array. Each call rewrites everything it reads, so no
+      clearing is needed, but calls whose work overlaps on the GPU race on it: order them
+      (one stream, or events).
+   Arguments and errors as for precond_apply; p->stream selects the stream. */
+int precond_apply_static(const aao_problem* p, const double* v_dev, double* z_dev);
+
 /* Message of the calling thread's most recent failure ("" if none). */
 const char* aao_last_error(void);
 

@@ -23,7 +23,7 @@ PRECISIONS = {"fp64": 0, "mixed": 1}
 STATUS = {0: "ok", -1: "einval", -2: "ecuda", -3: "enomem", -4: "not_converged",
           -5: "breakdown", -6: "timeout", -7: "unsupported"}
 
-EXPORTS = ["aao_create", "aao_destroy", "aao_rhs", "aao_matvec", "precond_apply",
+EXPORTS = ["aao_create", "aao_destroy", "aao_rhs", "aao_matvec", "precond_apply", "precond_apply_static",
            "fgmres_solve", "fgmres_solve_host", "aao_last_error", "aao_launch_count",
            "aao_profile_enable", "aao_profile_read"]
 
@@ -74,6 +74,7 @@ def load(path=None):
     lib.aao_rhs.argtypes = [vp, vp]
     lib.aao_matvec.argtypes = [vp, vp, vp]
     lib.precond_apply.argtypes = [vp, vp, vp]
+    lib.precond_apply_static.argtypes = [ctypes.POINTER(AaoProblem), vp, vp]
     lib.fgmres_solve.argtypes = [vp, vp, vp, dp, ip, ip, ctypes.POINTER(AaoStats)]
     lib.fgmres_solve_host.argtypes = [vp, vp, vp, dp, ip, ip, ctypes.POINTER(AaoStats)]
     lib.aao_last_error.restype = ctypes.c_char_p
@@ -81,7 +82,8 @@ def load(path=None):
     lib.aao_profile_enable.argtypes = [ctypes.c_int]
     lib.aao_profile_read.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_double)]
-    for name in ("aao_create", "aao_destroy", "aao_rhs", "aao_matvec", "precond_apply", "fgmres_solve",
+    for name in ("aao_create", "aao_destroy", "aao_rhs", "aao_matvec", "precond_apply", "precond_apply_static",
+                 "fgmres_solve",
                  "fgmres_solve_host", "aao_profile_enable", "aao_profile_read"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -159,6 +161,13 @@ def aao_matvec(h, x, y):
 
 def precond_apply(h, v, z):
     _check(load().precond_apply(h.ptr, _dev(v, h.n), _dev(z, h.n)))
+
+
+def precond_apply_static(p, v, z, stream=None):
+    """z = P_alpha^{-1} v without a handle and without any device allocation (the library's
+    static scratch is used; see include/aao.h). p is a problem dict."""
+    n = int(p["nx"]) * int(p["nt"])
+    _check(load().precond_apply_static(ctypes.byref(make_problem(p, _stream_of(stream))), _dev(v, n), _dev(z, n)))
 
 
 def fgmres_solve(h, b, x, tol, m, maxit, raise_on_failure=False):
