@@ -137,6 +137,37 @@ int fgmres_solve_host(aao_handle* h, const double* b_host, double* x_host, doubl
    Arguments and errors as for precond_apply; p->stream selects the stream. */
 int precond_apply_static(const aao_problem* p, const double* v_dev, double* z_dev);
 
+/* ---- Batched solves (many independent instances in one persistent launch) ----
+   A batch holds n problems (each with its own nx, nt, coefficients, alpha) solved by
+   right-preconditioned FGMRES(m) exactly as fgmres_solve does with precision AAO_MIXED.
+   One CTA owns one instance at a time and runs its whole solve (preconditioner, matvec,
+   Gram-Schmidt, Givens, convergence test) with no host round trip; instances are taken from
+   a queue, largest first, so uneven sizes balance across the GPU. Each instance has its own
+   status. The work of one instance does not depend on the others: its result is the same
+   whatever else is in the batch. */
+typedef struct aao_batch aao_batch;
+
+/* Build tables and workspace for n problems (all precision AAO_MIXED, op AAO_OP_BS or
+   AAO_OP_LOCALVOL, 2 <= nt <= 4096 a power of two, 2 <= nx <= 4096) with restart length
+   1 <= m <= 40. The FFT column tile of each nt class is autotuned here. Work is ordered after
+   ps[0].stream. Errors: AAO_EINVAL (names the first bad problem), AAO_ENOMEM, AAO_ECUDA. */
+int aao_batch_create(const aao_problem* ps, int n, int m, aao_batch** bt);
+
+/* b_dev[i] <- the right-hand side of instance i (as aao_rhs). b_dev: n device pointers to
+   nx_i*nt_i doubles. */
+int aao_batch_rhs(aao_batch* bt, double* const* b_dev);
+
+/* Solve instance i: M_i x_dev[i] = b_dev[i] from the initial guess in x_dev[i], to relative
+   residual tol, at most maxit inner iterations each. One persistent kernel launch, replayed
+   from a CUDA graph captured on the first call (re-captured if tol or maxit change).
+   Blocks until done. st (may be NULL) receives n records; ms is the wall time of the call.
+   Returns AAO_OK if every instance converged, else the first failing instance's status. */
+int batch_submit(aao_batch* bt, double* const* b_dev, double* const* x_dev, double tol, int maxit,
+                 aao_stats* st);
+
+/* Free the batch (NULL accepted). */
+int aao_batch_destroy(aao_batch* bt);
+
 /* Message of the calling thread's most recent failure ("" if none). */
 const char* aao_last_error(void);
 

@@ -24,6 +24,7 @@ STATUS = {0: "ok", -1: "einval", -2: "ecuda", -3: "enomem", -4: "not_converged",
           -5: "breakdown", -6: "timeout", -7: "unsupported"}
 
 EXPORTS = ["aao_create", "aao_destroy", "aao_rhs", "aao_matvec", "precond_apply", "precond_apply_static",
+           "aao_batch_create", "aao_batch_rhs", "batch_submit", "aao_batch_destroy",
            "fgmres_solve", "fgmres_solve_host", "aao_last_error", "aao_launch_count",
            "aao_profile_enable", "aao_profile_read"]
 
@@ -77,6 +78,10 @@ def load(path=None):
     lib.precond_apply_static.argtypes = [ctypes.POINTER(AaoProblem), vp, vp]
     lib.fgmres_solve.argtypes = [vp, vp, vp, dp, ip, ip, ctypes.POINTER(AaoStats)]
     lib.fgmres_solve_host.argtypes = [vp, vp, vp, dp, ip, ip, ctypes.POINTER(AaoStats)]
+    lib.aao_batch_create.argtypes = [ctypes.POINTER(AaoProblem), ip, ip, ctypes.POINTER(vp)]
+    lib.aao_batch_rhs.argtypes = [vp, ctypes.POINTER(vp)]
+    lib.batch_submit.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), dp, ip, ctypes.POINTER(AaoStats)]
+    lib.aao_batch_destroy.argtypes = [vp]
     lib.aao_last_error.restype = ctypes.c_char_p
     lib.aao_launch_count.restype = ctypes.c_uint64
     lib.aao_profile_enable.argtypes = [ctypes.c_int]
@@ -84,7 +89,8 @@ def load(path=None):
                                      ctypes.POINTER(ctypes.c_double)]
     for name in ("aao_create", "aao_destroy", "aao_rhs", "aao_matvec", "precond_apply", "precond_apply_static",
                  "fgmres_solve",
-                 "fgmres_solve_host", "aao_profile_enable", "aao_profile_read"):
+                 "fgmres_solve_host", "aao_profile_enable", "aao_profile_read", "aao_batch_create",
+                 "aao_batch_rhs", "batch_submit", "aao_batch_destroy"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -219,3 +225,56 @@ def aao_profile_read(cls):
     n, ms, by = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
     _check(load().aao_profile_read(int(c), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)))
     return int(n.value), float(ms.value), float(by.value)
+
+
+class Batch:
+    """Owns one aao_batch; frees it on close()/garbage collection."""
+
+    def __init__(self, ptr, problems, m):
+        self.ptr = ptr
+        self.problems = [dict(p) for p in problems]
+        self.m = m
+        self.sizes = [int(p["nx"]) * int(p["nt"]) for p in problems]
+
+    def close(self):
+        if self.ptr:
+            load().aao_batch_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def aao_batch_create(problems, m, stream=None):
+    arr = (AaoProblem * len(problems))()
+    s = _stream_of(stream)
+    for i, p in enumerate(problems):
+        arr[i] = make_problem(p, s)
+    ptr = ctypes.c_void_p()
+    _check(load().aao_batch_create(arr, len(problems), int(m), ctypes.byref(ptr)))
+    return Batch(ptr, problems, m)
+
+
+def _ptr_array(bt, tensors):
+    if len(tensors) != len(bt.sizes):
+        raise ValueError("one vector per instance expected")
+    arr = (ctypes.c_void_p * len(tensors))()
+    for i, (t, n) in enumerate(zip(tensors, bt.sizes)):
+        arr[i] = _dev(t, n)
+    return arr
+
+
+def aao_batch_rhs(bt, bs):
+    _check(load().aao_batch_rhs(bt.ptr, _ptr_array(bt, bs)))
+
+
+def batch_submit(bt, bs, xs, tol, maxit):
+    """Returns a list of per-instance aao_stats dicts (status 0 = converged)."""
+    st = (AaoStats * len(bt.sizes))()
+    code = load().batch_submit(bt.ptr, _ptr_array(bt, bs), _ptr_array(bt, xs), float(tol), int(maxit), st)
+    if code not in (AAO_OK, AAO_NOT_CONVERGED, AAO_BREAKDOWN):
+        _check(code)
+    return [st[i].to_dict() for i in range(len(bt.sizes))]

@@ -26,76 +26,13 @@
 #include <complex>
 #include <vector>
 
-#include "aao_internal.cuh"
+#include "krylov_dev.cuh"
 
 namespace aao {
 
 namespace {
 
-constexpr int kRedBlocks = 1216;   // 152 SMs x 8: blocks of the grid-stride kernels
-constexpr int kPartBlocks = 4096;  // capacity (blocks) of the partial-sum buffer
-constexpr int kPartLd = 16;        // partial sums per block
-constexpr int kThreads = 256;
-constexpr double kReorthEta = 1e-5;
-
-// device scalar slots (offsets into Handle::scal)
-enum : int {
-  S_D1 = 0,       // raw first-pass projections V_i . w
-  S_D2 = 128,     // raw second-pass projections
-  S_SIG = 256,    // sigma_i = 1 / ||V_i||, i = 0..m
-  S_WN2 = 330,    // ||w||^2 before orthogonalisation
-  S_WP2 = 331,    // ||w'||^2 after the last pass
-  S_EST = 332,    // |g_{j+1}| (residual estimate)
-  S_HN = 333,     // h_{j+1,j}
-  S_FLAG = 334,   // non-finite value seen
-  S_REORTH = 335, // second pass requested
-  S_BETA2 = 336,  // ||r||^2
-  S_BNORM2 = 337, // ||b||^2
-  S_G = 340,      // g, m+1
-  S_CS = 420,     // Givens cosines, m
-  S_SN = 500,     // Givens sines, m
-  S_HMAT = 580,   // Hessenberg, column-major (m+1) x m, ld 65
-  S_TOTAL = 580 + 65 * 64
-};
-constexpr int kLdH = 65;
-
-// exact float -> double by bit assembly (normal numbers and zero; subnormals via hardware)
-__device__ __forceinline__ double widen(float f) {
-  const unsigned b = __float_as_uint(f);
-  const unsigned e = (b >> 23) & 0xffu;
-  if (e == 0u || e == 0xffu) return (double)f;
-  const unsigned hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3);
-  return __hiloint2double((int)hi, (int)(b << 29));
-}
-__device__ __forceinline__ double widen(double d) { return d; }
-
-template <typename T> __device__ __forceinline__ double ld(const T* p) { return widen(__ldg(p)); }
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// block-reduce `cnt` per-thread accumulators into out[0..cnt); blockDim.x == kThreads
-template <int CNT>
-__device__ __forceinline__ void block_sums(const double (&acc)[CNT], int cnt, double* out) {
-  __shared__ double red[kThreads / 32][CNT];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int q = 0; q < CNT; ++q) {
-    double v = warp_sum(acc[q]);
-    if (lane == 0) red[warp][q] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < cnt) {
-    double s = 0.0;
-#pragma unroll
-    for (int wv = 0; wv < kThreads / 32; ++wv) s += red[wv][threadIdx.x];
-    out[threadIdx.x] = s;
-  }
-  __syncthreads();
-}
+using namespace kdev;
 
 // After every block wrote its partial sums: true in the block that finishes last.
 __device__ __forceinline__ bool last_block(unsigned int* counter, unsigned int nblocks) {
@@ -176,10 +113,8 @@ __global__ void k_rhs(double* __restrict__ b, int nx, int nt, const double* __re
   }
 }
 
-// y = M x, tiled: warp w of a block owns 32 consecutive spatial columns and walks a chunk of
-// tc time levels, keeping level t-1 in registers; spatial neighbours of s = x_t + x_{t-1} come
-// from lane shuffles (halo columns loaded by lanes 0 and 31). Five FP64 operations per unknown:
-//   y_t,i = (x_t - x_{t-1})_i - [L s_{i-1} + D s_i + U s_{i+1}],  (L, D, U) = tau/2 A_t row i.
+// y = M x over a (column strip, time chunk) grid: blockIdx.x picks 8 strips of 32 columns (one
+// per warp), blockIdx.y a chunk of tc time levels.
 // MODE 0: y = M x.
 // MODE 1: y = b - M x (the restart residual, written as the raw first basis vector); the last
 //         block sets ||r||^2, sigma_0 = 1/||r|| and g = (||r||, 0, ...).
@@ -194,57 +129,14 @@ __global__ void __launch_bounds__(kThreads) k_matvec(const IN* __restrict__ x, d
                                                      double* __restrict__ part, double* __restrict__ scal,
                                                      unsigned int* __restrict__ counter, int m) {
   constexpr int NA = MODE == 2 ? 9 : 1;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int warp = threadIdx.x >> 5;
   const int i0 = (blockIdx.x * (kThreads / 32) + warp) * 32;
-  const int i = i0 + lane;
-  const bool act = i < nx;
   const int t0 = blockIdx.y * tc;
   const int t1 = min(nt, t0 + tc);
   double acc[NA];
 #pragma unroll
   for (int q = 0; q < NA; ++q) acc[q] = 0.0;
-  double xp = 0.0, xpl = 0.0, xpr = 0.0;
-  if (t0 > 0) {
-    const size_t r = (size_t)(t0 - 1) * nx;
-    if (act) xp = ld(x + r + i);
-    if (lane == 0 && i0 > 0 && i0 - 1 < nx) xpl = ld(x + r + i0 - 1);
-    if (lane == 31 && i0 + 32 < nx) xpr = ld(x + r + i0 + 32);
-  }
-  for (int t = t0; t < t1; ++t) {
-    const size_t r = (size_t)t * nx;
-    const double xc = act ? ld(x + r + i) : 0.0;
-    const double s = xc + xp, d = xc - xp;
-    double sl = __shfl_up_sync(0xffffffffu, s, 1);
-    double sr = __shfl_down_sync(0xffffffffu, s, 1);
-    if (lane == 0) {
-      const double xl = (i0 > 0 && i0 - 1 < nx) ? ld(x + r + i0 - 1) : 0.0;
-      sl = xl + xpl;
-      xpl = xl;
-    }
-    if (lane == 31) {
-      const double xr = (i0 + 32 < nx) ? ld(x + r + i0 + 32) : 0.0;
-      sr = xr + xpr;
-      xpr = xr;
-    }
-    if (act) {
-      const size_t c = rows == 1 ? (size_t)i : r + i;
-      double v = fma(-__ldg(L + c), sl, d);
-      v = fma(-__ldg(D + c), s, v);
-      v = fma(-__ldg(U + c), sr, v);
-      if (MODE == 1) {
-        v = __ldg(b + r + i) - v;
-        acc[0] = fma(v, v, acc[0]);
-      }
-      y[r + i] = v;
-      if (MODE == 2) {
-#pragma unroll
-        for (int q = 0; q < NA - 1; ++q)
-          if (q < nd) acc[q] = fma(__ldg(V + (size_t)q * vstride + r + i), v, acc[q]);
-        acc[NA - 1] = fma(v, v, acc[NA - 1]);
-      }
-    }
-    xp = xc;
-  }
+  matvec_item<IN, MODE, NA>(x, y, b, nx, t0, t1, i0, L, D, U, rows, V, nd, vstride, acc);
   if constexpr (MODE == 0) return;
   const unsigned int nblk = gridDim.x * gridDim.y;
   const unsigned int bid = blockIdx.y * gridDim.x + blockIdx.x;
@@ -288,34 +180,6 @@ __global__ void __launch_bounds__(kThreads) k_mdot(const double* __restrict__ V,
   block_sums<8>(acc, nv, part + (size_t)blockIdx.x * kPartLd);
   if (!last_block(counter, gridDim.x)) return;
   finish_sums(part, gridDim.x, nv, [&](int q, double v) { out[c0 + q] = v; }, counter);
-}
-
-// Givens update of Hessenberg column j. w = M z_j with z_j = P^{-1} v_j for the normalised
-// v_j = sigma_j V_j, so h_ij = v_i . w = sigma_i d_i and h_{j+1,j} = ||w'||; one thread.
-__device__ void givens_column(double* __restrict__ scal, int j, const double* d1, const double* d2) {
-  double* H = scal + S_HMAT + (size_t)j * kLdH;
-  for (int i = 0; i <= j; ++i) H[i] = scal[S_SIG + i] * (d1[i] + (d2 ? d2[i] : 0.0));
-  const double wn = sqrt(fmax(scal[S_WP2], 0.0));
-  const double hn = wn;
-  H[j + 1] = hn;
-  for (int i = 0; i < j; ++i) {
-    const double a = H[i], c = H[i + 1];
-    H[i] = scal[S_CS + i] * a + scal[S_SN + i] * c;
-    H[i + 1] = -scal[S_SN + i] * a + scal[S_CS + i] * c;
-  }
-  const double rho = hypot(H[j], H[j + 1]);
-  const double cs = rho > 0.0 ? H[j] / rho : 1.0, sn = rho > 0.0 ? H[j + 1] / rho : 0.0;
-  scal[S_CS + j] = cs;
-  scal[S_SN + j] = sn;
-  H[j] = rho;
-  H[j + 1] = 0.0;
-  const double g = scal[S_G + j];
-  scal[S_G + j + 1] = -sn * g;
-  scal[S_G + j] = cs * g;
-  scal[S_EST] = fabs(sn * g);
-  scal[S_HN] = hn;
-  scal[S_SIG + j + 1] = wn > 0.0 ? 1.0 / wn : 0.0;
-  if (!isfinite(rho) || !isfinite(hn)) scal[S_FLAG] = 1.0;
 }
 
 // Gram-Schmidt pass `pass` (1 or 2) on w (the raw vector V_{j+1}, updated in place):
@@ -589,6 +453,17 @@ int launch_matvec(Handle& h, const void* x, bool x_is_float, double* y, const do
                        (b ? nn * 8.0 : 0.0) + (V ? nn * 8.0 * nd : 0.0);
   if (x_is_float) return matvec_t<float>(h, (const float*)x, y, b, V, nd, m, bytes);
   return matvec_t<double>(h, (const double*)x, y, b, V, nd, m, bytes);
+}
+
+void launch_rhs_raw(cudaStream_t s, double* b, int nx, int nt, const double* L, const double* D, const double* U,
+                    int rows, const double* gL, const double* gR, double h, double K, int payoff) {
+  k_rhs<<<grid_for((size_t)nx * nt), kThreads, 0, s>>>(b, nx, nt, L, D, U, rows, gL, gR, h, K, payoff);
+}
+
+void launch_coef_raw(cudaStream_t s, double* L, double* D, double* U, int nx, int rows, double h, double half_tau,
+                     double sigma, double r, double bump, double tslope, double tau, const double* gS) {
+  k_build_coef<<<grid_for((size_t)nx * rows), kThreads, 0, s>>>(L, D, U, nx, rows, h, half_tau, sigma, r, bump,
+                                                                  tslope, tau, gS);
 }
 
 int launch_rhs(Handle& h, double* b) {

@@ -1,0 +1,165 @@
+// Device building blocks of the FP64 outer loop (CN matvec, Gram-Schmidt sums, Givens), shared
+// by the single-instance kernels (krylov.cu) and the persistent batched solver (batch.cu).
+#pragma once
+
+#include <math.h>
+
+#include "aao_internal.cuh"
+
+namespace aao {
+namespace kdev {
+
+constexpr int kRedBlocks = 1216;   // 152 SMs x 8: blocks of the grid-stride kernels
+constexpr int kPartBlocks = 4096;  // capacity (blocks) of the partial-sum buffer
+constexpr int kPartLd = 16;        // partial sums per block
+constexpr int kThreads = 256;
+constexpr double kReorthEta = 1e-5;
+
+// device scalar slots (offsets into Handle::scal)
+enum : int {
+  S_D1 = 0,       // raw first-pass projections V_i . w
+  S_D2 = 128,     // raw second-pass projections
+  S_SIG = 256,    // sigma_i = 1 / ||V_i||, i = 0..m
+  S_WN2 = 330,    // ||w||^2 before orthogonalisation
+  S_WP2 = 331,    // ||w'||^2 after the last pass
+  S_EST = 332,    // |g_{j+1}| (residual estimate)
+  S_HN = 333,     // h_{j+1,j}
+  S_FLAG = 334,   // non-finite value seen
+  S_REORTH = 335, // second pass requested
+  S_BETA2 = 336,  // ||r||^2
+  S_BNORM2 = 337, // ||b||^2
+  S_G = 340,      // g, m+1
+  S_CS = 420,     // Givens cosines, m
+  S_SN = 500,     // Givens sines, m
+  S_HMAT = 580,   // Hessenberg, column-major (m+1) x m, ld 65
+  S_TOTAL = 580 + 65 * 64
+};
+constexpr int kLdH = 65;
+
+// exact float -> double by bit assembly (normal numbers and zero; subnormals via hardware)
+__device__ __forceinline__ double widen(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned e = (b >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) return (double)f;
+  const unsigned hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3);
+  return __hiloint2double((int)hi, (int)(b << 29));
+}
+__device__ __forceinline__ double widen(double d) { return d; }
+
+template <typename T> __device__ __forceinline__ double ld(const T* p) { return widen(__ldg(p)); }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block-reduce `cnt` per-thread accumulators into out[0..cnt); blockDim.x == kThreads
+template <int CNT>
+__device__ __forceinline__ void block_sums(const double (&acc)[CNT], int cnt, double* out) {
+  __shared__ double red[kThreads / 32][CNT];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < CNT; ++q) {
+    double v = warp_sum(acc[q]);
+    if (lane == 0) red[warp][q] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < cnt) {
+    double s = 0.0;
+#pragma unroll
+    for (int wv = 0; wv < kThreads / 32; ++wv) s += red[wv][threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+// Givens update of Hessenberg column j. w = M z_j with z_j = P^{-1} v_j for the normalised
+// v_j = sigma_j V_j, so h_ij = v_i . w = sigma_i d_i and h_{j+1,j} = ||w'||; one thread.
+__device__ inline void givens_column(double* __restrict__ scal, int j, const double* d1, const double* d2) {
+  double* H = scal + S_HMAT + (size_t)j * kLdH;
+  for (int i = 0; i <= j; ++i) H[i] = scal[S_SIG + i] * (d1[i] + (d2 ? d2[i] : 0.0));
+  const double wn = sqrt(fmax(scal[S_WP2], 0.0));
+  const double hn = wn;
+  H[j + 1] = hn;
+  for (int i = 0; i < j; ++i) {
+    const double a = H[i], c = H[i + 1];
+    H[i] = scal[S_CS + i] * a + scal[S_SN + i] * c;
+    H[i + 1] = -scal[S_SN + i] * a + scal[S_CS + i] * c;
+  }
+  const double rho = hypot(H[j], H[j + 1]);
+  const double cs = rho > 0.0 ? H[j] / rho : 1.0, sn = rho > 0.0 ? H[j + 1] / rho : 0.0;
+  scal[S_CS + j] = cs;
+  scal[S_SN + j] = sn;
+  H[j] = rho;
+  H[j + 1] = 0.0;
+  const double g = scal[S_G + j];
+  scal[S_G + j + 1] = -sn * g;
+  scal[S_G + j] = cs * g;
+  scal[S_EST] = fabs(sn * g);
+  scal[S_HN] = hn;
+  scal[S_SIG + j + 1] = wn > 0.0 ? 1.0 / wn : 0.0;
+  if (!isfinite(rho) || !isfinite(hn)) scal[S_FLAG] = 1.0;
+}
+
+// One work item of the tiled matvec y = M x: this warp's 32 spatial columns [i0, i0+32) over
+// time levels [t0, t1), keeping level t-1 in registers; spatial neighbours of s = x_t + x_{t-1}
+// come from lane shuffles (halo columns loaded by lanes 0 and 31). Five FP64 operations per
+// unknown:  y_t,i = (x_t - x_{t-1})_i - [L s_{i-1} + D s_i + U s_{i+1}], (L, D, U) = tau/2 A_t.
+// MODE 0: y only. MODE 1: y = b - M x, acc[0] += y.y. MODE 2: acc[q] += V_q . y (q < nd <= NA-1),
+// acc[NA-1] += y.y.
+template <typename IN, int MODE, int NA>
+__device__ __forceinline__ void matvec_item(const IN* __restrict__ x, double* __restrict__ y,
+                                            const double* __restrict__ b, int nx, int t0, int t1, int i0,
+                                            const double* __restrict__ L, const double* __restrict__ D,
+                                            const double* __restrict__ U, int rows, const double* __restrict__ V,
+                                            int nd, size_t vstride, double (&acc)[NA]) {
+  const int lane = threadIdx.x & 31;
+  const int i = i0 + lane;
+  const bool act = i < nx;
+  double xp = 0.0, xpl = 0.0, xpr = 0.0;
+  if (t0 > 0) {
+    const size_t r = (size_t)(t0 - 1) * nx;
+    if (act) xp = ld(x + r + i);
+    if (lane == 0 && i0 > 0 && i0 - 1 < nx) xpl = ld(x + r + i0 - 1);
+    if (lane == 31 && i0 + 32 < nx) xpr = ld(x + r + i0 + 32);
+  }
+  for (int t = t0; t < t1; ++t) {
+    const size_t r = (size_t)t * nx;
+    const double xc = act ? ld(x + r + i) : 0.0;
+    const double s = xc + xp, d = xc - xp;
+    double sl = __shfl_up_sync(0xffffffffu, s, 1);
+    double sr = __shfl_down_sync(0xffffffffu, s, 1);
+    if (lane == 0) {
+      const double xl = (i0 > 0 && i0 - 1 < nx) ? ld(x + r + i0 - 1) : 0.0;
+      sl = xl + xpl;
+      xpl = xl;
+    }
+    if (lane == 31) {
+      const double xr = (i0 + 32 < nx) ? ld(x + r + i0 + 32) : 0.0;
+      sr = xr + xpr;
+      xpr = xr;
+    }
+    if (act) {
+      const size_t c = rows == 1 ? (size_t)i : r + i;
+      double v = fma(-__ldg(L + c), sl, d);
+      v = fma(-__ldg(D + c), s, v);
+      v = fma(-__ldg(U + c), sr, v);
+      if (MODE == 1) {
+        v = __ldg(b + r + i) - v;
+        acc[0] = fma(v, v, acc[0]);
+      }
+      y[r + i] = v;
+      if (MODE == 2) {
+#pragma unroll
+        for (int q = 0; q < NA - 1; ++q)
+          if (q < nd) acc[q] = fma(__ldg(V + (size_t)q * vstride + r + i), v, acc[q]);
+        acc[NA - 1] = fma(v, v, acc[NA - 1]);
+      }
+    }
+    xp = xc;
+  }
+}
+
+}  // namespace kdev
+}  // namespace aao
