@@ -165,8 +165,50 @@ int aao_batch_rhs(aao_batch* bt, double* const* b_dev);
 int batch_submit(aao_batch* bt, double* const* b_dev, double* const* x_dev, double tol, int maxit,
                  aao_stats* st);
 
+/* Replace the alpha of every instance (alpha[i], 0 < alpha <= 1) and rebuild the tables that
+   depend on it (Lambda_alpha, lambda_{1,k}, lambda_{2,k}); used to sweep alpha. */
+int aao_batch_set_alpha(aao_batch* bt, const double* alpha);
+
 /* Free the batch (NULL accepted). */
 int aao_batch_destroy(aao_batch* bt);
+
+/* ---- The alpha/m predictor (a learned choice of the free parameter alpha of Sec. 3.1) ----
+   The paper leaves alpha to the user (alpha = 0.1 or 0.01 "suffices", too small an alpha
+   amplifies roundoff in steps (a) and (c), end of Sec. 4). This small network maps problem
+   features to the alpha and restart length m that minimised the mixed-precision solver's
+   iteration count on synthetic instances; the caller falls back to alpha = 1e-3 whenever a
+   prediction does not converge. MLP 6 -> 64 -> 64 -> 2 with ReLU, FP32 parameters (4738:
+   W1[64][6], b1[64], W2[64][64], b2[64], W3[2][64], b3[2], row-major), trained by the
+   library's CUDA kernels (forward/backward, Adam), queried in BF16.
+   Normalised features: x_i = (f_i - mean_i) / scale_i with f = (sigma, r, T, log2 nx,
+   log2 nt, cv) (cv = relative variation of the time-dependent operator, 0 for constant
+   coefficients); normalised targets y = ((log10 alpha - ym_0)/ys_0, (m - ym_1)/ys_1); the
+   constants come from aao_mlp_normalization. Loss: mean over samples of 1/2 ||y - target||^2. */
+typedef struct aao_mlp aao_mlp;
+
+/* Create with the 4738 initial parameters (host, FP32); work runs on `stream`. */
+int aao_mlp_create(const float* init_params, void* stream, aao_mlp** out);
+int aao_mlp_destroy(aao_mlp* h);
+/* Copy the current parameters to host (4738 floats). */
+int aao_mlp_params(aao_mlp* h, float* params_host);
+/* Loss and its gradient over B samples: X_dev B x 6, Y_dev B x 2 (normalised, FP32, device,
+   row-major); grad_host 4738 floats, loss_host 1 float. Deterministic (fixed-order sums). */
+int aao_mlp_grad(aao_mlp* h, const float* X_dev, const float* Y_dev, int B, float* grad_host, float* loss_host);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) with gradient grad_dev (4738
+   floats, device). */
+int aao_mlp_adam_step(aao_mlp* h, const float* grad_dev, float lr);
+/* Train: `epochs` passes over the B samples in minibatches, order shuffled per epoch by a
+   seeded 64-bit LCG; loss_host (may be NULL) receives the final full-batch loss. */
+int aao_mlp_train(aao_mlp* h, const float* X_dev, const float* Y_dev, int B, int epochs, int minibatch, float lr,
+                  unsigned long long seed, float* loss_host);
+/* Forward pass of B samples (normalised X_dev B x 6 -> Y_dev B x 2, device); bf16 != 0 rounds
+   weights and activations to bfloat16 (FP32 accumulation). */
+int aao_mlp_forward(aao_mlp* h, const float* X_dev, float* Y_dev, int B, int bf16);
+/* The normalisation constants: feat_mean[6], feat_scale[6], y_mean[2], y_scale[2]. */
+int aao_mlp_normalization(double* feat_mean, double* feat_scale, double* y_mean, double* y_scale);
+/* Predict (alpha, m) for raw features feats = (sigma, r, T, nx, nt, cv) with the BF16 forward;
+   alpha is clamped to [1e-5, 0.1] and m rounded up to the next of {5, 10, 20, 30, 40}. */
+int alpha_mlp_predict(aao_mlp* h, const float feats[6], double* alpha, int* m);
 
 /* Message of the calling thread's most recent failure ("" if none). */
 const char* aao_last_error(void);

@@ -24,7 +24,9 @@ STATUS = {0: "ok", -1: "einval", -2: "ecuda", -3: "enomem", -4: "not_converged",
           -5: "breakdown", -6: "timeout", -7: "unsupported"}
 
 EXPORTS = ["aao_create", "aao_destroy", "aao_rhs", "aao_matvec", "precond_apply", "precond_apply_static",
-           "aao_batch_create", "aao_batch_rhs", "batch_submit", "aao_batch_destroy",
+           "aao_batch_create", "aao_batch_rhs", "batch_submit", "aao_batch_set_alpha", "aao_batch_destroy",
+           "aao_mlp_create", "aao_mlp_destroy", "aao_mlp_params", "aao_mlp_grad", "aao_mlp_adam_step",
+           "aao_mlp_train", "aao_mlp_forward", "aao_mlp_normalization", "alpha_mlp_predict",
            "fgmres_solve", "fgmres_solve_host", "aao_last_error", "aao_launch_count",
            "aao_profile_enable", "aao_profile_read"]
 
@@ -82,6 +84,17 @@ def load(path=None):
     lib.aao_batch_rhs.argtypes = [vp, ctypes.POINTER(vp)]
     lib.batch_submit.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), dp, ip, ctypes.POINTER(AaoStats)]
     lib.aao_batch_destroy.argtypes = [vp]
+    lib.aao_batch_set_alpha.argtypes = [vp, ctypes.POINTER(dp)]
+    fp = ctypes.POINTER(ctypes.c_float)
+    lib.aao_mlp_create.argtypes = [fp, vp, ctypes.POINTER(vp)]
+    lib.aao_mlp_destroy.argtypes = [vp]
+    lib.aao_mlp_params.argtypes = [vp, fp]
+    lib.aao_mlp_grad.argtypes = [vp, vp, vp, ip, fp, fp]
+    lib.aao_mlp_adam_step.argtypes = [vp, vp, ctypes.c_float]
+    lib.aao_mlp_train.argtypes = [vp, vp, vp, ip, ip, ip, ctypes.c_float, ctypes.c_ulonglong, fp]
+    lib.aao_mlp_forward.argtypes = [vp, vp, vp, ip, ip]
+    lib.aao_mlp_normalization.argtypes = [ctypes.POINTER(dp)] * 4
+    lib.alpha_mlp_predict.argtypes = [vp, fp, ctypes.POINTER(dp), ctypes.POINTER(ip)]
     lib.aao_last_error.restype = ctypes.c_char_p
     lib.aao_launch_count.restype = ctypes.c_uint64
     lib.aao_profile_enable.argtypes = [ctypes.c_int]
@@ -90,7 +103,9 @@ def load(path=None):
     for name in ("aao_create", "aao_destroy", "aao_rhs", "aao_matvec", "precond_apply", "precond_apply_static",
                  "fgmres_solve",
                  "fgmres_solve_host", "aao_profile_enable", "aao_profile_read", "aao_batch_create",
-                 "aao_batch_rhs", "batch_submit", "aao_batch_destroy"):
+                 "aao_batch_rhs", "batch_submit", "aao_batch_destroy", "aao_batch_set_alpha", "aao_mlp_create",
+                 "aao_mlp_destroy", "aao_mlp_params", "aao_mlp_grad", "aao_mlp_adam_step", "aao_mlp_train",
+                 "aao_mlp_forward", "aao_mlp_normalization", "alpha_mlp_predict"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -278,3 +293,96 @@ def batch_submit(bt, bs, xs, tol, maxit):
     if code not in (AAO_OK, AAO_NOT_CONVERGED, AAO_BREAKDOWN):
         _check(code)
     return [st[i].to_dict() for i in range(len(bt.sizes))]
+
+
+def aao_batch_set_alpha(bt, alphas):
+    arr = (ctypes.c_double * len(bt.sizes))(*[float(a) for a in alphas])
+    _check(load().aao_batch_set_alpha(bt.ptr, arr))
+
+
+# ---------------------------------------------------------------- alpha/m MLP
+
+MLP_PARAMS = 4738
+
+
+class Mlp:
+    def __init__(self, ptr):
+        self.ptr = ptr
+
+    def close(self):
+        if self.ptr:
+            load().aao_mlp_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _fbuf(a, n):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if a.size != n:
+        raise ValueError(f"expected {n} values")
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def _fdev(t, n):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+            and t.numel() == n):
+        raise ValueError(f"expected a contiguous float32 CUDA tensor of {n} elements")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def aao_mlp_create(init_params, stream=None):
+    a, p = _fbuf(init_params, MLP_PARAMS)
+    ptr = ctypes.c_void_p()
+    _check(load().aao_mlp_create(p, ctypes.c_void_p(_stream_of(stream)), ctypes.byref(ptr)))
+    return Mlp(ptr)
+
+
+def aao_mlp_params(h):
+    out = np.empty(MLP_PARAMS, dtype=np.float32)
+    _check(load().aao_mlp_params(h.ptr, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+    return out
+
+
+def aao_mlp_grad(h, X, Y):
+    B = X.shape[0]
+    g = np.empty(MLP_PARAMS, dtype=np.float32)
+    loss = ctypes.c_float()
+    _check(load().aao_mlp_grad(h.ptr, _fdev(X, 6 * B), _fdev(Y, 2 * B), B,
+                               g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), ctypes.byref(loss)))
+    return g, float(loss.value)
+
+
+def aao_mlp_adam_step(h, grad_dev, lr):
+    _check(load().aao_mlp_adam_step(h.ptr, _fdev(grad_dev, MLP_PARAMS), float(lr)))
+
+
+def aao_mlp_train(h, X, Y, epochs, minibatch, lr, seed=0):
+    B = X.shape[0]
+    loss = ctypes.c_float()
+    _check(load().aao_mlp_train(h.ptr, _fdev(X, 6 * B), _fdev(Y, 2 * B), B, int(epochs), int(minibatch),
+                                float(lr), int(seed), ctypes.byref(loss)))
+    return float(loss.value)
+
+
+def aao_mlp_forward(h, X, Y, bf16=False):
+    B = X.shape[0]
+    _check(load().aao_mlp_forward(h.ptr, _fdev(X, 6 * B), _fdev(Y, 2 * B), B, 1 if bf16 else 0))
+
+
+def aao_mlp_normalization():
+    arrs = [(ctypes.c_double * 6)(), (ctypes.c_double * 6)(), (ctypes.c_double * 2)(), (ctypes.c_double * 2)()]
+    _check(load().aao_mlp_normalization(*arrs))
+    return [np.array(a[:]) for a in arrs]
+
+
+def alpha_mlp_predict(h, feats):
+    f = (ctypes.c_float * 6)(*[float(v) for v in feats])
+    a, m = ctypes.c_double(), ctypes.c_int()
+    _check(load().alpha_mlp_predict(h.ptr, f, ctypes.byref(a), ctypes.byref(m)))
+    return float(a.value), int(m.value)

@@ -690,6 +690,27 @@ extern "C" int batch_submit(aao_batch* bt, double* const* b, double* const* x, d
   return worst;
 }
 
+extern "C" int aao_batch_set_alpha(aao_batch* bt, const double* alpha) {
+  if (!bt || !alpha) { set_error("aao_batch_set_alpha: null argument"); return AAO_EINVAL; }
+  Batch& B = bt->B;
+  for (int i = 0; i < B.n; ++i)
+    if (!(alpha[i] > 0) || !(alpha[i] <= 1)) { set_error("aao_batch_set_alpha: need 0 < alpha <= 1"); return AAO_EINVAL; }
+  AAO_TRY_CUDA(cudaStreamSynchronize(B.s));
+  for (int i = 0; i < B.n; ++i) {
+    B.prob[i].alpha = alpha[i];
+    const BatchInst& I = B.inst[i];
+    std::vector<float> pl, pd, pu, lam, ilam;
+    std::vector<float2> mu, il2, tw;
+    host_tables(B.prob[i], I.nx, I.nt, pl, pd, pu, mu, il2, tw, lam, ilam);
+    AAO_TRY_CUDA(cudaMemcpyAsync((void*)I.mu, mu.data(), sizeof(float2) * I.K, cudaMemcpyHostToDevice, B.s));
+    AAO_TRY_CUDA(cudaMemcpyAsync((void*)I.il2, il2.data(), sizeof(float2) * I.K, cudaMemcpyHostToDevice, B.s));
+    AAO_TRY_CUDA(cudaMemcpyAsync((void*)I.lam, lam.data(), sizeof(float) * I.nt, cudaMemcpyHostToDevice, B.s));
+    AAO_TRY_CUDA(cudaMemcpyAsync((void*)I.ilam, ilam.data(), sizeof(float) * I.nt, cudaMemcpyHostToDevice, B.s));
+    AAO_TRY_CUDA(cudaStreamSynchronize(B.s));  // host vectors are released at scope end
+  }
+  return AAO_OK;
+}
+
 extern "C" int aao_batch_destroy(aao_batch* bt) {
   if (!bt) return AAO_OK;
   cudaStreamSynchronize(bt->B.s);
