@@ -33,6 +33,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and learned-alpha sections")
+    ap.add_argument("--train-instances", type=int, default=20000)
     return ap.parse_args()
 
 
@@ -283,6 +285,10 @@ def run_ours(args):
         e2e.append(time.perf_counter() - t0)
     e2e_val = world * n / (sum(e2e) / len(e2e))
 
+    extras = {}
+    if not args.no_extras:
+        extras = run_extras(args, flush, stream)
+
     pk = peaks()
     achieved = dbytes / dn / (dms / dn / 1e3) / 1e9 if dn else None
     peak = pk.get("hbm_gbs", 6800.0)
@@ -308,6 +314,7 @@ def run_ours(args):
                            "iterations": st64["iterations"]},
             "e2e": {"value": e2e_val, "unit": "unknowns/s", "h2d_bytes_per_step": 8 * n,
                     "d2h_bytes_per_step": 8 * n}}
+    line.update(extras)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r = cpu_oracle_solve_seconds(p)
         line["cpu_baseline"] = {"value": n / r["s"], "unit": "unknowns/s", "cores": 1, "kind": "oracle",
@@ -318,6 +325,97 @@ def run_ours(args):
     h.close()
     if dist:
         tdist.destroy_process_group()
+
+
+def run_extras(args, flush, stream):
+    """The batched workload (512 instances, one persistent launch) and the learned-alpha
+    deployment (8191 x 8192 local volatility); reported beside the headline number."""
+    import numpy as np
+    import torch
+
+    from paper_2401_16113_gb300 import aao, alpha_mlp as AM, workloads as W
+
+    out = {}
+    # batched: 512 put/call instances, Nx in {127..1023}, Nt in {64..1024}, FGMRES(20), tol 1e-8
+    ps = W.batch_instances(512, m=20)
+    bt = aao.aao_batch_create(ps, 20)
+    bs = [torch.empty(k, dtype=torch.float64, device="cuda") for k in bt.sizes]
+    xs = [torch.zeros(k, dtype=torch.float64, device="cuda") for k in bt.sizes]
+    aao.aao_batch_rhs(bt, bs)
+    for _ in range(3):
+        for x in xs:
+            x.zero_()
+        aao.batch_submit(bt, bs, xs, TOL, 300)
+    times, its = [], []
+    for _ in range(max(3, args.steps)):
+        flush.fill_(1.0)
+        for x in xs:
+            x.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = aao.batch_submit(bt, bs, xs, TOL, 300)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        assert all(s_["status"] == 0 for s_ in st)
+        its = [s_["iterations"] for s_ in st]
+    total = float(sum(bt.sizes))
+    ms = sum(times) / len(times)
+    out["batched"] = {"value": total / (ms / 1e3), "unit": "unknowns/s", "instances": len(ps), "unknowns": total,
+                      "ms": ms, "mean_iterations": float(np.mean(its)), "launches_per_step": 1,
+                      "config": "512 BS put/call, sigma U[0.1,0.6], r U[0,0.08], K U[50,150], T U[0.25,2], "
+                                "Nx {127..1023}, Nt {64..1024}, FGMRES(20), graph-replayed persistent launch"}
+    bt.close()
+    del bs, xs
+
+    # learned alpha: train on the batched distribution (labels from the solver's alpha sweep)
+    import time as _time
+    t0 = _time.time()
+    train_ps = W.batch_instances(args.train_instances, seed=W.SEED + 1)
+    h, loss, (a_lab, m_lab, _, _) = AM.train(train_ps, epochs=200, minibatch=512, lr=3e-3, seed=0, tol=TOL,
+                                             maxit=200)
+    t_train = _time.time() - t0
+    big = W.localvol_8191x8192("mixed")
+    a_pred, m_pred = AM.predict(h, big)
+
+    def solve(alpha, m):
+        q = W.with_(big, alpha=alpha)
+        hh = aao.aao_create(q)
+        n = W.unknowns(q)
+        b = torch.empty(n, dtype=torch.float64, device="cuda")
+        aao.aao_rhs(hh, b)
+        x = torch.zeros_like(b)
+        aao.fgmres_solve(hh, b, x, TOL, m, 300)
+        best = None
+        for _ in range(3):
+            x.zero_()
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = aao.fgmres_solve(hh, b, x, TOL, m, 300)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1)
+            best = t if best is None else min(best, t)
+        hh.close()
+        return st, best, n
+
+    st_l, ms_l, n = solve(a_pred, m_pred)
+    fell_back = st_l["status"] != 0
+    if fell_back:
+        st_l, ms_l, n = solve(AM.DEFAULT_ALPHA, 40)
+    st_f, ms_f, _ = solve(AM.DEFAULT_ALPHA, 40)
+    out["learned_alpha"] = {
+        "workload": "localvol_8191x8192_mixed", "unknowns": n,
+        "learned": {"alpha": a_pred, "m": m_pred, "iterations": st_l["iterations"], "ms": ms_l,
+                    "value": n / (ms_l / 1e3), "rel_residual": st_l["rel_residual"], "fallback": fell_back,
+                    "workspace_bytes": n * ((m_pred + 1) * 8 + m_pred * 4)},
+        "fixed": {"alpha": AM.DEFAULT_ALPHA, "m": 40, "iterations": st_f["iterations"], "ms": ms_f,
+                  "value": n / (ms_f / 1e3), "workspace_bytes": n * (41 * 8 + 40 * 4)},
+        "training": {"instances": args.train_instances, "seconds": t_train, "final_loss": loss,
+                     "epochs": 200}}
+    h.close()
+    return out
 
 
 def main():

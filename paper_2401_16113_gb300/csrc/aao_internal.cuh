@@ -85,6 +85,37 @@ template <typename C> __device__ __forceinline__ C cinv(C a) {
   return cmk<C>(a.x * s, -a.y * s);
 }
 
+// ------------------------------------------------------------------ conversions
+// FP64 instructions (conversions included) share the slow FP64 pipe on this part, so the
+// FP32 <-> FP64 conversions on the hot path are assembled from integer bit operations.
+// widen: exact for normal numbers, zero, inf and NaN; FP32 subnormals become zero.
+__device__ __forceinline__ double widen(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned e = (b >> 23) & 0xffu;
+  const unsigned mant = (e == 0u) ? 0u : (b & 0x7fffffu);
+  unsigned ed = e + 896u;
+  ed = (e == 0xffu) ? 2047u : ed;
+  ed = (e == 0u) ? 0u : ed;
+  const unsigned hi = (b & 0x80000000u) | (ed << 20) | (mant >> 3);
+  return __hiloint2double((int)hi, (int)(mant << 29));
+}
+__device__ __forceinline__ double widen(double d) { return d; }
+
+// narrow: round to nearest (ties away from zero) for results in the FP32 normal range;
+// overflow gives inf, results below the normal range give zero, NaN stays NaN.
+__device__ __forceinline__ float narrow(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const unsigned long long em = b & 0x7fffffffffffffffull;
+  const unsigned long long r = em + (1ull << 28);  // half of the 29 dropped bits; carries into the exponent
+  const long long fe = (long long)(r >> 52) - 896;
+  unsigned fb = ((unsigned)fe << 23) | (unsigned)((r >> 29) & 0x7fffffu);
+  fb = fe >= 255 ? 0x7f800000u : fb;
+  fb = fe <= 0 ? 0u : fb;
+  fb = (em >> 52) == 0x7ffull ? ((em & 0xfffffffffffffull) ? 0x7fc00000u : 0x7f800000u) : fb;
+  return __uint_as_float(sign | fb);
+}
+
 // ------------------------------------------------------------------ handle
 struct Handle {
   aao_problem p;

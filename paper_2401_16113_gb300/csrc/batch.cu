@@ -59,16 +59,33 @@ __device__ __forceinline__ void cta_sums(const double (&acc)[CNT], int cnt, doub
 }
 
 // y = M x over the instance: warp w takes work items w, w+8, ... (32-column strip x 16 levels)
-template <typename IN, int MODE, int NA>
-__device__ __noinline__ void cta_matvec(const BatchInst& I, const IN* x, double* y, const double* b, const double* V, int nd,
-                           double (&acc)[NA]) {
+template <typename IN, int MODE, int ND, int NA>
+__device__ __forceinline__ void cta_matvec(const BatchInst& I, const IN* x, double* y, const double* b,
+                                           const double* V, double (&acc)[NA]) {
   const int warp = threadIdx.x >> 5;
   const int strips = (I.nx + 31) / 32, chunks = (I.nt + 15) / 16;
   for (int it = warp; it < strips * chunks; it += kBT / 32) {
     const int sidx = it % strips, cidx = it / strips;
     const int t0 = cidx * 16, t1 = min(I.nt, t0 + 16);
-    matvec_item<IN, MODE, NA>(x, y, b, I.nx, t0, t1, sidx * 32, I.mL, I.mD, I.mU, I.rows, V, nd, I.n, acc);
+    matvec_item<IN, MODE, ND, NA>(x, y, b, I.nx, t0, t1, sidx * 32, I.mL, I.mD, I.mU, I.rows, V, I.n, acc);
   }
+}
+
+// restart residual r = b - M x into V_0; returns ||r||^2 in sm[0]
+__device__ __noinline__ void cta_residual(const BatchInst& I, double* sm) {
+  double acc[1] = {0.0};
+  cta_matvec<double, 1, 0, 1>(I, I.x, I.V, I.b, nullptr, acc);
+  block_sums<1>(acc, 1, sm);
+}
+
+// W = M z_j with the first-pass projections V_q . W (q < ND) and ||W||^2 into sm[0..ND]
+template <int ND>
+__device__ __noinline__ void cta_matvec_proj(const BatchInst& I, const float* z, double* W, double* sm) {
+  double acc[ND + 1];
+#pragma unroll
+  for (int q = 0; q <= ND; ++q) acc[q] = 0.0;
+  cta_matvec<float, 2, ND, ND + 1>(I, z, W, nullptr, I.V, acc);
+  block_sums<ND + 1>(acc, ND + 1, sm);
 }
 
 // P_alpha^{-1} (scale * v) -> z (FP32), Eq. 3.2 with Remark 1
@@ -93,21 +110,34 @@ __device__ __noinline__ void cta_precond(const BatchInst& I, const double* v, fl
   }
 }
 
-// out[c0 + q] = V_{c0+q} . w, q < cnt <= 8
-__device__ __noinline__ void cta_mdot(const BatchInst& I, int c0, int cnt, const double* w, double* out, double* sm) {
-  double acc[8];
+// out[c0 + q] = V_{c0+q} . w, q < CNT <= 8
+template <int CNT>
+__device__ __noinline__ void cta_mdot_t(const BatchInst& I, int c0, const double* w, double* out, double* sm) {
+  double acc[CNT];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+  for (int q = 0; q < CNT; ++q) acc[q] = 0.0;
   const double* Vc = I.V + (size_t)c0 * I.n;
   for (size_t e = threadIdx.x; e < I.n; e += kBT) {
     const double wv = w[e];
 #pragma unroll
-    for (int q = 0; q < 8; ++q)
-      if (q < cnt) acc[q] = fma(Vc[(size_t)q * I.n + e], wv, acc[q]);
+    for (int q = 0; q < CNT; ++q) acc[q] = fma(Vc[(size_t)q * I.n + e], wv, acc[q]);
   }
-  cta_sums<8>(acc, cnt, sm);
-  if (threadIdx.x < cnt) out[c0 + threadIdx.x] = sm[threadIdx.x];
+  cta_sums<CNT>(acc, CNT, sm);
+  if (threadIdx.x < CNT) out[c0 + threadIdx.x] = sm[threadIdx.x];
   __syncthreads();
+}
+
+__device__ void cta_mdot(const BatchInst& I, int c0, int cnt, const double* w, double* out, double* sm) {
+  switch (cnt) {
+    case 1: cta_mdot_t<1>(I, c0, w, out, sm); break;
+    case 2: cta_mdot_t<2>(I, c0, w, out, sm); break;
+    case 3: cta_mdot_t<3>(I, c0, w, out, sm); break;
+    case 4: cta_mdot_t<4>(I, c0, w, out, sm); break;
+    case 5: cta_mdot_t<5>(I, c0, w, out, sm); break;
+    case 6: cta_mdot_t<6>(I, c0, w, out, sm); break;
+    case 7: cta_mdot_t<7>(I, c0, w, out, sm); break;
+    default: cta_mdot_t<8>(I, c0, w, out, sm); break;
+  }
 }
 
 // Gram-Schmidt pass: w -= sum sigma_i^2 d_i V_i, then ||w||^2; thread 0 decides on a second
@@ -183,9 +213,7 @@ __device__ __noinline__ void cta_solve(const BatchInst& I, double tol, int maxit
     status = isfinite(bnorm) ? AAO_OK : AAO_BREAKDOWN;
   } else {
     for (;;) {
-      double acc[1] = {0.0};
-      cta_matvec<double, 1, 1>(I, I.x, I.V, I.b, nullptr, 0, acc);
-      cta_sums<1>(acc, 1, sm);
+      cta_residual(I, sm);
       const double beta = sqrt(sm[0]);
       rel = beta / bnorm;
       if (!isfinite(beta)) { status = AAO_BREAKDOWN; break; }
@@ -206,15 +234,15 @@ __device__ __noinline__ void cta_solve(const BatchInst& I, double tol, int maxit
         cta_precond(I, Vj, (float)scal[S_SIG + j], Zj, smem);
         const int nv = j + 1;
         const int nf = nv < 8 ? nv : 8;
-        double a9[9];
-#pragma unroll
-        for (int q = 0; q < 9; ++q) a9[q] = 0.0;
-        cta_matvec<float, 2, 9>(I, Zj, W, nullptr, I.V, nf, a9);
-        {
-          double out[9];
-#pragma unroll
-          for (int q = 0; q < 9; ++q) out[q] = q < nf ? a9[q] : (q == nf ? a9[8] : 0.0);
-          cta_sums<9>(out, nf + 1, sm);
+        switch (nf) {
+          case 1: cta_matvec_proj<1>(I, Zj, W, sm); break;
+          case 2: cta_matvec_proj<2>(I, Zj, W, sm); break;
+          case 3: cta_matvec_proj<3>(I, Zj, W, sm); break;
+          case 4: cta_matvec_proj<4>(I, Zj, W, sm); break;
+          case 5: cta_matvec_proj<5>(I, Zj, W, sm); break;
+          case 6: cta_matvec_proj<6>(I, Zj, W, sm); break;
+          case 7: cta_matvec_proj<7>(I, Zj, W, sm); break;
+          default: cta_matvec_proj<8>(I, Zj, W, sm); break;
         }
         if (threadIdx.x < nf) scal[S_D1 + threadIdx.x] = sm[threadIdx.x];
         if (threadIdx.x == 0) scal[S_WN2] = sm[nf];

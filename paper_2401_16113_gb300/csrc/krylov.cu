@@ -120,15 +120,16 @@ __global__ void k_rhs(double* __restrict__ b, int nx, int nt, const double* __re
 //         block sets ||r||^2, sigma_0 = 1/||r|| and g = (||r||, 0, ...).
 // MODE 2: y = M x, the first Gram-Schmidt projections d_q = V_q . y (q < nd <= 8) and ||y||^2,
 //         finished by the last block into scal[S_D1 + q] and scal[S_WN2].
-template <typename IN, int MODE>
+template <typename IN, int MODE, int ND>
 __global__ void __launch_bounds__(kThreads) k_matvec(const IN* __restrict__ x, double* __restrict__ y,
                                                      const double* __restrict__ b, int nx, int nt, int tc,
                                                      const double* __restrict__ L, const double* __restrict__ D,
                                                      const double* __restrict__ U, int rows,
-                                                     const double* __restrict__ V, int nd, size_t vstride,
+                                                     const double* __restrict__ V, size_t vstride,
                                                      double* __restrict__ part, double* __restrict__ scal,
                                                      unsigned int* __restrict__ counter, int m) {
-  constexpr int NA = MODE == 2 ? 9 : 1;
+  constexpr int NA = MODE == 2 ? ND + 1 : 1;
+  constexpr int nd = ND;
   const int warp = threadIdx.x >> 5;
   const int i0 = (blockIdx.x * (kThreads / 32) + warp) * 32;
   const int t0 = blockIdx.y * tc;
@@ -136,15 +137,12 @@ __global__ void __launch_bounds__(kThreads) k_matvec(const IN* __restrict__ x, d
   double acc[NA];
 #pragma unroll
   for (int q = 0; q < NA; ++q) acc[q] = 0.0;
-  matvec_item<IN, MODE, NA>(x, y, b, nx, t0, t1, i0, L, D, U, rows, V, nd, vstride, acc);
+  matvec_item<IN, MODE, ND, NA>(x, y, b, nx, t0, t1, i0, L, D, U, rows, V, vstride, acc);
   if constexpr (MODE == 0) return;
   const unsigned int nblk = gridDim.x * gridDim.y;
   const unsigned int bid = blockIdx.y * gridDim.x + blockIdx.x;
   if constexpr (MODE == 2) {
-    double out[NA];
-#pragma unroll
-    for (int q = 0; q < NA; ++q) out[q] = q < nd ? acc[q] : (q == nd ? acc[NA - 1] : 0.0);
-    block_sums<NA>(out, nd + 1, part + (size_t)bid * kPartLd);
+    block_sums<NA>(acc, nd + 1, part + (size_t)bid * kPartLd);
   } else {
     block_sums<NA>(acc, 1, part + (size_t)bid * kPartLd);
   }
@@ -163,21 +161,22 @@ __global__ void __launch_bounds__(kThreads) k_matvec(const IN* __restrict__ x, d
   }
 }
 
-// out[c0 + q] = V_{c0+q} . w for q < nv (chunk of <= 8 basis vectors), finished by the last block
-__global__ void __launch_bounds__(kThreads) k_mdot(const double* __restrict__ V, int c0, int nv, size_t n,
+// out[c0 + q] = V_{c0+q} . w for q < NV (chunk of <= 8 basis vectors), finished by the last block
+template <int NV>
+__global__ void __launch_bounds__(kThreads) k_mdot(const double* __restrict__ V, int c0, size_t n,
                                                    const double* __restrict__ w, double* __restrict__ part,
                                                    double* __restrict__ out, unsigned int* __restrict__ counter) {
-  double acc[8];
+  constexpr int nv = NV;
+  double acc[NV];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+  for (int q = 0; q < NV; ++q) acc[q] = 0.0;
   const double* Vc = V + (size_t)c0 * n;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     const double wv = __ldg(w + e);
 #pragma unroll
-    for (int q = 0; q < 8; ++q)
-      if (q < nv) acc[q] = fma(__ldg(Vc + (size_t)q * n + e), wv, acc[q]);
+    for (int q = 0; q < NV; ++q) acc[q] = fma(__ldg(Vc + (size_t)q * n + e), wv, acc[q]);
   }
-  block_sums<8>(acc, nv, part + (size_t)blockIdx.x * kPartLd);
+  block_sums<NV>(acc, nv, part + (size_t)blockIdx.x * kPartLd);
   if (!last_block(counter, gridDim.x)) return;
   finish_sums(part, gridDim.x, nv, [&](int q, double v) { out[c0 + q] = v; }, counter);
 }
@@ -201,10 +200,9 @@ __global__ void __launch_bounds__(kThreads) k_update(double* __restrict__ w, con
   double acc[1] = {0.0};
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     double wv = w[e];
-    if (NV > 0) {
+    if constexpr (NV > 0) {
 #pragma unroll
-      for (int q = 0; q < (NV > 0 ? NV : 1); ++q)
-        if (q < nv) wv = fma(-cf[q], __ldg(V + (size_t)q * n + e), wv);
+      for (int q = 0; q < NV; ++q) wv = fma(-cf[q], __ldg(V + (size_t)q * n + e), wv);
     } else {
       for (int q = 0; q < nv; ++q) wv = fma(-cf[q], __ldg(V + (size_t)q * n + e), wv);
     }
@@ -429,15 +427,28 @@ int matvec_t(Handle& h, const IN* x, double* y, const double* b, const double* V
   int tc;
   matvec_grid(h, grid, tc);
   ProfScope ps(AAO_K_MATVEC, h.stream, bytes);
-  if (V && nd > 0)
-    k_matvec<IN, 2><<<grid, kThreads, 0, h.stream>>>(x, y, nullptr, h.nx, h.nt, tc, h.mL, h.mD, h.mU, h.coef_rows, V,
-                                                     nd, h.n, h.part, h.scal, h.counter, m);
-  else if (b)
-    k_matvec<IN, 1><<<grid, kThreads, 0, h.stream>>>(x, y, b, h.nx, h.nt, tc, h.mL, h.mD, h.mU, h.coef_rows, nullptr,
-                                                     0, h.n, h.part, h.scal, h.counter, m);
-  else
-    k_matvec<IN, 0><<<grid, kThreads, 0, h.stream>>>(x, y, nullptr, h.nx, h.nt, tc, h.mL, h.mD, h.mU, h.coef_rows,
-                                                     nullptr, 0, h.n, h.part, h.scal, h.counter, m);
+#define AAO_MV2(ND)                                                                                    \
+  k_matvec<IN, 2, ND><<<grid, kThreads, 0, h.stream>>>(x, y, nullptr, h.nx, h.nt, tc, h.mL, h.mD, h.mU, \
+                                                       h.coef_rows, V, h.n, h.part, h.scal, h.counter, m)
+  if (V && nd > 0) {
+    switch (nd) {
+      case 1: AAO_MV2(1); break;
+      case 2: AAO_MV2(2); break;
+      case 3: AAO_MV2(3); break;
+      case 4: AAO_MV2(4); break;
+      case 5: AAO_MV2(5); break;
+      case 6: AAO_MV2(6); break;
+      case 7: AAO_MV2(7); break;
+      default: AAO_MV2(8); break;
+    }
+  } else if (b) {
+    k_matvec<IN, 1, 0><<<grid, kThreads, 0, h.stream>>>(x, y, b, h.nx, h.nt, tc, h.mL, h.mD, h.mU, h.coef_rows,
+                                                        nullptr, h.n, h.part, h.scal, h.counter, m);
+  } else {
+    k_matvec<IN, 0, 0><<<grid, kThreads, 0, h.stream>>>(x, y, nullptr, h.nx, h.nt, tc, h.mL, h.mD, h.mU,
+                                                        h.coef_rows, nullptr, h.n, h.part, h.scal, h.counter, m);
+  }
+#undef AAO_MV2
   AAO_CHECK_LAUNCH();
   return AAO_OK;
 }
@@ -485,17 +496,34 @@ int read_scalars(Handle& h, int first, int count) {
   return AAO_OK;
 }
 
+// out[c0 + q] = V_{c0+q} . w, q < cnt <= 8
+int mdot(Handle& h, int c0, int cnt, const double* w, double* out) {
+  const size_t n = h.n;
+  const int g = grid_for(n);
+  ProfScope ps(AAO_K_ARNOLDI, h.stream, 8.0 * (double)n * (cnt + 1));
+#define AAO_MD(NV) k_mdot<NV><<<g, kThreads, 0, h.stream>>>(h.V, c0, n, w, h.part, out, h.counter)
+  switch (cnt) {
+    case 1: AAO_MD(1); break;
+    case 2: AAO_MD(2); break;
+    case 3: AAO_MD(3); break;
+    case 4: AAO_MD(4); break;
+    case 5: AAO_MD(5); break;
+    case 6: AAO_MD(6); break;
+    case 7: AAO_MD(7); break;
+    default: AAO_MD(8); break;
+  }
+#undef AAO_MD
+  AAO_CHECK_LAUNCH();
+  return AAO_OK;
+}
+
 // second-pass projections of w onto V_0..V_{nv-1} into scal[S_D2..]
 int projections(Handle& h, const double* w, int nv, int slot) {
   const size_t n = h.n;
   const int g = grid_for(n);
   for (int c0 = 0; c0 < nv; c0 += 8) {
     const int cnt = (nv - c0) < 8 ? (nv - c0) : 8;
-    {
-      ProfScope ps(AAO_K_ARNOLDI, h.stream, 8.0 * (double)n * (cnt + 1));
-      k_mdot<<<g, kThreads, 0, h.stream>>>(h.V, c0, cnt, n, w, h.part, h.scal + slot, h.counter);
-    }
-    AAO_CHECK_LAUNCH();
+    AAO_TRY(mdot(h, c0, cnt, w, h.scal + slot));
   }
   return AAO_OK;
 }
@@ -505,12 +533,19 @@ int update(Handle& h, double* w, int j, int pass) {
   const int g = grid_for(n);
   const int nv = j + 1;
   ProfScope ps(AAO_K_ARNOLDI, h.stream, 8.0 * (double)n * (nv + 2));
-  if (nv <= 4)
-    k_update<4><<<g, kThreads, 0, h.stream>>>(w, h.V, j, n, pass, h.scal, h.part, h.counter);
-  else if (nv <= 8)
-    k_update<8><<<g, kThreads, 0, h.stream>>>(w, h.V, j, n, pass, h.scal, h.part, h.counter);
-  else
-    k_update<0><<<g, kThreads, 0, h.stream>>>(w, h.V, j, n, pass, h.scal, h.part, h.counter);
+#define AAO_UP(NV) k_update<NV><<<g, kThreads, 0, h.stream>>>(w, h.V, j, n, pass, h.scal, h.part, h.counter)
+  switch (nv) {
+    case 1: AAO_UP(1); break;
+    case 2: AAO_UP(2); break;
+    case 3: AAO_UP(3); break;
+    case 4: AAO_UP(4); break;
+    case 5: AAO_UP(5); break;
+    case 6: AAO_UP(6); break;
+    case 7: AAO_UP(7); break;
+    case 8: AAO_UP(8); break;
+    default: AAO_UP(0); break;
+  }
+#undef AAO_UP
   AAO_CHECK_LAUNCH();
   return AAO_OK;
 }
@@ -563,11 +598,7 @@ int run_fgmres(Handle& h, const double* b, double* x, double tol, int m, int max
         if (nv > 8) {
           for (int c0 = 8; c0 < nv; c0 += 8) {
             const int cnt = (nv - c0) < 8 ? (nv - c0) : 8;
-            {
-              ProfScope ps(AAO_K_ARNOLDI, h.stream, 8.0 * (double)n * (cnt + 1));
-              k_mdot<<<g, kThreads, 0, h.stream>>>(h.V, c0, cnt, n, W, h.part, h.scal + S_D1, h.counter);
-            }
-            AAO_CHECK_LAUNCH();
+            AAO_TRY(mdot(h, c0, cnt, W, h.scal + S_D1));
           }
         }
         AAO_TRY(update(h, W, j, 1));

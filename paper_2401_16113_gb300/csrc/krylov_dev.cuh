@@ -36,16 +36,6 @@ enum : int {
 };
 constexpr int kLdH = 65;
 
-// exact float -> double by bit assembly (normal numbers and zero; subnormals via hardware)
-__device__ __forceinline__ double widen(float f) {
-  const unsigned b = __float_as_uint(f);
-  const unsigned e = (b >> 23) & 0xffu;
-  if (e == 0u || e == 0xffu) return (double)f;
-  const unsigned hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3);
-  return __hiloint2double((int)hi, (int)(b << 29));
-}
-__device__ __forceinline__ double widen(double d) { return d; }
-
 template <typename T> __device__ __forceinline__ double ld(const T* p) { return widen(__ldg(p)); }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -106,14 +96,14 @@ __device__ inline void givens_column(double* __restrict__ scal, int j, const dou
 // time levels [t0, t1), keeping level t-1 in registers; spatial neighbours of s = x_t + x_{t-1}
 // come from lane shuffles (halo columns loaded by lanes 0 and 31). Five FP64 operations per
 // unknown:  y_t,i = (x_t - x_{t-1})_i - [L s_{i-1} + D s_i + U s_{i+1}], (L, D, U) = tau/2 A_t.
-// MODE 0: y only. MODE 1: y = b - M x, acc[0] += y.y. MODE 2: acc[q] += V_q . y (q < nd <= NA-1),
-// acc[NA-1] += y.y.
-template <typename IN, int MODE, int NA>
+// MODE 0: y only. MODE 1: y = b - M x, acc[0] += y.y. MODE 2: acc[q] += V_q . y (q < ND, a
+// compile-time count so that no predicated-off FP64 instruction is issued), acc[ND] += y.y.
+template <typename IN, int MODE, int ND, int NA>
 __device__ __forceinline__ void matvec_item(const IN* __restrict__ x, double* __restrict__ y,
                                             const double* __restrict__ b, int nx, int t0, int t1, int i0,
                                             const double* __restrict__ L, const double* __restrict__ D,
                                             const double* __restrict__ U, int rows, const double* __restrict__ V,
-                                            int nd, size_t vstride, double (&acc)[NA]) {
+                                            size_t vstride, double (&acc)[NA]) {
   const int lane = threadIdx.x & 31;
   const int i = i0 + lane;
   const bool act = i < nx;
@@ -152,9 +142,8 @@ __device__ __forceinline__ void matvec_item(const IN* __restrict__ x, double* __
       y[r + i] = v;
       if (MODE == 2) {
 #pragma unroll
-        for (int q = 0; q < NA - 1; ++q)
-          if (q < nd) acc[q] = fma(__ldg(V + (size_t)q * vstride + r + i), v, acc[q]);
-        acc[NA - 1] = fma(v, v, acc[NA - 1]);
+        for (int q = 0; q < ND; ++q) acc[q] = fma(__ldg(V + (size_t)q * vstride + r + i), v, acc[q]);
+        acc[ND] = fma(v, v, acc[ND]);
       }
     }
     xp = xc;

@@ -80,7 +80,7 @@ __device__ void smem_fft(C* data, int log2n, int lp, const C* tw) {
 }
 
 template <typename R> __device__ __forceinline__ R to_r(double v);
-template <> __device__ __forceinline__ float to_r<float>(double v) { return __double2float_rn(v); }
+template <> __device__ __forceinline__ float to_r<float>(double v) { return narrow(v); }
 template <> __device__ __forceinline__ double to_r<double>(double v) { return v; }
 
 // step (a) for the column tile starting at x0 (all threads of the CTA; smem holds P*N complex).
