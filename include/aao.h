@@ -50,7 +50,8 @@ extern "C" {
 
 /*
  * Problem descriptor (plain old data; copied by aao_create).
- *  nx, nt      interior spatial nodes (>= 2) and CN steps (power of two, 1..16384)
+ *  nx, nt      interior spatial nodes (2..8192 mixed, 2..4096 FP64) and CN steps (a power
+ *              of two, 1..8192 mixed, 1..4096 FP64)
  *  op, payoff  AAO_OP_*, AAO_PUT / AAO_CALL
  *  precision   AAO_FP64 or AAO_MIXED
  *  T, r, K, sigma   maturity, rate, strike, volatility
@@ -231,9 +232,10 @@ uint64_t aao_launch_count(void);
 int aao_profile_enable(int mask);
 
 /* For kernel class cls since the last aao_profile_enable: launches timed, their total device
-   milliseconds, and the algorithmic bytes they move (what each launch must read and write
-   once, by its arguments' sizes). Synchronises the recorded events. */
-int aao_profile_read(int cls, int64_t* launches, double* total_ms, double* bytes);
+   milliseconds, the algorithmic bytes they move (what each launch must read and write once,
+   by its arguments' sizes) and their algorithmic FP64 flops (an FMA counts 2). Synchronises
+   the recorded events. */
+int aao_profile_read(int cls, int64_t* launches, double* total_ms, double* bytes, double* fp64_flops);
 
 #ifdef __cplusplus
 }

@@ -99,7 +99,7 @@ def load(path=None):
     lib.aao_launch_count.restype = ctypes.c_uint64
     lib.aao_profile_enable.argtypes = [ctypes.c_int]
     lib.aao_profile_read.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
-                                     ctypes.POINTER(ctypes.c_double)]
+                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     for name in ("aao_create", "aao_destroy", "aao_rhs", "aao_matvec", "precond_apply", "precond_apply_static",
                  "fgmres_solve",
                  "fgmres_solve_host", "aao_profile_enable", "aao_profile_read", "aao_batch_create",
@@ -235,11 +235,11 @@ def aao_profile_enable(classes=None):
 
 
 def aao_profile_read(cls):
-    """(launches, total device ms, algorithmic bytes) recorded for a kernel class."""
+    """(launches, total device ms, algorithmic bytes, algorithmic FP64 flops) for a kernel class."""
     c = KERNEL_CLASSES.get(cls, cls)
-    n, ms, by = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
-    _check(load().aao_profile_read(int(c), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)))
-    return int(n.value), float(ms.value), float(by.value)
+    n, ms, by, fl = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(load().aao_profile_read(int(c), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by), ctypes.byref(fl)))
+    return int(n.value), float(ms.value), float(by.value), float(fl.value)
 
 
 class Batch:

@@ -43,20 +43,22 @@ extern std::atomic<uint64_t> g_launches;
 // ------------------------------------------------------------------ device timing
 // When enabled, every launch inside a ProfScope is bracketed by two CUDA events recorded on
 // the launching stream; aao_profile_read sums their elapsed times per kernel class.
+// Each scope also records the launch's algorithmic bytes (what it must read and write once) and
+// its algorithmic FP64 flops (an FMA counts 2), so that a roofline can name the binding resource.
 void prof_begin(int cls, cudaStream_t s);
-void prof_end(int cls, cudaStream_t s, double bytes);
+void prof_end(int cls, cudaStream_t s, double bytes, double fp64_flops);
 extern std::atomic<int> g_prof_mask;
 struct ProfScope {
   int cls;
   cudaStream_t s;
-  double bytes;
+  double bytes, flops;
   bool on;
-  ProfScope(int c, cudaStream_t st, double b = 0.0) : cls(c), s(st), bytes(b) {
+  ProfScope(int c, cudaStream_t st, double b = 0.0, double f = 0.0) : cls(c), s(st), bytes(b), flops(f) {
     on = (g_prof_mask.load(std::memory_order_relaxed) >> c) & 1;
     if (on) prof_begin(cls, s);
   }
   ~ProfScope() {
-    if (on) prof_end(cls, s, bytes);
+    if (on) prof_end(cls, s, bytes, flops);
   }
 };
 

@@ -23,6 +23,7 @@ struct ProfState {
   std::vector<cudaEvent_t> pool;                    // free events
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> done[AAO_K_COUNT];
   double bytes[AAO_K_COUNT] = {};
+  double flops[AAO_K_COUNT] = {};
   cudaEvent_t open[AAO_K_COUNT] = {};
 };
 ProfState& prof() {
@@ -49,11 +50,12 @@ void prof_begin(int cls, cudaStream_t s) {
   st.open[cls] = e;
 }
 
-void prof_end(int cls, cudaStream_t s, double bytes) {
+void prof_end(int cls, cudaStream_t s, double bytes, double fp64_flops) {
   ProfState& st = prof();
   std::lock_guard<std::mutex> lk(st.mu);
   if (!st.open[cls]) return;
   st.bytes[cls] += bytes;
+  st.flops[cls] += fp64_flops;
   cudaEvent_t e = take_event(st);
   cudaEventRecord(e, s);
   st.done[cls].emplace_back(st.open[cls], e);
@@ -72,7 +74,7 @@ int validate(const aao_problem* p) {
   if (p->payoff != AAO_PUT && p->payoff != AAO_CALL) { set_error("aao_create: unknown payoff"); return AAO_EINVAL; }
   if (p->precision != AAO_FP64 && p->precision != AAO_MIXED) { set_error("aao_create: unknown precision"); return AAO_EINVAL; }
   if (!is_pow2(p->nt)) { set_error("aao_create: nt must be a power of two"); return AAO_EUNSUPPORTED; }
-  const int nt_max = p->precision == AAO_MIXED ? 16384 : 8192;
+  const int nt_max = p->precision == AAO_MIXED ? 8192 : 4096;
   if (p->nt > nt_max) { set_error("aao_create: nt above the shared-memory FFT limit"); return AAO_EUNSUPPORTED; }
   const int nx_max = p->precision == AAO_MIXED ? 8192 : 4096;
   if (p->nx > nx_max) { set_error("aao_create: nx above the tridiagonal solver's limit (8192 mixed, 4096 FP64)"); return AAO_EUNSUPPORTED; }
@@ -191,13 +193,14 @@ int aao_profile_enable(int mask) {
     }
     st.done[c].clear();
     st.bytes[c] = 0.0;
+    st.flops[c] = 0.0;
   }
   g_prof_mask.store(mask);
   return AAO_OK;
 }
 
-int aao_profile_read(int cls, int64_t* launches, double* total_ms, double* bytes) {
-  if (cls < 0 || cls >= AAO_K_COUNT || !launches || !total_ms || !bytes) { set_error("aao_profile_read: bad argument"); return AAO_EINVAL; }
+int aao_profile_read(int cls, int64_t* launches, double* total_ms, double* bytes, double* fp64_flops) {
+  if (cls < 0 || cls >= AAO_K_COUNT || !launches || !total_ms || !bytes || !fp64_flops) { set_error("aao_profile_read: bad argument"); return AAO_EINVAL; }
   ProfState& st = prof();
   std::lock_guard<std::mutex> lk(st.mu);
   double tot = 0.0;
@@ -210,6 +213,7 @@ int aao_profile_read(int cls, int64_t* launches, double* total_ms, double* bytes
   *launches = (int64_t)st.done[cls].size();
   *total_ms = tot;
   *bytes = st.bytes[cls];
+  *fp64_flops = st.flops[cls];
   return AAO_OK;
 }
 

@@ -98,10 +98,16 @@ __device__ __noinline__ void cta_precond(const BatchInst& I, const double* v, fl
   const int G = kBT / I.tgrp;
   const int g = threadIdx.x / I.tgrp, tid = threadIdx.x - g * I.tgrp;
   const size_t gbytes = ((size_t)I.tgrp * I.cs + 8 * (size_t)I.tgrp) * sizeof(float2);
+  float* sa = reinterpret_cast<float*>(smem);
+  float* sd = sa + (size_t)I.tgrp * I.cs;
+  float* sc = sd + (size_t)I.tgrp * I.cs;
+  unsigned char* groups = smem + (((3 * (size_t)I.tgrp * I.cs * sizeof(float)) + 15) & ~(size_t)15);
+  tridiag_stage<float>(I.pL, I.pD, I.pU, I.nx, I.tgrp, I.ch, I.cs, sa, sd, sc);
+  __syncthreads();
   for (int k0 = 0; k0 < I.K; k0 += G) {
     const int k = k0 + g;
-    tridiag_bin<float, kCH>(I.spec, I.nx, I.pitch, I.ch, I.cs, I.pL, I.pD, I.pU, I.mu, I.il2, k < I.K ? k : 0, tid,
-                            I.tgrp, k < I.K, smem + g * gbytes);
+    tridiag_bin<float, kCH>(I.spec, I.nx, I.pitch, I.ch, I.cs, sa, sd, sc, I.mu, I.il2, k < I.K ? k : 0, tid,
+                            I.tgrp, k < I.K, groups + g * gbytes);
     __syncthreads();
   }
   for (int x0 = 0; x0 < I.nx; x0 += W) {
@@ -626,11 +632,13 @@ extern "C" int aao_batch_create(const aao_problem* ps, int n, int m, aao_batch**
     I.scal = reinterpret_cast<double*>(base + f.scal);
     B.gL.push_back(reinterpret_cast<double*>(base + f.gL));
     B.gR.push_back(reinterpret_cast<double*>(base + f.gR));
-    // shared memory: the FFT tile (P * nt <= 16 * kBT complex) or the tridiagonal groups
-    const size_t tri_b = (size_t)(kBT / I.tgrp) * ((size_t)I.tgrp * I.cs + 8 * (size_t)I.tgrp) * sizeof(float2);
+    // shared memory: the FFT tile and twiddles ((P + 1) * nt complex, P * nt <= 16 * kBT) or the
+    // staged diagonals plus the tridiagonal groups
+    const size_t tri_b = ((3 * (size_t)I.tgrp * I.cs * sizeof(float) + 15) & ~(size_t)15) +
+                         (size_t)(kBT / I.tgrp) * ((size_t)I.tgrp * I.cs + 8 * (size_t)I.tgrp) * sizeof(float2);
     smem = std::max(smem, tri_b);
+    smem = std::max(smem, (size_t)(16 * kBT + I.nt) * sizeof(float2));
   }
-  smem = std::max(smem, (size_t)16 * kBT * sizeof(float2));
   B.smem = smem;
   BTRY(cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   BTRY(cudaStreamSynchronize(B.s));

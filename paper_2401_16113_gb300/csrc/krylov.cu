@@ -422,11 +422,12 @@ void matvec_grid(const Handle& h, dim3& grid, int& tc) {
 }
 
 template <typename IN>
-int matvec_t(Handle& h, const IN* x, double* y, const double* b, const double* V, int nd, int m, double bytes) {
+int matvec_t(Handle& h, const IN* x, double* y, const double* b, const double* V, int nd, int m, double bytes,
+             double flops) {
   dim3 grid;
   int tc;
   matvec_grid(h, grid, tc);
-  ProfScope ps(AAO_K_MATVEC, h.stream, bytes);
+  ProfScope ps(AAO_K_MATVEC, h.stream, bytes, flops);
 #define AAO_MV2(ND)                                                                                    \
   k_matvec<IN, 2, ND><<<grid, kThreads, 0, h.stream>>>(x, y, nullptr, h.nx, h.nt, tc, h.mL, h.mD, h.mU, \
                                                        h.coef_rows, V, h.n, h.part, h.scal, h.counter, m)
@@ -462,8 +463,11 @@ int launch_matvec(Handle& h, const void* x, bool x_is_float, double* y, const do
   // x once, coefficients (3 per row of the time-dependent operator), y, b and V_q if present
   const double bytes = nn * (x_is_float ? 4.0 : 8.0) + 3.0 * 8.0 * (double)h.nx * h.coef_rows + nn * 8.0 +
                        (b ? nn * 8.0 : 0.0) + (V ? nn * 8.0 * nd : 0.0);
-  if (x_is_float) return matvec_t<float>(h, (const float*)x, y, b, V, nd, m, bytes);
-  return matvec_t<double>(h, (const double*)x, y, b, V, nd, m, bytes);
+  // per unknown: s and d (2 adds), three FMAs; residual: b - (1) and r.r (FMA); projections:
+  // nd FMAs and y.y (FMA)
+  const double flops = nn * (2.0 + 6.0 + (b ? 3.0 : 0.0) + (V ? 2.0 * (nd + 1) : 0.0));
+  if (x_is_float) return matvec_t<float>(h, (const float*)x, y, b, V, nd, m, bytes, flops);
+  return matvec_t<double>(h, (const double*)x, y, b, V, nd, m, bytes, flops);
 }
 
 void launch_rhs_raw(cudaStream_t s, double* b, int nx, int nt, const double* L, const double* D, const double* U,
@@ -500,7 +504,7 @@ int read_scalars(Handle& h, int first, int count) {
 int mdot(Handle& h, int c0, int cnt, const double* w, double* out) {
   const size_t n = h.n;
   const int g = grid_for(n);
-  ProfScope ps(AAO_K_ARNOLDI, h.stream, 8.0 * (double)n * (cnt + 1));
+  ProfScope ps(AAO_K_ARNOLDI, h.stream, 8.0 * (double)n * (cnt + 1), 2.0 * (double)n * cnt);
 #define AAO_MD(NV) k_mdot<NV><<<g, kThreads, 0, h.stream>>>(h.V, c0, n, w, h.part, out, h.counter)
   switch (cnt) {
     case 1: AAO_MD(1); break;
@@ -532,7 +536,7 @@ int update(Handle& h, double* w, int j, int pass) {
   const size_t n = h.n;
   const int g = grid_for(n);
   const int nv = j + 1;
-  ProfScope ps(AAO_K_ARNOLDI, h.stream, 8.0 * (double)n * (nv + 2));
+  ProfScope ps(AAO_K_ARNOLDI, h.stream, 8.0 * (double)n * (nv + 2), 2.0 * (double)n * (nv + 1));
 #define AAO_UP(NV) k_update<NV><<<g, kThreads, 0, h.stream>>>(w, h.V, j, n, pass, h.scal, h.part, h.counter)
   switch (nv) {
     case 1: AAO_UP(1); break;

@@ -153,9 +153,9 @@ extern "C" int precond_apply_static(const aao_problem* p, const double* v, doubl
     return AAO_EINVAL;
   }
   const bool mixed = p->precision == AAO_MIXED;
-  if (p->nx < 2 || !is_pow2(p->nt) || p->nt > (mixed ? 16384 : 8192) || p->nx > (mixed ? 8192 : 4096)) {
+  if (p->nx < 2 || !is_pow2(p->nt) || p->nt > (mixed ? 8192 : 4096) || p->nx > (mixed ? 8192 : 4096)) {
     set_error("precond_apply_static: need nx >= 2 (<= 8192 mixed, <= 4096 FP64) and nt a power of two "
-              "(<= 16384 mixed, <= 8192 FP64)");
+              "(<= 8192 mixed, <= 4096 FP64)");
     return AAO_EINVAL;
   }
   if (!(p->T > 0) || !(p->K > 0) || !(p->sigma > 0) || !(p->s_max > 0) || !(p->r >= 0) || !(p->alpha > 0) ||

@@ -54,7 +54,7 @@ int run_precond(Handle& h, const double* v, void* z, bool z_is_float, const doub
   const int N = h.nt, nx = h.nx;
   const int P = h.fft_p > 0 ? h.fft_p : default_tile(nx, N, sizeof(R));
   int threads = fft_threads(P, N, sizeof(R));
-  const size_t smem = (size_t)P * N * sizeof(C);
+  const size_t smem = (size_t)(P + 1) * N * sizeof(C);  // tile + twiddle table
   const int grid = (nx + 2 * P - 1) / (2 * P);
   C* spec = reinterpret_cast<C*>(h.spec);
   const R* lam = (sizeof(R) == 4) ? (const R*)h.lamf : (const R*)h.lam;
@@ -80,7 +80,13 @@ int run_precond(Handle& h, const double* v, void* z, bool z_is_float, const doub
   int ch = (nx + T - 1) / T;
   if (ch < 2) ch = 2;
   const int cs = (ch & 1) ? ch + 2 : ch + 1;  // odd chunk stride: conflict-free shared memory
-  const size_t smem2 = ((size_t)T * cs + 8 * (size_t)T) * sizeof(C);
+  const size_t gbytes = ((size_t)T * cs + 8 * (size_t)T) * sizeof(C);
+  const size_t cbytes = ((3 * (size_t)T * cs * sizeof(R)) + 15) & ~(size_t)15;
+  int G = (int)((96 * 1024 - cbytes) / gbytes);  // bins per CTA sharing the staged diagonals
+  if (G > 512 / T) G = 512 / T;
+  if (G > 4) G = 4;
+  if (G < 1) G = 1;
+  const size_t smem2 = cbytes + G * gbytes;
   const R* lo = (sizeof(R) == 4) ? (const R*)h.pLf : (const R*)h.pL;
   const R* di = (sizeof(R) == 4) ? (const R*)h.pDf : (const R*)h.pD;
   const R* up = (sizeof(R) == 4) ? (const R*)h.pUf : (const R*)h.pU;
@@ -89,7 +95,8 @@ int run_precond(Handle& h, const double* v, void* z, bool z_is_float, const doub
   AAO_TRY_CUDA(cudaFuncSetAttribute(k_tridiag<R, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
   {
     ProfScope ps(AAO_K_TRIDIAG, h.stream, 2.0 * nsp);
-    k_tridiag<R, CH><<<h.K, T, smem2, h.stream>>>(spec, nx, h.pitch, ch, cs, lo, di, up, mu, il2);
+    k_tridiag<R, CH><<<(h.K + G - 1) / G, G * T, smem2, h.stream>>>(spec, nx, h.K, h.pitch, ch, cs, T, lo, di, up,
+                                                                    mu, il2);
   }
   AAO_CHECK_LAUNCH();
 

@@ -42,7 +42,7 @@ __device__ __forceinline__ void stockham_stage(C* __restrict__ data, int log2n, 
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         C a = data[((j + r * stride_in) << lp) + p];
-        if (r > 0 && k > 0) a = cmul(a, __ldg(&tw[(r * k) << lts]));
+        if (r > 0 && k > 0) a = cmul(a, tw[(r * k) << lts]);
         reg[q][r] = a;
       }
     }
@@ -83,7 +83,8 @@ template <typename R> __device__ __forceinline__ R to_r(double v);
 template <> __device__ __forceinline__ float to_r<float>(double v) { return narrow(v); }
 template <> __device__ __forceinline__ double to_r<double>(double v) { return v; }
 
-// step (a) for the column tile starting at x0 (all threads of the CTA; smem holds P*N complex).
+// step (a) for the column tile starting at x0 (all threads of the CTA; smem holds (P+1)*N complex:
+// the tile, then a copy of the twiddle table).
 // Ends without a barrier: synchronise before reusing smem.
 template <typename R>
 __device__ __forceinline__ void fft_fwd_tile(const double* __restrict__ v, C_t<R>* __restrict__ spec, int nx, int N,
@@ -92,6 +93,8 @@ __device__ __forceinline__ void fft_fwd_tile(const double* __restrict__ v, C_t<R
   using C = C_t<R>;
   C* data = reinterpret_cast<C*>(smraw);
   R* flat = reinterpret_cast<R*>(smraw);
+  C* stw = data + (size_t)P * N;  // twiddle table copy (N complex) after the tile
+  for (int m = threadIdx.x; m < N; m += blockDim.x) stw[m] = __ldg(&tw[m]);
   // P is a power of two <= 16 and blockDim.x a multiple of 32, so W = 2P divides blockDim.x:
   // thread owns tile column c and rows t = tr, tr + tstep, ... (independent loads in flight)
   const int W = 2 * P;
@@ -107,7 +110,7 @@ __device__ __forceinline__ void fft_fwd_tile(const double* __restrict__ v, C_t<R
   }
   __syncthreads();
   const int lp = __ffs(P) - 1;
-  smem_fft(data, log2n, lp, tw);
+  smem_fft(data, log2n, lp, stw);
   const int half = N / 2;
   for (int e = threadIdx.x; e < (half + 1) * P; e += blockDim.x) {
     const int k = e >> lp, p = e & (P - 1);
@@ -133,7 +136,8 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 512 : 1024) k_fft_fwd(const d
   fft_fwd_tile<R>(v, spec, nx, N, log2n, P, pitch, lam, tw, sc, blockIdx.x * 2 * P, smraw);
 }
 
-// step (c) for the column tile starting at x0 (all threads of the CTA; smem holds P*N complex).
+// step (c) for the column tile starting at x0 (all threads of the CTA; smem holds (P+1)*N complex:
+// the tile, then a copy of the twiddle table).
 // Ends without a barrier: synchronise before reusing smem.
 template <typename R, typename OUT>
 __device__ __forceinline__ void fft_inv_tile(const C_t<R>* __restrict__ spec, OUT* __restrict__ z, int nx, int N,
@@ -141,6 +145,8 @@ __device__ __forceinline__ void fft_inv_tile(const C_t<R>* __restrict__ spec, OU
                                              const C_t<R>* __restrict__ tw, int x0, unsigned char* smraw) {
   using C = C_t<R>;
   C* data = reinterpret_cast<C*>(smraw);
+  C* stw = data + (size_t)P * N;  // twiddle table copy (N complex) after the tile
+  for (int m = threadIdx.x; m < N; m += blockDim.x) stw[m] = __ldg(&tw[m]);
   const int W = 2 * P;
   const int half = N / 2;
   const int lp = __ffs(P) - 1;
@@ -160,7 +166,7 @@ __device__ __forceinline__ void fft_inv_tile(const C_t<R>* __restrict__ spec, OU
     }
   }
   __syncthreads();
-  smem_fft(data, log2n, lp, tw);
+  smem_fft(data, log2n, lp, stw);
   const int c = threadIdx.x & (W - 1), tr = threadIdx.x / W, tstep = blockDim.x / W;
   const int x = x0 + c;
   if (x < nx) {
@@ -189,13 +195,28 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 512 : 1024) k_fft_inv(const C
 // registers, right-hand sides in shared memory); the 2T first/last rows form a tridiagonal
 // interface system solved by parallel cyclic reduction in shared memory; back substitution
 // recovers the interior rows.
+// Stage the diagonals of tau*Abar for the row layout of tridiag_bin: row i = L*ch + j goes to
+// L*cs + j (odd stride cs: conflict-free per-thread chunks). a_i = -lo_i (0 for i = 0), c_i =
+// -up_i (0 for i = nx-1), rows i >= nx are padding. All threads of the CTA; synchronise after.
+template <typename R>
+__device__ __forceinline__ void tridiag_stage(const R* __restrict__ lo, const R* __restrict__ di,
+                                              const R* __restrict__ up, int nx, int T, int ch, int cs, R* sa,
+                                              R* sd, R* sc) {
+  for (int i = threadIdx.x; i < T * ch; i += blockDim.x) {
+    const int L = i / ch, j = i - L * ch, o = L * cs + j;
+    sa[o] = (i > 0 && i < nx) ? -__ldg(&lo[i]) : (R)0;
+    sd[o] = i < nx ? __ldg(&di[i]) : (R)0;
+    sc[o] = (i < nx - 1) ? -__ldg(&up[i]) : (R)0;
+  }
+}
+
 // The solve of bin k by a group of T threads (thread tid of the group) with smem region smraw of
-// (T*cs + 8T) complex. Every thread of the CTA must call it together (it uses __syncthreads); a
-// group with valid == false takes part in the barriers only.
+// (T*cs + 8T) complex and the staged diagonals sa, sd, sc. Every thread of the CTA must call it
+// together (it uses __syncthreads); a group with valid == false takes part in the barriers only.
 template <typename R, int CH>
 __device__ __forceinline__ void tridiag_bin(C_t<R>* __restrict__ spec, int nx, int pitch, int ch, int cs,
-                                            const R* __restrict__ lo, const R* __restrict__ di,
-                                            const R* __restrict__ up, const C_t<R>* __restrict__ mu,
+                                            const R* __restrict__ sa, const R* __restrict__ sd,
+                                            const R* __restrict__ sc, const C_t<R>* __restrict__ mu,
                                             const C_t<R>* __restrict__ il2, int k, int tid, int T, bool valid,
                                             unsigned char* smraw) {
   using C = C_t<R>;
@@ -221,12 +242,9 @@ __device__ __forceinline__ void tridiag_bin(C_t<R>* __restrict__ spec, int nx, i
   for (int j = 0; j < CH; ++j) {
     if (j < ch) {
       const int i = s + j;
-      C a = zero, b = one, c = zero;
-      if (i < nx) {
-        a = cmk<C>(i > 0 ? -__ldg(&lo[i]) : (R)0, 0);
-        b = cmk<C>(muk.x - __ldg(&di[i]), muk.y);
-        c = cmk<C>(i < nx - 1 ? -__ldg(&up[i]) : (R)0, 0);
-      }
+      const int o = tid * cs + j;
+      const C a = cmk<C>(sa[o], 0), c = cmk<C>(sc[o], 0);
+      const C b = i < nx ? cmk<C>(muk.x - sd[o], muk.y) : one;
       C dj;
       if (j < 2) {
         const C ib = cinv(b);
@@ -304,13 +322,27 @@ __device__ __forceinline__ void tridiag_bin(C_t<R>* __restrict__ spec, int nx, i
   }
 }
 
+// G groups of T threads per CTA, one bin per group (bins blockIdx.x * G + g); the diagonals are
+// staged once per CTA and shared by the groups.
 template <typename R, int CH>
-__global__ void __launch_bounds__(512) k_tridiag(C_t<R>* __restrict__ spec, int nx, int pitch, int ch, int cs,
-                                                 const R* __restrict__ lo, const R* __restrict__ di,
+__global__ void __launch_bounds__(512) k_tridiag(C_t<R>* __restrict__ spec, int nx, int K, int pitch, int ch,
+                                                 int cs, int T, const R* __restrict__ lo, const R* __restrict__ di,
                                                  const R* __restrict__ up, const C_t<R>* __restrict__ mu,
                                                  const C_t<R>* __restrict__ il2) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  tridiag_bin<R, CH>(spec, nx, pitch, ch, cs, lo, di, up, mu, il2, blockIdx.x, threadIdx.x, blockDim.x, true, smraw);
+  using C = C_t<R>;
+  const int G = blockDim.x / T;
+  R* sa = reinterpret_cast<R*>(smraw);
+  R* sd = sa + (size_t)T * cs;
+  R* sc = sd + (size_t)T * cs;
+  unsigned char* groups = reinterpret_cast<unsigned char*>(sc + (size_t)T * cs);
+  groups = reinterpret_cast<unsigned char*>(((size_t)groups + 15) & ~(size_t)15);
+  tridiag_stage<R>(lo, di, up, nx, T, ch, cs, sa, sd, sc);
+  __syncthreads();
+  const int g = threadIdx.x / T, tid = threadIdx.x - g * T;
+  const int k = blockIdx.x * G + g;
+  const size_t gbytes = ((size_t)T * cs + 8 * (size_t)T) * sizeof(C);
+  tridiag_bin<R, CH>(spec, nx, pitch, ch, cs, sa, sd, sc, mu, il2, k < K ? k : 0, tid, T, k < K, groups + g * gbytes);
 }
 
 
