@@ -204,11 +204,18 @@ def sequential_cn(p):
     _, tau = time_grid(p)
     u = payoff(p)
     out = np.empty((nt, u.size))
+    lu = None
     for k in range(nt):
         A, _, _ = step_operator(p, k)
         I = _eye_like(A)
         rhs = (I + 0.5 * tau * A) @ u + tau * forcing(p, k)
-        u = _solve(I - 0.5 * tau * A, rhs)
+        if not sp.issparse(A) and p["op"] != "localvol":
+            # constant dense A: the same matrix I - tau/2 A at every step, factored once
+            if lu is None:
+                lu = sla.lu_factor(I - 0.5 * tau * A)
+            u = sla.lu_solve(lu, rhs)
+        else:
+            u = _solve(I - 0.5 * tau * A, rhs)
         out[k] = u
     return out
 
@@ -250,6 +257,18 @@ def matvec(p, x, M=None):
     if M is None:
         M = assemble_M(p)
     return M @ x
+
+
+def matvec_blocks(p, x):
+    """y = M x by the block rows of Eq. 2.2 for a constant A: y_t = Q1 x_t - Q2 x_{t-1},
+    Q1 = I - A~/2, Q2 = I + A~/2 (dense A, all time levels in one matrix product)."""
+    nt, nx = int(p["nt"]), int(p["nx"])
+    _, tau = time_grid(p)
+    A = _dense(step_operator(p, 0)[0])
+    X = np.asarray(x, dtype=np.float64).reshape(nt, nx)
+    Xm = np.vstack([np.zeros((1, nx)), X[:-1]])
+    S = X + Xm
+    return ((X - Xm) - 0.5 * tau * (S @ A.T)).reshape(-1)
 
 
 # ----------------------------------------------------------------------------------------

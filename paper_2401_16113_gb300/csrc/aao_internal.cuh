@@ -145,6 +145,13 @@ struct Handle {
   void* spec = nullptr;   // half spectrum, K * pitch complex (float2 or double2)
   int fft_p = 0;          // FFT tile: 2*fft_p spatial columns per CTA (0 = heuristic)
 
+  // Riesz operator (dense Toeplitz): circulant-embedding spectrum (scaled by tau/2 / N2), its
+  // twiddles, (tau/2) first column / row / left-exterior coefficients, LU factors of step (b)
+  int rz_n2 = 0, rz_log2n2 = 0;
+  double2 *rz_chat = nullptr, *rz_tw = nullptr;
+  double *rz_hcol = nullptr, *rz_hrow = nullptr, *rz_hcl = nullptr;
+  float2* rz_lu = nullptr;
+
   // FGMRES workspace (grown on demand)
   int ws_m = 0;
   double* V = nullptr;    // (m+1) * n
@@ -161,6 +168,10 @@ struct Handle {
 int build_tables(Handle& h);
 int launch_precond(Handle& h, const double* v, void* z, bool z_is_float, const double* in_scale = nullptr);
 int tune_precond(Handle& h);
+int riesz_build(Handle& h);
+int riesz_matvec(Handle& h, const void* x, bool x_is_float, double* y, const double* b, const double* V, int nd, int m);
+int riesz_rhs(Handle& h, double* b);
+int riesz_solve_bins(Handle& h, void* spec);
 int launch_matvec(Handle& h, const void* x, bool x_is_float, double* y, const double* b, const double* V = nullptr,
                   int nd = 0, int m = 0);
 int launch_rhs(Handle& h, double* b);

@@ -69,8 +69,14 @@ bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 int validate(const aao_problem* p) {
   if (!p) { set_error("aao_create: null problem"); return AAO_EINVAL; }
   if (p->nx < 2 || p->nt < 1) { set_error("aao_create: need nx >= 2 and nt >= 1"); return AAO_EINVAL; }
-  if (p->op == AAO_OP_RIESZ) { set_error("aao_create: the Riesz operator is not built in this library"); return AAO_EUNSUPPORTED; }
-  if (p->op != AAO_OP_BS && p->op != AAO_OP_LOCALVOL) { set_error("aao_create: unknown op"); return AAO_EINVAL; }
+  if (p->op != AAO_OP_BS && p->op != AAO_OP_LOCALVOL && p->op != AAO_OP_RIESZ) { set_error("aao_create: unknown op"); return AAO_EINVAL; }
+  if (p->op == AAO_OP_RIESZ) {
+    if (p->precision != AAO_MIXED) { set_error("aao_create: the Riesz operator is built for precision AAO_MIXED only"); return AAO_EUNSUPPORTED; }
+    if (!(p->beta > 1.0) || !(p->beta <= 2.0)) { set_error("aao_create: Riesz order beta must lie in (1, 2]"); return AAO_EINVAL; }
+    if (p->nx > 2048) { set_error("aao_create: Riesz operator needs nx <= 2048"); return AAO_EUNSUPPORTED; }
+    const double factors = (double)(p->nt / 2 + 1) * p->nx * (double)p->nx * 8.0;
+    if (factors > 32e9) { set_error("aao_create: Riesz LU factors would exceed 32 GB"); return AAO_EUNSUPPORTED; }
+  }
   if (p->payoff != AAO_PUT && p->payoff != AAO_CALL) { set_error("aao_create: unknown payoff"); return AAO_EINVAL; }
   if (p->precision != AAO_FP64 && p->precision != AAO_MIXED) { set_error("aao_create: unknown precision"); return AAO_EINVAL; }
   if (!is_pow2(p->nt)) { set_error("aao_create: nt must be a power of two"); return AAO_EUNSUPPORTED; }

@@ -283,6 +283,7 @@ int build_tables(Handle& h) {
   const aao_problem& p = h.p;
   const int nx = h.nx, nt = h.nt, N = nt;
   h.tau = p.T / nt;
+  const bool riesz = p.op == AAO_OP_RIESZ;
   const double hS = p.s_max / (nx + 1);
   h.coef_rows = (p.op == AAO_OP_LOCALVOL) ? nt : 1;
   const size_t ncoef = (size_t)nx * h.coef_rows;
@@ -296,6 +297,7 @@ int build_tables(Handle& h) {
     gS[i] = exp(-l * l);
   }
   double* d_gS = nullptr;
+  if (!riesz) {
   AAO_TRY_CUDA(cudaMalloc(&h.mL, sizeof(double) * ncoef));
   AAO_TRY_CUDA(cudaMalloc(&h.mD, sizeof(double) * ncoef));
   AAO_TRY_CUDA(cudaMalloc(&h.mU, sizeof(double) * ncoef));
@@ -317,6 +319,7 @@ int build_tables(Handle& h) {
   AAO_TRY_CUDA(cudaMalloc(&h.gR, sizeof(double) * (nt + 1)));
   AAO_TRY_CUDA(cudaMemcpyAsync(h.gL, gl.data(), sizeof(double) * (nt + 1), cudaMemcpyHostToDevice, h.stream));
   AAO_TRY_CUDA(cudaMemcpyAsync(h.gR, gr.data(), sizeof(double) * (nt + 1), cudaMemcpyHostToDevice, h.stream));
+  }  // !riesz
 
   // preconditioner operator tau * Abar: time mean of sigma^2 in closed form,
   // mean_k (s0 + b_i c_k)^2 = s0^2 + 2 s0 b_i mean(c) + b_i^2 mean(c^2)
@@ -375,8 +378,10 @@ int build_tables(Handle& h) {
     AAO_TRY_CUDA(cudaMemcpyAsync(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, h.stream));
     return AAO_OK;
   };
-  AAO_TRY(up(&h.pL, pl)); AAO_TRY(up(&h.pD, pd)); AAO_TRY(up(&h.pU, pu));
-  AAO_TRY(up(&h.pLf, plf)); AAO_TRY(up(&h.pDf, pdf)); AAO_TRY(up(&h.pUf, puf));
+  if (!riesz) {
+    AAO_TRY(up(&h.pL, pl)); AAO_TRY(up(&h.pD, pd)); AAO_TRY(up(&h.pU, pu));
+    AAO_TRY(up(&h.pLf, plf)); AAO_TRY(up(&h.pDf, pdf)); AAO_TRY(up(&h.pUf, puf));
+  }
   AAO_TRY(up(&h.mu, mu)); AAO_TRY(up(&h.il2, il2)); AAO_TRY(up(&h.tw, tw));
   AAO_TRY(up(&h.muf, muf)); AAO_TRY(up(&h.il2f, il2f)); AAO_TRY(up(&h.twf, twf));
   AAO_TRY(up(&h.lam, lam)); AAO_TRY(up(&h.ilam, ilam));
@@ -394,14 +399,15 @@ int build_tables(Handle& h) {
   AAO_TRY_CUDA(cudaMallocHost(&h.host_scal, sizeof(double) * 8));
   // the temporary gS buffer must outlive the build kernel
   AAO_TRY_CUDA(cudaStreamSynchronize(h.stream));
-  cudaFree(d_gS);
+  if (d_gS) cudaFree(d_gS);
+  if (riesz) AAO_TRY(riesz_build(h));
   return AAO_OK;
 }
 
 void free_handle(Handle& h) {
   void* bufs[] = {h.mL, h.mD, h.mU, h.gL, h.gR, h.pL, h.pD, h.pU, h.pLf, h.pDf, h.pUf, h.mu, h.il2, h.tw,
                   h.muf, h.il2f, h.twf, h.lam, h.ilam, h.lamf, h.ilamf, h.spec, h.V, h.Z, h.w, h.scal, h.part,
-                  h.counter};
+                  h.counter, h.rz_chat, h.rz_tw, h.rz_hcol, h.rz_hrow, h.rz_hcl, h.rz_lu};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (h.host_scal) cudaFreeHost(h.host_scal);
@@ -459,6 +465,7 @@ int matvec_t(Handle& h, const IN* x, double* y, const double* b, const double* V
 // y = M x; with b: y = b - M x (restart residual); with V (nd <= 8): first Gram-Schmidt pass
 int launch_matvec(Handle& h, const void* x, bool x_is_float, double* y, const double* b, const double* V, int nd,
                   int m) {
+  if (h.p.op == AAO_OP_RIESZ) return riesz_matvec(h, x, x_is_float, y, b, V, nd, m);
   const double nn = (double)h.n;
   // x once, coefficients (3 per row of the time-dependent operator), y, b and V_q if present
   const double bytes = nn * (x_is_float ? 4.0 : 8.0) + 3.0 * 8.0 * (double)h.nx * h.coef_rows + nn * 8.0 +
@@ -482,6 +489,7 @@ void launch_coef_raw(cudaStream_t s, double* L, double* D, double* U, int nx, in
 }
 
 int launch_rhs(Handle& h, double* b) {
+  if (h.p.op == AAO_OP_RIESZ) return riesz_rhs(h, b);
   k_rhs<<<grid_for(h.n), kThreads, 0, h.stream>>>(b, h.nx, h.nt, h.mL, h.mD, h.mU, h.coef_rows, h.gL, h.gR,
                                                    h.p.s_max / (h.nx + 1), h.p.K, h.p.payoff);
   AAO_CHECK_LAUNCH();

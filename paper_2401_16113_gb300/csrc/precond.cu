@@ -70,6 +70,10 @@ int run_precond(Handle& h, const double* v, void* z, bool z_is_float, const doub
   }
   AAO_CHECK_LAUNCH();
 
+  if (h.p.op == AAO_OP_RIESZ) {
+    // step (b) with the dense Toeplitz operator: LU factors from aao_create
+    AAO_TRY(riesz_solve_bins(h, spec));
+  } else {
   // step (b): threads per bin T (multiple of 32, <= 512), chunk ch <= CH rows per thread
   constexpr int CH = sizeof(R) == 4 ? 16 : 8;
   int T = 32 * ((nx + 32 * CH - 1) / (32 * CH));
@@ -98,6 +102,7 @@ int run_precond(Handle& h, const double* v, void* z, bool z_is_float, const doub
     k_tridiag<R, CH><<<(h.K + G - 1) / G, G * T, smem2, h.stream>>>(spec, nx, h.K, h.pitch, ch, cs, T, lo, di, up,
                                                                     mu, il2);
   }
+  }  // tridiagonal operators
   AAO_CHECK_LAUNCH();
 
   if (z_is_float) {

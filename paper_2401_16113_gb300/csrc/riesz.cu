@@ -1,0 +1,523 @@
+// The Riesz fractional operator (Eq. 1.2, second case) in log-price: a dense Toeplitz A.
+//
+//   A = -kappa h^-beta toeplitz(g_|i-j|) + (r - kappa)/(2h) (central first difference) - r I,
+//   kappa = sigma^2/2, g_k = (-1)^k Gamma(beta+1)/(Gamma(beta/2-k+1) Gamma(beta/2+k+1)) (fractional
+//   centred difference, computed by its recurrence g_{k+1} = g_k (k - beta/2)/(beta/2 + k + 1)).
+//   The nodes beyond x = -x_max carry the left Dirichlet value K e^{-rt} - e^{-x_max}, those beyond
+//   x = x_max carry 0; row i collects sum_{m > i} g_m = -g_0/2 - sum_{m=1}^{i} g_m of the left ones.
+//
+// Kernels:
+//   k_rz_matvec  FP64 y = M x with the Toeplitz product A s by circulant embedding of length
+//                N2 >= 2 nx - 1: two time levels are packed as the real and imaginary parts of one
+//                complex FFT (A is real), forward FFT, pointwise product with the circulant's
+//                spectrum, inverse FFT (shared-memory Stockham, FP64). Fused with the residual norm
+//                or the first Gram-Schmidt projections, finished by the last block.
+//   k_rz_rhs     b = xi + tau f (xi needs one dense product A u^0).
+//   k_rz_form / k_lu_panel / k_lu_trsm / k_lu_update
+//                at aao_create: the shifted matrices mu_k I - A~ of step (b) of Eq. 3.2 for the
+//                nt/2+1 bins, factored in place by blocked right-looking LU without pivoting
+//                (FP32 complex; the matrices are diagonally dominant, see the design notes).
+//   k_rz_trsv    per apply: forward (unit L) and backward (U) blocked substitution of every bin.
+#include <math.h>
+
+#include <complex>
+#include <vector>
+
+#include "krylov_dev.cuh"
+#include "precond_dev.cuh"
+
+namespace aao {
+
+namespace {
+
+using namespace kdev;
+using namespace pdev;
+
+constexpr int kNB = 32;  // LU / substitution block
+
+// ------------------------------------------------------------------------------- matvec
+template <typename IN, int MODE, int ND>
+__global__ void __launch_bounds__(256) k_rz_matvec(const IN* __restrict__ x, double* __restrict__ y,
+                                                   const double* __restrict__ b, int nx, int nt, int n2, int log2n2,
+                                                   const double2* __restrict__ chat, const double2* __restrict__ tw2,
+                                                   const double* __restrict__ V, size_t vstride,
+                                                   double* __restrict__ part, double* __restrict__ scal,
+                                                   unsigned int* __restrict__ counter, int m) {
+  constexpr int NA = MODE == 2 ? ND + 1 : 1;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double2* data = reinterpret_cast<double2*>(smraw);
+  double2* stw = data + n2;
+  const int t0 = 2 * blockIdx.x, t1 = t0 + 1;
+  const bool has1 = t1 < nt;
+  for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+    stw[i] = tw2[i];
+    double s0 = 0.0, s1 = 0.0;
+    if (i < nx) {
+      const double x0 = ld(x + (size_t)t0 * nx + i);
+      const double xm = t0 > 0 ? ld(x + (size_t)(t0 - 1) * nx + i) : 0.0;
+      s0 = x0 + xm;
+      if (has1) s1 = ld(x + (size_t)t1 * nx + i) + x0;
+    }
+    data[i] = make_double2(s0, s1);
+  }
+  __syncthreads();
+  smem_fft(data, log2n2, 0, stw);
+  // pointwise product with the circulant spectrum (already scaled by tau/2 / N2), conjugated so
+  // that a second forward transform gives the conjugate of the inverse transform
+  for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+    const double2 z = data[i], c = chat[i];
+    data[i] = make_double2(z.x * c.x - z.y * c.y, -(z.x * c.y + z.y * c.x));
+  }
+  __syncthreads();
+  smem_fft(data, log2n2, 0, stw);
+  double acc[NA];
+#pragma unroll
+  for (int q = 0; q < NA; ++q) acc[q] = 0.0;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+    const double2 r = data[i];  // conj of (tau/2 A s): real part row t0, -imag part row t1
+    for (int h = 0; h < 2; ++h) {
+      const int t = t0 + h;
+      if (t >= nt) break;
+      const size_t e = (size_t)t * nx + i;
+      const double xc = ld(x + e);
+      const double xm = t > 0 ? ld(x + e - nx) : 0.0;
+      double v = (xc - xm) - (h == 0 ? r.x : -r.y);
+      if (MODE == 1) {
+        v = __ldg(b + e) - v;
+        acc[0] = fma(v, v, acc[0]);
+      }
+      y[e] = v;
+      if (MODE == 2) {
+#pragma unroll
+        for (int q = 0; q < ND; ++q) acc[q] = fma(__ldg(V + (size_t)q * vstride + e), v, acc[q]);
+        acc[ND] = fma(v, v, acc[ND]);
+      }
+    }
+  }
+  if constexpr (MODE == 0) return;
+  __shared__ double red[8][NA];
+  {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NA; ++q) {
+      const double v = warp_sum(acc[q]);
+      if (lane == 0) red[warp][q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < NA) {
+      double s = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
+      part[(size_t)blockIdx.x * kPartLd + threadIdx.x] = s;
+    }
+  }
+  __shared__ bool am_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) am_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < NA; ++q) {
+      double s = 0.0;
+      for (unsigned bb = 0; bb < gridDim.x; ++bb) s += __ldcg(part + (size_t)bb * kPartLd + q);
+      if (MODE == 2) {
+        scal[q < ND ? S_D1 + q : S_WN2] = s;
+      } else {
+        scal[S_BETA2] = s;
+        const double beta = sqrt(s);
+        scal[S_SIG] = beta > 0.0 ? 1.0 / beta : 0.0;
+        scal[S_G] = beta;
+        for (int k = 1; k <= m; ++k) scal[S_G + k] = 0.0;
+        scal[S_FLAG] = isfinite(s) ? 0.0 : 1.0;
+      }
+    }
+    *counter = 0u;
+  }
+}
+
+// b = xi + tau f: f from the left exterior value averaged over t_k and t_{k+1}; xi = u0 + A~ u0 / 2
+__global__ void k_rz_rhs(double* __restrict__ b, int nx, int nt, const double* __restrict__ hcol,
+                         const double* __restrict__ hrow, const double* __restrict__ hcl,
+                         const double* __restrict__ gL, double xmax, double h, double K) {
+  const size_t n = (size_t)nx * nt;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const int t = (int)(e / nx), i = (int)(e - (size_t)t * nx);
+    double v = hcl[i] * (gL[t] + gL[t + 1]);
+    if (t == 0) {
+      auto u0 = [&](int j) { return fmax(K - exp(-xmax + h * (j + 1)), 0.0); };
+      double a = u0(i);
+      for (int j = 0; j < nx; ++j) a = fma(j <= i ? hcol[i - j] : hrow[j - i], u0(j), a);
+      v += a;
+    }
+    b[e] = v;
+  }
+}
+
+// ------------------------------------------------------------------------------- LU at create
+// M_k = mu_k I - A~ (row-major, complex FP32), A~ = tau A from its first column / row
+__global__ void k_rz_form(float2* __restrict__ M, int nx, const double* __restrict__ tcol,
+                          const double* __restrict__ trow, const float2* __restrict__ mu) {
+  const int k = blockIdx.y;
+  const size_t nn = (size_t)nx * nx;
+  float2* Mk = M + (size_t)k * nn;
+  const float2 muk = mu[k];
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / nx), j = (int)(e - (size_t)i * nx);
+    const double a = j <= i ? tcol[i - j] : trow[j - i];
+    Mk[e] = make_float2((float)((i == j ? (double)muk.x : 0.0) - a), i == j ? muk.y : 0.f);
+  }
+}
+
+// unblocked LU of the panel rows [kb, n), columns [kb, kb+w): one CTA per bin
+__global__ void __launch_bounds__(256) k_lu_panel(float2* __restrict__ M, int n, int kb, int w) {
+  float2* A = M + (size_t)blockIdx.x * n * n;
+  __shared__ float2 prow[kNB];
+  for (int j = kb; j < kb + w; ++j) {
+    if (threadIdx.x < kb + w - j) prow[threadIdx.x] = A[(size_t)j * n + j + threadIdx.x];
+    __syncthreads();
+    const float2 inv = cinv(prow[0]);
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
+      float2* ri = A + (size_t)i * n;
+      const float2 l = cmul(ri[j], inv);
+      ri[j] = l;
+      for (int c = 1; c < kb + w - j; ++c) ri[j + c] = csub(ri[j + c], cmul(l, prow[c]));
+    }
+    __syncthreads();
+  }
+}
+
+// U12 = L11^{-1} A12 for rows [kb, kb+w) and columns [kb+w, n): one thread per column
+__global__ void k_lu_trsm(float2* __restrict__ M, int n, int kb, int w) {
+  float2* A = M + (size_t)blockIdx.y * n * n;
+  const int c = kb + w + blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  float2 col[kNB];
+  for (int i = 0; i < w; ++i) col[i] = A[(size_t)(kb + i) * n + c];
+  for (int i = 1; i < w; ++i) {
+    float2 s = col[i];
+    for (int j = 0; j < i; ++j) s = csub(s, cmul(A[(size_t)(kb + i) * n + kb + j], col[j]));
+    col[i] = s;
+  }
+  for (int i = 1; i < w; ++i) A[(size_t)(kb + i) * n + c] = col[i];
+}
+
+// A22 -= L21 U12, rows and columns [kb+w, n), inner dimension w <= 32: 64 x 64 tiles, 4 x 4 per thread
+__global__ void __launch_bounds__(256) k_lu_update(float2* __restrict__ M, int n, int kb, int w) {
+  float2* A = M + (size_t)blockIdx.z * n * n;
+  const int r0 = kb + w + blockIdx.y * 64, c0 = kb + w + blockIdx.x * 64;
+  __shared__ float2 Ls[64][kNB + 1];
+  __shared__ float2 Us[kNB][64 + 1];
+  for (int e = threadIdx.x; e < 64 * kNB; e += blockDim.x) {
+    const int r = e / kNB, k = e % kNB;
+    Ls[r][k] = (r0 + r < n && k < w) ? A[(size_t)(r0 + r) * n + kb + k] : make_float2(0.f, 0.f);
+    const int kk = e / 64, c = e % 64;
+    Us[kk][c] = (c0 + c < n && kk < w) ? A[(size_t)(kb + kk) * n + c0 + c] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  const int tr = threadIdx.x / 16, tc = threadIdx.x % 16;
+  float2 acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[a][q] = make_float2(0.f, 0.f);
+  for (int k = 0; k < w; ++k) {
+    float2 l[4], u[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) l[a] = Ls[tr + 16 * a][k];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) u[q] = Us[k][tc + 16 * q];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        acc[a][q].x = fmaf(l[a].x, u[q].x, fmaf(-l[a].y, u[q].y, acc[a][q].x));
+        acc[a][q].y = fmaf(l[a].x, u[q].y, fmaf(l[a].y, u[q].x, acc[a][q].y));
+      }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = r0 + tr + 16 * a, c = c0 + tc + 16 * q;
+      if (r < n && c < n) {
+        float2* p = A + (size_t)r * n + c;
+        *p = csub(*p, acc[a][q]);
+      }
+    }
+}
+
+// ------------------------------------------------------------------------------- solves per apply
+// Bin k: (mu_k I - A~) z = z1_k / lambda2_k with the LU factors; in place on the half spectrum.
+__global__ void __launch_bounds__(256) k_rz_trsv(float2* __restrict__ spec, int nx, int pitch,
+                                                 const float2* __restrict__ LU, const float2* __restrict__ il2) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* z = reinterpret_cast<float2*>(smraw);  // nx
+  float2* acc = z + nx;                          // kNB
+  const int k = blockIdx.x;
+  const float2* A = LU + (size_t)k * nx * nx;
+  float2* row = spec + (size_t)k * pitch;
+  const float2 sk = il2[k];
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) z[i] = cmul(row[i], sk);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nb = (nx + kNB - 1) / kNB;
+  // forward: L y = z (unit lower)
+  for (int bi = 0; bi < nb; ++bi) {
+    const int r0 = bi * kNB, r1 = min(nx, r0 + kNB);
+    for (int i = r0 + warp; i < r1; i += nw) {
+      const float2* ri = A + (size_t)i * nx;
+      float sx = 0.f, sy = 0.f;
+      for (int j = lane; j < r0; j += 32) {
+        const float2 l = __ldg(ri + j), v = z[j];
+        sx = fmaf(l.x, v.x, fmaf(-l.y, v.y, sx));
+        sy = fmaf(l.x, v.y, fmaf(l.y, v.x, sy));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_down_sync(0xffffffffu, sx, o);
+        sy += __shfl_down_sync(0xffffffffu, sy, o);
+      }
+      if (lane == 0) acc[i - r0] = make_float2(sx, sy);
+    }
+    __syncthreads();
+    if (warp == 0) {
+      // the diagonal block: lane j holds z_j of the block; row by row
+      const int w = r1 - r0;
+      float2 zj = lane < w ? csub(z[r0 + lane], acc[lane]) : make_float2(0.f, 0.f);
+      for (int i = 1; i < w; ++i) {
+        const float2 l = lane < i ? __ldg(A + (size_t)(r0 + i) * nx + r0 + lane) : make_float2(0.f, 0.f);
+        const float2 p = cmul(l, zj);
+        float px = p.x, py = p.y;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          px += __shfl_xor_sync(0xffffffffu, px, o);
+          py += __shfl_xor_sync(0xffffffffu, py, o);
+        }
+        if (lane == i) zj = make_float2(zj.x - px, zj.y - py);
+      }
+      if (lane < w) z[r0 + lane] = zj;
+    }
+    __syncthreads();
+  }
+  // backward: U x = y
+  for (int bi = nb - 1; bi >= 0; --bi) {
+    const int r0 = bi * kNB, r1 = min(nx, r0 + kNB);
+    for (int i = r0 + warp; i < r1; i += nw) {
+      const float2* ri = A + (size_t)i * nx;
+      float sx = 0.f, sy = 0.f;
+      for (int j = r1 + lane; j < nx; j += 32) {
+        const float2 u = __ldg(ri + j), v = z[j];
+        sx = fmaf(u.x, v.x, fmaf(-u.y, v.y, sx));
+        sy = fmaf(u.x, v.y, fmaf(u.y, v.x, sy));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_down_sync(0xffffffffu, sx, o);
+        sy += __shfl_down_sync(0xffffffffu, sy, o);
+      }
+      if (lane == 0) acc[i - r0] = make_float2(sx, sy);
+    }
+    __syncthreads();
+    if (warp == 0) {
+      const int w = r1 - r0;
+      float2 zj = lane < w ? csub(z[r0 + lane], acc[lane]) : make_float2(0.f, 0.f);
+      const float2 dj = lane < w ? __ldg(A + (size_t)(r0 + lane) * nx + r0 + lane) : make_float2(1.f, 0.f);
+      for (int i = w - 1; i >= 0; --i) {
+        if (lane == i) zj = cmul(zj, cinv(dj));
+        const float2 xi = make_float2(__shfl_sync(0xffffffffu, zj.x, i), __shfl_sync(0xffffffffu, zj.y, i));
+        if (lane < i) {
+          const float2 u = __ldg(A + (size_t)(r0 + lane) * nx + r0 + i);
+          zj = csub(zj, cmul(u, xi));
+        }
+      }
+      if (lane < w) z[r0 + lane] = zj;
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) row[i] = z[i];
+}
+
+int grid_for(size_t n) {
+  size_t g = (n + kThreads - 1) / kThreads;
+  return (int)(g < (size_t)kRedBlocks ? g : (size_t)kRedBlocks);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------- host
+int riesz_build(Handle& h) {
+  const aao_problem& p = h.p;
+  const int nx = h.nx, nt = h.nt;
+  const double xmax = p.s_max, hx = 2.0 * xmax / (nx + 1);
+  const double kappa = 0.5 * p.sigma * p.sigma;
+  const double c0 = -kappa * pow(hx, -p.beta);
+  const double dr = (p.r - kappa) / (2.0 * hx);
+  // fractional centred difference weights by recurrence
+  std::vector<double> g(nx + 1);
+  g[0] = tgamma(p.beta + 1.0) / (tgamma(0.5 * p.beta + 1.0) * tgamma(0.5 * p.beta + 1.0));
+  for (int k = 0; k < nx; ++k) g[k + 1] = g[k] * ((double)k - 0.5 * p.beta) / (0.5 * p.beta + k + 1.0);
+  // first column / row of A
+  std::vector<double> col(nx), row(nx);
+  for (int k = 0; k < nx; ++k) {
+    col[k] = c0 * g[k] - (k == 1 ? dr : 0.0) - (k == 0 ? p.r : 0.0);
+    row[k] = c0 * g[k] + (k == 1 ? dr : 0.0) - (k == 0 ? p.r : 0.0);
+  }
+  // left exterior coefficient: row i collects sum_{m > i} g_m = -g_0/2 - sum_{m=1}^{i} g_m, plus the
+  // drift's coefficient on the left neighbour of row 0
+  std::vector<double> cl(nx);
+  double run = 0.0;  // sum_{m=1}^{i} g_m
+  for (int i = 0; i < nx; ++i) {
+    if (i >= 1) run += g[i];
+    cl[i] = c0 * (-0.5 * g[0] - run) + (i == 0 ? -dr : 0.0);
+  }
+  // circulant embedding of length N2 >= 2 nx - 1 and its spectrum (direct DFT in FP64)
+  int l2 = 0;
+  while ((1 << l2) < 2 * nx - 1) ++l2;
+  const int n2 = 1 << l2;
+  h.rz_n2 = n2;
+  h.rz_log2n2 = l2;
+  std::vector<double> cc(n2, 0.0);
+  for (int k = 0; k < nx; ++k) cc[k] = col[k];
+  for (int k = 1; k < nx; ++k) cc[n2 - k] = row[k];
+  std::vector<double> cs(n2), sn(n2);
+  for (int q = 0; q < n2; ++q) {
+    const double a = -2.0 * M_PI * (double)q / n2;
+    cs[q] = cos(a);
+    sn[q] = sin(a);
+  }
+  std::vector<double2> chat(n2), tw2(n2);
+  const double sc = 0.5 * h.tau / n2;
+  for (int f = 0; f < n2; ++f) {
+    double re = 0.0, im = 0.0;
+    for (int q = 0; q < n2; ++q) {
+      if (cc[q] == 0.0) continue;
+      const int idx = (int)(((long long)f * q) % n2);
+      re += cc[q] * cs[idx];
+      im += cc[q] * sn[idx];
+    }
+    chat[f] = make_double2(re * sc, im * sc);
+    tw2[f] = make_double2(cs[f], sn[f]);
+  }
+  std::vector<double> hcol(nx), hrow(nx), hcl(nx), tcol(nx), trow(nx);
+  for (int k = 0; k < nx; ++k) {
+    hcol[k] = 0.5 * h.tau * col[k];
+    hrow[k] = 0.5 * h.tau * row[k];
+    hcl[k] = 0.5 * h.tau * cl[k];
+    tcol[k] = h.tau * col[k];
+    trow[k] = h.tau * row[k];
+  }
+  std::vector<double> gl(nt + 1);
+  for (int k = 0; k <= nt; ++k) gl[k] = p.K * exp(-p.r * h.tau * k) - exp(-xmax);
+  auto up = [&](auto** dst, const auto& src) -> int {
+    using T = typename std::decay<decltype(src)>::type::value_type;
+    AAO_TRY_CUDA(cudaMalloc((void**)dst, sizeof(T) * src.size()));
+    AAO_TRY_CUDA(cudaMemcpyAsync(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, h.stream));
+    return AAO_OK;
+  };
+  double *d_tcol = nullptr, *d_trow = nullptr;
+  AAO_TRY(up(&h.rz_chat, chat));
+  AAO_TRY(up(&h.rz_tw, tw2));
+  AAO_TRY(up(&h.rz_hcol, hcol));
+  AAO_TRY(up(&h.rz_hrow, hrow));
+  AAO_TRY(up(&h.rz_hcl, hcl));
+  AAO_TRY(up(&h.gL, gl));
+  AAO_TRY(up(&d_tcol, tcol));
+  AAO_TRY(up(&d_trow, trow));
+  // shifted matrices and their LU factors (FP32 complex)
+  const int K = h.K;
+  const size_t nn = (size_t)nx * nx;
+  AAO_TRY_CUDA(cudaMalloc(&h.rz_lu, sizeof(float2) * nn * K));
+  k_rz_form<<<dim3(256, K), 256, 0, h.stream>>>(h.rz_lu, nx, d_tcol, d_trow, h.muf);
+  AAO_CHECK_LAUNCH();
+  for (int kb = 0; kb < nx; kb += kNB) {
+    const int w = nx - kb < kNB ? nx - kb : kNB;
+    k_lu_panel<<<K, 256, 0, h.stream>>>(h.rz_lu, nx, kb, w);
+    AAO_CHECK_LAUNCH();
+    const int rest = nx - kb - w;
+    if (rest > 0) {
+      k_lu_trsm<<<dim3((rest + 127) / 128, K), 128, 0, h.stream>>>(h.rz_lu, nx, kb, w);
+      AAO_CHECK_LAUNCH();
+      k_lu_update<<<dim3((rest + 63) / 64, (rest + 63) / 64, K), 256, 0, h.stream>>>(h.rz_lu, nx, kb, w);
+      AAO_CHECK_LAUNCH();
+    }
+  }
+  AAO_TRY_CUDA(cudaStreamSynchronize(h.stream));
+  cudaFree(d_tcol);
+  cudaFree(d_trow);
+  return AAO_OK;
+}
+
+int riesz_matvec(Handle& h, const void* x, bool x_is_float, double* y, const double* b, const double* V, int nd,
+                 int m) {
+  const int grid = (h.nt + 1) / 2;
+  const size_t smem = sizeof(double2) * 2 * (size_t)h.rz_n2;
+  int threads = h.rz_n2 / 16;
+  if (threads < 128) threads = 128;
+  if (threads > 256) threads = 256;
+  const double nn = (double)h.n;
+  const double bytes = nn * (x_is_float ? 4.0 : 8.0) + nn * 8.0 + (b ? nn * 8.0 : 0.0) + (V ? nn * 8.0 * nd : 0.0);
+  // two FP64 FFTs of length N2 per pair of time levels (5 N2 log2 N2 flops each), the product (6 N2)
+  const double flops = (double)grid * (2.0 * 5.0 * h.rz_n2 * h.rz_log2n2 + 6.0 * h.rz_n2) +
+                       nn * (3.0 + (b ? 3.0 : 0.0) + (V ? 2.0 * (nd + 1) : 0.0));
+  ProfScope ps(AAO_K_MATVEC, h.stream, bytes, flops);
+#define RZ(IN, MODE, ND)                                                                                     \
+  do {                                                                                                       \
+    AAO_TRY_CUDA(cudaFuncSetAttribute(k_rz_matvec<IN, MODE, ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                      (int)smem));                                                           \
+    k_rz_matvec<IN, MODE, ND><<<grid, threads, smem, h.stream>>>(                                            \
+        (const IN*)x, y, b, h.nx, h.nt, h.rz_n2, h.rz_log2n2, h.rz_chat, h.rz_tw, V, h.n, h.part, h.scal,    \
+        h.counter, m);                                                                                       \
+  } while (0)
+  if (V && nd > 0) {
+    if (x_is_float) {
+      switch (nd) {
+        case 1: RZ(float, 2, 1); break;
+        case 2: RZ(float, 2, 2); break;
+        case 3: RZ(float, 2, 3); break;
+        case 4: RZ(float, 2, 4); break;
+        case 5: RZ(float, 2, 5); break;
+        case 6: RZ(float, 2, 6); break;
+        case 7: RZ(float, 2, 7); break;
+        default: RZ(float, 2, 8); break;
+      }
+    } else {
+      switch (nd) {
+        case 1: RZ(double, 2, 1); break;
+        case 2: RZ(double, 2, 2); break;
+        case 3: RZ(double, 2, 3); break;
+        case 4: RZ(double, 2, 4); break;
+        case 5: RZ(double, 2, 5); break;
+        case 6: RZ(double, 2, 6); break;
+        case 7: RZ(double, 2, 7); break;
+        default: RZ(double, 2, 8); break;
+      }
+    }
+  } else if (b) {
+    if (x_is_float) RZ(float, 1, 0); else RZ(double, 1, 0);
+  } else {
+    if (x_is_float) RZ(float, 0, 0); else RZ(double, 0, 0);
+  }
+#undef RZ
+  AAO_CHECK_LAUNCH();
+  return AAO_OK;
+}
+
+int riesz_rhs(Handle& h, double* b) {
+  const double hx = 2.0 * h.p.s_max / (h.nx + 1);
+  k_rz_rhs<<<grid_for(h.n), kThreads, 0, h.stream>>>(b, h.nx, h.nt, h.rz_hcol, h.rz_hrow, h.rz_hcl, h.gL,
+                                                      h.p.s_max, hx, h.p.K);
+  AAO_CHECK_LAUNCH();
+  return AAO_OK;
+}
+
+int riesz_solve_bins(Handle& h, void* spec) {
+  const size_t smem = sizeof(float2) * ((size_t)h.nx + kNB);
+  const double bytes = (double)h.K * ((double)h.nx * h.nx * 8.0 + 2.0 * h.nx * 8.0);
+  ProfScope ps(AAO_K_TRIDIAG, h.stream, bytes);
+  k_rz_trsv<<<h.K, 256, smem, h.stream>>>((float2*)spec, h.nx, h.pitch, h.rz_lu, h.il2f);
+  AAO_CHECK_LAUNCH();
+  return AAO_OK;
+}
+
+}  // namespace aao

@@ -56,8 +56,11 @@ def _create(lib, p):
     (dict(alpha=1.5), aao.AAO_EINVAL),
     (dict(sigma=-0.1), aao.AAO_EINVAL),
     (dict(T=0.0), aao.AAO_EINVAL),
-    (dict(op="riesz"), aao.AAO_EUNSUPPORTED),
-    (dict(nt=16384, precision="fp64"), aao.AAO_EUNSUPPORTED),
+    (dict(op="riesz", precision="fp64"), aao.AAO_EUNSUPPORTED),
+    (dict(op="riesz", precision="mixed", beta=2.5), aao.AAO_EINVAL),
+    (dict(op="riesz", precision="mixed", nx=4095), aao.AAO_EUNSUPPORTED),
+    (dict(nt=8192, precision="fp64"), aao.AAO_EUNSUPPORTED),
+    (dict(nt=16384, precision="mixed"), aao.AAO_EUNSUPPORTED),
 ])
 def test_create_rejects_bad_problems_on_host(lib, bad, code):
     rc, h = _create(lib, W.with_(W.bs_put_255x256(), **bad))

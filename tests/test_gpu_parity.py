@@ -231,3 +231,67 @@ def test_fgmres_nan_rhs_reports_breakdown(aao):
     x = torch.zeros(31 * 16, dtype=torch.float64, device="cuda")
     st = aao.fgmres_solve(h, b, x, 1e-10, 10, 10)
     assert st["status"] == aao.AAO_BREAKDOWN
+
+
+# ---------------------------------------------------------------- Riesz (dense Toeplitz) operator
+
+RZ = W.riesz_1023x512()
+RZ_SHAPES = [(15, 16), (31, 8), (63, 32), (127, 64), (100, 2)]
+
+
+@pytest.mark.parametrize("beta", [1.5, 2.0])
+@pytest.mark.parametrize("nx,nt", RZ_SHAPES)
+def test_riesz_rhs_matvec_match_oracle(aao, nx, nt, beta):
+    p = W.with_(RZ, nx=nx, nt=nt, beta=beta)
+    h = aao.aao_create(p)
+    n = nx * nt
+    b = torch.empty(n, dtype=torch.float64, device="cuda")
+    aao.aao_rhs(h, b)
+    ref = O.assemble_b(p)
+    assert relmax(host(b), ref) <= 1e-12
+    x = W.random_vector(n, seed=nx + nt)
+    y = torch.empty(n, dtype=torch.float64, device="cuda")
+    aao.aao_matvec(h, dev(x), y)
+    assert relmax(host(y), O.matvec(p, x)) <= 1e-12
+
+
+@pytest.mark.parametrize("alpha", [1e-2, 1e-3])
+@pytest.mark.parametrize("nx,nt", RZ_SHAPES)
+def test_riesz_precond_matches_oracle(aao, nx, nt, alpha):
+    p = W.with_(RZ, nx=nx, nt=nt, alpha=alpha)
+    h = aao.aao_create(p)
+    v = W.random_vector(nx * nt, seed=5 * nx + nt)
+    z = torch.empty(nx * nt, dtype=torch.float64, device="cuda")
+    aao.precond_apply(h, dev(v), z)
+    ref = O.precond_fft(p, v)
+    assert rel(host(z), ref) <= precond_bound(p), rel(host(z), ref)
+
+
+def test_riesz_precond_small_matches_dense_inverse(aao):
+    for nx, nt in [(7, 4), (9, 8)]:
+        p = W.with_(RZ, nx=nx, nt=nt, alpha=1e-2)
+        h = aao.aao_create(p)
+        v = W.random_vector(nx * nt, seed=nx)
+        z = torch.empty(nx * nt, dtype=torch.float64, device="cuda")
+        aao.precond_apply(h, dev(v), z)
+        assert rel(host(z), O.precond_dense(p, v)) <= precond_bound(p)
+
+
+def test_riesz_full_size_solve():
+    """1023 x 512 Riesz (beta 1.5) put, mixed precision: the true residual (FP64, by the
+    oracle's block-row product with the dense A) <= 1e-8 and the solution against sequential CN."""
+    from paper_2401_16113_gb300 import aao as A
+    p = RZ
+    h = A.aao_create(p)
+    n = W.unknowns(p)
+    b = torch.empty(n, dtype=torch.float64, device="cuda")
+    A.aao_rhs(h, b)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    st = A.fgmres_solve(h, b, x, 1e-8, 30, 300)
+    assert st["status"] == 0, st
+    xs, bs = host(x), host(b)
+    assert np.linalg.norm(bs - O.matvec_blocks(p, xs)) <= 1.01e-8 * np.linalg.norm(bs)
+    U = O.sequential_cn(p)
+    err = np.abs(xs.reshape(p["nt"], p["nx"])[-1] - U[-1]).max() / np.abs(U[-1]).max()
+    print("riesz full size: its", st["iterations"], "maturity error", err)
+    assert err <= 1e-6

@@ -372,3 +372,9 @@ def test_planted_dropped_forcing_is_caught(monkeypatch):
         sel = (S >= lo) & (S <= hi)
         ref = O.bs_price(S[sel], q["K"], q["r"], q["sigma"], q["T"], kind)
         assert np.abs(U[-1][sel] - ref).max() > 1e-1, kind
+
+
+def test_block_matvec_equals_assembled_M():
+    for p in (W.with_(RZ, nx=17, nt=12), W.with_(BS, nx=13, nt=9)):
+        x = W.random_vector(p["nx"] * p["nt"], seed=2)
+        assert np.allclose(O.matvec_blocks(p, x), O.matvec(p, x), rtol=1e-13, atol=1e-13)
