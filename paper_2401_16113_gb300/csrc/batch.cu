@@ -22,8 +22,12 @@
 #include <string>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "krylov_dev.cuh"
 #include "precond_dev.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace aao {
 namespace {
@@ -34,6 +38,7 @@ using namespace pdev;
 constexpr int kBT = 256;       // threads of a batched-solver CTA
 constexpr int kCH = 16;        // tridiagonal rows per thread (at most)
 constexpr int kMaxM = 40;      // restart length bound of the batched solver
+constexpr int kMaxC = 8;       // largest cluster (CTAs per instance)
 
 struct BatchInst {
   int nx, nt, log2n, K, pitch, P, tgrp, ch, cs, rows, m, pad;
@@ -50,51 +55,80 @@ struct BatchInst {
   double* scal;
 };
 
-// ---------------------------------------------------------------- CTA-level building blocks
+// ---------------------------------------------------------------- cluster-level building blocks
+// A cluster of C CTAs (C = cluster size) works on one instance. Work is split by cluster rank;
+// phases that read what other CTAs wrote are separated by cluster barriers (release/acquire at
+// cluster scope, so global-memory writes before the barrier are visible after it). Sums are
+// formed per CTA, then every CTA adds the C partials from distributed shared memory in rank
+// order: all CTAs hold identical, deterministic totals. Each CTA keeps its own copy of the
+// instance's scalars (Hessenberg, Givens, scales) and runs the scalar updates redundantly.
 
-// CTA sum of CNT accumulators -> sm_out[0..cnt) (visible to all threads on return)
-template <int CNT>
-__device__ __forceinline__ void cta_sums(const double (&acc)[CNT], int cnt, double* sm_out) {
-  block_sums<CNT>(acc, cnt, sm_out);
+struct Ctx {
+  int rank, C;
+};
+
+__device__ __forceinline__ Ctx ctx() {
+  cg::cluster_group cl = cg::this_cluster();
+  return Ctx{(int)cl.block_rank(), (int)cl.num_blocks()};
 }
 
-// y = M x over the instance: warp w takes work items w, w+8, ... (32-column strip x 16 levels)
+__device__ __forceinline__ void cluster_sync() { cg::this_cluster().sync(); }
+
+// cluster sum of CNT per-thread accumulators -> out[0..cnt) (CTA-local shared, in every CTA)
+template <int CNT>
+__device__ __forceinline__ void cluster_sums(const double (&acc)[CNT], int cnt, double* part_sm, double* out) {
+  block_sums<CNT>(acc, cnt, part_sm);
+  cg::cluster_group cl = cg::this_cluster();
+  cl.sync();
+  if (threadIdx.x < cnt) {
+    double s = 0.0;
+    for (unsigned r = 0; r < cl.num_blocks(); ++r) s += cl.map_shared_rank(part_sm, r)[threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+  cl.sync();
+}
+
+// y = M x over the instance: warp (rank, w) takes work items rank*8 + w, + C*8, ... (32-column
+// strip x 16 time levels)
 template <typename IN, int MODE, int ND, int NA>
-__device__ __forceinline__ void cta_matvec(const BatchInst& I, const IN* x, double* y, const double* b,
-                                           const double* V, double (&acc)[NA]) {
+__device__ __forceinline__ void cl_matvec(const BatchInst& I, Ctx c, const IN* x, double* y, const double* b,
+                                          const double* V, double (&acc)[NA]) {
   const int warp = threadIdx.x >> 5;
   const int strips = (I.nx + 31) / 32, chunks = (I.nt + 15) / 16;
-  for (int it = warp; it < strips * chunks; it += kBT / 32) {
+  for (int it = c.rank * (kBT / 32) + warp; it < strips * chunks; it += c.C * (kBT / 32)) {
     const int sidx = it % strips, cidx = it / strips;
     const int t0 = cidx * 16, t1 = min(I.nt, t0 + 16);
     matvec_item<IN, MODE, ND, NA>(x, y, b, I.nx, t0, t1, sidx * 32, I.mL, I.mD, I.mU, I.rows, V, I.n, acc);
   }
 }
 
-// restart residual r = b - M x into V_0; returns ||r||^2 in sm[0]
-__device__ __noinline__ void cta_residual(const BatchInst& I, double* sm) {
+// restart residual r = b - M x into V_0; ||r||^2 -> out[0]
+__device__ __noinline__ void cl_residual(const BatchInst& I, Ctx c, double* psm, double* out) {
   double acc[1] = {0.0};
-  cta_matvec<double, 1, 0, 1>(I, I.x, I.V, I.b, nullptr, acc);
-  block_sums<1>(acc, 1, sm);
+  cl_matvec<double, 1, 0, 1>(I, c, I.x, I.V, I.b, nullptr, acc);
+  cluster_sums<1>(acc, 1, psm, out);
 }
 
-// W = M z_j with the first-pass projections V_q . W (q < ND) and ||W||^2 into sm[0..ND]
+// W = M z_j with the first-pass projections V_q . W (q < ND) and ||W||^2 -> out[0..ND]
 template <int ND>
-__device__ __noinline__ void cta_matvec_proj(const BatchInst& I, const float* z, double* W, double* sm) {
+__device__ __noinline__ void cl_matvec_proj(const BatchInst& I, Ctx c, const float* z, double* W, double* psm,
+                                            double* out) {
   double acc[ND + 1];
 #pragma unroll
   for (int q = 0; q <= ND; ++q) acc[q] = 0.0;
-  cta_matvec<float, 2, ND, ND + 1>(I, z, W, nullptr, I.V, acc);
-  block_sums<ND + 1>(acc, ND + 1, sm);
+  cl_matvec<float, 2, ND, ND + 1>(I, c, z, W, nullptr, I.V, acc);
+  cluster_sums<ND + 1>(acc, ND + 1, psm, out);
 }
 
-// P_alpha^{-1} (scale * v) -> z (FP32), Eq. 3.2 with Remark 1
-__device__ __noinline__ void cta_precond(const BatchInst& I, const double* v, float scale, float* z, unsigned char* smem) {
+// P_alpha^{-1} (scale * v) -> z (FP32), Eq. 3.2 with Remark 1; tiles and bins split by rank
+__device__ __noinline__ void cl_precond(const BatchInst& I, Ctx c, const double* v, float scale, float* z,
+                                        unsigned char* smem) {
   const int W = 2 * I.P;
-  for (int x0 = 0; x0 < I.nx; x0 += W) {
+  for (int x0 = c.rank * W; x0 < I.nx; x0 += c.C * W) {
     fft_fwd_tile<float>(v, I.spec, I.nx, I.nt, I.log2n, I.P, I.pitch, I.lam, I.tw, scale, x0, smem);
     __syncthreads();
   }
+  cluster_sync();
   const int G = kBT / I.tgrp;
   const int g = threadIdx.x / I.tgrp, tid = threadIdx.x - g * I.tgrp;
   const size_t gbytes = ((size_t)I.tgrp * I.cs + 8 * (size_t)I.tgrp) * sizeof(float2);
@@ -104,52 +138,56 @@ __device__ __noinline__ void cta_precond(const BatchInst& I, const double* v, fl
   unsigned char* groups = smem + (((3 * (size_t)I.tgrp * I.cs * sizeof(float)) + 15) & ~(size_t)15);
   tridiag_stage<float>(I.pL, I.pD, I.pU, I.nx, I.tgrp, I.ch, I.cs, sa, sd, sc);
   __syncthreads();
-  for (int k0 = 0; k0 < I.K; k0 += G) {
+  for (int k0 = c.rank * G; k0 < I.K; k0 += c.C * G) {
     const int k = k0 + g;
     tridiag_bin<float, kCH>(I.spec, I.nx, I.pitch, I.ch, I.cs, sa, sd, sc, I.mu, I.il2, k < I.K ? k : 0, tid,
                             I.tgrp, k < I.K, groups + g * gbytes);
     __syncthreads();
   }
-  for (int x0 = 0; x0 < I.nx; x0 += W) {
+  cluster_sync();
+  for (int x0 = c.rank * W; x0 < I.nx; x0 += c.C * W) {
     fft_inv_tile<float, float>(I.spec, z, I.nx, I.nt, I.log2n, I.P, I.pitch, I.ilam, I.tw, x0, smem);
     __syncthreads();
   }
+  cluster_sync();
 }
 
-// out[c0 + q] = V_{c0+q} . w, q < CNT <= 8
+// out[c0 + q] = V_{c0+q} . w, q < CNT <= 8 (into this CTA's scalar copy)
 template <int CNT>
-__device__ __noinline__ void cta_mdot_t(const BatchInst& I, int c0, const double* w, double* out, double* sm) {
+__device__ __noinline__ void cl_mdot_t(const BatchInst& I, Ctx c, int c0, const double* w, double* out, double* psm,
+                                       double* tot) {
   double acc[CNT];
 #pragma unroll
   for (int q = 0; q < CNT; ++q) acc[q] = 0.0;
   const double* Vc = I.V + (size_t)c0 * I.n;
-  for (size_t e = threadIdx.x; e < I.n; e += kBT) {
+  for (size_t e = (size_t)c.rank * kBT + threadIdx.x; e < I.n; e += (size_t)c.C * kBT) {
     const double wv = w[e];
 #pragma unroll
     for (int q = 0; q < CNT; ++q) acc[q] = fma(Vc[(size_t)q * I.n + e], wv, acc[q]);
   }
-  cta_sums<CNT>(acc, CNT, sm);
-  if (threadIdx.x < CNT) out[c0 + threadIdx.x] = sm[threadIdx.x];
+  cluster_sums<CNT>(acc, CNT, psm, tot);
+  if (threadIdx.x < CNT) out[c0 + threadIdx.x] = tot[threadIdx.x];
   __syncthreads();
 }
 
-__device__ void cta_mdot(const BatchInst& I, int c0, int cnt, const double* w, double* out, double* sm) {
+__device__ void cl_mdot(const BatchInst& I, Ctx c, int c0, int cnt, const double* w, double* out, double* psm,
+                        double* tot) {
   switch (cnt) {
-    case 1: cta_mdot_t<1>(I, c0, w, out, sm); break;
-    case 2: cta_mdot_t<2>(I, c0, w, out, sm); break;
-    case 3: cta_mdot_t<3>(I, c0, w, out, sm); break;
-    case 4: cta_mdot_t<4>(I, c0, w, out, sm); break;
-    case 5: cta_mdot_t<5>(I, c0, w, out, sm); break;
-    case 6: cta_mdot_t<6>(I, c0, w, out, sm); break;
-    case 7: cta_mdot_t<7>(I, c0, w, out, sm); break;
-    default: cta_mdot_t<8>(I, c0, w, out, sm); break;
+    case 1: cl_mdot_t<1>(I, c, c0, w, out, psm, tot); break;
+    case 2: cl_mdot_t<2>(I, c, c0, w, out, psm, tot); break;
+    case 3: cl_mdot_t<3>(I, c, c0, w, out, psm, tot); break;
+    case 4: cl_mdot_t<4>(I, c, c0, w, out, psm, tot); break;
+    case 5: cl_mdot_t<5>(I, c, c0, w, out, psm, tot); break;
+    case 6: cl_mdot_t<6>(I, c, c0, w, out, psm, tot); break;
+    case 7: cl_mdot_t<7>(I, c, c0, w, out, psm, tot); break;
+    default: cl_mdot_t<8>(I, c, c0, w, out, psm, tot); break;
   }
 }
 
-// Gram-Schmidt pass: w -= sum sigma_i^2 d_i V_i, then ||w||^2; thread 0 decides on a second
-// pass or runs the Givens update of column j
-__device__ __noinline__ void cta_update(const BatchInst& I, int j, int pass, double* w, double* sm) {
-  double* scal = I.scal;
+// Gram-Schmidt pass: w -= sum sigma_i^2 d_i V_i, then ||w||^2; thread 0 of every CTA decides on a
+// second pass or runs the Givens update of column j on its own scalar copy
+__device__ __noinline__ void cl_update(const BatchInst& I, Ctx c, double* scal, int j, int pass, double* w,
+                                       double* psm, double* tot) {
   const int nv = j + 1;
   const int off = pass == 1 ? S_D1 : S_D2;
   __shared__ double cf[kMaxM + 1];
@@ -159,15 +197,15 @@ __device__ __noinline__ void cta_update(const BatchInst& I, int j, int pass, dou
   }
   __syncthreads();
   double acc[1] = {0.0};
-  for (size_t e = threadIdx.x; e < I.n; e += kBT) {
+  for (size_t e = (size_t)c.rank * kBT + threadIdx.x; e < I.n; e += (size_t)c.C * kBT) {
     double wv = w[e];
     for (int q = 0; q < nv; ++q) wv = fma(-cf[q], I.V[(size_t)q * I.n + e], wv);
     w[e] = wv;
     acc[0] = fma(wv, wv, acc[0]);
   }
-  cta_sums<1>(acc, 1, sm);
+  cluster_sums<1>(acc, 1, psm, tot);
   if (threadIdx.x == 0) {
-    const double v = sm[0];
+    const double v = tot[0];
     scal[S_WP2] = v;
     if (pass == 1 && v < kReorthEta * kReorthEta * scal[S_WN2]) {
       scal[S_REORTH] = 1.0;
@@ -180,9 +218,8 @@ __device__ __noinline__ void cta_update(const BatchInst& I, int j, int pass, dou
 }
 
 // x += sum_{i<jd} y_i Z_i, y = H^{-1} g
-__device__ __noinline__ void cta_xupdate(const BatchInst& I, int jd) {
+__device__ __noinline__ void cl_xupdate(const BatchInst& I, Ctx c, const double* scal, int jd) {
   __shared__ double ys[kMaxM];
-  const double* scal = I.scal;
   if (threadIdx.x == 0) {
     for (int i = jd - 1; i >= 0; --i) {
       double s = scal[S_G + i];
@@ -191,36 +228,37 @@ __device__ __noinline__ void cta_xupdate(const BatchInst& I, int jd) {
     }
   }
   __syncthreads();
-  for (size_t e = threadIdx.x; e < I.n; e += kBT) {
+  for (size_t e = (size_t)c.rank * kBT + threadIdx.x; e < I.n; e += (size_t)c.C * kBT) {
     double v = I.x[e];
     for (int i = 0; i < jd; ++i) v = fma(ys[i], widen(I.Z[(size_t)i * I.n + e]), v);
     I.x[e] = v;
   }
-  __syncthreads();
+  cluster_sync();
 }
 
-// FGMRES(m) of one instance by one CTA
-__device__ __noinline__ void cta_solve(const BatchInst& I, double tol, int maxit, aao_stats* st, unsigned char* smem) {
-  __shared__ double sm[16];
-  double* scal = I.scal;
+// FGMRES(m) of one instance by one cluster
+__device__ __noinline__ void cl_solve(const BatchInst& I, Ctx c, double tol, int maxit, aao_stats* st,
+                                      unsigned char* smem) {
+  __shared__ double psm[16];
+  __shared__ double tot[16];
+  double* scal = I.scal + (size_t)c.rank * S_TOTAL;
   const int m = I.m;
   {
     double acc[1] = {0.0};
-    for (size_t e = threadIdx.x; e < I.n; e += kBT) acc[0] = fma(I.b[e], I.b[e], acc[0]);
-    cta_sums<1>(acc, 1, sm);
+    for (size_t e = (size_t)c.rank * kBT + threadIdx.x; e < I.n; e += (size_t)c.C * kBT)
+      acc[0] = fma(I.b[e], I.b[e], acc[0]);
+    cluster_sums<1>(acc, 1, psm, tot);
   }
-  const double bn2 = sm[0];
-  __syncthreads();
-  const double bnorm = sqrt(bn2);
+  const double bnorm = sqrt(tot[0]);
   int its = 0, restarts = 0, status = AAO_OK;
   double rel = 0.0, est = 0.0;
   if (!(bnorm > 0.0)) {
-    for (size_t e = threadIdx.x; e < I.n; e += kBT) I.x[e] = 0.0;
+    for (size_t e = (size_t)c.rank * kBT + threadIdx.x; e < I.n; e += (size_t)c.C * kBT) I.x[e] = 0.0;
     status = isfinite(bnorm) ? AAO_OK : AAO_BREAKDOWN;
   } else {
     for (;;) {
-      cta_residual(I, sm);
-      const double beta = sqrt(sm[0]);
+      cl_residual(I, c, psm, tot);
+      const double beta = sqrt(tot[0]);
       rel = beta / bnorm;
       if (!isfinite(beta)) { status = AAO_BREAKDOWN; break; }
       if (beta <= tol * bnorm) { status = AAO_OK; break; }
@@ -237,27 +275,27 @@ __device__ __noinline__ void cta_solve(const BatchInst& I, double tol, int maxit
         double* Vj = I.V + (size_t)j * I.n;
         double* W = I.V + (size_t)(j + 1) * I.n;
         float* Zj = I.Z + (size_t)j * I.n;
-        cta_precond(I, Vj, (float)scal[S_SIG + j], Zj, smem);
+        cl_precond(I, c, Vj, (float)scal[S_SIG + j], Zj, smem);
         const int nv = j + 1;
         const int nf = nv < 8 ? nv : 8;
         switch (nf) {
-          case 1: cta_matvec_proj<1>(I, Zj, W, sm); break;
-          case 2: cta_matvec_proj<2>(I, Zj, W, sm); break;
-          case 3: cta_matvec_proj<3>(I, Zj, W, sm); break;
-          case 4: cta_matvec_proj<4>(I, Zj, W, sm); break;
-          case 5: cta_matvec_proj<5>(I, Zj, W, sm); break;
-          case 6: cta_matvec_proj<6>(I, Zj, W, sm); break;
-          case 7: cta_matvec_proj<7>(I, Zj, W, sm); break;
-          default: cta_matvec_proj<8>(I, Zj, W, sm); break;
+          case 1: cl_matvec_proj<1>(I, c, Zj, W, psm, tot); break;
+          case 2: cl_matvec_proj<2>(I, c, Zj, W, psm, tot); break;
+          case 3: cl_matvec_proj<3>(I, c, Zj, W, psm, tot); break;
+          case 4: cl_matvec_proj<4>(I, c, Zj, W, psm, tot); break;
+          case 5: cl_matvec_proj<5>(I, c, Zj, W, psm, tot); break;
+          case 6: cl_matvec_proj<6>(I, c, Zj, W, psm, tot); break;
+          case 7: cl_matvec_proj<7>(I, c, Zj, W, psm, tot); break;
+          default: cl_matvec_proj<8>(I, c, Zj, W, psm, tot); break;
         }
-        if (threadIdx.x < nf) scal[S_D1 + threadIdx.x] = sm[threadIdx.x];
-        if (threadIdx.x == 0) scal[S_WN2] = sm[nf];
+        if (threadIdx.x < nf) scal[S_D1 + threadIdx.x] = tot[threadIdx.x];
+        if (threadIdx.x == 0) scal[S_WN2] = tot[nf];
         __syncthreads();
-        for (int c0 = 8; c0 < nv; c0 += 8) cta_mdot(I, c0, min(8, nv - c0), W, scal + S_D1, sm);
-        cta_update(I, j, 1, W, sm);
+        for (int c0 = 8; c0 < nv; c0 += 8) cl_mdot(I, c, c0, min(8, nv - c0), W, scal + S_D1, psm, tot);
+        cl_update(I, c, scal, j, 1, W, psm, tot);
         if (scal[S_REORTH] != 0.0) {
-          for (int c0 = 0; c0 < nv; c0 += 8) cta_mdot(I, c0, min(8, nv - c0), W, scal + S_D2, sm);
-          cta_update(I, j, 2, W, sm);
+          for (int c0 = 0; c0 < nv; c0 += 8) cl_mdot(I, c, c0, min(8, nv - c0), W, scal + S_D2, psm, tot);
+          cl_update(I, c, scal, j, 2, W, psm, tot);
         }
         est = scal[S_EST];
         const double hn = scal[S_HN];
@@ -269,11 +307,11 @@ __device__ __noinline__ void cta_solve(const BatchInst& I, double tol, int maxit
         if (est <= tol * bnorm || hn <= 1e-300 || its >= maxit) break;
       }
       if (status == AAO_BREAKDOWN) break;
-      cta_xupdate(I, jd);
+      cl_xupdate(I, c, scal, jd);
       ++restarts;
     }
   }
-  if (threadIdx.x == 0) {
+  if (c.rank == 0 && threadIdx.x == 0) {
     st->status = status;
     st->iterations = its;
     st->restarts = restarts;
@@ -282,28 +320,31 @@ __device__ __noinline__ void cta_solve(const BatchInst& I, double tol, int maxit
     st->est_residual = est / (bnorm > 0 ? bnorm : 1.0);
     st->ms = 0.0;
   }
-  __syncthreads();
+  cluster_sync();
 }
 
-// mode 0: solve; mode 1: two preconditioner applies only (FFT tile tuning)
+// mode 0: solve; mode 1: two preconditioner applies only (FFT tile tuning). Rank 0 of each
+// cluster takes the next instance from the queue and the cluster reads it from its shared memory.
 __global__ void __launch_bounds__(kBT, 2) k_batch(const BatchInst* __restrict__ insts, const int* __restrict__ order,
-                                               int n, unsigned int* __restrict__ next, double tol, int maxit,
-                                               aao_stats* __restrict__ st, int mode) {
+                                                  int n, unsigned int* __restrict__ next, double tol, int maxit,
+                                                  aao_stats* __restrict__ st, int mode) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int cur;
+  const Ctx c = ctx();
+  cg::cluster_group cl = cg::this_cluster();
   for (;;) {
-    if (threadIdx.x == 0) cur = (int)atomicAdd(next, 1u);
-    __syncthreads();
-    const int q = cur;
-    __syncthreads();
+    if (c.rank == 0 && threadIdx.x == 0) cur = (int)atomicAdd(next, 1u);
+    cl.sync();
+    const int q = *cl.map_shared_rank(&cur, 0);
+    cl.sync();
     if (q >= n) return;
     const int id = order[q];
     const BatchInst& I = insts[id];
     if (mode == 1) {
-      cta_precond(I, I.V, 1.0f, I.Z, smem);
-      cta_precond(I, I.V, 1.0f, I.Z, smem);
+      cl_precond(I, c, I.V, 1.0f, I.Z, smem);
+      cl_precond(I, c, I.V, 1.0f, I.Z, smem);
     } else {
-      cta_solve(I, tol, maxit, st + id, smem);
+      cl_solve(I, c, tol, maxit, st + id, smem);
     }
   }
 }
@@ -339,6 +380,8 @@ struct Batch {
   double g_tol = -1.0;
   int g_maxit = -1;
   size_t smem = 0;
+  int C = 4;          // CTAs per instance (thread-block cluster size)
+  int nclusters = 1;  // clusters resident at once for C
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
@@ -391,18 +434,52 @@ void host_tables(const aao_problem& p, int nx, int nt, std::vector<float>& pl, s
   }
 }
 
+// launch the persistent kernel with clusters of B.C CTAs, as many clusters as fit at once
+int launch_k_batch(Batch& B, int mode, double tol, int maxit) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = B.C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(kBT);
+  cfg.dynamicSmemBytes = B.smem;
+  cfg.stream = B.s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.gridDim = dim3(B.C * std::min(B.n, B.nclusters));
+  AAO_TRY_CUDA(cudaLaunchKernelEx(&cfg, k_batch, (const BatchInst*)B.d_inst, (const int*)B.d_order, B.n, B.d_next,
+                                  tol, maxit, B.d_st, mode));
+  return AAO_OK;
+}
+
+int set_cluster(Batch& B, int C) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(kBT);
+  cfg.dynamicSmemBytes = B.smem;
+  cfg.gridDim = dim3(C);
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nc = 0;
+  AAO_TRY_CUDA(cudaOccupancyMaxActiveClusters(&nc, (const void*)k_batch, &cfg));
+  if (nc < 1) {
+    set_error("aao_batch: no cluster of this size fits on the GPU");
+    return AAO_EUNSUPPORTED;
+  }
+  B.C = C;
+  B.nclusters = nc;
+  return AAO_OK;
+}
+
 int run_batch(Batch& B, int mode, double tol, int maxit) {
   AAO_TRY_CUDA(cudaMemsetAsync(B.d_next, 0, sizeof(unsigned int), B.s));
-  int dev = 0, sms = 0;
-  AAO_TRY_CUDA(cudaGetDevice(&dev));
-  AAO_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  int per_sm = 0;
-  AAO_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, kBT, B.smem));
-  if (per_sm < 1) per_sm = 1;
-  const int grid = std::min(B.n, sms * per_sm);
-  k_batch<<<grid, kBT, B.smem, B.s>>>(B.d_inst, B.d_order, B.n, B.d_next, tol, maxit, B.d_st, mode);
-  AAO_CHECK_LAUNCH();
-  return AAO_OK;
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return launch_k_batch(B, mode, tol, maxit);
 }
 
 // FFT column tile per nt class: time two preconditioner applies of that class's instances
@@ -445,6 +522,27 @@ int tune_tiles(Batch& B) {
   memcpy(B.h_inst, B.inst.data(), sizeof(BatchInst) * B.n);
   if (rc == AAO_OK && cudaMemcpyAsync(B.d_inst, B.h_inst, sizeof(BatchInst) * B.n, cudaMemcpyHostToDevice, B.s) != cudaSuccess)
     rc = AAO_ECUDA;
+  // cluster size: time the preconditioner pass over the whole batch (largest first) for each size
+  if (rc == AAO_OK) {
+    std::vector<int> ord(B.n);
+    for (int i = 0; i < B.n; ++i) ord[i] = i;
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return B.inst[a].n > B.inst[b].n; });
+    if (cudaMemcpyAsync(B.d_order, ord.data(), sizeof(int) * B.n, cudaMemcpyHostToDevice, B.s) != cudaSuccess) rc = AAO_ECUDA;
+    float best = 1e30f;
+    int bestC = B.C;
+    for (int C : {2, 4, 8}) {
+      if (rc != AAO_OK) break;
+      if (set_cluster(B, C) != AAO_OK) continue;
+      cudaEventRecord(e0, B.s);
+      rc = run_batch(B, 1, 1.0, 1);
+      cudaEventRecord(e1, B.s);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) { best = ms; bestC = C; }
+    }
+    if (rc == AAO_OK) rc = set_cluster(B, bestC);
+  }
   cudaStreamSynchronize(B.s);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -539,7 +637,7 @@ extern "C" int aao_batch_create(const aao_problem* ps, int n, int m, aao_batch**
     f.gL = o; o = al(o + sizeof(double) * (nt + 1));
     f.gR = o; o = al(o + sizeof(double) * (nt + 1));
     f.gS = o; o = al(o + sizeof(double) * nx);
-    f.scal = o; o = al(o + sizeof(double) * S_TOTAL);
+    f.scal = o; o = al(o + sizeof(double) * S_TOTAL * kMaxC);  // one scalar copy per cluster rank
     f.tab = o;
     f.pl = o; o = al(o + sizeof(float) * nx);
     f.pd = o; o = al(o + sizeof(float) * nx);
@@ -642,7 +740,8 @@ extern "C" int aao_batch_create(const aao_problem* ps, int n, int m, aao_batch**
   B.smem = smem;
   BTRY(cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   BTRY(cudaStreamSynchronize(B.s));
-  int rc = tune_tiles(B);
+  int rc = set_cluster(B, 4);
+  if (rc == AAO_OK) rc = tune_tiles(B);
   if (rc != AAO_OK) return fail(rc);
   B.order.resize(n);
   for (int i = 0; i < n; ++i) B.order[i] = i;
@@ -687,18 +786,13 @@ extern "C" int batch_submit(aao_batch* bt, double* const* b, double* const* x, d
   if (!B.exec || B.g_tol != tol || B.g_maxit != maxit) {
     if (B.exec) { cudaGraphExecDestroy(B.exec); B.exec = nullptr; }
     if (B.graph) { cudaGraphDestroy(B.graph); B.graph = nullptr; }
-    int dev = 0, sms = 0, per_sm = 0;
-    AAO_TRY_CUDA(cudaGetDevice(&dev));
-    AAO_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    AAO_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, kBT, B.smem));
-    if (per_sm < 1) per_sm = 1;
-    const int grid = std::min(B.n, sms * per_sm);
     AAO_TRY_CUDA(cudaStreamBeginCapture(B.s, cudaStreamCaptureModeThreadLocal));
     cudaMemcpyAsync(B.d_inst, B.h_inst, sizeof(BatchInst) * B.n, cudaMemcpyHostToDevice, B.s);
     cudaMemsetAsync(B.d_next, 0, sizeof(unsigned int), B.s);
-    k_batch<<<grid, kBT, B.smem, B.s>>>(B.d_inst, B.d_order, B.n, B.d_next, tol, maxit, B.d_st, 0);
+    const int lrc = launch_k_batch(B, 0, tol, maxit);
     cudaMemcpyAsync(B.h_st, B.d_st, sizeof(aao_stats) * B.n, cudaMemcpyDeviceToHost, B.s);
     cudaError_t ec = cudaStreamEndCapture(B.s, &B.graph);
+    if (lrc != AAO_OK) return lrc;
     if (ec != cudaSuccess) {
       set_error(std::string("batch_submit: graph capture: ") + cudaGetErrorString(ec));
       return AAO_ECUDA;
@@ -710,7 +804,7 @@ extern "C" int batch_submit(aao_batch* bt, double* const* b, double* const* x, d
   AAO_TRY_CUDA(cudaEventRecord(B.ev0, B.user));
   AAO_TRY_CUDA(cudaStreamWaitEvent(B.s, B.ev0, 0));
   AAO_TRY_CUDA(cudaGraphLaunch(B.exec, B.s));
-  g_launches.fetch_add(1, std::memory_order_relaxed);
+  g_launches.fetch_add(1, std::memory_order_relaxed);  // the graph holds one kernel
   AAO_TRY_CUDA(cudaStreamSynchronize(B.s));
   const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   int worst = AAO_OK;
