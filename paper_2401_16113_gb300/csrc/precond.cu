@@ -4,7 +4,8 @@
 //   k_fft_fwd   step (a): Lambda_alpha scaling (first factor of V_alpha^{-1} = F Lambda_alpha)
 //               fused with a real-to-complex FFT along t for a tile of 2P spatial columns.
 //               Two real columns are packed into one complex column; the FFT is a Stockham
-//               radix-4/2 transform in shared memory. Output: bins k = 0..nt/2 of every
+//               transform, radix 16/16/8 with 16 values per thread in registers for nt >= 128
+//               (radix 4/2 in shared memory below). Output: bins k = 0..nt/2 of every
 //               column, frequency-major [k][x] (the layout step (b) reads contiguously).
 //   k_tridiag   step (b): for each bin k one warp solves the complex-shifted tridiagonal system
 //               (lambda_{1,k} I - lambda_{2,k} A~) z2_k = z1_k, A~ = tau * Abar, by a partitioned
@@ -54,7 +55,7 @@ int run_precond(Handle& h, const double* v, void* z, bool z_is_float, const doub
   const int N = h.nt, nx = h.nx;
   const int P = h.fft_p > 0 ? h.fft_p : default_tile(nx, N, sizeof(R));
   int threads = fft_threads(P, N, sizeof(R));
-  const size_t smem = (size_t)(P + 1) * N * sizeof(C);  // tile + twiddle table
+  const size_t smem = fft_tile_bytes(P, N, sizeof(C));
   const int grid = (nx + 2 * P - 1) / (2 * P);
   C* spec = reinterpret_cast<C*>(h.spec);
   const R* lam = (sizeof(R) == 4) ? (const R*)h.lamf : (const R*)h.lam;

@@ -83,11 +83,11 @@ template <typename R> __device__ __forceinline__ R to_r(double v);
 template <> __device__ __forceinline__ float to_r<float>(double v) { return narrow(v); }
 template <> __device__ __forceinline__ double to_r<double>(double v) { return v; }
 
-// step (a) for the column tile starting at x0 (all threads of the CTA; smem holds (P+1)*N complex:
-// the tile, then a copy of the twiddle table).
+// step (a) for the column tile starting at x0, N < 128 (all threads of the CTA; smem holds
+// (P+1)*N complex: the tile, then a copy of the twiddle table).
 // Ends without a barrier: synchronise before reusing smem.
 template <typename R>
-__device__ __forceinline__ void fft_fwd_tile(const double* __restrict__ v, C_t<R>* __restrict__ spec, int nx, int N,
+__device__ __forceinline__ void fft_fwd_tile_smem(const double* __restrict__ v, C_t<R>* __restrict__ spec, int nx, int N,
                                              int log2n, int P, int pitch, const R* __restrict__ lam,
                                              const C_t<R>* __restrict__ tw, R sc, int x0, unsigned char* smraw) {
   using C = C_t<R>;
@@ -126,21 +126,11 @@ __device__ __forceinline__ void fft_fwd_tile(const double* __restrict__ v, C_t<R
   }
 }
 
-template <typename R>
-__global__ void __launch_bounds__(sizeof(R) == 8 ? 512 : 1024) k_fft_fwd(const double* __restrict__ v, C_t<R>* __restrict__ spec,
-                                                  int nx, int N, int log2n, int P, int pitch,
-                                                  const R* __restrict__ lam, const C_t<R>* __restrict__ tw,
-                                                  const double* __restrict__ in_scale) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const R sc = in_scale ? (R)(*in_scale) : (R)1;
-  fft_fwd_tile<R>(v, spec, nx, N, log2n, P, pitch, lam, tw, sc, blockIdx.x * 2 * P, smraw);
-}
-
-// step (c) for the column tile starting at x0 (all threads of the CTA; smem holds (P+1)*N complex:
-// the tile, then a copy of the twiddle table).
+// step (c) for the column tile starting at x0, N < 128 (all threads of the CTA; smem holds
+// (P+1)*N complex: the tile, then a copy of the twiddle table).
 // Ends without a barrier: synchronise before reusing smem.
 template <typename R, typename OUT>
-__device__ __forceinline__ void fft_inv_tile(const C_t<R>* __restrict__ spec, OUT* __restrict__ z, int nx, int N,
+__device__ __forceinline__ void fft_inv_tile_smem(const C_t<R>* __restrict__ spec, OUT* __restrict__ z, int nx, int N,
                                              int log2n, int P, int pitch, const R* __restrict__ ilam,
                                              const C_t<R>* __restrict__ tw, int x0, unsigned char* smraw) {
   using C = C_t<R>;
@@ -178,6 +168,327 @@ __device__ __forceinline__ void fft_inv_tile(const C_t<R>* __restrict__ spec, OU
       dst[(size_t)t * nx] = (OUT)val;
     }
   }
+}
+
+// ------------------------------------------------------------------ register FFT, N >= 128
+// For N = 2^log2n >= 128 each column transform is a sequence of Stockham stages (the same
+// recursion as stockham_stage) in which every thread holds 16 complex values of one column in
+// registers: radix-16 stages, one stage of radix 2, 4 or 8 to use up log2n - 3 bits, and a final
+// radix-8 stage. The first stage reads global memory and the last writes it, so a transform of
+// 2^11 points makes two shared-memory round trips (instead of seven radix-4/2 passes).
+// Virtual thread (p, u), p < P the complex column, u < N/16, is CTA thread u*P + p.
+// Shared tile: element t of column p at (t + t/16) * P + p; the pad row per 16 rows keeps the
+// stride-16 scatter of the first stage free of bank conflicts.
+constexpr int kRegFftMinLog2 = 7;
+
+__host__ __device__ __forceinline__ size_t reg_fft_elems(int P, int N) { return (size_t)P * (N + N / 16); }
+
+__device__ __forceinline__ int tix(int t, int lp, int p) { return ((t + (t >> 4)) << lp) + p; }
+
+// a * (c + i s)
+template <typename C>
+__device__ __forceinline__ C cmulc(C a, decltype(C::x) c, decltype(C::x) s) {
+  return cmk<C>(a.x * c - a.y * s, a.x * s + a.y * c);
+}
+
+template <typename C>
+__device__ __forceinline__ void dft2(C& a, C& b) {
+  const C t = a;
+  a = cadd(t, b);
+  b = csub(t, b);
+}
+
+// forward 8-point DFT in registers, natural order in and out: 8 = 2 x 4 (radix 2 over the
+// stride-4 index, twiddles w8^(n2 k1), radix 4 over n2; X[k1 + 2 k2] lands in a[4 k1 + k2])
+template <typename C>
+__device__ __forceinline__ void dft8(C* a) {
+  using R = decltype(C::x);
+  const R h = (R)0.70710678118654752440;  // cos(pi/4)
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) dft2(a[n2], a[4 + n2]);
+  a[5] = cmulc(a[5], h, -h);   // w8^1
+  a[6] = cmul_mi(a[6]);        // w8^2 = -i
+  a[7] = cmulc(a[7], -h, -h);  // w8^3
+  dft4(a[0], a[1], a[2], a[3]);
+  dft4(a[4], a[5], a[6], a[7]);
+  const C x1 = a[4], x2 = a[1], x3 = a[5], x4 = a[2], x5 = a[6], x6 = a[3];
+  a[1] = x1; a[2] = x2; a[3] = x3; a[4] = x4; a[5] = x5; a[6] = x6;
+}
+
+// forward 16-point DFT in registers, natural order in and out: 16 = 4 x 4 (radix 4 over the
+// stride-4 index, twiddles w16^(n2 k1), radix 4 over n2; X[k1 + 4 k2] lands in a[4 k1 + k2])
+template <typename C>
+__device__ __forceinline__ void dft16(C* a) {
+  using R = decltype(C::x);
+  const R c1 = (R)0.92387953251128675613, s1 = (R)0.38268343236508977173;  // cos, sin(pi/8)
+  const R h = (R)0.70710678118654752440;
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) dft4(a[n2], a[4 + n2], a[8 + n2], a[12 + n2]);
+  a[5] = cmulc(a[5], c1, -s1);    // w16^1
+  a[6] = cmulc(a[6], h, -h);      // w16^2
+  a[7] = cmulc(a[7], s1, -c1);    // w16^3
+  a[9] = cmulc(a[9], h, -h);      // w16^2
+  a[10] = cmul_mi(a[10]);         // w16^4 = -i
+  a[11] = cmulc(a[11], -h, -h);   // w16^6
+  a[13] = cmulc(a[13], s1, -c1);  // w16^3
+  a[14] = cmulc(a[14], -h, -h);   // w16^6
+  a[15] = cmulc(a[15], -c1, s1);  // w16^9
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) dft4(a[4 * k1], a[4 * k1 + 1], a[4 * k1 + 2], a[4 * k1 + 3]);
+  C t;
+  t = a[1]; a[1] = a[4]; a[4] = t;
+  t = a[2]; a[2] = a[8]; a[8] = t;
+  t = a[3]; a[3] = a[12]; a[12] = t;
+  t = a[6]; a[6] = a[9]; a[9] = t;
+  t = a[7]; a[7] = a[13]; a[13] = t;
+  t = a[11]; a[11] = a[14]; a[14] = t;
+}
+
+template <int LR, typename C>
+__device__ __forceinline__ void dft_pow2(C* a) {
+  if constexpr (LR == 1) dft2(a[0], a[1]);
+  else if constexpr (LR == 2) dft4(a[0], a[1], a[2], a[3]);
+  else if constexpr (LR == 3) dft8(a);
+  else dft16(a);
+}
+
+// One shared-to-shared Stockham stage of radix 2^LR with Ns = 2^lns: virtual thread (p, u) takes
+// butterflies j = u + q N/16 (q < 16 / 2^LR) of column p. Two barriers (reads, then writes).
+template <typename C, int LR>
+__device__ __forceinline__ void reg_stage(C* __restrict__ data, int log2n, int lp, int lns,
+                                          const C* __restrict__ tw, int p, int u, bool act) {
+  constexpr int RR = 1 << LR, B = 16 / RR;
+  const int n16 = 1 << (log2n - 4), stride = 1 << (log2n - LR), lts = log2n - lns - LR;
+  const int nsm = (1 << lns) - 1;
+  C a[16];
+  if (act) {
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+      const int j = u + q * n16, k = j & nsm;
+      a[q * RR] = data[tix(j, lp, p)];
+#pragma unroll
+      for (int r = 1; r < RR; ++r) a[q * RR + r] = cmul(data[tix(j + r * stride, lp, p)], __ldg(tw + ((r * k) << lts)));
+    }
+  }
+  __syncthreads();
+  if (act) {
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+      const int j = u + q * n16, k = j & nsm;
+      dft_pow2<LR>(a + q * RR);
+      const int base = ((j >> lns) << (lns + LR)) + k;
+#pragma unroll
+      for (int r = 0; r < RR; ++r) data[tix(base + (r << lns), lp, p)] = a[q * RR + r];
+    }
+  }
+  __syncthreads();
+}
+
+// The stages between the first (radix 16, from global memory) and the last (radix 8); on entry
+// the first stage's output is in shared memory and a barrier has passed.
+template <typename C>
+__device__ __forceinline__ void reg_middle(C* data, int log2n, int lp, const C* tw, int p, int u, bool act) {
+  int lns = 4;
+  for (; lns + 4 <= log2n - 3; lns += 4) reg_stage<C, 4>(data, log2n, lp, lns, tw, p, u, act);
+  switch (log2n - 3 - lns) {
+    case 1: reg_stage<C, 1>(data, log2n, lp, lns, tw, p, u, act); break;
+    case 2: reg_stage<C, 2>(data, log2n, lp, lns, tw, p, u, act); break;
+    case 3: reg_stage<C, 3>(data, log2n, lp, lns, tw, p, u, act); break;
+    default: break;
+  }
+}
+
+// The last stage (radix 8, Ns = N/8) for virtual thread u: butterflies ja = u and jb = Ns - u
+// (u = 0: 0 and Ns/2), so that bin k and its mirror N - k sit in the same thread. Element r of
+// butterfly j is bin j + r Ns. Reads shared memory only (no barrier needed afterwards).
+template <typename C>
+__device__ __forceinline__ void reg_last(const C* __restrict__ data, int log2n, int lp, const C* __restrict__ tw,
+                                         int p, int u, C (&a)[8], C (&b)[8], int& ja, int& jb) {
+  const int ns = 1 << (log2n - 3);
+  ja = u;
+  jb = u == 0 ? ns / 2 : ns - u;
+  a[0] = data[tix(ja, lp, p)];
+  b[0] = data[tix(jb, lp, p)];
+#pragma unroll
+  for (int r = 1; r < 8; ++r) {
+    a[r] = cmul(data[tix(ja + r * ns, lp, p)], __ldg(tw + r * ja));
+    b[r] = cmul(data[tix(jb + r * ns, lp, p)], __ldg(tw + r * jb));
+  }
+  dft8(a);
+  dft8(b);
+}
+
+template <typename C>
+__device__ __forceinline__ void store_pair(C* out, C xa, C xb, bool ok0, bool ok1) {
+  if (ok1) {
+    if constexpr (sizeof(C) == 8) {
+      *reinterpret_cast<float4*>(out) = make_float4(xa.x, xa.y, xb.x, xb.y);
+    } else {
+      out[0] = xa;
+      out[1] = xb;
+    }
+  } else if (ok0) {
+    out[0] = xa;
+  }
+}
+
+template <typename C>
+__device__ __forceinline__ void load_pair(const C* in, C& A, C& B, bool ok0, bool ok1) {
+  A = cmk<C>(0, 0);
+  B = cmk<C>(0, 0);
+  if (ok1) {
+    if constexpr (sizeof(C) == 8) {
+      const float4 q = __ldg(reinterpret_cast<const float4*>(in));
+      A = cmk<C>(q.x, q.y);
+      B = cmk<C>(q.z, q.w);
+    } else {
+      A = __ldg(in);
+      B = __ldg(in + 1);
+    }
+  } else if (ok0) {
+    A = __ldg(in);
+  }
+}
+
+// step (a) for the column tile starting at x0, N >= 128 (spec rows 16-byte aligned, x0 even;
+// smem holds reg_fft_elems(P, N) complex). Ends without a barrier: synchronise before reusing smem.
+template <typename R>
+__device__ __forceinline__ void fft_fwd_tile_reg(const double* __restrict__ v, C_t<R>* __restrict__ spec, int nx,
+                                                 int N, int log2n, int P, int pitch, const R* __restrict__ lam,
+                                                 const C_t<R>* __restrict__ tw, R sc, int x0, unsigned char* smraw) {
+  using C = C_t<R>;
+  C* data = reinterpret_cast<C*>(smraw);
+  const int lp = __ffs(P) - 1, n16 = N >> 4;
+  const bool act = (int)threadIdx.x < (P << (log2n - 4));
+  const int p = threadIdx.x & (P - 1), u = threadIdx.x >> lp;
+  const int x = x0 + 2 * p;
+  const bool ok0 = x < nx, ok1 = x + 1 < nx;
+  if (act) {
+    // first stage: radix 16 over rows u + r N/16, scaled by Lambda_alpha and the input scale
+    C a[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int t = u + r * n16;
+      const double* row = v + (size_t)t * nx + x;
+      const R l = __ldg(&lam[t]) * sc;
+      R re = (R)0, im = (R)0;
+      if (ok0) re = to_r<R>(__ldg(row)) * l;
+      if (ok1) im = to_r<R>(__ldg(row + 1)) * l;
+      a[r] = cmk<C>(re, im);
+    }
+    dft16(a);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) data[tix(u * 16 + r, lp, p)] = a[r];
+  }
+  __syncthreads();
+  reg_middle(data, log2n, lp, tw, p, u, act);
+  if (act) {
+    C a[8], b[8];
+    int ja, jb;
+    reg_last(data, log2n, lp, tw, p, u, a, b, ja, jb);
+    // Z = A + iB packs the two real columns; A[k] = (Z[k] + conj Z[N-k]) / 2,
+    // B[k] = (Z[k] - conj Z[N-k]) / 2i, for the bins k <= N/2 this thread holds
+    const int ns = N >> 3;
+    const R h = (R)0.5;
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+      if (r < 4 || u == 0) {
+        const C zk = a[r];
+        const C zn = u == 0 ? a[(8 - r) & 7] : b[7 - r];
+        const C xa = cmk<C>(h * (zk.x + zn.x), h * (zk.y - zn.y));
+        const C xb = cmk<C>(h * (zk.y + zn.y), h * (zn.x - zk.x));
+        store_pair(spec + (size_t)(ja + r * ns) * pitch + x, xa, xb, ok0, ok1);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const C zk = b[r];
+      const C zn = u == 0 ? b[7 - r] : a[7 - r];
+      const C xa = cmk<C>(h * (zk.x + zn.x), h * (zk.y - zn.y));
+      const C xb = cmk<C>(h * (zk.y + zn.y), h * (zn.x - zk.x));
+      store_pair(spec + (size_t)(jb + r * ns) * pitch + x, xa, xb, ok0, ok1);
+    }
+  }
+}
+
+// step (c) for the column tile starting at x0, N >= 128 (spec rows 16-byte aligned, x0 even;
+// smem holds reg_fft_elems(P, N) complex). Ends without a barrier: synchronise before reusing smem.
+template <typename R, typename OUT>
+__device__ __forceinline__ void fft_inv_tile_reg(const C_t<R>* __restrict__ spec, OUT* __restrict__ z, int nx, int N,
+                                                 int log2n, int P, int pitch, const R* __restrict__ ilam,
+                                                 const C_t<R>* __restrict__ tw, int x0, unsigned char* smraw) {
+  using C = C_t<R>;
+  C* data = reinterpret_cast<C*>(smraw);
+  const int lp = __ffs(P) - 1, n16 = N >> 4, half = N >> 1;
+  const bool act = (int)threadIdx.x < (P << (log2n - 4));
+  const int p = threadIdx.x & (P - 1), u = threadIdx.x >> lp;
+  const int x = x0 + 2 * p;
+  const bool ok0 = x < nx, ok1 = x + 1 < nx;
+  if (act) {
+    // first stage: the conjugate of the full spectrum Z = A + iB, bins above N/2 from their
+    // mirrors (Remark 1), so that the forward transform gives the conjugated inverse DFT
+    C a[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int t = u + r * n16;
+      const int k = t <= half ? t : N - t;
+      C A, B;
+      load_pair(spec + (size_t)k * pitch + x, A, B, ok0, ok1);
+      if (k == 0 || k == half) { A.y = 0; B.y = 0; }  // DC / Nyquist bins of a real signal
+      a[r] = t <= half ? cmk<C>(A.x - B.y, -(A.y + B.x)) : cmk<C>(A.x + B.y, A.y - B.x);
+    }
+    dft16(a);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) data[tix(u * 16 + r, lp, p)] = a[r];
+  }
+  __syncthreads();
+  reg_middle(data, log2n, lp, tw, p, u, act);
+  if (act) {
+    C a[8], b[8];
+    int ja, jb;
+    reg_last(data, log2n, lp, tw, p, u, a, b, ja, jb);
+    const int ns = N >> 3;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int ta = ja + r * ns, tb = jb + r * ns;
+      const R la = __ldg(&ilam[ta]), lb = __ldg(&ilam[tb]);
+      OUT* da = z + (size_t)ta * nx + x;
+      OUT* db = z + (size_t)tb * nx + x;
+      if (ok0) { da[0] = (OUT)(a[r].x * la); db[0] = (OUT)(b[r].x * lb); }
+      if (ok1) { da[1] = (OUT)(-a[r].y * la); db[1] = (OUT)(-b[r].y * lb); }
+    }
+  }
+}
+
+// shared memory of one FFT tile (both directions)
+__host__ __device__ __forceinline__ size_t fft_tile_bytes(int P, int N, size_t csize) {
+  return (N >= (1 << kRegFftMinLog2) ? reg_fft_elems(P, N) : (size_t)(P + 1) * N) * csize;
+}
+
+template <typename R>
+__device__ __forceinline__ void fft_fwd_tile(const double* __restrict__ v, C_t<R>* __restrict__ spec, int nx, int N,
+                                             int log2n, int P, int pitch, const R* __restrict__ lam,
+                                             const C_t<R>* __restrict__ tw, R sc, int x0, unsigned char* smraw) {
+  if (log2n >= kRegFftMinLog2) fft_fwd_tile_reg<R>(v, spec, nx, N, log2n, P, pitch, lam, tw, sc, x0, smraw);
+  else fft_fwd_tile_smem<R>(v, spec, nx, N, log2n, P, pitch, lam, tw, sc, x0, smraw);
+}
+
+template <typename R, typename OUT>
+__device__ __forceinline__ void fft_inv_tile(const C_t<R>* __restrict__ spec, OUT* __restrict__ z, int nx, int N,
+                                             int log2n, int P, int pitch, const R* __restrict__ ilam,
+                                             const C_t<R>* __restrict__ tw, int x0, unsigned char* smraw) {
+  if (log2n >= kRegFftMinLog2) fft_inv_tile_reg<R, OUT>(spec, z, nx, N, log2n, P, pitch, ilam, tw, x0, smraw);
+  else fft_inv_tile_smem<R, OUT>(spec, z, nx, N, log2n, P, pitch, ilam, tw, x0, smraw);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(sizeof(R) == 8 ? 512 : 1024) k_fft_fwd(const double* __restrict__ v, C_t<R>* __restrict__ spec,
+                                                  int nx, int N, int log2n, int P, int pitch,
+                                                  const R* __restrict__ lam, const C_t<R>* __restrict__ tw,
+                                                  const double* __restrict__ in_scale) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const R sc = in_scale ? (R)(*in_scale) : (R)1;
+  fft_fwd_tile<R>(v, spec, nx, N, log2n, P, pitch, lam, tw, sc, blockIdx.x * 2 * P, smraw);
 }
 
 template <typename R, typename OUT>
