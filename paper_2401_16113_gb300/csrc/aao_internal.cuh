@@ -104,17 +104,18 @@ __device__ __forceinline__ double widen(float f) {
 __device__ __forceinline__ double widen(double d) { return d; }
 
 // narrow: round to nearest (ties away from zero) for results in the FP32 normal range;
-// overflow gives inf, results below the normal range give zero, NaN stays NaN.
+// overflow gives inf, results below the normal range give zero, NaN stays NaN. Only 32-bit
+// integer operations: the rounding carry from the low word is propagated by hand.
 __device__ __forceinline__ float narrow(double d) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
-  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
-  const unsigned long long em = b & 0x7fffffffffffffffull;
-  const unsigned long long r = em + (1ull << 28);  // half of the 29 dropped bits; carries into the exponent
-  const long long fe = (long long)(r >> 52) - 896;
-  unsigned fb = ((unsigned)fe << 23) | (unsigned)((r >> 29) & 0x7fffffu);
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  const unsigned sign = hi & 0x80000000u, ehi = hi & 0x7fffffffu;
+  const unsigned lo2 = lo + 0x10000000u;                 // half of the 29 dropped bits
+  const unsigned hi2 = ehi + (lo2 < lo ? 1u : 0u);        // carry, possibly into the exponent
+  const int fe = (int)(hi2 >> 20) - 896;
+  unsigned fb = (((hi2 << 3) | (lo2 >> 29)) & 0x7fffffu) | ((unsigned)fe << 23);
   fb = fe >= 255 ? 0x7f800000u : fb;
   fb = fe <= 0 ? 0u : fb;
-  fb = (em >> 52) == 0x7ffull ? ((em & 0xfffffffffffffull) ? 0x7fc00000u : 0x7f800000u) : fb;
+  fb = ehi >= 0x7ff00000u ? ((ehi > 0x7ff00000u || lo != 0u) ? 0x7fc00000u : 0x7f800000u) : fb;
   return __uint_as_float(sign | fb);
 }
 
@@ -144,6 +145,10 @@ struct Handle {
   float *lamf = nullptr, *ilamf = nullptr;
   void* spec = nullptr;   // half spectrum, K * pitch complex (float2 or double2)
   int fft_p = 0;          // FFT tile: 2*fft_p spatial columns per CTA (0 = heuristic)
+  // step (b) partition: tri_T (a power of two) threads per bin, tri_ch rows each; coefficients a, diag, c chunk-
+  // transposed ([j][l]) in one buffer of 3 * tri_ch * tri_T reals (precision of the preconditioner)
+  void* tri = nullptr;
+  int tri_T = 0, tri_ch = 0;
 
   // Riesz operator (dense Toeplitz): circulant-embedding spectrum (scaled by tau/2 / N2), its
   // twiddles, (tau/2) first column / row / left-exterior coefficients, LU factors of step (b)

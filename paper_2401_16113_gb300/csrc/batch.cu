@@ -94,11 +94,11 @@ template <typename IN, int MODE, int ND, int NA>
 __device__ __forceinline__ void cl_matvec(const BatchInst& I, Ctx c, const IN* x, double* y, const double* b,
                                           const double* V, double (&acc)[NA]) {
   const int warp = threadIdx.x >> 5;
-  const int strips = (I.nx + 31) / 32, chunks = (I.nt + 15) / 16;
+  const int strips = (I.nx + kMvCols - 1) / kMvCols, chunks = (I.nt + 15) / 16;
   for (int it = c.rank * (kBT / 32) + warp; it < strips * chunks; it += c.C * (kBT / 32)) {
     const int sidx = it % strips, cidx = it / strips;
     const int t0 = cidx * 16, t1 = min(I.nt, t0 + 16);
-    matvec_item<IN, MODE, ND, NA>(x, y, b, I.nx, t0, t1, sidx * 32, I.mL, I.mD, I.mU, I.rows, V, I.n, acc);
+    matvec_item<IN, MODE, ND, NA>(x, y, b, I.nx, t0, t1, sidx * kMvCols, I.mL, I.mD, I.mU, I.rows, V, I.n, acc);
   }
 }
 

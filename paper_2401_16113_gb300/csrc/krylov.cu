@@ -131,13 +131,13 @@ __global__ void __launch_bounds__(kThreads) k_matvec(const IN* __restrict__ x, d
   constexpr int NA = MODE == 2 ? ND + 1 : 1;
   constexpr int nd = ND;
   const int warp = threadIdx.x >> 5;
-  const int i0 = (blockIdx.x * (kThreads / 32) + warp) * 32;
+  const int o0 = (blockIdx.x * (kThreads / 32) + warp) * kMvCols;
   const int t0 = blockIdx.y * tc;
   const int t1 = min(nt, t0 + tc);
   double acc[NA];
 #pragma unroll
   for (int q = 0; q < NA; ++q) acc[q] = 0.0;
-  matvec_item<IN, MODE, ND, NA>(x, y, b, nx, t0, t1, i0, L, D, U, rows, V, vstride, acc);
+  matvec_item<IN, MODE, ND, NA>(x, y, b, nx, t0, t1, o0, L, D, U, rows, V, vstride, acc);
   if constexpr (MODE == 0) return;
   const unsigned int nblk = gridDim.x * gridDim.y;
   const unsigned int bid = blockIdx.y * gridDim.x + blockIdx.x;
@@ -381,6 +381,35 @@ int build_tables(Handle& h) {
   if (!riesz) {
     AAO_TRY(up(&h.pL, pl)); AAO_TRY(up(&h.pD, pd)); AAO_TRY(up(&h.pU, pu));
     AAO_TRY(up(&h.pLf, plf)); AAO_TRY(up(&h.pDf, pdf)); AAO_TRY(up(&h.pUf, puf));
+    // step (b) partition: T = 2^k >= 32 threads per bin with at most 16 rows each (up to T = 512),
+    // rows l*ch .. l*ch+ch-1 on thread l; the coefficients a_i = -lo_i (0 for i = 0), diag_i,
+    // c_i = -up_i (0 for i = nx-1) stored [j][l]
+    int T = 32;
+    while (T < 512 && (nx + T - 1) / T > 16) T *= 2;
+    const int ch = (nx + T - 1) / T;
+    const size_t plane = (size_t)ch * T;
+    std::vector<double> tri(3 * plane, 0.0);
+    for (int l = 0; l < T; ++l)
+      for (int j = 0; j < ch; ++j) {
+        const int i = l * ch + j;
+        const size_t o = (size_t)j * T + l;
+        tri[o] = (i > 0 && i < nx) ? -pl[i] : 0.0;
+        tri[plane + o] = i < nx ? pd[i] : 0.0;
+        tri[2 * plane + o] = (i < nx - 1) ? -pu[i] : 0.0;
+      }
+    h.tri_T = T;
+    h.tri_ch = ch;
+    if (h.mixed) {
+      std::vector<float> trif(tri.size());
+      for (size_t q = 0; q < tri.size(); ++q) trif[q] = (float)tri[q];
+      float* d = nullptr;
+      AAO_TRY(up(&d, trif));
+      h.tri = d;
+    } else {
+      double* d = nullptr;
+      AAO_TRY(up(&d, tri));
+      h.tri = d;
+    }
   }
   AAO_TRY(up(&h.mu, mu)); AAO_TRY(up(&h.il2, il2)); AAO_TRY(up(&h.tw, tw));
   AAO_TRY(up(&h.muf, muf)); AAO_TRY(up(&h.il2f, il2f)); AAO_TRY(up(&h.twf, twf));
@@ -407,7 +436,7 @@ int build_tables(Handle& h) {
 void free_handle(Handle& h) {
   void* bufs[] = {h.mL, h.mD, h.mU, h.gL, h.gR, h.pL, h.pD, h.pU, h.pLf, h.pDf, h.pUf, h.mu, h.il2, h.tw,
                   h.muf, h.il2f, h.twf, h.lam, h.ilam, h.lamf, h.ilamf, h.spec, h.V, h.Z, h.w, h.scal, h.part,
-                  h.counter, h.rz_chat, h.rz_tw, h.rz_hcol, h.rz_hrow, h.rz_hcl, h.rz_lu};
+                  h.counter, h.rz_chat, h.rz_tw, h.rz_hcol, h.rz_hrow, h.rz_hcl, h.rz_lu, h.tri};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (h.host_scal) cudaFreeHost(h.host_scal);
@@ -421,7 +450,8 @@ namespace {
 
 // time-chunk length: enough blocks to fill the GPU, at most kPartBlocks partial sums
 void matvec_grid(const Handle& h, dim3& grid, int& tc) {
-  const int gx = (h.nx + kThreads - 1) / kThreads;
+  const int cols = (kThreads / 32) * kMvCols;  // output columns per block
+  const int gx = (h.nx + cols - 1) / cols;
   tc = 16;
   while ((size_t)gx * ((h.nt + tc - 1) / tc) > (size_t)kPartBlocks) tc *= 2;
   grid = dim3(gx, (h.nt + tc - 1) / tc);

@@ -92,62 +92,46 @@ __device__ inline void givens_column(double* __restrict__ scal, int j, const dou
   if (!isfinite(rho) || !isfinite(hn)) scal[S_FLAG] = 1.0;
 }
 
-// One work item of the tiled matvec y = M x: this warp's 32 spatial columns [i0, i0+32) over
-// time levels [t0, t1), keeping level t-1 in registers; spatial neighbours of s = x_t + x_{t-1}
-// come from lane shuffles (halo columns loaded by lanes 0 and 31). Five FP64 operations per
-// unknown:  y_t,i = (x_t - x_{t-1})_i - [L s_{i-1} + D s_i + U s_{i+1}], (L, D, U) = tau/2 A_t.
+// One work item of the tiled matvec y = M x: this warp's kMvCols = 30 output columns
+// [o0, o0 + 30) over time levels [t0, t1), keeping level t-1 in registers. Lane L holds column
+// o0 - 1 + L (lanes 0 and 31 are the halo), so the spatial neighbours of s = x_t + x_{t-1} come
+// from lane shuffles with no FP64 work of their own. Five FP64 operations per unknown:
+//  y_t,i = (x_t - x_{t-1})_i - [L s_{i-1} + D s_i + U s_{i+1}], (L, D, U) = tau/2 A_t.
 // MODE 0: y only. MODE 1: y = b - M x, acc[0] += y.y. MODE 2: acc[q] += V_q . y (q < ND, a
 // compile-time count so that no predicated-off FP64 instruction is issued), acc[ND] += y.y.
+constexpr int kMvCols = 30;
 template <typename IN, int MODE, int ND, int NA>
 __device__ __forceinline__ void matvec_item(const IN* __restrict__ x, double* __restrict__ y,
-                                            const double* __restrict__ b, int nx, int t0, int t1, int i0,
+                                            const double* __restrict__ b, int nx, int t0, int t1, int o0,
                                             const double* __restrict__ L, const double* __restrict__ D,
                                             const double* __restrict__ U, int rows, const double* __restrict__ V,
                                             size_t vstride, double (&acc)[NA]) {
   const int lane = threadIdx.x & 31;
-  const int i = i0 + lane;
-  const bool act = i < nx;
-  double xp = 0.0, xpl = 0.0, xpr = 0.0;
-  if (t0 > 0) {
-    const size_t r = (size_t)(t0 - 1) * nx;
-    if (act) xp = ld(x + r + i);
-    if (lane == 0 && i0 > 0 && i0 - 1 < nx) xpl = ld(x + r + i0 - 1);
-    if (lane == 31 && i0 + 32 < nx) xpr = ld(x + r + i0 + 32);
-  }
+  const int i = o0 - 1 + lane;
+  const bool in = i >= 0 && i < nx;               // the column exists (x is zero outside)
+  const bool act = in && lane > 0 && lane < 31;   // an output column of this item
+  double xp = 0.0;
+  if (t0 > 0 && in) xp = ld(x + (size_t)(t0 - 1) * nx + i);
   for (int t = t0; t < t1; ++t) {
     const size_t r = (size_t)t * nx;
-    const double xc = act ? ld(x + r + i) : 0.0;
-    const double s = xc + xp, d = xc - xp;
-    double sl = __shfl_up_sync(0xffffffffu, s, 1);
-    double sr = __shfl_down_sync(0xffffffffu, s, 1);
-    double xl = 0.0, xr = 0.0;
-    if (lane == 0) {
-      xl = (i0 > 0 && i0 - 1 < nx) ? ld(x + r + i0 - 1) : 0.0;
-      sl = xl + xpl;
-    }
-    if (lane == 31) {
-      xr = (i0 + 32 < nx) ? ld(x + r + i0 + 32) : 0.0;
-      sr = xr + xpr;
-    }
+    const double xc = in ? ld(x + r + i) : 0.0;
     if (MODE == 1) {
       // restart residual from a zero initial guess: when every value this warp reads is +-0
       // (integer test, warp-uniform), y = b - M x = b without any FP64 arithmetic
       auto z = [](double v) { return (__double_as_longlong(v) << 1) == 0; };
-      const bool mine = z(xc) && z(xp) && (lane != 0 || (z(xl) && z(xpl))) && (lane != 31 || (z(xr) && z(xpr)));
-      if (__all_sync(0xffffffffu, mine)) {
+      if (__all_sync(0xffffffffu, z(xc) && z(xp))) {
         if (act) {
           const double v = __ldg(b + r + i);
           acc[0] = fma(v, v, acc[0]);
           y[r + i] = v;
         }
         xp = xc;
-        if (lane == 0) xpl = xl;  // both zero here
-        if (lane == 31) xpr = xr;
         continue;
       }
     }
-    if (lane == 0) xpl = xl;
-    if (lane == 31) xpr = xr;
+    const double s = xc + xp, d = xc - xp;
+    const double sl = __shfl_up_sync(0xffffffffu, s, 1);
+    const double sr = __shfl_down_sync(0xffffffffu, s, 1);
     if (act) {
       const size_t c = rows == 1 ? (size_t)i : r + i;
       double v = fma(-__ldg(L + c), sl, d);

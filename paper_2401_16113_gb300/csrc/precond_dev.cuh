@@ -657,5 +657,176 @@ __global__ void __launch_bounds__(512) k_tridiag(C_t<R>* __restrict__ spec, int 
 }
 
 
+// ------------------------------------------------------------------ partitioned tridiagonal solve
+// step (b) by the partition method, T = 2^lgT >= 32 threads per bin and G bins per
+// CTA: thread l of a bin owns the chunk of rows [l ch, (l+1) ch), rows >= nx being identity rows,
+// and keeps its per-row data in shared memory (layout l*cs + j, odd stride cs):
+//  (1) downward Thomas elimination with the previous chunk's last unknown y_{l-1} as a parameter,
+//      x_i + c'_i x_{i+1} = d'_i + v_i y_{l-1}, storing (c', d', v);
+//  (2) an upward recurrence writing the chunk's first unknown as x_s = G + H y_{l-1} + J y_l,
+//      y_l the chunk's last unknown;
+//  the T last-row unknowns then satisfy a tridiagonal system (row e_l of (1) with x_{e+1} taken
+//  from chunk l+1's (G, H, J)), solved by parallel cyclic reduction in shared memory;
+//  (3) upward back substitution x_i = d'_i + v_i y_{l-1} - c'_i x_{i+1} from x_e = y_l.
+// The right-hand sides and the coefficients a_i = -lo_i, dg_i = di_i, c_i = -up_i (chunk-
+// transposed tables [j][l] built with the handle) are staged by asynchronous copies, all in
+// flight at once; the coefficients are shared by the CTA's G bins. The 1/lambda_2 scaling of the
+// right-hand side is applied to the solution (the system is linear).
+__host__ __device__ __forceinline__ size_t tri_part_bin_elems(int T, int cs) { return 3 * (size_t)T * cs + 4 * (size_t)T; }
+__host__ __device__ __forceinline__ size_t tri_part_bytes(int G, int T, int cs, size_t rsize) {
+  const size_t coef = ((3 * (size_t)T * cs * rsize) + 15) & ~(size_t)15;
+  return coef + (size_t)G * tri_part_bin_elems(T, cs) * 2 * rsize;
+}
+
+template <typename R>
+__device__ __forceinline__ C_t<R> crcp(C_t<R> a);
+template <>
+__device__ __forceinline__ float2 crcp<float>(float2 a) {
+  float s;  // hardware reciprocal (about 1 ulp): the FP32 preconditioner needs no correct rounding
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(fmaf(a.x, a.x, a.y * a.y)));
+  return make_float2(a.x * s, -a.y * s);
+}
+template <>
+__device__ __forceinline__ double2 crcp<double>(double2 a) {
+  const double s = 1.0 / fma(a.x, a.x, a.y * a.y);
+  return make_double2(a.x * s, -a.y * s);
+}
+
+// asynchronous global -> shared copy of 4, 8 or 16 bytes (both addresses aligned to the size)
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem_dst, const void* gmem_src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(gmem_src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+template <typename R>
+__global__ void __launch_bounds__(512) k_tridiag_part(C_t<R>* __restrict__ spec, int nx, int K, int pitch, int ch,
+                                                      int cs, int lgT, const R* __restrict__ tri,
+                                                      const C_t<R>* __restrict__ mu, const C_t<R>* __restrict__ il2) {
+  using C = C_t<R>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int T = 1 << lgT, G = blockDim.x >> lgT;
+  const int g = threadIdx.x >> lgT, l = threadIdx.x & (T - 1);
+  const int k = blockIdx.x * G + g;
+  const bool valid = k < K;
+  R* sa = reinterpret_cast<R*>(smraw);  // staged coefficients, layout l*cs + j
+  R* sdg = sa + (size_t)T * cs;
+  R* sc = sdg + (size_t)T * cs;
+  const size_t coef = ((3 * (size_t)T * cs * sizeof(R)) + 15) & ~(size_t)15;
+  C* sd = reinterpret_cast<C*>(smraw + coef) + (size_t)g * tri_part_bin_elems(T, cs);  // rhs -> d' -> x
+  C* scp = sd + (size_t)T * cs;  // c'
+  C* sv = scp + (size_t)T * cs;  // v
+  C* pa = sv + (size_t)T * cs;   // reduced system
+  C* pb = pa + T;
+  C* pc = pb + T;
+  C* pd = pc + T;
+  const C zero = cmk<C>(0, 0), one = cmk<C>(1, 0);
+  C* row = spec + (size_t)(valid ? k : 0) * pitch;
+
+  // staging: coefficients by the whole CTA (table row j = chunk row j of every thread), right-
+  // hand side by the bin's threads (element i = L ch + j)
+  for (int e = threadIdx.x; e < 3 * ch * T; e += blockDim.x) {
+    const int jq = e >> lgT, L = e & (T - 1);  // jq = q ch + j
+    const int q = jq >= 2 * ch ? 2 : (jq >= ch ? 1 : 0), j = jq - q * ch;
+    cp_async<sizeof(R)>(sa + (size_t)q * T * cs + L * cs + j, tri + e);
+  }
+  const int dL = T / ch, dj = T - dL * ch;  // i += T moves (L, j) by (dL, dj), dj < ch
+  for (int L = l / ch, j = l - (l / ch) * ch; L < T;) {
+    const int i = L * ch + j;
+    if (valid && i < nx) cp_async<sizeof(C)>(sd + L * cs + j, row + i);
+    else sd[L * cs + j] = zero;
+    j += dj;
+    L += dL;
+    if (j >= ch) { j -= ch; ++L; }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+
+  const C muk = valid ? mu[k] : one;
+  C* D = sd + l * cs;
+  C* CP = scp + l * cs;
+  C* V = sv + l * cs;
+  const R* A = sa + l * cs;
+  const R* DG = sdg + l * cs;
+  const R* CC = sc + l * cs;
+  // (1) downward elimination
+  C cpr = zero, dpr = zero, vpr = one;
+  const int nrow = nx - l * ch;  // rows j >= nrow are identity rows
+  for (int j = 0; j < ch; ++j) {
+    const R a = A[j], c = CC[j];
+    const C b = j < nrow ? cmk<C>(muk.x - DG[j], muk.y) : one;
+    const C inv = crcp<R>(cmk<C>(b.x - a * cpr.x, b.y - a * cpr.y));
+    const C dj = D[j];
+    cpr = cscale(inv, c);
+    dpr = cmul(cmk<C>(dj.x - a * dpr.x, dj.y - a * dpr.y), inv);
+    vpr = cmul(cscale(vpr, -a), inv);
+    CP[j] = cpr;
+    D[j] = dpr;
+    V[j] = vpr;
+  }
+  // (2) upward: x_s = G + H y_{l-1} + J y_l
+  C Gs = zero, Hs = zero, Js = one;
+  for (int j = ch - 2; j >= 0; --j) {
+    const C cj = CP[j];
+    Gs = csub(D[j], cmul(cj, Gs));
+    Hs = csub(V[j], cmul(cj, Hs));
+    Js = cscale(cmul(cj, Js), (R)-1);
+  }
+  pa[l] = Gs;
+  pb[l] = Hs;
+  pc[l] = Js;
+  __syncthreads();
+  C Gn = zero, Hn = zero, Jn = zero;
+  if (l + 1 < T) {
+    Gn = pa[l + 1];
+    Hn = pb[l + 1];
+    Jn = pc[l + 1];
+  }
+  __syncthreads();
+  // row l: -v_e y_{l-1} + (1 + c'_e H_{l+1}) y_l + c'_e J_{l+1} y_{l+1} = d'_e - c'_e G_{l+1}
+  pa[l] = cscale(vpr, (R)-1);
+  pb[l] = cadd(one, cmul(cpr, Hn));
+  pc[l] = cmul(cpr, Jn);
+  pd[l] = csub(dpr, cmul(cpr, Gn));
+  __syncthreads();
+  for (int delta = 1; delta < T; delta <<= 1) {
+    C lA = zero, lB = one, lC = zero, lD = zero, hA = zero, hB = one, hC = zero, hD = zero;
+    if (l - delta >= 0) { lA = pa[l - delta]; lB = pb[l - delta]; lC = pc[l - delta]; lD = pd[l - delta]; }
+    if (l + delta < T) { hA = pa[l + delta]; hB = pb[l + delta]; hC = pc[l + delta]; hD = pd[l + delta]; }
+    const C k1 = cmul(pa[l], crcp<R>(lB)), k2 = cmul(pc[l], crcp<R>(hB));
+    const C nA = cscale(cmul(lA, k1), (R)-1);
+    const C nC = cscale(cmul(hC, k2), (R)-1);
+    const C nB = csub(csub(pb[l], cmul(lC, k1)), cmul(hA, k2));
+    const C nD = csub(csub(pd[l], cmul(lD, k1)), cmul(hD, k2));
+    __syncthreads();
+    pa[l] = nA; pb[l] = nB; pc[l] = nC; pd[l] = nD;
+    __syncthreads();
+  }
+  const C y = cmul(pd[l], crcp<R>(pb[l]));
+  pa[l] = y;
+  __syncthreads();
+  const C yp = l > 0 ? pa[l - 1] : zero;
+  // (3) back substitution
+  C x = y;
+  D[ch - 1] = x;
+  for (int j = ch - 2; j >= 0; --j) {
+    x = csub(cadd(D[j], cmul(V[j], yp)), cmul(CP[j], x));
+    D[j] = x;
+  }
+  __syncthreads();
+  if (valid) {
+    const C sk = il2[k];
+    for (int L = l / ch, j = l - (l / ch) * ch; L < T;) {
+      const int i = L * ch + j;
+      if (i >= nx) break;
+      row[i] = cmul(sd[L * cs + j], sk);
+      j += dj;
+      L += dL;
+      if (j >= ch) { j -= ch; ++L; }
+    }
+  }
+}
+
 }  // namespace pdev
 }  // namespace aao
