@@ -142,9 +142,9 @@ __global__ void __launch_bounds__(kThreads) k_matvec(const IN* __restrict__ x, d
   const unsigned int nblk = gridDim.x * gridDim.y;
   const unsigned int bid = blockIdx.y * gridDim.x + blockIdx.x;
   if constexpr (MODE == 2) {
-    block_sums<NA>(acc, nd + 1, part + (size_t)bid * kPartLd);
+    block_sums_wide<NA>(acc, nd + 1, part + (size_t)bid * kPartLd);
   } else {
-    block_sums<NA>(acc, 1, part + (size_t)bid * kPartLd);
+    block_sums_wide<NA>(acc, 1, part + (size_t)bid * kPartLd);
   }
   if (!last_block(counter, nblk)) return;
   if constexpr (MODE == 2) {
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(kThreads) k_mdot(const double* __restrict__ V,
 #pragma unroll
     for (int q = 0; q < NV; ++q) acc[q] = fma(__ldg(Vc + (size_t)q * n + e), wv, acc[q]);
   }
-  block_sums<NV>(acc, nv, part + (size_t)blockIdx.x * kPartLd);
+  block_sums_wide<NV>(acc, nv, part + (size_t)blockIdx.x * kPartLd);
   if (!last_block(counter, gridDim.x)) return;
   finish_sums(part, gridDim.x, nv, [&](int q, double v) { out[c0 + q] = v; }, counter);
 }
@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(kThreads) k_update(double* __restrict__ w, con
     w[e] = wv;
     acc[0] = fma(wv, wv, acc[0]);
   }
-  block_sums<1>(acc, 1, part + (size_t)blockIdx.x * kPartLd);
+  block_sums_wide<1>(acc, 1, part + (size_t)blockIdx.x * kPartLd);
   if (!last_block(counter, gridDim.x)) return;
   finish_sums(part, gridDim.x, 1, [&](int, double v) {
     scal[S_WP2] = v;
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(kThreads) k_dot_self(const double* __restrict_
     const double a = __ldg(v + e);
     acc[0] = fma(a, a, acc[0]);
   }
-  block_sums<1>(acc, 1, part + (size_t)blockIdx.x * kPartLd);
+  block_sums_wide<1>(acc, 1, part + (size_t)blockIdx.x * kPartLd);
   if (!last_block(counter, gridDim.x)) return;
   finish_sums(part, gridDim.x, 1, [&](int, double s) { scal[slot] = s; }, counter);
 }

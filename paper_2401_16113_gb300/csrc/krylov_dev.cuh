@@ -64,6 +64,26 @@ __device__ __forceinline__ void block_sums(const double (&acc)[CNT], int cnt, do
   __syncthreads();
 }
 
+// The same with fewer FP64 instructions, for kernels that can spare CNT * kThreads doubles of
+// static shared memory: value q is summed by warp q mod 8, each lane adding the 8 partials of its
+// lane position before one shuffle tree (12 FP64 warp instructions per value instead of 48).
+template <int CNT>
+__device__ __forceinline__ void block_sums_wide(const double (&acc)[CNT], int cnt, double* out) {
+  __shared__ double red[CNT][kThreads];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < CNT; ++q) red[q][threadIdx.x] = acc[q];
+  __syncthreads();
+  for (int q = warp; q < cnt; q += kThreads / 32) {
+    double v = red[q][lane];
+#pragma unroll
+    for (int k = 1; k < kThreads / 32; ++k) v += red[q][lane + 32 * k];
+    v = warp_sum(v);
+    if (lane == 0) out[q] = v;
+  }
+  __syncthreads();
+}
+
 // Givens update of Hessenberg column j. w = M z_j with z_j = P^{-1} v_j for the normalised
 // v_j = sigma_j V_j, so h_ij = v_i . w = sigma_i d_i and h_{j+1,j} = ||w'||; one thread.
 __device__ inline void givens_column(double* __restrict__ scal, int j, const double* d1, const double* d2) {
