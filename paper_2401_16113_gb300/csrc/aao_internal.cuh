@@ -166,6 +166,7 @@ struct Handle {
   double* part = nullptr; // block partial sums
   unsigned int* counter = nullptr;  // completion counter of the last-block reductions
   int part_blocks = 0;
+  int sms = 0;            // multiprocessors of the handle's device
   double* host_scal = nullptr;  // pinned mirror
 };
 

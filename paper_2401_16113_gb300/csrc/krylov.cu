@@ -24,6 +24,8 @@
 
 #include <chrono>
 #include <complex>
+#include <mutex>
+#include <unordered_map>
 #include <vector>
 
 #include "krylov_dev.cuh"
@@ -113,8 +115,8 @@ __global__ void k_rhs(double* __restrict__ b, int nx, int nt, const double* __re
   }
 }
 
-// y = M x over a (column strip, time chunk) grid: blockIdx.x picks 8 strips of 32 columns (one
-// per warp), blockIdx.y a chunk of tc time levels.
+// y = M x over strips of kMvCols columns (one warp item each, with a halo column per side) and all
+// time levels.
 // MODE 0: y = M x.
 // MODE 1: y = b - M x (the restart residual, written as the raw first basis vector); the last
 //         block sets ||r||^2, sigma_0 = 1/||r|| and g = (||r||, 0, ...).
@@ -122,7 +124,7 @@ __global__ void k_rhs(double* __restrict__ b, int nx, int nt, const double* __re
 //         finished by the last block into scal[S_D1 + q] and scal[S_WN2].
 template <typename IN, int MODE, int ND>
 __global__ void __launch_bounds__(kThreads) k_matvec(const IN* __restrict__ x, double* __restrict__ y,
-                                                     const double* __restrict__ b, int nx, int nt, int tc,
+                                                     const double* __restrict__ b, int nx, int nt,
                                                      const double* __restrict__ L, const double* __restrict__ D,
                                                      const double* __restrict__ U, int rows,
                                                      const double* __restrict__ V, size_t vstride,
@@ -130,17 +132,28 @@ __global__ void __launch_bounds__(kThreads) k_matvec(const IN* __restrict__ x, d
                                                      unsigned int* __restrict__ counter, int m) {
   constexpr int NA = MODE == 2 ? ND + 1 : 1;
   constexpr int nd = ND;
-  const int warp = threadIdx.x >> 5;
-  const int o0 = (blockIdx.x * (kThreads / 32) + warp) * kMvCols;
-  const int t0 = blockIdx.y * tc;
-  const int t1 = min(nt, t0 + tc);
+  // one wave of blocks: the (strip, time level) rows, strip-major, are split into one contiguous
+  // range per warp, so every warp does the same work to within one row and keeps level t-1 in
+  // registers along its range
+  const int strips = (nx + kMvCols - 1) / kMvCols;
+  const long long R = (long long)strips * nt;
+  const long long W = (long long)gridDim.x * (kThreads / 32);
+  const long long w = (long long)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+  long long r = w * R / W;
+  const long long r1 = (w + 1) * R / W;
   double acc[NA];
 #pragma unroll
   for (int q = 0; q < NA; ++q) acc[q] = 0.0;
-  matvec_item<IN, MODE, ND, NA>(x, y, b, nx, t0, t1, o0, L, D, U, rows, V, vstride, acc);
+  while (r < r1) {
+    const int strip = (int)(r / nt);
+    const int t0 = (int)(r - (long long)strip * nt);
+    const int t1 = (int)((long long)t0 + (r1 - r) < (long long)nt ? (long long)t0 + (r1 - r) : (long long)nt);
+    matvec_item<IN, MODE, ND, NA>(x, y, b, nx, t0, t1, strip * kMvCols, L, D, U, rows, V, vstride, acc);
+    r += t1 - t0;
+  }
   if constexpr (MODE == 0) return;
-  const unsigned int nblk = gridDim.x * gridDim.y;
-  const unsigned int bid = blockIdx.y * gridDim.x + blockIdx.x;
+  const unsigned int nblk = gridDim.x;
+  const unsigned int bid = blockIdx.x;
   if constexpr (MODE == 2) {
     block_sums_wide<NA>(acc, nd + 1, part + (size_t)bid * kPartLd);
   } else {
@@ -260,6 +273,28 @@ __global__ void __launch_bounds__(kThreads) k_dot_self(const double* __restrict_
 int grid_for(size_t n) {
   size_t g = (n + kThreads - 1) / kThreads;
   return (int)(g < (size_t)kRedBlocks ? g : (size_t)kRedBlocks);
+}
+
+// Blocks of kThreads threads that are resident at once on h's device (one full wave, so that no
+// partial second wave idles most SMs), at most `need` and at most kPartBlocks.
+int wave_blocks(const Handle& h, const void* kernel, size_t need) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, int> occ;
+  int o = 0;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = occ.find(kernel);
+    if (it == occ.end()) {
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kernel, kThreads, 0) != cudaSuccess || o < 1) o = 1;
+      occ[kernel] = o;
+    } else {
+      o = it->second;
+    }
+  }
+  size_t g = (size_t)o * (size_t)(h.sms > 0 ? h.sms : 1);
+  if (g > need) g = need;
+  if (g > (size_t)kPartBlocks) g = kPartBlocks;
+  return (int)(g > 0 ? g : 1);
 }
 
 int ensure_workspace(Handle& h, int m) {
@@ -424,6 +459,11 @@ int build_tables(Handle& h) {
   AAO_TRY_CUDA(cudaMalloc(&h.counter, sizeof(unsigned int) * 4));
   AAO_TRY_CUDA(cudaMemsetAsync(h.counter, 0, sizeof(unsigned int) * 4, h.stream));
   h.part_blocks = kRedBlocks;
+  {
+    int dev = 0;
+    AAO_TRY_CUDA(cudaGetDevice(&dev));
+    AAO_TRY_CUDA(cudaDeviceGetAttribute(&h.sms, cudaDevAttrMultiProcessorCount, dev));
+  }
   AAO_TRY_CUDA(cudaMalloc(&h.part, sizeof(double) * (size_t)kPartBlocks * kPartLd));
   AAO_TRY_CUDA(cudaMallocHost(&h.host_scal, sizeof(double) * 8));
   // the temporary gS buffer must outlive the build kernel
@@ -449,24 +489,15 @@ void free_handle(Handle& h) {
 namespace {
 
 // time-chunk length: enough blocks to fill the GPU, at most kPartBlocks partial sums
-void matvec_grid(const Handle& h, dim3& grid, int& tc) {
-  const int cols = (kThreads / 32) * kMvCols;  // output columns per block
-  const int gx = (h.nx + cols - 1) / cols;
-  tc = 16;
-  while ((size_t)gx * ((h.nt + tc - 1) / tc) > (size_t)kPartBlocks) tc *= 2;
-  grid = dim3(gx, (h.nt + tc - 1) / tc);
-}
-
 template <typename IN>
 int matvec_t(Handle& h, const IN* x, double* y, const double* b, const double* V, int nd, int m, double bytes,
              double flops) {
-  dim3 grid;
-  int tc;
-  matvec_grid(h, grid, tc);
+  const size_t rowsw = (size_t)((h.nx + kMvCols - 1) / kMvCols) * h.nt;  // warp rows
+  const size_t need = (rowsw + kThreads / 32 - 1) / (kThreads / 32);
   ProfScope ps(AAO_K_MATVEC, h.stream, bytes, flops);
-#define AAO_MV2(ND)                                                                                    \
-  k_matvec<IN, 2, ND><<<grid, kThreads, 0, h.stream>>>(x, y, nullptr, h.nx, h.nt, tc, h.mL, h.mD, h.mU, \
-                                                       h.coef_rows, V, h.n, h.part, h.scal, h.counter, m)
+#define AAO_MV2(ND)                                                                                              \
+  k_matvec<IN, 2, ND><<<wave_blocks(h, (const void*)k_matvec<IN, 2, ND>, need), kThreads, 0, h.stream>>>(        \
+      x, y, nullptr, h.nx, h.nt, h.mL, h.mD, h.mU, h.coef_rows, V, h.n, h.part, h.scal, h.counter, m)
   if (V && nd > 0) {
     switch (nd) {
       case 1: AAO_MV2(1); break;
@@ -479,11 +510,11 @@ int matvec_t(Handle& h, const IN* x, double* y, const double* b, const double* V
       default: AAO_MV2(8); break;
     }
   } else if (b) {
-    k_matvec<IN, 1, 0><<<grid, kThreads, 0, h.stream>>>(x, y, b, h.nx, h.nt, tc, h.mL, h.mD, h.mU, h.coef_rows,
-                                                        nullptr, h.n, h.part, h.scal, h.counter, m);
+    k_matvec<IN, 1, 0><<<wave_blocks(h, (const void*)k_matvec<IN, 1, 0>, need), kThreads, 0, h.stream>>>(
+        x, y, b, h.nx, h.nt, h.mL, h.mD, h.mU, h.coef_rows, nullptr, h.n, h.part, h.scal, h.counter, m);
   } else {
-    k_matvec<IN, 0, 0><<<grid, kThreads, 0, h.stream>>>(x, y, nullptr, h.nx, h.nt, tc, h.mL, h.mD, h.mU,
-                                                        h.coef_rows, nullptr, h.n, h.part, h.scal, h.counter, m);
+    k_matvec<IN, 0, 0><<<wave_blocks(h, (const void*)k_matvec<IN, 0, 0>, need), kThreads, 0, h.stream>>>(
+        x, y, nullptr, h.nx, h.nt, h.mL, h.mD, h.mU, h.coef_rows, nullptr, h.n, h.part, h.scal, h.counter, m);
   }
 #undef AAO_MV2
   AAO_CHECK_LAUNCH();
@@ -543,7 +574,7 @@ int mdot(Handle& h, int c0, int cnt, const double* w, double* out) {
   const size_t n = h.n;
   const int g = grid_for(n);
   ProfScope ps(AAO_K_ARNOLDI, h.stream, 8.0 * (double)n * (cnt + 1), 2.0 * (double)n * cnt);
-#define AAO_MD(NV) k_mdot<NV><<<g, kThreads, 0, h.stream>>>(h.V, c0, n, w, h.part, out, h.counter)
+#define AAO_MD(NV) k_mdot<NV><<<wave_blocks(h, (const void*)k_mdot<NV>, g), kThreads, 0, h.stream>>>(h.V, c0, n, w, h.part, out, h.counter)
   switch (cnt) {
     case 1: AAO_MD(1); break;
     case 2: AAO_MD(2); break;
@@ -575,7 +606,7 @@ int update(Handle& h, double* w, int j, int pass) {
   const int g = grid_for(n);
   const int nv = j + 1;
   ProfScope ps(AAO_K_ARNOLDI, h.stream, 8.0 * (double)n * (nv + 2), 2.0 * (double)n * (nv + 1));
-#define AAO_UP(NV) k_update<NV><<<g, kThreads, 0, h.stream>>>(w, h.V, j, n, pass, h.scal, h.part, h.counter)
+#define AAO_UP(NV) k_update<NV><<<wave_blocks(h, (const void*)k_update<NV>, g), kThreads, 0, h.stream>>>(w, h.V, j, n, pass, h.scal, h.part, h.counter)
   switch (nv) {
     case 1: AAO_UP(1); break;
     case 2: AAO_UP(2); break;
@@ -605,7 +636,7 @@ int run_fgmres(Handle& h, const double* b, double* x, double tol, int m, int max
 
   {
     ProfScope ps(AAO_K_OTHER, h.stream, 8.0 * (double)n);
-    k_dot_self<<<g, kThreads, 0, h.stream>>>(b, n, h.part, h.scal, S_BNORM2, h.counter);
+    k_dot_self<<<wave_blocks(h, (const void*)k_dot_self, g), kThreads, 0, h.stream>>>(b, n, h.part, h.scal, S_BNORM2, h.counter);
   }
   AAO_CHECK_LAUNCH();
   AAO_TRY(read_scalars(h, S_BNORM2, 1));
@@ -661,9 +692,9 @@ int run_fgmres(Handle& h, const double* b, double* x, double tol, int m, int max
       {
         ProfScope ps(AAO_K_OTHER, h.stream, (double)n * (16.0 + zsz * jd));
         if (h.mixed)
-          k_xupdate<float><<<g, kThreads, 0, h.stream>>>(x, (const float*)h.Z, jd, n, h.scal);
+          k_xupdate<float><<<wave_blocks(h, (const void*)k_xupdate<float>, g), kThreads, 0, h.stream>>>(x, (const float*)h.Z, jd, n, h.scal);
         else
-          k_xupdate<double><<<g, kThreads, 0, h.stream>>>(x, (const double*)h.Z, jd, n, h.scal);
+          k_xupdate<double><<<wave_blocks(h, (const void*)k_xupdate<double>, g), kThreads, 0, h.stream>>>(x, (const double*)h.Z, jd, n, h.scal);
       }
       AAO_CHECK_LAUNCH();
       ++restarts;
