@@ -179,7 +179,7 @@ int riesz_matvec(Handle& h, const void* x, bool x_is_float, double* y, const dou
 int riesz_rhs(Handle& h, double* b);
 int riesz_solve_bins(Handle& h, void* spec);
 int launch_matvec(Handle& h, const void* x, bool x_is_float, double* y, const double* b, const double* V = nullptr,
-                  int nd = 0, int m = 0);
+                  int nd = 0, int m = 0, bool with_bnorm = false);
 int launch_rhs(Handle& h, double* b);
 int run_fgmres(Handle& h, const double* b, double* x, double tol, int m, int maxit, aao_stats* st);
 void free_handle(Handle& h);

@@ -119,7 +119,7 @@ __global__ void k_rhs(double* __restrict__ b, int nx, int nt, const double* __re
 // time levels.
 // MODE 0: y = M x.
 // MODE 1: y = b - M x (the restart residual, written as the raw first basis vector); the last
-//         block sets ||r||^2, sigma_0 = 1/||r|| and g = (||r||, 0, ...).
+//         block sets ||r||^2, sigma_0 = 1/||r|| and g = (||r||, 0, ...). MODE 3: MODE 1 and ||b||^2.
 // MODE 2: y = M x, the first Gram-Schmidt projections d_q = V_q . y (q < nd <= 8) and ||y||^2,
 //         finished by the last block into scal[S_D1 + q] and scal[S_WN2].
 template <typename IN, int MODE, int ND>
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(kThreads) k_matvec(const IN* __restrict__ x, d
                                                      const double* __restrict__ V, size_t vstride,
                                                      double* __restrict__ part, double* __restrict__ scal,
                                                      unsigned int* __restrict__ counter, int m) {
-  constexpr int NA = MODE == 2 ? ND + 1 : 1;
+  constexpr int NA = MODE == 2 ? ND + 1 : (MODE == 3 ? 2 : 1);
   constexpr int nd = ND;
   // one wave of blocks: the (strip, time level) rows, strip-major, are split into one contiguous
   // range per warp, so every warp does the same work to within one row and keeps level t-1 in
@@ -157,13 +157,17 @@ __global__ void __launch_bounds__(kThreads) k_matvec(const IN* __restrict__ x, d
   if constexpr (MODE == 2) {
     block_sums_wide<NA>(acc, nd + 1, part + (size_t)bid * kPartLd);
   } else {
-    block_sums_wide<NA>(acc, 1, part + (size_t)bid * kPartLd);
+    block_sums_wide<NA>(acc, NA, part + (size_t)bid * kPartLd);
   }
   if (!last_block(counter, nblk)) return;
   if constexpr (MODE == 2) {
     finish_sums(part, nblk, nd + 1, [&](int q, double v) { scal[q < nd ? S_D1 + q : S_WN2] = v; }, counter);
   } else {
-    finish_sums(part, nblk, 1, [&](int, double v) {
+    finish_sums(part, nblk, NA, [&](int q, double v) {
+      if (q == 1) {
+        scal[S_BNORM2] = v;
+        return;
+      }
       scal[S_BETA2] = v;
       const double beta = sqrt(v);
       scal[S_SIG] = beta > 0.0 ? 1.0 / beta : 0.0;
@@ -491,7 +495,7 @@ namespace {
 // time-chunk length: enough blocks to fill the GPU, at most kPartBlocks partial sums
 template <typename IN>
 int matvec_t(Handle& h, const IN* x, double* y, const double* b, const double* V, int nd, int m, double bytes,
-             double flops) {
+             double flops, bool with_bnorm) {
   const size_t rowsw = (size_t)((h.nx + kMvCols - 1) / kMvCols) * h.nt;  // warp rows
   const size_t need = (rowsw + kThreads / 32 - 1) / (kThreads / 32);
   ProfScope ps(AAO_K_MATVEC, h.stream, bytes, flops);
@@ -509,6 +513,9 @@ int matvec_t(Handle& h, const IN* x, double* y, const double* b, const double* V
       case 7: AAO_MV2(7); break;
       default: AAO_MV2(8); break;
     }
+  } else if (b && with_bnorm) {
+    k_matvec<IN, 3, 0><<<wave_blocks(h, (const void*)k_matvec<IN, 3, 0>, need), kThreads, 0, h.stream>>>(
+        x, y, b, h.nx, h.nt, h.mL, h.mD, h.mU, h.coef_rows, nullptr, h.n, h.part, h.scal, h.counter, m);
   } else if (b) {
     k_matvec<IN, 1, 0><<<wave_blocks(h, (const void*)k_matvec<IN, 1, 0>, need), kThreads, 0, h.stream>>>(
         x, y, b, h.nx, h.nt, h.mL, h.mD, h.mU, h.coef_rows, nullptr, h.n, h.part, h.scal, h.counter, m);
@@ -525,17 +532,25 @@ int matvec_t(Handle& h, const IN* x, double* y, const double* b, const double* V
 
 // y = M x; with b: y = b - M x (restart residual); with V (nd <= 8): first Gram-Schmidt pass
 int launch_matvec(Handle& h, const void* x, bool x_is_float, double* y, const double* b, const double* V, int nd,
-                  int m) {
-  if (h.p.op == AAO_OP_RIESZ) return riesz_matvec(h, x, x_is_float, y, b, V, nd, m);
+                  int m, bool with_bnorm) {
+  if (h.p.op == AAO_OP_RIESZ) {
+    if (b && with_bnorm) {
+      ProfScope ps(AAO_K_OTHER, h.stream, 8.0 * (double)h.n);
+      k_dot_self<<<wave_blocks(h, (const void*)k_dot_self, grid_for(h.n)), kThreads, 0, h.stream>>>(
+          b, h.n, h.part, h.scal, S_BNORM2, h.counter);
+      AAO_CHECK_LAUNCH();
+    }
+    return riesz_matvec(h, x, x_is_float, y, b, V, nd, m);
+  }
   const double nn = (double)h.n;
   // x once, coefficients (3 per row of the time-dependent operator), y, b and V_q if present
   const double bytes = nn * (x_is_float ? 4.0 : 8.0) + 3.0 * 8.0 * (double)h.nx * h.coef_rows + nn * 8.0 +
                        (b ? nn * 8.0 : 0.0) + (V ? nn * 8.0 * nd : 0.0);
-  // per unknown: s and d (2 adds), three FMAs; residual: b - (1) and r.r (FMA); projections:
-  // nd FMAs and y.y (FMA)
-  const double flops = nn * (2.0 + 6.0 + (b ? 3.0 : 0.0) + (V ? 2.0 * (nd + 1) : 0.0));
-  if (x_is_float) return matvec_t<float>(h, (const float*)x, y, b, V, nd, m, bytes, flops);
-  return matvec_t<double>(h, (const double*)x, y, b, V, nd, m, bytes, flops);
+  // per unknown: s and d (2 adds), three FMAs; residual: b - (1) and r.r (FMA), b.b (FMA);
+  // projections: nd FMAs and y.y (FMA)
+  const double flops = nn * (2.0 + 6.0 + (b ? 3.0 : 0.0) + (b && with_bnorm ? 2.0 : 0.0) + (V ? 2.0 * (nd + 1) : 0.0));
+  if (x_is_float) return matvec_t<float>(h, (const float*)x, y, b, V, nd, m, bytes, flops, with_bnorm);
+  return matvec_t<double>(h, (const double*)x, y, b, V, nd, m, bytes, flops, with_bnorm);
 }
 
 void launch_rhs_raw(cudaStream_t s, double* b, int nx, int nt, const double* L, const double* D, const double* U,
@@ -634,25 +649,23 @@ int run_fgmres(Handle& h, const double* b, double* x, double tol, int m, int max
   const size_t zsz = h.mixed ? sizeof(float) : sizeof(double);
   char* Zb = reinterpret_cast<char*>(h.Z);
 
-  {
-    ProfScope ps(AAO_K_OTHER, h.stream, 8.0 * (double)n);
-    k_dot_self<<<wave_blocks(h, (const void*)k_dot_self, g), kThreads, 0, h.stream>>>(b, n, h.part, h.scal, S_BNORM2, h.counter);
-  }
-  AAO_CHECK_LAUNCH();
-  AAO_TRY(read_scalars(h, S_BNORM2, 1));
-  const double bnorm = sqrt(h.host_scal[0]);
-
   int its = 0, restarts = 0, status = AAO_OK;
-  double rel = 0.0, est = 0.0;
-  if (!(bnorm > 0.0)) {
-    AAO_TRY_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, h.stream));
-    AAO_TRY_CUDA(cudaStreamSynchronize(h.stream));
-    status = isfinite(bnorm) ? AAO_OK : AAO_BREAKDOWN;
-  } else {
-    for (;;) {
-      // restart residual r = b - M x, written as the raw first basis vector V_0
-      AAO_TRY(launch_matvec(h, x, false, h.V, b, nullptr, 0, m));
-      AAO_TRY(read_scalars(h, S_BETA2, 1));
+  double rel = 0.0, est = 0.0, bnorm = 0.0;
+  for (bool first = true;; first = false) {
+    // restart residual r = b - M x, written as the raw first basis vector V_0 (the first one also
+    // forms ||b||^2)
+    AAO_TRY(launch_matvec(h, x, false, h.V, b, nullptr, 0, m, first));
+    AAO_TRY(read_scalars(h, S_BETA2, 2));  // BETA2, BNORM2
+    if (first) {
+      bnorm = sqrt(h.host_scal[1]);
+      if (!(bnorm > 0.0)) {
+        AAO_TRY_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, h.stream));
+        AAO_TRY_CUDA(cudaStreamSynchronize(h.stream));
+        status = isfinite(bnorm) ? AAO_OK : AAO_BREAKDOWN;
+        break;
+      }
+    }
+    {
       const double beta = sqrt(h.host_scal[0]);
       rel = beta / bnorm;
       if (!isfinite(beta)) { status = AAO_BREAKDOWN; break; }

@@ -117,8 +117,9 @@ __device__ inline void givens_column(double* __restrict__ scal, int j, const dou
 // o0 - 1 + L (lanes 0 and 31 are the halo), so the spatial neighbours of s = x_t + x_{t-1} come
 // from lane shuffles with no FP64 work of their own. Five FP64 operations per unknown:
 //  y_t,i = (x_t - x_{t-1})_i - [L s_{i-1} + D s_i + U s_{i+1}], (L, D, U) = tau/2 A_t.
-// MODE 0: y only. MODE 1: y = b - M x, acc[0] += y.y. MODE 2: acc[q] += V_q . y (q < ND, a
-// compile-time count so that no predicated-off FP64 instruction is issued), acc[ND] += y.y.
+// MODE 0: y only. MODE 1: y = b - M x, acc[0] += y.y. MODE 3: as MODE 1, and acc[1] += b.b.
+// MODE 2: acc[q] += V_q . y (q < ND, a compile-time count so that no predicated-off FP64
+// instruction is issued), acc[ND] += y.y.
 constexpr int kMvCols = 30;
 template <typename IN, int MODE, int ND, int NA>
 __device__ __forceinline__ void matvec_item(const IN* __restrict__ x, double* __restrict__ y,
@@ -135,7 +136,7 @@ __device__ __forceinline__ void matvec_item(const IN* __restrict__ x, double* __
   for (int t = t0; t < t1; ++t) {
     const size_t r = (size_t)t * nx;
     const double xc = in ? ld(x + r + i) : 0.0;
-    if (MODE == 1) {
+    if (MODE == 1 || MODE == 3) {
       // restart residual from a zero initial guess: when every value this warp reads is +-0
       // (integer test, warp-uniform), y = b - M x = b without any FP64 arithmetic
       auto z = [](double v) { return (__double_as_longlong(v) << 1) == 0; };
@@ -143,6 +144,7 @@ __device__ __forceinline__ void matvec_item(const IN* __restrict__ x, double* __
         if (act) {
           const double v = __ldg(b + r + i);
           acc[0] = fma(v, v, acc[0]);
+          if constexpr (MODE == 3) acc[NA - 1] = fma(v, v, acc[NA - 1]);
           y[r + i] = v;
         }
         xp = xc;
@@ -157,9 +159,11 @@ __device__ __forceinline__ void matvec_item(const IN* __restrict__ x, double* __
       double v = fma(-__ldg(L + c), sl, d);
       v = fma(-__ldg(D + c), s, v);
       v = fma(-__ldg(U + c), sr, v);
-      if (MODE == 1) {
-        v = __ldg(b + r + i) - v;
+      if (MODE == 1 || MODE == 3) {
+        const double bv = __ldg(b + r + i);
+        v = bv - v;
         acc[0] = fma(v, v, acc[0]);
+        if constexpr (MODE == 3) acc[NA - 1] = fma(bv, bv, acc[NA - 1]);
       }
       y[r + i] = v;
       if (MODE == 2) {

@@ -487,7 +487,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 512 : 1024) k_fft_fwd(const d
                                                   const R* __restrict__ lam, const C_t<R>* __restrict__ tw,
                                                   const double* __restrict__ in_scale) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const R sc = in_scale ? (R)(*in_scale) : (R)1;
+  const R sc = in_scale ? to_r<R>(*in_scale) : (R)1;
   fft_fwd_tile<R>(v, spec, nx, N, log2n, P, pitch, lam, tw, sc, blockIdx.x * 2 * P, smraw);
 }
 
