@@ -127,25 +127,46 @@ __device__ __forceinline__ void matvec_item(const IN* __restrict__ x, double* __
                                             const double* __restrict__ L, const double* __restrict__ D,
                                             const double* __restrict__ U, int rows, const double* __restrict__ V,
                                             size_t vstride, double (&acc)[NA]) {
+  constexpr bool RES = MODE == 1 || MODE == 3;
+  constexpr int NVQ = MODE == 2 ? ND : 0;
   const int lane = threadIdx.x & 31;
   const int i = o0 - 1 + lane;
   const bool in = i >= 0 && i < nx;               // the column exists (x is zero outside)
   const bool act = in && lane > 0 && lane < 31;   // an output column of this item
   double xp = 0.0;
   if (t0 > 0 && in) xp = ld(x + (size_t)(t0 - 1) * nx + i);
+  // the loads of row t + 1 are issued before row t is computed (one row in flight ahead)
+  double xn = 0.0, ln = 0.0, dn = 0.0, un = 0.0, bn = 0.0, vn[NVQ > 0 ? NVQ : 1];
+  auto fetch = [&](int t) {
+    const size_t r = (size_t)t * nx;
+    xn = in ? ld(x + r + i) : 0.0;
+    if (act) {
+      const size_t c = rows == 1 ? (size_t)i : r + i;
+      ln = __ldg(L + c);
+      dn = __ldg(D + c);
+      un = __ldg(U + c);
+      if constexpr (RES) bn = __ldg(b + r + i);
+#pragma unroll
+      for (int q = 0; q < NVQ; ++q) vn[q] = __ldg(V + (size_t)q * vstride + r + i);
+    }
+  };
+  if (t0 < t1) fetch(t0);
   for (int t = t0; t < t1; ++t) {
     const size_t r = (size_t)t * nx;
-    const double xc = in ? ld(x + r + i) : 0.0;
-    if (MODE == 1 || MODE == 3) {
+    const double xc = xn, lc = ln, dc = dn, uc = un, bc = bn;
+    double vc[NVQ > 0 ? NVQ : 1];
+#pragma unroll
+    for (int q = 0; q < NVQ; ++q) vc[q] = vn[q];
+    if (t + 1 < t1) fetch(t + 1);
+    if constexpr (RES) {
       // restart residual from a zero initial guess: when every value this warp reads is +-0
       // (integer test, warp-uniform), y = b - M x = b without any FP64 arithmetic
       auto z = [](double v) { return (__double_as_longlong(v) << 1) == 0; };
       if (__all_sync(0xffffffffu, z(xc) && z(xp))) {
         if (act) {
-          const double v = __ldg(b + r + i);
-          acc[0] = fma(v, v, acc[0]);
-          if constexpr (MODE == 3) acc[NA - 1] = fma(v, v, acc[NA - 1]);
-          y[r + i] = v;
+          acc[0] = fma(bc, bc, acc[0]);
+          if constexpr (MODE == 3) acc[NA - 1] = fma(bc, bc, acc[NA - 1]);
+          y[r + i] = bc;
         }
         xp = xc;
         continue;
@@ -155,20 +176,18 @@ __device__ __forceinline__ void matvec_item(const IN* __restrict__ x, double* __
     const double sl = __shfl_up_sync(0xffffffffu, s, 1);
     const double sr = __shfl_down_sync(0xffffffffu, s, 1);
     if (act) {
-      const size_t c = rows == 1 ? (size_t)i : r + i;
-      double v = fma(-__ldg(L + c), sl, d);
-      v = fma(-__ldg(D + c), s, v);
-      v = fma(-__ldg(U + c), sr, v);
-      if (MODE == 1 || MODE == 3) {
-        const double bv = __ldg(b + r + i);
-        v = bv - v;
+      double v = fma(-lc, sl, d);
+      v = fma(-dc, s, v);
+      v = fma(-uc, sr, v);
+      if constexpr (RES) {
+        v = bc - v;
         acc[0] = fma(v, v, acc[0]);
-        if constexpr (MODE == 3) acc[NA - 1] = fma(bv, bv, acc[NA - 1]);
+        if constexpr (MODE == 3) acc[NA - 1] = fma(bc, bc, acc[NA - 1]);
       }
       y[r + i] = v;
-      if (MODE == 2) {
+      if constexpr (MODE == 2) {
 #pragma unroll
-        for (int q = 0; q < ND; ++q) acc[q] = fma(__ldg(V + (size_t)q * vstride + r + i), v, acc[q]);
+        for (int q = 0; q < ND; ++q) acc[q] = fma(vc[q], v, acc[q]);
         acc[ND] = fma(v, v, acc[ND]);
       }
     }
