@@ -47,27 +47,6 @@ __device__ __forceinline__ bool last_block(unsigned int* counter, unsigned int n
   return am_last;
 }
 
-// Executed by the last block: out(q) = sum over blocks b = 0..nblk-1 of part[b*ld + q], in a
-// fixed order; resets the counter for the next kernel.
-template <typename OUT>
-__device__ void finish_sums(const double* part, int nblk, int cnt, OUT out, unsigned int* counter) {
-  __shared__ double red[kThreads / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int q = 0; q < cnt; ++q) {
-    double s = 0.0;
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += __ldcg(part + (size_t)b * kPartLd + q);
-    s = warp_sum(s);
-    if (lane == 0) red[warp] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int wv = 0; wv < kThreads / 32; ++wv) t += red[wv];
-      out(q, t);
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *counter = 0u;
-}
 
 __global__ void k_build_coef(double* __restrict__ L, double* __restrict__ D, double* __restrict__ U, int nx,
                              int rows, double h, double half_tau, double sigma, double r, double bump,
@@ -161,9 +140,9 @@ __global__ void __launch_bounds__(kThreads) k_matvec(const IN* __restrict__ x, d
   }
   if (!last_block(counter, nblk)) return;
   if constexpr (MODE == 2) {
-    finish_sums(part, nblk, nd + 1, [&](int q, double v) { scal[q < nd ? S_D1 + q : S_WN2] = v; }, counter);
+    finish_sums_wide<NA>(part, nblk, nd + 1, [&](int q, double v) { scal[q < nd ? S_D1 + q : S_WN2] = v; }, counter);
   } else {
-    finish_sums(part, nblk, NA, [&](int q, double v) {
+    finish_sums_wide<NA>(part, nblk, NA, [&](int q, double v) {
       if (q == 1) {
         scal[S_BNORM2] = v;
         return;
@@ -195,7 +174,7 @@ __global__ void __launch_bounds__(kThreads) k_mdot(const double* __restrict__ V,
   }
   block_sums_wide<NV>(acc, nv, part + (size_t)blockIdx.x * kPartLd);
   if (!last_block(counter, gridDim.x)) return;
-  finish_sums(part, gridDim.x, nv, [&](int q, double v) { out[c0 + q] = v; }, counter);
+  finish_sums_wide<NV>(part, gridDim.x, nv, [&](int q, double v) { out[c0 + q] = v; }, counter);
 }
 
 // Gram-Schmidt pass `pass` (1 or 2) on w (the raw vector V_{j+1}, updated in place):
@@ -215,7 +194,29 @@ __global__ void __launch_bounds__(kThreads) k_update(double* __restrict__ w, con
   }
   __syncthreads();
   double acc[1] = {0.0};
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if constexpr (NV > 0) {
+    // two elements per step: all loads of both are issued before either is combined
+    for (; e + stride < n; e += 2 * stride) {
+      double wa = w[e], wb = w[e + stride], va[NV], vb[NV];
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        va[q] = __ldg(V + (size_t)q * n + e);
+        vb[q] = __ldg(V + (size_t)q * n + e + stride);
+      }
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        wa = fma(-cf[q], va[q], wa);
+        wb = fma(-cf[q], vb[q], wb);
+      }
+      w[e] = wa;
+      w[e + stride] = wb;
+      acc[0] = fma(wa, wa, acc[0]);
+      acc[0] = fma(wb, wb, acc[0]);
+    }
+  }
+  for (; e < n; e += stride) {
     double wv = w[e];
     if constexpr (NV > 0) {
 #pragma unroll
@@ -228,15 +229,18 @@ __global__ void __launch_bounds__(kThreads) k_update(double* __restrict__ w, con
   }
   block_sums_wide<1>(acc, 1, part + (size_t)blockIdx.x * kPartLd);
   if (!last_block(counter, gridDim.x)) return;
-  finish_sums(part, gridDim.x, 1, [&](int, double v) {
+  __shared__ double wp2;
+  finish_sums_wide<1>(part, gridDim.x, 1, [&](int, double v) {
     scal[S_WP2] = v;
-    if (pass == 1 && v < kReorthEta * kReorthEta * scal[S_WN2]) {
-      scal[S_REORTH] = 1.0;
-    } else {
-      scal[S_REORTH] = 0.0;
-      givens_column(scal, j, scal + S_D1, pass == 2 ? scal + S_D2 : nullptr);
-    }
+    wp2 = v;
   }, counter);
+  __syncthreads();
+  if (pass == 1 && wp2 < kReorthEta * kReorthEta * scal[S_WN2]) {
+    if (threadIdx.x == 0) scal[S_REORTH] = 1.0;
+    return;
+  }
+  if (threadIdx.x == 0) scal[S_REORTH] = 0.0;
+  givens_column_block(scal, j, wp2, scal + S_D1, pass == 2 ? scal + S_D2 : nullptr);
 }
 
 // x += sum_{i<jd} y_i Z_i with y = H(0:jd,0:jd)^{-1} g(0:jd) (each block solves the small
@@ -253,7 +257,28 @@ __global__ void __launch_bounds__(kThreads) k_xupdate(double* __restrict__ x, co
     }
   }
   __syncthreads();
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  // two elements per step, loads first
+  for (; e + stride < n; e += 2 * stride) {
+    double va = x[e], vb = x[e + stride];
+    int i = 0;
+    for (; i + 2 <= jd; i += 2) {
+      const double z0 = ld(Z + (size_t)i * n + e), z1 = ld(Z + (size_t)(i + 1) * n + e);
+      const double z2 = ld(Z + (size_t)i * n + e + stride), z3 = ld(Z + (size_t)(i + 1) * n + e + stride);
+      va = fma(ys[i], z0, va);
+      vb = fma(ys[i], z2, vb);
+      va = fma(ys[i + 1], z1, va);
+      vb = fma(ys[i + 1], z3, vb);
+    }
+    if (i < jd) {
+      va = fma(ys[i], ld(Z + (size_t)i * n + e), va);
+      vb = fma(ys[i], ld(Z + (size_t)i * n + e + stride), vb);
+    }
+    x[e] = va;
+    x[e + stride] = vb;
+  }
+  for (; e < n; e += stride) {
     double v = x[e];
     for (int i = 0; i < jd; ++i) v = fma(ys[i], ld(Z + (size_t)i * n + e), v);
     x[e] = v;
@@ -271,7 +296,7 @@ __global__ void __launch_bounds__(kThreads) k_dot_self(const double* __restrict_
   }
   block_sums_wide<1>(acc, 1, part + (size_t)blockIdx.x * kPartLd);
   if (!last_block(counter, gridDim.x)) return;
-  finish_sums(part, gridDim.x, 1, [&](int, double s) { scal[slot] = s; }, counter);
+  finish_sums_wide<1>(part, gridDim.x, 1, [&](int, double s) { scal[slot] = s; }, counter);
 }
 
 int grid_for(size_t n) {

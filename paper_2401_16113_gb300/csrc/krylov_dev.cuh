@@ -64,12 +64,20 @@ __device__ __forceinline__ void block_sums(const double (&acc)[CNT], int cnt, do
   __syncthreads();
 }
 
+// Shared scratch of CNT x kThreads doubles, one per CNT, used by the two reductions below (which
+// never run at the same time).
+template <int CNT>
+__device__ __forceinline__ double (&red_scratch())[CNT][kThreads] {
+  __shared__ double red[CNT][kThreads];
+  return red;
+}
+
 // The same with fewer FP64 instructions, for kernels that can spare CNT * kThreads doubles of
 // static shared memory: value q is summed by warp q mod 8, each lane adding the 8 partials of its
 // lane position before one shuffle tree (12 FP64 warp instructions per value instead of 48).
 template <int CNT>
 __device__ __forceinline__ void block_sums_wide(const double (&acc)[CNT], int cnt, double* out) {
-  __shared__ double red[CNT][kThreads];
+  auto& red = red_scratch<CNT>();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int q = 0; q < CNT; ++q) red[q][threadIdx.x] = acc[q];
@@ -82,6 +90,41 @@ __device__ __forceinline__ void block_sums_wide(const double (&acc)[CNT], int cn
     if (lane == 0) out[q] = v;
   }
   __syncthreads();
+}
+
+// Executed by the last block (blockDim.x == kThreads): out(q, total_q) for q < cnt <= CNT, total_q
+// = the sum over blocks b < nblk of part[b * kPartLd + q] in a fixed order. All values are reduced
+// at once (every thread loads its blocks' partials of every value, then warp q mod 8 reduces value
+// q), so the serial tail of the kernel is one round trip and one shuffle tree; out runs on thread
+// 0 in order of q. Resets the counter for the next kernel.
+template <int CNT, typename OUT>
+__device__ void finish_sums_wide(const double* part, int nblk, int cnt, OUT out, unsigned int* counter) {
+  auto& red = red_scratch<CNT>();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double s[CNT];
+#pragma unroll
+  for (int q = 0; q < CNT; ++q) s[q] = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += kThreads) {
+#pragma unroll
+    for (int q = 0; q < CNT; ++q)
+      if (q < cnt) s[q] += __ldcg(part + (size_t)b * kPartLd + q);
+  }
+#pragma unroll
+  for (int q = 0; q < CNT; ++q) red[q][threadIdx.x] = s[q];
+  __syncthreads();
+  for (int q = warp; q < cnt; q += kThreads / 32) {
+    double v = red[q][lane];
+#pragma unroll
+    for (int k = 1; k < kThreads / 32; ++k) v += red[q][lane + 32 * k];
+    v = warp_sum(v);
+    __syncwarp();
+    if (lane == 0) red[q][0] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < cnt; ++q) out(q, red[q][0]);
+    *counter = 0u;
+  }
 }
 
 // Givens update of Hessenberg column j. w = M z_j with z_j = P^{-1} v_j for the normalised
@@ -110,6 +153,46 @@ __device__ inline void givens_column(double* __restrict__ scal, int j, const dou
   scal[S_HN] = hn;
   scal[S_SIG + j + 1] = wn > 0.0 ? 1.0 / wn : 0.0;
   if (!isfinite(rho) || !isfinite(hn)) scal[S_FLAG] = 1.0;
+}
+
+// givens_column run by a whole block (the last block of a kernel): its inputs are staged in
+// shared memory by all threads in one round trip, then thread 0 runs the sequential rotations
+// out of shared memory and writes the results back. wp2 = ||w'||^2 as seen by every thread.
+__device__ inline void givens_column_block(double* __restrict__ scal, int j, double wp2, const double* d1,
+                                           const double* d2) {
+  __shared__ double sh_h[kLdH + 1], sh_cs[kLdH], sh_sn[kLdH];
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+    sh_h[i] = scal[S_SIG + i] * (d1[i] + (d2 ? d2[i] : 0.0));
+    if (i < j) {
+      sh_cs[i] = scal[S_CS + i];
+      sh_sn[i] = scal[S_SN + i];
+    }
+  }
+  __shared__ double g;
+  if (threadIdx.x == 0) g = scal[S_G + j];
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const double wn = sqrt(fmax(wp2, 0.0));
+  sh_h[j + 1] = wn;
+  for (int i = 0; i < j; ++i) {
+    const double a = sh_h[i], c = sh_h[i + 1];
+    sh_h[i] = sh_cs[i] * a + sh_sn[i] * c;
+    sh_h[i + 1] = -sh_sn[i] * a + sh_cs[i] * c;
+  }
+  const double rho = hypot(sh_h[j], sh_h[j + 1]);
+  const double cs = rho > 0.0 ? sh_h[j] / rho : 1.0, sn = rho > 0.0 ? sh_h[j + 1] / rho : 0.0;
+  double* H = scal + S_HMAT + (size_t)j * kLdH;
+  for (int i = 0; i < j; ++i) H[i] = sh_h[i];
+  H[j] = rho;
+  H[j + 1] = 0.0;
+  scal[S_CS + j] = cs;
+  scal[S_SN + j] = sn;
+  scal[S_G + j + 1] = -sn * g;
+  scal[S_G + j] = cs * g;
+  scal[S_EST] = fabs(sn * g);
+  scal[S_HN] = wn;
+  scal[S_SIG + j + 1] = wn > 0.0 ? 1.0 / wn : 0.0;
+  if (!isfinite(rho) || !isfinite(wn)) scal[S_FLAG] = 1.0;
 }
 
 // One work item of the tiled matvec y = M x: this warp's kMvCols = 30 output columns
