@@ -156,6 +156,7 @@ struct Handle {
   double2 *rz_chat = nullptr, *rz_tw = nullptr;
   double *rz_hcol = nullptr, *rz_hrow = nullptr, *rz_hcl = nullptr;
   float2* rz_lu = nullptr;
+  float2* rz_dinv = nullptr;  // inverses of the factors' diagonal blocks (L, U per block and bin)
 
   // FGMRES workspace (grown on demand)
   int ws_m = 0;

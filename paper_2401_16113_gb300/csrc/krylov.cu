@@ -505,7 +505,7 @@ int build_tables(Handle& h) {
 void free_handle(Handle& h) {
   void* bufs[] = {h.mL, h.mD, h.mU, h.gL, h.gR, h.pL, h.pD, h.pU, h.pLf, h.pDf, h.pUf, h.mu, h.il2, h.tw,
                   h.muf, h.il2f, h.twf, h.lam, h.ilam, h.lamf, h.ilamf, h.spec, h.V, h.Z, h.w, h.scal, h.part,
-                  h.counter, h.rz_chat, h.rz_tw, h.rz_hcol, h.rz_hrow, h.rz_hcl, h.rz_lu, h.tri};
+                  h.counter, h.rz_chat, h.rz_tw, h.rz_hcol, h.rz_hrow, h.rz_hcl, h.rz_lu, h.rz_dinv, h.tri};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (h.host_scal) cudaFreeHost(h.host_scal);

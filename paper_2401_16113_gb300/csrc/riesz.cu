@@ -248,12 +248,54 @@ __global__ void __launch_bounds__(256) k_lu_update(float2* __restrict__ M, int n
 }
 
 // ------------------------------------------------------------------------------- solves per apply
+// Inverses of the diagonal kNB x kNB blocks of every bin's factors (at aao_create): block bi of
+// bin k stores L_bb^{-1} (unit lower) and U_bb^{-1} (upper), row-major, zero beyond the block's
+// width. One warp per triangle: lane c forms column c of the inverse by substitution.
+__global__ void __launch_bounds__(64) k_rz_diaginv(const float2* __restrict__ LU, float2* __restrict__ dinv, int nx,
+                                                   int nb) {
+  __shared__ float2 blk[kNB][kNB + 1];
+  const int bi = blockIdx.x, k = blockIdx.y;
+  const int r0 = bi * kNB, w = min(kNB, nx - r0);
+  const float2* A = LU + (size_t)k * nx * nx;
+  for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x) {
+    const int i = e / kNB, j = e % kNB;
+    blk[i][j] = (i < w && j < w) ? A[(size_t)(r0 + i) * nx + r0 + j] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, tri = threadIdx.x >> 5;  // 0: L, 1: U
+  float2* out = dinv + (((size_t)k * nb + bi) * 2 + tri) * kNB * kNB;
+  float2 x[kNB];
+  if (tri == 0) {
+#pragma unroll
+    for (int i = 0; i < kNB; ++i) {
+      float2 v = make_float2(i == lane ? 1.f : 0.f, 0.f);
+#pragma unroll
+      for (int q = 0; q < i; ++q) v = csub(v, cmul(blk[i][q], x[q]));
+      x[i] = (i < w && lane < w) ? v : make_float2(0.f, 0.f);
+    }
+  } else {
+#pragma unroll
+    for (int i = kNB - 1; i >= 0; --i) {
+      float2 v = make_float2(i == lane ? 1.f : 0.f, 0.f);
+#pragma unroll
+      for (int q = i + 1; q < kNB; ++q) v = csub(v, cmul(blk[i][q], x[q]));
+      x[i] = (i < w && lane < w) ? cmul(v, cinv(blk[i][i])) : make_float2(0.f, 0.f);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < kNB; ++i) out[i * kNB + lane] = x[i];
+}
+
 // Bin k: (mu_k I - A~) z = z1_k / lambda2_k with the LU factors; in place on the half spectrum.
-__global__ void __launch_bounds__(256) k_rz_trsv(float2* __restrict__ spec, int nx, int pitch,
-                                                 const float2* __restrict__ LU, const float2* __restrict__ il2) {
+// Blocked substitution: for each kNB-row block, the rows' products with the solved part of z
+// (warps over rows, lanes over columns, four loads in flight per lane), then the block itself by
+// its stored inverse (one product instead of kNB dependent steps).
+__global__ void __launch_bounds__(512) k_rz_trsv(float2* __restrict__ spec, int nx, int pitch,
+                                                 const float2* __restrict__ LU, const float2* __restrict__ dinv,
+                                                 const float2* __restrict__ il2) {
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* z = reinterpret_cast<float2*>(smraw);  // nx
-  float2* acc = z + nx;                          // kNB
+  float2* t = z + nx;                            // kNB
   const int k = blockIdx.x;
   const float2* A = LU + (size_t)k * nx * nx;
   float2* row = spec + (size_t)k * pitch;
@@ -262,77 +304,67 @@ __global__ void __launch_bounds__(256) k_rz_trsv(float2* __restrict__ spec, int 
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int nb = (nx + kNB - 1) / kNB;
-  // forward: L y = z (unit lower)
-  for (int bi = 0; bi < nb; ++bi) {
-    const int r0 = bi * kNB, r1 = min(nx, r0 + kNB);
-    for (int i = r0 + warp; i < r1; i += nw) {
-      const float2* ri = A + (size_t)i * nx;
-      float sx = 0.f, sy = 0.f;
-      for (int j = lane; j < r0; j += 32) {
-        const float2 l = __ldg(ri + j), v = z[j];
-        sx = fmaf(l.x, v.x, fmaf(-l.y, v.y, sx));
-        sy = fmaf(l.x, v.y, fmaf(l.y, v.x, sy));
-      }
+  auto rowdot = [&](const float2* ri, int j0, int j1) {
+    float ax = 0.f, ay = 0.f, bx = 0.f, by = 0.f;
+    int j = j0 + lane;
+    for (; j + 96 < j1; j += 128) {
+      const float2 l0 = __ldg(ri + j), l1 = __ldg(ri + j + 32), l2 = __ldg(ri + j + 64), l3 = __ldg(ri + j + 96);
+      const float2 v0 = z[j], v1 = z[j + 32], v2 = z[j + 64], v3 = z[j + 96];
+      ax = fmaf(l0.x, v0.x, fmaf(-l0.y, v0.y, ax));
+      ay = fmaf(l0.x, v0.y, fmaf(l0.y, v0.x, ay));
+      bx = fmaf(l1.x, v1.x, fmaf(-l1.y, v1.y, bx));
+      by = fmaf(l1.x, v1.y, fmaf(l1.y, v1.x, by));
+      ax = fmaf(l2.x, v2.x, fmaf(-l2.y, v2.y, ax));
+      ay = fmaf(l2.x, v2.y, fmaf(l2.y, v2.x, ay));
+      bx = fmaf(l3.x, v3.x, fmaf(-l3.y, v3.y, bx));
+      by = fmaf(l3.x, v3.y, fmaf(l3.y, v3.x, by));
+    }
+    for (; j < j1; j += 32) {
+      const float2 l = __ldg(ri + j), v = z[j];
+      ax = fmaf(l.x, v.x, fmaf(-l.y, v.y, ax));
+      ay = fmaf(l.x, v.y, fmaf(l.y, v.x, ay));
+    }
+    float sx = ax + bx, sy = ay + by;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      sx += __shfl_down_sync(0xffffffffu, sx, o);
+      sy += __shfl_down_sync(0xffffffffu, sy, o);
+    }
+    return make_float2(sx, sy);
+  };
+  // z_b <- Inv t over the block's w rows (warps over rows, lanes over columns)
+  auto apply_inv = [&](const float2* inv, int r0, int w) {
+    for (int i = warp; i < w; i += nw) {
+      const float2 p = lane < w ? cmul(__ldg(inv + i * kNB + lane), t[lane]) : make_float2(0.f, 0.f);
+      float px = p.x, py = p.y;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        sx += __shfl_down_sync(0xffffffffu, sx, o);
-        sy += __shfl_down_sync(0xffffffffu, sy, o);
+        px += __shfl_down_sync(0xffffffffu, px, o);
+        py += __shfl_down_sync(0xffffffffu, py, o);
       }
-      if (lane == 0) acc[i - r0] = make_float2(sx, sy);
+      if (lane == 0) z[r0 + i] = make_float2(px, py);
+    }
+  };
+  // forward: L y = z (unit lower)
+  for (int bi = 0; bi < nb; ++bi) {
+    const int r0 = bi * kNB, w = min(kNB, nx - r0);
+    for (int i = warp; i < w; i += nw) {
+      const float2 d = rowdot(A + (size_t)(r0 + i) * nx, 0, r0);
+      if (lane == 0) t[i] = csub(z[r0 + i], d);
     }
     __syncthreads();
-    if (warp == 0) {
-      // the diagonal block: lane j holds z_j of the block; row by row
-      const int w = r1 - r0;
-      float2 zj = lane < w ? csub(z[r0 + lane], acc[lane]) : make_float2(0.f, 0.f);
-      for (int i = 1; i < w; ++i) {
-        const float2 l = lane < i ? __ldg(A + (size_t)(r0 + i) * nx + r0 + lane) : make_float2(0.f, 0.f);
-        const float2 p = cmul(l, zj);
-        float px = p.x, py = p.y;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          px += __shfl_xor_sync(0xffffffffu, px, o);
-          py += __shfl_xor_sync(0xffffffffu, py, o);
-        }
-        if (lane == i) zj = make_float2(zj.x - px, zj.y - py);
-      }
-      if (lane < w) z[r0 + lane] = zj;
-    }
+    apply_inv(dinv + (((size_t)k * nb + bi) * 2 + 0) * kNB * kNB, r0, w);
     __syncthreads();
   }
   // backward: U x = y
   for (int bi = nb - 1; bi >= 0; --bi) {
-    const int r0 = bi * kNB, r1 = min(nx, r0 + kNB);
-    for (int i = r0 + warp; i < r1; i += nw) {
-      const float2* ri = A + (size_t)i * nx;
-      float sx = 0.f, sy = 0.f;
-      for (int j = r1 + lane; j < nx; j += 32) {
-        const float2 u = __ldg(ri + j), v = z[j];
-        sx = fmaf(u.x, v.x, fmaf(-u.y, v.y, sx));
-        sy = fmaf(u.x, v.y, fmaf(u.y, v.x, sy));
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        sx += __shfl_down_sync(0xffffffffu, sx, o);
-        sy += __shfl_down_sync(0xffffffffu, sy, o);
-      }
-      if (lane == 0) acc[i - r0] = make_float2(sx, sy);
+    const int r0 = bi * kNB, w = min(kNB, nx - r0);
+    for (int i = warp; i < w; i += nw) {
+      const float2 d = rowdot(A + (size_t)(r0 + i) * nx, r0 + w, nx);
+      if (lane == 0) t[i] = csub(z[r0 + i], d);
     }
     __syncthreads();
-    if (warp == 0) {
-      const int w = r1 - r0;
-      float2 zj = lane < w ? csub(z[r0 + lane], acc[lane]) : make_float2(0.f, 0.f);
-      const float2 dj = lane < w ? __ldg(A + (size_t)(r0 + lane) * nx + r0 + lane) : make_float2(1.f, 0.f);
-      for (int i = w - 1; i >= 0; --i) {
-        if (lane == i) zj = cmul(zj, cinv(dj));
-        const float2 xi = make_float2(__shfl_sync(0xffffffffu, zj.x, i), __shfl_sync(0xffffffffu, zj.y, i));
-        if (lane < i) {
-          const float2 u = __ldg(A + (size_t)(r0 + lane) * nx + r0 + i);
-          zj = csub(zj, cmul(u, xi));
-        }
-      }
-      if (lane < w) z[r0 + lane] = zj;
-    }
+    apply_inv(dinv + (((size_t)k * nb + bi) * 2 + 1) * kNB * kNB, r0, w);
     __syncthreads();
   }
   for (int i = threadIdx.x; i < nx; i += blockDim.x) row[i] = z[i];
@@ -442,6 +474,12 @@ int riesz_build(Handle& h) {
       AAO_CHECK_LAUNCH();
     }
   }
+  {
+    const int nb = (nx + kNB - 1) / kNB;
+    AAO_TRY_CUDA(cudaMalloc(&h.rz_dinv, sizeof(float2) * (size_t)K * nb * 2 * kNB * kNB));
+    k_rz_diaginv<<<dim3(nb, K), 64, 0, h.stream>>>(h.rz_lu, h.rz_dinv, nx, nb);
+    AAO_CHECK_LAUNCH();
+  }
   AAO_TRY_CUDA(cudaStreamSynchronize(h.stream));
   cudaFree(d_tcol);
   cudaFree(d_trow);
@@ -515,7 +553,7 @@ int riesz_solve_bins(Handle& h, void* spec) {
   const size_t smem = sizeof(float2) * ((size_t)h.nx + kNB);
   const double bytes = (double)h.K * ((double)h.nx * h.nx * 8.0 + 2.0 * h.nx * 8.0);
   ProfScope ps(AAO_K_TRIDIAG, h.stream, bytes);
-  k_rz_trsv<<<h.K, 256, smem, h.stream>>>((float2*)spec, h.nx, h.pitch, h.rz_lu, h.il2f);
+  k_rz_trsv<<<h.K, 512, smem, h.stream>>>((float2*)spec, h.nx, h.pitch, h.rz_lu, h.rz_dinv, h.il2f);
   AAO_CHECK_LAUNCH();
   return AAO_OK;
 }
