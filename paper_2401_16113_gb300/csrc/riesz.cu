@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(64) k_rz_diaginv(const float2* __restrict__ LU
 
 // Bin k: (mu_k I - A~) z = z1_k / lambda2_k with the LU factors; in place on the half spectrum.
 // Blocked substitution: for each kNB-row block, the rows' products with the solved part of z
-// (warps over rows, lanes over columns, four loads in flight per lane), then the block itself by
+// (warps over rows, lanes over columns, eight loads in flight per lane), then the block itself by
 // its stored inverse (one product instead of kNB dependent steps).
 __global__ void __launch_bounds__(512) k_rz_trsv(float2* __restrict__ spec, int nx, int pitch,
                                                  const float2* __restrict__ LU, const float2* __restrict__ dinv,
@@ -307,17 +307,19 @@ __global__ void __launch_bounds__(512) k_rz_trsv(float2* __restrict__ spec, int 
   auto rowdot = [&](const float2* ri, int j0, int j1) {
     float ax = 0.f, ay = 0.f, bx = 0.f, by = 0.f;
     int j = j0 + lane;
-    for (; j + 96 < j1; j += 128) {
-      const float2 l0 = __ldg(ri + j), l1 = __ldg(ri + j + 32), l2 = __ldg(ri + j + 64), l3 = __ldg(ri + j + 96);
-      const float2 v0 = z[j], v1 = z[j + 32], v2 = z[j + 64], v3 = z[j + 96];
-      ax = fmaf(l0.x, v0.x, fmaf(-l0.y, v0.y, ax));
-      ay = fmaf(l0.x, v0.y, fmaf(l0.y, v0.x, ay));
-      bx = fmaf(l1.x, v1.x, fmaf(-l1.y, v1.y, bx));
-      by = fmaf(l1.x, v1.y, fmaf(l1.y, v1.x, by));
-      ax = fmaf(l2.x, v2.x, fmaf(-l2.y, v2.y, ax));
-      ay = fmaf(l2.x, v2.y, fmaf(l2.y, v2.x, ay));
-      bx = fmaf(l3.x, v3.x, fmaf(-l3.y, v3.y, bx));
-      by = fmaf(l3.x, v3.y, fmaf(l3.y, v3.x, by));
+    for (; j + 224 < j1; j += 256) {
+      float2 l[8], v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) l[u] = __ldg(ri + j + 32 * u);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = z[j + 32 * u];
+#pragma unroll
+      for (int u = 0; u < 8; u += 2) {
+        ax = fmaf(l[u].x, v[u].x, fmaf(-l[u].y, v[u].y, ax));
+        ay = fmaf(l[u].x, v[u].y, fmaf(l[u].y, v[u].x, ay));
+        bx = fmaf(l[u + 1].x, v[u + 1].x, fmaf(-l[u + 1].y, v[u + 1].y, bx));
+        by = fmaf(l[u + 1].x, v[u + 1].y, fmaf(l[u + 1].y, v[u + 1].x, by));
+      }
     }
     for (; j < j1; j += 32) {
       const float2 l = __ldg(ri + j), v = z[j];
