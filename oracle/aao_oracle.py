@@ -309,6 +309,20 @@ def dense_P(p, alpha=None):
     return np.kron(C1, np.eye(nx)) - np.kron(C2, tau * _dense(mean_operator(p)))
 
 
+def apply_P(p, z, alpha=None):
+    """P_alpha z = (C1 (x) I_s - C2 (x) A~) z (Eq. 3.1) without forming P: C1 and C2 act along time
+    as B1 and B2 (z_t - z_{t-1}, (z_t + z_{t-1})/2) with the alpha corner at t = 0 (Sec. 3.1),
+    A~ = tau A-bar along space. Any size."""
+    alpha = p["alpha"] if alpha is None else alpha
+    nt, nx = int(p["nt"]), int(p["nx"])
+    _, tau = time_grid(p)
+    Z = np.asarray(z, dtype=np.float64).reshape(nt, nx)
+    prev = np.roll(Z, 1, axis=0)  # z_{t-1}; row 0 holds z_{nt-1}
+    prev[0] = alpha * prev[0]
+    At = tau * mean_operator(p)
+    return ((Z - prev) - (At @ (0.5 * (Z + prev)).T).T).reshape(-1)
+
+
 def dense_M(p):
     return assemble_M(p).toarray()
 

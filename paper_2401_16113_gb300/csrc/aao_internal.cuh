@@ -19,6 +19,7 @@ extern std::atomic<uint64_t> g_launches;
   do {                                                                                  \
     cudaError_t e_ = (expr);                                                            \
     if (e_ != cudaSuccess) {                                                            \
+      (void)cudaGetLastError(); /* clear a non-sticky error so later calls do not see it */ \
       ::aao::set_error(std::string(#expr) + ": " + cudaGetErrorString(e_));             \
       return e_ == cudaErrorMemoryAllocation ? AAO_ENOMEM : AAO_ECUDA;                  \
     }                                                                                   \

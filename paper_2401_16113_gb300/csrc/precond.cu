@@ -76,22 +76,32 @@ int run_precond(Handle& h, const double* v, void* z, bool z_is_float, const doub
   if (h.p.op == AAO_OP_RIESZ) {
     // step (b) with the dense Toeplitz operator: LU factors from aao_create
     AAO_TRY(riesz_solve_bins(h, spec));
-  } else if (h.tri && tri_part_bytes(1, h.tri_T, (h.tri_ch & 1) ? h.tri_ch + 2 : h.tri_ch + 1, sizeof(R)) <= kTriSmemMax) {
+  } else if (h.tri && tri_part_bytes(1, h.tri_T, (h.tri_ch & 1) ? h.tri_ch + 2 : h.tri_ch + 1, sizeof(R), false) <=
+                          kTriSmemMax) {
     // step (b): partition method, G bins of tri_T = 2^lgT threads per CTA (as many as shared
-    // memory holds, at most 512 threads)
+    // memory holds, at most 512 threads); the coefficients are staged in shared memory when
+    // they fit beside one bin, else read from global memory
     const int T = h.tri_T, ch = h.tri_ch;
     int lgT = 0;
     while ((1 << lgT) < T) ++lgT;
     const int cs = (ch & 1) ? ch + 2 : ch + 1;  // odd chunk stride: conflict-free shared memory
+    const bool staged = tri_part_bytes(1, T, cs, sizeof(R), true) <= kTriSmemMax;
     int G = 512 / T;
-    while (G > 1 && tri_part_bytes(G, T, cs, sizeof(R)) > kTriSmemMax) --G;
-    const size_t smem2 = tri_part_bytes(G, T, cs, sizeof(R));
+    while (G > 1 && tri_part_bytes(G, T, cs, sizeof(R), staged) > kTriSmemMax) --G;
+    const size_t smem2 = tri_part_bytes(G, T, cs, sizeof(R), staged);
     const C* mu = (sizeof(R) == 4) ? (const C*)h.muf : (const C*)h.mu;
     const C* il2 = (sizeof(R) == 4) ? (const C*)h.il2f : (const C*)h.il2;
-    AAO_TRY_CUDA(cudaFuncSetAttribute(k_tridiag_part<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
+    const R* tri = reinterpret_cast<const R*>(h.tri);
     ProfScope ps(AAO_K_TRIDIAG, h.stream, 2.0 * nsp);
-    k_tridiag_part<R><<<(h.K + G - 1) / G, G * T, smem2, h.stream>>>(spec, nx, h.K, h.pitch, ch, cs, lgT,
-                                                                     reinterpret_cast<const R*>(h.tri), mu, il2);
+    if (staged) {
+      AAO_TRY_CUDA(cudaFuncSetAttribute(k_tridiag_part<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
+      k_tridiag_part<R, true><<<(h.K + G - 1) / G, G * T, smem2, h.stream>>>(spec, nx, h.K, h.pitch, ch, cs, lgT, tri,
+                                                                             mu, il2);
+    } else {
+      AAO_TRY_CUDA(cudaFuncSetAttribute(k_tridiag_part<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
+      k_tridiag_part<R, false><<<(h.K + G - 1) / G, G * T, smem2, h.stream>>>(spec, nx, h.K, h.pitch, ch, cs, lgT,
+                                                                              tri, mu, il2);
+    }
   } else {
   // step (b): threads per bin T (multiple of 32, <= 512), chunk ch <= CH rows per thread
   constexpr int CH = sizeof(R) == 4 ? 16 : 8;

@@ -673,9 +673,11 @@ __global__ void __launch_bounds__(512) k_tridiag(C_t<R>* __restrict__ spec, int 
 // flight at once; the coefficients are shared by the CTA's G bins. The 1/lambda_2 scaling of the
 // right-hand side is applied to the solution (the system is linear).
 __host__ __device__ __forceinline__ size_t tri_part_bin_elems(int T, int cs) { return 3 * (size_t)T * cs + 4 * (size_t)T; }
-__host__ __device__ __forceinline__ size_t tri_part_bytes(int G, int T, int cs, size_t rsize) {
-  const size_t coef = ((3 * (size_t)T * cs * rsize) + 15) & ~(size_t)15;
-  return coef + (size_t)G * tri_part_bin_elems(T, cs) * 2 * rsize;
+__host__ __device__ __forceinline__ size_t tri_part_coef_bytes(int T, int cs, size_t rsize, bool staged) {
+  return staged ? (((3 * (size_t)T * cs * rsize) + 15) & ~(size_t)15) : 0;
+}
+__host__ __device__ __forceinline__ size_t tri_part_bytes(int G, int T, int cs, size_t rsize, bool staged = true) {
+  return tri_part_coef_bytes(T, cs, rsize, staged) + (size_t)G * tri_part_bin_elems(T, cs) * 2 * rsize;
 }
 
 template <typename R>
@@ -700,7 +702,9 @@ __device__ __forceinline__ void cp_async(void* smem_dst, const void* gmem_src) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-template <typename R>
+// STAGED = false (large Nx, where the coefficients do not fit beside the bin's rows): the downward
+// sweep reads the chunk-transposed coefficient table from global memory, one row ahead.
+template <typename R, bool STAGED>
 __global__ void __launch_bounds__(512) k_tridiag_part(C_t<R>* __restrict__ spec, int nx, int K, int pitch, int ch,
                                                       int cs, int lgT, const R* __restrict__ tri,
                                                       const C_t<R>* __restrict__ mu, const C_t<R>* __restrict__ il2) {
@@ -713,7 +717,7 @@ __global__ void __launch_bounds__(512) k_tridiag_part(C_t<R>* __restrict__ spec,
   R* sa = reinterpret_cast<R*>(smraw);  // staged coefficients, layout l*cs + j
   R* sdg = sa + (size_t)T * cs;
   R* sc = sdg + (size_t)T * cs;
-  const size_t coef = ((3 * (size_t)T * cs * sizeof(R)) + 15) & ~(size_t)15;
+  const size_t coef = tri_part_coef_bytes(T, cs, sizeof(R), STAGED);
   C* sd = reinterpret_cast<C*>(smraw + coef) + (size_t)g * tri_part_bin_elems(T, cs);  // rhs -> d' -> x
   C* scp = sd + (size_t)T * cs;  // c'
   C* sv = scp + (size_t)T * cs;  // v
@@ -726,10 +730,12 @@ __global__ void __launch_bounds__(512) k_tridiag_part(C_t<R>* __restrict__ spec,
 
   // staging: coefficients by the whole CTA (table row j = chunk row j of every thread), right-
   // hand side by the bin's threads (element i = L ch + j)
-  for (int e = threadIdx.x; e < 3 * ch * T; e += blockDim.x) {
-    const int jq = e >> lgT, L = e & (T - 1);  // jq = q ch + j
-    const int q = jq >= 2 * ch ? 2 : (jq >= ch ? 1 : 0), j = jq - q * ch;
-    cp_async<sizeof(R)>(sa + (size_t)q * T * cs + L * cs + j, tri + e);
+  if constexpr (STAGED) {
+    for (int e = threadIdx.x; e < 3 * ch * T; e += blockDim.x) {
+      const int jq = e >> lgT, L = e & (T - 1);  // jq = q ch + j
+      const int q = jq >= 2 * ch ? 2 : (jq >= ch ? 1 : 0), j = jq - q * ch;
+      cp_async<sizeof(R)>(sa + (size_t)q * T * cs + L * cs + j, tri + e);
+    }
   }
   const int dL = T / ch, dj = T - dL * ch;  // i += T moves (L, j) by (dL, dj), dj < ch
   for (int L = l / ch, j = l - (l / ch) * ch; L < T;) {
@@ -753,9 +759,25 @@ __global__ void __launch_bounds__(512) k_tridiag_part(C_t<R>* __restrict__ spec,
   // (1) downward elimination
   C cpr = zero, dpr = zero, vpr = one;
   const int nrow = nx - l * ch;  // rows j >= nrow are identity rows
+  const size_t plane = (size_t)T * ch;
+  auto coef_row = [&](int j, R& a, R& dg, R& c) {
+    if constexpr (STAGED) {
+      a = A[j];
+      dg = DG[j];
+      c = CC[j];
+    } else {
+      const size_t o = (size_t)j * T + l;
+      a = __ldg(tri + o);
+      dg = __ldg(tri + plane + o);
+      c = __ldg(tri + 2 * plane + o);
+    }
+  };
+  R an, dgn, cn;
+  coef_row(0, an, dgn, cn);
   for (int j = 0; j < ch; ++j) {
-    const R a = A[j], c = CC[j];
-    const C b = j < nrow ? cmk<C>(muk.x - DG[j], muk.y) : one;
+    const R a = an, c = cn, dgj = dgn;
+    if (j + 1 < ch) coef_row(j + 1, an, dgn, cn);
+    const C b = j < nrow ? cmk<C>(muk.x - dgj, muk.y) : one;
     const C inv = crcp<R>(cmk<C>(b.x - a * cpr.x, b.y - a * cpr.y));
     const C dj = D[j];
     cpr = cscale(inv, c);

@@ -133,6 +133,33 @@ def test_precond_full_size_localvol(aao, precision):
     assert rel(host(z), ref) <= precond_bound(p)
 
 
+# Every radix plan of the register FFT (nt = 2^7 .. 2^13: 16|8, 16|2|8, 16|4|8, 16|8|8, 16|16|8,
+# 16|16|2|8, 16|16|4|8) and every configuration of the partitioned tridiagonal solve (32 .. 512
+# threads per bin, coefficients staged in shared memory or read from global memory).
+# The check is the backward error ||v - P_alpha z|| / ||v|| (P_alpha applied by the oracle in
+# FP64), bounded like the forward error above: an FP32 solve's backward error does not depend on
+# the conditioning of the shifted systems. Their forward error does (mu_0 I - tau A-bar reaches a
+# condition number ~1e5 for Nx = 8191, Nt = 128), so it is checked only where Nx <= 2047.
+PLAN_SHAPES = [(1023, 512, "fp64"), (1023, 512, "mixed"), (1500, 1024, "mixed"), (700, 4096, "fp64"),
+               (700, 4096, "mixed"), (300, 8192, "mixed"), (4095, 256, "fp64"), (4095, 256, "mixed"),
+               (5000, 128, "mixed"), (8191, 128, "mixed")]
+
+
+@pytest.mark.parametrize("nx,nt,precision", PLAN_SHAPES)
+def test_precond_fft_plans_and_solver_sizes(aao, nx, nt, precision):
+    p = W.with_(LV, nx=nx, nt=nt, precision=precision)
+    h = aao.aao_create(p)
+    v = W.random_vector(nx * nt, seed=5 * nx + nt)
+    z = torch.empty(nx * nt, dtype=torch.float64, device="cuda")
+    aao.precond_apply(h, dev(v), z)
+    zh = host(z)
+    back = rel(O.apply_P(p, zh), v)
+    assert back <= precond_bound(p), back
+    if nx <= 2047:
+        assert rel(zh, O.precond_fft(p, v)) <= precond_bound(p)
+    h.close()
+
+
 def test_fgmres_fp64_bs_put(aao):
     """Plain FP64 solve of the 255 x 256 put to 1e-10: equals sequential CN and the
     closed form within the discretisation error."""

@@ -378,3 +378,22 @@ def test_block_matvec_equals_assembled_M():
     for p in (W.with_(RZ, nx=17, nt=12), W.with_(BS, nx=13, nt=9)):
         x = W.random_vector(p["nx"] * p["nt"], seed=2)
         assert np.allclose(O.matvec_blocks(p, x), O.matvec(p, x), rtol=1e-13, atol=1e-13)
+
+
+def test_apply_P_equals_dense_P():
+    """The blockwise P_alpha product equals the dense Kronecker form of Eq. 3.1, including the
+    alpha corner and Nt = 1, 2."""
+    rng = np.random.default_rng(3)
+    for nx, nt in [(5, 1), (6, 2), (7, 8), (4, 12)]:
+        for p in (W.with_(W.bs_put_255x256(), nx=nx, nt=nt), W.with_(W.localvol_2047x2048("fp64"), nx=nx, nt=nt)):
+            z = rng.standard_normal(nx * nt)
+            assert np.allclose(O.apply_P(p, z), O.dense_P(p) @ z, rtol=1e-13, atol=1e-13)
+
+
+def test_apply_P_inverts_precond_fft():
+    """P_alpha (P_alpha^{-1} v) = v for the FFT apply of Eq. 3.2 at a size the dense form cannot
+    reach."""
+    p = W.with_(W.localvol_2047x2048("fp64"), nx=200, nt=64)
+    v = W.random_vector(200 * 64, seed=4)
+    r = O.apply_P(p, O.precond_fft(p, v)) - v
+    assert np.linalg.norm(r) <= 1e-11 * np.linalg.norm(v)
