@@ -156,6 +156,7 @@ struct Handle {
   int rz_n2 = 0, rz_log2n2 = 0;
   double2 *rz_chat = nullptr, *rz_tw = nullptr;
   double *rz_hcol = nullptr, *rz_hrow = nullptr, *rz_hcl = nullptr;
+  float* Vf = nullptr;  // FP32 copy of the basis vector the next preconditioner apply reads (mixed)
   float2* rz_lu = nullptr;
   float2* rz_dinv = nullptr;  // inverses of the factors' diagonal blocks (L, U per block and bin)
 
@@ -174,14 +175,17 @@ struct Handle {
 
 // launchers (return AAO_* codes)
 int build_tables(Handle& h);
-int launch_precond(Handle& h, const double* v, void* z, bool z_is_float, const double* in_scale = nullptr);
+// vf (mixed precision only): an FP32 copy of v, read instead of v by the first kernel
+int launch_precond(Handle& h, const double* v, void* z, bool z_is_float, const double* in_scale = nullptr,
+                   const float* vf = nullptr);
 int tune_precond(Handle& h);
 int riesz_build(Handle& h);
 int riesz_matvec(Handle& h, const void* x, bool x_is_float, double* y, const double* b, const double* V, int nd, int m);
 int riesz_rhs(Handle& h, double* b);
 int riesz_solve_bins(Handle& h, void* spec);
+// yf (residual modes, mixed precision): also write an FP32 copy of y
 int launch_matvec(Handle& h, const void* x, bool x_is_float, double* y, const double* b, const double* V = nullptr,
-                  int nd = 0, int m = 0, bool with_bnorm = false);
+                  int nd = 0, int m = 0, bool with_bnorm = false, float* yf = nullptr);
 int launch_rhs(Handle& h, double* b);
 int run_fgmres(Handle& h, const double* b, double* x, double tol, int m, int maxit, aao_stats* st);
 void free_handle(Handle& h);

@@ -108,7 +108,8 @@ __global__ void __launch_bounds__(kThreads) k_matvec(const IN* __restrict__ x, d
                                                      const double* __restrict__ U, int rows,
                                                      const double* __restrict__ V, size_t vstride,
                                                      double* __restrict__ part, double* __restrict__ scal,
-                                                     unsigned int* __restrict__ counter, int m) {
+                                                     unsigned int* __restrict__ counter, int m,
+                                                     float* __restrict__ yf) {
   constexpr int NA = MODE == 2 ? ND + 1 : (MODE == 3 ? 2 : 1);
   constexpr int nd = ND;
   // one wave of blocks: the (strip, time level) rows, strip-major, are split into one contiguous
@@ -127,7 +128,7 @@ __global__ void __launch_bounds__(kThreads) k_matvec(const IN* __restrict__ x, d
     const int strip = (int)(r / nt);
     const int t0 = (int)(r - (long long)strip * nt);
     const int t1 = (int)((long long)t0 + (r1 - r) < (long long)nt ? (long long)t0 + (r1 - r) : (long long)nt);
-    matvec_item<IN, MODE, ND, NA>(x, y, b, nx, t0, t1, strip * kMvCols, L, D, U, rows, V, vstride, acc);
+    matvec_item<IN, MODE, ND, NA>(x, y, b, nx, t0, t1, strip * kMvCols, L, D, U, rows, V, vstride, acc, yf);
     r += t1 - t0;
   }
   if constexpr (MODE == 0) return;
@@ -184,7 +185,8 @@ __global__ void __launch_bounds__(kThreads) k_mdot(const double* __restrict__ V,
 template <int NV>
 __global__ void __launch_bounds__(kThreads) k_update(double* __restrict__ w, const double* __restrict__ V,
                                                      int j, size_t n, int pass, double* __restrict__ scal,
-                                                     double* __restrict__ part, unsigned int* __restrict__ counter) {
+                                                     double* __restrict__ part, unsigned int* __restrict__ counter,
+                                                     float* __restrict__ vf) {
   __shared__ double cf[128];
   const int nv = j + 1;
   const int off = pass == 1 ? S_D1 : S_D2;
@@ -212,6 +214,10 @@ __global__ void __launch_bounds__(kThreads) k_update(double* __restrict__ w, con
       }
       w[e] = wa;
       w[e + stride] = wb;
+      if (vf) {
+        vf[e] = narrow(wa);
+        vf[e + stride] = narrow(wb);
+      }
       acc[0] = fma(wa, wa, acc[0]);
       acc[0] = fma(wb, wb, acc[0]);
     }
@@ -225,6 +231,7 @@ __global__ void __launch_bounds__(kThreads) k_update(double* __restrict__ w, con
       for (int q = 0; q < nv; ++q) wv = fma(-cf[q], __ldg(V + (size_t)q * n + e), wv);
     }
     w[e] = wv;
+    if (vf) vf[e] = narrow(wv);
     acc[0] = fma(wv, wv, acc[0]);
   }
   block_sums_wide<1>(acc, 1, part + (size_t)blockIdx.x * kPartLd);
@@ -330,9 +337,11 @@ int ensure_workspace(Handle& h, int m) {
   if (h.ws_m >= m && h.V) return AAO_OK;
   if (h.V) cudaFree(h.V);
   if (h.Z) cudaFree(h.Z);
-  h.V = nullptr; h.Z = nullptr; h.ws_m = 0;
+  if (h.Vf) cudaFree(h.Vf);
+  h.V = nullptr; h.Z = nullptr; h.Vf = nullptr; h.ws_m = 0;
   AAO_TRY_CUDA(cudaMalloc(&h.V, sizeof(double) * h.n * (size_t)(m + 1)));
   AAO_TRY_CUDA(cudaMalloc(&h.Z, (h.mixed ? sizeof(float) : sizeof(double)) * h.n * (size_t)m));
+  if (h.mixed) AAO_TRY_CUDA(cudaMalloc(&h.Vf, sizeof(float) * h.n));
   h.ws_m = m;
   return AAO_OK;
 }
@@ -505,7 +514,7 @@ int build_tables(Handle& h) {
 void free_handle(Handle& h) {
   void* bufs[] = {h.mL, h.mD, h.mU, h.gL, h.gR, h.pL, h.pD, h.pU, h.pLf, h.pDf, h.pUf, h.mu, h.il2, h.tw,
                   h.muf, h.il2f, h.twf, h.lam, h.ilam, h.lamf, h.ilamf, h.spec, h.V, h.Z, h.w, h.scal, h.part,
-                  h.counter, h.rz_chat, h.rz_tw, h.rz_hcol, h.rz_hrow, h.rz_hcl, h.rz_lu, h.rz_dinv, h.tri};
+                  h.counter, h.rz_chat, h.rz_tw, h.rz_hcol, h.rz_hrow, h.rz_hcl, h.rz_lu, h.rz_dinv, h.tri, h.Vf};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (h.host_scal) cudaFreeHost(h.host_scal);
@@ -520,13 +529,13 @@ namespace {
 // time-chunk length: enough blocks to fill the GPU, at most kPartBlocks partial sums
 template <typename IN>
 int matvec_t(Handle& h, const IN* x, double* y, const double* b, const double* V, int nd, int m, double bytes,
-             double flops, bool with_bnorm) {
+             double flops, bool with_bnorm, float* yf) {
   const size_t rowsw = (size_t)((h.nx + kMvCols - 1) / kMvCols) * h.nt;  // warp rows
   const size_t need = (rowsw + kThreads / 32 - 1) / (kThreads / 32);
   ProfScope ps(AAO_K_MATVEC, h.stream, bytes, flops);
 #define AAO_MV2(ND)                                                                                              \
   k_matvec<IN, 2, ND><<<wave_blocks(h, (const void*)k_matvec<IN, 2, ND>, need), kThreads, 0, h.stream>>>(        \
-      x, y, nullptr, h.nx, h.nt, h.mL, h.mD, h.mU, h.coef_rows, V, h.n, h.part, h.scal, h.counter, m)
+      x, y, nullptr, h.nx, h.nt, h.mL, h.mD, h.mU, h.coef_rows, V, h.n, h.part, h.scal, h.counter, m, nullptr)
   if (V && nd > 0) {
     switch (nd) {
       case 1: AAO_MV2(1); break;
@@ -540,13 +549,14 @@ int matvec_t(Handle& h, const IN* x, double* y, const double* b, const double* V
     }
   } else if (b && with_bnorm) {
     k_matvec<IN, 3, 0><<<wave_blocks(h, (const void*)k_matvec<IN, 3, 0>, need), kThreads, 0, h.stream>>>(
-        x, y, b, h.nx, h.nt, h.mL, h.mD, h.mU, h.coef_rows, nullptr, h.n, h.part, h.scal, h.counter, m);
+        x, y, b, h.nx, h.nt, h.mL, h.mD, h.mU, h.coef_rows, nullptr, h.n, h.part, h.scal, h.counter, m, yf);
   } else if (b) {
     k_matvec<IN, 1, 0><<<wave_blocks(h, (const void*)k_matvec<IN, 1, 0>, need), kThreads, 0, h.stream>>>(
-        x, y, b, h.nx, h.nt, h.mL, h.mD, h.mU, h.coef_rows, nullptr, h.n, h.part, h.scal, h.counter, m);
+        x, y, b, h.nx, h.nt, h.mL, h.mD, h.mU, h.coef_rows, nullptr, h.n, h.part, h.scal, h.counter, m, yf);
   } else {
     k_matvec<IN, 0, 0><<<wave_blocks(h, (const void*)k_matvec<IN, 0, 0>, need), kThreads, 0, h.stream>>>(
-        x, y, nullptr, h.nx, h.nt, h.mL, h.mD, h.mU, h.coef_rows, nullptr, h.n, h.part, h.scal, h.counter, m);
+        x, y, nullptr, h.nx, h.nt, h.mL, h.mD, h.mU, h.coef_rows, nullptr, h.n, h.part, h.scal, h.counter, m,
+        nullptr);
   }
 #undef AAO_MV2
   AAO_CHECK_LAUNCH();
@@ -557,7 +567,7 @@ int matvec_t(Handle& h, const IN* x, double* y, const double* b, const double* V
 
 // y = M x; with b: y = b - M x (restart residual); with V (nd <= 8): first Gram-Schmidt pass
 int launch_matvec(Handle& h, const void* x, bool x_is_float, double* y, const double* b, const double* V, int nd,
-                  int m, bool with_bnorm) {
+                  int m, bool with_bnorm, float* yf) {
   if (h.p.op == AAO_OP_RIESZ) {
     if (b && with_bnorm) {
       ProfScope ps(AAO_K_OTHER, h.stream, 8.0 * (double)h.n);
@@ -574,8 +584,8 @@ int launch_matvec(Handle& h, const void* x, bool x_is_float, double* y, const do
   // per unknown: s and d (2 adds), three FMAs; residual: b - (1) and r.r (FMA), b.b (FMA);
   // projections: nd FMAs and y.y (FMA)
   const double flops = nn * (2.0 + 6.0 + (b ? 3.0 : 0.0) + (b && with_bnorm ? 2.0 : 0.0) + (V ? 2.0 * (nd + 1) : 0.0));
-  if (x_is_float) return matvec_t<float>(h, (const float*)x, y, b, V, nd, m, bytes, flops, with_bnorm);
-  return matvec_t<double>(h, (const double*)x, y, b, V, nd, m, bytes, flops, with_bnorm);
+  if (x_is_float) return matvec_t<float>(h, (const float*)x, y, b, V, nd, m, bytes, flops, with_bnorm, yf);
+  return matvec_t<double>(h, (const double*)x, y, b, V, nd, m, bytes, flops, with_bnorm, yf);
 }
 
 void launch_rhs_raw(cudaStream_t s, double* b, int nx, int nt, const double* L, const double* D, const double* U,
@@ -641,12 +651,12 @@ int projections(Handle& h, const double* w, int nv, int slot) {
   return AAO_OK;
 }
 
-int update(Handle& h, double* w, int j, int pass) {
+int update(Handle& h, double* w, int j, int pass, float* vf) {
   const size_t n = h.n;
   const int g = grid_for(n);
   const int nv = j + 1;
   ProfScope ps(AAO_K_ARNOLDI, h.stream, 8.0 * (double)n * (nv + 2), 2.0 * (double)n * (nv + 1));
-#define AAO_UP(NV) k_update<NV><<<wave_blocks(h, (const void*)k_update<NV>, g), kThreads, 0, h.stream>>>(w, h.V, j, n, pass, h.scal, h.part, h.counter)
+#define AAO_UP(NV) k_update<NV><<<wave_blocks(h, (const void*)k_update<NV>, g), kThreads, 0, h.stream>>>(w, h.V, j, n, pass, h.scal, h.part, h.counter, vf)
   switch (nv) {
     case 1: AAO_UP(1); break;
     case 2: AAO_UP(2); break;
@@ -673,13 +683,16 @@ int run_fgmres(Handle& h, const double* b, double* x, double tol, int m, int max
   const int g = grid_for(n);
   const size_t zsz = h.mixed ? sizeof(float) : sizeof(double);
   char* Zb = reinterpret_cast<char*>(h.Z);
+  // mixed precision: the residual and update kernels also write an FP32 copy of the basis vector
+  // that the next preconditioner apply reads (the Riesz matvec does not write one)
+  float* vf = (h.mixed && h.p.op != AAO_OP_RIESZ) ? h.Vf : nullptr;
 
   int its = 0, restarts = 0, status = AAO_OK;
   double rel = 0.0, est = 0.0, bnorm = 0.0;
   for (bool first = true;; first = false) {
     // restart residual r = b - M x, written as the raw first basis vector V_0 (the first one also
     // forms ||b||^2)
-    AAO_TRY(launch_matvec(h, x, false, h.V, b, nullptr, 0, m, first));
+    AAO_TRY(launch_matvec(h, x, false, h.V, b, nullptr, 0, m, first, vf));
     AAO_TRY(read_scalars(h, S_BETA2, 2));  // BETA2, BNORM2
     if (first) {
       bnorm = sqrt(h.host_scal[1]);
@@ -702,7 +715,7 @@ int run_fgmres(Handle& h, const double* b, double* x, double tol, int m, int max
         double* W = h.V + (size_t)(j + 1) * n;  // raw next basis vector, orthogonalised in place
         void* Zj = Zb + zsz * (size_t)j * n;
         // z_j = P^{-1} (sigma_j V_j): the scale is applied inside the first FFT kernel
-        AAO_TRY(launch_precond(h, Vj, Zj, h.mixed, h.scal + S_SIG + j));
+        AAO_TRY(launch_precond(h, Vj, Zj, h.mixed, h.scal + S_SIG + j, vf));
         const int nv = j + 1;
         const int nf = nv < 8 ? nv : 8;
         AAO_TRY(launch_matvec(h, Zj, h.mixed, W, nullptr, h.V, nf, m));
@@ -712,11 +725,11 @@ int run_fgmres(Handle& h, const double* b, double* x, double tol, int m, int max
             AAO_TRY(mdot(h, c0, cnt, W, h.scal + S_D1));
           }
         }
-        AAO_TRY(update(h, W, j, 1));
+        AAO_TRY(update(h, W, j, 1, vf));
         AAO_TRY(read_scalars(h, S_EST, 4));  // EST, HN, FLAG, REORTH
         if (h.host_scal[3] != 0.0) {
           AAO_TRY(projections(h, W, nv, S_D2));
-          AAO_TRY(update(h, W, j, 2));
+          AAO_TRY(update(h, W, j, 2, vf));
           AAO_TRY(read_scalars(h, S_EST, 4));
         }
         est = h.host_scal[0];

@@ -200,7 +200,8 @@ __device__ inline void givens_column_block(double* __restrict__ scal, int j, dou
 // o0 - 1 + L (lanes 0 and 31 are the halo), so the spatial neighbours of s = x_t + x_{t-1} come
 // from lane shuffles with no FP64 work of their own. Five FP64 operations per unknown:
 //  y_t,i = (x_t - x_{t-1})_i - [L s_{i-1} + D s_i + U s_{i+1}], (L, D, U) = tau/2 A_t.
-// MODE 0: y only. MODE 1: y = b - M x, acc[0] += y.y. MODE 3: as MODE 1, and acc[1] += b.b.
+// MODE 0: y only. MODE 1: y = b - M x, acc[0] += y.y, and the FP32 copy yf if given. MODE 3: as
+// MODE 1, and acc[1] += b.b.
 // MODE 2: acc[q] += V_q . y (q < ND, a compile-time count so that no predicated-off FP64
 // instruction is issued), acc[ND] += y.y.
 constexpr int kMvCols = 30;
@@ -209,7 +210,7 @@ __device__ __forceinline__ void matvec_item(const IN* __restrict__ x, double* __
                                             const double* __restrict__ b, int nx, int t0, int t1, int o0,
                                             const double* __restrict__ L, const double* __restrict__ D,
                                             const double* __restrict__ U, int rows, const double* __restrict__ V,
-                                            size_t vstride, double (&acc)[NA]) {
+                                            size_t vstride, double (&acc)[NA], float* __restrict__ yf = nullptr) {
   constexpr bool RES = MODE == 1 || MODE == 3;
   constexpr int NVQ = MODE == 2 ? ND : 0;
   const int lane = threadIdx.x & 31;
@@ -250,6 +251,7 @@ __device__ __forceinline__ void matvec_item(const IN* __restrict__ x, double* __
           acc[0] = fma(bc, bc, acc[0]);
           if constexpr (MODE == 3) acc[NA - 1] = fma(bc, bc, acc[NA - 1]);
           y[r + i] = bc;
+          if (yf) yf[r + i] = narrow(bc);
         }
         xp = xc;
         continue;
@@ -268,6 +270,9 @@ __device__ __forceinline__ void matvec_item(const IN* __restrict__ x, double* __
         if constexpr (MODE == 3) acc[NA - 1] = fma(bc, bc, acc[NA - 1]);
       }
       y[r + i] = v;
+      if constexpr (RES) {
+        if (yf) yf[r + i] = narrow(v);
+      }
       if constexpr (MODE == 2) {
 #pragma unroll
         for (int q = 0; q < ND; ++q) acc[q] = fma(vc[q], v, acc[q]);

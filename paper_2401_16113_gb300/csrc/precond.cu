@@ -52,7 +52,7 @@ int default_tile(int nx, int N, size_t rsize) {
 }
 
 template <typename R>
-int run_precond(Handle& h, const double* v, void* z, bool z_is_float, const double* in_scale) {
+int run_precond(Handle& h, const double* v, void* z, bool z_is_float, const double* in_scale, const float* vf) {
   using C = C_t<R>;
   const int N = h.nt, nx = h.nx;
   const int P = h.fft_p > 0 ? h.fft_p : default_tile(nx, N, sizeof(R));
@@ -64,12 +64,17 @@ int run_precond(Handle& h, const double* v, void* z, bool z_is_float, const doub
   const R* ilam = (sizeof(R) == 4) ? (const R*)h.ilamf : (const R*)h.ilam;
   const C* tw = (sizeof(R) == 4) ? (const C*)h.twf : (const C*)h.tw;
 
-  AAO_TRY_CUDA(cudaFuncSetAttribute(k_fft_fwd<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const double nsp = (double)h.K * nx * sizeof(C);   // half spectrum, bins 0..nt/2
   const double nv = (double)nx * N;
-  {
+  if (vf && sizeof(R) == 4) {
+    // the FP32 copy of v written by the kernel that produced v
+    AAO_TRY_CUDA(cudaFuncSetAttribute(k_fft_fwd<R, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ProfScope ps(AAO_K_FFT_FWD, h.stream, nv * sizeof(float) + nsp);
+    k_fft_fwd<R, float><<<grid, threads, smem, h.stream>>>(vf, spec, nx, N, h.log2n, P, h.pitch, lam, tw, in_scale);
+  } else {
+    AAO_TRY_CUDA(cudaFuncSetAttribute(k_fft_fwd<R, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     ProfScope ps(AAO_K_FFT_FWD, h.stream, nv * sizeof(double) + nsp);
-    k_fft_fwd<R><<<grid, threads, smem, h.stream>>>(v, spec, nx, N, h.log2n, P, h.pitch, lam, tw, in_scale);
+    k_fft_fwd<R, double><<<grid, threads, smem, h.stream>>>(v, spec, nx, N, h.log2n, P, h.pitch, lam, tw, in_scale);
   }
   AAO_CHECK_LAUNCH();
 
@@ -149,9 +154,9 @@ int run_precond(Handle& h, const double* v, void* z, bool z_is_float, const doub
 
 }  // namespace
 
-int launch_precond(Handle& h, const double* v, void* z, bool z_is_float, const double* in_scale) {
-  if (h.mixed) return run_precond<float>(h, v, z, z_is_float, in_scale);
-  return run_precond<double>(h, v, z, z_is_float, in_scale);
+int launch_precond(Handle& h, const double* v, void* z, bool z_is_float, const double* in_scale, const float* vf) {
+  if (h.mixed) return run_precond<float>(h, v, z, z_is_float, in_scale, vf);
+  return run_precond<double>(h, v, z, z_is_float, in_scale, nullptr);
 }
 
 // FFT tile autotuner: time the whole apply for every admissible tile width 2P (P = 1, 2, 4, ...)

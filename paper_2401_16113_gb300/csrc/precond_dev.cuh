@@ -82,12 +82,15 @@ __device__ void smem_fft(C* data, int log2n, int lp, const C* tw) {
 template <typename R> __device__ __forceinline__ R to_r(double v);
 template <> __device__ __forceinline__ float to_r<float>(double v) { return narrow(v); }
 template <> __device__ __forceinline__ double to_r<double>(double v) { return v; }
+// an input element (FP64, or an FP32 copy made by the kernel that produced the vector) as R
+template <typename R> __device__ __forceinline__ R in_r(double v) { return to_r<R>(v); }
+template <typename R> __device__ __forceinline__ R in_r(float v) { return (R)v; }
 
 // step (a) for the column tile starting at x0, N < 128 (all threads of the CTA; smem holds
 // (P+1)*N complex: the tile, then a copy of the twiddle table).
 // Ends without a barrier: synchronise before reusing smem.
-template <typename R>
-__device__ __forceinline__ void fft_fwd_tile_smem(const double* __restrict__ v, C_t<R>* __restrict__ spec, int nx, int N,
+template <typename R, typename IN>
+__device__ __forceinline__ void fft_fwd_tile_smem(const IN* __restrict__ v, C_t<R>* __restrict__ spec, int nx, int N,
                                              int log2n, int P, int pitch, const R* __restrict__ lam,
                                              const C_t<R>* __restrict__ tw, R sc, int x0, unsigned char* smraw) {
   using C = C_t<R>;
@@ -101,11 +104,11 @@ __device__ __forceinline__ void fft_fwd_tile_smem(const double* __restrict__ v, 
   const int c = threadIdx.x & (W - 1), tr = threadIdx.x / W, tstep = blockDim.x / W;
   const int x = x0 + c;
   const bool ok = x < nx;
-  const double* src = v + x;
+  const IN* src = v + x;
 #pragma unroll 8
   for (int t = tr; t < N; t += tstep) {
     R val = (R)0;
-    if (ok) val = to_r<R>(__ldg(src + (size_t)t * nx)) * (__ldg(&lam[t]) * sc);
+    if (ok) val = in_r<R>(__ldg(src + (size_t)t * nx)) * (__ldg(&lam[t]) * sc);
     flat[t * W + c] = val;  // complex column c/2: real part for even c, imaginary for odd c
   }
   __syncthreads();
@@ -352,8 +355,8 @@ __device__ __forceinline__ void load_pair(const C* in, C& A, C& B, bool ok0, boo
 
 // step (a) for the column tile starting at x0, N >= 128 (spec rows 16-byte aligned, x0 even;
 // smem holds reg_fft_elems(P, N) complex). Ends without a barrier: synchronise before reusing smem.
-template <typename R>
-__device__ __forceinline__ void fft_fwd_tile_reg(const double* __restrict__ v, C_t<R>* __restrict__ spec, int nx,
+template <typename R, typename IN>
+__device__ __forceinline__ void fft_fwd_tile_reg(const IN* __restrict__ v, C_t<R>* __restrict__ spec, int nx,
                                                  int N, int log2n, int P, int pitch, const R* __restrict__ lam,
                                                  const C_t<R>* __restrict__ tw, R sc, int x0, unsigned char* smraw) {
   using C = C_t<R>;
@@ -369,11 +372,11 @@ __device__ __forceinline__ void fft_fwd_tile_reg(const double* __restrict__ v, C
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
       const int t = u + r * n16;
-      const double* row = v + (size_t)t * nx + x;
+      const IN* row = v + (size_t)t * nx + x;
       const R l = __ldg(&lam[t]) * sc;
       R re = (R)0, im = (R)0;
-      if (ok0) re = to_r<R>(__ldg(row)) * l;
-      if (ok1) im = to_r<R>(__ldg(row + 1)) * l;
+      if (ok0) re = in_r<R>(__ldg(row)) * l;
+      if (ok1) im = in_r<R>(__ldg(row + 1)) * l;
       a[r] = cmk<C>(re, im);
     }
     dft16(a);
@@ -465,12 +468,12 @@ __host__ __device__ __forceinline__ size_t fft_tile_bytes(int P, int N, size_t c
   return (N >= (1 << kRegFftMinLog2) ? reg_fft_elems(P, N) : (size_t)(P + 1) * N) * csize;
 }
 
-template <typename R>
-__device__ __forceinline__ void fft_fwd_tile(const double* __restrict__ v, C_t<R>* __restrict__ spec, int nx, int N,
+template <typename R, typename IN = double>
+__device__ __forceinline__ void fft_fwd_tile(const IN* __restrict__ v, C_t<R>* __restrict__ spec, int nx, int N,
                                              int log2n, int P, int pitch, const R* __restrict__ lam,
                                              const C_t<R>* __restrict__ tw, R sc, int x0, unsigned char* smraw) {
-  if (log2n >= kRegFftMinLog2) fft_fwd_tile_reg<R>(v, spec, nx, N, log2n, P, pitch, lam, tw, sc, x0, smraw);
-  else fft_fwd_tile_smem<R>(v, spec, nx, N, log2n, P, pitch, lam, tw, sc, x0, smraw);
+  if (log2n >= kRegFftMinLog2) fft_fwd_tile_reg<R, IN>(v, spec, nx, N, log2n, P, pitch, lam, tw, sc, x0, smraw);
+  else fft_fwd_tile_smem<R, IN>(v, spec, nx, N, log2n, P, pitch, lam, tw, sc, x0, smraw);
 }
 
 template <typename R, typename OUT>
@@ -481,14 +484,14 @@ __device__ __forceinline__ void fft_inv_tile(const C_t<R>* __restrict__ spec, OU
   else fft_inv_tile_smem<R, OUT>(spec, z, nx, N, log2n, P, pitch, ilam, tw, x0, smraw);
 }
 
-template <typename R>
-__global__ void __launch_bounds__(sizeof(R) == 8 ? 512 : 1024) k_fft_fwd(const double* __restrict__ v, C_t<R>* __restrict__ spec,
+template <typename R, typename IN>
+__global__ void __launch_bounds__(sizeof(R) == 8 ? 512 : 1024) k_fft_fwd(const IN* __restrict__ v, C_t<R>* __restrict__ spec,
                                                   int nx, int N, int log2n, int P, int pitch,
                                                   const R* __restrict__ lam, const C_t<R>* __restrict__ tw,
                                                   const double* __restrict__ in_scale) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const R sc = in_scale ? to_r<R>(*in_scale) : (R)1;
-  fft_fwd_tile<R>(v, spec, nx, N, log2n, P, pitch, lam, tw, sc, blockIdx.x * 2 * P, smraw);
+  fft_fwd_tile<R, IN>(v, spec, nx, N, log2n, P, pitch, lam, tw, sc, blockIdx.x * 2 * P, smraw);
 }
 
 template <typename R, typename OUT>
