@@ -179,12 +179,15 @@ int tune_precond(Handle& h) {
   float best = 1e30f;
   int bestp = default_tile(h.nx, h.nt, rs);
   int rc = AAO_OK;
+  // time the form the solver runs: mixed solves read an FP32 copy of the input (the zero bytes of
+  // v serve as one)
+  const float* vf = (h.mixed && h.p.op != AAO_OP_RIESZ) ? reinterpret_cast<const float*>(v) : nullptr;
   for (int P = 1; P <= pmax && rc == AAO_OK; P <<= 1) {
     h.fft_p = P;
-    rc = launch_precond(h, v, z, h.mixed);
+    rc = launch_precond(h, v, z, h.mixed, nullptr, vf);
     if (rc != AAO_OK) break;
     cudaEventRecord(e0, h.stream);
-    for (int r = 0; r < 3 && rc == AAO_OK; ++r) rc = launch_precond(h, v, z, h.mixed);
+    for (int r = 0; r < 3 && rc == AAO_OK; ++r) rc = launch_precond(h, v, z, h.mixed, nullptr, vf);
     cudaEventRecord(e1, h.stream);
     cudaEventSynchronize(e1);
     float ms = 0.f;
