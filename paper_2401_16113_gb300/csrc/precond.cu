@@ -16,6 +16,9 @@
 //
 // The unitary DFT of Sec. 3.1 carries 1/sqrt(nt) in each direction; here the forward FFT is
 // unnormalised and the single 1/nt is folded into the unscaling table.
+#include <mutex>
+#include <unordered_map>
+
 #include "precond_dev.cuh"
 
 namespace aao {
@@ -25,6 +28,21 @@ namespace {
 using namespace pdev;
 
 constexpr size_t kTriSmemMax = 227 * 1024;  // dynamic shared memory per CTA
+
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) only when a launch needs more than was set
+// before for that kernel (the call is not free on the host, and the host's lead over the GPU
+// matters after every status read-back of the solver)
+int ensure_smem(const void* kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, size_t> set;
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& cur = set[kernel];
+  if (bytes <= 48 * 1024 || bytes <= cur) return AAO_OK;
+  AAO_TRY_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  cur = bytes;
+  return AAO_OK;
+}
+
 
 // threads of the FFT kernels: kVals complex values per thread per stage, a multiple of 32,
 // within the kernels' launch bounds
@@ -68,11 +86,11 @@ int run_precond(Handle& h, const double* v, void* z, bool z_is_float, const doub
   const double nv = (double)nx * N;
   if (vf && sizeof(R) == 4) {
     // the FP32 copy of v written by the kernel that produced v
-    AAO_TRY_CUDA(cudaFuncSetAttribute(k_fft_fwd<R, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    AAO_TRY(ensure_smem((const void*)k_fft_fwd<R, float>, smem));
     ProfScope ps(AAO_K_FFT_FWD, h.stream, nv * sizeof(float) + nsp);
     k_fft_fwd<R, float><<<grid, threads, smem, h.stream>>>(vf, spec, nx, N, h.log2n, P, h.pitch, lam, tw, in_scale);
   } else {
-    AAO_TRY_CUDA(cudaFuncSetAttribute(k_fft_fwd<R, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    AAO_TRY(ensure_smem((const void*)k_fft_fwd<R, double>, smem));
     ProfScope ps(AAO_K_FFT_FWD, h.stream, nv * sizeof(double) + nsp);
     k_fft_fwd<R, double><<<grid, threads, smem, h.stream>>>(v, spec, nx, N, h.log2n, P, h.pitch, lam, tw, in_scale);
   }
@@ -99,11 +117,11 @@ int run_precond(Handle& h, const double* v, void* z, bool z_is_float, const doub
     const R* tri = reinterpret_cast<const R*>(h.tri);
     ProfScope ps(AAO_K_TRIDIAG, h.stream, 2.0 * nsp);
     if (staged) {
-      AAO_TRY_CUDA(cudaFuncSetAttribute(k_tridiag_part<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
+      AAO_TRY(ensure_smem((const void*)k_tridiag_part<R, true>, smem2));
       k_tridiag_part<R, true><<<(h.K + G - 1) / G, G * T, smem2, h.stream>>>(spec, nx, h.K, h.pitch, ch, cs, lgT, tri,
                                                                              mu, il2);
     } else {
-      AAO_TRY_CUDA(cudaFuncSetAttribute(k_tridiag_part<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
+      AAO_TRY(ensure_smem((const void*)k_tridiag_part<R, false>, smem2));
       k_tridiag_part<R, false><<<(h.K + G - 1) / G, G * T, smem2, h.stream>>>(spec, nx, h.K, h.pitch, ch, cs, lgT,
                                                                               tri, mu, il2);
     }
@@ -130,7 +148,7 @@ int run_precond(Handle& h, const double* v, void* z, bool z_is_float, const doub
   const R* up = (sizeof(R) == 4) ? (const R*)h.pUf : (const R*)h.pU;
   const C* mu = (sizeof(R) == 4) ? (const C*)h.muf : (const C*)h.mu;
   const C* il2 = (sizeof(R) == 4) ? (const C*)h.il2f : (const C*)h.il2;
-  AAO_TRY_CUDA(cudaFuncSetAttribute(k_tridiag<R, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
+  AAO_TRY(ensure_smem((const void*)k_tridiag<R, CH>, smem2));
   {
     ProfScope ps(AAO_K_TRIDIAG, h.stream, 2.0 * nsp);
     k_tridiag<R, CH><<<(h.K + G - 1) / G, G * T, smem2, h.stream>>>(spec, nx, h.K, h.pitch, ch, cs, T, lo, di, up,
@@ -140,11 +158,11 @@ int run_precond(Handle& h, const double* v, void* z, bool z_is_float, const doub
   AAO_CHECK_LAUNCH();
 
   if (z_is_float) {
-    AAO_TRY_CUDA(cudaFuncSetAttribute(k_fft_inv<R, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    AAO_TRY(ensure_smem((const void*)k_fft_inv<R, float>, smem));
     ProfScope ps(AAO_K_FFT_INV, h.stream, nsp + nv * sizeof(float));
     k_fft_inv<R, float><<<grid, threads, smem, h.stream>>>(spec, (float*)z, nx, N, h.log2n, P, h.pitch, ilam, tw);
   } else {
-    AAO_TRY_CUDA(cudaFuncSetAttribute(k_fft_inv<R, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    AAO_TRY(ensure_smem((const void*)k_fft_inv<R, double>, smem));
     ProfScope ps(AAO_K_FFT_INV, h.stream, nsp + nv * sizeof(double));
     k_fft_inv<R, double><<<grid, threads, smem, h.stream>>>(spec, (double*)z, nx, N, h.log2n, P, h.pitch, ilam, tw);
   }
