@@ -230,6 +230,22 @@ def test_fgmres_restart_small_m(aao):
     assert relmax(host(x), ref) <= 1e-9
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_fgmres_exhausted_krylov_space(aao, precision):
+    """A 3 x 2 system (6 unknowns) with FGMRES(10) and alpha = 1: the Krylov space fills up, the
+    last raw vector cancels almost entirely (the second Gram-Schmidt pass and the steps queued
+    behind it are exercised) and the solve still ends at the tolerance."""
+    p = W.with_(BS, nx=3, nt=2, alpha=1.0, precision=precision)
+    h = aao.aao_create(p)
+    b = torch.empty(6, dtype=torch.float64, device="cuda")
+    aao.aao_rhs(h, b)
+    x = torch.zeros(6, dtype=torch.float64, device="cuda")
+    st = aao.fgmres_solve(h, b, x, 1e-13, 10, 50)
+    assert st["status"] == 0 and st["rel_residual"] <= 1e-13, st
+    ref, _ = O.solve(W.with_(p, tol=1e-13))
+    assert relmax(host(x), ref) <= 1e-10
+
+
 def test_fgmres_maxit_reports_not_converged(aao):
     p = W.with_(BS, nx=63, nt=64, alpha=1.0)
     h = aao.aao_create(p)
