@@ -99,8 +99,9 @@ __global__ void k_rhs(double* __restrict__ b, int nx, int nt, const double* __re
 // MODE 0: y = M x.
 // MODE 1: y = b - M x (the restart residual, written as the raw first basis vector); the last
 //         block sets ||r||^2, sigma_0 = 1/||r|| and g = (||r||, 0, ...). MODE 3: MODE 1 and ||b||^2.
-// MODE 2: y = M x, the first Gram-Schmidt projections d_q = V_q . y (q < nd <= 8) and ||y||^2,
-//         finished by the last block into scal[S_D1 + q] and scal[S_WN2].
+// MODE 2: y = M x and the first Gram-Schmidt projections d_q = V_q . y (q < nd <= 8),
+//         finished by the last block into scal[S_D1 + q]. (||w||^2 is not formed: the update
+//         kernel recovers it as ||w'||^2 + sum_q sigma_q^2 d_q^2.)
 template <typename IN, int MODE, int ND>
 __global__ void __launch_bounds__(kThreads) k_matvec(const IN* __restrict__ x, double* __restrict__ y,
                                                      const double* __restrict__ b, int nx, int nt,
@@ -110,7 +111,7 @@ __global__ void __launch_bounds__(kThreads) k_matvec(const IN* __restrict__ x, d
                                                      double* __restrict__ part, double* __restrict__ scal,
                                                      unsigned int* __restrict__ counter, int m,
                                                      float* __restrict__ yf) {
-  constexpr int NA = MODE == 2 ? ND + 1 : (MODE == 3 ? 2 : 1);
+  constexpr int NA = MODE == 2 ? ND : (MODE == 3 ? 2 : 1);
   constexpr int nd = ND;
   // one wave of blocks: the (strip, time level) rows, strip-major, are split into one contiguous
   // range per warp, so every warp does the same work to within one row and keeps level t-1 in
@@ -135,13 +136,13 @@ __global__ void __launch_bounds__(kThreads) k_matvec(const IN* __restrict__ x, d
   const unsigned int nblk = gridDim.x;
   const unsigned int bid = blockIdx.x;
   if constexpr (MODE == 2) {
-    block_sums_wide<NA>(acc, nd + 1, part + (size_t)bid * kPartLd);
+    block_sums_wide<NA>(acc, nd, part + (size_t)bid * kPartLd);
   } else {
     block_sums_wide<NA>(acc, NA, part + (size_t)bid * kPartLd);
   }
   if (!last_block(counter, nblk)) return;
   if constexpr (MODE == 2) {
-    finish_sums_wide<NA>(part, nblk, nd + 1, [&](int q, double v) { scal[q < nd ? S_D1 + q : S_WN2] = v; }, counter);
+    finish_sums_wide<NA>(part, nblk, nd, [&](int q, double v) { scal[S_D1 + q] = v; }, counter);
   } else {
     finish_sums_wide<NA>(part, nblk, NA, [&](int q, double v) {
       if (q == 1) {
@@ -242,7 +243,16 @@ __global__ void __launch_bounds__(kThreads) k_update(double* __restrict__ w, con
     wp2 = v;
   }, counter);
   __syncthreads();
-  if (pass == 1 && wp2 < kReorthEta * kReorthEta * scal[S_WN2]) {
+  // ||w||^2 = ||w'||^2 + sum_i sigma_i^2 d_i^2 (Pythagoras over the orthonormal basis; a sum of
+  // positive terms, so no cancellation), compared with ||w'||^2 for the second-pass decision
+  double wn2 = wp2;
+  if (pass == 1) {
+    for (int i = 0; i < nv; ++i) {
+      const double si = scal[S_SIG + i] * scal[S_D1 + i];
+      wn2 = fma(si, si, wn2);
+    }
+  }
+  if (pass == 1 && wp2 < kReorthEta * kReorthEta * wn2) {
     if (threadIdx.x == 0) scal[S_REORTH] = 1.0;
     return;
   }
@@ -582,8 +592,8 @@ int launch_matvec(Handle& h, const void* x, bool x_is_float, double* y, const do
   const double bytes = nn * (x_is_float ? 4.0 : 8.0) + 3.0 * 8.0 * (double)h.nx * h.coef_rows + nn * 8.0 +
                        (b ? nn * 8.0 : 0.0) + (V ? nn * 8.0 * nd : 0.0);
   // per unknown: s and d (2 adds), three FMAs; residual: b - (1) and r.r (FMA), b.b (FMA);
-  // projections: nd FMAs and y.y (FMA)
-  const double flops = nn * (2.0 + 6.0 + (b ? 3.0 : 0.0) + (b && with_bnorm ? 2.0 : 0.0) + (V ? 2.0 * (nd + 1) : 0.0));
+  // projections: nd FMAs
+  const double flops = nn * (2.0 + 6.0 + (b ? 3.0 : 0.0) + (b && with_bnorm ? 2.0 : 0.0) + (V ? 2.0 * nd : 0.0));
   if (x_is_float) return matvec_t<float>(h, (const float*)x, y, b, V, nd, m, bytes, flops, with_bnorm, yf);
   return matvec_t<double>(h, (const double*)x, y, b, V, nd, m, bytes, flops, with_bnorm, yf);
 }

@@ -203,7 +203,7 @@ __device__ inline void givens_column_block(double* __restrict__ scal, int j, dou
 // MODE 0: y only. MODE 1: y = b - M x, acc[0] += y.y, and the FP32 copy yf if given. MODE 3: as
 // MODE 1, and acc[1] += b.b.
 // MODE 2: acc[q] += V_q . y (q < ND, a compile-time count so that no predicated-off FP64
-// instruction is issued), acc[ND] += y.y.
+// instruction is issued), and acc[ND] += y.y when the caller has room for it (NA > ND).
 constexpr int kMvCols = 30;
 template <typename IN, int MODE, int ND, int NA>
 __device__ __forceinline__ void matvec_item(const IN* __restrict__ x, double* __restrict__ y,
@@ -276,7 +276,7 @@ __device__ __forceinline__ void matvec_item(const IN* __restrict__ x, double* __
       if constexpr (MODE == 2) {
 #pragma unroll
         for (int q = 0; q < ND; ++q) acc[q] = fma(vc[q], v, acc[q]);
-        acc[ND] = fma(v, v, acc[ND]);
+        if constexpr (NA > ND) acc[ND] = fma(v, v, acc[ND]);
       }
     }
     xp = xc;
