@@ -88,6 +88,33 @@ template <typename C> __device__ __forceinline__ C cinv(C a) {
   return cmk<C>(a.x * s, -a.y * s);
 }
 
+// ------------------------------------------------------------------ programmatic dependent launch
+// The solver's kernels are launched with programmatic stream serialisation: a kernel's CTAs may
+// be scheduled while the previous kernel's last CTAs still run; each kernel starts with
+// pdl_sync(), which waits until the previous grid has completed (its writes visible) and then
+// lets the next grid be scheduled once all of this grid's CTAs are resident. Launched without
+// the attribute, both instructions return at once.
+__device__ __forceinline__ void pdl_sync() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // ------------------------------------------------------------------ conversions
 // FP64 instructions (conversions included) share the slow FP64 pipe on this part, so the
 // FP32 <-> FP64 conversions on the hot path are assembled from integer bit operations.

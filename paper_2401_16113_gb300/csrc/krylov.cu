@@ -111,6 +111,7 @@ __global__ void __launch_bounds__(kThreads) k_matvec(const IN* __restrict__ x, d
                                                      double* __restrict__ part, double* __restrict__ scal,
                                                      unsigned int* __restrict__ counter, int m,
                                                      float* __restrict__ yf) {
+  pdl_sync();
   constexpr int NA = MODE == 2 ? ND : (MODE == 3 ? 2 : 1);
   constexpr int nd = ND;
   // one wave of blocks: the (strip, time level) rows, strip-major, are split into one contiguous
@@ -164,6 +165,7 @@ template <int NV>
 __global__ void __launch_bounds__(kThreads) k_mdot(const double* __restrict__ V, int c0, size_t n,
                                                    const double* __restrict__ w, double* __restrict__ part,
                                                    double* __restrict__ out, unsigned int* __restrict__ counter) {
+  pdl_sync();
   constexpr int nv = NV;
   double acc[NV];
 #pragma unroll
@@ -188,6 +190,7 @@ __global__ void __launch_bounds__(kThreads) k_update(double* __restrict__ w, con
                                                      int j, size_t n, int pass, double* __restrict__ scal,
                                                      double* __restrict__ part, unsigned int* __restrict__ counter,
                                                      float* __restrict__ vf) {
+  pdl_sync();
   __shared__ double cf[128];
   const int nv = j + 1;
   const int off = pass == 1 ? S_D1 : S_D2;
@@ -265,6 +268,7 @@ __global__ void __launch_bounds__(kThreads) k_update(double* __restrict__ w, con
 template <typename ZT>
 __global__ void __launch_bounds__(kThreads) k_xupdate(double* __restrict__ x, const ZT* __restrict__ Z, int jd,
                                                       size_t n, const double* __restrict__ scal) {
+  pdl_sync();
   __shared__ double ys[128];
   if (threadIdx.x == 0) {
     for (int i = jd - 1; i >= 0; --i) {
@@ -306,6 +310,7 @@ __global__ void __launch_bounds__(kThreads) k_xupdate(double* __restrict__ x, co
 __global__ void __launch_bounds__(kThreads) k_dot_self(const double* __restrict__ v, size_t n, double* part,
                                                        double* __restrict__ scal, int slot,
                                                        unsigned int* __restrict__ counter) {
+  pdl_sync();
   double acc[1] = {0.0};
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     const double a = __ldg(v + e);
@@ -544,8 +549,9 @@ int matvec_t(Handle& h, const IN* x, double* y, const double* b, const double* V
   const size_t need = (rowsw + kThreads / 32 - 1) / (kThreads / 32);
   ProfScope ps(AAO_K_MATVEC, h.stream, bytes, flops);
 #define AAO_MV2(ND)                                                                                              \
-  k_matvec<IN, 2, ND><<<wave_blocks(h, (const void*)k_matvec<IN, 2, ND>, need), kThreads, 0, h.stream>>>(        \
-      x, y, nullptr, h.nx, h.nt, h.mL, h.mD, h.mU, h.coef_rows, V, h.n, h.part, h.scal, h.counter, m, nullptr)
+  AAO_TRY_CUDA(launch_pdl(k_matvec<IN, 2, ND>, wave_blocks(h, (const void*)k_matvec<IN, 2, ND>, need), kThreads, 0, \
+                          h.stream, x, y, nullptr, h.nx, h.nt, h.mL, h.mD, h.mU, h.coef_rows, V, h.n, h.part,      \
+                          h.scal, h.counter, m, nullptr))
   if (V && nd > 0) {
     switch (nd) {
       case 1: AAO_MV2(1); break;
@@ -558,15 +564,17 @@ int matvec_t(Handle& h, const IN* x, double* y, const double* b, const double* V
       default: AAO_MV2(8); break;
     }
   } else if (b && with_bnorm) {
-    k_matvec<IN, 3, 0><<<wave_blocks(h, (const void*)k_matvec<IN, 3, 0>, need), kThreads, 0, h.stream>>>(
-        x, y, b, h.nx, h.nt, h.mL, h.mD, h.mU, h.coef_rows, nullptr, h.n, h.part, h.scal, h.counter, m, yf);
+    AAO_TRY_CUDA(launch_pdl(k_matvec<IN, 3, 0>, wave_blocks(h, (const void*)k_matvec<IN, 3, 0>, need), kThreads, 0,
+                            h.stream, x, y, b, h.nx, h.nt, h.mL, h.mD, h.mU, h.coef_rows, nullptr, h.n, h.part, h.scal,
+                            h.counter, m, yf));
   } else if (b) {
-    k_matvec<IN, 1, 0><<<wave_blocks(h, (const void*)k_matvec<IN, 1, 0>, need), kThreads, 0, h.stream>>>(
-        x, y, b, h.nx, h.nt, h.mL, h.mD, h.mU, h.coef_rows, nullptr, h.n, h.part, h.scal, h.counter, m, yf);
+    AAO_TRY_CUDA(launch_pdl(k_matvec<IN, 1, 0>, wave_blocks(h, (const void*)k_matvec<IN, 1, 0>, need), kThreads, 0,
+                            h.stream, x, y, b, h.nx, h.nt, h.mL, h.mD, h.mU, h.coef_rows, nullptr, h.n, h.part, h.scal,
+                            h.counter, m, yf));
   } else {
-    k_matvec<IN, 0, 0><<<wave_blocks(h, (const void*)k_matvec<IN, 0, 0>, need), kThreads, 0, h.stream>>>(
-        x, y, nullptr, h.nx, h.nt, h.mL, h.mD, h.mU, h.coef_rows, nullptr, h.n, h.part, h.scal, h.counter, m,
-        nullptr);
+    AAO_TRY_CUDA(launch_pdl(k_matvec<IN, 0, 0>, wave_blocks(h, (const void*)k_matvec<IN, 0, 0>, need), kThreads, 0,
+                            h.stream, x, y, nullptr, h.nx, h.nt, h.mL, h.mD, h.mU, h.coef_rows, nullptr, h.n, h.part,
+                            h.scal, h.counter, m, nullptr));
   }
 #undef AAO_MV2
   AAO_CHECK_LAUNCH();
@@ -634,7 +642,9 @@ int mdot(Handle& h, int c0, int cnt, const double* w, double* out) {
   const size_t n = h.n;
   const int g = grid_for(n);
   ProfScope ps(AAO_K_ARNOLDI, h.stream, 8.0 * (double)n * (cnt + 1), 2.0 * (double)n * cnt);
-#define AAO_MD(NV) k_mdot<NV><<<wave_blocks(h, (const void*)k_mdot<NV>, g), kThreads, 0, h.stream>>>(h.V, c0, n, w, h.part, out, h.counter)
+#define AAO_MD(NV)                                                                                      \
+  AAO_TRY_CUDA(launch_pdl(k_mdot<NV>, wave_blocks(h, (const void*)k_mdot<NV>, g), kThreads, 0, h.stream, h.V, c0, n, \
+                          w, h.part, out, h.counter))
   switch (cnt) {
     case 1: AAO_MD(1); break;
     case 2: AAO_MD(2); break;
@@ -666,7 +676,9 @@ int update(Handle& h, double* w, int j, int pass, float* vf) {
   const int g = grid_for(n);
   const int nv = j + 1;
   ProfScope ps(AAO_K_ARNOLDI, h.stream, 8.0 * (double)n * (nv + 2), 2.0 * (double)n * (nv + 1));
-#define AAO_UP(NV) k_update<NV><<<wave_blocks(h, (const void*)k_update<NV>, g), kThreads, 0, h.stream>>>(w, h.V, j, n, pass, h.scal, h.part, h.counter, vf)
+#define AAO_UP(NV)                                                                                        \
+  AAO_TRY_CUDA(launch_pdl(k_update<NV>, wave_blocks(h, (const void*)k_update<NV>, g), kThreads, 0, h.stream, w, h.V, j, \
+                          n, pass, h.scal, h.part, h.counter, vf))
   switch (nv) {
     case 1: AAO_UP(1); break;
     case 2: AAO_UP(2); break;
@@ -753,9 +765,11 @@ int run_fgmres(Handle& h, const double* b, double* x, double tol, int m, int max
       {
         ProfScope ps(AAO_K_OTHER, h.stream, (double)n * (16.0 + zsz * jd));
         if (h.mixed)
-          k_xupdate<float><<<wave_blocks(h, (const void*)k_xupdate<float>, g), kThreads, 0, h.stream>>>(x, (const float*)h.Z, jd, n, h.scal);
+          AAO_TRY_CUDA(launch_pdl(k_xupdate<float>, wave_blocks(h, (const void*)k_xupdate<float>, g), kThreads, 0,
+                                  h.stream, x, (const float*)h.Z, jd, n, h.scal));
         else
-          k_xupdate<double><<<wave_blocks(h, (const void*)k_xupdate<double>, g), kThreads, 0, h.stream>>>(x, (const double*)h.Z, jd, n, h.scal);
+          AAO_TRY_CUDA(launch_pdl(k_xupdate<double>, wave_blocks(h, (const void*)k_xupdate<double>, g), kThreads, 0,
+                                  h.stream, x, (const double*)h.Z, jd, n, h.scal));
       }
       AAO_CHECK_LAUNCH();
       ++restarts;

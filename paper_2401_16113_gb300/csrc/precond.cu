@@ -88,11 +88,13 @@ int run_precond(Handle& h, const double* v, void* z, bool z_is_float, const doub
     // the FP32 copy of v written by the kernel that produced v
     AAO_TRY(ensure_smem((const void*)k_fft_fwd<R, float>, smem));
     ProfScope ps(AAO_K_FFT_FWD, h.stream, nv * sizeof(float) + nsp);
-    k_fft_fwd<R, float><<<grid, threads, smem, h.stream>>>(vf, spec, nx, N, h.log2n, P, h.pitch, lam, tw, in_scale);
+    AAO_TRY_CUDA(launch_pdl(k_fft_fwd<R, float>, grid, threads, smem, h.stream, vf, spec, nx, N, h.log2n, P, h.pitch,
+                            lam, tw, in_scale));
   } else {
     AAO_TRY(ensure_smem((const void*)k_fft_fwd<R, double>, smem));
     ProfScope ps(AAO_K_FFT_FWD, h.stream, nv * sizeof(double) + nsp);
-    k_fft_fwd<R, double><<<grid, threads, smem, h.stream>>>(v, spec, nx, N, h.log2n, P, h.pitch, lam, tw, in_scale);
+    AAO_TRY_CUDA(launch_pdl(k_fft_fwd<R, double>, grid, threads, smem, h.stream, v, spec, nx, N, h.log2n, P, h.pitch,
+                            lam, tw, in_scale));
   }
   AAO_CHECK_LAUNCH();
 
@@ -118,12 +120,12 @@ int run_precond(Handle& h, const double* v, void* z, bool z_is_float, const doub
     ProfScope ps(AAO_K_TRIDIAG, h.stream, 2.0 * nsp);
     if (staged) {
       AAO_TRY(ensure_smem((const void*)k_tridiag_part<R, true>, smem2));
-      k_tridiag_part<R, true><<<(h.K + G - 1) / G, G * T, smem2, h.stream>>>(spec, nx, h.K, h.pitch, ch, cs, lgT, tri,
-                                                                             mu, il2);
+      AAO_TRY_CUDA(launch_pdl(k_tridiag_part<R, true>, (h.K + G - 1) / G, G * T, smem2, h.stream, spec, nx, h.K,
+                              h.pitch, ch, cs, lgT, tri, mu, il2));
     } else {
       AAO_TRY(ensure_smem((const void*)k_tridiag_part<R, false>, smem2));
-      k_tridiag_part<R, false><<<(h.K + G - 1) / G, G * T, smem2, h.stream>>>(spec, nx, h.K, h.pitch, ch, cs, lgT,
-                                                                              tri, mu, il2);
+      AAO_TRY_CUDA(launch_pdl(k_tridiag_part<R, false>, (h.K + G - 1) / G, G * T, smem2, h.stream, spec, nx, h.K,
+                              h.pitch, ch, cs, lgT, tri, mu, il2));
     }
   } else {
   // step (b): threads per bin T (multiple of 32, <= 512), chunk ch <= CH rows per thread
@@ -151,8 +153,8 @@ int run_precond(Handle& h, const double* v, void* z, bool z_is_float, const doub
   AAO_TRY(ensure_smem((const void*)k_tridiag<R, CH>, smem2));
   {
     ProfScope ps(AAO_K_TRIDIAG, h.stream, 2.0 * nsp);
-    k_tridiag<R, CH><<<(h.K + G - 1) / G, G * T, smem2, h.stream>>>(spec, nx, h.K, h.pitch, ch, cs, T, lo, di, up,
-                                                                    mu, il2);
+    AAO_TRY_CUDA(launch_pdl(k_tridiag<R, CH>, (h.K + G - 1) / G, G * T, smem2, h.stream, spec, nx, h.K, h.pitch, ch,
+                            cs, T, lo, di, up, mu, il2));
   }
   }  // tridiagonal operators
   AAO_CHECK_LAUNCH();
@@ -160,11 +162,13 @@ int run_precond(Handle& h, const double* v, void* z, bool z_is_float, const doub
   if (z_is_float) {
     AAO_TRY(ensure_smem((const void*)k_fft_inv<R, float>, smem));
     ProfScope ps(AAO_K_FFT_INV, h.stream, nsp + nv * sizeof(float));
-    k_fft_inv<R, float><<<grid, threads, smem, h.stream>>>(spec, (float*)z, nx, N, h.log2n, P, h.pitch, ilam, tw);
+    AAO_TRY_CUDA(launch_pdl(k_fft_inv<R, float>, grid, threads, smem, h.stream, spec, (float*)z, nx, N, h.log2n, P,
+                            h.pitch, ilam, tw));
   } else {
     AAO_TRY(ensure_smem((const void*)k_fft_inv<R, double>, smem));
     ProfScope ps(AAO_K_FFT_INV, h.stream, nsp + nv * sizeof(double));
-    k_fft_inv<R, double><<<grid, threads, smem, h.stream>>>(spec, (double*)z, nx, N, h.log2n, P, h.pitch, ilam, tw);
+    AAO_TRY_CUDA(launch_pdl(k_fft_inv<R, double>, grid, threads, smem, h.stream, spec, (double*)z, nx, N, h.log2n, P,
+                            h.pitch, ilam, tw));
   }
   AAO_CHECK_LAUNCH();
   return AAO_OK;

@@ -490,6 +490,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 512 : 1024) k_fft_fwd(const I
                                                   const R* __restrict__ lam, const C_t<R>* __restrict__ tw,
                                                   const double* __restrict__ in_scale) {
   extern __shared__ __align__(16) unsigned char smraw[];
+  pdl_sync();
   const R sc = in_scale ? to_r<R>(*in_scale) : (R)1;
   fft_fwd_tile<R, IN>(v, spec, nx, N, log2n, P, pitch, lam, tw, sc, blockIdx.x * 2 * P, smraw);
 }
@@ -499,6 +500,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 512 : 1024) k_fft_inv(const C
                                                   int nx, int N, int log2n, int P, int pitch,
                                                   const R* __restrict__ ilam, const C_t<R>* __restrict__ tw) {
   extern __shared__ __align__(16) unsigned char smraw[];
+  pdl_sync();
   fft_inv_tile<R, OUT>(spec, z, nx, N, log2n, P, pitch, ilam, tw, blockIdx.x * 2 * P, smraw);
 }
 
@@ -643,6 +645,7 @@ __global__ void __launch_bounds__(512) k_tridiag(C_t<R>* __restrict__ spec, int 
                                                  int cs, int T, const R* __restrict__ lo, const R* __restrict__ di,
                                                  const R* __restrict__ up, const C_t<R>* __restrict__ mu,
                                                  const C_t<R>* __restrict__ il2) {
+  pdl_sync();
   extern __shared__ __align__(16) unsigned char smraw[];
   using C = C_t<R>;
   const int G = blockDim.x / T;
@@ -713,6 +716,7 @@ __global__ void __launch_bounds__(512) k_tridiag_part(C_t<R>* __restrict__ spec,
                                                       const C_t<R>* __restrict__ mu, const C_t<R>* __restrict__ il2) {
   using C = C_t<R>;
   extern __shared__ __align__(16) unsigned char smraw[];
+  pdl_sync();
   const int T = 1 << lgT, G = blockDim.x >> lgT;
   const int g = threadIdx.x >> lgT, l = threadIdx.x & (T - 1);
   const int k = blockIdx.x * G + g;
