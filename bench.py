@@ -226,8 +226,11 @@ def run_ours(args):
     total_prof = sum(v[1] for v in prof.values())
     dominant = max(prof, key=lambda c: prof[c][1])
 
-    # timed region: only the dominant kernel class is bracketed by events
-    aao.aao_profile_enable([dominant])
+    # timed region. The dominant kernel class is bracketed by CUDA events in the last timed step
+    # only: an event between two kernels stops the next one from being scheduled while the
+    # previous one drains (programmatic dependent launch), so the events cost time themselves
+    # and the other steps run without them.
+    aao.aao_profile_enable([])
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if dist:
         tdist.barrier()
@@ -236,6 +239,8 @@ def run_ours(args):
     stats = []
     with ClockSampler(local) as clk:
         for k in range(args.steps):
+            if k == args.steps - 1:
+                aao.aao_profile_enable([dominant])
             stats.append(step(evs[k]))
         torch.cuda.synchronize()
     launches = aao.aao_launch_count() - l0
