@@ -191,13 +191,22 @@ __global__ void __launch_bounds__(kThreads) k_update(double* __restrict__ w, con
                                                      double* __restrict__ part, unsigned int* __restrict__ counter,
                                                      float* __restrict__ vf) {
   pdl_sync();
-  __shared__ double cf[128];
+  // every scalar the kernel needs, the last block's tail included, is staged at the start, while
+  // the loads are cheap; the tail then works out of shared memory
+  __shared__ double cf[kLdH], sh_h[kLdH + 1], sh_cs[kLdH], sh_sn[kLdH], sh_g;
   const int nv = j + 1;
   const int off = pass == 1 ? S_D1 : S_D2;
   for (int i = threadIdx.x; i < nv; i += blockDim.x) {
-    const double si = scal[S_SIG + i];
-    cf[i] = si * si * scal[off + i];
+    const double si = scal[S_SIG + i], di = scal[off + i];
+    cf[i] = si * si * di;
+    // column j of H before the rotations: sigma_i (d1_i + d2_i)
+    sh_h[i] = si * (pass == 2 ? scal[S_D1 + i] + di : di);
+    if (i < j) {
+      sh_cs[i] = scal[S_CS + i];
+      sh_sn[i] = scal[S_SN + i];
+    }
   }
+  if (threadIdx.x == 0) sh_g = scal[S_G + j];
   __syncthreads();
   double acc[1] = {0.0};
   const size_t stride = (size_t)gridDim.x * blockDim.x;
@@ -248,19 +257,17 @@ __global__ void __launch_bounds__(kThreads) k_update(double* __restrict__ w, con
   __syncthreads();
   // ||w||^2 = ||w'||^2 + sum_i sigma_i^2 d_i^2 (Pythagoras over the orthonormal basis; a sum of
   // positive terms, so no cancellation), compared with ||w'||^2 for the second-pass decision
-  double wn2 = wp2;
   if (pass == 1) {
-    for (int i = 0; i < nv; ++i) {
-      const double si = scal[S_SIG + i] * scal[S_D1 + i];
-      wn2 = fma(si, si, wn2);
+    double wn2 = wp2;
+    for (int i = 0; i < nv; ++i) wn2 = fma(sh_h[i], sh_h[i], wn2);
+    if (wp2 < kReorthEta * kReorthEta * wn2) {
+      if (threadIdx.x == 0) scal[S_REORTH] = 1.0;
+      return;
     }
   }
-  if (pass == 1 && wp2 < kReorthEta * kReorthEta * wn2) {
-    if (threadIdx.x == 0) scal[S_REORTH] = 1.0;
-    return;
-  }
-  if (threadIdx.x == 0) scal[S_REORTH] = 0.0;
-  givens_column_block(scal, j, wp2, scal + S_D1, pass == 2 ? scal + S_D2 : nullptr);
+  if (threadIdx.x != 0) return;
+  scal[S_REORTH] = 0.0;
+  givens_column_staged(scal, j, wp2, sh_h, sh_cs, sh_sn, sh_g);
 }
 
 // x += sum_{i<jd} y_i Z_i with y = H(0:jd,0:jd)^{-1} g(0:jd) (each block solves the small

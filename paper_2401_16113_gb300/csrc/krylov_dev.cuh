@@ -104,6 +104,7 @@ __device__ void finish_sums_wide(const double* part, int nblk, int cnt, OUT out,
   double s[CNT];
 #pragma unroll
   for (int q = 0; q < CNT; ++q) s[q] = 0.0;
+#pragma unroll 4
   for (int b = threadIdx.x; b < nblk; b += kThreads) {
 #pragma unroll
     for (int q = 0; q < CNT; ++q)
@@ -155,34 +156,23 @@ __device__ inline void givens_column(double* __restrict__ scal, int j, const dou
   if (!isfinite(rho) || !isfinite(hn)) scal[S_FLAG] = 1.0;
 }
 
-// givens_column run by a whole block (the last block of a kernel): its inputs are staged in
-// shared memory by all threads in one round trip, then thread 0 runs the sequential rotations
-// out of shared memory and writes the results back. wp2 = ||w'||^2 as seen by every thread.
-__device__ inline void givens_column_block(double* __restrict__ scal, int j, double wp2, const double* d1,
-                                           const double* d2) {
-  __shared__ double sh_h[kLdH + 1], sh_cs[kLdH], sh_sn[kLdH];
-  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-    sh_h[i] = scal[S_SIG + i] * (d1[i] + (d2 ? d2[i] : 0.0));
-    if (i < j) {
-      sh_cs[i] = scal[S_CS + i];
-      sh_sn[i] = scal[S_SN + i];
-    }
-  }
-  __shared__ double g;
-  if (threadIdx.x == 0) g = scal[S_G + j];
-  __syncthreads();
-  if (threadIdx.x != 0) return;
+// givens_column on one thread with its inputs already in shared memory: h = column j of H before
+// the rotations (sigma_i (d1_i + d2_i), i <= j; updated in place, needs j + 2 entries), cs/sn the
+// previous rotations, g = g_j, wp2 = ||w'||^2. Writes the results to scal.
+__device__ inline void givens_column_staged(double* __restrict__ scal, int j, double wp2, double* h, const double* cs_,
+                                            const double* sn_, double g) {
   const double wn = sqrt(fmax(wp2, 0.0));
-  sh_h[j + 1] = wn;
+  h[j + 1] = wn;
   for (int i = 0; i < j; ++i) {
-    const double a = sh_h[i], c = sh_h[i + 1];
-    sh_h[i] = sh_cs[i] * a + sh_sn[i] * c;
-    sh_h[i + 1] = -sh_sn[i] * a + sh_cs[i] * c;
+    const double a = h[i], c = h[i + 1];
+    h[i] = cs_[i] * a + sn_[i] * c;
+    h[i + 1] = -sn_[i] * a + cs_[i] * c;
   }
-  const double rho = hypot(sh_h[j], sh_h[j + 1]);
-  const double cs = rho > 0.0 ? sh_h[j] / rho : 1.0, sn = rho > 0.0 ? sh_h[j + 1] / rho : 0.0;
+  const double rho = hypot(h[j], h[j + 1]);
+  const double rr = rho > 0.0 ? 1.0 / rho : 0.0;
+  const double cs = rho > 0.0 ? h[j] * rr : 1.0, sn = rho > 0.0 ? h[j + 1] * rr : 0.0;
   double* H = scal + S_HMAT + (size_t)j * kLdH;
-  for (int i = 0; i < j; ++i) H[i] = sh_h[i];
+  for (int i = 0; i < j; ++i) H[i] = h[i];
   H[j] = rho;
   H[j + 1] = 0.0;
   scal[S_CS + j] = cs;
