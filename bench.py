@@ -29,7 +29,8 @@ TOL = 1e-8
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 200 GPU solves; 3 oracle solves for --impl reference)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -55,30 +56,42 @@ def config_of(p, extra=None):
 
 # ------------------------------------------------------------------------------ clocks
 class ClockSampler:
+    """nvidia-smi clock/throttle samples every 100 ms. The sampler is running (first row seen) before
+    the timed region starts; the summary keeps the rows taken inside the region plus the first row
+    after it, so a short region still gets the sample that closes it."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index=0):
         self.rows, self.proc, self.index = [], None, index
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                          "-i", str(self.index), "-lms", "200"], stdout=subprocess.PIPE,
+                                          "-i", str(self.index), "-lms", "100"], stdout=subprocess.PIPE,
                                          stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            deadline = time.time() + 5.0
+            while not self.rows and time.time() < deadline and self.proc.poll() is None:
+                time.sleep(0.01)
         except (OSError, ValueError):
             self.proc = None
+        self.t0 = time.time()
         return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.rows.append([c.strip() for c in line.split(",")])
+            self.rows.append((time.time(), [c.strip() for c in line.split(",")]))
 
     def __exit__(self, *a):
+        self.t1 = time.time()
         if self.proc:
+            deadline = self.t1 + 0.5
+            while not any(t >= self.t1 for t, _ in self.rows) and time.time() < deadline:
+                time.sleep(0.01)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -86,14 +99,17 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        if not self.rows:
+        inside = [r for t, r in self.rows if self.t0 <= t <= self.t1]
+        after = [r for t, r in self.rows if t > self.t1][:1]
+        rows = inside + after
+        if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = sorted(float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit())
-        mx = max((float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()), default=None)
+        sm = sorted(float(r[1]) for r in rows if len(r) > 1 and r[1].replace(".", "").isdigit())
+        mx = max((float(r[2]) for r in rows if len(r) > 2 and r[2].replace(".", "").isdigit()), default=None)
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in self.rows for i in range(4) if len(r) > 5 + i and r[5 + i] == "Active"})
+        reasons = sorted({names[i] for r in rows for i in range(4) if len(r) > 5 + i and r[5 + i] == "Active"})
         return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": reasons,
-                "samples": len(self.rows)}
+                "samples": len(inside), "samples_after": len(after)}
 
 
 # ------------------------------------------------------------------------------ roofline bits
@@ -466,6 +482,8 @@ def run_extras(args, flush, stream):
 
 def main():
     args = parse()
+    if args.steps is None:
+        args.steps = 3 if args.impl == "reference" else 200
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -109,15 +109,16 @@ __device__ __noinline__ void cl_residual(const BatchInst& I, Ctx c, double* psm,
   cluster_sums<1>(acc, 1, psm, out);
 }
 
-// W = M z_j with the first-pass projections V_q . W (q < ND) and ||W||^2 -> out[0..ND]
+// W = M z_j with the first-pass projections V_q . W (q < ND) -> out[0..ND) (||W||^2 is recovered
+// by the update from ||W'||^2 and the projections)
 template <int ND>
 __device__ __noinline__ void cl_matvec_proj(const BatchInst& I, Ctx c, const float* z, double* W, double* psm,
                                             double* out) {
-  double acc[ND + 1];
+  double acc[ND];
 #pragma unroll
-  for (int q = 0; q <= ND; ++q) acc[q] = 0.0;
-  cl_matvec<float, 2, ND, ND + 1>(I, c, z, W, nullptr, I.V, acc);
-  cluster_sums<ND + 1>(acc, ND + 1, psm, out);
+  for (int q = 0; q < ND; ++q) acc[q] = 0.0;
+  cl_matvec<float, 2, ND, ND>(I, c, z, W, nullptr, I.V, acc);
+  cluster_sums<ND>(acc, ND, psm, out);
 }
 
 // P_alpha^{-1} (scale * v) -> z (FP32), Eq. 3.2 with Remark 1; tiles and bins split by rank
@@ -207,7 +208,14 @@ __device__ __noinline__ void cl_update(const BatchInst& I, Ctx c, double* scal, 
   if (threadIdx.x == 0) {
     const double v = tot[0];
     scal[S_WP2] = v;
-    if (pass == 1 && v < kReorthEta * kReorthEta * scal[S_WN2]) {
+    // ||w||^2 = ||w'||^2 + sum_i (sigma_i d_i)^2 (Pythagoras over the orthonormal basis)
+    double wn2 = v;
+    if (pass == 1)
+      for (int i = 0; i < nv; ++i) {
+        const double hi = scal[S_SIG + i] * scal[S_D1 + i];
+        wn2 = fma(hi, hi, wn2);
+      }
+    if (pass == 1 && v < kReorthEta * kReorthEta * wn2) {
       scal[S_REORTH] = 1.0;
     } else {
       scal[S_REORTH] = 0.0;
@@ -289,7 +297,6 @@ __device__ __noinline__ void cl_solve(const BatchInst& I, Ctx c, double tol, int
           default: cl_matvec_proj<8>(I, c, Zj, W, psm, tot); break;
         }
         if (threadIdx.x < nf) scal[S_D1 + threadIdx.x] = tot[threadIdx.x];
-        if (threadIdx.x == 0) scal[S_WN2] = tot[nf];
         __syncthreads();
         for (int c0 = 8; c0 < nv; c0 += 8) cl_mdot(I, c, c0, min(8, nv - c0), W, scal + S_D1, psm, tot);
         cl_update(I, c, scal, j, 1, W, psm, tot);

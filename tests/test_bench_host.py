@@ -1,0 +1,51 @@
+"""Host-side logic of bench.py: the clock-sample window and the default step counts."""
+import importlib.util
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def load_bench():
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    m = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(m)
+    return m
+
+
+def row(sm, reasons=("Not Active",) * 4):
+    return ["0", str(sm), "2070", "900.0", "0x0", *reasons]
+
+
+def test_clock_summary_keeps_region_rows_and_the_closing_sample():
+    b = load_bench()
+    c = b.ClockSampler()
+    c.t0, c.t1 = 10.0, 11.0
+    c.rows = [(9.5, row(345)), (10.2, row(2070)), (10.6, row(1980)), (11.05, row(2055)), (11.2, row(345))]
+    s = c.summary()
+    assert s["samples"] == 2 and s["samples_after"] == 1
+    assert s["sm_mhz"] == 2055.0 and s["sm_max_mhz"] == 2070.0 and s["reasons"] == []
+
+
+def test_clock_summary_reports_throttle_reasons_and_unsampled():
+    b = load_bench()
+    c = b.ClockSampler()
+    c.t0, c.t1 = 0.0, 1.0
+    c.rows = [(0.5, row(1800, ("Not Active", "Active", "Not Active", "Active")))]
+    assert c.summary()["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
+    c.rows = [(2.0, row(2070)), (3.0, row(2070))]
+    s = c.summary()
+    assert s["samples"] == 0 and s["samples_after"] == 1
+    c.rows = []
+    assert c.summary()["reasons"] == ["unsampled"]
+
+
+def test_default_steps_per_arm(monkeypatch):
+    b = load_bench()
+    seen = {}
+    monkeypatch.setattr(b, "run_ours", lambda a: seen.setdefault("ours", a.steps))
+    monkeypatch.setattr(b, "run_reference", lambda a: seen.setdefault("reference", a.steps))
+    for argv in (["bench.py"], ["bench.py", "--impl", "reference"], ["bench.py", "--steps", "7"]):
+        monkeypatch.setattr(sys, "argv", argv)
+        b.main()
+    assert seen == {"ours": 200, "reference": 3}
