@@ -131,6 +131,39 @@ __device__ __forceinline__ double widen(float f) {
 }
 __device__ __forceinline__ double widen(double d) { return d; }
 
+// twice: 2 x, exactly, from integer bit operations. FP32 input: widen with the exponent one
+// higher (never overflows in FP64). FP64 input: a normal number gets exponent + 1 (the top binade
+// overflows to inf); a zero or subnormal doubles its magnitude bits (the carry moves into the
+// exponent field, which is the exact 2 x); inf and NaN are returned unchanged.
+__device__ __forceinline__ double twice(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned e = (b >> 23) & 0xffu;
+  const unsigned mant = (e == 0u) ? 0u : (b & 0x7fffffu);
+  unsigned ed = e + 897u;
+  ed = (e == 0xffu) ? 2047u : ed;
+  ed = (e == 0u) ? 0u : ed;
+  const unsigned hi = (b & 0x80000000u) | (ed << 20) | (mant >> 3);
+  return __hiloint2double((int)hi, (int)(mant << 29));
+}
+__device__ __forceinline__ double twice(double d) {
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  const unsigned e = (hi >> 20) & 0x7ffu, sign = hi & 0x80000000u;
+  unsigned nhi = hi + 0x00100000u, nlo = lo;
+  if (e == 0u) {
+    nhi = sign | ((hi & 0x7fffffffu) << 1) | (lo >> 31);
+    nlo = lo << 1;
+  }
+  if (e == 0x7feu) {
+    nhi = sign | 0x7ff00000u;
+    nlo = 0u;
+  }
+  if (e == 0x7ffu) {
+    nhi = hi;
+    nlo = lo;
+  }
+  return __hiloint2double((int)nhi, (int)nlo);
+}
+
 // narrow: round to nearest (ties away from zero) for results in the FP32 normal range;
 // overflow gives inf, results below the normal range give zero, NaN stays NaN. Only 32-bit
 // integer operations: the rounding carry from the low word is propagated by hand.
@@ -158,8 +191,9 @@ struct Handle {
   bool mixed = false;
   int coef_rows = 1;      // 1 (constant operator) or nt (time-dependent)
 
-  // matvec coefficients: (1/2) tau A_t, rows of nx (lower, diag, upper), coef_rows rows each.
-  // lower[0] and upper[nx-1] hold the Dirichlet-node coefficients (used by aao_rhs only).
+  // matvec coefficients: rows of nx, coef_rows rows each: lower and upper of (1/2) tau A_t and
+  // the diagonal of I + (1/2) tau A_t. lower[0] and upper[nx-1] hold the Dirichlet-node
+  // coefficients (used by aao_rhs only).
   double *mL = nullptr, *mD = nullptr, *mU = nullptr;
   double* gL = nullptr;   // left Dirichlet values at t_0..t_nt
   double* gR = nullptr;   // right Dirichlet values

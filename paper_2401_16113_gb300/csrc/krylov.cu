@@ -1,7 +1,8 @@
 // Operator, right-hand side and FGMRES(m) for the CN all-at-once system on GB300.
 //
 //   k_build_coef  (1/2) tau A(t_{k+1/2}) for Black-Scholes (constant or local volatility),
-//                 3-point central differences on S_i = i h; FP64.
+//                 3-point central differences on S_i = i h; FP64. The diagonal is stored as
+//                 1 + (1/2) tau a_ii (the matvec's form y_t = 2 x_t - (I + A~_t/2)(x_t + x_{t-1})).
 //   k_rhs         b = xi + tau f (Eq. 2.2).
 //   k_matvec      y = M x, block-bidiagonal M = B1 (x) I - B2 (x) A~ (Eq. 2.2; Eq. 5.8 form for
 //                 time-dependent A): y_t = (x_t - x_{t-1}) - (1/2) A~_t (x_t + x_{t-1}), FP64;
@@ -63,7 +64,7 @@ __global__ void k_build_coef(double* __restrict__ L, double* __restrict__ D, dou
     const double diff = 0.5 * sig * sig * S * S / (h * h);
     const double conv = 0.5 * r * S / h;
     L[e] = half_tau * (diff - conv);
-    D[e] = half_tau * (-2.0 * diff - r);
+    D[e] = 1.0 + half_tau * (-2.0 * diff - r);  // diagonal of I + (1/2) tau A
     U[e] = half_tau * (diff + conv);
   }
 }
@@ -85,7 +86,7 @@ __global__ void k_rhs(double* __restrict__ b, int nx, int nt, const double* __re
         const double S = h * (double)(j + 1);
         return payoff == AAO_PUT ? fmax(K - S, 0.0) : fmax(S - K, 0.0);
       };
-      double xi = u0(i) + D[i] * u0(i);
+      double xi = D[i] * u0(i);  // D holds the diagonal of I + (1/2) tau A
       if (i > 0) xi += L[i] * u0(i - 1);
       if (i < nx - 1) xi += U[i] * u0(i + 1);
       val += xi;
@@ -606,9 +607,9 @@ int launch_matvec(Handle& h, const void* x, bool x_is_float, double* y, const do
   // x once, coefficients (3 per row of the time-dependent operator), y, b and V_q if present
   const double bytes = nn * (x_is_float ? 4.0 : 8.0) + 3.0 * 8.0 * (double)h.nx * h.coef_rows + nn * 8.0 +
                        (b ? nn * 8.0 : 0.0) + (V ? nn * 8.0 * nd : 0.0);
-  // per unknown: s and d (2 adds), three FMAs; residual: b - (1) and r.r (FMA), b.b (FMA);
-  // projections: nd FMAs
-  const double flops = nn * (2.0 + 6.0 + (b ? 3.0 : 0.0) + (b && with_bnorm ? 2.0 : 0.0) + (V ? 2.0 * nd : 0.0));
+  // per unknown, as executed: s = x_t + x_{t-1} (1 add; 2 x_t is an exponent increment), three
+  // FMAs; residual: b - 2 x_t (1) and r.r (FMA), b.b (FMA); projections: nd FMAs
+  const double flops = nn * (1.0 + 6.0 + (b ? 3.0 : 0.0) + (b && with_bnorm ? 2.0 : 0.0) + (V ? 2.0 * nd : 0.0));
   if (x_is_float) return matvec_t<float>(h, (const float*)x, y, b, V, nd, m, bytes, flops, with_bnorm, yf);
   return matvec_t<double>(h, (const double*)x, y, b, V, nd, m, bytes, flops, with_bnorm, yf);
 }

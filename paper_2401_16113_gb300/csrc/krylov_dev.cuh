@@ -20,7 +20,7 @@ enum : int {
   S_D1 = 0,       // raw first-pass projections V_i . w
   S_D2 = 128,     // raw second-pass projections
   S_SIG = 256,    // sigma_i = 1 / ||V_i||, i = 0..m
-  S_WN2 = 330,    // ||w||^2 before orthogonalisation
+  // slot 330 unused: ||w||^2 before orthogonalisation is recovered from S_WP2 and the projections
   S_WP2 = 331,    // ||w'||^2 after the last pass
   S_EST = 332,    // |g_{j+1}| (residual estimate)
   S_HN = 333,     // h_{j+1,j}
@@ -188,10 +188,12 @@ __device__ inline void givens_column_staged(double* __restrict__ scal, int j, do
 // One work item of the tiled matvec y = M x: this warp's kMvCols = 30 output columns
 // [o0, o0 + 30) over time levels [t0, t1), keeping level t-1 in registers. Lane L holds column
 // o0 - 1 + L (lanes 0 and 31 are the halo), so the spatial neighbours of s = x_t + x_{t-1} come
-// from lane shuffles with no FP64 work of their own. Five FP64 operations per unknown:
-//  y_t,i = (x_t - x_{t-1})_i - [L s_{i-1} + D s_i + U s_{i+1}], (L, D, U) = tau/2 A_t.
-// MODE 0: y only. MODE 1: y = b - M x, acc[0] += y.y, and the FP32 copy yf if given. MODE 3: as
-// MODE 1, and acc[1] += b.b.
+// from lane shuffles with no FP64 work of their own. With (L, D - 1, U) = tau/2 A_t and
+// x_t - x_{t-1} = 2 x_t - s,
+//  y_t,i = (x_t - x_{t-1})_i - [tau/2 A_t s]_i = 2 x_t,i - [L s_{i-1} + D s_i + U s_{i+1}],
+// four FP64 operations per unknown (one add, three FMAs): 2 x is formed by integer bit operations.
+// MODE 0: y only. MODE 1: y = b - M x = (b - 2 x_t) + [...], acc[0] += y.y, and the FP32 copy yf
+// if given. MODE 3: as MODE 1, and acc[1] += b.b.
 // MODE 2: acc[q] += V_q . y (q < ND, a compile-time count so that no predicated-off FP64
 // instruction is issued), and acc[ND] += y.y when the caller has room for it (NA > ND).
 constexpr int kMvCols = 30;
@@ -210,10 +212,11 @@ __device__ __forceinline__ void matvec_item(const IN* __restrict__ x, double* __
   double xp = 0.0;
   if (t0 > 0 && in) xp = ld(x + (size_t)(t0 - 1) * nx + i);
   // the loads of row t + 1 are issued before row t is computed (one row in flight ahead)
-  double xn = 0.0, ln = 0.0, dn = 0.0, un = 0.0, bn = 0.0, vn[NVQ > 0 ? NVQ : 1];
+  IN xn = IN(0);
+  double ln = 0.0, dn = 0.0, un = 0.0, bn = 0.0, vn[NVQ > 0 ? NVQ : 1];
   auto fetch = [&](int t) {
     const size_t r = (size_t)t * nx;
-    xn = in ? ld(x + r + i) : 0.0;
+    xn = in ? __ldg(x + r + i) : IN(0);
     if (act) {
       const size_t c = rows == 1 ? (size_t)i : r + i;
       ln = __ldg(L + c);
@@ -227,7 +230,8 @@ __device__ __forceinline__ void matvec_item(const IN* __restrict__ x, double* __
   if (t0 < t1) fetch(t0);
   for (int t = t0; t < t1; ++t) {
     const size_t r = (size_t)t * nx;
-    const double xc = xn, lc = ln, dc = dn, uc = un, bc = bn;
+    const double xc = widen(xn), x2 = twice(xn);
+    const double lc = ln, dc = dn, uc = un, bc = bn;
     double vc[NVQ > 0 ? NVQ : 1];
 #pragma unroll
     for (int q = 0; q < NVQ; ++q) vc[q] = vn[q];
@@ -247,17 +251,21 @@ __device__ __forceinline__ void matvec_item(const IN* __restrict__ x, double* __
         continue;
       }
     }
-    const double s = xc + xp, d = xc - xp;
+    const double s = xc + xp;
     const double sl = __shfl_up_sync(0xffffffffu, s, 1);
     const double sr = __shfl_down_sync(0xffffffffu, s, 1);
     if (act) {
-      double v = fma(-lc, sl, d);
-      v = fma(-dc, s, v);
-      v = fma(-uc, sr, v);
+      double v;
       if constexpr (RES) {
-        v = bc - v;
+        v = fma(dc, s, bc - x2);
+        v = fma(lc, sl, v);
+        v = fma(uc, sr, v);
         acc[0] = fma(v, v, acc[0]);
         if constexpr (MODE == 3) acc[NA - 1] = fma(bc, bc, acc[NA - 1]);
+      } else {
+        v = fma(-dc, s, x2);
+        v = fma(-lc, sl, v);
+        v = fma(-uc, sr, v);
       }
       y[r + i] = v;
       if constexpr (RES) {

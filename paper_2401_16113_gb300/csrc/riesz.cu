@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(256) k_rz_matvec(const IN* __restrict__ x, dou
                                                    const double* __restrict__ V, size_t vstride,
                                                    double* __restrict__ part, double* __restrict__ scal,
                                                    unsigned int* __restrict__ counter, int m) {
-  constexpr int NA = MODE == 2 ? ND + 1 : 1;
+  constexpr int NA = MODE == 2 ? ND : 1;
   extern __shared__ __align__(16) unsigned char smraw[];
   double2* data = reinterpret_cast<double2*>(smraw);
   double2* stw = data + n2;
@@ -90,7 +90,6 @@ __global__ void __launch_bounds__(256) k_rz_matvec(const IN* __restrict__ x, dou
       if (MODE == 2) {
 #pragma unroll
         for (int q = 0; q < ND; ++q) acc[q] = fma(__ldg(V + (size_t)q * vstride + e), v, acc[q]);
-        acc[ND] = fma(v, v, acc[ND]);
       }
     }
   }
@@ -122,7 +121,7 @@ __global__ void __launch_bounds__(256) k_rz_matvec(const IN* __restrict__ x, dou
       double s = 0.0;
       for (unsigned bb = 0; bb < gridDim.x; ++bb) s += __ldcg(part + (size_t)bb * kPartLd + q);
       if (MODE == 2) {
-        scal[q < ND ? S_D1 + q : S_WN2] = s;
+        scal[S_D1 + q] = s;
       } else {
         scal[S_BETA2] = s;
         const double beta = sqrt(s);
@@ -499,7 +498,7 @@ int riesz_matvec(Handle& h, const void* x, bool x_is_float, double* y, const dou
   const double bytes = nn * (x_is_float ? 4.0 : 8.0) + nn * 8.0 + (b ? nn * 8.0 : 0.0) + (V ? nn * 8.0 * nd : 0.0);
   // two FP64 FFTs of length N2 per pair of time levels (5 N2 log2 N2 flops each), the product (6 N2)
   const double flops = (double)grid * (2.0 * 5.0 * h.rz_n2 * h.rz_log2n2 + 6.0 * h.rz_n2) +
-                       nn * (3.0 + (b ? 3.0 : 0.0) + (V ? 2.0 * (nd + 1) : 0.0));
+                       nn * (3.0 + (b ? 3.0 : 0.0) + (V ? 2.0 * nd : 0.0));
   ProfScope ps(AAO_K_MATVEC, h.stream, bytes, flops);
 #define RZ(IN, MODE, ND)                                                                                     \
   do {                                                                                                       \

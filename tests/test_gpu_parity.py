@@ -80,6 +80,25 @@ def test_matvec_matches_oracle(aao, nx, nt):
         h.close()
 
 
+@pytest.mark.parametrize("scale", [1.0, 1e-310])
+def test_matvec_zeros_and_subnormals(aao, scale):
+    # the kernel forms 2 x_t by bit operations: exact zeros (both signs) mixed into the input, and
+    # an input entirely in the FP64 subnormal range (scale 1e-310), where 2 x is a shift of the
+    # magnitude bits, must give the oracle's product
+    nx, nt = 67, 32
+    for p in problems(nx, nt):
+        h = aao.aao_create(p)
+        x = W.random_vector(nx * nt, seed=11) * scale
+        x[::3] = 0.0
+        x[1::7] = -0.0
+        x[5 * nx:7 * nx] = 0.0
+        y = torch.empty(nx * nt, dtype=torch.float64, device="cuda")
+        aao.aao_matvec(h, dev(x), y)
+        ref = O.matvec(p, x)
+        assert relmax(host(y), ref) <= 1e-13, p
+        h.close()
+
+
 def precond_bound(p):
     u = U32 if p["precision"] == "mixed" else U64
     return 20.0 * u * math.log2(2 * p["nt"]) / p["alpha"]
