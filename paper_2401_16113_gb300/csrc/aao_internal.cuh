@@ -211,6 +211,10 @@ struct Handle {
   // transposed ([j][l]) in one buffer of 3 * tri_ch * tri_T reals (precision of the preconditioner)
   void* tri = nullptr;
   int tri_T = 0, tri_ch = 0;
+  // factors of step (b) per bin (complex, precision of the preconditioner): pivots and fill-in
+  // [K][tri_T * tri_ch], reduction multipliers [K][2 lgT + 1][tri_T]; null where the
+  // partition method does not fit in shared memory
+  void *tri_fp = nullptr, *tri_fv = nullptr, *tri_fpcr = nullptr;
 
   // Riesz operator (dense Toeplitz): circulant-embedding spectrum (scaled by tau/2 / N2), its
   // twiddles, (tau/2) first column / row / left-exterior coefficients, LU factors of step (b)
@@ -240,6 +244,8 @@ int build_tables(Handle& h);
 int launch_precond(Handle& h, const double* v, void* z, bool z_is_float, const double* in_scale = nullptr,
                    const float* vf = nullptr);
 int tune_precond(Handle& h);
+// factors of the partitioned tridiagonal solves of step (b) (needs tri, mu/muf)
+int build_tri_factors(Handle& h);
 int riesz_build(Handle& h);
 int riesz_matvec(Handle& h, const void* x, bool x_is_float, double* y, const double* b, const double* V, int nd, int m);
 int riesz_rhs(Handle& h, double* b);

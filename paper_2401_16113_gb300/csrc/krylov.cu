@@ -511,6 +511,7 @@ int build_tables(Handle& h) {
   AAO_TRY(up(&h.muf, muf)); AAO_TRY(up(&h.il2f, il2f)); AAO_TRY(up(&h.twf, twf));
   AAO_TRY(up(&h.lam, lam)); AAO_TRY(up(&h.ilam, ilam));
   AAO_TRY(up(&h.lamf, lamf)); AAO_TRY(up(&h.ilamf, ilamf));
+  if (h.tri) AAO_TRY(build_tri_factors(h));
 
   const size_t csz = h.mixed ? sizeof(float2) : sizeof(double2);
   AAO_TRY_CUDA(cudaMalloc(&h.spec, csz * (size_t)K * h.pitch));
@@ -537,7 +538,8 @@ int build_tables(Handle& h) {
 void free_handle(Handle& h) {
   void* bufs[] = {h.mL, h.mD, h.mU, h.gL, h.gR, h.pL, h.pD, h.pU, h.pLf, h.pDf, h.pUf, h.mu, h.il2, h.tw,
                   h.muf, h.il2f, h.twf, h.lam, h.ilam, h.lamf, h.ilamf, h.spec, h.V, h.Z, h.w, h.scal, h.part,
-                  h.counter, h.rz_chat, h.rz_tw, h.rz_hcol, h.rz_hrow, h.rz_hcl, h.rz_lu, h.rz_dinv, h.tri, h.Vf};
+                  h.counter, h.rz_chat, h.rz_tw, h.rz_hcol, h.rz_hrow, h.rz_hcl, h.rz_lu, h.rz_dinv, h.tri, h.Vf, h.tri_fp,
+                  h.tri_fv, h.tri_fpcr};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (h.host_scal) cudaFreeHost(h.host_scal);

@@ -7,10 +7,15 @@
 //               transform, radix 16/16/8 with 16 values per thread in registers for nt >= 128
 //               (radix 4/2 in shared memory below). Output: bins k = 0..nt/2 of every
 //               column, frequency-major [k][x] (the layout step (b) reads contiguously).
-//   k_tridiag   step (b): for each bin k one warp solves the complex-shifted tridiagonal system
-//               (lambda_{1,k} I - lambda_{2,k} A~) z2_k = z1_k, A~ = tau * Abar, by a partitioned
-//               Thomas sweep per lane (chunks of ceil(nx/32) rows) and parallel cyclic reduction
-//               of the 64-row interface system across the warp with shuffles.
+//   k_tridiag_part
+//               step (b): for each bin k, T threads solve the complex-shifted tridiagonal system
+//               (lambda_{1,k} I - lambda_{2,k} A~) z2_k = z1_k, A~ = tau * Abar, by the partition
+//               method (chunks of ceil(nx/T) rows per thread, parallel cyclic reduction of the
+//               T-row interface system in shared memory). The matrix-only parts (pivots,
+//               fill-in, reduction multipliers) are factored once per bin when the handle is built
+//               (k_tridiag_part_factor); an apply carries only the right-hand side. k_tridiag
+//               (one bin per group of lanes, coefficients recomputed) serves the shapes whose
+//               rows do not fit in shared memory.
 //   k_fft_inv   step (c): complex-to-real inverse FFT along t (bins nt/2+1.. are the conjugates,
 //               Remark 1) fused with Lambda_alpha^{-1} and the 1/nt normalisation.
 //
@@ -69,6 +74,44 @@ int default_tile(int nx, int N, size_t rsize) {
   return P;
 }
 
+// partition-method layout of step (b): lgT, the odd chunk stride cs, coefficient staging and the
+// bins per CTA G; false when one bin's rows do not fit in shared memory
+struct TriPart {
+  int lgT, cs, G;
+  bool staged;
+  size_t smem;
+};
+bool tri_part_layout(const Handle& h, size_t rsize, TriPart& t) {
+  if (!h.tri || h.tri_T <= 0) return false;
+  const int T = h.tri_T, ch = h.tri_ch;
+  t.lgT = 0;
+  while ((1 << t.lgT) < T) ++t.lgT;
+  if (t.lgT > kTriMaxLgT) return false;
+  t.cs = (ch & 1) ? ch + 2 : ch + 1;
+  if (tri_part_bytes(1, T, t.cs, rsize, false) > kTriSmemMax) return false;
+  t.staged = tri_part_bytes(1, T, t.cs, rsize, true) <= kTriSmemMax;
+  t.G = 512 / T;
+  while (t.G > 1 && tri_part_bytes(t.G, T, t.cs, rsize, t.staged) > kTriSmemMax) --t.G;
+  t.smem = tri_part_bytes(t.G, T, t.cs, rsize, t.staged);
+  return true;
+}
+
+template <typename R>
+int tri_factors_t(Handle& h, int lgT) {
+  using C = C_t<R>;
+  const int T = h.tri_T, ch = h.tri_ch, K = h.K;
+  const size_t rows = (size_t)T * ch;
+  AAO_TRY_CUDA(cudaMalloc(&h.tri_fp, sizeof(C) * rows * K));
+  AAO_TRY_CUDA(cudaMalloc(&h.tri_fv, sizeof(C) * rows * K));
+  AAO_TRY_CUDA(cudaMalloc(&h.tri_fpcr, sizeof(C) * tri_fact_pcr_elems(lgT, T) * K));
+  const C* mu = (sizeof(R) == 4) ? (const C*)h.muf : (const C*)h.mu;
+  k_tridiag_part_factor<R><<<K, T, 5 * T * sizeof(C), h.stream>>>(
+      h.nx, ch, lgT, reinterpret_cast<const R*>(h.tri), mu, reinterpret_cast<C*>(h.tri_fp),
+      reinterpret_cast<C*>(h.tri_fv), reinterpret_cast<C*>(h.tri_fpcr));
+  AAO_CHECK_LAUNCH();
+  return AAO_OK;
+}
+
 template <typename R>
 int run_precond(Handle& h, const double* v, void* z, bool z_is_float, const double* in_scale, const float* vf) {
   using C = C_t<R>;
@@ -101,31 +144,26 @@ int run_precond(Handle& h, const double* v, void* z, bool z_is_float, const doub
   if (h.p.op == AAO_OP_RIESZ) {
     // step (b) with the dense Toeplitz operator: LU factors from aao_create
     AAO_TRY(riesz_solve_bins(h, spec));
-  } else if (h.tri && tri_part_bytes(1, h.tri_T, (h.tri_ch & 1) ? h.tri_ch + 2 : h.tri_ch + 1, sizeof(R), false) <=
-                          kTriSmemMax) {
-    // step (b): partition method, G bins of tri_T = 2^lgT threads per CTA (as many as shared
-    // memory holds, at most 512 threads); the coefficients are staged in shared memory when
-    // they fit beside one bin, else read from global memory
-    const int T = h.tri_T, ch = h.tri_ch;
-    int lgT = 0;
-    while ((1 << lgT) < T) ++lgT;
-    const int cs = (ch & 1) ? ch + 2 : ch + 1;  // odd chunk stride: conflict-free shared memory
-    const bool staged = tri_part_bytes(1, T, cs, sizeof(R), true) <= kTriSmemMax;
-    int G = 512 / T;
-    while (G > 1 && tri_part_bytes(G, T, cs, sizeof(R), staged) > kTriSmemMax) --G;
-    const size_t smem2 = tri_part_bytes(G, T, cs, sizeof(R), staged);
-    const C* mu = (sizeof(R) == 4) ? (const C*)h.muf : (const C*)h.mu;
+  } else if (TriPart tp; h.tri_fp && tri_part_layout(h, sizeof(R), tp)) {
+    // step (b): partition method with the per-bin factors built with the handle, G bins of
+    // tri_T = 2^lgT threads per CTA
+    const int ch = h.tri_ch;
     const C* il2 = (sizeof(R) == 4) ? (const C*)h.il2f : (const C*)h.il2;
     const R* tri = reinterpret_cast<const R*>(h.tri);
-    ProfScope ps(AAO_K_TRIDIAG, h.stream, 2.0 * nsp);
-    if (staged) {
-      AAO_TRY(ensure_smem((const void*)k_tridiag_part<R, true>, smem2));
-      AAO_TRY_CUDA(launch_pdl(k_tridiag_part<R, true>, (h.K + G - 1) / G, G * T, smem2, h.stream, spec, nx, h.K,
-                              h.pitch, ch, cs, lgT, tri, mu, il2));
+    const C* fp = reinterpret_cast<const C*>(h.tri_fp);
+    const C* fv = reinterpret_cast<const C*>(h.tri_fv);
+    const C* fpcr = reinterpret_cast<const C*>(h.tri_fpcr);
+    const int T = h.tri_T;
+    // right-hand side in and out, the pivots and the fill-in (the multipliers are ~T/ch smaller)
+    ProfScope ps(AAO_K_TRIDIAG, h.stream, 2.0 * nsp + 2.0 * (double)h.K * T * ch * sizeof(C));
+    if (tp.staged) {
+      AAO_TRY(ensure_smem((const void*)k_tridiag_part<R, true>, tp.smem));
+      AAO_TRY_CUDA(launch_pdl(k_tridiag_part<R, true>, (h.K + tp.G - 1) / tp.G, tp.G * T, tp.smem, h.stream, spec,
+                              nx, h.K, h.pitch, ch, tp.cs, tp.lgT, tri, fp, fv, fpcr, il2));
     } else {
-      AAO_TRY(ensure_smem((const void*)k_tridiag_part<R, false>, smem2));
-      AAO_TRY_CUDA(launch_pdl(k_tridiag_part<R, false>, (h.K + G - 1) / G, G * T, smem2, h.stream, spec, nx, h.K,
-                              h.pitch, ch, cs, lgT, tri, mu, il2));
+      AAO_TRY(ensure_smem((const void*)k_tridiag_part<R, false>, tp.smem));
+      AAO_TRY_CUDA(launch_pdl(k_tridiag_part<R, false>, (h.K + tp.G - 1) / tp.G, tp.G * T, tp.smem, h.stream, spec,
+                              nx, h.K, h.pitch, ch, tp.cs, tp.lgT, tri, fp, fv, fpcr, il2));
     }
   } else {
   // step (b): threads per bin T (multiple of 32, <= 512), chunk ch <= CH rows per thread
@@ -184,6 +222,13 @@ int launch_precond(Handle& h, const double* v, void* z, bool z_is_float, const d
 // FFT tile autotuner: time the whole apply for every admissible tile width 2P (P = 1, 2, 4, ...)
 // on this problem's sizes and keep the fastest. Every tile width computes identical results
 // (each column's transform runs the same operations in the same order); only speed differs.
+int build_tri_factors(Handle& h) {
+  const size_t rsize = h.mixed ? sizeof(float) : sizeof(double);
+  TriPart tp;
+  if (!tri_part_layout(h, rsize, tp)) return AAO_OK;  // the per-bin fallback solver needs none
+  return h.mixed ? tri_factors_t<float>(h, tp.lgT) : tri_factors_t<double>(h, tp.lgT);
+}
+
 int tune_precond(Handle& h) {
   const size_t rs = h.mixed ? 4 : 8;
   const int pmax = max_tile(h.nt, rs);

@@ -664,25 +664,36 @@ __global__ void __launch_bounds__(512) k_tridiag(C_t<R>* __restrict__ spec, int 
 
 
 // ------------------------------------------------------------------ partitioned tridiagonal solve
-// step (b) by the partition method, T = 2^lgT >= 32 threads per bin and G bins per
-// CTA: thread l of a bin owns the chunk of rows [l ch, (l+1) ch), rows >= nx being identity rows,
-// and keeps its per-row data in shared memory (layout l*cs + j, odd stride cs):
-//  (1) downward Thomas elimination with the previous chunk's last unknown y_{l-1} as a parameter,
-//      x_i + c'_i x_{i+1} = d'_i + v_i y_{l-1}, storing (c', d', v);
+// step (b) by the partition method, T = 2^lgT >= 32 threads per bin and G bins per CTA: thread l
+// of a bin owns the chunk of rows [l ch, (l+1) ch), rows >= nx being identity rows. For the
+// system (mu_k I - Abar) x = d of bin k (a_i, c_i the off-diagonals as stored, dg_i the diagonal):
+//  (1) downward elimination inside the chunk, the previous chunk's last unknown y_{l-1} kept as a
+//      parameter: x_i + c'_i x_{i+1} = d'_i + v_i y_{l-1}, with p_i = 1 / (mu_k - dg_i - a_i c'_{i-1}),
+//      c'_i = c_i p_i, d'_i = (d_i - a_i d'_{i-1}) p_i, v_i = -a_i v_{i-1} p_i (v = 1 before the chunk);
 //  (2) an upward recurrence writing the chunk's first unknown as x_s = G + H y_{l-1} + J y_l,
 //      y_l the chunk's last unknown;
 //  the T last-row unknowns then satisfy a tridiagonal system (row e_l of (1) with x_{e+1} taken
-//  from chunk l+1's (G, H, J)), solved by parallel cyclic reduction in shared memory;
+//  from chunk l+1's (G, H, J)), solved by parallel cyclic reduction;
 //  (3) upward back substitution x_i = d'_i + v_i y_{l-1} - c'_i x_{i+1} from x_e = y_l.
-// The right-hand sides and the coefficients a_i = -lo_i, dg_i = di_i, c_i = -up_i (chunk-
-// transposed tables [j][l] built with the handle) are staged by asynchronous copies, all in
-// flight at once; the coefficients are shared by the CTA's G bins. The 1/lambda_2 scaling of the
-// right-hand side is applied to the solution (the system is linear).
-__host__ __device__ __forceinline__ size_t tri_part_bin_elems(int T, int cs) { return 3 * (size_t)T * cs + 4 * (size_t)T; }
+// Everything that depends on the matrix alone -- the pivots p_i, the fill-in v_i, H and J, the
+// reduced system and the multipliers of every reduction level -- is the same for every apply, so
+// k_tridiag_part_factor computes it once per bin when the handle is built. An apply carries only
+// the right-hand side through the recurrences: d' (one real FMA pair and a complex product per
+// row), G, the reduced right-hand side and the back substitution.
+// Factor tables, per bin k: p and v at [k][i] (i = l ch + j < T ch, identity rows included), and
+// [k][2 s][l], [k][2 s + 1][l] the level-s multipliers (s < lgT), [k][2 lgT][l] 1 / the final
+// reduced diagonal. An apply stages the bin's p and v rows (before waiting for the previous kernel:
+// programmatic dependent launch), its right-hand side and the a and c planes of the coefficient
+// table (shared by the CTA's G bins) in shared memory with asynchronous copies, all in flight at
+// once; thread l keeps rows l*cs + j (odd stride cs: conflict-free). G bins per CTA fill shared
+// memory (at most 512 threads).
+constexpr int kTriMaxLgT = 9;  // T <= 512
+__host__ __device__ __forceinline__ size_t tri_fact_pcr_elems(int lgT, int T) { return (size_t)(2 * lgT + 1) * T; }
+__host__ __device__ __forceinline__ size_t tri_part_bin_elems(int T, int cs) { return 3 * (size_t)T * cs + 2 * (size_t)T; }
 __host__ __device__ __forceinline__ size_t tri_part_coef_bytes(int T, int cs, size_t rsize, bool staged) {
-  return staged ? (((3 * (size_t)T * cs * rsize) + 15) & ~(size_t)15) : 0;
+  return staged ? (((2 * (size_t)T * cs * rsize) + 15) & ~(size_t)15) : 0;
 }
-__host__ __device__ __forceinline__ size_t tri_part_bytes(int G, int T, int cs, size_t rsize, bool staged = true) {
+__host__ __device__ __forceinline__ size_t tri_part_bytes(int G, int T, int cs, size_t rsize, bool staged) {
   return tri_part_coef_bytes(T, cs, rsize, staged) + (size_t)G * tri_part_bin_elems(T, cs) * 2 * rsize;
 }
 
@@ -708,139 +719,197 @@ __device__ __forceinline__ void cp_async(void* smem_dst, const void* gmem_src) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// STAGED = false (large Nx, where the coefficients do not fit beside the bin's rows): the downward
-// sweep reads the chunk-transposed coefficient table from global memory, one row ahead.
+// Factor kernel: one bin per CTA of T threads (shared memory: 5 T complex). The coefficient table
+// is chunk-transposed: planes a, dg, c of T ch reals each, entry (j, l) at j T + l.
+template <typename R>
+__global__ void __launch_bounds__(512) k_tridiag_part_factor(int nx, int ch, int lgT, const R* __restrict__ tri,
+                                                             const C_t<R>* __restrict__ mu, C_t<R>* __restrict__ fp,
+                                                             C_t<R>* __restrict__ fv, C_t<R>* __restrict__ fpcr) {
+  using C = C_t<R>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int T = 1 << lgT, l = threadIdx.x, k = blockIdx.x;
+  C* pa = reinterpret_cast<C*>(smraw);
+  C* pb = pa + T;
+  C* pc = pb + T;
+  C* ph = pc + T;
+  C* pj = ph + T;
+  const C zero = cmk<C>(0, 0), one = cmk<C>(1, 0);
+  const C muk = mu[k];
+  const size_t plane = (size_t)T * ch, rows = (size_t)T * ch;
+  C* P = fp + (size_t)k * rows + (size_t)l * ch;
+  C* Vv = fv + (size_t)k * rows + (size_t)l * ch;
+  const int nrow = nx - l * ch;
+  C cpr = zero, vpr = one;
+  for (int j = 0; j < ch; ++j) {
+    const size_t o = (size_t)j * T + l;
+    const R a = tri[o], dg = tri[plane + o], c = tri[2 * plane + o];
+    const C b = j < nrow ? cmk<C>(muk.x - dg, muk.y) : one;
+    const C inv = crcp<R>(cmk<C>(b.x - a * cpr.x, b.y - a * cpr.y));
+    cpr = cscale(inv, c);
+    vpr = cmul(cscale(vpr, -a), inv);
+    P[j] = inv;
+    Vv[j] = vpr;
+  }
+  // (2) H and J (this thread re-reads its own stores)
+  C Hs = zero, Js = one;
+  for (int j = ch - 2; j >= 0; --j) {
+    const C cj = cscale(P[j], tri[2 * plane + (size_t)j * T + l]);
+    Hs = csub(Vv[j], cmul(cj, Hs));
+    Js = cscale(cmul(cj, Js), (R)-1);
+  }
+  ph[l] = Hs;
+  pj[l] = Js;
+  __syncthreads();
+  const C Hn = l + 1 < T ? ph[l + 1] : zero, Jn = l + 1 < T ? pj[l + 1] : zero;
+  // row l of the reduced system: -v_e y_{l-1} + (1 + c'_e H_{l+1}) y_l + c'_e J_{l+1} y_{l+1}
+  pa[l] = cscale(vpr, (R)-1);
+  pb[l] = cadd(one, cmul(cpr, Hn));
+  pc[l] = cmul(cpr, Jn);
+  __syncthreads();
+  C* F = fpcr + (size_t)k * tri_fact_pcr_elems(lgT, T) + l;
+  for (int s = 0; s < lgT; ++s) {
+    const int delta = 1 << s;
+    C lA = zero, lB = one, lC = zero, hA = zero, hB = one, hC = zero;
+    if (l - delta >= 0) { lA = pa[l - delta]; lB = pb[l - delta]; lC = pc[l - delta]; }
+    if (l + delta < T) { hA = pa[l + delta]; hB = pb[l + delta]; hC = pc[l + delta]; }
+    const C k1 = l - delta >= 0 ? cmul(pa[l], crcp<R>(lB)) : zero;
+    const C k2 = l + delta < T ? cmul(pc[l], crcp<R>(hB)) : zero;
+    const C nA = cscale(cmul(lA, k1), (R)-1);
+    const C nC = cscale(cmul(hC, k2), (R)-1);
+    const C nB = csub(csub(pb[l], cmul(lC, k1)), cmul(hA, k2));
+    F[(size_t)(2 * s) * T] = k1;
+    F[(size_t)(2 * s + 1) * T] = k2;
+    __syncthreads();
+    pa[l] = nA; pb[l] = nB; pc[l] = nC;
+    __syncthreads();
+  }
+  F[(size_t)(2 * lgT) * T] = crcp<R>(pb[l]);
+}
+
+// Apply kernel: G bins of T threads per CTA. STAGED = false (large Nx, where the coefficient planes
+// do not fit beside one bin): the sweeps read them from global memory, one row ahead.
 template <typename R, bool STAGED>
 __global__ void __launch_bounds__(512) k_tridiag_part(C_t<R>* __restrict__ spec, int nx, int K, int pitch, int ch,
                                                       int cs, int lgT, const R* __restrict__ tri,
-                                                      const C_t<R>* __restrict__ mu, const C_t<R>* __restrict__ il2) {
+                                                      const C_t<R>* __restrict__ fp, const C_t<R>* __restrict__ fv,
+                                                      const C_t<R>* __restrict__ fpcr,
+                                                      const C_t<R>* __restrict__ il2) {
   using C = C_t<R>;
   extern __shared__ __align__(16) unsigned char smraw[];
-  pdl_sync();
   const int T = 1 << lgT, G = blockDim.x >> lgT;
   const int g = threadIdx.x >> lgT, l = threadIdx.x & (T - 1);
   const int k = blockIdx.x * G + g;
   const bool valid = k < K;
-  R* sa = reinterpret_cast<R*>(smraw);  // staged coefficients, layout l*cs + j
-  R* sdg = sa + (size_t)T * cs;
-  R* sc = sdg + (size_t)T * cs;
+  const int kk = valid ? k : 0;
+  R* sa = reinterpret_cast<R*>(smraw);
+  R* sc = sa + (size_t)T * cs;
   const size_t coef = tri_part_coef_bytes(T, cs, sizeof(R), STAGED);
-  C* sd = reinterpret_cast<C*>(smraw + coef) + (size_t)g * tri_part_bin_elems(T, cs);  // rhs -> d' -> x
-  C* scp = sd + (size_t)T * cs;  // c'
-  C* sv = scp + (size_t)T * cs;  // v
-  C* pa = sv + (size_t)T * cs;   // reduced system
-  C* pb = pa + T;
-  C* pc = pb + T;
-  C* pd = pc + T;
-  const C zero = cmk<C>(0, 0), one = cmk<C>(1, 0);
-  C* row = spec + (size_t)(valid ? k : 0) * pitch;
-
-  // staging: coefficients by the whole CTA (table row j = chunk row j of every thread), right-
-  // hand side by the bin's threads (element i = L ch + j)
+  C* sd = reinterpret_cast<C*>(smraw + coef) + (size_t)g * tri_part_bin_elems(T, cs);
+  C* sp = sd + (size_t)T * cs;
+  C* sv = sp + (size_t)T * cs;
+  C* pd = sv + (size_t)T * cs;
+  C* pg = pd + T;
+  const C zero = cmk<C>(0, 0);
+  C* row = spec + (size_t)kk * pitch;
+  const size_t rows = (size_t)T * ch, plane = (size_t)T * ch;
+  const C* gp = fp + (size_t)kk * rows;
+  const C* gv = fv + (size_t)kk * rows;
+  C m1[kTriMaxLgT], m2[kTriMaxLgT];
+  const C* F = fpcr + (size_t)kk * tri_fact_pcr_elems(lgT, T) + l;
+#pragma unroll
+  for (int s = 0; s < kTriMaxLgT; ++s) {
+    m1[s] = s < lgT ? __ldg(F + (size_t)(2 * s) * T) : zero;
+    m2[s] = s < lgT ? __ldg(F + (size_t)(2 * s + 1) * T) : zero;
+  }
+  const C rb = __ldg(F + (size_t)(2 * lgT) * T);
   if constexpr (STAGED) {
-    for (int e = threadIdx.x; e < 3 * ch * T; e += blockDim.x) {
-      const int jq = e >> lgT, L = e & (T - 1);  // jq = q ch + j
-      const int q = jq >= 2 * ch ? 2 : (jq >= ch ? 1 : 0), j = jq - q * ch;
-      cp_async<sizeof(R)>(sa + (size_t)q * T * cs + L * cs + j, tri + e);
+    for (int e = threadIdx.x; e < 2 * ch * T; e += blockDim.x) {
+      const int jq = e >> lgT, L = e & (T - 1);
+      const int q = jq >= ch ? 1 : 0, j = jq - q * ch;
+      cp_async<sizeof(R)>(sa + (size_t)q * T * cs + L * cs + j, tri + (q == 0 ? 0 : 2 * plane) + (size_t)j * T + L);
     }
   }
-  const int dL = T / ch, dj = T - dL * ch;  // i += T moves (L, j) by (dL, dj), dj < ch
+  const int dL = T / ch, dj = T - dL * ch;
   for (int L = l / ch, j = l - (l / ch) * ch; L < T;) {
     const int i = L * ch + j;
-    if (valid && i < nx) cp_async<sizeof(C)>(sd + L * cs + j, row + i);
-    else sd[L * cs + j] = zero;
+    const int o = L * cs + j;
+    cp_async<sizeof(C)>(sp + o, gp + i);
+    cp_async<sizeof(C)>(sv + o, gv + i);
+    j += dj;
+    L += dL;
+    if (j >= ch) { j -= ch; ++L; }
+  }
+  pdl_sync();
+  for (int L = l / ch, j = l - (l / ch) * ch; L < T;) {
+    const int i = L * ch + j;
+    const int o = L * cs + j;
+    if (valid && i < nx) cp_async<sizeof(C)>(sd + o, row + i);
+    else sd[o] = zero;
     j += dj;
     L += dL;
     if (j >= ch) { j -= ch; ++L; }
   }
   cp_async_wait_all();
   __syncthreads();
-
-  const C muk = valid ? mu[k] : one;
   C* D = sd + l * cs;
-  C* CP = scp + l * cs;
-  C* V = sv + l * cs;
+  const C* Pp = sp + l * cs;
+  const C* Vv = sv + l * cs;
   const R* A = sa + l * cs;
-  const R* DG = sdg + l * cs;
   const R* CC = sc + l * cs;
-  // (1) downward elimination
-  C cpr = zero, dpr = zero, vpr = one;
-  const int nrow = nx - l * ch;  // rows j >= nrow are identity rows
-  const size_t plane = (size_t)T * ch;
-  auto coef_row = [&](int j, R& a, R& dg, R& c) {
-    if constexpr (STAGED) {
-      a = A[j];
-      dg = DG[j];
-      c = CC[j];
-    } else {
-      const size_t o = (size_t)j * T + l;
-      a = __ldg(tri + o);
-      dg = __ldg(tri + plane + o);
-      c = __ldg(tri + 2 * plane + o);
-    }
+  auto coef_a = [&](int j) -> R {
+    if constexpr (STAGED) return A[j];
+    else return __ldg(tri + (size_t)j * T + l);
   };
-  R an, dgn, cn;
-  coef_row(0, an, dgn, cn);
+  auto coef_c = [&](int j) -> R {
+    if constexpr (STAGED) return CC[j];
+    else return __ldg(tri + 2 * plane + (size_t)j * T + l);
+  };
+  C dpr = zero;
+  R an = coef_a(0);
   for (int j = 0; j < ch; ++j) {
-    const R a = an, c = cn, dgj = dgn;
-    if (j + 1 < ch) coef_row(j + 1, an, dgn, cn);
-    const C b = j < nrow ? cmk<C>(muk.x - dgj, muk.y) : one;
-    const C inv = crcp<R>(cmk<C>(b.x - a * cpr.x, b.y - a * cpr.y));
+    const R a = an;
+    if (j + 1 < ch) an = coef_a(j + 1);
     const C dj = D[j];
-    cpr = cscale(inv, c);
-    dpr = cmul(cmk<C>(dj.x - a * dpr.x, dj.y - a * dpr.y), inv);
-    vpr = cmul(cscale(vpr, -a), inv);
-    CP[j] = cpr;
+    dpr = cmul(cmk<C>(dj.x - a * dpr.x, dj.y - a * dpr.y), Pp[j]);
     D[j] = dpr;
-    V[j] = vpr;
   }
-  // (2) upward: x_s = G + H y_{l-1} + J y_l
-  C Gs = zero, Hs = zero, Js = one;
+  const C cpe = cscale(Pp[ch - 1], coef_c(ch - 1));
+  C Gs = zero;
+  R cn = ch >= 2 ? coef_c(ch - 2) : (R)0;
   for (int j = ch - 2; j >= 0; --j) {
-    const C cj = CP[j];
-    Gs = csub(D[j], cmul(cj, Gs));
-    Hs = csub(V[j], cmul(cj, Hs));
-    Js = cscale(cmul(cj, Js), (R)-1);
+    const R c = cn;
+    if (j > 0) cn = coef_c(j - 1);
+    Gs = csub(D[j], cmul(cscale(Pp[j], c), Gs));
   }
-  pa[l] = Gs;
-  pb[l] = Hs;
-  pc[l] = Js;
+  pg[l] = Gs;
   __syncthreads();
-  C Gn = zero, Hn = zero, Jn = zero;
-  if (l + 1 < T) {
-    Gn = pa[l + 1];
-    Hn = pb[l + 1];
-    Jn = pc[l + 1];
+  const C Gn = l + 1 < T ? pg[l + 1] : zero;
+  C cur = csub(dpr, cmul(cpe, Gn));
+  pd[l] = cur;
+  __syncthreads();
+#pragma unroll
+  for (int s = 0; s < kTriMaxLgT; ++s) {
+    if (s < lgT) {
+      const int delta = 1 << s;
+      const C lD = l - delta >= 0 ? pd[l - delta] : zero;
+      const C hD = l + delta < T ? pd[l + delta] : zero;
+      cur = csub(csub(cur, cmul(lD, m1[s])), cmul(hD, m2[s]));
+      __syncthreads();
+      pd[l] = cur;
+      __syncthreads();
+    }
   }
+  const C y = cmul(cur, rb);
+  pg[l] = y;
   __syncthreads();
-  // row l: -v_e y_{l-1} + (1 + c'_e H_{l+1}) y_l + c'_e J_{l+1} y_{l+1} = d'_e - c'_e G_{l+1}
-  pa[l] = cscale(vpr, (R)-1);
-  pb[l] = cadd(one, cmul(cpr, Hn));
-  pc[l] = cmul(cpr, Jn);
-  pd[l] = csub(dpr, cmul(cpr, Gn));
-  __syncthreads();
-  for (int delta = 1; delta < T; delta <<= 1) {
-    C lA = zero, lB = one, lC = zero, lD = zero, hA = zero, hB = one, hC = zero, hD = zero;
-    if (l - delta >= 0) { lA = pa[l - delta]; lB = pb[l - delta]; lC = pc[l - delta]; lD = pd[l - delta]; }
-    if (l + delta < T) { hA = pa[l + delta]; hB = pb[l + delta]; hC = pc[l + delta]; hD = pd[l + delta]; }
-    const C k1 = cmul(pa[l], crcp<R>(lB)), k2 = cmul(pc[l], crcp<R>(hB));
-    const C nA = cscale(cmul(lA, k1), (R)-1);
-    const C nC = cscale(cmul(hC, k2), (R)-1);
-    const C nB = csub(csub(pb[l], cmul(lC, k1)), cmul(hA, k2));
-    const C nD = csub(csub(pd[l], cmul(lD, k1)), cmul(hD, k2));
-    __syncthreads();
-    pa[l] = nA; pb[l] = nB; pc[l] = nC; pd[l] = nD;
-    __syncthreads();
-  }
-  const C y = cmul(pd[l], crcp<R>(pb[l]));
-  pa[l] = y;
-  __syncthreads();
-  const C yp = l > 0 ? pa[l - 1] : zero;
-  // (3) back substitution
+  const C yp = l > 0 ? pg[l - 1] : zero;
   C x = y;
   D[ch - 1] = x;
+  cn = ch >= 2 ? coef_c(ch - 2) : (R)0;
   for (int j = ch - 2; j >= 0; --j) {
-    x = csub(cadd(D[j], cmul(V[j], yp)), cmul(CP[j], x));
+    const R c = cn;
+    if (j > 0) cn = coef_c(j - 1);
+    x = csub(cadd(D[j], cmul(Vv[j], yp)), cmul(cscale(Pp[j], c), x));
     D[j] = x;
   }
   __syncthreads();
