@@ -455,28 +455,44 @@ def run_extras(args, flush, stream):
     h.close()
 
     # Riesz fractional operator (beta 1.5), 1023 x 512: dense Toeplitz step (b) by the batched LU
-    rz = W.riesz_1023x512()
-    hr = aao.aao_create(rz)
-    nr = W.unknowns(rz)
-    br = torch.empty(nr, dtype=torch.float64, device="cuda")
-    aao.aao_rhs(hr, br)
-    xr = torch.zeros_like(br)
-    aao.fgmres_solve(hr, br, xr, TOL, rz["m"], 300)
-    best, st_r = None, None
-    for _ in range(3):
-        xr.zero_()
-        flush.fill_(1.0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        st_r = aao.fgmres_solve(hr, br, xr, TOL, rz["m"], 300)
-        e1.record(stream)
+    # (with drift), and without drift (r = sigma^2/2) by the eigendecomposition (two products
+    # with Q per apply); aao_create time reported beside each
+    def riesz_solve(rz, key, how):
+        t0 = time.time()
+        hr = aao.aao_create(rz)
         torch.cuda.synchronize()
-        t = e0.elapsed_time(e1)
-        best = t if best is None else min(best, t)
-    hr.close()
-    out["riesz"] = {"workload": "riesz_1023x512_mixed", "unknowns": nr, "beta": rz["beta"], "ms": best,
-                    "value": nr / (best / 1e3), "unit": "unknowns/s", "iterations": st_r["iterations"],
-                    "rel_residual": st_r["rel_residual"]}
+        t_create = time.time() - t0
+        nr = W.unknowns(rz)
+        br = torch.empty(nr, dtype=torch.float64, device="cuda")
+        aao.aao_rhs(hr, br)
+        xr = torch.zeros_like(br)
+        aao.fgmres_solve(hr, br, xr, TOL, rz["m"], 300)
+        best, st_r = None, None
+        for _ in range(3):
+            xr.zero_()
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st_r = aao.fgmres_solve(hr, br, xr, TOL, rz["m"], 300)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1)
+            best = t if best is None else min(best, t)
+        aao.aao_profile_enable(None)
+        xr.zero_()
+        aao.fgmres_solve(hr, br, xr, TOL, rz["m"], 300)
+        torch.cuda.synchronize()
+        tri = aao.aao_profile_read("tridiag")
+        aao.aao_profile_enable([])
+        hr.close()
+        out[key] = {"workload": f"{key}_1023x512_mixed", "unknowns": nr, "beta": rz["beta"], "r": rz["r"],
+                    "step_b": how, "ms": best, "value": nr / (best / 1e3), "unit": "unknowns/s",
+                    "iterations": st_r["iterations"], "rel_residual": st_r["rel_residual"],
+                    "step_b_ms_per_apply": tri[1] / max(tri[0], 1), "create_s": t_create}
+
+    riesz_solve(W.riesz_1023x512(), "riesz", "dense shifted LU factors (2.15 GB) read per apply")
+    riesz_solve(W.riesz_sym_1023x512(), "riesz_sym",
+                "eigendecomposition tau Abar = Q diag(lambda) Q^T; two complex x real products with Q per apply")
     return out
 
 

@@ -40,7 +40,11 @@ extern "C" {
                              exp(-ln(S/K)^2) * (1 + lv_tslope * t); row k of the AaO system
                              uses A(t_{k+1/2}) (the time-dependent form of Eq. 5.8), the
                              preconditioner the time mean of those matrices (Sec. 5.3)      */
-#define AAO_OP_RIESZ 2    /* Riesz fractional operator in log-price (reserved)           */
+#define AAO_OP_RIESZ 2    /* Riesz fractional operator (beta, Eq. 1.2 second case) in
+                             log-price x in [-s_max, s_max] with drift (r - sigma^2/2) u_x;
+                             step (b) by dense shifted LU factors, or, when the drift vanishes
+                             (r = sigma^2/2, a symmetric operator), by the eigendecomposition
+                             tau Abar = Q diag(lambda) Q^T: two products with Q per apply   */
 
 #define AAO_PUT 0
 #define AAO_CALL 1
@@ -81,8 +85,10 @@ typedef struct aao_handle aao_handle;
 /* Validate *p, build the operator coefficients, the eigenvalues lambda_{1,k}, lambda_{2,k}
    (Sec. 3.1, Eq. eigCx), Lambda_alpha, the FFT twiddles and the preconditioner workspace
    on the device. Ownership: *h owns all of it until aao_destroy. Errors: AAO_EINVAL for
-   bad sizes or parameters, AAO_EUNSUPPORTED for op = AAO_OP_RIESZ or non-power-of-two nt,
-   AAO_ENOMEM / AAO_ECUDA from the device. On error *h is set to NULL. */
+   bad sizes or parameters, AAO_EUNSUPPORTED for non-power-of-two nt or a size the operator's
+   step (b) does not support, AAO_ENOMEM / AAO_ECUDA from the device, AAO_BREAKDOWN if the
+   eigendecomposition of a symmetric Riesz operator does not converge. On error *h is set to
+   NULL. */
 int aao_create(const aao_problem* p, aao_handle** h);
 
 /* Free every device buffer of h (NULL is accepted). */
@@ -106,8 +112,9 @@ int precond_apply(aao_handle* h, const double* v_dev, double* z_dev);
 /* Solve M x = b (Eq. 2.2) by right-preconditioned flexible GMRES(m) with P_alpha
    (Sec. 5: right preconditioning, relative-residual stop). x_dev holds the initial guess on
    entry (zero it for the paper's protocol) and the solution on exit. Orthogonalisation is
-   classical Gram-Schmidt applied twice, the least-squares update uses Givens rotations,
-   all in FP64; the true residual is recomputed at every restart. 1 <= m <= 64,
+   classical Gram-Schmidt with a second pass when the first cancels more than 1 - 1e-5 of
+   the vector's norm, the least-squares update uses Givens rotations, all in FP64; the true
+   residual is recomputed at every restart. 1 <= m <= 64,
    maxit >= 1 bounds the total inner iterations. st may be NULL. Returns AAO_OK,
    AAO_NOT_CONVERGED, AAO_BREAKDOWN or an error. */
 int fgmres_solve(aao_handle* h, const double* b_dev, double* x_dev, double tol, int m, int maxit,
@@ -210,6 +217,16 @@ int aao_mlp_normalization(double* feat_mean, double* feat_scale, double* y_mean,
 /* Predict (alpha, m) for raw features feats = (sigma, r, T, nx, nt, cv) with the BF16 forward;
    alpha is clamped to [1e-5, 0.1] and m rounded up to the next of {5, 10, 20, 30, 40}. */
 int alpha_mlp_predict(aao_mlp* h, const float feats[6], double* alpha, int* m);
+
+/* Dense symmetric eigendecomposition on the host, FP64: A = Q diag(w) Q^T. A_host (n*n doubles,
+   row-major, symmetric; only its values are used, the upper and lower triangles must agree) is
+   overwritten with Q^T (row j = the unit eigenvector of w[j]); w_host receives the n eigenvalues
+   (unsorted). Householder tridiagonalisation, then the implicit-shift QL iteration. This is the
+   setup of the spectral step (b) for a symmetric spatial operator (AAO_OP_RIESZ with
+   r = sigma^2/2), exported for tests and for callers with their own symmetric operator. Needs no
+   GPU. Errors: AAO_EINVAL (n < 1 or a NULL pointer), AAO_BREAKDOWN (the QL iteration did not
+   converge within 64 sweeps for some eigenvalue). */
+int aao_sym_eig(int n, double* A_host, double* w_host);
 
 /* Message of the calling thread's most recent failure ("" if none). */
 const char* aao_last_error(void);

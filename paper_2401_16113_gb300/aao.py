@@ -28,7 +28,7 @@ EXPORTS = ["aao_create", "aao_destroy", "aao_rhs", "aao_matvec", "precond_apply"
            "aao_mlp_create", "aao_mlp_destroy", "aao_mlp_params", "aao_mlp_grad", "aao_mlp_adam_step",
            "aao_mlp_train", "aao_mlp_forward", "aao_mlp_normalization", "alpha_mlp_predict",
            "fgmres_solve", "fgmres_solve_host", "aao_last_error", "aao_launch_count",
-           "aao_profile_enable", "aao_profile_read"]
+           "aao_profile_enable", "aao_profile_read", "aao_sym_eig"]
 
 
 class AaoProblem(ctypes.Structure):
@@ -95,6 +95,7 @@ def load(path=None):
     lib.aao_mlp_forward.argtypes = [vp, vp, vp, ip, ip]
     lib.aao_mlp_normalization.argtypes = [ctypes.POINTER(dp)] * 4
     lib.alpha_mlp_predict.argtypes = [vp, fp, ctypes.POINTER(dp), ctypes.POINTER(ip)]
+    lib.aao_sym_eig.argtypes = [ip, ctypes.POINTER(dp), ctypes.POINTER(dp)]
     lib.aao_last_error.restype = ctypes.c_char_p
     lib.aao_launch_count.restype = ctypes.c_uint64
     lib.aao_profile_enable.argtypes = [ctypes.c_int]
@@ -105,7 +106,7 @@ def load(path=None):
                  "fgmres_solve_host", "aao_profile_enable", "aao_profile_read", "aao_batch_create",
                  "aao_batch_rhs", "batch_submit", "aao_batch_destroy", "aao_batch_set_alpha", "aao_mlp_create",
                  "aao_mlp_destroy", "aao_mlp_params", "aao_mlp_grad", "aao_mlp_adam_step", "aao_mlp_train",
-                 "aao_mlp_forward", "aao_mlp_normalization", "alpha_mlp_predict"):
+                 "aao_mlp_forward", "aao_mlp_normalization", "alpha_mlp_predict", "aao_sym_eig"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -174,6 +175,19 @@ def aao_destroy(h):
 
 def aao_rhs(h, b):
     _check(load().aao_rhs(h.ptr, _dev(b, h.n)))
+
+
+def sym_eig(A):
+    """Eigendecomposition A = Q diag(w) Q^T of a symmetric matrix by the library's host routine
+    (aao_sym_eig; no GPU needed). Returns (w, Qt) with Qt[j] the unit eigenvector of w[j]."""
+    a = np.array(A, dtype=np.float64, order="C", copy=True)
+    n = a.shape[0]
+    if a.ndim != 2 or a.shape[1] != n:
+        raise ValueError("sym_eig: A must be square")
+    w = np.empty(n, dtype=np.float64)
+    dpp = ctypes.POINTER(ctypes.c_double)
+    _check(load().aao_sym_eig(n, a.ctypes.data_as(dpp), w.ctypes.data_as(dpp)))
+    return w, a
 
 
 def aao_matvec(h, x, y):

@@ -224,6 +224,13 @@ struct Handle {
   float* Vf = nullptr;  // FP32 copy of the basis vector the next preconditioner apply reads (mixed)
   float2* rz_lu = nullptr;
   float2* rz_dinv = nullptr;  // inverses of the factors' diagonal blocks (L, U per block and bin)
+  // symmetric Riesz operator (no drift): tau Abar = Q diag(lambda) Q^T; step (b) is
+  // z2_k = Q diag(D_k) Q^T z1_k with D_k,j = (1/lambda_{2,k}) / (mu_k - lambda_j)
+  bool rz_sym = false;
+  float* rz_q = nullptr;    // Q, row-major [x][j] (FP32)
+  float* rz_qt = nullptr;   // Q^T, row-major [j][x] (FP32)
+  float2* rz_dk = nullptr;  // D, [k][j] (FP32 complex)
+  float2* rz_w = nullptr;   // Q^T z1 per bin, K x pitch complex
 
   // FGMRES workspace (grown on demand)
   int ws_m = 0;
@@ -246,6 +253,11 @@ int launch_precond(Handle& h, const double* v, void* z, bool z_is_float, const d
 int tune_precond(Handle& h);
 // factors of the partitioned tridiagonal solves of step (b) (needs tri, mu/muf)
 int build_tri_factors(Handle& h);
+// The Riesz operator has no drift term ((r - sigma^2/2) u_x vanishes): its matrix is symmetric.
+inline bool riesz_symmetric(const aao_problem& p) { return p.r - 0.5 * p.sigma * p.sigma == 0.0; }
+// A = Q diag(w) Q^T for a dense symmetric n x n A (row-major, FP64, host); A is overwritten with
+// Q^T. False if the QL iteration does not converge.
+bool sym_eig(int n, double* A, double* w);
 int riesz_build(Handle& h);
 int riesz_matvec(Handle& h, const void* x, bool x_is_float, double* y, const double* b, const double* V, int nd, int m);
 int riesz_rhs(Handle& h, double* b);

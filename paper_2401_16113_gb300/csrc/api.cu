@@ -75,7 +75,7 @@ int validate(const aao_problem* p) {
     if (!(p->beta > 1.0) || !(p->beta <= 2.0)) { set_error("aao_create: Riesz order beta must lie in (1, 2]"); return AAO_EINVAL; }
     if (p->nx > 2048) { set_error("aao_create: Riesz operator needs nx <= 2048"); return AAO_EUNSUPPORTED; }
     const double factors = (double)(p->nt / 2 + 1) * p->nx * (double)p->nx * 8.0;
-    if (factors > 32e9) { set_error("aao_create: Riesz LU factors would exceed 32 GB"); return AAO_EUNSUPPORTED; }
+    if (!riesz_symmetric(*p) && factors > 32e9) { set_error("aao_create: Riesz LU factors would exceed 32 GB"); return AAO_EUNSUPPORTED; }
   }
   if (p->payoff != AAO_PUT && p->payoff != AAO_CALL) { set_error("aao_create: unknown payoff"); return AAO_EINVAL; }
   if (p->precision != AAO_FP64 && p->precision != AAO_MIXED) { set_error("aao_create: unknown precision"); return AAO_EINVAL; }
@@ -182,6 +182,15 @@ int fgmres_solve_host(aao_handle* hd, const double* b_host, double* x_host, doub
     return AAO_ECUDA;
   }
   return s;
+}
+
+int aao_sym_eig(int n, double* A_host, double* w_host) {
+  if (n < 1 || !A_host || !w_host) { set_error("aao_sym_eig: bad argument"); return AAO_EINVAL; }
+  if (!sym_eig(n, A_host, w_host)) {
+    set_error("aao_sym_eig: the QL iteration did not converge");
+    return AAO_BREAKDOWN;
+  }
+  return AAO_OK;
 }
 
 const char* aao_last_error(void) { return t_last_error.c_str(); }

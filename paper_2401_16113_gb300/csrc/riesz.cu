@@ -18,6 +18,9 @@
 //                nt/2+1 bins, factored in place by blocked right-looking LU without pivoting
 //                (FP32 complex; the matrices are diagonally dominant, see the design notes).
 //   k_rz_trsv    per apply: forward (unit L) and backward (U) blocked substitution of every bin.
+//   k_rz_cgemm   step (b) when the operator is symmetric (no drift): with tau Abar = Q diag(lambda) Q^T
+//                (eigendecomposition at aao_create), z2_k = Q diag(D_k) Q^T z1_k for every bin is two
+//                products of the K x Nx complex half spectrum with the real Nx x Nx matrix Q.
 #include <math.h>
 
 #include <complex>
@@ -34,6 +37,84 @@ using namespace kdev;
 using namespace pdev;
 
 constexpr int kNB = 32;  // LU / substitution block
+
+// ------------------------------------------------------------------- spectral step (b)
+// C[k][n] = (D[k][n] *) sum_{m < Mp} A[k][m] B[m][n] for bins k < Kb: A and C complex rows of
+// pitch lda / ldc (FP32 complex), B real row-major with leading dimension ldb, Mp a multiple of
+// kGM and the grid's column tiles within ldb (the tables are zero-padded to 64-multiples, so
+// padded rows and columns contribute zeros). A CTA computes kGB bins x kGN columns; thread
+// (tb, tn) holds bins 2 tb, 2 tb + 1 and columns 4 tn .. 4 tn + 3. B tiles go through shared
+// memory (the next tile is fetched into registers during the current one's products); A values
+// are read through L1 (16 threads share each).
+constexpr int kGB = 16, kGN = 64, kGM = 16;
+__global__ void __launch_bounds__(128) k_rz_cgemm(const float2* __restrict__ A, int lda, const float* __restrict__ B,
+                                                  int ldb, float2* __restrict__ C, int ldc,
+                                                  const float2* __restrict__ D, int ldd, int Kb, int Mp) {
+  __shared__ __align__(16) float Bs[kGM][kGN];
+  pdl_sync();
+  const int tb = threadIdx.x >> 4, tn = threadIdx.x & 15;
+  const int b0 = blockIdx.y * kGB, n0 = blockIdx.x * kGN;
+  const int ba = b0 + 2 * tb, bb = ba + 1;
+  const bool va = ba < Kb, vb = bb < Kb;
+  const float2* Aa = A + (size_t)(va ? ba : 0) * lda;
+  const float2* Ab = A + (size_t)(vb ? bb : 0) * lda;
+  const float2 zero = make_float2(0.f, 0.f);
+  float2 acc[2][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[i][q] = zero;
+  // B tile: kGM rows x kGN floats = 256 float4, two per thread (rows e >> 4, column groups e & 15)
+  const int e0 = threadIdx.x, e1 = threadIdx.x + 128;
+  auto ldB = [&](int m0, int e) {
+    return __ldg(reinterpret_cast<const float4*>(B + (size_t)(m0 + (e >> 4)) * ldb + n0 + 4 * (e & 15)));
+  };
+  float4 f0 = ldB(0, e0), f1 = ldB(0, e1);
+  for (int m0 = 0; m0 < Mp; m0 += kGM) {
+    *reinterpret_cast<float4*>(&Bs[e0 >> 4][4 * (e0 & 15)]) = f0;
+    *reinterpret_cast<float4*>(&Bs[e1 >> 4][4 * (e1 & 15)]) = f1;
+    __syncthreads();
+    if (m0 + kGM < Mp) {
+      f0 = ldB(m0 + kGM, e0);
+      f1 = ldB(m0 + kGM, e1);
+    }
+#pragma unroll
+    for (int mm = 0; mm < kGM; ++mm) {
+      const float2 a0 = va ? __ldg(Aa + m0 + mm) : zero;
+      const float2 a1 = vb ? __ldg(Ab + m0 + mm) : zero;
+      const float4 bq = *reinterpret_cast<const float4*>(&Bs[mm][4 * tn]);
+      const float bv[4] = {bq.x, bq.y, bq.z, bq.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        acc[0][q].x = fmaf(a0.x, bv[q], acc[0][q].x);
+        acc[0][q].y = fmaf(a0.y, bv[q], acc[0][q].y);
+        acc[1][q].x = fmaf(a1.x, bv[q], acc[1][q].x);
+        acc[1][q].y = fmaf(a1.y, bv[q], acc[1][q].y);
+      }
+    }
+    __syncthreads();
+  }
+  const int n = n0 + 4 * tn;
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int b = i == 0 ? ba : bb;
+    if (b >= Kb) continue;
+    float2 v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = acc[i][q];
+    if (D) {
+      const float2* Dr = D + (size_t)b * ldd + n;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float2 dq = __ldg(Dr + q);
+        v[q] = make_float2(v[q].x * dq.x - v[q].y * dq.y, v[q].x * dq.y + v[q].y * dq.x);
+      }
+    }
+    float4* Cr = reinterpret_cast<float4*>(C + (size_t)b * ldc + n);
+    Cr[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+    Cr[1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+  }
+}
 
 // ------------------------------------------------------------------------------- matvec
 template <typename IN, int MODE, int ND>
@@ -457,9 +538,56 @@ int riesz_build(Handle& h) {
   AAO_TRY(up(&h.gL, gl));
   AAO_TRY(up(&d_tcol, tcol));
   AAO_TRY(up(&d_trow, trow));
-  // shifted matrices and their LU factors (FP32 complex)
   const int K = h.K;
   const size_t nn = (size_t)nx * nx;
+  if (riesz_symmetric(p)) {
+    // no drift: tau Abar is the symmetric Toeplitz matrix of tcol; tau Abar = Q diag(lambda) Q^T
+    std::vector<double> Ad(nn), lam(nx);
+    for (int i = 0; i < nx; ++i)
+      for (int j = 0; j < nx; ++j) Ad[(size_t)i * nx + j] = tcol[i > j ? i - j : j - i];
+    if (!sym_eig(nx, Ad.data(), lam.data())) {
+      set_error("aao_create: eigendecomposition of the symmetric Riesz operator did not converge");
+      cudaFree(d_tcol);
+      cudaFree(d_trow);
+      return AAO_BREAKDOWN;
+    }
+    // Ad holds Q^T. Both orientations in FP32, zero-padded to ldq = pitch (a multiple of 64)
+    const int ldq = h.pitch;
+    std::vector<float> q((size_t)ldq * ldq, 0.f), qt((size_t)ldq * ldq, 0.f);
+    for (int j = 0; j < nx; ++j)
+      for (int x = 0; x < nx; ++x) {
+        const float v = (float)Ad[(size_t)j * nx + x];
+        qt[(size_t)j * ldq + x] = v;
+        q[(size_t)x * ldq + j] = v;
+      }
+    // D_k,j = (1/lambda_{2,k}) / (mu_k - lambda_j)
+    std::vector<double2> mu(K), il2(K);
+    AAO_TRY_CUDA(cudaMemcpyAsync(mu.data(), h.mu, sizeof(double2) * K, cudaMemcpyDeviceToHost, h.stream));
+    AAO_TRY_CUDA(cudaMemcpyAsync(il2.data(), h.il2, sizeof(double2) * K, cudaMemcpyDeviceToHost, h.stream));
+    AAO_TRY_CUDA(cudaStreamSynchronize(h.stream));
+    std::vector<float2> dk((size_t)K * ldq, make_float2(0.f, 0.f));
+    for (int k = 0; k < K; ++k) {
+      const std::complex<double> m(mu[k].x, mu[k].y), s(il2[k].x, il2[k].y);
+      for (int j = 0; j < nx; ++j) {
+        const std::complex<double> v = s / (m - lam[j]);
+        dk[(size_t)k * ldq + j] = make_float2((float)v.real(), (float)v.imag());
+      }
+    }
+    AAO_TRY(up(&h.rz_q, q));
+    AAO_TRY(up(&h.rz_qt, qt));
+    AAO_TRY(up(&h.rz_dk, dk));
+    AAO_TRY_CUDA(cudaMalloc(&h.rz_w, sizeof(float2) * (size_t)K * ldq));
+    // the padding columns of the spectrum and of the workspace stay zero: every kernel writes
+    // columns < nx only, or zeros
+    AAO_TRY_CUDA(cudaMemsetAsync(h.rz_w, 0, sizeof(float2) * (size_t)K * ldq, h.stream));
+    AAO_TRY_CUDA(cudaMemsetAsync(h.spec, 0, sizeof(float2) * (size_t)K * h.pitch, h.stream));
+    AAO_TRY_CUDA(cudaStreamSynchronize(h.stream));
+    h.rz_sym = true;
+    cudaFree(d_tcol);
+    cudaFree(d_trow);
+    return AAO_OK;
+  }
+  // shifted matrices and their LU factors (FP32 complex)
   AAO_TRY_CUDA(cudaMalloc(&h.rz_lu, sizeof(float2) * nn * K));
   k_rz_form<<<dim3(256, K), 256, 0, h.stream>>>(h.rz_lu, nx, d_tcol, d_trow, h.muf);
   AAO_CHECK_LAUNCH();
@@ -551,6 +679,19 @@ int riesz_rhs(Handle& h, double* b) {
 }
 
 int riesz_solve_bins(Handle& h, void* spec) {
+  if (h.rz_sym) {
+    // W = (Z1 Q) o D, then Z2 = W Q^T (rows: bins; the half spectrum is [k][x])
+    const int ldq = h.pitch;
+    const dim3 grid(ldq / kGN, (h.K + kGB - 1) / kGB);
+    const double nq = (double)ldq * ldq;
+    ProfScope ps(AAO_K_TRIDIAG, h.stream, 2.0 * (nq * 4.0 + 2.0 * (double)h.K * ldq * 8.0));
+    AAO_TRY_CUDA(launch_pdl(k_rz_cgemm, grid, 128, 0, h.stream, (const float2*)spec, h.pitch, (const float*)h.rz_q,
+                            ldq, h.rz_w, ldq, (const float2*)h.rz_dk, ldq, h.K, ldq));
+    AAO_TRY_CUDA(launch_pdl(k_rz_cgemm, grid, 128, 0, h.stream, (const float2*)h.rz_w, ldq, (const float*)h.rz_qt,
+                            ldq, (float2*)spec, h.pitch, (const float2*)nullptr, ldq, h.K, ldq));
+    AAO_CHECK_LAUNCH();
+    return AAO_OK;
+  }
   const size_t smem = sizeof(float2) * ((size_t)h.nx + kNB);
   const double bytes = (double)h.K * ((double)h.nx * h.nx * 8.0 + 2.0 * h.nx * 8.0);
   ProfScope ps(AAO_K_TRIDIAG, h.stream, bytes);

@@ -67,6 +67,12 @@ def riesz_1023x512():
                  beta=1.5, alpha=1e-3, precision="mixed", m=30, tol=1e-8)
 
 
+def riesz_sym_1023x512():
+    """The Riesz workload without drift: r = sigma^2/2 = 0.03125 cancels the (r - sigma^2/2) u_x
+    term, so the spatial matrix is symmetric and step (b) runs on its eigendecomposition."""
+    return with_(riesz_1023x512(), r=0.03125)
+
+
 def batch_instances(n=512, seed=SEED, nx_choices=(127, 255, 511, 1023),
                     nt_choices=(64, 128, 256, 512, 1024), precision="mixed", alpha=1e-3, m=20,
                     tol=1e-8):

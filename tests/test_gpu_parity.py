@@ -339,6 +339,58 @@ def test_riesz_precond_small_matches_dense_inverse(aao):
         assert rel(host(z), O.precond_dense(p, v)) <= precond_bound(p)
 
 
+RZS = W.riesz_sym_1023x512()
+
+
+@pytest.mark.parametrize("alpha", [1e-2, 1e-3])
+@pytest.mark.parametrize("nx,nt", RZ_SHAPES + [(200, 4), (64, 1)])
+def test_riesz_symmetric_precond_matches_oracle(aao, nx, nt, alpha):
+    """No drift (r = sigma^2/2): step (b) by the eigendecomposition and two complex x real
+    products per apply, against the oracle's dense shifted solves."""
+    p = W.with_(RZS, nx=nx, nt=nt, alpha=alpha)
+    assert p["r"] == 0.5 * p["sigma"] ** 2
+    h = aao.aao_create(p)
+    v = W.random_vector(nx * nt, seed=7 * nx + nt)
+    z = torch.empty(nx * nt, dtype=torch.float64, device="cuda")
+    aao.precond_apply(h, dev(v), z)
+    ref = O.precond_fft(p, v)
+    assert rel(host(z), ref) <= precond_bound(p), rel(host(z), ref)
+    # a second apply (the padding of the half spectrum must still be zero) gives the same bits
+    z2 = torch.empty(nx * nt, dtype=torch.float64, device="cuda")
+    aao.precond_apply(h, dev(v), z2)
+    assert np.array_equal(host(z), host(z2))
+
+
+def test_riesz_symmetric_precond_small_matches_dense_inverse(aao):
+    for nx, nt in [(7, 4), (9, 8), (2, 2)]:
+        p = W.with_(RZS, nx=nx, nt=nt, alpha=1e-2)
+        h = aao.aao_create(p)
+        v = W.random_vector(nx * nt, seed=nx)
+        z = torch.empty(nx * nt, dtype=torch.float64, device="cuda")
+        aao.precond_apply(h, dev(v), z)
+        assert rel(host(z), O.precond_dense(p, v)) <= precond_bound(p)
+
+
+def test_riesz_symmetric_full_size_solve():
+    """1023 x 512 Riesz without drift, mixed precision, spectral step (b): true residual <= 1e-8
+    and the solution against sequential CN."""
+    from paper_2401_16113_gb300 import aao as A
+    p = RZS
+    h = A.aao_create(p)
+    n = W.unknowns(p)
+    b = torch.empty(n, dtype=torch.float64, device="cuda")
+    A.aao_rhs(h, b)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    st = A.fgmres_solve(h, b, x, 1e-8, 30, 300)
+    assert st["status"] == 0, st
+    xs, bs = host(x), host(b)
+    assert np.linalg.norm(bs - O.matvec_blocks(p, xs)) <= 1.01e-8 * np.linalg.norm(bs)
+    U = O.sequential_cn(p)
+    err = np.abs(xs.reshape(p["nt"], p["nx"])[-1] - U[-1]).max() / np.abs(U[-1]).max()
+    print("riesz symmetric full size: its", st["iterations"], "maturity error", err)
+    assert err <= 1e-6
+
+
 def test_riesz_full_size_solve():
     """1023 x 512 Riesz (beta 1.5) put, mixed precision: the true residual (FP64, by the
     oracle's block-row product with the dense A) <= 1e-8 and the solution against sequential CN."""
