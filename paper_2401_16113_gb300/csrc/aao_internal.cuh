@@ -230,7 +230,9 @@ struct Handle {
   float* rz_q = nullptr;    // Q, row-major [x][j] (FP32)
   float* rz_qt = nullptr;   // Q^T, row-major [j][x] (FP32)
   float2* rz_dk = nullptr;  // D, [k][j] (FP32 complex)
-  float2* rz_w = nullptr;   // Q^T z1 per bin, K x pitch complex
+  float2* rz_w = nullptr;   // D o (Q^T z1) per bin, K x rz_ldq complex
+  float2* rz_part = nullptr;  // partial products of the contraction segments
+  int rz_ldq = 0;           // leading dimension of Q, Q^T, D and the workspaces
 
   // FGMRES workspace (grown on demand)
   int ws_m = 0;

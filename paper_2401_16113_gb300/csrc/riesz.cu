@@ -39,80 +39,104 @@ using namespace pdev;
 constexpr int kNB = 32;  // LU / substitution block
 
 // ------------------------------------------------------------------- spectral step (b)
-// C[k][n] = (D[k][n] *) sum_{m < Mp} A[k][m] B[m][n] for bins k < Kb: A and C complex rows of
-// pitch lda / ldc (FP32 complex), B real row-major with leading dimension ldb, Mp a multiple of
-// kGM and the grid's column tiles within ldb (the tables are zero-padded to 64-multiples, so
-// padded rows and columns contribute zeros). A CTA computes kGB bins x kGN columns; thread
-// (tb, tn) holds bins 2 tb, 2 tb + 1 and columns 4 tn .. 4 tn + 3. B tiles go through shared
-// memory (the next tile is fetched into registers during the current one's products); A values
-// are read through L1 (16 threads share each).
-constexpr int kGB = 16, kGN = 64, kGM = 16;
+// Partial products P[s][k][n] = sum_{m in segment s} A[k][m] B[m][n] for bins k < Kb: A complex
+// rows of pitch lda (FP32 complex), B real row-major with leading dimension ldb, segment s =
+// [s Mseg, (s+1) Mseg) with Mseg a multiple of kGM, columns n < gridDim.x kGN <= ldb (the tables
+// are zero-padded, so padded rows and columns contribute zeros). A CTA computes kGB bins x kGN
+// columns of one segment; thread (tb, tn) holds bins 4 tb .. 4 tb + 3 and columns 4 tn + {0..3}
+// and 64 + 4 tn + {0..3}: per contraction index 4 shared loads of 16 bytes feed 64 FMAs. Both
+// tiles go through shared memory, the next chunk's loads are issued before the current products.
+// The segments are summed in a fixed order by k_rz_cgemm_sum (deterministic, no atomics).
+constexpr int kGB = 32, kGN = 128, kGM = 16, kGSplit = 4;
 __global__ void __launch_bounds__(128) k_rz_cgemm(const float2* __restrict__ A, int lda, const float* __restrict__ B,
-                                                  int ldb, float2* __restrict__ C, int ldc,
-                                                  const float2* __restrict__ D, int ldd, int Kb, int Mp) {
+                                                  int ldb, float2* __restrict__ P, int ldp, int Kb, int Mseg) {
+  __shared__ __align__(16) float2 As[kGM][kGB + 2];  // [m][bin], +2: transposed stores 2-way
   __shared__ __align__(16) float Bs[kGM][kGN];
   pdl_sync();
   const int tb = threadIdx.x >> 4, tn = threadIdx.x & 15;
-  const int b0 = blockIdx.y * kGB, n0 = blockIdx.x * kGN;
-  const int ba = b0 + 2 * tb, bb = ba + 1;
-  const bool va = ba < Kb, vb = bb < Kb;
-  const float2* Aa = A + (size_t)(va ? ba : 0) * lda;
-  const float2* Ab = A + (size_t)(vb ? bb : 0) * lda;
+  const int b0 = blockIdx.y * kGB, n0 = blockIdx.x * kGN, seg = blockIdx.z;
+  const int mbeg = seg * Mseg, mend = mbeg + Mseg;
   const float2 zero = make_float2(0.f, 0.f);
-  float2 acc[2][4];
+  float2 acc[4][8];
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[i][q] = zero;
-  // B tile: kGM rows x kGN floats = 256 float4, two per thread (rows e >> 4, column groups e & 15)
-  const int e0 = threadIdx.x, e1 = threadIdx.x + 128;
-  auto ldB = [&](int m0, int e) {
-    return __ldg(reinterpret_cast<const float4*>(B + (size_t)(m0 + (e >> 4)) * ldb + n0 + 4 * (e & 15)));
-  };
-  float4 f0 = ldB(0, e0), f1 = ldB(0, e1);
-  for (int m0 = 0; m0 < Mp; m0 += kGM) {
-    *reinterpret_cast<float4*>(&Bs[e0 >> 4][4 * (e0 & 15)]) = f0;
-    *reinterpret_cast<float4*>(&Bs[e1 >> 4][4 * (e1 & 15)]) = f1;
-    __syncthreads();
-    if (m0 + kGM < Mp) {
-      f0 = ldB(m0 + kGM, e0);
-      f1 = ldB(m0 + kGM, e1);
+    for (int q = 0; q < 8; ++q) acc[i][q] = zero;
+  // A tile: 32 bins x 16 m complex (4 per thread: bin = e >> 4, m = e & 15, e = t + 128 i);
+  // B tile: 16 rows x 128 floats (4 float4 per thread: row = e >> 5, column group = e & 31)
+  float2 ra[4];
+  float4 rb[4];
+  auto fetch = [&](int m0) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int e = threadIdx.x + 128 * i, bin = b0 + (e >> 4);
+      ra[i] = bin < Kb ? __ldg(A + (size_t)bin * lda + m0 + (e & 15)) : zero;
+      rb[i] = __ldg(reinterpret_cast<const float4*>(B + (size_t)(m0 + (e >> 5)) * ldb + n0 + 4 * (e & 31)));
     }
+  };
+  fetch(mbeg);
+  for (int m0 = mbeg; m0 < mend; m0 += kGM) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int e = threadIdx.x + 128 * i;
+      As[e & 15][e >> 4] = ra[i];
+      *reinterpret_cast<float4*>(&Bs[e >> 5][4 * (e & 31)]) = rb[i];
+    }
+    __syncthreads();
+    if (m0 + kGM < mend) fetch(m0 + kGM);
 #pragma unroll
     for (int mm = 0; mm < kGM; ++mm) {
-      const float2 a0 = va ? __ldg(Aa + m0 + mm) : zero;
-      const float2 a1 = vb ? __ldg(Ab + m0 + mm) : zero;
-      const float4 bq = *reinterpret_cast<const float4*>(&Bs[mm][4 * tn]);
-      const float bv[4] = {bq.x, bq.y, bq.z, bq.w};
+      const float4 a01 = *reinterpret_cast<const float4*>(&As[mm][4 * tb]);
+      const float4 a23 = *reinterpret_cast<const float4*>(&As[mm][4 * tb + 2]);
+      const float4 bl = *reinterpret_cast<const float4*>(&Bs[mm][4 * tn]);
+      const float4 bh = *reinterpret_cast<const float4*>(&Bs[mm][64 + 4 * tn]);
+      const float ar[4] = {a01.x, a01.z, a23.x, a23.z}, ai[4] = {a01.y, a01.w, a23.y, a23.w};
+      const float bv[8] = {bl.x, bl.y, bl.z, bl.w, bh.x, bh.y, bh.z, bh.w};
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        acc[0][q].x = fmaf(a0.x, bv[q], acc[0][q].x);
-        acc[0][q].y = fmaf(a0.y, bv[q], acc[0][q].y);
-        acc[1][q].x = fmaf(a1.x, bv[q], acc[1][q].x);
-        acc[1][q].y = fmaf(a1.y, bv[q], acc[1][q].y);
-      }
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          acc[i][q].x = fmaf(ar[i], bv[q], acc[i][q].x);
+          acc[i][q].y = fmaf(ai[i], bv[q], acc[i][q].y);
+        }
     }
     __syncthreads();
   }
-  const int n = n0 + 4 * tn;
+  float2* Ps = P + (size_t)seg * Kb * ldp;
 #pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const int b = i == 0 ? ba : bb;
+  for (int i = 0; i < 4; ++i) {
+    const int b = b0 + 4 * tb + i;
     if (b >= Kb) continue;
-    float2 v[4];
+    float4* lo = reinterpret_cast<float4*>(Ps + (size_t)b * ldp + n0 + 4 * tn);
+    float4* hi = reinterpret_cast<float4*>(Ps + (size_t)b * ldp + n0 + 64 + 4 * tn);
+    lo[0] = make_float4(acc[i][0].x, acc[i][0].y, acc[i][1].x, acc[i][1].y);
+    lo[1] = make_float4(acc[i][2].x, acc[i][2].y, acc[i][3].x, acc[i][3].y);
+    hi[0] = make_float4(acc[i][4].x, acc[i][4].y, acc[i][5].x, acc[i][5].y);
+    hi[1] = make_float4(acc[i][6].x, acc[i][6].y, acc[i][7].x, acc[i][7].y);
+  }
+}
+
+// C[k][n] = (D[k][n] *) sum_s P[s][k][n] for k < Kb, n < N (N even; pairs of complex per thread)
+__global__ void __launch_bounds__(256) k_rz_cgemm_sum(const float2* __restrict__ P, int ldp, int Kb, int N,
+                                                      float2* __restrict__ C, int ldc,
+                                                      const float2* __restrict__ D, int ldd) {
+  pdl_sync();
+  const int half = N >> 1;
+  const size_t total = (size_t)Kb * half, plane = (size_t)Kb * ldp;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(e / half), n = 2 * (int)(e - (size_t)k * half);
+    const float4* src = reinterpret_cast<const float4*>(P + (size_t)k * ldp + n);
+    float4 v = __ldg(src);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = acc[i][q];
-    if (D) {
-      const float2* Dr = D + (size_t)b * ldd + n;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float2 dq = __ldg(Dr + q);
-        v[q] = make_float2(v[q].x * dq.x - v[q].y * dq.y, v[q].x * dq.y + v[q].y * dq.x);
-      }
+    for (int s = 1; s < kGSplit; ++s) {
+      const float4 w = __ldg(reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(src) + s * plane));
+      v.x += w.x; v.y += w.y; v.z += w.z; v.w += w.w;
     }
-    float4* Cr = reinterpret_cast<float4*>(C + (size_t)b * ldc + n);
-    Cr[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
-    Cr[1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+    if (D) {
+      const float4 d = __ldg(reinterpret_cast<const float4*>(D + (size_t)k * ldd + n));
+      v = make_float4(v.x * d.x - v.y * d.y, v.x * d.y + v.y * d.x, v.z * d.z - v.w * d.w, v.z * d.w + v.w * d.z);
+    }
+    *reinterpret_cast<float4*>(C + (size_t)k * ldc + n) = v;
   }
 }
 
@@ -551,8 +575,9 @@ int riesz_build(Handle& h) {
       cudaFree(d_trow);
       return AAO_BREAKDOWN;
     }
-    // Ad holds Q^T. Both orientations in FP32, zero-padded to ldq = pitch (a multiple of 64)
-    const int ldq = h.pitch;
+    // Ad holds Q^T. Both orientations in FP32, zero-padded to ldq (a multiple of the products'
+    // column tile, >= the spectrum's pitch)
+    const int ldq = ((nx + kGN - 1) / kGN) * kGN;
     std::vector<float> q((size_t)ldq * ldq, 0.f), qt((size_t)ldq * ldq, 0.f);
     for (int j = 0; j < nx; ++j)
       for (int x = 0; x < nx; ++x) {
@@ -577,6 +602,8 @@ int riesz_build(Handle& h) {
     AAO_TRY(up(&h.rz_qt, qt));
     AAO_TRY(up(&h.rz_dk, dk));
     AAO_TRY_CUDA(cudaMalloc(&h.rz_w, sizeof(float2) * (size_t)K * ldq));
+    AAO_TRY_CUDA(cudaMalloc(&h.rz_part, sizeof(float2) * (size_t)kGSplit * K * ldq));
+    h.rz_ldq = ldq;
     // the padding columns of the spectrum and of the workspace stay zero: every kernel writes
     // columns < nx only, or zeros
     AAO_TRY_CUDA(cudaMemsetAsync(h.rz_w, 0, sizeof(float2) * (size_t)K * ldq, h.stream));
@@ -680,15 +707,21 @@ int riesz_rhs(Handle& h, double* b) {
 
 int riesz_solve_bins(Handle& h, void* spec) {
   if (h.rz_sym) {
-    // W = (Z1 Q) o D, then Z2 = W Q^T (rows: bins; the half spectrum is [k][x])
-    const int ldq = h.pitch;
-    const dim3 grid(ldq / kGN, (h.K + kGB - 1) / kGB);
+    // W = (Z1 Q) o D, then Z2 = W Q^T (rows: bins; the half spectrum is [k][x]); each product in
+    // kGSplit contraction segments, summed in order
+    const int ldq = h.rz_ldq;
     const double nq = (double)ldq * ldq;
     ProfScope ps(AAO_K_TRIDIAG, h.stream, 2.0 * (nq * 4.0 + 2.0 * (double)h.K * ldq * 8.0));
+    const dim3 grid(ldq / kGN, (h.K + kGB - 1) / kGB, kGSplit);
+    const int sgrid = (int)((((size_t)h.K * ldq / 2) + 255) / 256);
     AAO_TRY_CUDA(launch_pdl(k_rz_cgemm, grid, 128, 0, h.stream, (const float2*)spec, h.pitch, (const float*)h.rz_q,
-                            ldq, h.rz_w, ldq, (const float2*)h.rz_dk, ldq, h.K, ldq));
+                            ldq, h.rz_part, ldq, h.K, h.pitch / kGSplit));
+    AAO_TRY_CUDA(launch_pdl(k_rz_cgemm_sum, sgrid, 256, 0, h.stream, (const float2*)h.rz_part, ldq, h.K, ldq,
+                            h.rz_w, ldq, (const float2*)h.rz_dk, ldq));
     AAO_TRY_CUDA(launch_pdl(k_rz_cgemm, grid, 128, 0, h.stream, (const float2*)h.rz_w, ldq, (const float*)h.rz_qt,
-                            ldq, (float2*)spec, h.pitch, (const float2*)nullptr, ldq, h.K, ldq));
+                            ldq, h.rz_part, ldq, h.K, ldq / kGSplit));
+    AAO_TRY_CUDA(launch_pdl(k_rz_cgemm_sum, sgrid, 256, 0, h.stream, (const float2*)h.rz_part, ldq, h.K, h.pitch,
+                            (float2*)spec, h.pitch, (const float2*)nullptr, ldq));
     AAO_CHECK_LAUNCH();
     return AAO_OK;
   }
