@@ -308,7 +308,7 @@ def run_ours(args):
 
     extras = {}
     if not args.no_extras:
-        extras = run_extras(args, flush, stream)
+        extras = run_extras(args, flush, stream, (p, b, n, ms, stats[-1]))
 
     pk = peaks()
     hbm_peak = pk.get("hbm_gbs", 6800.0)
@@ -364,10 +364,11 @@ def run_ours(args):
         tdist.destroy_process_group()
 
 
-def run_extras(args, flush, stream):
+def run_extras(args, flush, stream, main):
     """The batched workload (512 instances, one persistent launch), the learned-alpha
-    deployment (8191 x 8192 local volatility) and the Riesz fractional operator (1023 x 512);
-    reported beside the headline number."""
+    deployment (8191 x 8192 local volatility), P_1 against P_alpha on the headline workload and
+    the Riesz fractional operator (1023 x 512, with and without drift); reported beside the
+    headline number. main = (problem, device b, unknowns, ms per solve, stats) of the headline."""
     import numpy as np
     import torch
 
@@ -489,6 +490,29 @@ def run_extras(args, flush, stream):
                     "step_b": how, "ms": best, "value": nr / (best / 1e3), "unit": "unknowns/s",
                     "iterations": st_r["iterations"], "rel_residual": st_r["rel_residual"],
                     "step_b_ms_per_apply": tri[1] / max(tri[0], 1), "create_s": t_create}
+
+    # P_1 (alpha = 1, the block-circulant preconditioner) against P_alpha on the bench workload
+    p, b, n, ms_main, st_main = main
+    p1 = W.with_(p, alpha=1.0)
+    h1 = aao.aao_create(p1)
+    x1 = torch.zeros(n, dtype=torch.float64, device="cuda")
+    aao.fgmres_solve(h1, b, x1, TOL, p["m"], 300)
+    best1, st1 = None, None
+    for _ in range(3):
+        x1.zero_()
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st1 = aao.fgmres_solve(h1, b, x1, TOL, p["m"], 300)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1)
+        best1 = t if best1 is None else min(best1, t)
+    h1.close()
+    out["p1_vs_palpha"] = {"workload": "localvol_2047x2048_mixed", "P_1": {"alpha": 1.0, "iterations": st1["iterations"],
+                           "ms": best1, "value": n / (best1 / 1e3), "rel_residual": st1["rel_residual"]},
+                           "P_alpha": {"alpha": p["alpha"], "iterations": st_main["iterations"], "ms": ms_main,
+                                       "value": n / (ms_main / 1e3)}}
 
     riesz_solve(W.riesz_1023x512(), "riesz", "dense shifted LU factors (2.15 GB) read per apply")
     riesz_solve(W.riesz_sym_1023x512(), "riesz_sym",

@@ -339,6 +339,37 @@ def test_riesz_precond_small_matches_dense_inverse(aao):
         assert rel(host(z), O.precond_dense(p, v)) <= precond_bound(p)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_P_alpha_beats_P_1_on_the_gpu_and_matches_oracle_counts(aao, precision):
+    """Sec. 3-4: P_alpha (alpha = 1e-3) needs fewer FGMRES iterations than the block-circulant
+    P_1 (alpha = 1), and its count does not grow with the mesh (nx = 2^k - 1, nt = 2^k). In FP64
+    the GPU counts equal the oracle's on the smallest mesh."""
+    its_a, its_1 = [], []
+    for k in (6, 7, 8):
+        q = W.with_(BS, nx=2 ** k - 1, nt=2 ** k, precision=precision)
+        res = {}
+        for alpha in (1e-3, 1.0):
+            p = W.with_(q, alpha=alpha)
+            h = aao.aao_create(p)
+            n = W.unknowns(p)
+            b = torch.empty(n, dtype=torch.float64, device="cuda")
+            aao.aao_rhs(h, b)
+            x = torch.zeros(n, dtype=torch.float64, device="cuda")
+            st = aao.fgmres_solve(h, b, x, 1e-9, 40, 400)
+            assert st["status"] == 0, (k, alpha, st)
+            res[alpha] = st["iterations"]
+            h.close()
+        its_a.append(res[1e-3])
+        its_1.append(res[1.0])
+        assert res[1e-3] < res[1.0], (k, res)
+        if precision == "fp64" and k == 6:
+            for alpha in (1e-3, 1.0):
+                _, info = O.solve(W.with_(q, alpha=alpha, tol=1e-9, m=40), maxit=400)
+                assert abs(info["its"] - res[alpha]) <= 1, (alpha, info["its"], res[alpha])
+    assert max(its_a) - min(its_a) <= 1, its_a
+    print(precision, "P_alpha its", its_a, "P_1 its", its_1)
+
+
 RZS = W.riesz_sym_1023x512()
 
 
