@@ -227,12 +227,15 @@ struct Handle {
   // symmetric Riesz operator (no drift): tau Abar = Q diag(lambda) Q^T; step (b) is
   // z2_k = Q diag(D_k) Q^T z1_k with D_k,j = (1/lambda_{2,k}) / (mu_k - lambda_j)
   bool rz_sym = false;
-  float* rz_q = nullptr;    // Q, row-major [x][j] (FP32)
-  float* rz_qt = nullptr;   // Q^T, row-major [j][x] (FP32)
   float2* rz_dk = nullptr;  // D, [k][j] (FP32 complex)
   float2* rz_w = nullptr;   // D o (Q^T z1) per bin, K x rz_ldq complex
   float2* rz_part = nullptr;  // partial products of the contraction segments
   int rz_ldq = 0;           // leading dimension of Q, Q^T, D and the workspaces
+  // TF32 head and tail (x = hi + lo) of Q, row-major [x][j], and of Q^T, [j][x]: the tensor-core
+  // operands, zero-padded to rz_ldq
+  float *rz_qh = nullptr, *rz_ql = nullptr;
+  float *rz_qth = nullptr, *rz_qtl = nullptr;
+  int* rz_err = nullptr;    // set by a tensor-core product whose bounded wait gave up
 
   // FGMRES workspace (grown on demand)
   int ws_m = 0;

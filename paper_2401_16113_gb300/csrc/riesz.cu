@@ -18,10 +18,12 @@
 //                nt/2+1 bins, factored in place by blocked right-looking LU without pivoting
 //                (FP32 complex; the matrices are diagonally dominant, see the design notes).
 //   k_rz_trsv    per apply: forward (unit L) and backward (U) blocked substitution of every bin.
-//   k_rz_cgemm   step (b) when the operator is symmetric (no drift): with tau Abar = Q diag(lambda) Q^T
+//   k_rz_tc      step (b) when the operator is symmetric (no drift): with tau Abar = Q diag(lambda) Q^T
 //                (eigendecomposition at aao_create), z2_k = Q diag(D_k) Q^T z1_k for every bin is two
-//                products of the K x Nx complex half spectrum with the real Nx x Nx matrix Q.
+//                products of the K x Nx complex half spectrum with the real Nx x Nx matrix Q, on the
+//                tensor cores (3xTF32); k_rz_cgemm_sum adds their contraction segments in order.
 #include <math.h>
+#include <string.h>
 
 #include <complex>
 #include <vector>
@@ -39,86 +41,10 @@ using namespace pdev;
 constexpr int kNB = 32;  // LU / substitution block
 
 // ------------------------------------------------------------------- spectral step (b)
-// Partial products P[s][k][n] = sum_{m in segment s} A[k][m] B[m][n] for bins k < Kb: A complex
-// rows of pitch lda (FP32 complex), B real row-major with leading dimension ldb, segment s =
-// [s Mseg, (s+1) Mseg) with Mseg a multiple of kGM, columns n < gridDim.x kGN <= ldb (the tables
-// are zero-padded, so padded rows and columns contribute zeros). A CTA computes kGB bins x kGN
-// columns of one segment; thread (tb, tn) holds bins 4 tb .. 4 tb + 3 and columns 4 tn + {0..3}
-// and 64 + 4 tn + {0..3}: per contraction index 4 shared loads of 16 bytes feed 64 FMAs. Both
-// tiles go through shared memory, the next chunk's loads are issued before the current products.
-// The segments are summed in a fixed order by k_rz_cgemm_sum (deterministic, no atomics).
-constexpr int kGB = 32, kGN = 128, kGM = 16, kGSplit = 4;
-__global__ void __launch_bounds__(128) k_rz_cgemm(const float2* __restrict__ A, int lda, const float* __restrict__ B,
-                                                  int ldb, float2* __restrict__ P, int ldp, int Kb, int Mseg) {
-  __shared__ __align__(16) float2 As[kGM][kGB + 2];  // [m][bin], +2: transposed stores 2-way
-  __shared__ __align__(16) float Bs[kGM][kGN];
-  pdl_sync();
-  const int tb = threadIdx.x >> 4, tn = threadIdx.x & 15;
-  const int b0 = blockIdx.y * kGB, n0 = blockIdx.x * kGN, seg = blockIdx.z;
-  const int mbeg = seg * Mseg, mend = mbeg + Mseg;
-  const float2 zero = make_float2(0.f, 0.f);
-  float2 acc[4][8];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int q = 0; q < 8; ++q) acc[i][q] = zero;
-  // A tile: 32 bins x 16 m complex (4 per thread: bin = e >> 4, m = e & 15, e = t + 128 i);
-  // B tile: 16 rows x 128 floats (4 float4 per thread: row = e >> 5, column group = e & 31)
-  float2 ra[4];
-  float4 rb[4];
-  auto fetch = [&](int m0) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int e = threadIdx.x + 128 * i, bin = b0 + (e >> 4);
-      ra[i] = bin < Kb ? __ldg(A + (size_t)bin * lda + m0 + (e & 15)) : zero;
-      rb[i] = __ldg(reinterpret_cast<const float4*>(B + (size_t)(m0 + (e >> 5)) * ldb + n0 + 4 * (e & 31)));
-    }
-  };
-  fetch(mbeg);
-  for (int m0 = mbeg; m0 < mend; m0 += kGM) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int e = threadIdx.x + 128 * i;
-      As[e & 15][e >> 4] = ra[i];
-      *reinterpret_cast<float4*>(&Bs[e >> 5][4 * (e & 31)]) = rb[i];
-    }
-    __syncthreads();
-    if (m0 + kGM < mend) fetch(m0 + kGM);
-#pragma unroll
-    for (int mm = 0; mm < kGM; ++mm) {
-      const float4 a01 = *reinterpret_cast<const float4*>(&As[mm][4 * tb]);
-      const float4 a23 = *reinterpret_cast<const float4*>(&As[mm][4 * tb + 2]);
-      const float4 bl = *reinterpret_cast<const float4*>(&Bs[mm][4 * tn]);
-      const float4 bh = *reinterpret_cast<const float4*>(&Bs[mm][64 + 4 * tn]);
-      const float ar[4] = {a01.x, a01.z, a23.x, a23.z}, ai[4] = {a01.y, a01.w, a23.y, a23.w};
-      const float bv[8] = {bl.x, bl.y, bl.z, bl.w, bh.x, bh.y, bh.z, bh.w};
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          acc[i][q].x = fmaf(ar[i], bv[q], acc[i][q].x);
-          acc[i][q].y = fmaf(ai[i], bv[q], acc[i][q].y);
-        }
-    }
-    __syncthreads();
-  }
-  float2* Ps = P + (size_t)seg * Kb * ldp;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int b = b0 + 4 * tb + i;
-    if (b >= Kb) continue;
-    float4* lo = reinterpret_cast<float4*>(Ps + (size_t)b * ldp + n0 + 4 * tn);
-    float4* hi = reinterpret_cast<float4*>(Ps + (size_t)b * ldp + n0 + 64 + 4 * tn);
-    lo[0] = make_float4(acc[i][0].x, acc[i][0].y, acc[i][1].x, acc[i][1].y);
-    lo[1] = make_float4(acc[i][2].x, acc[i][2].y, acc[i][3].x, acc[i][3].y);
-    hi[0] = make_float4(acc[i][4].x, acc[i][4].y, acc[i][5].x, acc[i][5].y);
-    hi[1] = make_float4(acc[i][6].x, acc[i][6].y, acc[i][7].x, acc[i][7].y);
-  }
-}
-
-// C[k][n] = (D[k][n] *) sum_s P[s][k][n] for k < Kb, n < N (N even; pairs of complex per thread)
+// C[k][n] = (D[k][n] *) sum_{s < nseg} P[s][k][n] for k < Kb, n < N (N even; pairs of complex
+// per thread), the segments added in order
 __global__ void __launch_bounds__(256) k_rz_cgemm_sum(const float2* __restrict__ P, int ldp, int Kb, int N,
-                                                      float2* __restrict__ C, int ldc,
+                                                      int nseg, float2* __restrict__ C, int ldc,
                                                       const float2* __restrict__ D, int ldd) {
   pdl_sync();
   const int half = N >> 1;
@@ -127,8 +53,7 @@ __global__ void __launch_bounds__(256) k_rz_cgemm_sum(const float2* __restrict__
     const int k = (int)(e / half), n = 2 * (int)(e - (size_t)k * half);
     const float4* src = reinterpret_cast<const float4*>(P + (size_t)k * ldp + n);
     float4 v = __ldg(src);
-#pragma unroll
-    for (int s = 1; s < kGSplit; ++s) {
+    for (int s = 1; s < nseg; ++s) {
       const float4 w = __ldg(reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(src) + s * plane));
       v.x += w.x; v.y += w.y; v.z += w.z; v.w += w.w;
     }
@@ -138,6 +63,211 @@ __global__ void __launch_bounds__(256) k_rz_cgemm_sum(const float2* __restrict__
     }
     *reinterpret_cast<float4*>(C + (size_t)k * ldc + n) = v;
   }
+}
+
+// ------------------------------------------------------- spectral step (b) on tensor cores
+// The same two products on the 5th-generation tensor cores (tcgen05.mma, FP32 accumulator in
+// TMEM). A CTA owns 128 output columns n and 32 bins of one contraction segment:
+//   D[n][(bin, c)] = sum_m Op[n][m] * Z[bin][m].c,  c = re, im  (MMA M = 128, N = 64, K = 8),
+// Op = Q^T (first product) or Q (second), both stored K-major ([n][m]). TF32 keeps 10 mantissa
+// bits, and step (c) multiplies errors by up to 1/alpha, so each operand is split into a TF32
+// head and a TF32 tail (x = hi + lo) and three products are accumulated,
+// hi*hi + hi*lo + lo*hi (the lo*lo term is below FP32 rounding): FP32 accuracy. Q's split is
+// made at create; the half spectrum's when it is staged. Operand tiles use the K-major layout
+// without swizzling: 8-row x 16-byte core matrices, adjacent along K 128 bytes apart and along
+// the rows 1024 bytes apart (32 contraction entries per staged chunk). Two chunks are staged
+// alternately; the MMAs of one run while the threads stage the next, a tcgen05.commit per chunk
+// arriving on that buffer's mbarrier. Every wait is bounded: on a timeout the kernel records an
+// error code and skips its output (the solve then reports a failure instead of hanging).
+namespace tcg {
+constexpr int kM = 128, kN = 64, kKC = 32, kBins = kN / 2, kSeg = 4;  // kSeg contraction segments
+constexpr uint32_t kAop = kM * kKC * 4, kBop = kN * kKC * 4;  // bytes of one operand tile
+constexpr uint32_t kStage = 2 * kAop + 2 * kBop;               // hi and lo of both operands
+constexpr uint32_t kSmem = 2 * kStage + 64 + 1024;             // two stages, barriers, alignment
+constexpr long long kSpinLimit = 1ll << 22;
+
+// byte offset of (row r, contraction index k < 32) in a K-major tile without swizzling
+__host__ __device__ constexpr uint32_t core_off(int r, int k) {
+  return (uint32_t)((((r >> 3) << 3) + (k >> 2)) * 128 + (r & 7) * 16 + (k & 3) * 4);
+}
+// shared-memory matrix descriptor: start address >> 4 (bits 0-13), leading byte offset (next
+// core matrix along K) >> 4 (bits 16-29), stride byte offset (next 8-row group) >> 4 (bits
+// 32-45), descriptor version 1 (bits 46-47), no swizzle (bits 61-63 zero)
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(1024u >> 4) << 32) |
+         (1ull << 46);
+}
+// instruction descriptor, kind::tf32: D FP32 (bits 4-5 = 1), A and B TF32 (bits 7-9 and 10-12 =
+// 2), both K-major (bits 15, 16 = 0), N >> 3 (bits 17-22), M >> 4 (bits 24-28)
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kN >> 3) << 17) |
+                            ((uint32_t)(kM >> 4) << 24);
+
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+__device__ __forceinline__ void mma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+      "l"(da), "l"(db), "r"(kIdesc), "r"(acc));
+}
+__device__ __forceinline__ void commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+// bounded wait for the completion of phase `parity` of an mbarrier; false on timeout
+__device__ __forceinline__ bool wait_parity(uint32_t mbar, uint32_t parity) {
+  for (long long i = 0; i < kSpinLimit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+}  // namespace tcg
+
+// P[seg][k][n] for k < Kb (see above). A: complex rows of pitch lda; Ohi/Olo: the operator's
+// head and tail, [n][m] with leading dimension ldo; segment seg = blockIdx.z covers
+// [seg Mseg, (seg+1) Mseg), Mseg a multiple of 32. err: set to 1 if a wait gave up.
+__global__ void __launch_bounds__(128, 1) k_rz_tc(const float2* __restrict__ A, int lda, const float* __restrict__ Ohi,
+                                                  const float* __restrict__ Olo, int ldo, float2* __restrict__ P,
+                                                  int ldp, int Kb, int Mseg, int* __restrict__ err) {
+  using namespace tcg;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  pdl_sync();
+  const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(smraw);
+  const uint32_t base = (s0 + 1023u) & ~1023u;  // 1024-aligned operand tiles
+  unsigned char* gbase = smraw + (base - s0);
+  const uint32_t mbar0 = base + 2 * kStage, slot = mbar0 + 16;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int n0 = blockIdx.x * kM, b0 = blockIdx.y * kBins, seg = blockIdx.z;
+  const int mbeg = seg * Mseg, nch = Mseg / kKC;
+
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar0) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar0 + 8) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(kN) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(gbase + 2 * kStage + 16);
+
+  // staging maps: 8 consecutive threads fill one 128-byte core matrix (conflict-free stores).
+  // Operator piece i of this thread: core matrix (row group rg, K group kc), row r7.
+  // Spectrum piece i: core matrix (rows of bins 4 rg .. 4 rg + 3, K group kc); thread t8 loads 2
+  // complex (K entries 4 kc + 2 (t8 >> 2) + {0, 1}) of bin 4 rg + (t8 & 3) and writes its re row
+  // 2 (t8 & 3) and im row 2 (t8 & 3) + 1.
+  float4 zv[4];
+  auto fetch_z = [&](int m0) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int e = tid + 128 * i, cm = e >> 3, t8 = e & 7;
+      const int bin = b0 + 4 * (cm >> 3) + (t8 & 3), q = 2 * (cm & 7) + (t8 >> 2);
+      zv[i] = bin < Kb ? __ldg(reinterpret_cast<const float4*>(A + (size_t)bin * lda + m0 + 2 * q))
+                       : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  };
+  if (nch > 0) fetch_z(mbeg);
+  bool ok = true;
+  for (int c = 0; c < nch; ++c) {
+    const int buf = c & 1;
+    const uint32_t st = base + buf * kStage;
+    unsigned char* gst = gbase + buf * kStage;
+    // that buffer's MMAs are done (the verdict is made block-uniform, so every thread takes the
+    // same path through the barriers below)
+    if (c >= 2) ok = __syncthreads_and(wait_parity(mbar0 + 8 * buf, ((c - 2) >> 1) & 1)) != 0;
+    if (!ok) break;
+    const int m0 = mbeg + c * kKC;
+    // operator tiles (head and tail): 16 core matrices x 8 K groups, 16-byte async copies
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int e = tid + 128 * i, r7 = e & 7, kc = (e >> 3) & 7, rg = e >> 6;
+      const int r = 8 * rg + r7;
+      const size_t src = (size_t)(n0 + r) * ldo + m0 + 4 * kc;
+      const uint32_t off = (uint32_t)((rg * 8 + kc) * 128 + r7 * 16);
+      cp_async<16>(gst + off, Ohi + src);
+      cp_async<16>(gst + kAop + off, Olo + src);
+    }
+    // spectrum tiles (head and tail) from the registers fetched during the previous chunk
+    float4 v[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = zv[i];
+    if (c + 1 < nch) fetch_z(m0 + kKC);
+    unsigned char* bh = gst + 2 * kAop;
+    unsigned char* bl = bh + kBop;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int e = tid + 128 * i, cm = e >> 3, t8 = e & 7;
+      const uint32_t off = (uint32_t)(cm * 128 + (2 * (t8 & 3)) * 16 + (t8 >> 2) * 8);
+      const float hr0 = tf32_rna(v[i].x), hi0 = tf32_rna(v[i].y), hr1 = tf32_rna(v[i].z), hi1 = tf32_rna(v[i].w);
+      const float lr0 = tf32_rna(v[i].x - hr0), li0 = tf32_rna(v[i].y - hi0), lr1 = tf32_rna(v[i].z - hr1),
+                  li1 = tf32_rna(v[i].w - hi1);
+      *reinterpret_cast<float2*>(bh + off) = make_float2(hr0, hr1);
+      *reinterpret_cast<float2*>(bh + off + 16) = make_float2(hi0, hi1);
+      *reinterpret_cast<float2*>(bl + off) = make_float2(lr0, lr1);
+      *reinterpret_cast<float2*>(bl + off + 16) = make_float2(li0, li1);
+    }
+    cp_async_wait_all();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int ks = 0; ks < kKC / 8; ++ks) {
+        const uint32_t ko = ks * 256;  // two core matrices along K per MMA
+        const uint64_t ah = sdesc(st + ko), al = sdesc(st + kAop + ko);
+        const uint64_t bh = sdesc(st + 2 * kAop + ko), bl = sdesc(st + 2 * kAop + kBop + ko);
+        mma(tmem, ah, bh, (c > 0 || ks > 0) ? 1u : 0u);
+        mma(tmem, ah, bl, 1u);
+        mma(tmem, al, bh, 1u);
+      }
+      commit(mbar0 + 8 * buf);
+    }
+  }
+  if (ok && nch > 0) {
+    const int last = nch - 1;
+    ok = __syncthreads_and(wait_parity(mbar0 + 8 * (last & 1), (last >> 1) & 1)) != 0;
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (ok) {
+    // warp w reads TMEM lanes 32 w .. 32 w + 31 (output columns n0 + 32 w + lane), 64 columns
+    const int n = n0 + 32 * warp + (tid & 31);
+    float2* Ps = P + (size_t)seg * Kb * ldp;
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      uint32_t v[32];
+      const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + 32 * half;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+          "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+            "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+            "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int bin = b0 + 16 * half + j;
+        if (bin < Kb) Ps[(size_t)bin * ldp + n] = make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
+      }
+    }
+  } else if (tid == 0) {
+    atomicExch(err, 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kN) : "memory");
 }
 
 // ------------------------------------------------------------------------------- matvec
@@ -577,7 +707,7 @@ int riesz_build(Handle& h) {
     }
     // Ad holds Q^T. Both orientations in FP32, zero-padded to ldq (a multiple of the products'
     // column tile, >= the spectrum's pitch)
-    const int ldq = ((nx + kGN - 1) / kGN) * kGN;
+    const int ldq = ((nx + tcg::kM - 1) / tcg::kM) * tcg::kM;
     std::vector<float> q((size_t)ldq * ldq, 0.f), qt((size_t)ldq * ldq, 0.f);
     for (int j = 0; j < nx; ++j)
       for (int x = 0; x < nx; ++x) {
@@ -598,11 +728,35 @@ int riesz_build(Handle& h) {
         dk[(size_t)k * ldq + j] = make_float2((float)v.real(), (float)v.imag());
       }
     }
-    AAO_TRY(up(&h.rz_q, q));
-    AAO_TRY(up(&h.rz_qt, qt));
+    // TF32 head and tail of Q and Q^T for the tensor-core products (x = hi + lo)
+    auto tf32 = [](float x) {
+      uint32_t u;
+      memcpy(&u, &x, 4);
+      if ((u & 0x7f800000u) != 0x7f800000u) {
+        u += 0x0fffu + ((u >> 13) & 1u);  // round to nearest even at 10 mantissa bits
+        u &= 0xffffe000u;
+      }
+      float r;
+      memcpy(&r, &u, 4);
+      return r;
+    };
+    std::vector<float> qh(q.size()), ql(q.size()), qth(q.size()), qtl(q.size());
+    for (size_t i = 0; i < q.size(); ++i) {
+      qh[i] = tf32(q[i]);
+      ql[i] = tf32(q[i] - qh[i]);
+      qth[i] = tf32(qt[i]);
+      qtl[i] = tf32(qt[i] - qth[i]);
+    }
+    AAO_TRY(up(&h.rz_qh, qh));
+    AAO_TRY(up(&h.rz_ql, ql));
+    AAO_TRY(up(&h.rz_qth, qth));
+    AAO_TRY(up(&h.rz_qtl, qtl));
+    AAO_TRY_CUDA(cudaMalloc(&h.rz_err, sizeof(int)));
+    AAO_TRY_CUDA(cudaMemsetAsync(h.rz_err, 0, sizeof(int), h.stream));
+    AAO_TRY_CUDA(cudaFuncSetAttribute(k_rz_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tcg::kSmem));
     AAO_TRY(up(&h.rz_dk, dk));
     AAO_TRY_CUDA(cudaMalloc(&h.rz_w, sizeof(float2) * (size_t)K * ldq));
-    AAO_TRY_CUDA(cudaMalloc(&h.rz_part, sizeof(float2) * (size_t)kGSplit * K * ldq));
+    AAO_TRY_CUDA(cudaMalloc(&h.rz_part, sizeof(float2) * (size_t)tcg::kSeg * K * ldq));
     h.rz_ldq = ldq;
     // the padding columns of the spectrum and of the workspace stay zero: every kernel writes
     // columns < nx only, or zeros
@@ -707,20 +861,26 @@ int riesz_rhs(Handle& h, double* b) {
 
 int riesz_solve_bins(Handle& h, void* spec) {
   if (h.rz_sym) {
-    // W = (Z1 Q) o D, then Z2 = W Q^T (rows: bins; the half spectrum is [k][x]); each product in
-    // kGSplit contraction segments, summed in order
+    // W = (Z1 Q) o D, then Z2 = W Q^T (rows: bins; the half spectrum is [k][x]) on the tensor
+    // cores, each product in tcg::kSeg contraction segments added in order
     const int ldq = h.rz_ldq;
     const double nq = (double)ldq * ldq;
-    ProfScope ps(AAO_K_TRIDIAG, h.stream, 2.0 * (nq * 4.0 + 2.0 * (double)h.K * ldq * 8.0));
-    const dim3 grid(ldq / kGN, (h.K + kGB - 1) / kGB, kGSplit);
+    ProfScope ps(AAO_K_TRIDIAG, h.stream, 2.0 * (nq * 8.0 + 2.0 * (double)h.K * ldq * 8.0));
+    // segments: as many as keep whole 32-entry chunks (the contraction lengths are multiples of 64)
+    auto segs = [](int mp) { return mp % (tcg::kKC * tcg::kSeg) == 0 ? tcg::kSeg : (mp % (2 * tcg::kKC) == 0 ? 2 : 1); };
+    const int s1 = segs(h.pitch), s2 = segs(ldq);
+    const dim3 g1(ldq / tcg::kM, (h.K + tcg::kBins - 1) / tcg::kBins, s1);
+    const dim3 g2(ldq / tcg::kM, (h.K + tcg::kBins - 1) / tcg::kBins, s2);
     const int sgrid = (int)((((size_t)h.K * ldq / 2) + 255) / 256);
-    AAO_TRY_CUDA(launch_pdl(k_rz_cgemm, grid, 128, 0, h.stream, (const float2*)spec, h.pitch, (const float*)h.rz_q,
-                            ldq, h.rz_part, ldq, h.K, h.pitch / kGSplit));
-    AAO_TRY_CUDA(launch_pdl(k_rz_cgemm_sum, sgrid, 256, 0, h.stream, (const float2*)h.rz_part, ldq, h.K, ldq,
+    AAO_TRY_CUDA(launch_pdl(k_rz_tc, g1, 128, tcg::kSmem, h.stream, (const float2*)spec, h.pitch,
+                            (const float*)h.rz_qth, (const float*)h.rz_qtl, ldq, h.rz_part, ldq, h.K, h.pitch / s1,
+                            h.rz_err));
+    AAO_TRY_CUDA(launch_pdl(k_rz_cgemm_sum, sgrid, 256, 0, h.stream, (const float2*)h.rz_part, ldq, h.K, ldq, s1,
                             h.rz_w, ldq, (const float2*)h.rz_dk, ldq));
-    AAO_TRY_CUDA(launch_pdl(k_rz_cgemm, grid, 128, 0, h.stream, (const float2*)h.rz_w, ldq, (const float*)h.rz_qt,
-                            ldq, h.rz_part, ldq, h.K, ldq / kGSplit));
-    AAO_TRY_CUDA(launch_pdl(k_rz_cgemm_sum, sgrid, 256, 0, h.stream, (const float2*)h.rz_part, ldq, h.K, h.pitch,
+    AAO_TRY_CUDA(launch_pdl(k_rz_tc, g2, 128, tcg::kSmem, h.stream, (const float2*)h.rz_w, ldq,
+                            (const float*)h.rz_qh, (const float*)h.rz_ql, ldq, h.rz_part, ldq, h.K, ldq / s2,
+                            h.rz_err));
+    AAO_TRY_CUDA(launch_pdl(k_rz_cgemm_sum, sgrid, 256, 0, h.stream, (const float2*)h.rz_part, ldq, h.K, h.pitch, s2,
                             (float2*)spec, h.pitch, (const float2*)nullptr, ldq));
     AAO_CHECK_LAUNCH();
     return AAO_OK;
