@@ -231,11 +231,13 @@ struct Handle {
   float2* rz_w = nullptr;   // D o (Q^T z1) per bin, K x rz_ldq complex
   float2* rz_part = nullptr;  // partial products of the contraction segments
   int rz_ldq = 0;           // leading dimension of Q, Q^T, D and the workspaces
-  // TF32 head and tail (x = hi + lo) of Q, row-major [x][j], and of Q^T, [j][x]: the tensor-core
-  // operands, zero-padded to rz_ldq
+  // TF32 head and tail (x = hi + lo) of Q (rows x, entries j) and of Q^T (rows j, entries x):
+  // the tensor-core operands, zero-padded to rz_ldq and stored in 8 x 16-byte core-matrix tiles
   float *rz_qh = nullptr, *rz_ql = nullptr;
   float *rz_qth = nullptr, *rz_qtl = nullptr;
   int* rz_err = nullptr;    // set by a tensor-core product whose bounded wait gave up
+  // TMA tensor maps (CUtensorMap, 128 bytes each) of the tiled Q^T head, tail, Q head, tail
+  alignas(64) unsigned char rz_tmap[4 * 128] = {};
 
   // FGMRES workspace (grown on demand)
   int ws_m = 0;

@@ -28,6 +28,9 @@
 #include <complex>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "krylov_dev.cuh"
 #include "precond_dev.cuh"
 
@@ -132,11 +135,37 @@ __device__ __forceinline__ bool wait_parity(uint32_t mbar, uint32_t parity) {
 }
 }  // namespace tcg
 
-// P[seg][k][n] for k < Kb (see above). A: complex rows of pitch lda; Ohi/Olo: the operator's
-// head and tail, [n][m] with leading dimension ldo; segment seg = blockIdx.z covers
-// [seg Mseg, (seg+1) Mseg), Mseg a multiple of 32. err: set to 1 if a wait gave up.
-__global__ void __launch_bounds__(128, 1) k_rz_tc(const float2* __restrict__ A, int lda, const float* __restrict__ Ohi,
-                                                  const float* __restrict__ Olo, int ldo, float2* __restrict__ P,
+// TMA load of one 16 KB operator tile: a box of 256 floats (8 core matrices of one row group) x 16
+// row groups from the tiled operator (see the tensor map made at create), completing on mbar
+__device__ __forceinline__ void tma_tile(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar)
+      : "memory");
+}
+// all 128 staging threads: true iff every one of them passes true (named barrier 1)
+__device__ __forceinline__ bool staging_all(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.and.pred q, 1, 128, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v)
+      : "memory");
+  return r != 0;
+}
+
+// P[seg][k][n] for k < Kb (see above). A: complex rows of pitch lda; thi / tlo: tensor maps of the
+// operator's head and tail, stored tiled at create (row group rg, K group kg, row r, entry q at
+// float ((rg (ldo/4) + kg) 8 + r) 4 + q); segment seg = blockIdx.z covers [seg Mseg, (seg+1) Mseg),
+// Mseg a multiple of 32. err: set to 1 if a wait gave up.
+// Warps 0-3 stage the spectrum tiles and write the output (thread 0 issues the MMAs); warp 4 is
+// the TMA producer of the operator tiles, running ahead as far as the two buffers allow. Per
+// buffer: `full` completes when both operator tiles have landed (transaction count), `empty`
+// when the MMAs that read the buffer have finished (tcgen05.commit).
+__global__ void __launch_bounds__(160, 1) k_rz_tc(const float2* __restrict__ A, int lda,
+                                                  const __grid_constant__ CUtensorMap thi,
+                                                  const __grid_constant__ CUtensorMap tlo, float2* __restrict__ P,
                                                   int ldp, int Kb, int Mseg, int* __restrict__ err) {
   using namespace tcg;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -144,14 +173,14 @@ __global__ void __launch_bounds__(128, 1) k_rz_tc(const float2* __restrict__ A, 
   const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(smraw);
   const uint32_t base = (s0 + 1023u) & ~1023u;  // 1024-aligned operand tiles
   unsigned char* gbase = smraw + (base - s0);
-  const uint32_t mbar0 = base + 2 * kStage, slot = mbar0 + 16;
+  const uint32_t bars = base + 2 * kStage;  // full[2] at +0, +8; empty[2] at +16, +24; TMEM slot +32
+  const uint32_t full0 = bars, empty0 = bars + 16, slot = bars + 32;
   const int tid = threadIdx.x, warp = tid >> 5;
   const int n0 = blockIdx.x * kM, b0 = blockIdx.y * kBins, seg = blockIdx.z;
   const int mbeg = seg * Mseg, nch = Mseg / kKC;
 
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar0) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar0 + 8) : "memory");
+    for (int i = 0; i < 4; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bars + 8 * i) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -160,110 +189,117 @@ __global__ void __launch_bounds__(128, 1) k_rz_tc(const float2* __restrict__ A, 
   }
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(gbase + 2 * kStage + 16);
+  const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(gbase + 2 * kStage + 32);
 
-  // staging maps: 8 consecutive threads fill one 128-byte core matrix (conflict-free stores).
-  // Operator piece i of this thread: core matrix (row group rg, K group kc), row r7.
-  // Spectrum piece i: core matrix (rows of bins 4 rg .. 4 rg + 3, K group kc); thread t8 loads 2
-  // complex (K entries 4 kc + 2 (t8 >> 2) + {0, 1}) of bin 4 rg + (t8 & 3) and writes its re row
-  // 2 (t8 & 3) and im row 2 (t8 & 3) + 1.
-  float4 zv[4];
-  auto fetch_z = [&](int m0) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int e = tid + 128 * i, cm = e >> 3, t8 = e & 7;
-      const int bin = b0 + 4 * (cm >> 3) + (t8 & 3), q = 2 * (cm & 7) + (t8 >> 2);
-      zv[i] = bin < Kb ? __ldg(reinterpret_cast<const float4*>(A + (size_t)bin * lda + m0 + 2 * q))
-                       : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-  };
-  if (nch > 0) fetch_z(mbeg);
   bool ok = true;
-  for (int c = 0; c < nch; ++c) {
-    const int buf = c & 1;
-    const uint32_t st = base + buf * kStage;
-    unsigned char* gst = gbase + buf * kStage;
-    // that buffer's MMAs are done (the verdict is made block-uniform, so every thread takes the
-    // same path through the barriers below)
-    if (c >= 2) ok = __syncthreads_and(wait_parity(mbar0 + 8 * buf, ((c - 2) >> 1) & 1)) != 0;
-    if (!ok) break;
-    const int m0 = mbeg + c * kKC;
-    // operator tiles (head and tail): 16 core matrices x 8 K groups, 16-byte async copies
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int e = tid + 128 * i, r7 = e & 7, kc = (e >> 3) & 7, rg = e >> 6;
-      const int r = 8 * rg + r7;
-      const size_t src = (size_t)(n0 + r) * ldo + m0 + 4 * kc;
-      const uint32_t off = (uint32_t)((rg * 8 + kc) * 128 + r7 * 16);
-      cp_async<16>(gst + off, Ohi + src);
-      cp_async<16>(gst + kAop + off, Olo + src);
-    }
-    // spectrum tiles (head and tail) from the registers fetched during the previous chunk
-    float4 v[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) v[i] = zv[i];
-    if (c + 1 < nch) fetch_z(m0 + kKC);
-    unsigned char* bh = gst + 2 * kAop;
-    unsigned char* bl = bh + kBop;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int e = tid + 128 * i, cm = e >> 3, t8 = e & 7;
-      const uint32_t off = (uint32_t)(cm * 128 + (2 * (t8 & 3)) * 16 + (t8 >> 2) * 8);
-      const float hr0 = tf32_rna(v[i].x), hi0 = tf32_rna(v[i].y), hr1 = tf32_rna(v[i].z), hi1 = tf32_rna(v[i].w);
-      const float lr0 = tf32_rna(v[i].x - hr0), li0 = tf32_rna(v[i].y - hi0), lr1 = tf32_rna(v[i].z - hr1),
-                  li1 = tf32_rna(v[i].w - hi1);
-      *reinterpret_cast<float2*>(bh + off) = make_float2(hr0, hr1);
-      *reinterpret_cast<float2*>(bh + off + 16) = make_float2(hi0, hi1);
-      *reinterpret_cast<float2*>(bl + off) = make_float2(lr0, lr1);
-      *reinterpret_cast<float2*>(bl + off + 16) = make_float2(li0, li1);
-    }
-    cp_async_wait_all();
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-      for (int ks = 0; ks < kKC / 8; ++ks) {
-        const uint32_t ko = ks * 256;  // two core matrices along K per MMA
-        const uint64_t ah = sdesc(st + ko), al = sdesc(st + kAop + ko);
-        const uint64_t bh = sdesc(st + 2 * kAop + ko), bl = sdesc(st + 2 * kAop + kBop + ko);
-        mma(tmem, ah, bh, (c > 0 || ks > 0) ? 1u : 0u);
-        mma(tmem, ah, bl, 1u);
-        mma(tmem, al, bh, 1u);
+  if (warp == 4) {
+    // producer: chunk c into buffer c & 1 once the MMAs of chunk c - 2 have released it
+    if ((tid & 31) == 0) {
+      for (int c = 0; c < nch; ++c) {
+        const int buf = c & 1;
+        if (c >= 2 && !wait_parity(empty0 + 8 * buf, ((c - 2) >> 1) & 1)) { ok = false; break; }
+        const uint32_t st = base + buf * kStage;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full0 + 8 * buf), "r"(2 * kAop)
+                     : "memory");
+        const int x = ((mbeg + c * kKC) / kKC) * 256, y = n0 / 8;
+        tma_tile(st, &thi, x, y, full0 + 8 * buf);
+        tma_tile(st + kAop, &tlo, x, y, full0 + 8 * buf);
       }
-      commit(mbar0 + 8 * buf);
+      if (!ok) atomicExch(err, 1);
     }
-  }
-  if (ok && nch > 0) {
-    const int last = nch - 1;
-    ok = __syncthreads_and(wait_parity(mbar0 + 8 * (last & 1), (last >> 1) & 1)) != 0;
-  }
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (ok) {
-    // warp w reads TMEM lanes 32 w .. 32 w + 31 (output columns n0 + 32 w + lane), 64 columns
-    const int n = n0 + 32 * warp + (tid & 31);
-    float2* Ps = P + (size_t)seg * Kb * ldp;
+    __syncwarp();  // the producer lane rejoins its warp before the final barrier
+  } else {
+    // spectrum piece i of this thread: core matrix cm = (row group: bins 4 (cm >> 3) ..,
+    // K group cm & 7), thread t8 loads 2 complex of bin 4 (cm >> 3) + (t8 & 3) at K entries
+    // 4 (cm & 7) + 2 (t8 >> 2) + {0, 1} and writes its re row and im row
+    float4 zv[4];
+    auto fetch_z = [&](int m0) {
 #pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      uint32_t v[32];
-      const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + 32 * half;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-          "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-            "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-            "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int bin = b0 + 16 * half + j;
-        if (bin < Kb) Ps[(size_t)bin * ldp + n] = make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
+      for (int i = 0; i < 4; ++i) {
+        const int e = tid + 128 * i, cm = e >> 3, t8 = e & 7;
+        const int bin = b0 + 4 * (cm >> 3) + (t8 & 3), q = 2 * (cm & 7) + (t8 >> 2);
+        zv[i] = bin < Kb ? __ldg(reinterpret_cast<const float4*>(A + (size_t)bin * lda + m0 + 2 * q))
+                         : make_float4(0.f, 0.f, 0.f, 0.f);
       }
+    };
+    if (nch > 0) fetch_z(mbeg);
+    for (int c = 0; c < nch; ++c) {
+      const int buf = c & 1;
+      const uint32_t st = base + buf * kStage;
+      unsigned char* gst = gbase + buf * kStage;
+      if (c >= 2) ok = staging_all(wait_parity(empty0 + 8 * buf, ((c - 2) >> 1) & 1));
+      if (!ok) break;
+      float4 v[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) v[i] = zv[i];
+      if (c + 1 < nch) fetch_z(mbeg + (c + 1) * kKC);
+      unsigned char* bh = gst + 2 * kAop;
+      unsigned char* bl = bh + kBop;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int e = tid + 128 * i, cm = e >> 3, t8 = e & 7;
+        const uint32_t off = (uint32_t)(cm * 128 + (2 * (t8 & 3)) * 16 + (t8 >> 2) * 8);
+        const float hr0 = tf32_rna(v[i].x), hi0 = tf32_rna(v[i].y), hr1 = tf32_rna(v[i].z), hi1 = tf32_rna(v[i].w);
+        const float lr0 = tf32_rna(v[i].x - hr0), li0 = tf32_rna(v[i].y - hi0), lr1 = tf32_rna(v[i].z - hr1),
+                    li1 = tf32_rna(v[i].w - hi1);
+        *reinterpret_cast<float2*>(bh + off) = make_float2(hr0, hr1);
+        *reinterpret_cast<float2*>(bh + off + 16) = make_float2(hi0, hi1);
+        *reinterpret_cast<float2*>(bl + off) = make_float2(lr0, lr1);
+        *reinterpret_cast<float2*>(bl + off + 16) = make_float2(li0, li1);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      // the operator tiles have landed (thread 0 waits; the verdict is shared at the barrier)
+      bool landed = true;
+      if (tid == 0) landed = wait_parity(full0 + 8 * buf, (c >> 1) & 1);
+      __syncwarp();
+      ok = staging_all(landed);
+      if (!ok) break;
+      if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+        for (int ks = 0; ks < kKC / 8; ++ks) {
+          const uint32_t ko = ks * 256;  // two core matrices along K per MMA
+          const uint64_t ah = sdesc(st + ko), al = sdesc(st + kAop + ko);
+          const uint64_t bh2 = sdesc(st + 2 * kAop + ko), bl2 = sdesc(st + 2 * kAop + kBop + ko);
+          mma(tmem, ah, bh2, (c > 0 || ks > 0) ? 1u : 0u);
+          mma(tmem, ah, bl2, 1u);
+          mma(tmem, al, bh2, 1u);
+        }
+        commit(empty0 + 8 * buf);
+      }
+      __syncwarp();
     }
-  } else if (tid == 0) {
-    atomicExch(err, 1);
+    if (ok && nch > 0) {
+      const int last = nch - 1;
+      ok = staging_all(wait_parity(empty0 + 8 * (last & 1), (last >> 1) & 1));
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+      // warp w reads TMEM lanes 32 w .. 32 w + 31 (output columns n0 + 32 w + lane), 64 columns
+      const int n = n0 + 32 * warp + (tid & 31);
+      float2* Ps = P + (size_t)seg * Kb * ldp;
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        uint32_t v[32];
+        const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + 32 * half;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+              "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+              "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int bin = b0 + 16 * half + j;
+          if (bin < Kb) Ps[(size_t)bin * ldp + n] = make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
+        }
+      }
+    } else if (tid == 0) {
+      atomicExch(err, 1);
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -614,6 +650,45 @@ int grid_for(size_t n) {
 }  // namespace
 
 // ------------------------------------------------------------------------------- host
+namespace {
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link against libcuda)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    cudaGetLastError();
+  }
+  return fn;
+}
+// the 2-D map over a tiled operator: rows of ldq * 8 floats (one row group: ldq / 4 core
+// matrices of 8 rows x 4 entries), ldq / 8 row groups; boxes of 256 floats x 16 row groups
+int encode_operator_map(void* map, float* tiled, int ldq) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) {
+    set_error("aao_create: cuTensorMapEncodeTiled is not available");
+    return AAO_ECUDA;
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)ldq * 8, (cuuint64_t)ldq / 8};
+  const cuuint64_t strides[1] = {(cuuint64_t)ldq * 8 * sizeof(float)};
+  const cuuint32_t box[2] = {256, 16};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(reinterpret_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, tiled, dims, strides,
+                         box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("aao_create: cuTensorMapEncodeTiled failed for the spectral operator");
+    return AAO_ECUDA;
+  }
+  return AAO_OK;
+}
+}  // namespace
+
 int riesz_build(Handle& h) {
   const aao_problem& p = h.p;
   const int nx = h.nx, nt = h.nt;
@@ -740,17 +815,27 @@ int riesz_build(Handle& h) {
       memcpy(&r, &u, 4);
       return r;
     };
+    // stored tiled for the TMA boxes: entry (row r, contraction index k) at float
+    // ((r/8 (ldq/4) + k/4) 8 + r%8) 4 + k%4, i.e. 8 x 16-byte core matrices, K groups of a row
+    // group contiguous
     std::vector<float> qh(q.size()), ql(q.size()), qth(q.size()), qtl(q.size());
-    for (size_t i = 0; i < q.size(); ++i) {
-      qh[i] = tf32(q[i]);
-      ql[i] = tf32(q[i] - qh[i]);
-      qth[i] = tf32(qt[i]);
-      qtl[i] = tf32(qt[i] - qth[i]);
-    }
+    for (int r = 0; r < ldq; ++r)
+      for (int k = 0; k < ldq; ++k) {
+        const size_t t = ((((size_t)(r >> 3) * (ldq / 4) + (k >> 2)) * 8 + (r & 7)) * 4) + (k & 3);
+        const float a = q[(size_t)r * ldq + k], b = qt[(size_t)r * ldq + k];
+        qh[t] = tf32(a);
+        ql[t] = tf32(a - qh[t]);
+        qth[t] = tf32(b);
+        qtl[t] = tf32(b - qth[t]);
+      }
     AAO_TRY(up(&h.rz_qh, qh));
     AAO_TRY(up(&h.rz_ql, ql));
     AAO_TRY(up(&h.rz_qth, qth));
     AAO_TRY(up(&h.rz_qtl, qtl));
+    AAO_TRY(encode_operator_map(h.rz_tmap + 0 * 128, h.rz_qth, ldq));
+    AAO_TRY(encode_operator_map(h.rz_tmap + 1 * 128, h.rz_qtl, ldq));
+    AAO_TRY(encode_operator_map(h.rz_tmap + 2 * 128, h.rz_qh, ldq));
+    AAO_TRY(encode_operator_map(h.rz_tmap + 3 * 128, h.rz_ql, ldq));
     AAO_TRY_CUDA(cudaMalloc(&h.rz_err, sizeof(int)));
     AAO_TRY_CUDA(cudaMemsetAsync(h.rz_err, 0, sizeof(int), h.stream));
     AAO_TRY_CUDA(cudaFuncSetAttribute(k_rz_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tcg::kSmem));
@@ -872,14 +957,14 @@ int riesz_solve_bins(Handle& h, void* spec) {
     const dim3 g1(ldq / tcg::kM, (h.K + tcg::kBins - 1) / tcg::kBins, s1);
     const dim3 g2(ldq / tcg::kM, (h.K + tcg::kBins - 1) / tcg::kBins, s2);
     const int sgrid = (int)((((size_t)h.K * ldq / 2) + 255) / 256);
-    AAO_TRY_CUDA(launch_pdl(k_rz_tc, g1, 128, tcg::kSmem, h.stream, (const float2*)spec, h.pitch,
-                            (const float*)h.rz_qth, (const float*)h.rz_qtl, ldq, h.rz_part, ldq, h.K, h.pitch / s1,
-                            h.rz_err));
+    CUtensorMap m[4];
+    memcpy(m, h.rz_tmap, sizeof m);
+    AAO_TRY_CUDA(launch_pdl(k_rz_tc, g1, 160, tcg::kSmem, h.stream, (const float2*)spec, h.pitch, m[0], m[1],
+                            h.rz_part, ldq, h.K, h.pitch / s1, h.rz_err));
     AAO_TRY_CUDA(launch_pdl(k_rz_cgemm_sum, sgrid, 256, 0, h.stream, (const float2*)h.rz_part, ldq, h.K, ldq, s1,
                             h.rz_w, ldq, (const float2*)h.rz_dk, ldq));
-    AAO_TRY_CUDA(launch_pdl(k_rz_tc, g2, 128, tcg::kSmem, h.stream, (const float2*)h.rz_w, ldq,
-                            (const float*)h.rz_qh, (const float*)h.rz_ql, ldq, h.rz_part, ldq, h.K, ldq / s2,
-                            h.rz_err));
+    AAO_TRY_CUDA(launch_pdl(k_rz_tc, g2, 160, tcg::kSmem, h.stream, (const float2*)h.rz_w, ldq, m[2], m[3],
+                            h.rz_part, ldq, h.K, ldq / s2, h.rz_err));
     AAO_TRY_CUDA(launch_pdl(k_rz_cgemm_sum, sgrid, 256, 0, h.stream, (const float2*)h.rz_part, ldq, h.K, h.pitch, s2,
                             (float2*)spec, h.pitch, (const float2*)nullptr, ldq));
     AAO_CHECK_LAUNCH();
