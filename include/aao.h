@@ -116,7 +116,8 @@ int precond_apply(aao_handle* h, const double* v_dev, double* z_dev);
    the vector's norm, the least-squares update uses Givens rotations, all in FP64; the true
    residual is recomputed at every restart. 1 <= m <= 64,
    maxit >= 1 bounds the total inner iterations. st may be NULL. Returns AAO_OK,
-   AAO_NOT_CONVERGED, AAO_BREAKDOWN or an error. */
+   AAO_NOT_CONVERGED, AAO_BREAKDOWN, AAO_TIMEOUT (a tensor-core product of the symmetric Riesz
+   operator's step (b) gave up a bounded wait and skipped its output) or an error. */
 int fgmres_solve(aao_handle* h, const double* b_dev, double* x_dev, double tol, int m, int maxit,
                  aao_stats* st);
 

@@ -786,6 +786,17 @@ int run_fgmres(Handle& h, const double* b, double* x, double tol, int m, int max
       ++restarts;
     }
   }
+  if (h.rz_err) {
+    // a tensor-core product of the spectral step (b) whose bounded wait gave up (its output was
+    // skipped): report it rather than the solve's status
+    int e = 0;
+    AAO_TRY_CUDA(cudaMemcpyAsync(&e, h.rz_err, sizeof(int), cudaMemcpyDeviceToHost, h.stream));
+    AAO_TRY_CUDA(cudaStreamSynchronize(h.stream));
+    if (e) {
+      AAO_TRY_CUDA(cudaMemsetAsync(h.rz_err, 0, sizeof(int), h.stream));
+      status = AAO_TIMEOUT;
+    }
+  }
   const auto t1 = std::chrono::steady_clock::now();
   if (st) {
     st->status = status;
