@@ -556,54 +556,43 @@ __global__ void __launch_bounds__(64) k_rz_diaginv(const float2* __restrict__ LU
   for (int i = 0; i < kNB; ++i) out[i * kNB + lane] = x[i];
 }
 
-// Bin k: (mu_k I - A~) z = z1_k / lambda2_k with the LU factors; in place on the half spectrum.
-// Blocked substitution: for each kNB-row block, the rows' products with the solved part of z
-// (warps over rows, lanes over columns, eight loads in flight per lane), then the block itself by
-// its stored inverse (one product instead of kNB dependent steps).
+// In-place transpose of every bin's nx x nx factor matrix (made once at create, after the
+// diagonal-block inverses): the substitutions read the factors column by column.
+__global__ void k_rz_transpose(float2* __restrict__ LU, int nx) {
+  float2* M = LU + (size_t)blockIdx.y * nx * nx;
+  const size_t total = (size_t)nx * nx;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / nx), j = (int)(e - (size_t)i * nx);
+    if (i < j) {
+      const float2 a = M[e], b = M[(size_t)j * nx + i];
+      M[e] = b;
+      M[(size_t)j * nx + i] = a;
+    }
+  }
+}
+
+// Step (b) per apply for the Riesz operator with drift: for bin k, z <- (1/lambda_2) z, then
+// L y = z (unit lower) and U x = y with the LU factors of aao_create, stored transposed
+// (F[j nx + i] = LU[i][j]). Right-looking blocked substitution over 32-row blocks: solve the
+// block with its stored diagonal-block inverse (a 32 x 32 product), then remove its
+// contribution from every remaining row, z_i -= sum_{j in block} F[j nx + i] x_j, one row per
+// thread: for each column j of the block the threads read consecutive rows (coalesced), the 32
+// loads of a row issued together. One 512-thread CTA per bin; z in shared memory.
 __global__ void __launch_bounds__(512) k_rz_trsv(float2* __restrict__ spec, int nx, int pitch,
-                                                 const float2* __restrict__ LU, const float2* __restrict__ dinv,
+                                                 const float2* __restrict__ LUt, const float2* __restrict__ dinv,
                                                  const float2* __restrict__ il2) {
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* z = reinterpret_cast<float2*>(smraw);  // nx
   float2* t = z + nx;                            // kNB
+  pdl_sync();
   const int k = blockIdx.x;
-  const float2* A = LU + (size_t)k * nx * nx;
+  const float2* F = LUt + (size_t)k * nx * nx;
   float2* row = spec + (size_t)k * pitch;
   const float2 sk = il2[k];
   for (int i = threadIdx.x; i < nx; i += blockDim.x) z[i] = cmul(row[i], sk);
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int nb = (nx + kNB - 1) / kNB;
-  auto rowdot = [&](const float2* ri, int j0, int j1) {
-    float ax = 0.f, ay = 0.f, bx = 0.f, by = 0.f;
-    int j = j0 + lane;
-    for (; j + 224 < j1; j += 256) {
-      float2 l[8], v[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) l[u] = __ldg(ri + j + 32 * u);
-#pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = z[j + 32 * u];
-#pragma unroll
-      for (int u = 0; u < 8; u += 2) {
-        ax = fmaf(l[u].x, v[u].x, fmaf(-l[u].y, v[u].y, ax));
-        ay = fmaf(l[u].x, v[u].y, fmaf(l[u].y, v[u].x, ay));
-        bx = fmaf(l[u + 1].x, v[u + 1].x, fmaf(-l[u + 1].y, v[u + 1].y, bx));
-        by = fmaf(l[u + 1].x, v[u + 1].y, fmaf(l[u + 1].y, v[u + 1].x, by));
-      }
-    }
-    for (; j < j1; j += 32) {
-      const float2 l = __ldg(ri + j), v = z[j];
-      ax = fmaf(l.x, v.x, fmaf(-l.y, v.y, ax));
-      ay = fmaf(l.x, v.y, fmaf(l.y, v.x, ay));
-    }
-    float sx = ax + bx, sy = ay + by;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      sx += __shfl_down_sync(0xffffffffu, sx, o);
-      sy += __shfl_down_sync(0xffffffffu, sy, o);
-    }
-    return make_float2(sx, sy);
-  };
   // z_b <- Inv t over the block's w rows (warps over rows, lanes over columns)
   auto apply_inv = [&](const float2* inv, int r0, int w) {
     for (int i = warp; i < w; i += nw) {
@@ -617,26 +606,53 @@ __global__ void __launch_bounds__(512) k_rz_trsv(float2* __restrict__ spec, int 
       if (lane == 0) z[r0 + i] = make_float2(px, py);
     }
   };
+  // z_i -= sum_{jj < w} F[(r0 + jj) nx + i] x_{r0 + jj} for rows i in [i0, i1)
+  auto update = [&](int r0, int w, int i0, int i1) {
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+      const float2* col = F + (size_t)r0 * nx + i;
+      float ax = 0.f, ay = 0.f, bx = 0.f, by = 0.f;
+      int jj = 0;
+      if (w == kNB) {  // full block: all 32 loads of the row issued before any product
+        float2 f[kNB];
+#pragma unroll
+        for (int u = 0; u < kNB; ++u) f[u] = __ldg(col + (size_t)u * nx);
+#pragma unroll
+        for (int u = 0; u < kNB; u += 2) {
+          const float2 xa = z[r0 + u], xb = z[r0 + u + 1];
+          ax = fmaf(f[u].x, xa.x, fmaf(-f[u].y, xa.y, ax));
+          ay = fmaf(f[u].x, xa.y, fmaf(f[u].y, xa.x, ay));
+          bx = fmaf(f[u + 1].x, xb.x, fmaf(-f[u + 1].y, xb.y, bx));
+          by = fmaf(f[u + 1].x, xb.y, fmaf(f[u + 1].y, xb.x, by));
+        }
+        jj = kNB;
+      }
+      for (; jj < w; ++jj) {
+        const float2 f = __ldg(col + (size_t)jj * nx), x = z[r0 + jj];
+        ax = fmaf(f.x, x.x, fmaf(-f.y, x.y, ax));
+        ay = fmaf(f.x, x.y, fmaf(f.y, x.x, ay));
+      }
+      const float2 zi = z[i];
+      z[i] = make_float2(zi.x - (ax + bx), zi.y - (ay + by));
+    }
+  };
   // forward: L y = z (unit lower)
   for (int bi = 0; bi < nb; ++bi) {
     const int r0 = bi * kNB, w = min(kNB, nx - r0);
-    for (int i = warp; i < w; i += nw) {
-      const float2 d = rowdot(A + (size_t)(r0 + i) * nx, 0, r0);
-      if (lane == 0) t[i] = csub(z[r0 + i], d);
-    }
+    if (threadIdx.x < w) t[threadIdx.x] = z[r0 + threadIdx.x];
     __syncthreads();
     apply_inv(dinv + (((size_t)k * nb + bi) * 2 + 0) * kNB * kNB, r0, w);
+    __syncthreads();
+    update(r0, w, r0 + w, nx);
     __syncthreads();
   }
   // backward: U x = y
   for (int bi = nb - 1; bi >= 0; --bi) {
     const int r0 = bi * kNB, w = min(kNB, nx - r0);
-    for (int i = warp; i < w; i += nw) {
-      const float2 d = rowdot(A + (size_t)(r0 + i) * nx, r0 + w, nx);
-      if (lane == 0) t[i] = csub(z[r0 + i], d);
-    }
+    if (threadIdx.x < w) t[threadIdx.x] = z[r0 + threadIdx.x];
     __syncthreads();
     apply_inv(dinv + (((size_t)k * nb + bi) * 2 + 1) * kNB * kNB, r0, w);
+    __syncthreads();
+    update(r0, w, 0, r0);
     __syncthreads();
   }
   for (int i = threadIdx.x; i < nx; i += blockDim.x) row[i] = z[i];
@@ -874,6 +890,9 @@ int riesz_build(Handle& h) {
     AAO_TRY_CUDA(cudaMalloc(&h.rz_dinv, sizeof(float2) * (size_t)K * nb * 2 * kNB * kNB));
     k_rz_diaginv<<<dim3(nb, K), 64, 0, h.stream>>>(h.rz_lu, h.rz_dinv, nx, nb);
     AAO_CHECK_LAUNCH();
+    // the substitutions read the factors transposed (column j contiguous)
+    k_rz_transpose<<<dim3(256, K), 256, 0, h.stream>>>(h.rz_lu, nx);
+    AAO_CHECK_LAUNCH();
   }
   AAO_TRY_CUDA(cudaStreamSynchronize(h.stream));
   cudaFree(d_tcol);
@@ -973,7 +992,8 @@ int riesz_solve_bins(Handle& h, void* spec) {
   const size_t smem = sizeof(float2) * ((size_t)h.nx + kNB);
   const double bytes = (double)h.K * ((double)h.nx * h.nx * 8.0 + 2.0 * h.nx * 8.0);
   ProfScope ps(AAO_K_TRIDIAG, h.stream, bytes);
-  k_rz_trsv<<<h.K, 512, smem, h.stream>>>((float2*)spec, h.nx, h.pitch, h.rz_lu, h.rz_dinv, h.il2f);
+  AAO_TRY_CUDA(launch_pdl(k_rz_trsv, h.K, 512, smem, h.stream, (float2*)spec, h.nx, h.pitch,
+                          (const float2*)h.rz_lu, (const float2*)h.rz_dinv, (const float2*)h.il2f));
   AAO_CHECK_LAUNCH();
   return AAO_OK;
 }
