@@ -134,6 +134,22 @@ def ncu_traffic(kernel_class):
     return e.get("dram_bytes_per_launch")
 
 
+def precond_roofline(prof, hbm_peak):
+    """The preconditioner apply (its three kernel classes) as one unit: algorithmic bytes per
+    apply (the kernels' argument sizes: the FP32 input, the half spectrum in and out of each
+    exchange, the tridiagonal factors, the FP32 output) over its device time per apply."""
+    cls = ("fft_fwd", "tridiag", "fft_inv")
+    applies = prof["fft_fwd"][0]
+    if not applies:
+        return None
+    ms = sum(prof[c][1] for c in cls) / applies
+    by = sum(prof[c][2] for c in cls) / applies
+    gbs = by / (ms / 1e3) / 1e9
+    return {"ms_per_apply": ms, "algorithmic_bytes_per_apply": by, "achieved": gbs, "unit": "GB/s",
+            "peak": hbm_peak, "frac": gbs / hbm_peak, "bound": "latency and issue (half spectrum L2-resident)",
+            "applies": applies}
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -347,6 +363,7 @@ def run_ours(args):
             "clocks": clk.summary(),
             "roofline": roof,
             "kernel_ms_per_solve": {c: prof[c][1] for c in prof},
+            "precond_apply": precond_roofline(prof, hbm_peak),
             "fp64_plain": {"value": fp64_value, "unit": "unknowns/s", "ms": min(ms64),
                            "iterations": st64["iterations"]},
             "e2e": {"value": e2e_val, "unit": "unknowns/s", "h2d_bytes_per_step": 8 * n,

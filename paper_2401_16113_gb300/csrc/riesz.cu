@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(160, 1) k_rz_tc(const float2* __restrict__ A, 
         *reinterpret_cast<float2*>(bl + off + 16) = make_float2(li0, li1);
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      // the operator tiles have landed (thread 0 waits; the verdict is shared at the barrier)
+      // the operator tiles have landed (thread 0 waits; the outcome is shared at the barrier)
       bool landed = true;
       if (tid == 0) landed = wait_parity(full0 + 8 * buf, (c >> 1) & 1);
       __syncwarp();
