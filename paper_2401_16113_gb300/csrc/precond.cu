@@ -22,6 +22,7 @@
 // The unitary DFT of Sec. 3.1 carries 1/sqrt(nt) in each direction; here the forward FFT is
 // unnormalised and the single 1/nt is folded into the unscaling table.
 #include <mutex>
+#include <vector>
 #include <unordered_map>
 
 #include "precond_dev.cuh"
@@ -249,8 +250,21 @@ int tune_precond(Handle& h) {
   // time the form the solver runs: mixed solves read an FP32 copy of the input (the zero bytes of
   // v serve as one)
   const float* vf = (h.mixed && h.p.op != AAO_OP_RIESZ) ? reinterpret_cast<const float*>(v) : nullptr;
+  // widths: the powers of two up to pmax and, for the register FFT (nt >= 128, any width), the
+  // widths whose tile count just fills the SMs once or twice (ceil(pairs / (k SMs))), so that no
+  // SM is left without a tile
+  std::vector<int> cand;
+  for (int P = 1; P <= pmax; P <<= 1) cand.push_back(P);
+  if (h.nt >= (1 << kRegFftMinLog2) && h.sms > 0) {
+    const int pairs = (h.nx + 1) / 2;
+    for (int k = 1; k <= 2; ++k) {
+      const int P = (pairs + k * h.sms - 1) / (k * h.sms);
+      if (P > 1 && P <= pmax && (P & (P - 1)) != 0) cand.push_back(P);
+    }
+  }
   // each width: one warm-up apply, then the fastest of five timed applies (robust to a slow rep)
-  for (int P = 1; P <= pmax && rc == AAO_OK; P <<= 1) {
+  for (size_t ci = 0; ci < cand.size() && rc == AAO_OK; ++ci) {
+    const int P = cand[ci];
     h.fft_p = P;
     rc = launch_precond(h, v, z, h.mixed, nullptr, vf);
     float pbest = 1e30f;

@@ -186,7 +186,7 @@ constexpr int kRegFftMinLog2 = 7;
 
 __host__ __device__ __forceinline__ size_t reg_fft_elems(int P, int N) { return (size_t)P * (N + N / 16); }
 
-__device__ __forceinline__ int tix(int t, int lp, int p) { return ((t + (t >> 4)) << lp) + p; }
+__device__ __forceinline__ int tix(int t, int P, int p) { return (t + (t >> 4)) * P + p; }
 
 // a * (c + i s)
 template <typename C>
@@ -258,7 +258,7 @@ __device__ __forceinline__ void dft_pow2(C* a) {
 // One shared-to-shared Stockham stage of radix 2^LR with Ns = 2^lns: virtual thread (p, u) takes
 // butterflies j = u + q N/16 (q < 16 / 2^LR) of column p. Two barriers (reads, then writes).
 template <typename C, int LR>
-__device__ __forceinline__ void reg_stage(C* __restrict__ data, int log2n, int lp, int lns,
+__device__ __forceinline__ void reg_stage(C* __restrict__ data, int log2n, int P, int lns,
                                           const C* __restrict__ tw, int p, int u, bool act) {
   constexpr int RR = 1 << LR, B = 16 / RR;
   const int n16 = 1 << (log2n - 4), stride = 1 << (log2n - LR), lts = log2n - lns - LR;
@@ -268,9 +268,9 @@ __device__ __forceinline__ void reg_stage(C* __restrict__ data, int log2n, int l
 #pragma unroll
     for (int q = 0; q < B; ++q) {
       const int j = u + q * n16, k = j & nsm;
-      a[q * RR] = data[tix(j, lp, p)];
+      a[q * RR] = data[tix(j, P, p)];
 #pragma unroll
-      for (int r = 1; r < RR; ++r) a[q * RR + r] = cmul(data[tix(j + r * stride, lp, p)], __ldg(tw + ((r * k) << lts)));
+      for (int r = 1; r < RR; ++r) a[q * RR + r] = cmul(data[tix(j + r * stride, P, p)], __ldg(tw + ((r * k) << lts)));
     }
   }
   __syncthreads();
@@ -281,7 +281,7 @@ __device__ __forceinline__ void reg_stage(C* __restrict__ data, int log2n, int l
       dft_pow2<LR>(a + q * RR);
       const int base = ((j >> lns) << (lns + LR)) + k;
 #pragma unroll
-      for (int r = 0; r < RR; ++r) data[tix(base + (r << lns), lp, p)] = a[q * RR + r];
+      for (int r = 0; r < RR; ++r) data[tix(base + (r << lns), P, p)] = a[q * RR + r];
     }
   }
   __syncthreads();
@@ -290,13 +290,13 @@ __device__ __forceinline__ void reg_stage(C* __restrict__ data, int log2n, int l
 // The stages between the first (radix 16, from global memory) and the last (radix 8); on entry
 // the first stage's output is in shared memory and a barrier has passed.
 template <typename C>
-__device__ __forceinline__ void reg_middle(C* data, int log2n, int lp, const C* tw, int p, int u, bool act) {
+__device__ __forceinline__ void reg_middle(C* data, int log2n, int P, const C* tw, int p, int u, bool act) {
   int lns = 4;
-  for (; lns + 4 <= log2n - 3; lns += 4) reg_stage<C, 4>(data, log2n, lp, lns, tw, p, u, act);
+  for (; lns + 4 <= log2n - 3; lns += 4) reg_stage<C, 4>(data, log2n, P, lns, tw, p, u, act);
   switch (log2n - 3 - lns) {
-    case 1: reg_stage<C, 1>(data, log2n, lp, lns, tw, p, u, act); break;
-    case 2: reg_stage<C, 2>(data, log2n, lp, lns, tw, p, u, act); break;
-    case 3: reg_stage<C, 3>(data, log2n, lp, lns, tw, p, u, act); break;
+    case 1: reg_stage<C, 1>(data, log2n, P, lns, tw, p, u, act); break;
+    case 2: reg_stage<C, 2>(data, log2n, P, lns, tw, p, u, act); break;
+    case 3: reg_stage<C, 3>(data, log2n, P, lns, tw, p, u, act); break;
     default: break;
   }
 }
@@ -305,17 +305,17 @@ __device__ __forceinline__ void reg_middle(C* data, int log2n, int lp, const C* 
 // (u = 0: 0 and Ns/2), so that bin k and its mirror N - k sit in the same thread. Element r of
 // butterfly j is bin j + r Ns. Reads shared memory only (no barrier needed afterwards).
 template <typename C>
-__device__ __forceinline__ void reg_last(const C* __restrict__ data, int log2n, int lp, const C* __restrict__ tw,
+__device__ __forceinline__ void reg_last(const C* __restrict__ data, int log2n, int P, const C* __restrict__ tw,
                                          int p, int u, C (&a)[8], C (&b)[8], int& ja, int& jb) {
   const int ns = 1 << (log2n - 3);
   ja = u;
   jb = u == 0 ? ns / 2 : ns - u;
-  a[0] = data[tix(ja, lp, p)];
-  b[0] = data[tix(jb, lp, p)];
+  a[0] = data[tix(ja, P, p)];
+  b[0] = data[tix(jb, P, p)];
 #pragma unroll
   for (int r = 1; r < 8; ++r) {
-    a[r] = cmul(data[tix(ja + r * ns, lp, p)], __ldg(tw + r * ja));
-    b[r] = cmul(data[tix(jb + r * ns, lp, p)], __ldg(tw + r * jb));
+    a[r] = cmul(data[tix(ja + r * ns, P, p)], __ldg(tw + r * ja));
+    b[r] = cmul(data[tix(jb + r * ns, P, p)], __ldg(tw + r * jb));
   }
   dft8(a);
   dft8(b);
@@ -361,9 +361,9 @@ __device__ __forceinline__ void fft_fwd_tile_reg(const IN* __restrict__ v, C_t<R
                                                  const C_t<R>* __restrict__ tw, R sc, int x0, unsigned char* smraw) {
   using C = C_t<R>;
   C* data = reinterpret_cast<C*>(smraw);
-  const int lp = __ffs(P) - 1, n16 = N >> 4;
-  const bool act = (int)threadIdx.x < (P << (log2n - 4));
-  const int p = threadIdx.x & (P - 1), u = threadIdx.x >> lp;
+  const int n16 = N >> 4;
+  const bool act = (int)threadIdx.x < P * n16;  // P need not be a power of two here
+  const int u = (int)threadIdx.x / P, p = (int)threadIdx.x - u * P;
   const int x = x0 + 2 * p;
   const bool ok0 = x < nx, ok1 = x + 1 < nx;
   if (act) {
@@ -381,14 +381,14 @@ __device__ __forceinline__ void fft_fwd_tile_reg(const IN* __restrict__ v, C_t<R
     }
     dft16(a);
 #pragma unroll
-    for (int r = 0; r < 16; ++r) data[tix(u * 16 + r, lp, p)] = a[r];
+    for (int r = 0; r < 16; ++r) data[tix(u * 16 + r, P, p)] = a[r];
   }
   __syncthreads();
-  reg_middle(data, log2n, lp, tw, p, u, act);
+  reg_middle(data, log2n, P, tw, p, u, act);
   if (act) {
     C a[8], b[8];
     int ja, jb;
-    reg_last(data, log2n, lp, tw, p, u, a, b, ja, jb);
+    reg_last(data, log2n, P, tw, p, u, a, b, ja, jb);
     // Z = A + iB packs the two real columns; A[k] = (Z[k] + conj Z[N-k]) / 2,
     // B[k] = (Z[k] - conj Z[N-k]) / 2i, for the bins k <= N/2 this thread holds
     const int ns = N >> 3;
@@ -422,9 +422,9 @@ __device__ __forceinline__ void fft_inv_tile_reg(const C_t<R>* __restrict__ spec
                                                  const C_t<R>* __restrict__ tw, int x0, unsigned char* smraw) {
   using C = C_t<R>;
   C* data = reinterpret_cast<C*>(smraw);
-  const int lp = __ffs(P) - 1, n16 = N >> 4, half = N >> 1;
-  const bool act = (int)threadIdx.x < (P << (log2n - 4));
-  const int p = threadIdx.x & (P - 1), u = threadIdx.x >> lp;
+  const int n16 = N >> 4, half = N >> 1;
+  const bool act = (int)threadIdx.x < P * n16;  // P need not be a power of two here
+  const int u = (int)threadIdx.x / P, p = (int)threadIdx.x - u * P;
   const int x = x0 + 2 * p;
   const bool ok0 = x < nx, ok1 = x + 1 < nx;
   if (act) {
@@ -442,14 +442,14 @@ __device__ __forceinline__ void fft_inv_tile_reg(const C_t<R>* __restrict__ spec
     }
     dft16(a);
 #pragma unroll
-    for (int r = 0; r < 16; ++r) data[tix(u * 16 + r, lp, p)] = a[r];
+    for (int r = 0; r < 16; ++r) data[tix(u * 16 + r, P, p)] = a[r];
   }
   __syncthreads();
-  reg_middle(data, log2n, lp, tw, p, u, act);
+  reg_middle(data, log2n, P, tw, p, u, act);
   if (act) {
     C a[8], b[8];
     int ja, jb;
-    reg_last(data, log2n, lp, tw, p, u, a, b, ja, jb);
+    reg_last(data, log2n, P, tw, p, u, a, b, ja, jb);
     const int ns = N >> 3;
 #pragma unroll
     for (int r = 0; r < 8; ++r) {

@@ -203,7 +203,8 @@ def test_fgmres_fp64_bs_put(aao):
 
 
 def test_fgmres_mixed_localvol_full_size(aao):
-    """Mixed precision 2047 x 2048 local volatility to relative residual 1e-8 (FP64 check)."""
+    """Mixed precision 2047 x 2048 local volatility to relative residual 1e-8 (FP64 check); the
+    option values at maturity within 1e-8 of sequential CN."""
     p = W.localvol_2047x2048("mixed")
     h = aao.aao_create(p)
     n = W.unknowns(p)
@@ -218,7 +219,7 @@ def test_fgmres_mixed_localvol_full_size(aao):
     U = O.sequential_cn(p)
     err = np.abs(xs.reshape(p["nt"], p["nx"])[-1] - U[-1]).max() / np.abs(U[-1]).max()
     print("mixed localvol: its", st["iterations"], "maturity error", err)
-    assert err <= 1e-7
+    assert err <= 1e-8
 
 
 def test_fgmres_host_variant_matches_device(aao):
@@ -419,7 +420,7 @@ def test_riesz_symmetric_full_size_solve():
     U = O.sequential_cn(p)
     err = np.abs(xs.reshape(p["nt"], p["nx"])[-1] - U[-1]).max() / np.abs(U[-1]).max()
     print("riesz symmetric full size: its", st["iterations"], "maturity error", err)
-    assert err <= 1e-6
+    assert err <= 1e-8
 
 
 def test_riesz_full_size_solve():
@@ -439,4 +440,4 @@ def test_riesz_full_size_solve():
     U = O.sequential_cn(p)
     err = np.abs(xs.reshape(p["nt"], p["nx"])[-1] - U[-1]).max() / np.abs(U[-1]).max()
     print("riesz full size: its", st["iterations"], "maturity error", err)
-    assert err <= 1e-6
+    assert err <= 1e-8
