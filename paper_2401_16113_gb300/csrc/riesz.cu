@@ -89,10 +89,9 @@ constexpr uint32_t kStage = 2 * kAop + 2 * kBop;               // hi and lo of b
 constexpr uint32_t kSmem = 2 * kStage + 64 + 1024;             // two stages, barriers, alignment
 constexpr long long kSpinLimit = 1ll << 22;
 
-// byte offset of (row r, contraction index k < 32) in a K-major tile without swizzling
-__host__ __device__ constexpr uint32_t core_off(int r, int k) {
-  return (uint32_t)((((r >> 3) << 3) + (k >> 2)) * 128 + (r & 7) * 16 + (k & 3) * 4);
-}
+// A staged operand tile (rows x 32 contraction entries, K-major, no swizzling) keeps entry
+// (row r, k) at byte ((r / 8) * 8 + k / 4) * 128 + (r % 8) * 16 + (k % 4) * 4: 8-row x 16-byte core
+// matrices, the 8 K groups of a row group contiguous.
 // shared-memory matrix descriptor: start address >> 4 (bits 0-13), leading byte offset (next
 // core matrix along K) >> 4 (bits 16-29), stride byte offset (next 8-row group) >> 4 (bits
 // 32-45), descriptor version 1 (bits 46-47), no swizzle (bits 61-63 zero)
