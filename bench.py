@@ -531,7 +531,7 @@ def run_extras(args, flush, stream, main):
                            "P_alpha": {"alpha": p["alpha"], "iterations": st_main["iterations"], "ms": ms_main,
                                        "value": n / (ms_main / 1e3)}}
 
-    riesz_solve(W.riesz_1023x512(), "riesz", "dense shifted LU factors (2.15 GB) read per apply")
+    riesz_solve(W.riesz_1023x512(), "riesz", "explicit inverses of the shifted matrices (2.15 GB) read per apply")
     riesz_solve(W.riesz_sym_1023x512(), "riesz_sym",
                 "eigendecomposition tau Abar = Q diag(lambda) Q^T; two complex x real products with Q per apply")
     return out

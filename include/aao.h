@@ -42,7 +42,9 @@ extern "C" {
                              preconditioner the time mean of those matrices (Sec. 5.3)      */
 #define AAO_OP_RIESZ 2    /* Riesz fractional operator (beta, Eq. 1.2 second case) in
                              log-price x in [-s_max, s_max] with drift (r - sigma^2/2) u_x;
-                             step (b) by dense shifted LU factors, or, when the drift vanishes
+                             step (b) by the explicit inverses of the shifted matrices (made at
+                             create from their LU factors; one dense product per bin and
+                             apply, nt/2+1 x nx^2 complex64 resident), or, when the drift vanishes
                              (r = sigma^2/2, a symmetric operator), by the eigendecomposition
                              tau Abar = Q diag(lambda) Q^T: two products with Q per apply   */
 

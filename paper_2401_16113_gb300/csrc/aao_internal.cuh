@@ -217,13 +217,14 @@ struct Handle {
   void *tri_fp = nullptr, *tri_fv = nullptr, *tri_fpcr = nullptr;
 
   // Riesz operator (dense Toeplitz): circulant-embedding spectrum (scaled by tau/2 / N2), its
-  // twiddles, (tau/2) first column / row / left-exterior coefficients, LU factors of step (b)
+  // twiddles, (tau/2) first column / row / left-exterior coefficients, inverses of step (b)
   int rz_n2 = 0, rz_log2n2 = 0;
   double2 *rz_chat = nullptr, *rz_tw = nullptr;
   double *rz_hcol = nullptr, *rz_hrow = nullptr, *rz_hcl = nullptr;
   float* Vf = nullptr;  // FP32 copy of the basis vector the next preconditioner apply reads (mixed)
-  float2* rz_lu = nullptr;
+  float2* rz_lu = nullptr;    // LU factors of the shifted matrices (freed once the inverses are made)
   float2* rz_dinv = nullptr;  // inverses of the factors' diagonal blocks (L, U per block and bin)
+  float2* rz_inv = nullptr;   // the inverses X_k of the shifted matrices, [k][i][j] (with drift)
   // symmetric Riesz operator (no drift): tau Abar = Q diag(lambda) Q^T; step (b) is
   // z2_k = Q diag(D_k) Q^T z1_k with D_k,j = (1/lambda_{2,k}) / (mu_k - lambda_j)
   bool rz_sym = false;
@@ -268,7 +269,9 @@ bool sym_eig(int n, double* A, double* w);
 int riesz_build(Handle& h);
 int riesz_matvec(Handle& h, const void* x, bool x_is_float, double* y, const double* b, const double* V, int nd, int m);
 int riesz_rhs(Handle& h, double* b);
-int riesz_solve_bins(Handle& h, void* spec);
+// step (b) of the Riesz operator on the half spectrum spec; *result: the buffer holding z2
+// (spec itself, or the workspace rz_w)
+int riesz_solve_bins(Handle& h, void* spec, void** result);
 // yf (residual modes, mixed precision): also write an FP32 copy of y
 int launch_matvec(Handle& h, const void* x, bool x_is_float, double* y, const double* b, const double* V = nullptr,
                   int nd = 0, int m = 0, bool with_bnorm = false, float* yf = nullptr);

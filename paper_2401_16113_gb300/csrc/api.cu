@@ -75,7 +75,7 @@ int validate(const aao_problem* p) {
     if (!(p->beta > 1.0) || !(p->beta <= 2.0)) { set_error("aao_create: Riesz order beta must lie in (1, 2]"); return AAO_EINVAL; }
     if (p->nx > 2048) { set_error("aao_create: Riesz operator needs nx <= 2048"); return AAO_EUNSUPPORTED; }
     const double factors = (double)(p->nt / 2 + 1) * p->nx * (double)p->nx * 8.0;
-    if (!riesz_symmetric(*p) && factors > 32e9) { set_error("aao_create: Riesz LU factors would exceed 32 GB"); return AAO_EUNSUPPORTED; }
+    if (!riesz_symmetric(*p) && factors > 32e9) { set_error("aao_create: Riesz step-(b) inverses would exceed 32 GB (twice that while they are made)"); return AAO_EUNSUPPORTED; }
   }
   if (p->payoff != AAO_PUT && p->payoff != AAO_CALL) { set_error("aao_create: unknown payoff"); return AAO_EINVAL; }
   if (p->precision != AAO_FP64 && p->precision != AAO_MIXED) { set_error("aao_create: unknown precision"); return AAO_EINVAL; }

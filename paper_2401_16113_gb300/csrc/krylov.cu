@@ -540,7 +540,7 @@ void free_handle(Handle& h) {
                   h.muf, h.il2f, h.twf, h.lam, h.ilam, h.lamf, h.ilamf, h.spec, h.V, h.Z, h.w, h.scal, h.part,
                   h.counter, h.rz_chat, h.rz_tw, h.rz_hcol, h.rz_hrow, h.rz_hcl, h.rz_lu, h.rz_dinv, h.tri, h.Vf, h.tri_fp,
                   h.tri_fv, h.tri_fpcr, h.rz_dk, h.rz_w,
-                  h.rz_part, h.rz_qh, h.rz_ql, h.rz_qth, h.rz_qtl, h.rz_err};
+                  h.rz_part, h.rz_qh, h.rz_ql, h.rz_qth, h.rz_qtl, h.rz_err, h.rz_inv};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (h.host_scal) cudaFreeHost(h.host_scal);

@@ -142,9 +142,13 @@ int run_precond(Handle& h, const double* v, void* z, bool z_is_float, const doub
   }
   AAO_CHECK_LAUNCH();
 
+  C* spec_b = spec;  // where step (b) leaves its result for step (c)
   if (h.p.op == AAO_OP_RIESZ) {
-    // step (b) with the dense Toeplitz operator: LU factors from aao_create
-    AAO_TRY(riesz_solve_bins(h, spec));
+    // step (b) with the dense Toeplitz operator: the inverses of the shifted matrices (with
+    // drift) or the eigendecomposition (symmetric), both made by aao_create
+    void* res = nullptr;
+    AAO_TRY(riesz_solve_bins(h, spec, &res));
+    spec_b = reinterpret_cast<C*>(res);
   } else if (TriPart tp; h.tri_fp && tri_part_layout(h, sizeof(R), tp)) {
     // step (b): partition method with the per-bin factors built with the handle, G bins of
     // tri_T = 2^lgT threads per CTA
@@ -201,12 +205,12 @@ int run_precond(Handle& h, const double* v, void* z, bool z_is_float, const doub
   if (z_is_float) {
     AAO_TRY(ensure_smem((const void*)k_fft_inv<R, float>, smem));
     ProfScope ps(AAO_K_FFT_INV, h.stream, nsp + nv * sizeof(float));
-    AAO_TRY_CUDA(launch_pdl(k_fft_inv<R, float>, grid, threads, smem, h.stream, spec, (float*)z, nx, N, h.log2n, P,
+    AAO_TRY_CUDA(launch_pdl(k_fft_inv<R, float>, grid, threads, smem, h.stream, spec_b, (float*)z, nx, N, h.log2n, P,
                             h.pitch, ilam, tw));
   } else {
     AAO_TRY(ensure_smem((const void*)k_fft_inv<R, double>, smem));
     ProfScope ps(AAO_K_FFT_INV, h.stream, nsp + nv * sizeof(double));
-    AAO_TRY_CUDA(launch_pdl(k_fft_inv<R, double>, grid, threads, smem, h.stream, spec, (double*)z, nx, N, h.log2n, P,
+    AAO_TRY_CUDA(launch_pdl(k_fft_inv<R, double>, grid, threads, smem, h.stream, spec_b, (double*)z, nx, N, h.log2n, P,
                             h.pitch, ilam, tw));
   }
   AAO_CHECK_LAUNCH();

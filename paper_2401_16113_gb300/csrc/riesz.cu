@@ -17,7 +17,11 @@
 //                at aao_create: the shifted matrices mu_k I - A~ of step (b) of Eq. 3.2 for the
 //                nt/2+1 bins, factored in place by blocked right-looking LU without pivoting
 //                (FP32 complex; the matrices are diagonally dominant, see the design notes).
-//   k_rz_trsv    per apply: forward (unit L) and backward (U) blocked substitution of every bin.
+//   k_rz_diaginv / k_rz_transpose / k_rz_inv
+//                at aao_create: the explicit inverses X_k = (mu_k I - A~)^{-1} from those factors
+//                (the factors are freed afterwards).
+//   k_rz_gemv    per apply: z2_k = X_k z1_k / lambda_2,k for every bin, a dense complex
+//                matrix-vector product that streams the inverses once (HBM-bound).
 //   k_rz_tc      step (b) when the operator is symmetric (no drift): with tau Abar = Q diag(lambda) Q^T
 //                (eigendecomposition at aao_create), z2_k = Q diag(D_k) Q^T z1_k for every bin is two
 //                products of the K x Nx complex half spectrum with the real Nx x Nx matrix Q, on the
@@ -556,7 +560,7 @@ __global__ void __launch_bounds__(64) k_rz_diaginv(const float2* __restrict__ LU
 }
 
 // In-place transpose of every bin's nx x nx factor matrix (made once at create, after the
-// diagonal-block inverses): the substitutions read the factors column by column.
+// diagonal-block inverses): the substitutions of k_rz_inv read the factors column by column.
 __global__ void k_rz_transpose(float2* __restrict__ LU, int nx) {
   float2* M = LU + (size_t)blockIdx.y * nx * nx;
   const size_t total = (size_t)nx * nx;
@@ -570,91 +574,124 @@ __global__ void k_rz_transpose(float2* __restrict__ LU, int nx) {
   }
 }
 
-// Step (b) per apply for the Riesz operator with drift: for bin k, z <- (1/lambda_2) z, then
-// L y = z (unit lower) and U x = y with the LU factors of aao_create, stored transposed
-// (F[j nx + i] = LU[i][j]). Right-looking blocked substitution over 32-row blocks: solve the
-// block with its stored diagonal-block inverse (a 32 x 32 product), then remove its
-// contribution from every remaining row, z_i -= sum_{j in block} F[j nx + i] x_j, one row per
-// thread: for each column j of the block the threads read consecutive rows (coalesced), the 32
-// loads of a row issued together. One 512-thread CTA per bin; z in shared memory.
-__global__ void __launch_bounds__(512) k_rz_trsv(float2* __restrict__ spec, int nx, int pitch,
-                                                 const float2* __restrict__ LUt, const float2* __restrict__ dinv,
-                                                 const float2* __restrict__ il2) {
+// The inverse of each shifted matrix, made once at create from its LU factors (transposed,
+// F[j nx + i] = LU[i][j]) and diagonal-block inverses: X_k = (mu_k I - A~)^{-1}, kRzInvCols
+// columns of the identity per CTA (in shared memory, nx x kRzInvCols complex) taken through
+// L Y = E (unit lower) and U X = Y by right-looking blocked substitution over 32-row blocks:
+// solve the block with its stored diagonal-block inverse, then remove its contribution from
+// every remaining row, the factor column read by consecutive threads (coalesced).
+// X is row-major [k][i][j].
+constexpr int kRzInvCols = 16;
+__global__ void __launch_bounds__(512) k_rz_inv(const float2* __restrict__ LUt, const float2* __restrict__ dinv,
+                                                float2* __restrict__ X, int nx, int nb) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  float2* z = reinterpret_cast<float2*>(smraw);  // nx
-  float2* t = z + nx;                            // kNB
-  pdl_sync();
-  const int k = blockIdx.x;
+  float2* Z = reinterpret_cast<float2*>(smraw);  // [i][c], nx x kRzInvCols
+  float2* t = Z + (size_t)nx * kRzInvCols;       // kNB x kRzInvCols
+  const int k = blockIdx.y, c0 = blockIdx.x * kRzInvCols;
+  const int nc = min(kRzInvCols, nx - c0);
   const float2* F = LUt + (size_t)k * nx * nx;
-  float2* row = spec + (size_t)k * pitch;
-  const float2 sk = il2[k];
-  for (int i = threadIdx.x; i < nx; i += blockDim.x) z[i] = cmul(row[i], sk);
+  const float2 zero = make_float2(0.f, 0.f);
+  for (int e = threadIdx.x; e < nx * kRzInvCols; e += blockDim.x) {
+    const int i = e / kRzInvCols, c = e - i * kRzInvCols;
+    Z[e] = (c < nc && i == c0 + c) ? make_float2(1.f, 0.f) : zero;
+  }
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int nb = (nx + kNB - 1) / kNB;
-  // z_b <- Inv t over the block's w rows (warps over rows, lanes over columns)
-  auto apply_inv = [&](const float2* inv, int r0, int w) {
-    for (int i = warp; i < w; i += nw) {
-      const float2 p = lane < w ? cmul(__ldg(inv + i * kNB + lane), t[lane]) : make_float2(0.f, 0.f);
-      float px = p.x, py = p.y;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        px += __shfl_down_sync(0xffffffffu, px, o);
-        py += __shfl_down_sync(0xffffffffu, py, o);
+  for (int s = 0; s < 2 * nb; ++s) {
+    const bool fwd = s < nb;
+    const int bi = fwd ? s : 2 * nb - 1 - s;
+    const int r0 = bi * kNB, w = min(kNB, nx - r0);
+    const float2* inv = dinv + (((size_t)k * nb + bi) * 2 + (fwd ? 0 : 1)) * kNB * kNB;
+    for (int e = threadIdx.x; e < w * kRzInvCols; e += blockDim.x) t[e] = Z[(size_t)r0 * kRzInvCols + e];
+    __syncthreads();
+    // the block: Z_b <- Inv t (w x w times w x kRzInvCols), one output per thread
+    for (int e = threadIdx.x; e < w * kRzInvCols; e += blockDim.x) {
+      const int i = e / kRzInvCols, c = e - i * kRzInvCols;
+      float2 acc = zero;
+      for (int q = 0; q < w; ++q) {
+        const float2 a = __ldg(inv + i * kNB + q), b = t[q * kRzInvCols + c];
+        acc = make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y)));
       }
-      if (lane == 0) z[r0 + i] = make_float2(px, py);
+      Z[(size_t)(r0 + i) * kRzInvCols + c] = acc;
     }
-  };
-  // z_i -= sum_{jj < w} F[(r0 + jj) nx + i] x_{r0 + jj} for rows i in [i0, i1)
-  auto update = [&](int r0, int w, int i0, int i1) {
-    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-      const float2* col = F + (size_t)r0 * nx + i;
-      float ax = 0.f, ay = 0.f, bx = 0.f, by = 0.f;
-      int jj = 0;
-      if (w == kNB) {  // full block: all 32 loads of the row issued before any product
-        float2 f[kNB];
+    __syncthreads();
+    // the remaining rows: Z_i -= sum_{jj < w} F[(r0 + jj) nx + i] Z_{r0 + jj}, a task = one row and
+    // four columns
+    const int i0 = fwd ? r0 + w : 0, i1 = fwd ? nx : r0;
+    for (int task = threadIdx.x; task < (i1 - i0) * 4; task += blockDim.x) {
+      const int i = i0 + (task >> 2), q4 = (task & 3) * 4;
+      float2 acc[4] = {zero, zero, zero, zero};
+      for (int jj = 0; jj < w; ++jj) {
+        const float2 f = __ldg(F + (size_t)(r0 + jj) * nx + i);
+        const float4 za = *reinterpret_cast<const float4*>(Z + (size_t)(r0 + jj) * kRzInvCols + q4);
+        const float4 zb = *reinterpret_cast<const float4*>(Z + (size_t)(r0 + jj) * kRzInvCols + q4 + 2);
+        const float2 zv[4] = {make_float2(za.x, za.y), make_float2(za.z, za.w), make_float2(zb.x, zb.y),
+                              make_float2(zb.z, zb.w)};
 #pragma unroll
-        for (int u = 0; u < kNB; ++u) f[u] = __ldg(col + (size_t)u * nx);
-#pragma unroll
-        for (int u = 0; u < kNB; u += 2) {
-          const float2 xa = z[r0 + u], xb = z[r0 + u + 1];
-          ax = fmaf(f[u].x, xa.x, fmaf(-f[u].y, xa.y, ax));
-          ay = fmaf(f[u].x, xa.y, fmaf(f[u].y, xa.x, ay));
-          bx = fmaf(f[u + 1].x, xb.x, fmaf(-f[u + 1].y, xb.y, bx));
-          by = fmaf(f[u + 1].x, xb.y, fmaf(f[u + 1].y, xb.x, by));
+        for (int c = 0; c < 4; ++c) {
+          acc[c].x = fmaf(f.x, zv[c].x, fmaf(-f.y, zv[c].y, acc[c].x));
+          acc[c].y = fmaf(f.x, zv[c].y, fmaf(f.y, zv[c].x, acc[c].y));
         }
-        jj = kNB;
       }
-      for (; jj < w; ++jj) {
-        const float2 f = __ldg(col + (size_t)jj * nx), x = z[r0 + jj];
-        ax = fmaf(f.x, x.x, fmaf(-f.y, x.y, ax));
-        ay = fmaf(f.x, x.y, fmaf(f.y, x.x, ay));
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float2& zi = Z[(size_t)i * kRzInvCols + q4 + c];
+        zi = make_float2(zi.x - acc[c].x, zi.y - acc[c].y);
       }
-      const float2 zi = z[i];
-      z[i] = make_float2(zi.x - (ax + bx), zi.y - (ay + by));
     }
-  };
-  // forward: L y = z (unit lower)
-  for (int bi = 0; bi < nb; ++bi) {
-    const int r0 = bi * kNB, w = min(kNB, nx - r0);
-    if (threadIdx.x < w) t[threadIdx.x] = z[r0 + threadIdx.x];
-    __syncthreads();
-    apply_inv(dinv + (((size_t)k * nb + bi) * 2 + 0) * kNB * kNB, r0, w);
-    __syncthreads();
-    update(r0, w, r0 + w, nx);
     __syncthreads();
   }
-  // backward: U x = y
-  for (int bi = nb - 1; bi >= 0; --bi) {
-    const int r0 = bi * kNB, w = min(kNB, nx - r0);
-    if (threadIdx.x < w) t[threadIdx.x] = z[r0 + threadIdx.x];
-    __syncthreads();
-    apply_inv(dinv + (((size_t)k * nb + bi) * 2 + 1) * kNB * kNB, r0, w);
-    __syncthreads();
-    update(r0, w, 0, r0);
-    __syncthreads();
+  for (int e = threadIdx.x; e < nx * kRzInvCols; e += blockDim.x) {
+    const int i = e / kRzInvCols, c = e - i * kRzInvCols;
+    if (c < nc) X[((size_t)k * nx + i) * nx + c0 + c] = Z[e];
   }
-  for (int i = threadIdx.x; i < nx; i += blockDim.x) row[i] = z[i];
+}
+
+// Step (b) per apply for the Riesz operator with drift: z_k = X_k (z1_k / lambda_2,k) for every
+// bin, a dense complex matrix-vector product (the inverses made at create). A CTA owns 16 rows of
+// one bin, a warp one row (lanes over columns, eight loads in flight per lane); the bin's
+// right-hand side is staged in shared memory. The result goes to out (the half spectrum's shape),
+// not in place: other CTAs of the bin still read the right-hand side.
+constexpr int kRzGemvRows = 16;
+__global__ void __launch_bounds__(32 * kRzGemvRows) k_rz_gemv(const float2* __restrict__ spec, float2* __restrict__ out,
+                                                            int nx, int pitch, const float2* __restrict__ X,
+                                                            const float2* __restrict__ il2) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* zb = reinterpret_cast<float2*>(smraw);  // nx
+  pdl_sync();
+  const int k = blockIdx.y, i = blockIdx.x * kRzGemvRows + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  const float2 sk = il2[k];
+  const float2* rhs = spec + (size_t)k * pitch;
+  for (int j = threadIdx.x; j < nx; j += blockDim.x) zb[j] = cmul(rhs[j], sk);
+  __syncthreads();
+  if (i >= nx) return;
+  const float2* xr = X + ((size_t)k * nx + i) * nx;
+  float ax = 0.f, ay = 0.f, bx = 0.f, by = 0.f;
+  int j = lane;
+  for (; j + 224 < nx; j += 256) {
+    float2 l[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) l[u] = __ldg(xr + j + 32 * u);
+#pragma unroll
+    for (int u = 0; u < 8; u += 2) {
+      const float2 va = zb[j + 32 * u], vb = zb[j + 32 * (u + 1)];
+      ax = fmaf(l[u].x, va.x, fmaf(-l[u].y, va.y, ax));
+      ay = fmaf(l[u].x, va.y, fmaf(l[u].y, va.x, ay));
+      bx = fmaf(l[u + 1].x, vb.x, fmaf(-l[u + 1].y, vb.y, bx));
+      by = fmaf(l[u + 1].x, vb.y, fmaf(l[u + 1].y, vb.x, by));
+    }
+  }
+  for (; j < nx; j += 32) {
+    const float2 l = __ldg(xr + j), v = zb[j];
+    ax = fmaf(l.x, v.x, fmaf(-l.y, v.y, ax));
+    ay = fmaf(l.x, v.y, fmaf(l.y, v.x, ay));
+  }
+  float sx = ax + bx, sy = ay + by;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sx += __shfl_down_sync(0xffffffffu, sx, o);
+    sy += __shfl_down_sync(0xffffffffu, sy, o);
+  }
+  if (lane == 0) out[(size_t)k * pitch + i] = make_float2(sx, sy);
 }
 
 int grid_for(size_t n) {
@@ -892,6 +929,21 @@ int riesz_build(Handle& h) {
     // the substitutions read the factors transposed (column j contiguous)
     k_rz_transpose<<<dim3(256, K), 256, 0, h.stream>>>(h.rz_lu, nx);
     AAO_CHECK_LAUNCH();
+    // the inverses X_k (an apply is then one matrix-vector product per bin); the factors and the
+    // block inverses are released afterwards
+    AAO_TRY_CUDA(cudaMalloc(&h.rz_inv, sizeof(float2) * nn * K));
+    const size_t ismem = sizeof(float2) * ((size_t)nx * kRzInvCols + (size_t)kNB * kRzInvCols);
+    AAO_TRY_CUDA(cudaFuncSetAttribute(k_rz_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem));
+    k_rz_inv<<<dim3((nx + kRzInvCols - 1) / kRzInvCols, K), 512, ismem, h.stream>>>(h.rz_lu, h.rz_dinv, h.rz_inv, nx,
+                                                                                    nb);
+    AAO_CHECK_LAUNCH();
+    AAO_TRY_CUDA(cudaStreamSynchronize(h.stream));
+    cudaFree(h.rz_lu);
+    cudaFree(h.rz_dinv);
+    h.rz_lu = nullptr;
+    h.rz_dinv = nullptr;
+    AAO_TRY_CUDA(cudaMalloc(&h.rz_w, sizeof(float2) * (size_t)K * h.pitch));
+    AAO_TRY_CUDA(cudaMemsetAsync(h.rz_w, 0, sizeof(float2) * (size_t)K * h.pitch, h.stream));
   }
   AAO_TRY_CUDA(cudaStreamSynchronize(h.stream));
   cudaFree(d_tcol);
@@ -962,7 +1014,8 @@ int riesz_rhs(Handle& h, double* b) {
   return AAO_OK;
 }
 
-int riesz_solve_bins(Handle& h, void* spec) {
+int riesz_solve_bins(Handle& h, void* spec, void** result) {
+  *result = spec;
   if (h.rz_sym) {
     // W = (Z1 Q) o D, then Z2 = W Q^T (rows: bins; the half spectrum is [k][x]) on the tensor
     // cores, each product in tcg::kSeg contraction segments added in order
@@ -988,12 +1041,14 @@ int riesz_solve_bins(Handle& h, void* spec) {
     AAO_CHECK_LAUNCH();
     return AAO_OK;
   }
-  const size_t smem = sizeof(float2) * ((size_t)h.nx + kNB);
+  // with drift: z2_k = X_k (z1_k / lambda_2,k) into the workspace
+  const size_t smem = sizeof(float2) * (size_t)h.nx;
   const double bytes = (double)h.K * ((double)h.nx * h.nx * 8.0 + 2.0 * h.nx * 8.0);
   ProfScope ps(AAO_K_TRIDIAG, h.stream, bytes);
-  AAO_TRY_CUDA(launch_pdl(k_rz_trsv, h.K, 512, smem, h.stream, (float2*)spec, h.nx, h.pitch,
-                          (const float2*)h.rz_lu, (const float2*)h.rz_dinv, (const float2*)h.il2f));
+  AAO_TRY_CUDA(launch_pdl(k_rz_gemv, dim3((h.nx + kRzGemvRows - 1) / kRzGemvRows, h.K), 32 * kRzGemvRows, smem, h.stream,
+                          (const float2*)spec, h.rz_w, h.nx, h.pitch, (const float2*)h.rz_inv, (const float2*)h.il2f));
   AAO_CHECK_LAUNCH();
+  *result = h.rz_w;
   return AAO_OK;
 }
 
