@@ -383,8 +383,9 @@ def run_ours(args):
 
 def run_extras(args, flush, stream, main):
     """The batched workload (512 instances, one persistent launch), the learned-alpha
-    deployment (8191 x 8192 local volatility), P_1 against P_alpha on the headline workload and
-    the Riesz fractional operator (1023 x 512, with and without drift); reported beside the
+    deployment (8191 x 8192 local volatility), P_1 against P_alpha on the headline workload, the
+    mixed-radix FFT (nt = 1536 against 2048) and the Riesz fractional operator (1023 x 512, with
+    and without drift); reported beside the
     headline number. main = (problem, device b, unknowns, ms per solve, stats) of the headline."""
     import numpy as np
     import torch
@@ -472,9 +473,9 @@ def run_extras(args, flush, stream, main):
                      "epochs": 200}}
     h.close()
 
-    # Riesz fractional operator (beta 1.5), 1023 x 512: dense Toeplitz step (b) by the batched LU
-    # (with drift), and without drift (r = sigma^2/2) by the eigendecomposition (two products
-    # with Q per apply); aao_create time reported beside each
+    # Riesz fractional operator (beta 1.5), 1023 x 512: dense Toeplitz step (b) by the explicit
+    # inverses of the shifted matrices (with drift), and without drift (r = sigma^2/2) by the
+    # eigendecomposition (two products with Q per apply); aao_create time reported beside each
     def riesz_solve(rz, key, how):
         t0 = time.time()
         hr = aao.aao_create(rz)
@@ -530,6 +531,42 @@ def run_extras(args, flush, stream, main):
                            "ms": best1, "value": n / (best1 / 1e3), "rel_residual": st1["rel_residual"]},
                            "P_alpha": {"alpha": p["alpha"], "iterations": st_main["iterations"], "ms": ms_main,
                                        "value": n / (ms_main / 1e3)}}
+
+    # mixed-radix FFT along t: the headline workload with nt = 1536 = 3 x 2^9 (shared-memory
+    # Stockham, radices 4, 4, 4, 4, 2, 3) against nt = 2048 (register FFT); per-apply FFT times
+    def fft_profile(q, b_=None):
+        hq = aao.aao_create(q)
+        nq = W.unknowns(q)
+        bq = b_ if b_ is not None else torch.empty(nq, dtype=torch.float64, device="cuda")
+        if b_ is None:
+            aao.aao_rhs(hq, bq)
+        xq = torch.zeros(nq, dtype=torch.float64, device="cuda")
+        aao.fgmres_solve(hq, bq, xq, TOL, q["m"], 300)
+        best, stq = None, None
+        for _ in range(3):
+            xq.zero_()
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            stq = aao.fgmres_solve(hq, bq, xq, TOL, q["m"], 300)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1)
+            best = t if best is None else min(best, t)
+        aao.aao_profile_enable(None)
+        xq.zero_()
+        aao.fgmres_solve(hq, bq, xq, TOL, q["m"], 300)
+        torch.cuda.synchronize()
+        fw, iv = aao.aao_profile_read("fft_fwd"), aao.aao_profile_read("fft_inv")
+        aao.aao_profile_enable([])
+        hq.close()
+        return {"nt": q["nt"], "unknowns": nq, "ms": best, "value": nq / (best / 1e3), "unit": "unknowns/s",
+                "iterations": stq["iterations"], "rel_residual": stq["rel_residual"],
+                "fft_fwd_ms_per_apply": fw[1] / max(fw[0], 1), "fft_inv_ms_per_apply": iv[1] / max(iv[0], 1)}
+
+    out["mixed_radix"] = {"workload": "localvol_2047x1536_mixed",
+                          "nt_1536": fft_profile(W.with_(p, nt=1536)),
+                          "nt_2048": fft_profile(p, b)}
 
     riesz_solve(W.riesz_1023x512(), "riesz", "explicit inverses of the shifted matrices (2.15 GB) read per apply")
     riesz_solve(W.riesz_sym_1023x512(), "riesz_sym",

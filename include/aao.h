@@ -56,8 +56,9 @@ extern "C" {
 
 /*
  * Problem descriptor (plain old data; copied by aao_create).
- *  nx, nt      interior spatial nodes (2..8192 mixed, 2..4096 FP64) and CN steps (a power
- *              of two, 1..8192 mixed, 1..4096 FP64)
+ *  nx, nt      interior spatial nodes (2..8192 mixed, 2..4096 FP64) and CN steps (1..8192
+ *              mixed, 1..4096 FP64; prime factors 2, 3, 5, 7 only: a power of two takes the
+ *              register FFT, any other nt the mixed-radix shared-memory FFT)
  *  op, payoff  AAO_OP_*, AAO_PUT / AAO_CALL
  *  precision   AAO_FP64 or AAO_MIXED
  *  T, r, K, sigma   maturity, rate, strike, volatility
@@ -87,7 +88,7 @@ typedef struct aao_handle aao_handle;
 /* Validate *p, build the operator coefficients, the eigenvalues lambda_{1,k}, lambda_{2,k}
    (Sec. 3.1, Eq. eigCx), Lambda_alpha, the FFT twiddles and the preconditioner workspace
    on the device. Ownership: *h owns all of it until aao_destroy. Errors: AAO_EINVAL for
-   bad sizes or parameters, AAO_EUNSUPPORTED for non-power-of-two nt or a size the operator's
+   bad sizes or parameters, AAO_EUNSUPPORTED for nt with a prime factor above 7 or a size the operator's
    step (b) does not support, AAO_ENOMEM / AAO_ECUDA from the device, AAO_BREAKDOWN if the
    eigendecomposition of a symmetric Riesz operator does not converge. On error *h is set to
    NULL. */

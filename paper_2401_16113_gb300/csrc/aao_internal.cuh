@@ -181,6 +181,20 @@ __device__ __forceinline__ float narrow(double d) {
 }
 
 // ------------------------------------------------------------------ handle
+// Stages of the mixed-radix FFT along t (nt not a power of two): nt = rad[0] rad[1] ...
+// rad[nst-1], each radix 2, 3, 4, 5, 7 or 8; nst = 0 when nt is a power of two.
+struct MrPlan {
+  int nst;
+  int rad[15];
+};
+// the stages for n (eights first), false when n has a prime factor above 7
+inline bool mr_plan(int n, MrPlan& pl) {
+  pl.nst = 0;
+  for (int f : {8, 4, 2, 3, 5, 7})
+    while (n % f == 0 && pl.nst < 15) { pl.rad[pl.nst++] = f; n /= f; }
+  return n == 1;
+}
+
 struct Handle {
   aao_problem p;
   cudaStream_t stream = 0;
@@ -207,6 +221,7 @@ struct Handle {
   float *lamf = nullptr, *ilamf = nullptr;
   void* spec = nullptr;   // half spectrum, K * pitch complex (float2 or double2)
   int fft_p = 0;          // FFT tile: 2*fft_p spatial columns per CTA (0 = heuristic)
+  MrPlan mr{};            // mixed-radix stages when nt is not a power of two (mr.nst > 0)
   // step (b) partition: tri_T (a power of two) threads per bin, tri_ch rows each; coefficients a, diag, c chunk-
   // transposed ([j][l]) in one buffer of 3 * tri_ch * tri_T reals (precision of the preconditioner)
   void* tri = nullptr;

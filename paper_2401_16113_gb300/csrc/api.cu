@@ -79,7 +79,11 @@ int validate(const aao_problem* p) {
   }
   if (p->payoff != AAO_PUT && p->payoff != AAO_CALL) { set_error("aao_create: unknown payoff"); return AAO_EINVAL; }
   if (p->precision != AAO_FP64 && p->precision != AAO_MIXED) { set_error("aao_create: unknown precision"); return AAO_EINVAL; }
-  if (!is_pow2(p->nt)) { set_error("aao_create: nt must be a power of two"); return AAO_EUNSUPPORTED; }
+  MrPlan pl;
+  if (!is_pow2(p->nt) && !mr_plan(p->nt, pl)) {
+    set_error("aao_create: nt must have no prime factor above 7");
+    return AAO_EUNSUPPORTED;
+  }
   const int nt_max = p->precision == AAO_MIXED ? 8192 : 4096;
   if (p->nt > nt_max) { set_error("aao_create: nt above the shared-memory FFT limit"); return AAO_EUNSUPPORTED; }
   const int nx_max = p->precision == AAO_MIXED ? 8192 : 4096;
@@ -117,6 +121,7 @@ int aao_create(const aao_problem* p, aao_handle** out) {
   int l = 0;
   while ((1 << l) < p->nt) ++l;
   h.log2n = l;
+  if (!is_pow2(p->nt)) mr_plan(p->nt, h.mr);
   h.pitch = ((p->nx + 63) / 64) * 64;
   h.n = (size_t)p->nx * p->nt;
   h.mixed = p->precision == AAO_MIXED;

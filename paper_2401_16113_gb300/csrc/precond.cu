@@ -18,6 +18,9 @@
 //               rows do not fit in shared memory.
 //   k_fft_inv   step (c): complex-to-real inverse FFT along t (bins nt/2+1.. are the conjugates,
 //               Remark 1) fused with Lambda_alpha^{-1} and the 1/nt normalisation.
+//   k_fft_fwd_mr / k_fft_inv_mr
+//               steps (a) and (c) for nt that is not a power of two (prime factors 2, 3, 5, 7):
+//               shared-memory Stockham stages of radix 8, 4, 2, 3, 5, 7.
 //
 // The unitary DFT of Sec. 3.1 carries 1/sqrt(nt) in each direction; here the forward FFT is
 // unnormalised and the single 1/nt is folded into the unscaling table.
@@ -75,6 +78,190 @@ int default_tile(int nx, int N, size_t rsize) {
   return P;
 }
 
+// ------------------------------------------------------------ mixed-radix FFT along t
+// For nt not a power of two (prime factors 2, 3, 5, 7): the same steps (a) and (c) as
+// k_fft_fwd / k_fft_inv (two real columns per complex column, Lambda_alpha fused, bins
+// 0..nt/2 written frequency-major), the transform a shared-memory Stockham recursion over
+// the stages of MrPlan (radix 8, 4, 2, 3, 5, 7), out of place between two buffers of P
+// columns x N.
+// A stage of radix Q with Ns = the product of the earlier radices: butterfly j < N/Q of column
+// p reads elements j + q N/Q (q < Q), twiddles element q by w^(q (j mod Ns)), w = exp(-2 pi i /
+// (Ns Q)), takes their Q-point DFT and writes output m to (j / Ns) Ns Q + (j mod Ns) + m Ns.
+// Twiddle indices into tw[m] = exp(-2 pi i m / N): q (j mod Ns) N / (Ns Q) < N.
+// P = 2^lp columns per tile; j / Ns by a multiply-high with ceil(2^32 / Ns), exact for
+// j < 2^14 and Ns <= 2^13 (j < N/2 <= 4096 here).
+template <typename R> __host__ __device__ constexpr int mr_threads() { return sizeof(R) == 4 ? 512 : 256; }
+
+template <typename C, int Q>
+__device__ __forceinline__ void mr_stage(const C* __restrict__ in, C* __restrict__ out, int N, int lp, int Ns,
+                                         const C* __restrict__ tw) {
+  const int P = 1 << lp;
+  const int L = N / Q, ts = N / (Ns * Q);
+  const unsigned mag = Ns > 1 ? (unsigned)((0x100000000ull + (unsigned)Ns - 1) / (unsigned)Ns) : 0u;
+  C w[Q];  // Q-th roots of unity exp(-2 pi i s / Q)
+#pragma unroll
+  for (int s = 0; s < Q; ++s) w[s] = tw[s * L];
+  for (int e = threadIdx.x; e < L * P; e += blockDim.x) {
+    const int j = e >> lp, p = e & (P - 1);
+    const int jq = mag ? (int)__umulhi((unsigned)j, mag) : j;  // j / Ns
+    const int k = j - jq * Ns;
+    C a[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) a[q] = in[(j + q * L) * P + p];
+    if (k > 0) {
+#pragma unroll
+      for (int q = 1; q < Q; ++q) a[q] = cmul(a[q], tw[q * k * ts]);
+    }
+    C o[Q];
+    if constexpr (Q == 8) {
+      dft8(a);
+#pragma unroll
+      for (int m = 0; m < 8; ++m) o[m] = a[m];
+    } else if constexpr (Q == 4) {
+      dft4(a[0], a[1], a[2], a[3]);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) o[m] = a[m];
+    } else if constexpr (Q == 2) {
+      o[0] = cadd(a[0], a[1]);
+      o[1] = csub(a[0], a[1]);
+    } else {
+      // the Q-point DFT by its definition: o_m = sum_q a_q w^(q m mod Q)
+#pragma unroll
+      for (int m = 0; m < Q; ++m) {
+        C acc = a[0];
+#pragma unroll
+        for (int q = 1; q < Q; ++q) acc = cadd(acc, cmul(a[q], w[(q * m) % Q]));
+        o[m] = acc;
+      }
+    }
+    const int base = jq * Ns * Q + k;
+#pragma unroll
+    for (int m = 0; m < Q; ++m) out[(base + m * Ns) * P + p] = o[m];
+  }
+}
+
+// forward DFT of the P columns in b0 (tw: the twiddle table in shared memory); returns the
+// buffer that holds the result
+template <typename C>
+__device__ C* mr_fft(C* b0, C* b1, int N, int lp, const MrPlan& pl, const C* __restrict__ tw) {
+  C* in = b0;
+  C* out = b1;
+  int Ns = 1;
+  for (int s = 0; s < pl.nst; ++s) {
+    const int Q = pl.rad[s];
+    switch (Q) {
+      case 2: mr_stage<C, 2>(in, out, N, lp, Ns, tw); break;
+      case 3: mr_stage<C, 3>(in, out, N, lp, Ns, tw); break;
+      case 4: mr_stage<C, 4>(in, out, N, lp, Ns, tw); break;
+      case 5: mr_stage<C, 5>(in, out, N, lp, Ns, tw); break;
+      case 7: mr_stage<C, 7>(in, out, N, lp, Ns, tw); break;
+      default: mr_stage<C, 8>(in, out, N, lp, Ns, tw); break;
+    }
+    __syncthreads();
+    Ns *= Q;
+    C* t = in;
+    in = out;
+    out = t;
+  }
+  return in;
+}
+
+template <typename R, typename IN>
+__global__ void __launch_bounds__(mr_threads<R>(), 2) k_fft_fwd_mr(const IN* __restrict__ v, C_t<R>* __restrict__ spec,
+                                                              int nx, int N, MrPlan pl, int lp, int pitch,
+                                                              const R* __restrict__ lam,
+                                                        const C_t<R>* __restrict__ tw,
+                                                        const double* __restrict__ in_scale) {
+  using C = C_t<R>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int P = 1 << lp, W = 2 * P;
+  C* b0 = reinterpret_cast<C*>(smraw);
+  C* b1 = b0 + (size_t)P * N;
+  C* stw = b1 + (size_t)P * N;  // twiddle table copy (N complex)
+  R* flat = reinterpret_cast<R*>(smraw);
+  for (int m = threadIdx.x; m < N; m += blockDim.x) stw[m] = __ldg(&tw[m]);
+  pdl_sync();
+  const R sc = in_scale ? to_r<R>(*in_scale) : (R)1;
+  const int x0 = blockIdx.x * W;
+  // real column c of the tile is the real (c even) or imaginary (c odd) part of complex column c/2;
+  // unrolled so that a thread's global loads are in flight together
+  constexpr int NT = mr_threads<R>();
+#pragma unroll 8
+  for (int e = threadIdx.x; e < N * W; e += NT) {
+    const int t = e >> (lp + 1), c = e & (W - 1), x = x0 + c;
+    R val = (R)0;
+    if (x < nx) val = in_r<R>(__ldg(v + (size_t)t * nx + x)) * (__ldg(&lam[t]) * sc);
+    flat[e] = val;
+  }
+  __syncthreads();
+  const C* Z = mr_fft(b0, b1, N, lp, pl, stw);
+  // bins 0..N/2 of the two real columns: X_a = (Z_k + conj Z_{N-k}) / 2, X_b = (Z_k - conj Z_{N-k}) / 2i
+  const int K = N / 2 + 1;
+  for (int e = threadIdx.x; e < K * P; e += blockDim.x) {
+    const int k = e >> lp, p = e & (P - 1);
+    const C zk = Z[k * P + p];
+    const C zn = Z[(k == 0 ? 0 : N - k) * P + p];
+    const R h = (R)0.5;
+    const int x = x0 + 2 * p;
+    C* out = spec + (size_t)k * pitch + x;
+    if (x < nx) out[0] = cmk<C>(h * (zk.x + zn.x), h * (zk.y - zn.y));
+    if (x + 1 < nx) out[1] = cmk<C>(h * (zk.y + zn.y), h * (zn.x - zk.x));
+  }
+}
+
+template <typename R, typename OUT>
+__global__ void __launch_bounds__(mr_threads<R>(), 2) k_fft_inv_mr(const C_t<R>* __restrict__ spec, OUT* __restrict__ z,
+                                                              int nx, int N, MrPlan pl, int lp, int pitch,
+                                                              const R* __restrict__ ilam,
+                                                        const C_t<R>* __restrict__ tw) {
+  using C = C_t<R>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int P = 1 << lp, W = 2 * P;
+  C* b0 = reinterpret_cast<C*>(smraw);
+  C* b1 = b0 + (size_t)P * N;
+  C* stw = b1 + (size_t)P * N;  // twiddle table copy (N complex)
+  for (int m = threadIdx.x; m < N; m += blockDim.x) stw[m] = __ldg(&tw[m]);
+  pdl_sync();
+  const int x0 = blockIdx.x * W;
+  const int K = N / 2 + 1;
+  // Z_k = A_k + i B_k for all k from the half spectra (A_{N-k} = conj A_k), stored conjugated:
+  // the inverse DFT is the conjugate of the forward DFT of the conjugate
+  constexpr int NT = mr_threads<R>();
+#pragma unroll 4
+  for (int e = threadIdx.x; e < K * P; e += NT) {
+    const int k = e >> lp, p = e & (P - 1);
+    const int x = x0 + 2 * p;
+    const C* in = spec + (size_t)k * pitch + x;
+    C A = cmk<C>(0, 0), B = cmk<C>(0, 0);
+    if (x < nx) A = in[0];
+    if (x + 1 < nx) B = in[1];
+    const bool self = (k == 0) || (2 * k == N);  // DC and (N even) Nyquist bins of a real signal
+    if (self) { A.y = 0; B.y = 0; }
+    b0[k * P + p] = cmk<C>(A.x - B.y, -(A.y + B.x));
+    if (!self) b0[(N - k) * P + p] = cmk<C>(A.x + B.y, A.y - B.x);
+  }
+  __syncthreads();
+  const C* Y = mr_fft(b0, b1, N, lp, pl, stw);
+#pragma unroll 4
+  for (int e = threadIdx.x; e < N * W; e += NT) {
+    const int t = e >> (lp + 1), c = e & (W - 1), x = x0 + c;
+    if (x < nx) {
+      const C y = Y[t * P + (c >> 1)];
+      const R val = ((c & 1) ? -y.y : y.x) * __ldg(&ilam[t]);
+      z[(size_t)t * nx + x] = (OUT)val;
+    }
+  }
+}
+
+// tile of the mixed-radix kernels: the largest power of two P <= 16 with both buffers and the
+// twiddle table within 96 KB (two CTAs per SM)
+size_t mr_smem(int P, int N, size_t csize) { return (2 * (size_t)P + 1) * N * csize; }
+int mr_max_tile(int N, size_t csize) {
+  int P = 16;
+  while (P > 1 && mr_smem(P, N, csize) > 96 * 1024) P >>= 1;
+  return P;
+}
+
 // partition-method layout of step (b): lgT, the odd chunk stride cs, coefficient staging and the
 // bins per CTA G; false when one bin's rows do not fit in shared memory
 struct TriPart {
@@ -117,9 +304,12 @@ template <typename R>
 int run_precond(Handle& h, const double* v, void* z, bool z_is_float, const double* in_scale, const float* vf) {
   using C = C_t<R>;
   const int N = h.nt, nx = h.nx;
-  const int P = h.fft_p > 0 ? h.fft_p : default_tile(nx, N, sizeof(R));
-  int threads = fft_threads(P, N, sizeof(R));
-  const size_t smem = fft_tile_bytes(P, N, sizeof(C));
+  const bool mr = h.mr.nst > 0;  // nt not a power of two: the mixed-radix kernels
+  const int P = h.fft_p > 0 ? h.fft_p : (mr ? mr_max_tile(N, sizeof(C)) : default_tile(nx, N, sizeof(R)));
+  int threads = mr ? mr_threads<R>() : fft_threads(P, N, sizeof(R));
+  int lp = 0;  // the mixed-radix tiles are powers of two
+  while ((1 << lp) < P) ++lp;
+  const size_t smem = mr ? mr_smem(P, N, sizeof(C)) : fft_tile_bytes(P, N, sizeof(C));
   const int grid = (nx + 2 * P - 1) / (2 * P);
   C* spec = reinterpret_cast<C*>(h.spec);
   const R* lam = (sizeof(R) == 4) ? (const R*)h.lamf : (const R*)h.lam;
@@ -128,7 +318,18 @@ int run_precond(Handle& h, const double* v, void* z, bool z_is_float, const doub
 
   const double nsp = (double)h.K * nx * sizeof(C);   // half spectrum, bins 0..nt/2
   const double nv = (double)nx * N;
-  if (vf && sizeof(R) == 4) {
+  if (mr) {
+    ProfScope ps(AAO_K_FFT_FWD, h.stream, nv * (vf ? sizeof(float) : sizeof(double)) + nsp);
+    if (vf && sizeof(R) == 4) {
+      AAO_TRY(ensure_smem((const void*)k_fft_fwd_mr<R, float>, smem));
+      AAO_TRY_CUDA(launch_pdl(k_fft_fwd_mr<R, float>, grid, threads, smem, h.stream, vf, spec, nx, N, h.mr, lp,
+                              h.pitch, lam, tw, in_scale));
+    } else {
+      AAO_TRY(ensure_smem((const void*)k_fft_fwd_mr<R, double>, smem));
+      AAO_TRY_CUDA(launch_pdl(k_fft_fwd_mr<R, double>, grid, threads, smem, h.stream, v, spec, nx, N, h.mr, lp,
+                              h.pitch, lam, tw, in_scale));
+    }
+  } else if (vf && sizeof(R) == 4) {
     // the FP32 copy of v written by the kernel that produced v
     AAO_TRY(ensure_smem((const void*)k_fft_fwd<R, float>, smem));
     ProfScope ps(AAO_K_FFT_FWD, h.stream, nv * sizeof(float) + nsp);
@@ -202,7 +403,18 @@ int run_precond(Handle& h, const double* v, void* z, bool z_is_float, const doub
   }  // tridiagonal operators
   AAO_CHECK_LAUNCH();
 
-  if (z_is_float) {
+  if (mr) {
+    ProfScope ps(AAO_K_FFT_INV, h.stream, nsp + nv * (z_is_float ? sizeof(float) : sizeof(double)));
+    if (z_is_float) {
+      AAO_TRY(ensure_smem((const void*)k_fft_inv_mr<R, float>, smem));
+      AAO_TRY_CUDA(launch_pdl(k_fft_inv_mr<R, float>, grid, threads, smem, h.stream, spec_b, (float*)z, nx, N, h.mr,
+                              lp, h.pitch, ilam, tw));
+    } else {
+      AAO_TRY(ensure_smem((const void*)k_fft_inv_mr<R, double>, smem));
+      AAO_TRY_CUDA(launch_pdl(k_fft_inv_mr<R, double>, grid, threads, smem, h.stream, spec_b, (double*)z, nx, N, h.mr,
+                              lp, h.pitch, ilam, tw));
+    }
+  } else if (z_is_float) {
     AAO_TRY(ensure_smem((const void*)k_fft_inv<R, float>, smem));
     ProfScope ps(AAO_K_FFT_INV, h.stream, nsp + nv * sizeof(float));
     AAO_TRY_CUDA(launch_pdl(k_fft_inv<R, float>, grid, threads, smem, h.stream, spec_b, (float*)z, nx, N, h.log2n, P,
@@ -236,7 +448,7 @@ int build_tri_factors(Handle& h) {
 
 int tune_precond(Handle& h) {
   const size_t rs = h.mixed ? 4 : 8;
-  const int pmax = max_tile(h.nt, rs);
+  const int pmax = h.mr.nst > 0 ? mr_max_tile(h.nt, 2 * rs) : max_tile(h.nt, rs);
   if (pmax == 1) {
     h.fft_p = 1;
     return AAO_OK;
@@ -249,7 +461,7 @@ int tune_precond(Handle& h) {
   AAO_TRY_CUDA(cudaEventCreate(&e0));
   AAO_TRY_CUDA(cudaEventCreate(&e1));
   float best = 1e30f;
-  int bestp = default_tile(h.nx, h.nt, rs);
+  int bestp = h.mr.nst > 0 ? pmax : default_tile(h.nx, h.nt, rs);
   int rc = AAO_OK;
   // time the form the solver runs: mixed solves read an FP32 copy of the input (the zero bytes of
   // v serve as one)
@@ -259,7 +471,7 @@ int tune_precond(Handle& h) {
   // SM is left without a tile
   std::vector<int> cand;
   for (int P = 1; P <= pmax; P <<= 1) cand.push_back(P);
-  if (h.nt >= (1 << kRegFftMinLog2) && h.sms > 0) {
+  if (h.mr.nst == 0 && h.nt >= (1 << kRegFftMinLog2) && h.sms > 0) {
     const int pairs = (h.nx + 1) / 2;
     for (int k = 1; k <= 2; ++k) {
       const int P = (pairs + k * h.sms - 1) / (k * h.sms);

@@ -51,7 +51,8 @@ def _create(lib, p):
 @pytest.mark.parametrize("bad,code", [
     (dict(nx=1), aao.AAO_EINVAL),
     (dict(nt=0), aao.AAO_EINVAL),
-    (dict(nt=96), aao.AAO_EUNSUPPORTED),
+    (dict(nt=88), aao.AAO_EUNSUPPORTED),
+    (dict(nt=13), aao.AAO_EUNSUPPORTED),
     (dict(alpha=0.0), aao.AAO_EINVAL),
     (dict(alpha=1.5), aao.AAO_EINVAL),
     (dict(sigma=-0.1), aao.AAO_EINVAL),

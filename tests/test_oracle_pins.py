@@ -106,7 +106,7 @@ def test_P_block_form(p):
 # ---------------------------------------------------------------- the three-step apply
 
 @pytest.mark.parametrize("p", ALL, ids=IDS)
-@pytest.mark.parametrize("nt,nx", [(1, 7), (2, 5), (3, 6), (8, 7), (16, 15), (12, 9)])
+@pytest.mark.parametrize("nt,nx", [(1, 7), (2, 5), (3, 6), (8, 7), (16, 15), (12, 9), (15, 7), (35, 5)])
 def test_precond_fft_equals_dense_inverse(p, nt, nx):
     """Eq. (3.2) steps (a)-(c) reproduce the brute-force dense P_alpha^{-1} (eq. 3.1)."""
     q = W.with_(p, nt=nt, nx=nx)
