@@ -254,11 +254,11 @@ __global__ void __launch_bounds__(mr_threads<R>(), 2) k_fft_inv_mr(const C_t<R>*
 }
 
 // tile of the mixed-radix kernels: the largest power of two P <= 16 with both buffers and the
-// twiddle table within 96 KB (two CTAs per SM)
+// twiddle table within 112 KB (two CTAs per SM, each with its 1 KB reserve, in the SM's 228 KB)
 size_t mr_smem(int P, int N, size_t csize) { return (2 * (size_t)P + 1) * N * csize; }
 int mr_max_tile(int N, size_t csize) {
   int P = 16;
-  while (P > 1 && mr_smem(P, N, csize) > 96 * 1024) P >>= 1;
+  while (P > 1 && mr_smem(P, N, csize) > 112 * 1024) P >>= 1;
   return P;
 }
 
