@@ -153,9 +153,11 @@ extern "C" int precond_apply_static(const aao_problem* p, const double* v, doubl
     return AAO_EINVAL;
   }
   const bool mixed = p->precision == AAO_MIXED;
-  if (p->nx < 2 || !is_pow2(p->nt) || p->nt > (mixed ? 8192 : 4096) || p->nx > (mixed ? 8192 : 4096)) {
-    set_error("precond_apply_static: need nx >= 2 (<= 8192 mixed, <= 4096 FP64) and nt a power of two "
-              "(<= 8192 mixed, <= 4096 FP64)");
+  MrPlan plan;
+  const bool nt_ok = p->nt >= 1 && (is_pow2(p->nt) || mr_plan(p->nt, plan));
+  if (p->nx < 2 || !nt_ok || p->nt > (mixed ? 8192 : 4096) || p->nx > (mixed ? 8192 : 4096)) {
+    set_error("precond_apply_static: need nx >= 2 (<= 8192 mixed, <= 4096 FP64) and nt with no prime factor "
+              "above 7 (<= 8192 mixed, <= 4096 FP64)");
     return AAO_EINVAL;
   }
   if (!(p->T > 0) || !(p->K > 0) || !(p->sigma > 0) || !(p->s_max > 0) || !(p->r >= 0) || !(p->alpha > 0) ||
@@ -185,6 +187,7 @@ extern "C" int precond_apply_static(const aao_problem* p, const double* v, doubl
   int l = 0;
   while ((1 << l) < p->nt) ++l;
   h.log2n = l;
+  if (!is_pow2(p->nt)) h.mr = plan;  // the mixed-radix FFT kernels
   h.pitch = pitch;
   h.n = (size_t)p->nx * p->nt;
   h.mixed = mixed;

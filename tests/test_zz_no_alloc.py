@@ -32,10 +32,14 @@ CASES = [
     W.localvol_2047x2048("mixed"),
     W.with_(W.bs_put_255x256(), precision="fp64"),
     W.with_(W.bs_put_255x256(), nx=37, nt=16, precision="mixed", payoff="call"),
+    W.with_(W.localvol_2047x2048("mixed"), nt=1536),
+    W.with_(W.bs_put_255x256(), nx=100, nt=15, precision="fp64"),
+    W.with_(W.bs_put_255x256(), nx=63, nt=24, precision="mixed", payoff="call"),
 ]
 
 
-@pytest.mark.parametrize("p", CASES, ids=["localvol-2047x2048-mixed", "bs-255x256-fp64", "bs-37x16-mixed"])
+@pytest.mark.parametrize("p", CASES, ids=["localvol-2047x2048-mixed", "bs-255x256-fp64", "bs-37x16-mixed",
+                                          "localvol-2047x1536-mixed", "bs-100x15-fp64", "bs-63x24-mixed"])
 def test_static_matches_allocating_apply_twice(aao, p):
     n = W.unknowns(p)
     h = aao.aao_create(p)
