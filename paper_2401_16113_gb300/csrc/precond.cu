@@ -166,12 +166,11 @@ __device__ C* mr_fft(C* b0, C* b1, int N, int lp, const MrPlan& pl, const C* __r
   return in;
 }
 
+// Both kernels are launched with mr_threads<R>() threads (their strided loops assume it).
 template <typename R, typename IN>
-__global__ void __launch_bounds__(mr_threads<R>(), 2) k_fft_fwd_mr(const IN* __restrict__ v, C_t<R>* __restrict__ spec,
-                                                              int nx, int N, MrPlan pl, int lp, int pitch,
-                                                              const R* __restrict__ lam,
-                                                        const C_t<R>* __restrict__ tw,
-                                                        const double* __restrict__ in_scale) {
+__global__ void __launch_bounds__(mr_threads<R>(), 2)
+    k_fft_fwd_mr(const IN* __restrict__ v, C_t<R>* __restrict__ spec, int nx, int N, MrPlan pl, int lp, int pitch,
+                 const R* __restrict__ lam, const C_t<R>* __restrict__ tw, const double* __restrict__ in_scale) {
   using C = C_t<R>;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int P = 1 << lp, W = 2 * P;
@@ -210,10 +209,9 @@ __global__ void __launch_bounds__(mr_threads<R>(), 2) k_fft_fwd_mr(const IN* __r
 }
 
 template <typename R, typename OUT>
-__global__ void __launch_bounds__(mr_threads<R>(), 2) k_fft_inv_mr(const C_t<R>* __restrict__ spec, OUT* __restrict__ z,
-                                                              int nx, int N, MrPlan pl, int lp, int pitch,
-                                                              const R* __restrict__ ilam,
-                                                        const C_t<R>* __restrict__ tw) {
+__global__ void __launch_bounds__(mr_threads<R>(), 2)
+    k_fft_inv_mr(const C_t<R>* __restrict__ spec, OUT* __restrict__ z, int nx, int N, MrPlan pl, int lp, int pitch,
+                 const R* __restrict__ ilam, const C_t<R>* __restrict__ tw) {
   using C = C_t<R>;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int P = 1 << lp, W = 2 * P;
