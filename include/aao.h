@@ -88,8 +88,8 @@ typedef struct aao_handle aao_handle;
 /* Validate *p, build the operator coefficients, the eigenvalues lambda_{1,k}, lambda_{2,k}
    (Sec. 3.1, Eq. eigCx), Lambda_alpha, the FFT twiddles and the preconditioner workspace
    on the device. Ownership: *h owns all of it until aao_destroy. Errors: AAO_EINVAL for
-   bad sizes or parameters, AAO_EUNSUPPORTED for nt with a prime factor above 7 or a size the operator's
-   step (b) does not support, AAO_ENOMEM / AAO_ECUDA from the device, AAO_BREAKDOWN if the
+   bad sizes or parameters, AAO_EUNSUPPORTED for nt with a prime factor above 7 or a size
+   the operator's step (b) does not support, AAO_ENOMEM / AAO_ECUDA from the device, AAO_BREAKDOWN if the
    eigendecomposition of a symmetric Riesz operator does not converge. On error *h is set to
    NULL. */
 int aao_create(const aao_problem* p, aao_handle** h);
@@ -106,10 +106,11 @@ int aao_rhs(aao_handle* h, double* b_dev);
 int aao_matvec(aao_handle* h, const double* x_dev, double* y_dev);
 
 /* z_dev <- P_alpha^{-1} v_dev by the three steps of Eq. 3.2 with the conjugate-pair saving
-   of Remark 1: Lambda_alpha scaling and a real-to-complex FFT along t, nt/2+1 complex-shifted
-   tridiagonal solves (lambda_{1,k} I - lambda_{2,k} A~) z_k = z1_k, then the inverse FFT and
-   Lambda_alpha^{-1}. FP32 complex inside when precision = AAO_MIXED (z is still returned in
-   FP64). v_dev, z_dev: nx*nt doubles, device; may alias. */
+   of Remark 1: Lambda_alpha scaling and a real-to-complex FFT along t (mixed radix when nt is
+   not a power of two), floor(nt/2)+1 complex-shifted spatial solves
+   (lambda_{1,k} I - lambda_{2,k} A~) z_k = z1_k (tridiagonal; dense for AAO_OP_RIESZ), then
+   the inverse FFT and Lambda_alpha^{-1}. FP32 complex inside when precision = AAO_MIXED (z is
+   still returned in FP64). v_dev, z_dev: nx*nt doubles, device; may alias. */
 int precond_apply(aao_handle* h, const double* v_dev, double* z_dev);
 
 /* Solve M x = b (Eq. 2.2) by right-preconditioned flexible GMRES(m) with P_alpha
