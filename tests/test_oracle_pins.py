@@ -234,10 +234,11 @@ def test_cn_non_growth_symmetric_nsd():
 
 @pytest.mark.parametrize("p", [BS, LV, RZ], ids=["bs", "localvol-mean", "riesz"])
 @pytest.mark.parametrize("alpha", [0.5, 1e-1, 1e-2])
-def test_lemma31_theorem31(p, alpha):
+@pytest.mark.parametrize("nt", [8, 9, 10])
+def test_lemma31_theorem31(p, alpha, nt):
     """(Nt-1) Nx eigenvalues of P^{-1} M equal 1; the other Nx lie in the annulus
-    1/(1+alpha) <= |z| <= 1/(1-alpha) with Re z > 0 (constant operator)."""
-    q = W.with_(p, nx=9, nt=8, alpha=alpha)
+    1/(1+alpha) <= |z| <= 1/(1-alpha) with Re z > 0 (constant operator); for even and odd Nt."""
+    q = W.with_(p, nx=9, nt=nt, alpha=alpha)
     if q["op"] == "localvol":
         q = W.with_(q, op="matrix", A=O._dense(O.mean_operator(q)))
     A = O._dense(O.mean_operator(q))
