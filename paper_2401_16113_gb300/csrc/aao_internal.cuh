@@ -7,6 +7,8 @@
 #include <atomic>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/aao.h"
 
 namespace aao {
@@ -179,6 +181,15 @@ __device__ __forceinline__ float narrow(double d) {
   fb = ehi >= 0x7ff00000u ? ((ehi > 0x7ff00000u || lo != 0u) ? 0x7fc00000u : 0x7f800000u) : fb;
   return __uint_as_float(sign | fb);
 }
+
+// NVTX range for the duration of a scope (entry points, FGMRES restart cycles): header-only
+// NVTX v3, a no-op unless a profiler is attached
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ------------------------------------------------------------------ handle
 // Stages of the mixed-radix FFT along t (nt not a power of two): nt = rad[0] rad[1] ...

@@ -108,6 +108,7 @@ using namespace aao;
 extern "C" {
 
 int aao_create(const aao_problem* p, aao_handle** out) {
+  NvtxRange nv("aao_create");
   if (!out) { set_error("aao_create: null handle pointer"); return AAO_EINVAL; }
   *out = nullptr;
   AAO_TRY(validate(p));
@@ -145,22 +146,26 @@ int aao_destroy(aao_handle* hd) {
 }
 
 int aao_rhs(aao_handle* hd, double* b) {
+  NvtxRange nv("aao_rhs");
   if (!hd || !b) { set_error("aao_rhs: null argument"); return AAO_EINVAL; }
   return launch_rhs(hd->h, b);
 }
 
 int aao_matvec(aao_handle* hd, const double* x, double* y) {
+  NvtxRange nv("aao_matvec");
   if (!hd || !x || !y) { set_error("aao_matvec: null argument"); return AAO_EINVAL; }
   if (x == y) { set_error("aao_matvec: x and y must not alias"); return AAO_EINVAL; }
   return launch_matvec(hd->h, x, false, y, nullptr);
 }
 
 int precond_apply(aao_handle* hd, const double* v, double* z) {
+  NvtxRange nv("precond_apply");
   if (!hd || !v || !z) { set_error("precond_apply: null argument"); return AAO_EINVAL; }
   return launch_precond(hd->h, v, z, false);
 }
 
 int fgmres_solve(aao_handle* hd, const double* b, double* x, double tol, int m, int maxit, aao_stats* st) {
+  NvtxRange nv("fgmres_solve");
   if (!hd || !b || !x) { set_error("fgmres_solve: null argument"); return AAO_EINVAL; }
   if (m < 1 || m > 64 || maxit < 1 || !(tol > 0)) { set_error("fgmres_solve: need 1 <= m <= 64, maxit >= 1, tol > 0"); return AAO_EINVAL; }
   return run_fgmres(hd->h, b, x, tol, m, maxit, st);
@@ -168,6 +173,7 @@ int fgmres_solve(aao_handle* hd, const double* b, double* x, double tol, int m, 
 
 int fgmres_solve_host(aao_handle* hd, const double* b_host, double* x_host, double tol, int m, int maxit,
                       aao_stats* st) {
+  NvtxRange nv("fgmres_solve_host");
   if (!hd || !b_host || !x_host) { set_error("fgmres_solve_host: null argument"); return AAO_EINVAL; }
   if (m < 1 || m > 64 || maxit < 1 || !(tol > 0)) { set_error("fgmres_solve_host: need 1 <= m <= 64, maxit >= 1, tol > 0"); return AAO_EINVAL; }
   Handle& h = hd->h;

@@ -780,6 +780,7 @@ extern "C" int aao_batch_rhs(aao_batch* bt, double* const* b) {
 
 extern "C" int batch_submit(aao_batch* bt, double* const* b, double* const* x, double tol, int maxit,
                             aao_stats* st) {
+  NvtxRange nv("batch_submit");
   if (!bt || !b || !x) { set_error("batch_submit: null argument"); return AAO_EINVAL; }
   if (!(tol > 0) || maxit < 1) { set_error("batch_submit: need tol > 0 and maxit >= 1"); return AAO_EINVAL; }
   Batch& B = bt->B;

@@ -723,6 +723,7 @@ int run_fgmres(Handle& h, const double* b, double* x, double tol, int m, int max
   int its = 0, restarts = 0, status = AAO_OK;
   double rel = 0.0, est = 0.0, bnorm = 0.0;
   for (bool first = true;; first = false) {
+    NvtxRange nv_cycle("fgmres_cycle");
     // restart residual r = b - M x, written as the raw first basis vector V_0 (the first one also
     // forms ||b||^2)
     AAO_TRY(launch_matvec(h, x, false, h.V, b, nullptr, 0, m, first, vf));

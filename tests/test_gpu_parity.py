@@ -250,6 +250,32 @@ def test_fgmres_restart_small_m(aao):
     assert relmax(host(x), ref) <= 1e-9
 
 
+@pytest.mark.parametrize("precision,m,k", [("fp64", 1, 3), ("fp64", 2, 1), ("mixed", 2, 1)])
+def test_fgmres_checkpoint_resume(aao, precision, m, k):
+    """A restart boundary is a checkpoint: FGMRES(m) restarts from x alone, so a solve stopped
+    after k whole cycles (maxit = k m) and resumed from its x takes the same total number of
+    inner iterations and reaches the same x as the uninterrupted solve."""
+    p = W.with_(BS, nx=63, nt=64, precision=precision)
+    h = aao.aao_create(p)
+    n = W.unknowns(p)
+    b = torch.empty(n, dtype=torch.float64, device="cuda")
+    aao.aao_rhs(h, b)
+    tol = 1e-12 if precision == "fp64" else 1e-10
+    x_full = torch.zeros(n, dtype=torch.float64, device="cuda")
+    st_full = aao.fgmres_solve(h, b, x_full, tol, m, 400)
+    assert st_full["status"] == 0 and st_full["iterations"] > k * m
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    st1 = aao.fgmres_solve(h, b, x, tol, m, k * m)
+    assert st1["status"] == aao.AAO_NOT_CONVERGED and st1["iterations"] == k * m
+    saved = host(x).copy()                      # the checkpoint: x and the iteration count
+    x2 = dev(saved)
+    st2 = aao.fgmres_solve(h, b, x2, tol, m, 400)
+    assert st2["status"] == 0
+    assert st1["iterations"] + st2["iterations"] == st_full["iterations"]
+    assert relmax(host(x2), host(x_full)) <= 1e-13
+    h.close()
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_fgmres_exhausted_krylov_space(aao, precision):
     """A 3 x 2 system (6 unknowns) with FGMRES(10) and alpha = 1: the Krylov space fills up, the
