@@ -575,24 +575,25 @@ __global__ void k_rz_transpose(float2* __restrict__ LU, int nx) {
 }
 
 // The inverse of each shifted matrix, made once at create from its LU factors (transposed,
-// F[j nx + i] = LU[i][j]) and diagonal-block inverses: X_k = (mu_k I - A~)^{-1}, kRzInvCols
-// columns of the identity per CTA (in shared memory, nx x kRzInvCols complex) taken through
+// F[j nx + i] = LU[i][j]) and diagonal-block inverses: X_k = (mu_k I - A~)^{-1}, COLS
+// columns of the identity per CTA (in shared memory, nx x COLS complex; COLS a multiple of 4,
+// 16 where that fits in shared memory, else 8) taken through
 // L Y = E (unit lower) and U X = Y by right-looking blocked substitution over 32-row blocks:
 // solve the block with its stored diagonal-block inverse, then remove its contribution from
 // every remaining row, the factor column read by consecutive threads (coalesced).
 // X is row-major [k][i][j].
-constexpr int kRzInvCols = 16;
+template <int COLS>
 __global__ void __launch_bounds__(512) k_rz_inv(const float2* __restrict__ LUt, const float2* __restrict__ dinv,
                                                 float2* __restrict__ X, int nx, int nb) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  float2* Z = reinterpret_cast<float2*>(smraw);  // [i][c], nx x kRzInvCols
-  float2* t = Z + (size_t)nx * kRzInvCols;       // kNB x kRzInvCols
-  const int k = blockIdx.y, c0 = blockIdx.x * kRzInvCols;
-  const int nc = min(kRzInvCols, nx - c0);
+  float2* Z = reinterpret_cast<float2*>(smraw);  // [i][c], nx x COLS
+  float2* t = Z + (size_t)nx * COLS;             // kNB x COLS
+  const int k = blockIdx.y, c0 = blockIdx.x * COLS;
+  const int nc = min(COLS, nx - c0);
   const float2* F = LUt + (size_t)k * nx * nx;
   const float2 zero = make_float2(0.f, 0.f);
-  for (int e = threadIdx.x; e < nx * kRzInvCols; e += blockDim.x) {
-    const int i = e / kRzInvCols, c = e - i * kRzInvCols;
+  for (int e = threadIdx.x; e < nx * COLS; e += blockDim.x) {
+    const int i = e / COLS, c = e - i * COLS;
     Z[e] = (c < nc && i == c0 + c) ? make_float2(1.f, 0.f) : zero;
   }
   __syncthreads();
@@ -601,29 +602,30 @@ __global__ void __launch_bounds__(512) k_rz_inv(const float2* __restrict__ LUt, 
     const int bi = fwd ? s : 2 * nb - 1 - s;
     const int r0 = bi * kNB, w = min(kNB, nx - r0);
     const float2* inv = dinv + (((size_t)k * nb + bi) * 2 + (fwd ? 0 : 1)) * kNB * kNB;
-    for (int e = threadIdx.x; e < w * kRzInvCols; e += blockDim.x) t[e] = Z[(size_t)r0 * kRzInvCols + e];
+    for (int e = threadIdx.x; e < w * COLS; e += blockDim.x) t[e] = Z[(size_t)r0 * COLS + e];
     __syncthreads();
-    // the block: Z_b <- Inv t (w x w times w x kRzInvCols), one output per thread
-    for (int e = threadIdx.x; e < w * kRzInvCols; e += blockDim.x) {
-      const int i = e / kRzInvCols, c = e - i * kRzInvCols;
+    // the block: Z_b <- Inv t (w x w times w x COLS), one output per thread
+    for (int e = threadIdx.x; e < w * COLS; e += blockDim.x) {
+      const int i = e / COLS, c = e - i * COLS;
       float2 acc = zero;
       for (int q = 0; q < w; ++q) {
-        const float2 a = __ldg(inv + i * kNB + q), b = t[q * kRzInvCols + c];
+        const float2 a = __ldg(inv + i * kNB + q), b = t[q * COLS + c];
         acc = make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y)));
       }
-      Z[(size_t)(r0 + i) * kRzInvCols + c] = acc;
+      Z[(size_t)(r0 + i) * COLS + c] = acc;
     }
     __syncthreads();
     // the remaining rows: Z_i -= sum_{jj < w} F[(r0 + jj) nx + i] Z_{r0 + jj}, a task = one row and
     // four columns
+    constexpr int G4 = COLS / 4;
     const int i0 = fwd ? r0 + w : 0, i1 = fwd ? nx : r0;
-    for (int task = threadIdx.x; task < (i1 - i0) * 4; task += blockDim.x) {
-      const int i = i0 + (task >> 2), q4 = (task & 3) * 4;
+    for (int task = threadIdx.x; task < (i1 - i0) * G4; task += blockDim.x) {
+      const int i = i0 + task / G4, q4 = (task % G4) * 4;
       float2 acc[4] = {zero, zero, zero, zero};
       for (int jj = 0; jj < w; ++jj) {
         const float2 f = __ldg(F + (size_t)(r0 + jj) * nx + i);
-        const float4 za = *reinterpret_cast<const float4*>(Z + (size_t)(r0 + jj) * kRzInvCols + q4);
-        const float4 zb = *reinterpret_cast<const float4*>(Z + (size_t)(r0 + jj) * kRzInvCols + q4 + 2);
+        const float4 za = *reinterpret_cast<const float4*>(Z + (size_t)(r0 + jj) * COLS + q4);
+        const float4 zb = *reinterpret_cast<const float4*>(Z + (size_t)(r0 + jj) * COLS + q4 + 2);
         const float2 zv[4] = {make_float2(za.x, za.y), make_float2(za.z, za.w), make_float2(zb.x, zb.y),
                               make_float2(zb.z, zb.w)};
 #pragma unroll
@@ -634,14 +636,14 @@ __global__ void __launch_bounds__(512) k_rz_inv(const float2* __restrict__ LUt, 
       }
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        float2& zi = Z[(size_t)i * kRzInvCols + q4 + c];
+        float2& zi = Z[(size_t)i * COLS + q4 + c];
         zi = make_float2(zi.x - acc[c].x, zi.y - acc[c].y);
       }
     }
     __syncthreads();
   }
-  for (int e = threadIdx.x; e < nx * kRzInvCols; e += blockDim.x) {
-    const int i = e / kRzInvCols, c = e - i * kRzInvCols;
+  for (int e = threadIdx.x; e < nx * COLS; e += blockDim.x) {
+    const int i = e / COLS, c = e - i * COLS;
     if (c < nc) X[((size_t)k * nx + i) * nx + c0 + c] = Z[e];
   }
 }
@@ -932,10 +934,15 @@ int riesz_build(Handle& h) {
     // the inverses X_k (an apply is then one matrix-vector product per bin); the factors and the
     // block inverses are released afterwards
     AAO_TRY_CUDA(cudaMalloc(&h.rz_inv, sizeof(float2) * nn * K));
-    const size_t ismem = sizeof(float2) * ((size_t)nx * kRzInvCols + (size_t)kNB * kRzInvCols);
-    AAO_TRY_CUDA(cudaFuncSetAttribute(k_rz_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem));
-    k_rz_inv<<<dim3((nx + kRzInvCols - 1) / kRzInvCols, K), 512, ismem, h.stream>>>(h.rz_lu, h.rz_dinv, h.rz_inv, nx,
-                                                                                    nb);
+    // 16 identity columns per CTA where they fit in shared memory (nx <= 1784), else 8
+    auto inv_smem = [&](int cols) { return sizeof(float2) * ((size_t)nx + kNB) * cols; };
+    if (inv_smem(16) <= 227 * 1024) {
+      AAO_TRY_CUDA(cudaFuncSetAttribute(k_rz_inv<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inv_smem(16)));
+      k_rz_inv<16><<<dim3((nx + 15) / 16, K), 512, inv_smem(16), h.stream>>>(h.rz_lu, h.rz_dinv, h.rz_inv, nx, nb);
+    } else {
+      AAO_TRY_CUDA(cudaFuncSetAttribute(k_rz_inv<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inv_smem(8)));
+      k_rz_inv<8><<<dim3((nx + 7) / 8, K), 512, inv_smem(8), h.stream>>>(h.rz_lu, h.rz_dinv, h.rz_inv, nx, nb);
+    }
     AAO_CHECK_LAUNCH();
     AAO_TRY_CUDA(cudaStreamSynchronize(h.stream));
     cudaFree(h.rz_lu);

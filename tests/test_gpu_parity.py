@@ -356,6 +356,19 @@ def test_riesz_precond_matches_oracle(aao, nx, nt, alpha):
     assert rel(host(z), ref) <= precond_bound(p), rel(host(z), ref)
 
 
+@pytest.mark.parametrize("nx", [1800, 2047])
+def test_riesz_precond_wide_grids(aao, nx):
+    """The Riesz operator with drift at nx above 1784, where the create-time inverse runs with 8
+    identity columns per CTA (16 do not fit in shared memory)."""
+    p = W.with_(RZ, nx=nx, nt=4, alpha=1e-2)
+    h = aao.aao_create(p)
+    v = W.random_vector(nx * 4, seed=nx)
+    z = torch.empty(nx * 4, dtype=torch.float64, device="cuda")
+    aao.precond_apply(h, dev(v), z)
+    assert rel(host(z), O.precond_fft(p, v)) <= precond_bound(p)
+    h.close()
+
+
 def test_riesz_precond_small_matches_dense_inverse(aao):
     for nx, nt in [(7, 4), (9, 8)]:
         p = W.with_(RZ, nx=nx, nt=nt, alpha=1e-2)
