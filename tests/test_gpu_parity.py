@@ -359,13 +359,21 @@ def test_riesz_precond_matches_oracle(aao, nx, nt, alpha):
 @pytest.mark.parametrize("nx", [1800, 2047])
 def test_riesz_precond_wide_grids(aao, nx):
     """The Riesz operator with drift at nx above 1784, where the create-time inverse runs with 8
-    identity columns per CTA (16 do not fit in shared memory)."""
+    identity columns per CTA (16 do not fit in shared memory); its matvec and right-hand side at
+    the same widths."""
     p = W.with_(RZ, nx=nx, nt=4, alpha=1e-2)
     h = aao.aao_create(p)
     v = W.random_vector(nx * 4, seed=nx)
     z = torch.empty(nx * 4, dtype=torch.float64, device="cuda")
     aao.precond_apply(h, dev(v), z)
     assert rel(host(z), O.precond_fft(p, v)) <= precond_bound(p)
+    # the FP64 matvec and right-hand side at the widest circulant embedding (N2 = 4096)
+    b = torch.empty(nx * 4, dtype=torch.float64, device="cuda")
+    aao.aao_rhs(h, b)
+    assert relmax(host(b), O.assemble_b(p)) <= 1e-12
+    y = torch.empty(nx * 4, dtype=torch.float64, device="cuda")
+    aao.aao_matvec(h, dev(v), y)
+    assert relmax(host(y), O.matvec(p, v)) <= 1e-12
     h.close()
 
 
