@@ -63,6 +63,35 @@ def test_batch_agrees_with_single_instance_solves(aao):
     bt.close()
 
 
+def test_batch_size_limits_agree_with_single_instance_solves(aao):
+    """Instances at the batched solver's limits (nx = nt = 4096: 256 threads per tridiagonal bin,
+    a one-column FFT tile; nx = 4095 with nt = 64; the smallest 2 x 2) in one launch, each against
+    its single-instance solve and the true FP64 residual."""
+    base = W.bs_put_255x256()
+    ps = [W.with_(base, nx=4096, nt=4096, precision="mixed", alpha=1e-3, tol=1e-8, m=20, s_max=300.0),
+          W.with_(base, nx=4095, nt=64, precision="mixed", payoff="call", alpha=1e-3, tol=1e-8, m=20),
+          W.with_(base, nx=2, nt=2, precision="mixed", alpha=1e-3, tol=1e-8, m=20)]
+    bt = aao.aao_batch_create(ps, 20)
+    bs, xs = vectors(bt), vectors(bt)
+    aao.aao_batch_rhs(bt, bs)
+    st = aao.batch_submit(bt, bs, xs, 1e-8, 300)
+    for i, p in enumerate(ps):
+        assert st[i]["status"] == 0, (i, st[i])
+        h = aao.aao_create(p)
+        x1 = torch.zeros_like(xs[i])
+        s1 = aao.fgmres_solve(h, bs[i], x1, 1e-8, 20, 300)
+        assert s1["status"] == 0 and abs(s1["iterations"] - st[i]["iterations"]) <= 1, (s1, st[i])
+        r = torch.empty_like(xs[i])
+        aao.aao_matvec(h, xs[i], r)
+        torch.cuda.synchronize()
+        res = float(torch.linalg.norm(bs[i] - r) / torch.linalg.norm(bs[i]))
+        assert res <= 1.01e-8, (i, res)
+        a, b = xs[i].cpu().numpy(), x1.cpu().numpy()
+        assert np.abs(a - b).max() <= 1e-6 * np.abs(b).max(), i
+        h.close()
+    bt.close()
+
+
 def test_batch_failure_is_isolated_and_results_do_not_depend_on_neighbours(aao):
     ps = small_batch(12, seed=3)
     bt = aao.aao_batch_create(ps, 20)
