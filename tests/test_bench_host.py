@@ -1,4 +1,5 @@
-"""Host-side logic of bench.py: the clock-sample window and the default step counts."""
+"""Host-side logic of bench.py: the clock-sample window, the default step counts, the
+preconditioner roofline arithmetic and the traffic record's source check."""
 import importlib.util
 import os
 import sys
@@ -49,3 +50,31 @@ def test_default_steps_per_arm(monkeypatch):
         monkeypatch.setattr(sys, "argv", argv)
         b.main()
     assert seen == {"ours": 200, "reference": 3}
+
+
+def test_precond_roofline_arithmetic():
+    """The apply's three kernel classes as one unit: bytes and time summed per apply."""
+    B = load_bench()
+    # (launches, total ms, algorithmic bytes, flops) per class over 4 applies
+    prof = {"fft_fwd": (4, 0.08, 4 * 30e6, 0.0), "tridiag": (4, 0.12, 4 * 60e6, 0.0),
+            "fft_inv": (4, 0.08, 4 * 30e6, 0.0), "matvec": (5, 0.5, 1e9, 1e8)}
+    r = B.precond_roofline(prof, 6800.0)
+    assert r["applies"] == 4
+    assert abs(r["ms_per_apply"] - 0.07) < 1e-12
+    assert abs(r["algorithmic_bytes_per_apply"] - 120e6) < 1e-3
+    assert abs(r["achieved"] - 120e6 / 0.07e-3 / 1e9) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / 6800.0) < 1e-12
+    assert B.precond_roofline(dict(prof, fft_fwd=(0, 0.0, 0.0, 0.0)), 6800.0) is None
+
+
+def test_traffic_record_is_used_only_on_its_own_sources(monkeypatch):
+    """profiles/ncu_traffic.json gives DRAM bytes per launch only while its source hash matches
+    the sources; after any change to them the bench reports no traffic."""
+    import json
+    B = load_bench()
+    rec = json.load(open(os.path.join(B.ROOT, "profiles", "ncu_traffic.json")))["matvec"]
+    monkeypatch.setattr(B, "source_sha", lambda: rec["source_sha"])
+    assert B.ncu_traffic("matvec") == rec["dram_bytes_per_launch"]
+    monkeypatch.setattr(B, "source_sha", lambda: "0" * 16)
+    assert B.ncu_traffic("matvec") is None
+    assert B.ncu_traffic("no_such_kernel") is None
