@@ -45,7 +45,7 @@ def test_features_of_constant_and_local_volatility():
     assert math.isclose(s, 0.15, rel_tol=1e-14) and cv <= 1e-14 and (nx, nt) == (2047, 2048)
     # a bump without a time slope: the RMS over the S window rises above sigma, still no time
     # variation
-    bump = W.with_(flat, lv_bump=0.1)
+    bump = W.with_(flat, lv_bump=0.1, lv_tslope=0.0)
     s, *_, cv = AM.features(bump)
     assert s > 0.15 and cv <= 1e-14
     # the time slope makes sigma^2 vary in time: at the money sigma(t) = 0.15 + 0.1 (1 + 0.2 t),
