@@ -54,9 +54,16 @@ def time_grid(p):
 
 
 def local_sigma(p, S, t):
-    """sigma(S, t); constant sigma for 'bs'."""
+    """sigma(S, t) = sigma + lv_bump * g(S) * (1 + lv_tslope * t), t = time to maturity, with the
+    bump shape g(S) = exp(-ln^2(S/K)) (the local-volatility workload), or g = 1 when
+    p['lv_shape'] == 'flat' (a volatility that depends on time only, whose European price has a
+    closed form); constant sigma for 'bs'."""
     if p["op"] == "localvol":
-        return p["sigma"] + p["lv_bump"] * np.exp(-np.log(S / p["K"]) ** 2) * (1.0 + p["lv_tslope"] * t)
+        if p.get("lv_shape", "gauss") == "flat":
+            g = np.ones_like(S)
+        else:
+            g = np.exp(-np.log(S / p["K"]) ** 2)
+        return p["sigma"] + p["lv_bump"] * g * (1.0 + p["lv_tslope"] * t)
     return p["sigma"] * np.ones_like(S)
 
 

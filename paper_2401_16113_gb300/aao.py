@@ -119,6 +119,8 @@ def _check(code):
 
 
 def make_problem(p, stream=0):
+    if p.get("lv_shape", "gauss") != "gauss":
+        raise ValueError("the library builds the local-volatility bump exp(-ln^2(S/K)) only (lv_shape 'gauss')")
     s = AaoProblem()
     s.nx, s.nt = int(p["nx"]), int(p["nt"])
     s.op, s.payoff, s.precision = OPS[p["op"]], PAYOFFS[p["payoff"]], PRECISIONS[p["precision"]]

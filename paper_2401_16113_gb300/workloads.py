@@ -17,6 +17,9 @@ A problem is a dict with the keys
   s_max     S-domain [0, s_max] ('bs', 'localvol'); x-domain [-s_max, s_max] ('riesz')
   lv_bump, lv_tslope
             'localvol' only: sigma(S,t) = sigma + lv_bump*exp(-ln(S/K)^2)*(1 + lv_tslope*t)
+  lv_shape  optional, 'gauss' (the bump above, the default) or 'flat' (bump shape 1: a
+            volatility that depends on time only; the oracle's pins use it, the library
+            rejects it)
   beta      'riesz' only: fractional order in (1, 2]
   alpha     the free parameter of the alpha-circulant preconditioner (Sec. 3.1)
   precision 'fp64' or 'mixed' (FP32-complex preconditioner inside FP64 FGMRES)

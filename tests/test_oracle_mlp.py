@@ -1,4 +1,6 @@
 """Pins for the MLP oracle: finite differences, special cases, textbook Adam, bfloat16."""
+import math
+
 import numpy as np
 
 from oracle import mlp_oracle as MO
@@ -48,6 +50,27 @@ def test_adam_first_step_is_sign_step():
     g = np.array([0.3, -4.0, 1e-3])
     new, m, v = MO.adam_step(th, g, np.zeros(3), np.zeros(3), 1, lr=0.01)
     assert np.allclose(new, th - 0.01 * np.sign(g), atol=1e-7)
+
+
+def test_adam_three_steps_hand_worked():
+    """Adam (Kingma & Ba, Algorithm 1; beta1 0.9, beta2 0.999, eps 1e-8) on one parameter with
+    gradients +1, -1, +2, worked by hand from the definition:
+      t=1: m = 1/10, v = 1/1000;        m^ = 1,        v^ = 1
+      t=2: m = -1/100, v = 1999/1e6;    m^ = -1/19,    v^ = 1999/1999 = 1
+      t=3: m = 191/1000, v = 5997001/1e9; m^ = 191/271, v^ = 5997001/2997001
+    (1 - 0.9^2 = 19/100, 1 - 0.9^3 = 271/1000, 1 - 0.999^3 = 2997001/1e9). A moment update or a
+    bias correction that is right only at t = 1 fails steps 2 and 3."""
+    lr, eps = 0.1, 1e-8
+    steps = [lr * 1.0 / (1.0 + eps),
+             lr * (-1.0 / 19.0) / (1.0 + eps),
+             lr * (191.0 / 271.0) / (math.sqrt(5997001.0 / 2997001.0) + eps)]
+    th, m, v = np.array([0.5]), np.zeros(1), np.zeros(1)
+    want = 0.5
+    for t, (g, step) in enumerate(zip([1.0, -1.0, 2.0], steps), start=1):
+        th, m, v = MO.adam_step(th, np.array([g]), m, v, t, lr=lr)
+        want -= step
+        assert abs(th[0] - want) < 1e-14, (t, th[0], want)
+    assert abs(m[0] - 0.191) < 1e-15 and abs(v[0] - 5997001e-9) < 1e-17
 
 
 def test_bf16_rounding():
