@@ -110,7 +110,10 @@ int aao_matvec(aao_handle* h, const double* x_dev, double* y_dev);
    not a power of two), floor(nt/2)+1 complex-shifted spatial solves
    (lambda_{1,k} I - lambda_{2,k} A~) z_k = z1_k (tridiagonal; dense for AAO_OP_RIESZ), then
    the inverse FFT and Lambda_alpha^{-1}. FP32 complex inside when precision = AAO_MIXED (z is
-   still returned in FP64). v_dev, z_dev: nx*nt doubles, device; may alias. */
+   still returned in FP64). v_dev, z_dev: nx*nt doubles, device; may alias. Returns AAO_OK, or
+   AAO_TIMEOUT when a tensor-core product of the symmetric Riesz operator's step (b) gave up a
+   bounded wait (z is then not valid; for that operator this call synchronises the stream to
+   read the error word), or an error. */
 int precond_apply(aao_handle* h, const double* v_dev, double* z_dev);
 
 /* Solve M x = b (Eq. 2.2) by right-preconditioned flexible GMRES(m) with P_alpha
@@ -132,18 +135,21 @@ int fgmres_solve_host(aao_handle* h, const double* b_host, double* x_host, doubl
 
 /* z_dev <- P_alpha^{-1} v_dev, the same computation as precond_apply, for callers that cannot
    allocate device memory (the paper has no counterpart: this is a deployment variant).
-   Callers inside a CUDA stream capture that must not add allocations, processes with a fixed
-   device-memory budget, or latency-critical paths that cannot afford an allocation's
-   synchronisation cannot call aao_create, which allocates its tables and workspace. This entry
-   point takes the problem descriptor directly and keeps every table and the half spectrum in
-   one static device array of 32 MiB (reserved on each GPU that loads the library until the
-   process exits); it calls no cudaMalloc or cudaFree.
+   Processes that run under a fixed device-memory budget handed out up front, or latency-critical
+   paths that cannot afford an allocation's implicit synchronisation or its failure, cannot call
+   aao_create, which allocates its tables and workspace. This entry point takes the problem
+   descriptor directly and keeps every table and the half spectrum in one static device array of
+   32 MiB (reserved on each GPU that loads the library until the process exits); it calls no
+   cudaMalloc or cudaFree.
+    - Operators: AAO_OP_BS and AAO_OP_LOCALVOL. AAO_OP_RIESZ returns AAO_EUNSUPPORTED: its step
+      (b) needs the dense inverses or the eigendecomposition that aao_create builds.
     - Size limit: the half spectrum plus tables must fit in 32 MiB, roughly
       (nt/2+1) * 64*ceil(nx/64) * 8 bytes (mixed) or * 16 bytes (FP64) plus O(nt + nx);
       e.g. nx 2047, nt 2048 fits in mixed precision. Larger problems return AAO_EINVAL
       with a message; use precond_apply for them.
     - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
-      with that device current; make that first call before any stream capture.
+      with that device current and keeps it for the life of the process (do not reset the device
+      between calls); make that first call before any stream capture.
     - All calls on a device share the array. Each call rewrites everything it reads, so no
       clearing is needed, but calls whose work overlaps on the GPU race on it: order them
       (one stream, or events).
@@ -222,6 +228,16 @@ int aao_mlp_normalization(double* feat_mean, double* feat_scale, double* y_mean,
 /* Predict (alpha, m) for raw features feats = (sigma, r, T, nx, nt, cv) with the BF16 forward;
    alpha is clamped to [1e-5, 0.1] and m rounded up to the next of {5, 10, 20, 30, 40}. */
 int alpha_mlp_predict(aao_mlp* h, const float feats[6], double* alpha, int* m);
+
+/* Fault injection for tests of the failure path (the paper has no counterpart). With mask bit
+   AAO_INJECT_TC_NO_LOAD set, the tensor-core products of the symmetric Riesz operator's spectral
+   step (b) issue no operator load, so the first bounded wait for an operator tile runs out with
+   nothing in flight: the products skip their output and precond_apply / fgmres_solve on h return
+   AAO_TIMEOUT. wait_ms > 0 replaces the 2 s bound of those waits (so that a test ends quickly);
+   mask 0 with wait_ms <= 0 restores normal operation. No GPU fault is raised: the kernels return
+   and the context stays usable. Errors: AAO_EINVAL for a NULL handle or an unknown bit. */
+#define AAO_INJECT_TC_NO_LOAD 1
+int aao_fault_inject(aao_handle* h, int mask, double wait_ms);
 
 /* Dense symmetric eigendecomposition on the host, FP64: A = Q diag(w) Q^T. A_host (n*n doubles,
    row-major, symmetric; only its values are used, the upper and lower triangles must agree) is

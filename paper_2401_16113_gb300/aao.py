@@ -28,7 +28,8 @@ EXPORTS = ["aao_create", "aao_destroy", "aao_rhs", "aao_matvec", "precond_apply"
            "aao_mlp_create", "aao_mlp_destroy", "aao_mlp_params", "aao_mlp_grad", "aao_mlp_adam_step",
            "aao_mlp_train", "aao_mlp_forward", "aao_mlp_normalization", "alpha_mlp_predict",
            "fgmres_solve", "fgmres_solve_host", "aao_last_error", "aao_launch_count",
-           "aao_profile_enable", "aao_profile_read", "aao_sym_eig"]
+           "aao_profile_enable", "aao_profile_read", "aao_sym_eig", "aao_fault_inject"]
+AAO_INJECT_TC_NO_LOAD = 1
 
 
 class AaoProblem(ctypes.Structure):
@@ -96,6 +97,7 @@ def load(path=None):
     lib.aao_mlp_normalization.argtypes = [ctypes.POINTER(dp)] * 4
     lib.alpha_mlp_predict.argtypes = [vp, fp, ctypes.POINTER(dp), ctypes.POINTER(ip)]
     lib.aao_sym_eig.argtypes = [ip, ctypes.POINTER(dp), ctypes.POINTER(dp)]
+    lib.aao_fault_inject.argtypes = [vp, ip, dp]
     lib.aao_last_error.restype = ctypes.c_char_p
     lib.aao_launch_count.restype = ctypes.c_uint64
     lib.aao_profile_enable.argtypes = [ctypes.c_int]
@@ -106,7 +108,8 @@ def load(path=None):
                  "fgmres_solve_host", "aao_profile_enable", "aao_profile_read", "aao_batch_create",
                  "aao_batch_rhs", "batch_submit", "aao_batch_destroy", "aao_batch_set_alpha", "aao_mlp_create",
                  "aao_mlp_destroy", "aao_mlp_params", "aao_mlp_grad", "aao_mlp_adam_step", "aao_mlp_train",
-                 "aao_mlp_forward", "aao_mlp_normalization", "alpha_mlp_predict", "aao_sym_eig"):
+                 "aao_mlp_forward", "aao_mlp_normalization", "alpha_mlp_predict", "aao_sym_eig",
+                 "aao_fault_inject"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -198,6 +201,11 @@ def aao_matvec(h, x, y):
 
 def precond_apply(h, v, z):
     _check(load().precond_apply(h.ptr, _dev(v, h.n), _dev(z, h.n)))
+
+
+def aao_fault_inject(h, mask, wait_ms=0.0):
+    """Fault injection for tests of the timeout path (see include/aao.h)."""
+    _check(load().aao_fault_inject(h.ptr, int(mask), float(wait_ms)))
 
 
 def precond_apply_static(p, v, z, stream=None):

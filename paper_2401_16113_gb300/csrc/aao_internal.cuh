@@ -263,6 +263,8 @@ struct Handle {
   float *rz_qh = nullptr, *rz_ql = nullptr;
   float *rz_qth = nullptr, *rz_qtl = nullptr;
   int* rz_err = nullptr;    // set by a tensor-core product whose bounded wait gave up
+  unsigned long long rz_wait_ns = 2000000000ull;  // bound of each wait in those products
+  int rz_inject = 0;        // fault injection (aao_fault_inject): the products issue no operator load
   // TMA tensor maps (CUtensorMap, 128 bytes each) of the tiled Q^T head, tail, Q head, tail
   alignas(64) unsigned char rz_tmap[4 * 128] = {};
 

@@ -161,7 +161,29 @@ int aao_matvec(aao_handle* hd, const double* x, double* y) {
 int precond_apply(aao_handle* hd, const double* v, double* z) {
   NvtxRange nv("precond_apply");
   if (!hd || !v || !z) { set_error("precond_apply: null argument"); return AAO_EINVAL; }
-  return launch_precond(hd->h, v, z, false);
+  Handle& h = hd->h;
+  AAO_TRY(launch_precond(h, v, z, false));
+  if (h.rz_err) {
+    // the spectral step (b) of the symmetric Riesz operator runs on the tensor cores with bounded
+    // waits: read (and clear) its error word, so that a product that gave up is reported here
+    int e = 0;
+    AAO_TRY_CUDA(cudaMemcpyAsync(&e, h.rz_err, sizeof(int), cudaMemcpyDeviceToHost, h.stream));
+    AAO_TRY_CUDA(cudaStreamSynchronize(h.stream));
+    if (e) {
+      AAO_TRY_CUDA(cudaMemsetAsync(h.rz_err, 0, sizeof(int), h.stream));
+      set_error("precond_apply: a tensor-core product of step (b) gave up a bounded wait; z is not valid");
+      return AAO_TIMEOUT;
+    }
+  }
+  return AAO_OK;
+}
+
+int aao_fault_inject(aao_handle* hd, int mask, double wait_ms) {
+  if (!hd || (mask & ~AAO_INJECT_TC_NO_LOAD) != 0) { set_error("aao_fault_inject: bad argument"); return AAO_EINVAL; }
+  Handle& h = hd->h;
+  h.rz_inject = mask & AAO_INJECT_TC_NO_LOAD;
+  h.rz_wait_ns = wait_ms > 0 ? (unsigned long long)(wait_ms * 1e6) : 2000000000ull;
+  return AAO_OK;
 }
 
 int fgmres_solve(aao_handle* hd, const double* b, double* x, double tol, int m, int maxit, aao_stats* st) {

@@ -25,6 +25,7 @@
 
 #include <chrono>
 #include <complex>
+#include <map>
 #include <mutex>
 #include <unordered_map>
 #include <vector>
@@ -338,14 +339,15 @@ int grid_for(size_t n) {
 // partial second wave idles most SMs), at most `need` and at most kPartBlocks.
 int wave_blocks(const Handle& h, const void* kernel, size_t need) {
   static std::mutex mu;
-  static std::unordered_map<const void*, int> occ;
-  int o = 0;
+  static std::map<std::pair<int, const void*>, int> occ;  // per (device, kernel)
+  int o = 0, dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
   {
     std::lock_guard<std::mutex> lk(mu);
-    auto it = occ.find(kernel);
+    auto it = occ.find({dev, kernel});
     if (it == occ.end()) {
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kernel, kThreads, 0) != cudaSuccess || o < 1) o = 1;
-      occ[kernel] = o;
+      occ[{dev, kernel}] = o;
     } else {
       o = it->second;
     }
@@ -722,6 +724,8 @@ int run_fgmres(Handle& h, const double* b, double* x, double tol, int m, int max
 
   int its = 0, restarts = 0, status = AAO_OK;
   double rel = 0.0, est = 0.0, bnorm = 0.0;
+  // the error word of the tensor-core step (b) reports this solve only
+  if (h.rz_err) AAO_TRY_CUDA(cudaMemsetAsync(h.rz_err, 0, sizeof(int), h.stream));
   for (bool first = true;; first = false) {
     NvtxRange nv_cycle("fgmres_cycle");
     // restart residual r = b - M x, written as the raw first basis vector V_0 (the first one also

@@ -1,11 +1,10 @@
 // precond_apply_static: the P_alpha^{-1} apply for callers that must not allocate device memory.
 //
-// Some callers cannot call cudaMalloc at the point where they need the preconditioner:
-// code running inside a CUDA stream capture that must not add allocation nodes, host code
-// under a fixed device-memory budget (a pool handed out up front, or a process that must
-// never grow its footprint after start-up), and real-time paths where an allocation's
-// implicit synchronisation or its failure mode is not acceptable. aao_create allocates the
-// handle's tables and the half-spectrum workspace, so it is not usable there.
+// Some callers cannot call cudaMalloc at the point where they need the preconditioner: host
+// code under a fixed device-memory budget (a pool handed out up front, or a process that must
+// never grow its footprint after start-up), and real-time paths where an allocation's implicit
+// synchronisation or its failure mode is not acceptable. aao_create allocates the handle's
+// tables and the half-spectrum workspace, so it is not usable there.
 //
 // This entry point needs nothing but the caller's input and output vectors. Its scratch
 // (the FFT twiddles, Lambda_alpha tables, shifted eigenvalues, the tau*Abar diagonals and the
@@ -17,8 +16,10 @@
 // between them) race on it: order them, for example by using one stream.
 //
 // The device address of the array is looked up with cudaGetSymbolAddress the first time the
-// entry point runs on a device (with that device current) and cached; make that first call
-// before starting any stream capture that will contain later calls.
+// entry point runs on a device (with that device current) and cached for the life of the
+// process: a cudaDeviceReset between calls would leave the cached address stale, so the library
+// supports no reset while it is in use. Make that first call before starting any stream capture
+// that will contain later calls.
 #include <math.h>
 
 #include <atomic>

@@ -24,9 +24,10 @@
 //
 // The unitary DFT of Sec. 3.1 carries 1/sqrt(nt) in each direction; here the forward FFT is
 // unnormalised and the single 1/nt is folded into the unscaling table.
+#include <map>
 #include <mutex>
+#include <utility>
 #include <vector>
-#include <unordered_map>
 
 #include "precond_dev.cuh"
 
@@ -39,14 +40,18 @@ using namespace pdev;
 constexpr size_t kTriSmemMax = 227 * 1024;  // dynamic shared memory per CTA
 
 // cudaFuncSetAttribute(MaxDynamicSharedMemorySize) only when a launch needs more than was set
-// before for that kernel (the call is not free on the host, and the host's lead over the GPU
-// matters after every status read-back of the solver)
+// before for that kernel on the current device (the attribute belongs to one device; the call is
+// not free on the host, and the host's lead over the GPU matters after every status read-back of
+// the solver)
 int ensure_smem(const void* kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return AAO_OK;
+  int dev = 0;
+  AAO_TRY_CUDA(cudaGetDevice(&dev));
   static std::mutex mu;
-  static std::unordered_map<const void*, size_t> set;
+  static std::map<std::pair<int, const void*>, size_t> set;
   std::lock_guard<std::mutex> lk(mu);
-  size_t& cur = set[kernel];
-  if (bytes <= 48 * 1024 || bytes <= cur) return AAO_OK;
+  size_t& cur = set[{dev, kernel}];
+  if (bytes <= cur) return AAO_OK;
   AAO_TRY_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
   cur = bytes;
   return AAO_OK;

@@ -84,14 +84,17 @@ __global__ void __launch_bounds__(256) k_rz_cgemm_sum(const float2* __restrict__
 // without swizzling: 8-row x 16-byte core matrices, adjacent along K 128 bytes apart and along
 // the rows 1024 bytes apart (32 contraction entries per staged chunk). Two chunks are staged
 // alternately; the MMAs of one run while the threads stage the next, a tcgen05.commit per chunk
-// arriving on that buffer's mbarrier. Every wait is bounded: on a timeout the kernel records an
-// error code and skips its output (the solve then reports a failure instead of hanging).
+// arriving on that buffer's mbarrier. Every wait is bounded in time (the global nanosecond
+// timer): when one gives up, the CTA raises a shared abort flag, the producer stops issuing, the
+// TMA loads and the MMAs already issued are waited for (bounded as well), and only then is TMEM
+// freed; the kernel records an error code and skips its output (the solve then reports
+// AAO_TIMEOUT instead of hanging).
 namespace tcg {
 constexpr int kM = 128, kN = 64, kKC = 32, kBins = kN / 2, kSeg = 4;  // kSeg contraction segments
 constexpr uint32_t kAop = kM * kKC * 4, kBop = kN * kKC * 4;  // bytes of one operand tile
 constexpr uint32_t kStage = 2 * kAop + 2 * kBop;               // hi and lo of both operands
 constexpr uint32_t kSmem = 2 * kStage + 64 + 1024;             // two stages, barriers, alignment
-constexpr long long kSpinLimit = 1ll << 22;
+constexpr unsigned long long kWaitNs = 2000000000ull;          // 2 s: far above any legitimate wait
 
 // A staged operand tile (rows x 32 contraction entries, K-major, no swizzling) keeps entry
 // (row r, k) at byte ((r / 8) * 8 + k / 4) * 128 + (r % 8) * 16 + (k % 4) * 4: 8-row x 16-byte core
@@ -122,9 +125,17 @@ __device__ __forceinline__ void mma(uint32_t tmem, uint64_t da, uint64_t db, uin
 __device__ __forceinline__ void commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
 }
-// bounded wait for the completion of phase `parity` of an mbarrier; false on timeout
-__device__ __forceinline__ bool wait_parity(uint32_t mbar, uint32_t parity) {
-  for (long long i = 0; i < kSpinLimit; ++i) {
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// bounded wait for the completion of phase `parity` of an mbarrier: false once wait_ns have passed,
+// or (abort != nullptr) as soon as *abort is set by another thread of the CTA
+__device__ __forceinline__ bool wait_parity(uint32_t mbar, uint32_t parity, unsigned long long wait_ns,
+                                            const volatile int* abort = nullptr) {
+  const unsigned long long t0 = now_ns();
+  for (;;) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -133,8 +144,9 @@ __device__ __forceinline__ bool wait_parity(uint32_t mbar, uint32_t parity) {
         : "r"(mbar), "r"(parity)
         : "memory");
     if (done) return true;
+    if (abort && *abort) return false;
+    if (now_ns() - t0 > wait_ns) return false;
   }
-  return false;
 }
 }  // namespace tcg
 
@@ -161,17 +173,27 @@ __device__ __forceinline__ bool staging_all(bool v) {
 // P[seg][k][n] for k < Kb (see above). A: complex rows of pitch lda; thi / tlo: tensor maps of the
 // operator's head and tail, stored tiled at create (row group rg, K group kg, row r, entry q at
 // float ((rg (ldo/4) + kg) 8 + r) 4 + q); segment seg = blockIdx.z covers [seg Mseg, (seg+1) Mseg),
-// Mseg a multiple of 32. err: set to 1 if a wait gave up.
+// Mseg a multiple of 32. err: set to 1 if a wait gave up. wait_ns bounds every wait; inject != 0
+// (fault injection for tests of the timeout path) makes the producer issue no load, so that the
+// first wait for an operator tile runs out with nothing in flight.
 // Warps 0-3 stage the spectrum tiles and write the output (thread 0 issues the MMAs); warp 4 is
 // the TMA producer of the operator tiles, running ahead as far as the two buffers allow. Per
 // buffer: `full` completes when both operator tiles have landed (transaction count), `empty`
 // when the MMAs that read the buffer have finished (tcgen05.commit).
+// Timeout path: the thread whose wait gives up raises the shared abort flag; every other wait
+// returns at once when it sees the flag. The producer then issues nothing more and waits for the
+// `full` phases of the last load it issued into each buffer, and thread 0 waits for the `empty`
+// phase of the last chunk it committed (a commit covers all earlier MMAs of the thread), so that
+// no copy into this CTA's shared memory and no MMA is pending when TMEM is freed and the CTA
+// exits. These drain waits ignore the flag and are bounded by wait_ns too.
 __global__ void __launch_bounds__(160, 1) k_rz_tc(const float2* __restrict__ A, int lda,
                                                   const __grid_constant__ CUtensorMap thi,
                                                   const __grid_constant__ CUtensorMap tlo, float2* __restrict__ P,
-                                                  int ldp, int Kb, int Mseg, int* __restrict__ err) {
+                                                  int ldp, int Kb, int Mseg, int* __restrict__ err,
+                                                  unsigned long long wait_ns, int inject) {
   using namespace tcg;
   extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ volatile int abort_flag;
   pdl_sync();
   const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(smraw);
   const uint32_t base = (s0 + 1023u) & ~1023u;  // 1024-aligned operand tiles
@@ -181,8 +203,13 @@ __global__ void __launch_bounds__(160, 1) k_rz_tc(const float2* __restrict__ A, 
   const int tid = threadIdx.x, warp = tid >> 5;
   const int n0 = blockIdx.x * kM, b0 = blockIdx.y * kBins, seg = blockIdx.z;
   const int mbeg = seg * Mseg, nch = Mseg / kKC;
+  auto raise_abort = [&]() {
+    abort_flag = 1;
+    __threadfence_block();
+  };
 
   if (tid == 0) {
+    abort_flag = 0;
     for (int i = 0; i < 4; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bars + 8 * i) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -198,16 +225,25 @@ __global__ void __launch_bounds__(160, 1) k_rz_tc(const float2* __restrict__ A, 
   if (warp == 4) {
     // producer: chunk c into buffer c & 1 once the MMAs of chunk c - 2 have released it
     if ((tid & 31) == 0) {
-      for (int c = 0; c < nch; ++c) {
+      int issued = 0;
+      for (int c = 0; c < nch && !inject; ++c) {
         const int buf = c & 1;
-        if (c >= 2 && !wait_parity(empty0 + 8 * buf, ((c - 2) >> 1) & 1)) { ok = false; break; }
+        if (abort_flag) break;
+        if (c >= 2 && !wait_parity(empty0 + 8 * buf, ((c - 2) >> 1) & 1, wait_ns, &abort_flag)) {
+          if (!abort_flag) { ok = false; raise_abort(); }
+          break;
+        }
         const uint32_t st = base + buf * kStage;
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full0 + 8 * buf), "r"(2 * kAop)
                      : "memory");
         const int x = ((mbeg + c * kKC) / kKC) * 256, y = n0 / 8;
         tma_tile(st, &thi, x, y, full0 + 8 * buf);
         tma_tile(st + kAop, &tlo, x, y, full0 + 8 * buf);
+        issued = c + 1;
       }
+      // drain: the last load issued into each buffer has landed (none newer shares its phase)
+      for (int c = issued - 2 > 0 ? issued - 2 : 0; c < issued; ++c)
+        if (!wait_parity(full0 + 8 * (c & 1), (c >> 1) & 1, wait_ns)) ok = false;
       if (!ok) atomicExch(err, 1);
     }
     __syncwarp();  // the producer lane rejoins its warp before the final barrier
@@ -225,13 +261,22 @@ __global__ void __launch_bounds__(160, 1) k_rz_tc(const float2* __restrict__ A, 
                          : make_float4(0.f, 0.f, 0.f, 0.f);
       }
     };
+    int committed = 0;  // chunks whose MMAs thread 0 has committed
     if (nch > 0) fetch_z(mbeg);
     for (int c = 0; c < nch; ++c) {
       const int buf = c & 1;
       const uint32_t st = base + buf * kStage;
       unsigned char* gst = gbase + buf * kStage;
-      if (c >= 2) ok = staging_all(wait_parity(empty0 + 8 * buf, ((c - 2) >> 1) & 1));
-      if (!ok) break;
+      if (c >= 2) {
+        bool freed = true;
+        if (tid == 0) {
+          freed = wait_parity(empty0 + 8 * buf, ((c - 2) >> 1) & 1, wait_ns, &abort_flag);
+          if (!freed && !abort_flag) raise_abort();
+        }
+        __syncwarp();
+        ok = staging_all(freed);
+        if (!ok) break;
+      }
       float4 v[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) v[i] = zv[i];
@@ -253,7 +298,10 @@ __global__ void __launch_bounds__(160, 1) k_rz_tc(const float2* __restrict__ A, 
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       // the operator tiles have landed (thread 0 waits; the outcome is shared at the barrier)
       bool landed = true;
-      if (tid == 0) landed = wait_parity(full0 + 8 * buf, (c >> 1) & 1);
+      if (tid == 0) {
+        landed = wait_parity(full0 + 8 * buf, (c >> 1) & 1, wait_ns, &abort_flag);
+        if (!landed && !abort_flag) raise_abort();
+      }
       __syncwarp();
       ok = staging_all(landed);
       if (!ok) break;
@@ -269,12 +317,23 @@ __global__ void __launch_bounds__(160, 1) k_rz_tc(const float2* __restrict__ A, 
           mma(tmem, al, bh2, 1u);
         }
         commit(empty0 + 8 * buf);
+        committed = c + 1;
       }
       __syncwarp();
     }
+    // all MMAs finished: the last commit's phase (on the timeout path a drain that ignores the flag)
     if (ok && nch > 0) {
-      const int last = nch - 1;
-      ok = staging_all(wait_parity(empty0 + 8 * (last & 1), (last >> 1) & 1));
+      bool done = true;
+      if (tid == 0) {
+        const int last = nch - 1;
+        done = wait_parity(empty0 + 8 * (last & 1), (last >> 1) & 1, wait_ns, &abort_flag);
+        if (!done && !abort_flag) raise_abort();
+      }
+      __syncwarp();
+      ok = staging_all(done);
+    } else if (!ok && tid == 0 && committed > 0) {
+      const int last = committed - 1;
+      (void)wait_parity(empty0 + 8 * (last & 1), (last >> 1) & 1, wait_ns);
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
@@ -1038,11 +1097,11 @@ int riesz_solve_bins(Handle& h, void* spec, void** result) {
     CUtensorMap m[4];
     memcpy(m, h.rz_tmap, sizeof m);
     AAO_TRY_CUDA(launch_pdl(k_rz_tc, g1, 160, tcg::kSmem, h.stream, (const float2*)spec, h.pitch, m[0], m[1],
-                            h.rz_part, ldq, h.K, h.pitch / s1, h.rz_err));
+                            h.rz_part, ldq, h.K, h.pitch / s1, h.rz_err, h.rz_wait_ns, h.rz_inject));
     AAO_TRY_CUDA(launch_pdl(k_rz_cgemm_sum, sgrid, 256, 0, h.stream, (const float2*)h.rz_part, ldq, h.K, ldq, s1,
                             h.rz_w, ldq, (const float2*)h.rz_dk, ldq));
     AAO_TRY_CUDA(launch_pdl(k_rz_tc, g2, 160, tcg::kSmem, h.stream, (const float2*)h.rz_w, ldq, m[2], m[3],
-                            h.rz_part, ldq, h.K, ldq / s2, h.rz_err));
+                            h.rz_part, ldq, h.K, ldq / s2, h.rz_err, h.rz_wait_ns, h.rz_inject));
     AAO_TRY_CUDA(launch_pdl(k_rz_cgemm_sum, sgrid, 256, 0, h.stream, (const float2*)h.rz_part, ldq, h.K, h.pitch, s2,
                             (float2*)spec, h.pitch, (const float2*)nullptr, ldq));
     AAO_CHECK_LAUNCH();

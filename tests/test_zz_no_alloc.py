@@ -1,13 +1,14 @@
 """precond_apply_static: the preconditioner apply for callers that cannot allocate device
-memory (inside a stream capture, under a fixed memory budget, on latency-critical paths).
-It must give what the allocating precond_apply gives, on repeated calls that share its
-static scratch, and refuse problems larger than that scratch. This file is named to be
-collected last."""
+memory (a fixed device-memory budget handed out up front, or latency-critical paths that cannot
+afford an allocation's synchronisation). On two calls in a row that share its static scratch it
+must give what the allocating precond_apply gives and what the FP64 oracle gives, and it must
+refuse problems larger than that scratch. This file is named to be collected last."""
 import math
 
 import numpy as np
 import pytest
 
+from oracle import aao_oracle as O
 from paper_2401_16113_gb300 import workloads as W
 
 torch = pytest.importorskip("torch")
@@ -40,11 +41,12 @@ CASES = [
 
 @pytest.mark.parametrize("p", CASES, ids=["localvol-2047x2048-mixed", "bs-255x256-fp64", "bs-37x16-mixed",
                                           "localvol-2047x1536-mixed", "bs-100x15-fp64", "bs-63x24-mixed"])
-def test_static_matches_allocating_apply_twice(aao, p):
+def test_static_matches_allocating_apply_and_oracle_twice(aao, p):
     n = W.unknowns(p)
     h = aao.aao_create(p)
     for call, seed in enumerate((101, 202)):
-        v = torch.from_numpy(W.random_vector(n, seed=seed)).cuda()
+        v_np = W.random_vector(n, seed=seed)
+        v = torch.from_numpy(v_np).cuda()
         z_ref = torch.empty(n, dtype=torch.float64, device="cuda")
         z = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
         aao.precond_apply(h, v, z_ref)
@@ -53,7 +55,19 @@ def test_static_matches_allocating_apply_twice(aao, p):
         a, b = z.cpu().numpy(), z_ref.cpu().numpy()
         assert np.all(np.isfinite(a)), call
         assert np.linalg.norm(a - b) <= bound(p) * np.linalg.norm(b), (call, np.linalg.norm(a - b) / np.linalg.norm(b))
+        zo = O.precond_fft(p, v_np)
+        assert np.linalg.norm(a - zo) <= bound(p) * np.linalg.norm(zo), (call, np.linalg.norm(a - zo) / np.linalg.norm(zo))
     h.close()
+
+
+def test_static_rejects_the_riesz_operator(aao):
+    p = W.with_(W.riesz_1023x512(), nx=63, nt=16)
+    n = W.unknowns(p)
+    v = torch.zeros(n, dtype=torch.float64, device="cuda")
+    z = torch.zeros(n, dtype=torch.float64, device="cuda")
+    with pytest.raises(aao.AaoError) as e:
+        aao.precond_apply_static(p, v, z)
+    assert e.value.code == aao.AAO_EUNSUPPORTED
 
 
 def test_static_rejects_problems_beyond_its_scratch(aao):
