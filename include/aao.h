@@ -56,9 +56,9 @@ extern "C" {
 
 /*
  * Problem descriptor (plain old data; copied by aao_create).
- *  nx, nt      interior spatial nodes (2..8192 mixed, 2..4096 FP64) and CN steps (1..8192
- *              mixed, 1..4096 FP64; prime factors 2, 3, 5, 7 only: a power of two takes the
- *              register FFT, any other nt the mixed-radix shared-memory FFT)
+ *  nx, nt      interior spatial nodes (2..8192) and CN steps (1..8192; prime factors 2, 3, 5,
+ *              7 only: a power of two takes the register FFT, any other nt the mixed-radix
+ *              shared-memory FFT, up to 4096 in FP64)
  *  op, payoff  AAO_OP_*, AAO_PUT / AAO_CALL
  *  precision   AAO_FP64 or AAO_MIXED
  *  T, r, K, sigma   maturity, rate, strike, volatility
@@ -67,10 +67,15 @@ extern "C" {
  *              or s_max - K e^{-rt} (call), t = time to maturity
  *  alpha       the free parameter of P_alpha (Eq. 3.1), 0 < alpha < 1 (alpha = 1 allowed:
  *              the classical block-circulant preconditioner P_1)
+ *  flags       0, or one AAO_FLAG_STEPB_* to fix how the tridiagonal step (b) is solved (by
+ *              default aao_create times both and keeps the faster; both give P_alpha^{-1} v up
+ *              to rounding)
  *  stream      cudaStream_t on which all work is issued
  */
+#define AAO_FLAG_STEPB_FACTORED 1  /* partition method with per-bin pivot tables made at create */
+#define AAO_FLAG_STEPB_RECOMPUTE 2 /* partition method, pivots recomputed in every apply      */
 typedef struct aao_problem {
-  int32_t nx, nt, op, payoff, precision, reserved;
+  int32_t nx, nt, op, payoff, precision, flags;
   double T, r, K, sigma, s_max, lv_bump, lv_tslope, beta, alpha;
   void* stream;
 } aao_problem;

@@ -20,6 +20,7 @@ AAO_NOT_CONVERGED, AAO_BREAKDOWN, AAO_TIMEOUT, AAO_EUNSUPPORTED = -4, -5, -6, -7
 OPS = {"bs": 0, "localvol": 1, "riesz": 2}
 PAYOFFS = {"put": 0, "call": 1}
 PRECISIONS = {"fp64": 0, "mixed": 1}
+STEPB = {"auto": 0, "factored": 1, "recompute": 2}  # how the tridiagonal step (b) is solved
 STATUS = {0: "ok", -1: "einval", -2: "ecuda", -3: "enomem", -4: "not_converged",
           -5: "breakdown", -6: "timeout", -7: "unsupported"}
 
@@ -34,7 +35,7 @@ AAO_INJECT_TC_NO_LOAD = 1
 
 class AaoProblem(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("nt", ctypes.c_int32), ("op", ctypes.c_int32),
-                ("payoff", ctypes.c_int32), ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("payoff", ctypes.c_int32), ("precision", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("T", ctypes.c_double), ("r", ctypes.c_double), ("K", ctypes.c_double),
                 ("sigma", ctypes.c_double), ("s_max", ctypes.c_double), ("lv_bump", ctypes.c_double),
                 ("lv_tslope", ctypes.c_double), ("beta", ctypes.c_double), ("alpha", ctypes.c_double),
@@ -129,6 +130,7 @@ def make_problem(p, stream=0):
     s.op, s.payoff, s.precision = OPS[p["op"]], PAYOFFS[p["payoff"]], PRECISIONS[p["precision"]]
     s.T, s.r, s.K, s.sigma, s.s_max = p["T"], p["r"], p["K"], p["sigma"], p["s_max"]
     s.lv_bump, s.lv_tslope, s.beta, s.alpha = p["lv_bump"], p["lv_tslope"], p["beta"], p["alpha"]
+    s.flags = STEPB[p.get("step_b", "auto")]
     s.stream = int(stream or 0)
     return s
 

@@ -241,6 +241,9 @@ struct Handle {
   // [K][tri_T * tri_ch], reduction multipliers [K][2 lgT + 1][tri_T]; null where the
   // partition method does not fit in shared memory
   void *tri_fp = nullptr, *tri_fv = nullptr, *tri_fpcr = nullptr;
+  // step (b) by k_tridiag_rc (pivots recomputed from tri, no per-bin tables) instead of the
+  // factored partition method; chosen at create by timing both where both apply
+  bool tri_rc = false;
 
   // Riesz operator (dense Toeplitz): circulant-embedding spectrum (scaled by tau/2 / N2), its
   // twiddles, (tau/2) first column / row / left-exterior coefficients, inverses of step (b)

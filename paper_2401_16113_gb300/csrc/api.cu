@@ -84,15 +84,19 @@ int validate(const aao_problem* p) {
     set_error("aao_create: nt must have no prime factor above 7");
     return AAO_EUNSUPPORTED;
   }
-  const int nt_max = p->precision == AAO_MIXED ? 8192 : 4096;
-  if (p->nt > nt_max) { set_error("aao_create: nt above the shared-memory FFT limit"); return AAO_EUNSUPPORTED; }
-  const int nx_max = p->precision == AAO_MIXED ? 8192 : 4096;
-  if (p->nx > nx_max) { set_error("aao_create: nx above the tridiagonal solver's limit (8192 mixed, 4096 FP64)"); return AAO_EUNSUPPORTED; }
+  // the FP64 mixed-radix FFT keeps two columns of nt complex doubles in shared memory
+  const int nt_max = (p->precision == AAO_MIXED || is_pow2(p->nt)) ? 8192 : 4096;
+  if (p->nt > nt_max) { set_error("aao_create: nt above the shared-memory FFT limit (8192; 4096 for FP64 nt that is not a power of two)"); return AAO_EUNSUPPORTED; }
+  if (p->nx > 8192) { set_error("aao_create: nx above the tridiagonal solver's limit (8192)"); return AAO_EUNSUPPORTED; }
   if (!(p->T > 0) || !(p->K > 0) || !(p->sigma > 0) || !(p->s_max > 0) || !(p->r >= 0)) {
     set_error("aao_create: need T, K, sigma, s_max > 0 and r >= 0");
     return AAO_EINVAL;
   }
   if (!(p->alpha > 0) || !(p->alpha <= 1)) { set_error("aao_create: need 0 < alpha <= 1"); return AAO_EINVAL; }
+  if (p->flags != 0 && p->flags != AAO_FLAG_STEPB_FACTORED && p->flags != AAO_FLAG_STEPB_RECOMPUTE) {
+    set_error("aao_create: flags must be 0 or one AAO_FLAG_STEPB_* value");
+    return AAO_EINVAL;
+  }
   return AAO_OK;
 }
 

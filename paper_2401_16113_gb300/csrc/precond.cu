@@ -287,6 +287,44 @@ bool tri_part_layout(const Handle& h, size_t rsize, TriPart& t) {
   return true;
 }
 
+// layout of k_tridiag_rc: lgT, the odd chunk stride cs, bins per CTA G (at most 512 threads, shared
+// memory within one CTA's limit); false when one bin does not fit
+struct TriRc {
+  int lgT, cs, G, CH;
+  size_t smem;
+};
+bool tri_rc_layout(const Handle& h, size_t rsize, TriRc& t) {
+  if (!h.tri || h.tri_T <= 0 || h.tri_ch > 16) return false;
+  const int T = h.tri_T, ch = h.tri_ch;
+  t.lgT = 0;
+  while ((1 << t.lgT) < T) ++t.lgT;
+  if (t.lgT > kTriMaxLgT) return false;
+  t.cs = (ch & 1) ? ch + 2 : ch + 1;
+  t.CH = ch <= 4 ? 4 : (ch <= 8 ? 8 : 16);
+  const size_t bin = tri_rc_bin_bytes(T, t.cs, 2 * rsize);
+  if (bin > kTriSmemMax) return false;
+  t.G = 512 / T;
+  if (t.G > 15) t.G = 15;  // named barriers 1..15, one per bin
+  while (t.G > 1 && t.G * bin > kTriSmemMax) --t.G;
+  t.smem = t.G * bin;
+  return true;
+}
+
+template <typename R, int CH>
+int launch_tri_rc_ch(Handle& h, const TriRc& t, C_t<R>* spec, const C_t<R>* mu, const C_t<R>* il2) {
+  AAO_TRY(ensure_smem((const void*)k_tridiag_rc<R, CH>, t.smem));
+  AAO_TRY_CUDA(launch_pdl(k_tridiag_rc<R, CH>, (h.K + t.G - 1) / t.G, t.G << t.lgT, t.smem, h.stream, spec, h.nx,
+                          h.K, h.pitch, h.tri_ch, t.cs, t.lgT, reinterpret_cast<const R*>(h.tri), mu, il2));
+  return AAO_OK;
+}
+
+template <typename R>
+int launch_tri_rc(Handle& h, const TriRc& t, C_t<R>* spec, const C_t<R>* mu, const C_t<R>* il2) {
+  if (t.CH == 4) return launch_tri_rc_ch<R, 4>(h, t, spec, mu, il2);
+  if (t.CH == 8) return launch_tri_rc_ch<R, 8>(h, t, spec, mu, il2);
+  return launch_tri_rc_ch<R, 16>(h, t, spec, mu, il2);
+}
+
 template <typename R>
 int tri_factors_t(Handle& h, int lgT) {
   using C = C_t<R>;
@@ -347,12 +385,20 @@ int run_precond(Handle& h, const double* v, void* z, bool z_is_float, const doub
   AAO_CHECK_LAUNCH();
 
   C* spec_b = spec;  // where step (b) leaves its result for step (c)
+  TriRc rc;
   if (h.p.op == AAO_OP_RIESZ) {
     // step (b) with the dense Toeplitz operator: the inverses of the shifted matrices (with
     // drift) or the eigendecomposition (symmetric), both made by aao_create
     void* res = nullptr;
     AAO_TRY(riesz_solve_bins(h, spec, &res));
     spec_b = reinterpret_cast<C*>(res);
+  } else if (h.tri_rc && tri_rc_layout(h, sizeof(R), rc)) {
+    // step (b): partition method with every pivot recomputed from the shared diagonals (no
+    // per-bin tables), G bins of 2^lgT threads per CTA
+    const C* mu = (sizeof(R) == 4) ? (const C*)h.muf : (const C*)h.mu;
+    const C* il2 = (sizeof(R) == 4) ? (const C*)h.il2f : (const C*)h.il2;
+    ProfScope ps(AAO_K_TRIDIAG, h.stream, 2.0 * nsp);
+    AAO_TRY(launch_tri_rc<R>(h, rc, spec, mu, il2));
   } else if (TriPart tp; h.tri_fp && tri_part_layout(h, sizeof(R), tp)) {
     // step (b): partition method with the per-bin factors built with the handle, G bins of
     // tri_T = 2^lgT threads per CTA
@@ -443,6 +489,7 @@ int launch_precond(Handle& h, const double* v, void* z, bool z_is_float, const d
 // on this problem's sizes and keep the fastest. Every tile width computes identical results
 // (each column's transform runs the same operations in the same order); only speed differs.
 int build_tri_factors(Handle& h) {
+  if (h.p.flags == AAO_FLAG_STEPB_RECOMPUTE) return AAO_OK;  // the recomputing solver needs none
   const size_t rsize = h.mixed ? sizeof(float) : sizeof(double);
   TriPart tp;
   if (!tri_part_layout(h, rsize, tp)) return AAO_OK;  // the per-bin fallback solver needs none
@@ -451,6 +498,21 @@ int build_tri_factors(Handle& h) {
 
 int tune_precond(Handle& h) {
   const size_t rs = h.mixed ? 4 : 8;
+  if (h.p.op != AAO_OP_RIESZ) {
+    // without factor tables (one bin's staged rows do not fit, or the caller asked for it) the
+    // recomputing solver is the one
+    TriRc trc;
+    const bool rc_fits = tri_rc_layout(h, rs, trc);
+    if (h.p.flags == AAO_FLAG_STEPB_FACTORED && !h.tri_fp) {
+      set_error("aao_create: the factored step (b) does not fit this nx; use AAO_FLAG_STEPB_RECOMPUTE or 0");
+      return AAO_EUNSUPPORTED;
+    }
+    if (h.p.flags == AAO_FLAG_STEPB_RECOMPUTE && !rc_fits) {
+      set_error("aao_create: the recomputing step (b) does not fit this nx");
+      return AAO_EUNSUPPORTED;
+    }
+    if (!h.tri_fp && rc_fits) h.tri_rc = true;
+  }
   const int pmax = h.mr.nst > 0 ? mr_max_tile(h.nt, 2 * rs) : max_tile(h.nt, rs);
   if (pmax == 1) {
     h.fft_p = 1;
@@ -500,6 +562,34 @@ int tune_precond(Handle& h) {
     if (pbest < best) { best = pbest; bestp = P; }
   }
   h.fft_p = bestp;
+  // step (b): the factored partition method against the recomputing one, where both apply; the
+  // factor tables are freed when the recomputing solver is kept
+  TriRc trc;
+  const bool rc_ok = h.p.op != AAO_OP_RIESZ && tri_rc_layout(h, rs, trc);
+  if (rc == AAO_OK && rc_ok && h.tri_fp && h.p.flags == 0) {
+    float t_mode[2] = {1e30f, 1e30f};
+    for (int mode = 0; mode < 2 && rc == AAO_OK; ++mode) {
+      h.tri_rc = mode == 1;
+      rc = launch_precond(h, v, z, h.mixed, nullptr, vf);
+      for (int r = 0; r < 5 && rc == AAO_OK; ++r) {
+        cudaEventRecord(e0, h.stream);
+        rc = launch_precond(h, v, z, h.mixed, nullptr, vf);
+        cudaEventRecord(e1, h.stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < t_mode[mode]) t_mode[mode] = ms;
+      }
+    }
+    h.tri_rc = t_mode[1] <= t_mode[0];
+    if (h.tri_rc) {
+      cudaStreamSynchronize(h.stream);
+      cudaFree(h.tri_fp);
+      cudaFree(h.tri_fv);
+      cudaFree(h.tri_fpcr);
+      h.tri_fp = h.tri_fv = h.tri_fpcr = nullptr;
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(v);

@@ -60,14 +60,25 @@ def _create(lib, p):
     (dict(op="riesz", precision="fp64"), aao.AAO_EUNSUPPORTED),
     (dict(op="riesz", precision="mixed", beta=2.5), aao.AAO_EINVAL),
     (dict(op="riesz", precision="mixed", nx=4095), aao.AAO_EUNSUPPORTED),
-    (dict(nt=8192, precision="fp64"), aao.AAO_EUNSUPPORTED),
+    (dict(nt=6144, precision="fp64"), aao.AAO_EUNSUPPORTED),
     (dict(nt=16384, precision="mixed"), aao.AAO_EUNSUPPORTED),
+    (dict(nx=8193, precision="fp64"), aao.AAO_EUNSUPPORTED),
 ])
 def test_create_rejects_bad_problems_on_host(lib, bad, code):
     rc, h = _create(lib, W.with_(W.bs_put_255x256(), **bad))
     assert rc == code
     assert h.value is None
     assert lib.aao_last_error().decode()
+
+
+def test_create_rejects_unknown_flags_on_host(lib):
+    s = aao.make_problem(W.bs_put_255x256())
+    s.flags = 3
+    h = ctypes.c_void_p()
+    assert lib.aao_create(ctypes.byref(s), ctypes.byref(h)) == aao.AAO_EINVAL
+    assert h.value is None
+    with pytest.raises(KeyError):
+        aao.make_problem(W.with_(W.bs_put_255x256(), step_b="fastest"))
 
 
 def test_null_arguments_rejected(lib):

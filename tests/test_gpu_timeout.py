@@ -40,8 +40,9 @@ def test_tensor_core_wait_runs_out_and_the_handle_recovers(aao):
     b = torch.empty(n, dtype=torch.float64, device="cuda")
     aao.aao_rhs(h, b)
     x = torch.zeros_like(b)
-    st = aao.fgmres_solve(h, b, x, 1e-8, 30, 4)
-    assert st["status"] == aao.AAO_TIMEOUT, st
+    with pytest.raises(aao.AaoError) as e:
+        aao.fgmres_solve(h, b, x, 1e-8, 30, 4)
+    assert e.value.code == aao.AAO_TIMEOUT
 
     # injection off: the same handle applies and solves correctly
     aao.aao_fault_inject(h, 0, 0.0)
