@@ -179,6 +179,58 @@ def cpu_oracle_solve_seconds(p, reps=1):
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
+def host_cores():
+    """Cores this process may use, read with nproc (os.cpu_count() if nproc is missing)."""
+    try:
+        return int(subprocess.run(["nproc"], capture_output=True, text=True, timeout=10).stdout.strip())
+    except (OSError, ValueError, subprocess.SubprocessError):
+        return os.cpu_count() or 1
+
+
+def _run_py(code, threads=1, timeout=1800):
+    env = dict(os.environ, OMP_NUM_THREADS=str(threads), OPENBLAS_NUM_THREADS=str(threads),
+               MKL_NUM_THREADS=str(threads))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=timeout)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def cpu_sequential_cn_seconds(p):
+    """Sequential Crank-Nicolson time stepping (the oracle's O(Nx Nt) banded solve per step, the
+    optimal serial algorithm for the same discrete solution), single thread."""
+    code = (
+        "import sys,time,json; sys.path.insert(0, %r)\n"
+        "from oracle import aao_oracle as O\n"
+        "p = json.loads(%r)\n"
+        "t0 = time.perf_counter(); U = O.sequential_cn(p); s = time.perf_counter() - t0\n"
+        "print(json.dumps({'s': s}))\n"
+    ) % (ROOT, json.dumps(dict(p, precision="fp64")))
+    return _run_py(code)
+
+
+def cpu_oracle_batch_all_cores(ps, cores):
+    """The oracle's FP64 FGMRES on independent instances, one single-threaded worker process per
+    host core (a spawned pool in a separate process): aggregate unknowns per second."""
+    code = (
+        "import sys,time,json; sys.path.insert(0, %r)\n"
+        "import multiprocessing as mp\n"
+        "def one(p):\n"
+        "    from oracle import aao_oracle as O\n"
+        "    M = O.assemble_M(p); b = O.assemble_b(p)\n"
+        "    x, info = O.fgmres(lambda v: M @ v, lambda v: O.precond_fft(p, v), b, %r, p['m'], 300)\n"
+        "    return info['its']\n"
+        "if __name__ == '__main__':\n"
+        "    ps = json.loads(%r)\n"
+        "    ctx = mp.get_context('spawn')\n"
+        "    with ctx.Pool(%d) as pool:\n"
+        "        pool.map(one, ps[:%d])\n"
+        "        t0 = time.perf_counter(); its = pool.map(one, ps); s = time.perf_counter() - t0\n"
+        "    print(json.dumps({'s': s, 'its': sum(its) / len(its)}))\n"
+    ) % (ROOT, TOL, json.dumps([dict(p, precision="fp64") for p in ps]), cores, cores)
+    return _run_py(code, threads=1)
+
+
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle, as it stands, on this host's cores."""
     rank = int(os.environ.get("RANK", "0"))
@@ -377,15 +429,215 @@ def run_ours(args):
                     "d2h_bytes_per_step": 8 * n}}
     line.update(extras)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = host_cores()
         r = cpu_oracle_solve_seconds(p)
         line["cpu_baseline"] = {"value": n / r["s"], "unit": "unknowns/s", "cores": 1, "kind": "oracle",
                                 "sample": "one full FP64 FGMRES(30) solve of the same workload "
                                           f"({r['its']} iterations, numpy/scipy oracle, single thread)"}
+        cn = cpu_sequential_cn_seconds(p)
+        from paper_2401_16113_gb300 import workloads as W
+        sample = W.batch_instances(512, m=20)[:4 * cores]
+        ub = cpu_oracle_batch_all_cores(sample, cores)
+        line["cpu_baselines"] = {
+            "host_cores": cores,
+            "oracle_fgmres_1core": line["cpu_baseline"],
+            "sequential_cn_1core": {"value": n / cn["s"], "unit": "unknowns/s", "cores": 1, "kind": "oracle",
+                                    "sample": "sequential Crank-Nicolson (banded solve per step) of the same "
+                                              "workload, single thread"},
+            "oracle_fgmres_all_cores_batch": {
+                "value": sum(W.unknowns(q) for q in sample) / ub["s"], "unit": "unknowns/s", "cores": cores,
+                "kind": "oracle", "sample": f"the first {len(sample)} of the 512 batched instances, FP64 FGMRES(20) "
+                                            f"to 1e-8, one single-threaded worker per core "
+                                            f"(mean {ub['its']:.1f} iterations)"}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     h.close()
     if dist:
         tdist.destroy_process_group()
+
+
+def _timed(stream, fn):
+    """Device milliseconds of fn() bracketed by CUDA events on the stream, and its result."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    r = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), r
+
+
+def run_metric_arms(args, flush, stream):
+    """The metric's own comparison, on the same GB300, setup shown separately and included:
+    - c3: the 512 batched instances (seeded), mixed precision, one persistent graph-replayed launch,
+      alpha and m predicted per instance by the MLP (trained on the GPU on 20,000 instances of the
+      same distribution, labelled by the solver's alpha sweep), against the same 512 instances
+      solved one after another by the plain FP64 single-instance solver at the fixed alpha = 1e-3,
+      m = 20; two attribution arms in between (mixed one after another, mixed batched at fixed
+      alpha);
+    - c5: local volatility 8191 x 8192, the learned (alpha, m) with the mixed solver against the
+      plain FP64 solve at alpha = 1e-3, m = 40.
+    Every arm solves to relative residual 1e-8 from a zero guess; an instance whose predicted
+    alpha fails falls back to alpha = 1e-3 inside the timed arm."""
+    import numpy as np
+    import torch
+
+    from paper_2401_16113_gb300 import aao, alpha_mlp as AM, workloads as W
+
+    out = {}
+    t0 = time.time()
+    train_ps = W.batch_instances(args.train_instances, seed=W.SEED + 1)
+    mlp, loss, _ = AM.train(train_ps, epochs=200, minibatch=512, lr=3e-3, seed=0, tol=TOL, maxit=200)
+    t_train = time.time() - t0
+    ps = W.batch_instances(512, m=20)
+    total = float(sum(W.unknowns(p) for p in ps))
+    preds = [AM.predict(mlp, p) for p in ps]
+
+    def sequential(precision, alpha_m):
+        """Each instance: aao_create, aao_rhs and fgmres_solve, one after another (device-timed
+        setup and solve; the first pass warms the process's tuning cache for these shapes and is
+        not counted)."""
+        setup_ms = solve_ms = 0.0
+        its = []
+        for i, p in enumerate(ps):
+            a, m = alpha_m(i)
+            q = W.with_(p, precision=precision, alpha=a)
+            n = W.unknowns(q)
+            b = torch.empty(n, dtype=torch.float64, device="cuda")
+            x = torch.zeros(n, dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            c0 = time.perf_counter()
+            h = aao.aao_create(q)
+            aao.aao_rhs(h, b)
+            torch.cuda.synchronize()
+            setup_ms += 1e3 * (time.perf_counter() - c0)
+            c0 = time.perf_counter()
+            st = aao.fgmres_solve(h, b, x, TOL, m, 300)
+            solve_ms += 1e3 * (time.perf_counter() - c0)
+            if st["status"] != 0 or st["rel_residual"] > TOL:
+                raise RuntimeError(f"{precision} instance {i}: {st}")
+            its.append(st["iterations"])
+            h.close()
+        return setup_ms, solve_ms, its
+
+    def arm_line(setup_ms, solve_ms, its, extra=None):
+        d = {"value": total / (solve_ms / 1e3), "unit": "unknowns/s", "solve_ms": solve_ms, "setup_ms": setup_ms,
+             "value_with_setup": total / ((solve_ms + setup_ms) / 1e3), "mean_iterations": float(np.mean(its))}
+        if extra:
+            d.update(extra)
+        return d
+
+    sequential("fp64", lambda i: (AM.DEFAULT_ALPHA, 20))  # warm the tuning cache of every shape
+    fp64 = arm_line(*sequential("fp64", lambda i: (AM.DEFAULT_ALPHA, 20)), {"alpha": AM.DEFAULT_ALPHA, "m": 20})
+    sequential("mixed", lambda i: (AM.DEFAULT_ALPHA, 20))
+    mixed_seq = arm_line(*sequential("mixed", lambda i: (AM.DEFAULT_ALPHA, 20)), {"alpha": AM.DEFAULT_ALPHA, "m": 20})
+
+    def batched(alphas, m):
+        qs = [W.with_(p, alpha=a) for p, a in zip(ps, alphas)]
+        torch.cuda.synchronize()
+        c0 = time.perf_counter()
+        bt = aao.aao_batch_create(qs, m)
+        bs = [torch.empty(k, dtype=torch.float64, device="cuda") for k in bt.sizes]
+        xs = [torch.zeros(k, dtype=torch.float64, device="cuda") for k in bt.sizes]
+        aao.aao_batch_rhs(bt, bs)
+        torch.cuda.synchronize()
+        setup = 1e3 * (time.perf_counter() - c0)
+        st = aao.batch_submit(bt, bs, xs, TOL, 300)  # graph capture
+        times = []
+        for _ in range(max(3, args.steps)):
+            flush.fill_(1.0)
+            for x in xs:
+                x.zero_()
+            ms, st = _timed(stream, lambda: aao.batch_submit(bt, bs, xs, TOL, 300))
+            times.append(ms)
+        bt.close()
+        return setup, float(np.median(times)), st
+
+    setup_f, ms_f, st_f = batched([AM.DEFAULT_ALPHA] * len(ps), 20)
+    if any(s_["status"] != 0 for s_ in st_f):
+        raise RuntimeError("batched solve at the default alpha failed")
+    batched_fixed = arm_line(setup_f, ms_f, [s_["iterations"] for s_ in st_f],
+                             {"alpha": AM.DEFAULT_ALPHA, "m": 20, "launches_per_step": 1})
+    a_pred = [a for a, _ in preds]
+    m_pred = max(m for _, m in preds)
+    setup_l, ms_l, st_l = batched(a_pred, m_pred)
+    failed = [i for i, s_ in enumerate(st_l) if s_["status"] != 0]
+    fb_setup = fb_solve = 0.0
+    its_l = [s_["iterations"] for s_ in st_l]
+    if failed:
+        # fallback: the failed instances again, batched, at the default alpha (inside the arm)
+        sub = [ps[i] for i in failed]
+        c0 = time.perf_counter()
+        bt = aao.aao_batch_create(sub, 20)
+        bs = [torch.empty(k, dtype=torch.float64, device="cuda") for k in bt.sizes]
+        xs = [torch.zeros(k, dtype=torch.float64, device="cuda") for k in bt.sizes]
+        aao.aao_batch_rhs(bt, bs)
+        torch.cuda.synchronize()
+        fb_setup = 1e3 * (time.perf_counter() - c0)
+        fb_solve, st_fb = _timed(stream, lambda: aao.batch_submit(bt, bs, xs, TOL, 300))
+        bt.close()
+        for j, i in enumerate(failed):
+            its_l[i] += st_fb[j]["iterations"]
+    learned = arm_line(setup_l + fb_setup, ms_l + fb_solve, its_l,
+                       {"alpha_range": [min(a_pred), max(a_pred)], "m": m_pred, "fallbacks": len(failed),
+                        "launches_per_step": 1 + (1 if failed else 0)})
+    out["metric_c3"] = {
+        "workload": "batch_512_bs_mixed_sizes", "instances": len(ps), "unknowns": total, "tol": TOL,
+        "mixed_batched_learned": learned, "mixed_batched_fixed_alpha": batched_fixed,
+        "mixed_sequential": mixed_seq, "plain_fp64_sequential": fp64,
+        "ratio": learned["value"] / fp64["value"],
+        "ratio_with_setup": learned["value_with_setup"] / fp64["value_with_setup"],
+        "note": "value = unknowns / device solve time; value_with_setup adds aao_create / aao_batch_create "
+                "and the right-hand sides (process tuning cache warm); 512 put/call instances, sigma "
+                "U[0.1,0.6], r U[0,0.08], K U[50,150], T U[0.25,2], Nx {127..1023}, Nt {64..1024}",
+        "training": {"instances": args.train_instances, "seconds": t_train, "final_loss": loss, "epochs": 200}}
+
+    # c5: local volatility 8191 x 8192
+    big = W.localvol_8191x8192("mixed")
+    a5, m5 = AM.predict(mlp, big)
+
+    def single(q, m):
+        n = W.unknowns(q)
+        b = torch.empty(n, dtype=torch.float64, device="cuda")
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        c0 = time.perf_counter()
+        h = aao.aao_create(q)
+        aao.aao_rhs(h, b)
+        torch.cuda.synchronize()
+        setup = 1e3 * (time.perf_counter() - c0)
+        st = aao.fgmres_solve(h, b, x, TOL, m, 300)  # warm (workspace allocation)
+        best = None
+        for _ in range(3):
+            x.zero_()
+            flush.fill_(1.0)
+            ms, st = _timed(stream, lambda: aao.fgmres_solve(h, b, x, TOL, m, 300))
+            best = ms if best is None else min(best, ms)
+        h.close()
+        del b, x
+        torch.cuda.empty_cache()
+        return {"value": n / (best / 1e3), "unit": "unknowns/s", "solve_ms": best, "setup_ms": setup,
+                "value_with_setup": n / ((best + setup) / 1e3), "iterations": st["iterations"],
+                "rel_residual": st["rel_residual"], "status": st["status"]}
+
+    lrn = single(W.with_(big, alpha=a5), m5)
+    fell_back = lrn["status"] != 0
+    if fell_back:
+        lrn = single(W.with_(big, alpha=AM.DEFAULT_ALPHA), 40)
+    lrn.update({"alpha": a5, "m": m5, "fallback": fell_back})
+    f64 = single(W.with_(big, precision="fp64", alpha=AM.DEFAULT_ALPHA), 40)
+    f64.update({"alpha": AM.DEFAULT_ALPHA, "m": 40})
+    fixed_mixed = single(W.with_(big, alpha=AM.DEFAULT_ALPHA), 40)
+    fixed_mixed.update({"alpha": AM.DEFAULT_ALPHA, "m": 40})
+    n5 = W.unknowns(big)
+    out["metric_c5"] = {"workload": "localvol_8191x8192", "unknowns": n5, "tol": TOL,
+                        "mixed_learned": lrn, "mixed_fixed_alpha": fixed_mixed, "plain_fp64": f64,
+                        "ratio": lrn["value"] / f64["value"],
+                        "ratio_with_setup": lrn["value_with_setup"] / f64["value_with_setup"],
+                        "workspace_bytes": {"learned": n5 * ((m5 + 1) * 8 + m5 * 4),
+                                            "fixed_mixed": n5 * (41 * 8 + 40 * 4), "plain_fp64": n5 * (41 * 8 + 40 * 8)}}
+    mlp.close()
+    return out
 
 
 def run_extras(args, flush, stream, main):
@@ -400,85 +652,7 @@ def run_extras(args, flush, stream, main):
     from paper_2401_16113_gb300 import aao, alpha_mlp as AM, workloads as W
 
     out = {}
-    # batched: 512 put/call instances, Nx in {127..1023}, Nt in {64..1024}, FGMRES(20), tol 1e-8
-    ps = W.batch_instances(512, m=20)
-    bt = aao.aao_batch_create(ps, 20)
-    bs = [torch.empty(k, dtype=torch.float64, device="cuda") for k in bt.sizes]
-    xs = [torch.zeros(k, dtype=torch.float64, device="cuda") for k in bt.sizes]
-    aao.aao_batch_rhs(bt, bs)
-    for _ in range(3):
-        for x in xs:
-            x.zero_()
-        aao.batch_submit(bt, bs, xs, TOL, 300)
-    times, its = [], []
-    for _ in range(max(3, args.steps)):
-        flush.fill_(1.0)
-        for x in xs:
-            x.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        st = aao.batch_submit(bt, bs, xs, TOL, 300)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1))
-        assert all(s_["status"] == 0 for s_ in st)
-        its = [s_["iterations"] for s_ in st]
-    total = float(sum(bt.sizes))
-    ms = sum(times) / len(times)
-    out["batched"] = {"value": total / (ms / 1e3), "unit": "unknowns/s", "instances": len(ps), "unknowns": total,
-                      "ms": ms, "mean_iterations": float(np.mean(its)), "launches_per_step": 1,
-                      "config": "512 BS put/call, sigma U[0.1,0.6], r U[0,0.08], K U[50,150], T U[0.25,2], "
-                                "Nx {127..1023}, Nt {64..1024}, FGMRES(20), graph-replayed persistent launch"}
-    bt.close()
-    del bs, xs
-
-    # learned alpha: train on the batched distribution (labels from the solver's alpha sweep)
-    import time as _time
-    t0 = _time.time()
-    train_ps = W.batch_instances(args.train_instances, seed=W.SEED + 1)
-    h, loss, (a_lab, m_lab, _, _) = AM.train(train_ps, epochs=200, minibatch=512, lr=3e-3, seed=0, tol=TOL,
-                                             maxit=200)
-    t_train = _time.time() - t0
-    big = W.localvol_8191x8192("mixed")
-    a_pred, m_pred = AM.predict(h, big)
-
-    def solve(alpha, m):
-        q = W.with_(big, alpha=alpha)
-        hh = aao.aao_create(q)
-        n = W.unknowns(q)
-        b = torch.empty(n, dtype=torch.float64, device="cuda")
-        aao.aao_rhs(hh, b)
-        x = torch.zeros_like(b)
-        aao.fgmres_solve(hh, b, x, TOL, m, 300)
-        best = None
-        for _ in range(3):
-            x.zero_()
-            flush.fill_(1.0)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            st = aao.fgmres_solve(hh, b, x, TOL, m, 300)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            t = e0.elapsed_time(e1)
-            best = t if best is None else min(best, t)
-        hh.close()
-        return st, best, n
-
-    st_l, ms_l, n = solve(a_pred, m_pred)
-    fell_back = st_l["status"] != 0
-    if fell_back:
-        st_l, ms_l, n = solve(AM.DEFAULT_ALPHA, 40)
-    st_f, ms_f, _ = solve(AM.DEFAULT_ALPHA, 40)
-    out["learned_alpha"] = {
-        "workload": "localvol_8191x8192_mixed", "unknowns": n,
-        "learned": {"alpha": a_pred, "m": m_pred, "iterations": st_l["iterations"], "ms": ms_l,
-                    "value": n / (ms_l / 1e3), "rel_residual": st_l["rel_residual"], "fallback": fell_back,
-                    "workspace_bytes": n * ((m_pred + 1) * 8 + m_pred * 4)},
-        "fixed": {"alpha": AM.DEFAULT_ALPHA, "m": 40, "iterations": st_f["iterations"], "ms": ms_f,
-                  "value": n / (ms_f / 1e3), "workspace_bytes": n * (41 * 8 + 40 * 4)},
-        "training": {"instances": args.train_instances, "seconds": t_train, "final_loss": loss,
-                     "epochs": 200}}
-    h.close()
+    out.update(run_metric_arms(args, flush, stream))
 
     # Riesz fractional operator (beta 1.5), 1023 x 512: dense Toeplitz step (b) by the explicit
     # inverses of the shifted matrices (with drift), and without drift (r = sigma^2/2) by the

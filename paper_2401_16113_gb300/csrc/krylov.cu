@@ -513,7 +513,6 @@ int build_tables(Handle& h) {
   AAO_TRY(up(&h.muf, muf)); AAO_TRY(up(&h.il2f, il2f)); AAO_TRY(up(&h.twf, twf));
   AAO_TRY(up(&h.lam, lam)); AAO_TRY(up(&h.ilam, ilam));
   AAO_TRY(up(&h.lamf, lamf)); AAO_TRY(up(&h.ilamf, ilamf));
-  if (h.tri) AAO_TRY(build_tri_factors(h));
 
   const size_t csz = h.mixed ? sizeof(float2) : sizeof(double2);
   AAO_TRY_CUDA(cudaMalloc(&h.spec, csz * (size_t)K * h.pitch));

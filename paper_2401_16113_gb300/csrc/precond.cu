@@ -26,6 +26,7 @@
 // unnormalised and the single 1/nt is folded into the unscaling table.
 #include <map>
 #include <mutex>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -496,14 +497,29 @@ int build_tri_factors(Handle& h) {
   return h.mixed ? tri_factors_t<float>(h, tp.lgT) : tri_factors_t<double>(h, tp.lgT);
 }
 
+// Tuning results per (device, nx, nt, precision, operator class, flags): a second handle of the
+// same shape skips the timing (and, when the recomputing step (b) won, the factor tables).
+struct TuneKey {
+  int dev, nx, nt, mixed, riesz, flags;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(dev, nx, nt, mixed, riesz, flags) < std::tie(o.dev, o.nx, o.nt, o.mixed, o.riesz, o.flags);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, bool>> g_tune;  // -> (fft_p, tri_rc)
+
 int tune_precond(Handle& h) {
   const size_t rs = h.mixed ? 4 : 8;
-  if (h.p.op != AAO_OP_RIESZ) {
-    // without factor tables (one bin's staged rows do not fit, or the caller asked for it) the
-    // recomputing solver is the one
-    TriRc trc;
-    const bool rc_fits = tri_rc_layout(h, rs, trc);
-    if (h.p.flags == AAO_FLAG_STEPB_FACTORED && !h.tri_fp) {
+  int dev = 0;
+  AAO_TRY_CUDA(cudaGetDevice(&dev));
+  const bool riesz = h.p.op == AAO_OP_RIESZ;
+  const TuneKey key{dev, h.nx, h.nt, h.mixed ? 1 : 0, riesz ? (h.rz_sym ? 2 : 1) : 0, h.p.flags};
+  TriRc trc;
+  TriPart tpart;
+  const bool rc_fits = !riesz && tri_rc_layout(h, rs, trc);
+  const bool fact_fits = !riesz && tri_part_layout(h, rs, tpart);
+  if (!riesz) {
+    if (h.p.flags == AAO_FLAG_STEPB_FACTORED && !fact_fits) {
       set_error("aao_create: the factored step (b) does not fit this nx; use AAO_FLAG_STEPB_RECOMPUTE or 0");
       return AAO_EUNSUPPORTED;
     }
@@ -511,11 +527,31 @@ int tune_precond(Handle& h) {
       set_error("aao_create: the recomputing step (b) does not fit this nx");
       return AAO_EUNSUPPORTED;
     }
-    if (!h.tri_fp && rc_fits) h.tri_rc = true;
   }
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      h.fft_p = it->second.first;
+      h.tri_rc = it->second.second;
+      if (!riesz && !h.tri_rc) return build_tri_factors(h);
+      return AAO_OK;
+    }
+  }
+  if (!riesz) {
+    // the per-bin tables of the factored solver (skipped where they do not fit or are not wanted);
+    // without them the recomputing solver is the one
+    AAO_TRY(build_tri_factors(h));
+    if ((!h.tri_fp && rc_fits) || h.p.flags == AAO_FLAG_STEPB_RECOMPUTE) h.tri_rc = true;
+  }
+  auto remember = [&]() {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = {h.fft_p, h.tri_rc};
+  };
   const int pmax = h.mr.nst > 0 ? mr_max_tile(h.nt, 2 * rs) : max_tile(h.nt, rs);
   if (pmax == 1) {
     h.fft_p = 1;
+    remember();
     return AAO_OK;
   }
   double *v = nullptr, *z = nullptr;
@@ -564,9 +600,7 @@ int tune_precond(Handle& h) {
   h.fft_p = bestp;
   // step (b): the factored partition method against the recomputing one, where both apply; the
   // factor tables are freed when the recomputing solver is kept
-  TriRc trc;
-  const bool rc_ok = h.p.op != AAO_OP_RIESZ && tri_rc_layout(h, rs, trc);
-  if (rc == AAO_OK && rc_ok && h.tri_fp && h.p.flags == 0) {
+  if (rc == AAO_OK && rc_fits && h.tri_fp && h.p.flags == 0) {
     float t_mode[2] = {1e30f, 1e30f};
     for (int mode = 0; mode < 2 && rc == AAO_OK; ++mode) {
       h.tri_rc = mode == 1;
@@ -594,6 +628,7 @@ int tune_precond(Handle& h) {
   cudaEventDestroy(e1);
   cudaFree(v);
   cudaFree(z);
+  if (rc == AAO_OK) remember();
   return rc;
 }
 

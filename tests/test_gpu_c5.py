@@ -1,0 +1,57 @@
+"""Parity at the learned-alpha deployment size: local volatility 8191 x 8192 (67,100,672 unknowns,
+Eq. 2.2 with the time-dependent blocks of Eq. 5.8), solved through the C ABI by the mixed path
+(FP32 preconditioner, FP64 FGMRES(40), relative residual 1e-8) and by the plain FP64 path
+(residual 1e-10), each compared with the oracle's sequential Crank-Nicolson time stepping
+(Eq. 2.1), an independent computation of the same discrete solution: the option values at
+maturity and at sampled time levels."""
+import numpy as np
+import pytest
+
+from oracle import aao_oracle as O
+from paper_2401_16113_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+P = W.localvol_8191x8192("mixed")
+LEVELS = [0, 1, 17, 1000, 4095, 6000, 8190, 8191]
+
+
+@pytest.fixture(scope="module")
+def aao():
+    from paper_2401_16113_gb300 import aao as A, build
+    build.build()
+    A.load()
+    return A
+
+
+@pytest.fixture(scope="module")
+def cn():
+    return O.sequential_cn(P)
+
+
+def solve(aao, p, tol):
+    h = aao.aao_create(p)
+    n = W.unknowns(p)
+    b = torch.empty(n, dtype=torch.float64, device="cuda")
+    aao.aao_rhs(h, b)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    st = aao.fgmres_solve(h, b, x, tol, p["m"], 300)
+    torch.cuda.synchronize()
+    X = x.view(p["nt"], p["nx"])[LEVELS].cpu().numpy()
+    h.close()
+    del b, x
+    torch.cuda.empty_cache()
+    return st, X
+
+
+@pytest.mark.parametrize("precision,tol,gate", [("mixed", 1e-8, 1e-8), ("fp64", 1e-10, 1e-9)])
+def test_localvol_8191x8192_matches_sequential_cn(aao, cn, precision, tol, gate):
+    st, X = solve(aao, W.with_(P, precision=precision), tol)
+    assert st["status"] == 0 and st["rel_residual"] <= tol, st
+    U = cn[LEVELS]
+    scale = np.abs(cn[-1]).max()
+    err = np.abs(X - U).max() / scale
+    print(precision, "its", st["iterations"], "error against sequential CN", err)
+    assert err <= gate, err
+    assert np.abs(X[-1] - U[-1]).max() / scale <= gate

@@ -64,15 +64,26 @@ def test_step_b_variants_match_oracle(aao, nx, nt, precision, step_b):
 LARGE = [(4095, 64, "fp64"), (5000, 32, "fp64"), (8191, 16, "fp64"), (8191, 64, "mixed")]
 
 
+def norm_P_inf(p):
+    """||P_alpha||_inf <= ||C1||_inf + ||C2||_inf ||tau Abar||_inf = 2 + ||tau Abar||_inf (Eq. 3.1;
+    rows of C1 hold 1 and -1 or -alpha, rows of C2 two halves)."""
+    _, tau = O.time_grid(p)
+    A = O.mean_operator(p)
+    return 2.0 + tau * float(np.abs(A).sum(axis=1).max())
+
+
 @pytest.mark.parametrize("nx,nt,precision", LARGE)
 def test_step_b_recompute_large_nx(aao, nx, nt, precision):
-    """Backward error ||v - P_alpha z|| / ||v|| (P_alpha applied blockwise by the oracle): the
-    shifted systems of the largest nx are too ill-conditioned for a forward-error check in FP32."""
+    """Normwise backward error eta = ||v - P_alpha z|| / (||P_alpha|| ||z|| + ||v||) in the max norm
+    (P_alpha applied blockwise by the oracle): the shifted systems of the largest nx are too
+    ill-conditioned for a forward-error check in FP32, and with ||P_alpha|| ~ 1e5 the plain
+    ||v - P z|| / ||v|| of an FP64 solve sits at the rounding of the product P z itself."""
     p = W.with_(LV, nx=nx, nt=nt, precision=precision, step_b="recompute")
     v = W.random_vector(nx * nt, seed=nx + 3 * nt)
     z = apply(aao, p, v)
-    back = rel(O.apply_P(p, z), v)
-    assert back <= bound(p), back
+    r = O.apply_P(p, z) - v
+    eta = np.abs(r).max() / (norm_P_inf(p) * np.abs(z).max() + np.abs(v).max())
+    assert eta <= bound(p), eta
     if precision == "fp64":
         assert rel(z, O.precond_fft(p, v)) <= 1e3 * bound(p)
 
