@@ -3,146 +3,258 @@
 // Q diag(1 / (mu_k - lambda_j)) Q^T for every frequency k once tau Abar = Q diag(lambda) Q^T.
 //
 // Two classical stages (Golub and Van Loan, Matrix Computations, Sec. 8.3):
-//  1. Householder reduction to tridiagonal form, T = Q1^T A Q1, Q1 = H_0 H_1 ... H_{n-3}, each
-//     H_k = I - 2 v v^T / (v^T v) zeroing column k below its subdiagonal;
-//  2. the implicit-shift QL iteration on T (shift from the leading 2 x 2 block of the unreduced
-//     part), the plane rotations accumulated into the rows of Q^T.
+//  1. Householder tridiagonalisation (their Algorithm 8.3.1): T = Q1^T A Q1 with Q1 = H_0 ... H_{n-3},
+//     H_k = I - beta_k v_k v_k^T zeroing column k below the subdiagonal, the trailing block updated
+//     by the symmetric rank-2 form B - v w^T - w v^T;
+//  2. the symmetric QR algorithm (their Algorithms 8.3.2 and 8.3.3): off-diagonal entries below
+//     eps (|a_i| + |a_{i+1}|) are set to zero, and the last unreduced block is reduced by implicit
+//     QR steps with the Wilkinson shift (the eigenvalue of its trailing 2 x 2 block nearer to the
+//     last diagonal entry), each step a chase of the bulge down the block by plane rotations.
+// The QR iteration touches only the tridiagonal (O(n) per step), so it runs first and records its
+// rotations; the eigenvector matrix Q = Q1 G_1 G_2 ... is then formed by applying the reflectors and
+// the recorded rotations to blocks of rows in parallel, each block streaming through the whole list
+// once (rows of Q are independent under both kinds of update). For n = 1023 the 6 n^3 flops of the
+// rotations dominate; they run on all host cores.
 #include <math.h>
 
+#include <algorithm>
+#include <atomic>
+#include <functional>
+#include <thread>
 #include <vector>
 
 #include "aao_internal.cuh"
 
 namespace aao {
+namespace {
 
-bool sym_eig(int n, double* A, double* w) {
-  if (n <= 0) return true;
+// A pool of host threads kept spinning for the duration of one decomposition, so that the ~2n
+// parallel regions of the Householder stage cost a wake-up of a few microseconds each. run(n, f)
+// calls f(begin, end) over [0, n) in contiguous chunks, the caller taking the first.
+class SpinPool {
+ public:
+  explicit SpinPool(int threads) : nthr_(std::max(1, threads)) {
+    for (int t = 1; t < nthr_; ++t) th_.emplace_back([this, t] { worker(t); });
+  }
+  ~SpinPool() {
+    stop_.store(true, std::memory_order_release);
+    for (auto& t : th_) t.join();
+  }
+  int threads() const { return nthr_; }
+  void run(int n, const std::function<void(int, int)>& f) {
+    if (nthr_ == 1 || n < 2 * nthr_) {
+      f(0, n);
+      return;
+    }
+    job_ = &f;
+    n_ = n;
+    done_.store(0, std::memory_order_relaxed);
+    gen_.fetch_add(1, std::memory_order_acq_rel);
+    chunk(0);
+    while (done_.load(std::memory_order_acquire) < nthr_ - 1) std::this_thread::yield();
+  }
+
+ private:
+  void chunk(int t) {
+    const int per = (n_ + nthr_ - 1) / nthr_;
+    const int b = t * per, e = std::min(n_, b + per);
+    if (b < e) (*job_)(b, e);
+  }
+  void worker(int t) {
+    int seen = 0;
+    for (;;) {
+      int g;
+      while ((g = gen_.load(std::memory_order_acquire)) == seen) {
+        if (stop_.load(std::memory_order_acquire)) return;
+        std::this_thread::yield();
+      }
+      seen = g;
+      chunk(t);
+      done_.fetch_add(1, std::memory_order_acq_rel);
+    }
+  }
+  int nthr_;
+  std::vector<std::thread> th_;
+  std::atomic<int> gen_{0}, done_{0};
+  std::atomic<bool> stop_{false};
+  const std::function<void(int, int)>* job_ = nullptr;
+  int n_ = 0;
+};
+
+int host_threads(size_t work) {
+  if (work < (size_t)1 << 16) return 1;  // not worth the threads
+  const unsigned hw = std::thread::hardware_concurrency();
+  return (int)std::max(1u, std::min(hw == 0 ? 1u : hw, 32u));
+}
+
+struct Rotation {
+  int k;        // plane (k, k+1)
+  double c, s;  // columns k, k+1 of Q become c q_k + s q_{k+1} and -s q_k + c q_{k+1}
+};
+
+// Householder stage on A (n x n row-major, overwritten). Returns the diagonal a, the off-diagonal
+// b (b[i] couples i and i+1), the reflectors (v_k of length n-k-1) and their beta_k.
+void tridiagonalise(SpinPool& pool, int n, double* A, std::vector<double>& a, std::vector<double>& b,
+                    std::vector<std::vector<double>>& refl, std::vector<double>& beta) {
   const size_t N = (size_t)n;
-  std::vector<double> d(N), e(N, 0.0);
-  std::vector<std::vector<double>> refl;  // Householder vectors v_k (length n - k - 1)
-  std::vector<double> beta;               // 2 / (v^T v), 0 for an identity step
-  std::vector<double> p(N), q(N);
-  // 1. tridiagonalisation, trailing block updated by the symmetric rank-2 form
-  //    H B H = B - v q^T - q v^T, p = beta B v, q = p - (beta/2)(v^T p) v
+  a.assign(N, 0.0);
+  b.assign(N > 0 ? N - 1 : 0, 0.0);
+  std::vector<double> p(N), w(N);
   for (int k = 0; k + 2 < n; ++k) {
-    const int m = n - k - 1;  // length of the part below the diagonal
-    double* col = A + (size_t)(k + 1) * N + k;  // A[k+1+i][k] at col[i * n]
-    double s2 = 0.0;
-    for (int i = 0; i < m; ++i) s2 += col[(size_t)i * N] * col[(size_t)i * N];
+    const int m = n - k - 1;
+    const size_t o = (size_t)k + 1;
     std::vector<double> v(m);
-    double bk = 0.0;
-    double alpha = col[0];
+    double s2 = 0.0;
+    for (int i = 0; i < m; ++i) {
+      v[i] = A[(o + i) * N + k];
+      s2 += v[i] * v[i];
+    }
+    double sub = v[0], bk = 0.0;
     if (s2 > 0.0) {
-      const double x0 = col[0];
-      alpha = x0 >= 0.0 ? -sqrt(s2) : sqrt(s2);
-      for (int i = 0; i < m; ++i) v[i] = col[(size_t)i * N];
-      v[0] = x0 - alpha;
-      double vn = 0.0;
-      for (int i = 0; i < m; ++i) vn += v[i] * v[i];
-      bk = vn > 0.0 ? 2.0 / vn : 0.0;
+      // reflect x = column k below the diagonal onto -sign(x_0) ||x|| e_0 (no cancellation in v_0)
+      const double nrm = sqrt(s2);
+      sub = v[0] >= 0.0 ? -nrm : nrm;
+      v[0] -= sub;
+      const double vv = s2 - 2.0 * sub * (v[0] + sub) + sub * sub;  // ||x - sub e_0||^2
+      bk = vv > 0.0 ? 2.0 / vv : 0.0;
     }
     if (bk != 0.0) {
-      double* B = A + (size_t)(k + 1) * N + (k + 1);  // B[i][j] at B[i n + j]
-      for (int i = 0; i < m; ++i) {
-        const double* Bi = B + (size_t)i * N;
-        double acc = 0.0;
-        for (int j = 0; j < m; ++j) acc += Bi[j] * v[j];
-        p[i] = bk * acc;
-      }
+      // p = beta B v, w = p - (beta/2)(v^T p) v, B <- B - v w^T - w v^T on the trailing block
+      pool.run(m, [&](int r0, int r1) {
+        for (int i = r0; i < r1; ++i) {
+          const double* Bi = A + (o + i) * N + o;
+          double acc = 0.0;
+          for (int j = 0; j < m; ++j) acc += Bi[j] * v[j];
+          p[i] = bk * acc;
+        }
+      });
       double vp = 0.0;
       for (int i = 0; i < m; ++i) vp += v[i] * p[i];
-      const double kq = 0.5 * bk * vp;
-      for (int i = 0; i < m; ++i) q[i] = p[i] - kq * v[i];
-      for (int i = 0; i < m; ++i) {
-        double* Bi = B + (size_t)i * N;
-        const double vi = v[i], qi = q[i];
-        for (int j = 0; j < m; ++j) Bi[j] -= vi * q[j] + qi * v[j];
-      }
+      const double h = 0.5 * bk * vp;
+      for (int i = 0; i < m; ++i) w[i] = p[i] - h * v[i];
+      pool.run(m, [&](int r0, int r1) {
+        for (int i = r0; i < r1; ++i) {
+          double* Bi = A + (o + i) * N + o;
+          const double vi = v[i], wi = w[i];
+          for (int j = 0; j < m; ++j) Bi[j] -= vi * w[j] + wi * v[j];
+        }
+      });
     }
-    d[k] = A[(size_t)k * N + k];
-    e[k] = alpha;  // T[k+1][k]
+    a[k] = A[(size_t)k * N + k];
+    b[k] = sub;
     refl.push_back(std::move(v));
     beta.push_back(bk);
   }
   if (n >= 2) {
-    d[n - 2] = A[(size_t)(n - 2) * N + (n - 2)];
-    e[n - 2] = A[(size_t)(n - 1) * N + (n - 2)];
+    a[n - 2] = A[(N - 2) * N + (N - 2)];
+    b[n - 2] = A[(N - 1) * N + (N - 2)];
   }
-  d[n - 1] = A[(size_t)(n - 1) * N + (n - 1)];
+  a[n - 1] = A[(N - 1) * N + (N - 1)];
+}
 
-  // Q1 accumulated into A as Q1^T (row r of A = column r of Q1): Q1 = H_0 (H_1 (... H_{n-3})),
-  // applied innermost first; H_k touches indices >= k + 1 only. Row-wise: Q1^T <- Q1^T H_k is
-  // the same update on columns k+1.. of every row.
-  for (size_t i = 0; i < N * N; ++i) A[i] = 0.0;
-  for (int i = 0; i < n; ++i) A[(size_t)i * N + i] = 1.0;
-  for (int k = (int)refl.size() - 1; k >= 0; --k) {
-    if (beta[k] == 0.0) continue;
-    const std::vector<double>& v = refl[k];
-    const int m = (int)v.size(), o = k + 1;
-    // Q1 <- H_k Q1 on rows/cols >= o; in the transposed storage Qt = Q1^T: Qt <- Qt H_k,
-    // rows r >= o of Qt carry the non-identity part (Qt is identity on indices <= k)
-    for (int r = o; r < n; ++r) {
-      double* Qr = A + (size_t)r * N + o;
-      double dot = 0.0;
-      for (int j = 0; j < m; ++j) dot += Qr[j] * v[j];
-      const double f = beta[k] * dot;
-      for (int j = 0; j < m; ++j) Qr[j] -= f * v[j];
-    }
-  }
-  // (A now holds Q1^T: column j of Q1 is row j of A.)
-
-  // 2. implicit-shift QL on (d, e), e[i] = T[i+1][i]; rotations of columns (i, i+1) of the
-  //    eigenvector matrix Q = Q1 G_1 G_2 ... act on rows (i, i+1) of Q^T = A
+// Symmetric QR algorithm on (a, b); the rotations are appended to rot in the order applied.
+// False if some block needs more than 64 QR steps per eigenvalue found.
+bool symmetric_qr(int n, std::vector<double>& a, std::vector<double>& b, std::vector<Rotation>& rot) {
   const double eps = 2.220446049250313e-16;
-  for (int l = 0; l < n; ++l) {
-    int iter = 0;
-    for (;;) {
-      int m = l;
-      for (; m + 1 < n; ++m) {
-        const double dd = fabs(d[m]) + fabs(d[m + 1]);
-        if (fabs(e[m]) <= eps * dd) break;
+  int m = n - 1;  // rows m+1.. are finished (diagonal)
+  int steps = 0;
+  while (m > 0) {
+    // deflation: negligible couplings become zero
+    for (int i = 0; i < m; ++i)
+      if (fabs(b[i]) <= eps * (fabs(a[i]) + fabs(a[i + 1]))) b[i] = 0.0;
+    while (m > 0 && b[m - 1] == 0.0) --m;  // a[m] is an eigenvalue
+    if (m == 0) break;
+    int l = m - 1;
+    while (l > 0 && b[l - 1] != 0.0) --l;  // [l, m] is the last unreduced block
+    if (++steps > 64 * n) return false;
+    // Wilkinson shift: the eigenvalue of [[a_{m-1}, b_{m-1}], [b_{m-1}, a_m]] nearer to a_m
+    const double dlt = 0.5 * (a[m - 1] - a[m]);
+    const double bb = b[m - 1];
+    const double den = dlt + (dlt >= 0.0 ? 1.0 : -1.0) * hypot(dlt, bb);
+    const double mu = a[m] - (den != 0.0 ? bb * bb / den : 0.0);
+    // implicit QR step: the first rotation is fixed by the first column of T - mu I, the later
+    // ones chase the bulge (an entry at (k+1, k-1)) down to the end of the block
+    double x = a[l] - mu, z = b[l];
+    for (int k = l; k < m; ++k) {
+      const double r = hypot(x, z);
+      double c = 1.0, s = 0.0;
+      if (r > 0.0) {
+        c = x / r;
+        s = z / r;
       }
-      if (m == l) break;
-      if (++iter > 64) return false;
-      // Wilkinson-type shift from the 2 x 2 block at l
-      double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-      double r = hypot(g, 1.0);
-      g = d[m] - d[l] + e[l] / (g + (g >= 0.0 ? r : -r));
-      double s = 1.0, c = 1.0, pp = 0.0;
-      int i = m - 1;
-      bool deflated = false;
-      for (; i >= l; --i) {
-        const double f = s * e[i], b = c * e[i];
-        r = hypot(f, g);
-        e[i + 1] = r;
-        if (r == 0.0) {  // underflow: the block splits at i
-          d[i + 1] -= pp;
-          e[m] = 0.0;
-          deflated = true;
-          break;
-        }
-        s = f / r;
-        c = g / r;
-        g = d[i + 1] - pp;
-        r = (d[i] - g) * s + 2.0 * c * b;
-        pp = s * r;
-        d[i + 1] = g + pp;
-        g = c * r - b;
-        double* Qi = A + (size_t)i * N;
-        double* Qj = A + (size_t)(i + 1) * N;
-        for (int k = 0; k < n; ++k) {
-          const double qa = Qi[k], qb = Qj[k];
-          Qj[k] = s * qa + c * qb;
-          Qi[k] = c * qa - s * qb;
-        }
+      if (k > l) b[k - 1] = r;  // the bulge is absorbed
+      // similarity by [[c, s], [-s, c]] on rows and columns (k, k+1)
+      const double ak = a[k], ak1 = a[k + 1], bk = b[k];
+      const double cs = c * s;
+      a[k] = c * c * ak + 2.0 * cs * bk + s * s * ak1;
+      a[k + 1] = s * s * ak - 2.0 * cs * bk + c * c * ak1;
+      b[k] = cs * (ak1 - ak) + (c * c - s * s) * bk;
+      if (k + 1 < m) {
+        z = s * b[k + 1];  // the new bulge at (k+2, k)
+        b[k + 1] *= c;
+        x = b[k];
       }
-      if (deflated) continue;
-      d[l] -= pp;
-      e[l] = g;
-      e[m] = 0.0;
+      rot.push_back({k, c, s});
     }
   }
-  for (int j = 0; j < n; ++j) w[j] = d[j];
+  return true;
+}
+
+}  // namespace
+
+bool sym_eig(int n, double* A, double* w) {
+  if (n <= 0) return true;
+  const size_t N = (size_t)n;
+  SpinPool pool(host_threads(N * N));
+  std::vector<double> a, b, beta;
+  std::vector<std::vector<double>> refl;
+  tridiagonalise(pool, n, A, a, b, refl, beta);
+  std::vector<Rotation> rot;
+  rot.reserve(4 * N * N / 2 + 16);
+  if (!symmetric_qr(n, a, b, rot)) return false;
+
+  // Q = Q1 G_1 G_2 ..., formed row by row: row r of Q1 = e_r^T H_0 ... H_{n-3} (the reflectors in
+  // order; H_k changes entries k+1.. only), then the rotations in order. A block of kRows rows is
+  // held transposed (entry j of the block's row r at j kRows + r), so that each update touches
+  // kRows contiguous values.
+  std::vector<double> Q(N * N);
+  constexpr int kRows = 16;
+  const int blocks = (n + kRows - 1) / kRows;
+  pool.run(blocks, [&](int b0, int b1) {
+    std::vector<double> qb(N * kRows);
+    for (int blk = b0; blk < b1; ++blk) {
+      const int r0 = blk * kRows, nr = std::min(n, r0 + kRows) - r0;
+      std::fill(qb.begin(), qb.end(), 0.0);
+      for (int r = 0; r < nr; ++r) qb[(size_t)(r0 + r) * kRows + r] = 1.0;
+      for (size_t k = 0; k < refl.size(); ++k) {
+        if (beta[k] == 0.0) continue;
+        const double* v = refl[k].data();
+        const int m = (int)refl[k].size();
+        double* q = qb.data() + (k + 1) * kRows;
+        double dot[kRows] = {};
+        for (int j = 0; j < m; ++j)
+          for (int r = 0; r < kRows; ++r) dot[r] += q[(size_t)j * kRows + r] * v[j];
+        for (int r = 0; r < kRows; ++r) dot[r] *= beta[k];
+        for (int j = 0; j < m; ++j)
+          for (int r = 0; r < kRows; ++r) q[(size_t)j * kRows + r] -= dot[r] * v[j];
+      }
+      for (const Rotation& g : rot) {
+        double* x = qb.data() + (size_t)g.k * kRows;
+        double* y = x + kRows;
+        for (int r = 0; r < kRows; ++r) {
+          const double xr = x[r], yr = y[r];
+          x[r] = g.c * xr + g.s * yr;
+          y[r] = g.c * yr - g.s * xr;
+        }
+      }
+      for (int r = 0; r < nr; ++r)
+        for (size_t j = 0; j < N; ++j) Q[(size_t)(r0 + r) * N + j] = qb[j * kRows + r];
+    }
+  });
+  // A <- Q^T (row j = the eigenvector of a[j])
+  for (size_t r = 0; r < N; ++r)
+    for (size_t j = 0; j < N; ++j) A[j * N + r] = Q[r * N + j];
+  for (int j = 0; j < n; ++j) w[j] = a[j];
   return true;
 }
 
