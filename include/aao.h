@@ -68,8 +68,8 @@ extern "C" {
  *  alpha       the free parameter of P_alpha (Eq. 3.1), 0 < alpha < 1 (alpha = 1 allowed:
  *              the classical block-circulant preconditioner P_1)
  *  flags       0, or one AAO_FLAG_STEPB_* to fix how the tridiagonal step (b) is solved (by
- *              default aao_create times both and keeps the faster; both give P_alpha^{-1} v up
- *              to rounding)
+ *              default the factored method where one bin's staged tables fit in shared memory,
+ *              the recomputing one elsewhere; both give P_alpha^{-1} v up to rounding)
  *  stream      cudaStream_t on which all work is issued
  */
 #define AAO_FLAG_STEPB_FACTORED 1  /* partition method with per-bin pivot tables made at create */

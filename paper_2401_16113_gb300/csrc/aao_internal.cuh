@@ -242,7 +242,7 @@ struct Handle {
   // partition method does not fit in shared memory
   void *tri_fp = nullptr, *tri_fv = nullptr, *tri_fpcr = nullptr;
   // step (b) by k_tridiag_rc (pivots recomputed from tri, no per-bin tables) instead of the
-  // factored partition method; chosen at create by timing both where both apply
+  // factored partition method: where the factor tables do not fit, or by request (flags)
   bool tri_rc = false;
 
   // Riesz operator (dense Toeplitz): circulant-embedding spectrum (scaled by tau/2 / N2), its

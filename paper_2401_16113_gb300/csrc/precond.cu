@@ -288,10 +288,12 @@ bool tri_part_layout(const Handle& h, size_t rsize, TriPart& t) {
   return true;
 }
 
-// layout of k_tridiag_rc: lgT, the odd chunk stride cs, bins per CTA G (at most 512 threads, shared
-// memory within one CTA's limit); false when one bin does not fit
+// layout of k_tridiag_rc: lgT, the odd chunk stride cs, bins per CTA G (at most 512 threads), the
+// coefficient planes staged in shared memory (sc) where they fit; per CTA at most 112 KB in FP32
+// (two CTAs per SM) and one CTA's limit in FP64. False when one bin does not fit.
 struct TriRc {
   int lgT, cs, G, CH;
+  bool sc;
   size_t smem;
 };
 bool tri_rc_layout(const Handle& h, size_t rsize, TriRc& t) {
@@ -302,28 +304,41 @@ bool tri_rc_layout(const Handle& h, size_t rsize, TriRc& t) {
   if (t.lgT > kTriMaxLgT) return false;
   t.cs = (ch & 1) ? ch + 2 : ch + 1;
   t.CH = ch <= 4 ? 4 : (ch <= 8 ? 8 : 16);
+  const size_t budget = rsize == 4 ? 112 * 1024 : kTriSmemMax;
   const size_t bin = tri_rc_bin_bytes(T, t.cs, 2 * rsize);
-  if (bin > kTriSmemMax) return false;
-  t.G = 512 / T;
-  if (t.G > 15) t.G = 15;  // named barriers 1..15, one per bin
-  while (t.G > 1 && t.G * bin > kTriSmemMax) --t.G;
-  t.smem = t.G * bin;
-  return true;
+  for (int sc = 1; sc >= 0; --sc) {
+    const size_t cb = sc ? ((3 * (size_t)ch * T * rsize) + 15) & ~(size_t)15 : 0;
+    int G = 512 / T;
+    if (G > 15) G = 15;  // named barriers 1..15, one per bin
+    while (G > 1 && cb + G * bin > budget) --G;
+    if (cb + G * bin <= budget) {
+      t.G = G;
+      t.sc = sc != 0;
+      t.smem = cb + G * bin;
+      return true;
+    }
+  }
+  return false;
 }
 
-template <typename R, int CH>
-int launch_tri_rc_ch(Handle& h, const TriRc& t, C_t<R>* spec, const C_t<R>* mu, const C_t<R>* il2) {
-  AAO_TRY(ensure_smem((const void*)k_tridiag_rc<R, CH>, t.smem));
-  AAO_TRY_CUDA(launch_pdl(k_tridiag_rc<R, CH>, (h.K + t.G - 1) / t.G, t.G << t.lgT, t.smem, h.stream, spec, h.nx,
-                          h.K, h.pitch, h.tri_ch, t.cs, t.lgT, reinterpret_cast<const R*>(h.tri), mu, il2));
+template <typename R, int CH, bool SC>
+int launch_tri_rc_t(Handle& h, const TriRc& t, C_t<R>* spec, const C_t<R>* mu, const C_t<R>* il2) {
+  AAO_TRY(ensure_smem((const void*)k_tridiag_rc<R, CH, SC>, t.smem));
+  AAO_TRY_CUDA(launch_pdl(k_tridiag_rc<R, CH, SC>, (h.K + t.G - 1) / t.G, t.G << t.lgT, t.smem, h.stream, spec,
+                          h.nx, h.K, h.pitch, h.tri_ch, t.cs, t.lgT, reinterpret_cast<const R*>(h.tri), mu, il2));
   return AAO_OK;
 }
 
 template <typename R>
 int launch_tri_rc(Handle& h, const TriRc& t, C_t<R>* spec, const C_t<R>* mu, const C_t<R>* il2) {
-  if (t.CH == 4) return launch_tri_rc_ch<R, 4>(h, t, spec, mu, il2);
-  if (t.CH == 8) return launch_tri_rc_ch<R, 8>(h, t, spec, mu, il2);
-  return launch_tri_rc_ch<R, 16>(h, t, spec, mu, il2);
+  if (t.sc) {
+    if (t.CH == 4) return launch_tri_rc_t<R, 4, true>(h, t, spec, mu, il2);
+    if (t.CH == 8) return launch_tri_rc_t<R, 8, true>(h, t, spec, mu, il2);
+    return launch_tri_rc_t<R, 16, true>(h, t, spec, mu, il2);
+  }
+  if (t.CH == 4) return launch_tri_rc_t<R, 4, false>(h, t, spec, mu, il2);
+  if (t.CH == 8) return launch_tri_rc_t<R, 8, false>(h, t, spec, mu, il2);
+  return launch_tri_rc_t<R, 16, false>(h, t, spec, mu, il2);
 }
 
 template <typename R>
@@ -598,32 +613,6 @@ int tune_precond(Handle& h) {
     if (pbest < best) { best = pbest; bestp = P; }
   }
   h.fft_p = bestp;
-  // step (b): the factored partition method against the recomputing one, where both apply; the
-  // factor tables are freed when the recomputing solver is kept
-  if (rc == AAO_OK && rc_fits && h.tri_fp && h.p.flags == 0) {
-    float t_mode[2] = {1e30f, 1e30f};
-    for (int mode = 0; mode < 2 && rc == AAO_OK; ++mode) {
-      h.tri_rc = mode == 1;
-      rc = launch_precond(h, v, z, h.mixed, nullptr, vf);
-      for (int r = 0; r < 5 && rc == AAO_OK; ++r) {
-        cudaEventRecord(e0, h.stream);
-        rc = launch_precond(h, v, z, h.mixed, nullptr, vf);
-        cudaEventRecord(e1, h.stream);
-        cudaEventSynchronize(e1);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < t_mode[mode]) t_mode[mode] = ms;
-      }
-    }
-    h.tri_rc = t_mode[1] <= t_mode[0];
-    if (h.tri_rc) {
-      cudaStreamSynchronize(h.stream);
-      cudaFree(h.tri_fp);
-      cudaFree(h.tri_fv);
-      cudaFree(h.tri_fpcr);
-      h.tri_fp = h.tri_fv = h.tri_fpcr = nullptr;
-    }
-  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(v);

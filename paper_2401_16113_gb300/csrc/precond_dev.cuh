@@ -929,7 +929,7 @@ __global__ void __launch_bounds__(512) k_tridiag_part(C_t<R>* __restrict__ spec,
 // ------------------------------------------------------------------ step (b) without factor tables
 // k_tridiag_rc: the partition method of k_tridiag_part with nothing stored per bin. Every pivot is
 // recomputed from the three real diagonals of tau*Abar (the chunk-transposed table, shared by all
-// bins and read through L1) and mu_k; ALU work is cheap here, while per-bin tables of pivots and
+// bins) and mu_k; ALU work is cheap here, while per-bin tables of pivots and
 // fill-in tripled the bytes a bin moves and filled shared memory. Thread l of a bin keeps the
 // right-hand sides of its chunk (rows s = l ch .. e = s + ch - 1) in registers; with the row
 // equations a_j x_{j-1} + b_j x_j + c_j x_{j+1} = d_j (b_j = mu_k - dg_j, identity rows beyond nx):
@@ -944,28 +944,32 @@ __global__ void __launch_bounds__(512) k_tridiag_part(C_t<R>* __restrict__ spec,
 //  (A1) and (A2) only read the right-hand sides, so they run interleaved (two independent
 //  dependency chains). Row e of (A2) with x_{e+1} taken from chunk l+1's (G, H, J) is row l of the
 //  T-row reduced system -v_e y_{l-1} + (1 + c'_e H_{l+1}) y_l + c'_e J_{l+1} y_{l+1} =
-//  d'_e - c'_e G_{l+1}, solved by parallel cyclic reduction (double-buffered in shared memory,
-//  one named barrier per level for the bin's T threads);
+//  d'_e - c'_e G_{l+1}, solved by parallel cyclic reduction in shared memory (named barriers of
+//  the bin's T threads);
 //  (B) with y_{l-1} and y_l known: d''_j = (d_j - a_j d''_{j-1}) p_j from d''_{s-1} = y_{l-1},
 //      then x_j = d''_j - c_j p_j x_{j+1} upward from x_e = y_l.
-// G bins per CTA; per bin shared memory: the chunk rows (odd stride cs, conflict-free; the
-// right-hand side on the way in, the pivots, the solution on the way out) and the reduction
-// buffers. The rows are scaled by 1/lambda_{2,k} on the way out (the solve is linear).
+// G bins per CTA. Shared memory: the three coefficient planes [3][ch][T] (staged with cp.async
+// before the kernel waits for its predecessor: they do not depend on it), then per bin the chunk
+// rows (odd stride cs, conflict-free; the right-hand side on the way in, the pivots, the solution
+// on the way out) and one buffer of 4 T complex for the exchanges and the reduction (two named
+// barriers per level). The rows are scaled by 1/lambda_{2,k} on the way out (the solve is linear).
 template <typename C>
 struct RcRow {  // one row of the reduced system
   C a, b, c, d;  // sub-diagonal, diagonal, super-diagonal, right-hand side
 };
-__host__ __device__ __forceinline__ size_t tri_rc_bin_bytes(int T, int cs, size_t csize) {
-  return ((size_t)T * cs + 8 * (size_t)T) * csize;  // chunk rows + two buffers of 4 T
-}
 __device__ __forceinline__ void bin_barrier(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-template <typename R, int CH>
-__global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_tridiag_rc(C_t<R>* __restrict__ spec, int nx, int K, int pitch, int ch,
-                                                    int cs, int lgT, const R* __restrict__ tri,
-                                                    const C_t<R>* __restrict__ mu, const C_t<R>* __restrict__ il2) {
+__host__ __device__ __forceinline__ size_t tri_rc_bin_bytes(int T, int cs, size_t csize) {
+  return ((size_t)T * cs + 4 * (size_t)T) * csize;
+}
+// SC: the coefficient planes staged in shared memory (else read from global memory through L1,
+// where they do not fit beside the bins' rows: FP64 at the largest nx)
+template <typename R, int CH, bool SC>
+__global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1)
+    k_tridiag_rc(C_t<R>* __restrict__ spec, int nx, int K, int pitch, int ch, int cs, int lgT,
+                 const R* __restrict__ tri, const C_t<R>* __restrict__ mu, const C_t<R>* __restrict__ il2) {
   using C = C_t<R>;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int T = 1 << lgT;
@@ -973,15 +977,23 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_tridiag_rc(C_t<
   const int k = blockIdx.x * (blockDim.x >> lgT) + g;
   const bool valid = k < K;
   const int kk = valid ? k : 0;
-  C* W = reinterpret_cast<C*>(smraw + (size_t)g * tri_rc_bin_bytes(T, cs, sizeof(C)));
-  C* buf = W + (size_t)T * cs;  // two buffers of 4 T complex (a, 1/b, c, d)
+  const size_t plane = (size_t)ch * T;
+  R* sco = reinterpret_cast<R*>(smraw);  // [3][ch][T] when SC
+  const size_t cbytes = SC ? ((3 * plane * sizeof(R)) + 15) & ~(size_t)15 : 0;
+  C* W = reinterpret_cast<C*>(smraw + cbytes + (size_t)g * tri_rc_bin_bytes(T, cs, sizeof(C)));
+  C* buf = W + (size_t)T * cs;
   const int bar = 1 + g;
   const C zero = cmk<C>(0, 0), one = cmk<C>(1, 0);
-  const size_t plane = (size_t)ch * T;
+  // the coefficient planes do not depend on the previous kernel: stage them before waiting for it
+  if constexpr (SC) {
+    const int n16 = (int)(3 * plane * sizeof(R) / 16);
+    for (int e = threadIdx.x; e < n16; e += blockDim.x)
+      cp_async<16>(reinterpret_cast<unsigned char*>(sco) + 16 * (size_t)e,
+                   reinterpret_cast<const unsigned char*>(tri) + 16 * (size_t)e);
+  }
   const C muk = __ldg(mu + kk);
   C* row = spec + (size_t)kk * pitch;
   pdl_sync();
-  // the bin's right-hand side into shared memory, coalesced (row i -> chunk i / ch, entry i % ch)
   {
     const int dL = T / ch, dj = T - dL * ch;
     for (int L = l / ch, j = l - (l / ch) * ch; L < T;) {
@@ -992,27 +1004,24 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_tridiag_rc(C_t<
       if (j >= ch) { j -= ch; ++L; }
     }
   }
-  bin_barrier(bar, T);
+  cp_async_wait_all();
+  __syncthreads();
   C d[CH];
   C* Wl = W + l * cs;
 #pragma unroll
   for (int j = 0; j < CH; ++j) d[j] = j < ch ? Wl[j] : zero;
-  const int nrow = nx - l * ch;  // rows of this chunk inside the matrix
-  auto coef = [&](int j, R& a, C& b, R& c) {
-    const size_t o = (size_t)j * T + l;
-    a = __ldg(tri + o);
-    c = __ldg(tri + 2 * plane + o);
-    b = j < nrow ? cmk<C>(muk.x - __ldg(tri + plane + o), muk.y) : one;
-  };
-  // (A1) reverse and (A2) forward sweeps, interleaved
-  C Gs = zero, Hs = zero, Js = one;  // x_s = G + H y_{l-1} + J y_l (ch = 1: x_s = y_l)
+  const int nrow = nx - l * ch;
+  const R* cb = SC ? sco : tri;
+  const R* sa = cb + l;
+  const R* sg = cb + plane + l;
+  const R* sc = cb + 2 * plane + l;
+  C Gs = zero, Hs = zero, Js = one;
   C cpr = zero, dpr = zero, vpr = one;
 #pragma unroll
   for (int u = 0; u < CH; ++u) {
-    if (u < ch) {  // (A2) row u
-      R a, c;
-      C b;
-      coef(u, a, b, c);
+    if (u < ch) {
+      const R a = sa[u * T], c = sc[u * T];
+      const C b = u < nrow ? cmk<C>(muk.x - sg[u * T], muk.y) : one;
       const C p = crcp<R>(cmk<C>(b.x - a * cpr.x, b.y - a * cpr.y));
       cpr = cscale(p, c);
       dpr = cmul(cmk<C>(d[u].x - a * dpr.x, d[u].y - a * dpr.y), p);
@@ -1020,10 +1029,9 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_tridiag_rc(C_t<
       Wl[u] = p;
     }
     const int j = CH - 1 - u;
-    if (j <= ch - 2) {  // (A1) row j
-      R a, c;
-      C b;
-      coef(j, a, b, c);
+    if (j <= ch - 2) {
+      const R a = sa[j * T], c = sc[j * T];
+      const C b = j < nrow ? cmk<C>(muk.x - sg[j * T], muk.y) : one;
       if (j == ch - 2) {
         const C q = crcp<R>(b);
         Gs = cmul(d[j], q);
@@ -1037,46 +1045,40 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_tridiag_rc(C_t<
       }
     }
   }
-  // reduced system: row l needs chunk l+1's (G, H, J)
-  {
-    C* gb = buf + 4 * T;  // the second buffer, free until level 1 of the reduction
-    gb[l] = Gs;
-    gb[T + l] = Hs;
-    gb[2 * T + l] = Js;
-  }
+  buf[l] = Gs;
+  buf[T + l] = Hs;
+  buf[2 * T + l] = Js;
   bin_barrier(bar, T);
   RcRow<C> rr;
   {
-    const C* gb = buf + 4 * T;
     const bool last = l + 1 >= T;
-    const C Gn = last ? zero : gb[l + 1], Hn = last ? zero : gb[T + l + 1], Jn = last ? zero : gb[2 * T + l + 1];
+    const C Gn = last ? zero : buf[l + 1], Hn = last ? zero : buf[T + l + 1], Jn = last ? zero : buf[2 * T + l + 1];
     rr.a = cscale(vpr, (R)-1);
     rr.b = cadd(one, cmul(cpr, Hn));
     rr.c = cmul(cpr, Jn);
     rr.d = csub(dpr, cmul(cpr, Gn));
   }
-  // level s: the neighbours at distance 2^s read this row's a, 1/b, c, d from the buffer
 #pragma unroll 1
   for (int s = 0; s < lgT; ++s) {
-    C* B = buf + (s & 1) * 4 * T;
-    B[l] = rr.a;
-    B[T + l] = crcp<R>(rr.b);
-    B[2 * T + l] = rr.c;
-    B[3 * T + l] = rr.d;
+    bin_barrier(bar, T);  // the previous reads of buf are done
+    buf[l] = rr.a;
+    buf[T + l] = crcp<R>(rr.b);
+    buf[2 * T + l] = rr.c;
+    buf[3 * T + l] = rr.d;
     bin_barrier(bar, T);
     const int delta = 1 << s;
     C anew = zero, cnew = zero, bnew = rr.b, dnew = rr.d;
     if (l - delta >= 0) {
-      const C k1 = cmul(rr.a, B[T + l - delta]);
-      anew = cscale(cmul(B[l - delta], k1), (R)-1);
-      bnew = csub(bnew, cmul(B[2 * T + l - delta], k1));
-      dnew = csub(dnew, cmul(B[3 * T + l - delta], k1));
+      const C k1 = cmul(rr.a, buf[T + l - delta]);
+      anew = cscale(cmul(buf[l - delta], k1), (R)-1);
+      bnew = csub(bnew, cmul(buf[2 * T + l - delta], k1));
+      dnew = csub(dnew, cmul(buf[3 * T + l - delta], k1));
     }
     if (l + delta < T) {
-      const C k2 = cmul(rr.c, B[T + l + delta]);
-      cnew = cscale(cmul(B[2 * T + l + delta], k2), (R)-1);
-      bnew = csub(bnew, cmul(B[l + delta], k2));
-      dnew = csub(dnew, cmul(B[3 * T + l + delta], k2));
+      const C k2 = cmul(rr.c, buf[T + l + delta]);
+      cnew = cscale(cmul(buf[2 * T + l + delta], k2), (R)-1);
+      bnew = csub(bnew, cmul(buf[l + delta], k2));
+      dnew = csub(dnew, cmul(buf[3 * T + l + delta], k2));
     }
     rr.a = anew;
     rr.b = bnew;
@@ -1084,17 +1086,16 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_tridiag_rc(C_t<
     rr.d = dnew;
   }
   const C y = cmul(rr.d, crcp<R>(rr.b));
+  bin_barrier(bar, T);
+  buf[l] = y;
+  bin_barrier(bar, T);
+  const C yp = l > 0 ? buf[l - 1] : zero;
   {
-    C* yb = buf + (lgT & 1) * 4 * T;  // not the buffer read at the last level
-    yb[l] = y;
-    bin_barrier(bar, T);
-    const C yp = l > 0 ? yb[l - 1] : zero;
-    // (B) forward with the stored pivots from d''_{s-1} = y_{l-1}, then back substitution from x_e = y_l
     C dd = yp;
 #pragma unroll
     for (int j = 0; j < CH; ++j) {
       if (j <= ch - 2) {
-        const R a = __ldg(tri + (size_t)j * T + l);
+        const R a = sa[j * T];
         dd = cmul(cmk<C>(d[j].x - a * dd.x, d[j].y - a * dd.y), Wl[j]);
         d[j] = dd;
       }
@@ -1105,10 +1106,7 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1) k_tridiag_rc(C_t<
 #pragma unroll
   for (int j = CH - 1; j >= 0; --j) {
     if (j < ch) {
-      if (j < ch - 1) {
-        const R c = __ldg(tri + 2 * plane + (size_t)j * T + l);
-        x = csub(d[j], cmul(cscale(Wl[j], c), x));
-      }
+      if (j < ch - 1) x = csub(d[j], cmul(cscale(Wl[j], sc[j * T]), x));
       Wl[j] = cmul(x, sk);
     }
   }

@@ -1,6 +1,6 @@
 """Parity at the learned-alpha deployment size: local volatility 8191 x 8192 (67,100,672 unknowns,
 Eq. 2.2 with the time-dependent blocks of Eq. 5.8), solved through the C ABI by the mixed path
-(FP32 preconditioner, FP64 FGMRES(40), relative residual 1e-8) and by the plain FP64 path
+(FP32 preconditioner, FP64 FGMRES(40), relative residual 1e-9) and by the plain FP64 path
 (residual 1e-10), each compared with the oracle's sequential Crank-Nicolson time stepping
 (Eq. 2.1), an independent computation of the same discrete solution: the option values at
 maturity and at sampled time levels."""
@@ -45,7 +45,9 @@ def solve(aao, p, tol):
     return st, X
 
 
-@pytest.mark.parametrize("precision,tol,gate", [("mixed", 1e-8, 1e-8), ("fp64", 1e-10, 1e-9)])
+# The mixed path is solved to 1e-9 for its 1e-8 gate on option values: at this size a relative
+# residual of 5.6e-9 left the maturity values 1.6e-8 from sequential CN.
+@pytest.mark.parametrize("precision,tol,gate", [("mixed", 1e-9, 1e-8), ("fp64", 1e-10, 1e-9)])
 def test_localvol_8191x8192_matches_sequential_cn(aao, cn, precision, tol, gate):
     st, X = solve(aao, W.with_(P, precision=precision), tol)
     assert st["status"] == 0 and st["rel_residual"] <= tol, st
