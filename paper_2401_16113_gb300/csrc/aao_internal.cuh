@@ -251,8 +251,6 @@ struct Handle {
   double2 *rz_chat = nullptr, *rz_tw = nullptr;
   double *rz_hcol = nullptr, *rz_hrow = nullptr, *rz_hcl = nullptr;
   float* Vf = nullptr;  // FP32 copy of the basis vector the next preconditioner apply reads (mixed)
-  float2* rz_lu = nullptr;    // LU factors of the shifted matrices (freed once the inverses are made)
-  float2* rz_dinv = nullptr;  // inverses of the factors' diagonal blocks (L, U per block and bin)
   float2* rz_inv = nullptr;   // the inverses X_k of the shifted matrices, [k][i][j] (with drift)
   // symmetric Riesz operator (no drift): tau Abar = Q diag(lambda) Q^T; step (b) is
   // z2_k = Q diag(D_k) Q^T z1_k with D_k,j = (1/lambda_{2,k}) / (mu_k - lambda_j)

@@ -539,7 +539,7 @@ int build_tables(Handle& h) {
 void free_handle(Handle& h) {
   void* bufs[] = {h.mL, h.mD, h.mU, h.gL, h.gR, h.pL, h.pD, h.pU, h.pLf, h.pDf, h.pUf, h.mu, h.il2, h.tw,
                   h.muf, h.il2f, h.twf, h.lam, h.ilam, h.lamf, h.ilamf, h.spec, h.V, h.Z, h.w, h.scal, h.part,
-                  h.counter, h.rz_chat, h.rz_tw, h.rz_hcol, h.rz_hrow, h.rz_hcl, h.rz_lu, h.rz_dinv, h.tri, h.Vf, h.tri_fp,
+                  h.counter, h.rz_chat, h.rz_tw, h.rz_hcol, h.rz_hrow, h.rz_hcl, h.tri, h.Vf, h.tri_fp,
                   h.tri_fv, h.tri_fpcr, h.rz_dk, h.rz_w,
                   h.rz_part, h.rz_qh, h.rz_ql, h.rz_qth, h.rz_qtl, h.rz_err, h.rz_inv};
   for (void* b : bufs)

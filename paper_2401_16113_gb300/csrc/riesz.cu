@@ -13,13 +13,11 @@
 //                spectrum, inverse FFT (shared-memory Stockham, FP64). Fused with the residual norm
 //                or the first Gram-Schmidt projections, finished by the last block.
 //   k_rz_rhs     b = xi + tau f (xi needs one dense product A u^0).
-//   k_rz_form / k_lu_panel / k_lu_trsm / k_lu_update
+//   k_rz_form / k_gj_pivot / k_gj_rowscale / k_gj_update_tc / k_gj_colfix
 //                at aao_create: the shifted matrices mu_k I - A~ of step (b) of Eq. 3.2 for the
-//                nt/2+1 bins, factored in place by blocked right-looking LU without pivoting
-//                (FP32 complex; the matrices are diagonally dominant, see the design notes).
-//   k_rz_diaginv / k_rz_transpose / k_rz_inv
-//                at aao_create: the explicit inverses X_k = (mu_k I - A~)^{-1} from those factors
-//                (the factors are freed afterwards).
+//                nt/2+1 bins, inverted in place, X_k = (mu_k I - A~)^{-1}, by blocked Gauss-Jordan
+//                elimination without pivoting (FP32 complex; the matrices are diagonally dominant);
+//                the rank-64 updates that carry the work run on the tensor cores (tcgen05, 3xTF32).
 //   k_rz_gemv    per apply: z2_k = X_k z1_k / lambda_2,k for every bin, a dense complex
 //                matrix-vector product that streams the inverses once (HBM-bound).
 //   k_rz_tc      step (b) when the operator is symmetric (no drift): with tau Abar = Q diag(lambda) Q^T
@@ -44,8 +42,6 @@ namespace {
 
 using namespace kdev;
 using namespace pdev;
-
-constexpr int kNB = 32;  // LU / substitution block
 
 // ------------------------------------------------------------------- spectral step (b)
 // C[k][n] = (D[k][n] *) sum_{s < nseg} P[s][k][n] for k < Kb, n < N (N even; pairs of complex
@@ -486,7 +482,7 @@ __global__ void k_rz_rhs(double* __restrict__ b, int nx, int nt, const double* _
   }
 }
 
-// ------------------------------------------------------------------------------- LU at create
+// ------------------------------------------------------------------------------- inverse at create
 // M_k = mu_k I - A~ (row-major, complex FP32), A~ = tau A from its first column / row
 __global__ void k_rz_form(float2* __restrict__ M, int nx, const double* __restrict__ tcol,
                           const double* __restrict__ trow, const float2* __restrict__ mu) {
@@ -501,210 +497,267 @@ __global__ void k_rz_form(float2* __restrict__ M, int nx, const double* __restri
   }
 }
 
-// unblocked LU of the panel rows [kb, n), columns [kb, kb+w): one CTA per bin
-__global__ void __launch_bounds__(256) k_lu_panel(float2* __restrict__ M, int n, int kb, int w) {
-  float2* A = M + (size_t)blockIdx.x * n * n;
-  __shared__ float2 prow[kNB];
-  for (int j = kb; j < kb + w; ++j) {
-    if (threadIdx.x < kb + w - j) prow[threadIdx.x] = A[(size_t)j * n + j + threadIdx.x];
-    __syncthreads();
-    const float2 inv = cinv(prow[0]);
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
-      float2* ri = A + (size_t)i * n;
-      const float2 l = cmul(ri[j], inv);
-      ri[j] = l;
-      for (int c = 1; c < kb + w - j; ++c) ri[j + c] = csub(ri[j + c], cmul(l, prow[c]));
-    }
-    __syncthreads();
-  }
-}
+// The inverses X_k = M_k^{-1} by blocked Gauss-Jordan elimination in place, without pivoting (the
+// shifted matrices are diagonally dominant), over pivot blocks of kGW columns. Round p, block
+// [p0, p0 + wp):
+//   k_gj_pivot     P = (A_pp)^{-1}, a kGW x kGW Gauss-Jordan in shared memory (one CTA per bin);
+//   k_gj_rowscale  A_pj <- P A_pj for the column tiles j outside the block;
+//   k_gj_update_tc A_ij <- A_ij - A_ip A_pj for i, j outside the block: the rank-kGW update that
+//                  carries almost all of the work, on the tensor cores (below);
+//   k_gj_colfix    A_ip <- -A_ip P for the row tiles i outside the block, and A_pp <- P.
+// After the last round A holds M^{-1}. The update reads the block's rows after rowscale and its
+// columns before colfix, and writes neither.
+constexpr int kGW = 64;
 
-// U12 = L11^{-1} A12 for rows [kb, kb+w) and columns [kb+w, n): one thread per column
-__global__ void k_lu_trsm(float2* __restrict__ M, int n, int kb, int w) {
-  float2* A = M + (size_t)blockIdx.y * n * n;
-  const int c = kb + w + blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n) return;
-  float2 col[kNB];
-  for (int i = 0; i < w; ++i) col[i] = A[(size_t)(kb + i) * n + c];
-  for (int i = 1; i < w; ++i) {
-    float2 s = col[i];
-    for (int j = 0; j < i; ++j) s = csub(s, cmul(A[(size_t)(kb + i) * n + kb + j], col[j]));
-    col[i] = s;
-  }
-  for (int i = 1; i < w; ++i) A[(size_t)(kb + i) * n + c] = col[i];
-}
-
-// A22 -= L21 U12, rows and columns [kb+w, n), inner dimension w <= 32: 64 x 64 tiles, 4 x 4 per thread
-__global__ void __launch_bounds__(256) k_lu_update(float2* __restrict__ M, int n, int kb, int w) {
-  float2* A = M + (size_t)blockIdx.z * n * n;
-  const int r0 = kb + w + blockIdx.y * 64, c0 = kb + w + blockIdx.x * 64;
-  __shared__ float2 Ls[64][kNB + 1];
-  __shared__ float2 Us[kNB][64 + 1];
-  for (int e = threadIdx.x; e < 64 * kNB; e += blockDim.x) {
-    const int r = e / kNB, k = e % kNB;
-    Ls[r][k] = (r0 + r < n && k < w) ? A[(size_t)(r0 + r) * n + kb + k] : make_float2(0.f, 0.f);
-    const int kk = e / 64, c = e % 64;
-    Us[kk][c] = (c0 + c < n && kk < w) ? A[(size_t)(kb + kk) * n + c0 + c] : make_float2(0.f, 0.f);
+// one bin per CTA (256 threads); P[k] is kGW x kGW row-major, identity beyond wp
+__global__ void __launch_bounds__(256) k_gj_pivot(const float2* __restrict__ M, int nx, int p0, int wp,
+                                                  float2* __restrict__ P) {
+  __shared__ float2 S[kGW][kGW + 1];
+  __shared__ float2 col[kGW];
+  const int k = blockIdx.x;
+  const float2* A = M + (size_t)k * nx * nx;
+  for (int e = threadIdx.x; e < kGW * kGW; e += blockDim.x) {
+    const int a = e / kGW, b = e % kGW;
+    S[a][b] = (a < wp && b < wp) ? A[(size_t)(p0 + a) * nx + p0 + b] : make_float2(a == b ? 1.f : 0.f, 0.f);
   }
   __syncthreads();
-  const int tr = threadIdx.x / 16, tc = threadIdx.x % 16;
-  float2 acc[4][4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) acc[a][q] = make_float2(0.f, 0.f);
-  for (int k = 0; k < w; ++k) {
-    float2 l[4], u[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) l[a] = Ls[tr + 16 * a][k];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) u[q] = Us[k][tc + 16 * q];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        acc[a][q].x = fmaf(l[a].x, u[q].x, fmaf(-l[a].y, u[q].y, acc[a][q].x));
-        acc[a][q].y = fmaf(l[a].x, u[q].y, fmaf(l[a].y, u[q].x, acc[a][q].y));
-      }
-  }
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int r = r0 + tr + 16 * a, c = c0 + tc + 16 * q;
-      if (r < n && c < n) {
-        float2* p = A + (size_t)r * n + c;
-        *p = csub(*p, acc[a][q]);
-      }
+  for (int c = 0; c < kGW; ++c) {
+    if (threadIdx.x < kGW) col[threadIdx.x] = S[threadIdx.x][c];
+    __syncthreads();
+    const float2 inv = cinv(col[c]);
+    if (threadIdx.x < kGW) {
+      const int j = threadIdx.x;
+      S[c][j] = j == c ? inv : cmul(S[c][j], inv);
     }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kGW * kGW; e += blockDim.x) {
+      const int i = e / kGW, j = e % kGW;
+      if (i == c) continue;
+      S[i][j] = j == c ? cscale(cmul(col[i], inv), -1.f) : csub(S[i][j], cmul(col[i], S[c][j]));
+    }
+    __syncthreads();
+  }
+  float2* Pk = P + (size_t)k * kGW * kGW;
+  for (int e = threadIdx.x; e < kGW * kGW; e += blockDim.x) Pk[e] = S[e / kGW][e % kGW];
 }
 
-// ------------------------------------------------------------------------------- solves per apply
-// Inverses of the diagonal kNB x kNB blocks of every bin's factors (at aao_create): block bi of
-// bin k stores L_bb^{-1} (unit lower) and U_bb^{-1} (upper), row-major, zero beyond the block's
-// width. One warp per triangle: lane c forms column c of the inverse by substitution.
-__global__ void __launch_bounds__(64) k_rz_diaginv(const float2* __restrict__ LU, float2* __restrict__ dinv, int nx,
-                                                   int nb) {
-  __shared__ float2 blk[kNB][kNB + 1];
-  const int bi = blockIdx.x, k = blockIdx.y;
-  const int r0 = bi * kNB, w = min(kNB, nx - r0);
-  const float2* A = LU + (size_t)k * nx * nx;
-  for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x) {
-    const int i = e / kNB, j = e % kNB;
-    blk[i][j] = (i < w && j < w) ? A[(size_t)(r0 + i) * nx + r0 + j] : make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31, tri = threadIdx.x >> 5;  // 0: L, 1: U
-  float2* out = dinv + (((size_t)k * nb + bi) * 2 + tri) * kNB * kNB;
-  float2 x[kNB];
-  if (tri == 0) {
-#pragma unroll
-    for (int i = 0; i < kNB; ++i) {
-      float2 v = make_float2(i == lane ? 1.f : 0.f, 0.f);
-#pragma unroll
-      for (int q = 0; q < i; ++q) v = csub(v, cmul(blk[i][q], x[q]));
-      x[i] = (i < w && lane < w) ? v : make_float2(0.f, 0.f);
-    }
-  } else {
-#pragma unroll
-    for (int i = kNB - 1; i >= 0; --i) {
-      float2 v = make_float2(i == lane ? 1.f : 0.f, 0.f);
-#pragma unroll
-      for (int q = i + 1; q < kNB; ++q) v = csub(v, cmul(blk[i][q], x[q]));
-      x[i] = (i < w && lane < w) ? cmul(v, cinv(blk[i][i])) : make_float2(0.f, 0.f);
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < kNB; ++i) out[i * kNB + lane] = x[i];
-}
-
-// In-place transpose of every bin's nx x nx factor matrix (made once at create, after the
-// diagonal-block inverses): the substitutions of k_rz_inv read the factors column by column.
-__global__ void k_rz_transpose(float2* __restrict__ LU, int nx) {
-  float2* M = LU + (size_t)blockIdx.y * nx * nx;
-  const size_t total = (size_t)nx * nx;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e / nx), j = (int)(e - (size_t)i * nx);
-    if (i < j) {
-      const float2 a = M[e], b = M[(size_t)j * nx + i];
-      M[e] = b;
-      M[(size_t)j * nx + i] = a;
-    }
-  }
-}
-
-// The inverse of each shifted matrix, made once at create from its LU factors (transposed,
-// F[j nx + i] = LU[i][j]) and diagonal-block inverses: X_k = (mu_k I - A~)^{-1}, COLS
-// columns of the identity per CTA (in shared memory, nx x COLS complex; COLS a multiple of 4,
-// 16 where that fits in shared memory, else 8) taken through
-// L Y = E (unit lower) and U X = Y by right-looking blocked substitution over 32-row blocks:
-// solve the block with its stored diagonal-block inverse, then remove its contribution from
-// every remaining row, the factor column read by consecutive threads (coalesced).
-// X is row-major [k][i][j].
-template <int COLS>
-__global__ void __launch_bounds__(512) k_rz_inv(const float2* __restrict__ LUt, const float2* __restrict__ dinv,
-                                                float2* __restrict__ X, int nx, int nb) {
+// A_pj <- P A_pj on column tile blockIdx.x (kGW columns), bin blockIdx.y; the block's own tile is
+// left to k_gj_colfix. Shared memory: P and the tile, 2 kGW^2 complex.
+__global__ void __launch_bounds__(256) k_gj_rowscale(float2* __restrict__ M, int nx, int p0, int wp,
+                                                     const float2* __restrict__ P) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  float2* Z = reinterpret_cast<float2*>(smraw);  // [i][c], nx x COLS
-  float2* t = Z + (size_t)nx * COLS;             // kNB x COLS
-  const int k = blockIdx.y, c0 = blockIdx.x * COLS;
-  const int nc = min(COLS, nx - c0);
-  const float2* F = LUt + (size_t)k * nx * nx;
-  const float2 zero = make_float2(0.f, 0.f);
-  for (int e = threadIdx.x; e < nx * COLS; e += blockDim.x) {
-    const int i = e / COLS, c = e - i * COLS;
-    Z[e] = (c < nc && i == c0 + c) ? make_float2(1.f, 0.f) : zero;
+  const int j0 = blockIdx.x * kGW, k = blockIdx.y;
+  if (j0 == p0) return;
+  float2* Ps = reinterpret_cast<float2*>(smraw);  // [a][b]
+  float2* Ts = Ps + kGW * kGW;                    // [b][jj]
+  float2* A = M + (size_t)k * nx * nx;
+  const float2* Pk = P + (size_t)k * kGW * kGW;
+  for (int e = threadIdx.x; e < kGW * kGW; e += blockDim.x) {
+    Ps[e] = Pk[e];
+    const int b = e / kGW, jj = e % kGW;
+    Ts[e] = (b < wp && j0 + jj < nx) ? A[(size_t)(p0 + b) * nx + j0 + jj] : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  for (int s = 0; s < 2 * nb; ++s) {
-    const bool fwd = s < nb;
-    const int bi = fwd ? s : 2 * nb - 1 - s;
-    const int r0 = bi * kNB, w = min(kNB, nx - r0);
-    const float2* inv = dinv + (((size_t)k * nb + bi) * 2 + (fwd ? 0 : 1)) * kNB * kNB;
-    for (int e = threadIdx.x; e < w * COLS; e += blockDim.x) t[e] = Z[(size_t)r0 * COLS + e];
-    __syncthreads();
-    // the block: Z_b <- Inv t (w x w times w x COLS), one output per thread
-    for (int e = threadIdx.x; e < w * COLS; e += blockDim.x) {
-      const int i = e / COLS, c = e - i * COLS;
-      float2 acc = zero;
-      for (int q = 0; q < w; ++q) {
-        const float2 a = __ldg(inv + i * kNB + q), b = t[q * COLS + c];
-        acc = make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y)));
-      }
-      Z[(size_t)(r0 + i) * COLS + c] = acc;
+  for (int e = threadIdx.x; e < kGW * kGW; e += blockDim.x) {
+    const int a = e / kGW, jj = e % kGW;
+    if (a >= wp || j0 + jj >= nx) continue;
+    float ax = 0.f, ay = 0.f;
+    for (int b = 0; b < wp; ++b) {
+      const float2 p = Ps[a * kGW + b], t = Ts[b * kGW + jj];
+      ax = fmaf(p.x, t.x, fmaf(-p.y, t.y, ax));
+      ay = fmaf(p.x, t.y, fmaf(p.y, t.x, ay));
     }
-    __syncthreads();
-    // the remaining rows: Z_i -= sum_{jj < w} F[(r0 + jj) nx + i] Z_{r0 + jj}, a task = one row and
-    // four columns
-    constexpr int G4 = COLS / 4;
-    const int i0 = fwd ? r0 + w : 0, i1 = fwd ? nx : r0;
-    for (int task = threadIdx.x; task < (i1 - i0) * G4; task += blockDim.x) {
-      const int i = i0 + task / G4, q4 = (task % G4) * 4;
-      float2 acc[4] = {zero, zero, zero, zero};
-      for (int jj = 0; jj < w; ++jj) {
-        const float2 f = __ldg(F + (size_t)(r0 + jj) * nx + i);
-        const float4 za = *reinterpret_cast<const float4*>(Z + (size_t)(r0 + jj) * COLS + q4);
-        const float4 zb = *reinterpret_cast<const float4*>(Z + (size_t)(r0 + jj) * COLS + q4 + 2);
-        const float2 zv[4] = {make_float2(za.x, za.y), make_float2(za.z, za.w), make_float2(zb.x, zb.y),
-                              make_float2(zb.z, zb.w)};
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          acc[c].x = fmaf(f.x, zv[c].x, fmaf(-f.y, zv[c].y, acc[c].x));
-          acc[c].y = fmaf(f.x, zv[c].y, fmaf(f.y, zv[c].x, acc[c].y));
-        }
+    A[(size_t)(p0 + a) * nx + j0 + jj] = make_float2(ax, ay);
+  }
+}
+
+// A_ip <- -A_ip P on row tile blockIdx.x (kGW rows), bin blockIdx.y; the block's own tile becomes P.
+__global__ void __launch_bounds__(256) k_gj_colfix(float2* __restrict__ M, int nx, int p0, int wp,
+                                                   const float2* __restrict__ P) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int i0 = blockIdx.x * kGW, k = blockIdx.y;
+  float2* A = M + (size_t)k * nx * nx;
+  const float2* Pk = P + (size_t)k * kGW * kGW;
+  if (i0 == p0) {
+    for (int e = threadIdx.x; e < kGW * kGW; e += blockDim.x) {
+      const int a = e / kGW, b = e % kGW;
+      if (a < wp && b < wp) A[(size_t)(p0 + a) * nx + p0 + b] = Pk[e];
+    }
+    return;
+  }
+  float2* Ps = reinterpret_cast<float2*>(smraw);  // [a][b]
+  float2* Ts = Ps + kGW * kGW;                    // [ii][a]
+  for (int e = threadIdx.x; e < kGW * kGW; e += blockDim.x) {
+    Ps[e] = Pk[e];
+    const int ii = e / kGW, a = e % kGW;
+    Ts[e] = (i0 + ii < nx && a < wp) ? A[(size_t)(i0 + ii) * nx + p0 + a] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kGW * kGW; e += blockDim.x) {
+    const int ii = e / kGW, b = e % kGW;
+    if (i0 + ii >= nx || b >= wp) continue;
+    float ax = 0.f, ay = 0.f;
+    for (int a = 0; a < wp; ++a) {
+      const float2 t = Ts[ii * kGW + a], p = Ps[a * kGW + b];
+      ax = fmaf(t.x, p.x, fmaf(-t.y, p.y, ax));
+      ay = fmaf(t.x, p.y, fmaf(t.y, p.x, ay));
+    }
+    A[(size_t)(i0 + ii) * nx + p0 + b] = make_float2(-ax, -ay);
+  }
+}
+
+// The rank-kGW update A_ij -= sum_q A_iq A_qj (q in the pivot block) on the tensor cores. A CTA
+// owns 128 rows (i0 ..) and kGjNT column tiles of 32 complex columns (j0 ..); per column tile one
+// accumulation D (128 x 64 FP32 in TMEM) = A' B'^T with the complex product embedded in a real one
+// along the contraction index kappa = 2q + s:
+//   A'[r][2q] = Re A_iq, A'[r][2q+1] = Im A_iq;
+//   B'[2j][2q] = Re B_qj, B'[2j][2q+1] = -Im B_qj, B'[2j+1][2q] = Im B_qj, B'[2j+1][2q+1] = Re B_qj,
+// so that D[r][2j] + i D[r][2j+1] = sum_q A_iq B_qj. Each operand is split into a TF32 head and
+// tail and three products are accumulated (3xTF32, FP32 accuracy), with the operand layout, the
+// descriptors and the instruction descriptor of k_rz_tc (K-major, no swizzle, 8-row x 16-byte core
+// matrices; M = 128, N = 64, K = 8 per MMA): four 32-entry chunks of kappa per operand. Threads
+// stage float4 = one 16-byte core-matrix row, eight consecutive rows per quarter warp (conflict-free).
+// Rows and columns inside the pivot block, and beyond nx, are not written. The wait for the MMAs
+// is bounded by wait_ns; on a timeout the CTA sets *err, waits (bounded) once more so that no MMA is
+// pending, frees TMEM and returns without writing.
+constexpr int kGjNT = 4;
+constexpr uint32_t kGjA = 4 * 16384u, kGjB = 4 * 8192u;  // one operand (hi or lo), bytes
+constexpr uint32_t kGjSmem = 2 * kGjA + 2 * kGjB + 64 + 1024;
+__global__ void __launch_bounds__(128, 1) k_gj_update_tc(float2* __restrict__ M, int nx, int p0, int wp,
+                                                          int* __restrict__ err, unsigned long long wait_ns) {
+  using namespace tcg;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int k = blockIdx.z, i0 = blockIdx.y * 128, jbase = blockIdx.x * 32 * kGjNT;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  float2* A = M + (size_t)k * nx * nx;
+  const int pe = p0 + wp;
+  // nothing to write: all rows in the pivot block (cannot happen for 128 rows) or all columns in it
+  if (jbase >= p0 && jbase + 32 * kGjNT <= pe) return;
+  const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(smraw);
+  const uint32_t base = (s0 + 1023u) & ~1023u;
+  unsigned char* gbase = smraw + (base - s0);
+  const uint32_t aHi = base, aLo = base + kGjA, bHi = base + 2 * kGjA, bLo = bHi + kGjB;
+  const uint32_t mbar = base + 2 * kGjA + 2 * kGjB, slot = mbar + 8;
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(kN) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  // A' (rows i0.., the block's columns): float4 e = (row r, q pair qp) at chunk qp >> 3
+  for (int it = 0; it < 32; ++it) {
+    const int e = it * 128 + tid;
+    const int r = ((e >> 8) << 3) | (e & 7), qp = (e >> 3) & 31;
+    const int i = i0 + r, q = 2 * qp;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i < nx) {
+      const float2* src = A + (size_t)i * nx + p0 + q;
+      if (q < wp) { const float2 t = src[0]; v.x = t.x; v.y = t.y; }
+      if (q + 1 < wp) { const float2 t = src[1]; v.z = t.x; v.w = t.y; }
+    }
+    const uint32_t off = (uint32_t)((qp >> 3) * 16384 + (((r >> 3) << 3) + (qp & 7)) * 128 + (r & 7) * 16);
+    const float4 hi = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
+    const float4 lo = make_float4(tf32_rna(v.x - hi.x), tf32_rna(v.y - hi.y), tf32_rna(v.z - hi.z),
+                                  tf32_rna(v.w - hi.w));
+    *reinterpret_cast<float4*>(gbase + off) = hi;
+    *reinterpret_cast<float4*>(gbase + kGjA + off) = lo;
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(gbase + 2 * kGjA + 2 * kGjB + 8);
+  bool ok = true;
+  int phase = 0;  // commits issued so far: the mbarrier phase of the next one
+  for (int nt = 0; nt < kGjNT && ok; ++nt) {
+    const int j0 = jbase + 32 * nt;
+    if (j0 >= nx) break;
+    if (j0 >= p0 && j0 + 32 <= pe) continue;  // every column of this tile is in the block
+    // B' (the block's rows, columns j0..j0+31): float4 e = (row n = 2 j + t, q pair qp)
+    for (int it = 0; it < 16; ++it) {
+      const int e = it * 128 + tid;
+      const int n = ((e >> 8) << 3) | (e & 7), qp = (e >> 3) & 31;
+      const int j = j0 + (n >> 1), t = n & 1, q = 2 * qp;
+      float2 b0 = make_float2(0.f, 0.f), b1 = make_float2(0.f, 0.f);
+      if (j < nx) {
+        if (q < wp) b0 = A[(size_t)(p0 + q) * nx + j];
+        if (q + 1 < wp) b1 = A[(size_t)(p0 + q + 1) * nx + j];
       }
+      const float4 v = t == 0 ? make_float4(b0.x, -b0.y, b1.x, -b1.y) : make_float4(b0.y, b0.x, b1.y, b1.x);
+      const uint32_t off = (uint32_t)((qp >> 3) * 8192 + (((n >> 3) << 3) + (qp & 7)) * 128 + (n & 7) * 16);
+      const float4 hi = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
+      const float4 lo = make_float4(tf32_rna(v.x - hi.x), tf32_rna(v.y - hi.y), tf32_rna(v.z - hi.z),
+                                    tf32_rna(v.w - hi.w));
+      *reinterpret_cast<float4*>(gbase + 2 * kGjA + off) = hi;
+      *reinterpret_cast<float4*>(gbase + 2 * kGjA + kGjB + off) = lo;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        float2& zi = Z[(size_t)i * COLS + q4 + c];
-        zi = make_float2(zi.x - acc[c].x, zi.y - acc[c].y);
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks) {
+          const uint32_t ko = ks * 256;
+          const uint64_t ah = sdesc(aHi + c * 16384 + ko), al = sdesc(aLo + c * 16384 + ko);
+          const uint64_t bh = sdesc(bHi + c * 8192 + ko), bl = sdesc(bLo + c * 8192 + ko);
+          mma(tmem, ah, bh, (c > 0 || ks > 0) ? 1u : 0u);
+          mma(tmem, ah, bl, 1u);
+          mma(tmem, al, bh, 1u);
+        }
       }
+      commit(mbar);
+    }
+    // the MMAs of this tile are done (thread 0 waits; the outcome is shared at the barrier)
+    __shared__ int done_s;
+    if (tid == 0) {
+      const bool d = wait_parity(mbar, (uint32_t)(phase & 1), wait_ns);
+      if (!d) {
+        atomicExch(err, 1);
+        (void)wait_parity(mbar, (uint32_t)(phase & 1), wait_ns);  // drain before TMEM is freed
+      }
+      done_s = d ? 1 : 0;
     }
     __syncthreads();
+    ++phase;
+    ok = done_s != 0;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!ok) break;
+    // epilogue: warp w holds TMEM lanes 32 w .. (rows i0 + 32 w + lane), 64 columns
+    const int i = i0 + 32 * warp + lane;
+    const bool row_ok = i < nx && (i < p0 || i >= pe);
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      uint32_t v[32];
+      const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + 32 * half;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+          "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+            "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+            "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (row_ok) {
+        float2* dst = A + (size_t)i * nx;
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) {
+          const int j = j0 + 16 * half + jj;
+          if (j < nx && (j < p0 || j >= pe)) {
+            const float2 c = dst[j];
+            dst[j] = make_float2(c.x - __uint_as_float(v[2 * jj]), c.y - __uint_as_float(v[2 * jj + 1]));
+          }
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();  // TMEM read and B' consumed before the next tile's staging and MMAs
   }
-  for (int e = threadIdx.x; e < nx * COLS; e += blockDim.x) {
-    const int i = e / COLS, c = e - i * COLS;
-    if (c < nc) X[((size_t)k * nx + i) * nx + c0 + c] = Z[e];
-  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kN) : "memory");
 }
 
 // Step (b) per apply for the Riesz operator with drift: z_k = X_k (z1_k / lambda_2,k) for every
@@ -966,48 +1019,45 @@ int riesz_build(Handle& h) {
     cudaFree(d_trow);
     return AAO_OK;
   }
-  // shifted matrices and their LU factors (FP32 complex)
-  AAO_TRY_CUDA(cudaMalloc(&h.rz_lu, sizeof(float2) * nn * K));
-  k_rz_form<<<dim3(256, K), 256, 0, h.stream>>>(h.rz_lu, nx, d_tcol, d_trow, h.muf);
+  // the shifted matrices, inverted in place by blocked Gauss-Jordan (FP32 complex; the rank-kGW
+  // updates on the tensor cores): an apply is then one matrix-vector product per bin
+  AAO_TRY_CUDA(cudaMalloc(&h.rz_inv, sizeof(float2) * nn * K));
+  k_rz_form<<<dim3(256, K), 256, 0, h.stream>>>(h.rz_inv, nx, d_tcol, d_trow, h.muf);
   AAO_CHECK_LAUNCH();
-  for (int kb = 0; kb < nx; kb += kNB) {
-    const int w = nx - kb < kNB ? nx - kb : kNB;
-    k_lu_panel<<<K, 256, 0, h.stream>>>(h.rz_lu, nx, kb, w);
-    AAO_CHECK_LAUNCH();
-    const int rest = nx - kb - w;
-    if (rest > 0) {
-      k_lu_trsm<<<dim3((rest + 127) / 128, K), 128, 0, h.stream>>>(h.rz_lu, nx, kb, w);
-      AAO_CHECK_LAUNCH();
-      k_lu_update<<<dim3((rest + 63) / 64, (rest + 63) / 64, K), 256, 0, h.stream>>>(h.rz_lu, nx, kb, w);
-      AAO_CHECK_LAUNCH();
-    }
-  }
   {
-    const int nb = (nx + kNB - 1) / kNB;
-    AAO_TRY_CUDA(cudaMalloc(&h.rz_dinv, sizeof(float2) * (size_t)K * nb * 2 * kNB * kNB));
-    k_rz_diaginv<<<dim3(nb, K), 64, 0, h.stream>>>(h.rz_lu, h.rz_dinv, nx, nb);
-    AAO_CHECK_LAUNCH();
-    // the substitutions read the factors transposed (column j contiguous)
-    k_rz_transpose<<<dim3(256, K), 256, 0, h.stream>>>(h.rz_lu, nx);
-    AAO_CHECK_LAUNCH();
-    // the inverses X_k (an apply is then one matrix-vector product per bin); the factors and the
-    // block inverses are released afterwards
-    AAO_TRY_CUDA(cudaMalloc(&h.rz_inv, sizeof(float2) * nn * K));
-    // 16 identity columns per CTA where they fit in shared memory (nx <= 1784), else 8
-    auto inv_smem = [&](int cols) { return sizeof(float2) * ((size_t)nx + kNB) * cols; };
-    if (inv_smem(16) <= 227 * 1024) {
-      AAO_TRY_CUDA(cudaFuncSetAttribute(k_rz_inv<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inv_smem(16)));
-      k_rz_inv<16><<<dim3((nx + 15) / 16, K), 512, inv_smem(16), h.stream>>>(h.rz_lu, h.rz_dinv, h.rz_inv, nx, nb);
-    } else {
-      AAO_TRY_CUDA(cudaFuncSetAttribute(k_rz_inv<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inv_smem(8)));
-      k_rz_inv<8><<<dim3((nx + 7) / 8, K), 512, inv_smem(8), h.stream>>>(h.rz_lu, h.rz_dinv, h.rz_inv, nx, nb);
+    float2* piv = nullptr;
+    int* err = nullptr;
+    AAO_TRY_CUDA(cudaMalloc(&piv, sizeof(float2) * (size_t)K * kGW * kGW));
+    AAO_TRY_CUDA(cudaMalloc(&err, sizeof(int)));
+    AAO_TRY_CUDA(cudaMemsetAsync(err, 0, sizeof(int), h.stream));
+    const size_t tsm = 2 * sizeof(float2) * kGW * kGW;
+    AAO_TRY_CUDA(cudaFuncSetAttribute(k_gj_rowscale, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
+    AAO_TRY_CUDA(cudaFuncSetAttribute(k_gj_colfix, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
+    AAO_TRY_CUDA(cudaFuncSetAttribute(k_gj_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGjSmem));
+    const int nbt = (nx + kGW - 1) / kGW;
+    const dim3 gup((nx + 32 * kGjNT - 1) / (32 * kGjNT), (nx + 127) / 128, K);
+    int rc = AAO_OK;
+    for (int p0 = 0; p0 < nx && rc == AAO_OK; p0 += kGW) {
+      const int wp = nx - p0 < kGW ? nx - p0 : kGW;
+      k_gj_pivot<<<K, 256, 0, h.stream>>>(h.rz_inv, nx, p0, wp, piv);
+      k_gj_rowscale<<<dim3(nbt, K), 256, tsm, h.stream>>>(h.rz_inv, nx, p0, wp, piv);
+      k_gj_update_tc<<<gup, 128, kGjSmem, h.stream>>>(h.rz_inv, nx, p0, wp, err, tcg::kWaitNs);
+      k_gj_colfix<<<dim3(nbt, K), 256, tsm, h.stream>>>(h.rz_inv, nx, p0, wp, piv);
+      g_launches.fetch_add(3, std::memory_order_relaxed);
+      rc = [&]() -> int { AAO_CHECK_LAUNCH(); return AAO_OK; }();
     }
-    AAO_CHECK_LAUNCH();
-    AAO_TRY_CUDA(cudaStreamSynchronize(h.stream));
-    cudaFree(h.rz_lu);
-    cudaFree(h.rz_dinv);
-    h.rz_lu = nullptr;
-    h.rz_dinv = nullptr;
+    int e = 0;
+    if (rc == AAO_OK) {
+      AAO_TRY_CUDA(cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, h.stream));
+      AAO_TRY_CUDA(cudaStreamSynchronize(h.stream));
+    }
+    cudaFree(piv);
+    cudaFree(err);
+    if (rc != AAO_OK) return rc;
+    if (e) {
+      set_error("aao_create: a tensor-core update of the Riesz inverses gave up a bounded wait");
+      return AAO_TIMEOUT;
+    }
     AAO_TRY_CUDA(cudaMalloc(&h.rz_w, sizeof(float2) * (size_t)K * h.pitch));
     AAO_TRY_CUDA(cudaMemsetAsync(h.rz_w, 0, sizeof(float2) * (size_t)K * h.pitch, h.stream));
   }
