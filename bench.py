@@ -134,19 +134,26 @@ def ncu_traffic(kernel_class):
     return e.get("dram_bytes_per_launch")
 
 
-def precond_roofline(prof, hbm_peak):
-    """The preconditioner apply (its three kernel classes) as one unit: algorithmic bytes per
-    apply (the kernels' argument sizes: the FP32 input, the half spectrum in and out of each
-    exchange, the tridiagonal factors, the FP32 output) over its device time per apply."""
+def precond_roofline(prof, hbm_peak, unknowns):
+    """The preconditioner apply (its three kernel classes) as one unit, counted by the survey's
+    algorithmic bytes: 16 B per unknown (v read and z written once in FP64), over its device time
+    per apply inside the solve. Beside it: the same time against the bytes the solve's applies
+    actually move at their ends (FP32 copy of v in, FP32 z out: 8 B per unknown) and against the
+    kernels' argument sizes (both exchanges of the half spectrum and any per-bin factor tables
+    included), which the half spectrum's L2 residency makes an upper bound on DRAM traffic."""
     cls = ("fft_fwd", "tridiag", "fft_inv")
     applies = prof["fft_fwd"][0]
     if not applies:
         return None
     ms = sum(prof[c][1] for c in cls) / applies
-    by = sum(prof[c][2] for c in cls) / applies
+    args = sum(prof[c][2] for c in cls) / applies
+    by = 16.0 * unknowns
     gbs = by / (ms / 1e3) / 1e9
-    return {"ms_per_apply": ms, "algorithmic_bytes_per_apply": by, "achieved": gbs, "unit": "GB/s",
-            "peak": hbm_peak, "frac": gbs / hbm_peak, "bound": "latency and issue (half spectrum L2-resident)",
+    return {"ms_per_apply": ms, "algorithmic_bytes_per_apply": by, "bytes_per_unknown": 16,
+            "achieved": gbs, "unit": "GB/s", "peak": hbm_peak, "frac": gbs / hbm_peak,
+            "in_solve_io_gbs": 8.0 * unknowns / (ms / 1e3) / 1e9,
+            "argument_bytes_per_apply": args, "argument_gbs": args / (ms / 1e3) / 1e9,
+            "bound": "latency and issue (the half spectrum stays in L2 between the three kernels)",
             "applies": applies}
 
 
@@ -419,7 +426,7 @@ def run_ours(args):
             "clocks": clk.summary(),
             "roofline": roof,
             "kernel_ms_per_solve": {c: prof[c][1] for c in prof},
-            "precond_apply": precond_roofline(prof, hbm_peak),
+            "precond_apply": precond_roofline(prof, hbm_peak, n),
             "fp64_plain": {"value": fp64_value, "unit": "unknowns/s", "ms": min(ms64),
                            "iterations": st64["iterations"]},
             "precond_setup": {"ms": setup_s * 1e3, "what": "aao_create of the timed workload: coefficient and "

@@ -244,16 +244,19 @@ __global__ void __launch_bounds__(160, 1) k_rz_tc(const float2* __restrict__ A, 
     }
     __syncwarp();  // the producer lane rejoins its warp before the final barrier
   } else {
-    // spectrum piece i of this thread: core matrix cm = (row group: bins 4 (cm >> 3) ..,
-    // K group cm & 7), thread t8 loads 2 complex of bin 4 (cm >> 3) + (t8 & 3) at K entries
-    // 4 (cm & 7) + 2 (t8 >> 2) + {0, 1} and writes its re row and im row
+    // spectrum piece i of this thread: core matrix cm = e >> 3 (row group: bins 4 (cm >> 3) ..,
+    // K group cm & 7), lane pair (b, t) = ((e & 7) >> 1, e & 1) of bin 4 (cm >> 3) + b. Lane t loads
+    // the complex at K entries 4 (cm & 7) + 2 t + {0, 1}; the pair swaps halves with a shuffle, so
+    // that each lane holds the bin's four entries and writes one whole 16-byte core-matrix row,
+    // row 2 b + t (re for t = 0, im for t = 1) and then row 2 b + 1 - t: eight lanes fill one
+    // 128-byte core matrix per store (no bank conflicts)
     float4 zv[4];
     auto fetch_z = [&](int m0) {
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        const int e = tid + 128 * i, cm = e >> 3, t8 = e & 7;
-        const int bin = b0 + 4 * (cm >> 3) + (t8 & 3), q = 2 * (cm & 7) + (t8 >> 2);
-        zv[i] = bin < Kb ? __ldg(reinterpret_cast<const float4*>(A + (size_t)bin * lda + m0 + 2 * q))
+        const int e = tid + 128 * i, cm = e >> 3, l8 = e & 7;
+        const int bin = b0 + 4 * (cm >> 3) + (l8 >> 1), x = 4 * (cm & 7) + 2 * (l8 & 1);
+        zv[i] = bin < Kb ? __ldg(reinterpret_cast<const float4*>(A + (size_t)bin * lda + m0 + x))
                          : make_float4(0.f, 0.f, 0.f, 0.f);
       }
     };
@@ -281,15 +284,21 @@ __global__ void __launch_bounds__(160, 1) k_rz_tc(const float2* __restrict__ A, 
       unsigned char* bl = bh + kBop;
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        const int e = tid + 128 * i, cm = e >> 3, t8 = e & 7;
-        const uint32_t off = (uint32_t)(cm * 128 + (2 * (t8 & 3)) * 16 + (t8 >> 2) * 8);
-        const float hr0 = tf32_rna(v[i].x), hi0 = tf32_rna(v[i].y), hr1 = tf32_rna(v[i].z), hi1 = tf32_rna(v[i].w);
-        const float lr0 = tf32_rna(v[i].x - hr0), li0 = tf32_rna(v[i].y - hi0), lr1 = tf32_rna(v[i].z - hr1),
-                    li1 = tf32_rna(v[i].w - hi1);
-        *reinterpret_cast<float2*>(bh + off) = make_float2(hr0, hr1);
-        *reinterpret_cast<float2*>(bh + off + 16) = make_float2(hi0, hi1);
-        *reinterpret_cast<float2*>(bl + off) = make_float2(lr0, lr1);
-        *reinterpret_cast<float2*>(bl + off + 16) = make_float2(li0, li1);
+        const int e = tid + 128 * i, cm = e >> 3, l8 = e & 7, b = l8 >> 1, t = l8 & 1;
+        const float4 u = make_float4(__shfl_xor_sync(0xffffffffu, v[i].x, 1), __shfl_xor_sync(0xffffffffu, v[i].y, 1),
+                                     __shfl_xor_sync(0xffffffffu, v[i].z, 1), __shfl_xor_sync(0xffffffffu, v[i].w, 1));
+        const float4 lo2 = t ? u : v[i], hi2 = t ? v[i] : u;  // K entries 0, 1 and 2, 3 of the group
+        const float4 re = make_float4(lo2.x, lo2.z, hi2.x, hi2.z), im = make_float4(lo2.y, lo2.w, hi2.y, hi2.w);
+        const float4 first = t ? im : re, second = t ? re : im;
+        const uint32_t off1 = (uint32_t)(cm * 128 + (2 * b + t) * 16), off2 = (uint32_t)(cm * 128 + (2 * b + 1 - t) * 16);
+        const float4 h1 = make_float4(tf32_rna(first.x), tf32_rna(first.y), tf32_rna(first.z), tf32_rna(first.w));
+        const float4 h2 = make_float4(tf32_rna(second.x), tf32_rna(second.y), tf32_rna(second.z), tf32_rna(second.w));
+        *reinterpret_cast<float4*>(bh + off1) = h1;
+        *reinterpret_cast<float4*>(bh + off2) = h2;
+        *reinterpret_cast<float4*>(bl + off1) = make_float4(tf32_rna(first.x - h1.x), tf32_rna(first.y - h1.y),
+                                                            tf32_rna(first.z - h1.z), tf32_rna(first.w - h1.w));
+        *reinterpret_cast<float4*>(bl + off2) = make_float4(tf32_rna(second.x - h2.x), tf32_rna(second.y - h2.y),
+                                                            tf32_rna(second.z - h2.z), tf32_rna(second.w - h2.w));
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       // the operator tiles have landed (thread 0 waits; the outcome is shared at the barrier)
@@ -615,16 +624,18 @@ __global__ void __launch_bounds__(256) k_gj_colfix(float2* __restrict__ M, int n
 // so that D[r][2j] + i D[r][2j+1] = sum_q A_iq B_qj. Each operand is split into a TF32 head and
 // tail and three products are accumulated (3xTF32, FP32 accuracy), with the operand layout, the
 // descriptors and the instruction descriptor of k_rz_tc (K-major, no swizzle, 8-row x 16-byte core
-// matrices; M = 128, N = 64, K = 8 per MMA): four 32-entry chunks of kappa per operand. Threads
-// stage float4 = one 16-byte core-matrix row, eight consecutive rows per quarter warp (conflict-free).
+// matrices; M = 128, N = 64, K = 8 per MMA): four 32-entry chunks of kappa per operand. 256 threads
+// stage float4 = one 16-byte core-matrix row, eight consecutive rows per quarter warp (conflict-free);
+// thread 0 issues the MMAs; the eight warps read the accumulator back by lane quadrant and half.
 // Rows and columns inside the pivot block, and beyond nx, are not written. The wait for the MMAs
 // is bounded by wait_ns; on a timeout the CTA sets *err, waits (bounded) once more so that no MMA is
 // pending, frees TMEM and returns without writing.
 constexpr int kGjNT = 4;
 constexpr uint32_t kGjA = 4 * 16384u, kGjB = 4 * 8192u;  // one operand (hi or lo), bytes
 constexpr uint32_t kGjSmem = 2 * kGjA + 2 * kGjB + 64 + 1024;
-__global__ void __launch_bounds__(128, 1) k_gj_update_tc(float2* __restrict__ M, int nx, int p0, int wp,
-                                                          int* __restrict__ err, unsigned long long wait_ns) {
+constexpr int kGjThreads = 256;
+__global__ void __launch_bounds__(kGjThreads, 1) k_gj_update_tc(float2* __restrict__ M, int nx, int p0, int wp,
+                                                                int* __restrict__ err, unsigned long long wait_ns) {
   using namespace tcg;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int k = blockIdx.z, i0 = blockIdx.y * 128, jbase = blockIdx.x * 32 * kGjNT;
@@ -646,23 +657,34 @@ __global__ void __launch_bounds__(128, 1) k_gj_update_tc(float2* __restrict__ M,
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(kN) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  // A' (rows i0.., the block's columns): float4 e = (row r, q pair qp) at chunk qp >> 3
-  for (int it = 0; it < 32; ++it) {
-    const int e = it * 128 + tid;
-    const int r = ((e >> 8) << 3) | (e & 7), qp = (e >> 3) & 31;
-    const int i = i0 + r, q = 2 * qp;
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (i < nx) {
-      const float2* src = A + (size_t)i * nx + p0 + q;
-      if (q < wp) { const float2 t = src[0]; v.x = t.x; v.y = t.y; }
-      if (q + 1 < wp) { const float2 t = src[1]; v.z = t.x; v.w = t.y; }
+  // A' (rows i0.., the block's columns): float4 e = (row r, q pair qp) at chunk qp >> 3; the loads of
+  // four pieces are issued before any of them is converted
+  constexpr int kBatch = 4;
+  for (int it0 = 0; it0 < 4096 / kGjThreads; it0 += kBatch) {
+    float4 v[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int e = (it0 + u) * kGjThreads + tid;
+      const int r = ((e >> 8) << 3) | (e & 7), qp = (e >> 3) & 31;
+      const int i = i0 + r, q = 2 * qp;
+      v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (i < nx) {
+        const float2* src = A + (size_t)i * nx + p0 + q;
+        if (q < wp) { const float2 t = src[0]; v[u].x = t.x; v[u].y = t.y; }
+        if (q + 1 < wp) { const float2 t = src[1]; v[u].z = t.x; v[u].w = t.y; }
+      }
     }
-    const uint32_t off = (uint32_t)((qp >> 3) * 16384 + (((r >> 3) << 3) + (qp & 7)) * 128 + (r & 7) * 16);
-    const float4 hi = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
-    const float4 lo = make_float4(tf32_rna(v.x - hi.x), tf32_rna(v.y - hi.y), tf32_rna(v.z - hi.z),
-                                  tf32_rna(v.w - hi.w));
-    *reinterpret_cast<float4*>(gbase + off) = hi;
-    *reinterpret_cast<float4*>(gbase + kGjA + off) = lo;
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int e = (it0 + u) * kGjThreads + tid;
+      const int r = ((e >> 8) << 3) | (e & 7), qp = (e >> 3) & 31;
+      const uint32_t off = (uint32_t)((qp >> 3) * 16384 + (((r >> 3) << 3) + (qp & 7)) * 128 + (r & 7) * 16);
+      const float4 hi = make_float4(tf32_rna(v[u].x), tf32_rna(v[u].y), tf32_rna(v[u].z), tf32_rna(v[u].w));
+      const float4 lo = make_float4(tf32_rna(v[u].x - hi.x), tf32_rna(v[u].y - hi.y), tf32_rna(v[u].z - hi.z),
+                                    tf32_rna(v[u].w - hi.w));
+      *reinterpret_cast<float4*>(gbase + off) = hi;
+      *reinterpret_cast<float4*>(gbase + kGjA + off) = lo;
+    }
   }
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -674,8 +696,8 @@ __global__ void __launch_bounds__(128, 1) k_gj_update_tc(float2* __restrict__ M,
     if (j0 >= nx) break;
     if (j0 >= p0 && j0 + 32 <= pe) continue;  // every column of this tile is in the block
     // B' (the block's rows, columns j0..j0+31): float4 e = (row n = 2 j + t, q pair qp)
-    for (int it = 0; it < 16; ++it) {
-      const int e = it * 128 + tid;
+    for (int it = 0; it < 2048 / kGjThreads; ++it) {
+      const int e = it * kGjThreads + tid;
       const int n = ((e >> 8) << 3) | (e & 7), qp = (e >> 3) & 31;
       const int j = j0 + (n >> 1), t = n & 1, q = 2 * qp;
       float2 b0 = make_float2(0.f, 0.f), b1 = make_float2(0.f, 0.f);
@@ -724,13 +746,14 @@ __global__ void __launch_bounds__(128, 1) k_gj_update_tc(float2* __restrict__ M,
     ok = done_s != 0;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!ok) break;
-    // epilogue: warp w holds TMEM lanes 32 w .. (rows i0 + 32 w + lane), 64 columns
-    const int i = i0 + 32 * warp + lane;
+    // epilogue: warp w reads TMEM lanes 32 (w & 3) .. (rows i0 + 32 (w & 3) + lane) and columns
+    // 32 (w >> 2) .. (complex columns j0 + 16 (w >> 2) ..)
+    const int i = i0 + 32 * (warp & 3) + lane;
     const bool row_ok = i < nx && (i < p0 || i >= pe);
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
+    {
+      const int half = warp >> 2;
       uint32_t v[32];
-      const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + 32 * half;
+      const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 32 * half;
       asm volatile(
           "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
           "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
@@ -1041,7 +1064,7 @@ int riesz_build(Handle& h) {
       const int wp = nx - p0 < kGW ? nx - p0 : kGW;
       k_gj_pivot<<<K, 256, 0, h.stream>>>(h.rz_inv, nx, p0, wp, piv);
       k_gj_rowscale<<<dim3(nbt, K), 256, tsm, h.stream>>>(h.rz_inv, nx, p0, wp, piv);
-      k_gj_update_tc<<<gup, 128, kGjSmem, h.stream>>>(h.rz_inv, nx, p0, wp, err, tcg::kWaitNs);
+      k_gj_update_tc<<<gup, kGjThreads, kGjSmem, h.stream>>>(h.rz_inv, nx, p0, wp, err, tcg::kWaitNs);
       k_gj_colfix<<<dim3(nbt, K), 256, tsm, h.stream>>>(h.rz_inv, nx, p0, wp, piv);
       g_launches.fetch_add(3, std::memory_order_relaxed);
       rc = [&]() -> int { AAO_CHECK_LAUNCH(); return AAO_OK; }();

@@ -53,18 +53,22 @@ def test_default_steps_per_arm(monkeypatch):
 
 
 def test_precond_roofline_arithmetic():
-    """The apply's three kernel classes as one unit: bytes and time summed per apply."""
+    """The apply's three kernel classes as one unit: 16 B per unknown (FP64 v in, z out) over the
+    time per apply; the argument sizes and the in-solve FP32 ends are reported beside it."""
     B = load_bench()
-    # (launches, total ms, algorithmic bytes, flops) per class over 4 applies
+    # (launches, total ms, argument bytes, flops) per class over 4 applies
     prof = {"fft_fwd": (4, 0.08, 4 * 30e6, 0.0), "tridiag": (4, 0.12, 4 * 60e6, 0.0),
             "fft_inv": (4, 0.08, 4 * 30e6, 0.0), "matvec": (5, 0.5, 1e9, 1e8)}
-    r = B.precond_roofline(prof, 6800.0)
+    n = 4_192_256
+    r = B.precond_roofline(prof, 6800.0, n)
     assert r["applies"] == 4
     assert abs(r["ms_per_apply"] - 0.07) < 1e-12
-    assert abs(r["algorithmic_bytes_per_apply"] - 120e6) < 1e-3
-    assert abs(r["achieved"] - 120e6 / 0.07e-3 / 1e9) < 1e-9
+    assert r["algorithmic_bytes_per_apply"] == 16 * n
+    assert abs(r["achieved"] - 16 * n / 0.07e-3 / 1e9) < 1e-9
     assert abs(r["frac"] - r["achieved"] / 6800.0) < 1e-12
-    assert B.precond_roofline(dict(prof, fft_fwd=(0, 0.0, 0.0, 0.0)), 6800.0) is None
+    assert abs(r["in_solve_io_gbs"] - r["achieved"] / 2) < 1e-9
+    assert abs(r["argument_bytes_per_apply"] - 120e6) < 1e-3
+    assert B.precond_roofline(dict(prof, fft_fwd=(0, 0.0, 0.0, 0.0)), 6800.0, n) is None
 
 
 def test_traffic_record_is_used_only_on_its_own_sources(monkeypatch):
