@@ -20,6 +20,9 @@ Readings of points the paper leaves open (each one also listed in the design not
     A(t_{k+1/2}) for both time levels (the form of Eq. 5.8); the preconditioner uses the
     time mean of those matrices, the direct generalisation of d-bar in Sec. 5.3.
   * Riesz operator: fractional centred difference with Dirichlet exterior values.
+  * Heston operator (Sec. 5.1): central differences on a uniform (s, v) grid, the s = S_max
+    Neumann condition through a ghost node, the v = 0 boundary equation with a one-sided
+    second-order u_v.
 Parity pins for every function live in tests/test_oracle_*.py.
 """
 from __future__ import annotations
@@ -29,6 +32,7 @@ import math
 import numpy as np
 import scipy.linalg as sla
 import scipy.sparse as sp
+import scipy.sparse.linalg as spl
 import scipy.special as sps
 
 # ----------------------------------------------------------------------------------------
@@ -44,6 +48,11 @@ def spatial_grid(p):
         return -p["s_max"] + h * np.arange(1, nx + 1), h
     h = p["s_max"] / (nx + 1)
     return h * np.arange(1, nx + 1), h
+
+
+def n_space(p):
+    """Spatial unknowns per time level: Nx, or Ns Nv for the two-dimensional Heston operator."""
+    return int(p["nx"]) * (int(p["nv"]) if p["op"] == "heston" else 1)
 
 
 def time_grid(p):
@@ -118,6 +127,73 @@ def riesz_matrix(p):
     return A, left_ext, -drift
 
 
+def heston_grid(p):
+    """Heston unknowns (Sec. 5.1): s_i = i h_s, i = 1..Ns (s = S_max included: Neumann), v_j = j h_v,
+    j = 0..Nv-1 (v = 0 included: the degenerate boundary equation; v = V_max is Dirichlet),
+    h_s = S_max / Ns, h_v = V_max / Nv; unknown (i, j) at position j Ns + (i - 1)."""
+    ns, nv = int(p["nx"]), int(p["nv"])
+    hs, hv = p["s_max"] / ns, p["v_max"] / nv
+    return hs * np.arange(1, ns + 1), hv * np.arange(nv), hs, hv
+
+
+def heston_matrix(p):
+    """The Heston operator of Eq. 5.1 by second-order central differences on the uniform grid of
+    heston_grid (u_ss, u_vv, u_s, u_v central; u_sv by the four-point cross stencil), with
+    u(0, v) = 0, u(s, V_max) = s, u_s(S_max, v) = 1 through a ghost node u_{Ns+1} = u_{Ns-1} + 2 h_s,
+    and at v = 0 the boundary equation u_t = kappa eta u_v + r s u_s - r u with the one-sided
+    second-order u_v = (-3 u_0 + 4 u_1 - u_2) / (2 h_v). Returns the sparse A and the constant vector f
+    through which the boundary data enter (u' = A u + f)."""
+    ns, nv = int(p["nx"]), int(p["nv"])
+    S, V, hs, hv = heston_grid(p)
+    r, kap, eta, sig, rho = p["r"], p["kappa"], p["eta"], p["sigma"], p["rho"]
+    rows, cols, vals = [], [], []
+    f = np.zeros(ns * nv)
+
+    def add(i, j, ii, jj, c):
+        """coefficient c of u(ii, jj) in the equation of unknown (i, j), i, ii 1-based in s"""
+        row = j * ns + (i - 1)
+        if jj == nv:                       # v = V_max: u = s
+            f[row] += c * ii * hs
+        elif ii == 0:                      # s = 0: u = 0
+            pass
+        elif ii == ns + 1:                 # ghost beyond S_max
+            add(i, j, ns - 1, jj, c)
+            f[row] += c * 2.0 * hs
+        else:
+            rows.append(row)
+            cols.append(jj * ns + (ii - 1))
+            vals.append(c)
+
+    for j in range(nv):
+        v = V[j]
+        for i in range(1, ns + 1):
+            s_ = S[i - 1]
+            if j == 0:
+                add(i, j, i, 0, -3.0 * kap * eta / (2 * hv) - r)
+                add(i, j, i, 1, 4.0 * kap * eta / (2 * hv))
+                add(i, j, i, 2, -kap * eta / (2 * hv))
+                add(i, j, i + 1, 0, r * s_ / (2 * hs))
+                add(i, j, i - 1, 0, -r * s_ / (2 * hs))
+                continue
+            ass = 0.5 * v * s_ * s_ / hs ** 2
+            avv = 0.5 * sig * sig * v / hv ** 2
+            asv = sig * rho * s_ * v / (4 * hs * hv)
+            bs = r * s_ / (2 * hs)
+            bv = kap * (eta - v) / (2 * hv)
+            add(i, j, i, j, -2 * ass - 2 * avv - r)
+            add(i, j, i + 1, j, ass + bs)
+            add(i, j, i - 1, j, ass - bs)
+            add(i, j, i, j + 1, avv + bv)
+            add(i, j, i, j - 1, avv - bv)
+            add(i, j, i + 1, j + 1, asv)
+            add(i, j, i - 1, j - 1, asv)
+            add(i, j, i + 1, j - 1, -asv)
+            add(i, j, i - 1, j + 1, -asv)
+    A = sp.csr_matrix((vals, (rows, cols)), shape=(ns * nv, ns * nv))
+    A.sum_duplicates()
+    return A, f
+
+
 def operator_at(p, t):
     """A(t) as a dense matrix, plus the coefficients through which the left/right Dirichlet
     values enter the first/last interior rows. op 'matrix' takes a user matrix p['A']
@@ -125,6 +201,9 @@ def operator_at(p, t):
     if p["op"] == "matrix":
         A = np.asarray(p["A"], dtype=np.float64)
         return A, np.zeros(A.shape[0]), np.zeros(A.shape[0])
+    if p["op"] == "heston":
+        A, f = heston_matrix(p)
+        return A, f, np.zeros(A.shape[0])
     if p["op"] == "riesz":
         A, left_ext, left_drift = riesz_matrix(p)
         cl = left_ext.copy()
@@ -143,6 +222,8 @@ def boundary_values(p, t):
     """Dirichlet values (g_L(t), g_R(t)) in time-to-maturity t."""
     if p["op"] == "matrix":
         return 0.0, 0.0
+    if p["op"] == "heston":
+        return 1.0, 0.0  # time-independent data, carried by the vector f of heston_matrix
     disc = p["K"] * math.exp(-p["r"] * t)
     if p["op"] == "riesz":
         return disc - math.exp(-p["s_max"]), 0.0
@@ -155,6 +236,9 @@ def payoff(p):
     """u_0: the option payoff at the interior nodes (Eq. 1.1, u(., 0) = u_0)."""
     if p["op"] == "matrix":
         return np.asarray(p.get("u0", np.ones(int(p["nx"]))), dtype=np.float64)
+    if p["op"] == "heston":
+        S, _, _, _ = heston_grid(p)
+        return np.tile(np.maximum(S - p["K"], 0.0), int(p["nv"]))  # call, Eq. 5.2
     x, _ = spatial_grid(p)
     if p["op"] == "riesz":
         return np.maximum(p["K"] - np.exp(x), 0.0)
@@ -188,6 +272,10 @@ def _solve(Amat, rhs):
     dense LU otherwise."""
     if sp.issparse(Amat):
         n = Amat.shape[0]
+        coo = Amat.tocoo()
+        if coo.nnz and np.abs(coo.row - coo.col).max() > 1:
+            # wider than tridiagonal (the two-dimensional Heston operator): sparse LU
+            return spl.spsolve(sp.csc_matrix(Amat, dtype=np.result_type(Amat.dtype, rhs.dtype)), rhs)
         ab = np.zeros((3, n), dtype=np.result_type(Amat.dtype, rhs.dtype))
         ab[0, 1:] = Amat.diagonal(1)
         ab[1, :] = Amat.diagonal(0)
@@ -230,7 +318,7 @@ def sequential_cn(p):
 def assemble_M(p):
     """M of Eq. 2.2 (B1 (x) I - B2 (x) A~, A~ = tau A) for constant A; for time-dependent A the
     form of Eq. 5.8 with A~_k = tau A(t_{k+1/2}) in block row k. Sparse CSR, time-major."""
-    nt, nx = int(p["nt"]), int(p["nx"])
+    nt, nx = int(p["nt"]), n_space(p)
     _, tau = time_grid(p)
     I = sp.identity(nx, format="csr")
     if p["op"] != "localvol":
@@ -249,7 +337,7 @@ def assemble_M(p):
 
 def assemble_b(p):
     """b = xi + tau f (Eq. 2.2), xi = [(I + A~_0/2) u^0; 0; ...; 0]."""
-    nt, nx = int(p["nt"]), int(p["nx"])
+    nt, nx = int(p["nt"]), n_space(p)
     _, tau = time_grid(p)
     b = np.empty((nt, nx))
     for k in range(nt):
@@ -269,7 +357,7 @@ def matvec(p, x, M=None):
 def matvec_blocks(p, x):
     """y = M x by the block rows of Eq. 2.2 for a constant A: y_t = Q1 x_t - Q2 x_{t-1},
     Q1 = I - A~/2, Q2 = I + A~/2 (dense A, all time levels in one matrix product)."""
-    nt, nx = int(p["nt"]), int(p["nx"])
+    nt, nx = int(p["nt"]), n_space(p)
     _, tau = time_grid(p)
     A = _dense(step_operator(p, 0)[0])
     X = np.asarray(x, dtype=np.float64).reshape(nt, nx)
@@ -310,7 +398,7 @@ def mean_operator(p):
 def dense_P(p, alpha=None):
     """P_alpha = C1 (x) I_s - C2 (x) A~ (Eq. 3.1), A~ = tau A-bar. Dense; tiny sizes only."""
     alpha = p["alpha"] if alpha is None else alpha
-    nt, nx = int(p["nt"]), int(p["nx"])
+    nt, nx = int(p["nt"]), n_space(p)
     _, tau = time_grid(p)
     C1, C2 = alpha_circulants(nt, alpha)
     return np.kron(C1, np.eye(nx)) - np.kron(C2, tau * _dense(mean_operator(p)))
@@ -321,7 +409,7 @@ def apply_P(p, z, alpha=None):
     as B1 and B2 (z_t - z_{t-1}, (z_t + z_{t-1})/2) with the alpha corner at t = 0 (Sec. 3.1),
     A~ = tau A-bar along space. Any size."""
     alpha = p["alpha"] if alpha is None else alpha
-    nt, nx = int(p["nt"]), int(p["nx"])
+    nt, nx = int(p["nt"]), n_space(p)
     _, tau = time_grid(p)
     Z = np.asarray(z, dtype=np.float64).reshape(nt, nx)
     prev = np.roll(Z, 1, axis=0)  # z_{t-1}; row 0 holds z_{nt-1}
@@ -356,7 +444,7 @@ def precond_fft(p, v, alpha=None, return_spectrum=False):
     (c) z = (V_alpha (x) I) z2 with V_alpha = Lambda_alpha^{-1} F^*.
     All Nt shifted systems are solved (the conjugate-pair saving of Remark 1 is not used)."""
     alpha = p["alpha"] if alpha is None else alpha
-    nt, nx = int(p["nt"]), int(p["nx"])
+    nt, nx = int(p["nt"]), n_space(p)
     _, tau = time_grid(p)
     lam, d1, d2 = circulant_eigs(nt, alpha)
     At = tau * mean_operator(p)
@@ -477,6 +565,37 @@ def bs_price(S, K, r, sigma, T, kind="put"):
     return K * math.exp(-r * T) * N(-d2) - S * N(-d1)
 
 
+def heston_char(u, T, v0, kappa, eta, sigma, rho):
+    """E[exp(i u X_T)] for X_T = ln(S_T / S_0) - r T under the Heston dynamics (Heston 1993), in the
+    form of Albrecher et al. (2007), "The little Heston trap", whose complex logarithm stays on its
+    principal branch: d = sqrt((kappa - i rho sigma u)^2 + sigma^2 (i u + u^2)),
+    g = (kappa - i rho sigma u - d) / (kappa - i rho sigma u + d),
+    C = kappa eta / sigma^2 ((kappa - i rho sigma u - d) T - 2 ln((1 - g e^{-dT}) / (1 - g))),
+    D = (kappa - i rho sigma u - d) / sigma^2 (1 - e^{-dT}) / (1 - g e^{-dT}), phi = exp(C + D v0)."""
+    u = np.asarray(u, dtype=np.complex128)
+    b = kappa - 1j * rho * sigma * u
+    d = np.sqrt(b * b + sigma * sigma * (1j * u + u * u))
+    g = (b - d) / (b + d)
+    e = np.exp(-d * T)
+    C = kappa * eta / sigma ** 2 * ((b - d) * T - 2.0 * np.log((1.0 - g * e) / (1.0 - g)))
+    D = (b - d) / sigma ** 2 * (1.0 - e) / (1.0 - g * e)
+    return np.exp(C + D * v0)
+
+
+def heston_call(S0, v0, K, T, r, kappa, eta, sigma, rho):
+    """European call under Heston by the single-integral Fourier formula of Lewis (2000):
+    C = S0 - sqrt(S0 K) e^{-rT/2} / pi * int_0^inf Re[e^{i u k} phi(u - i/2)] / (u^2 + 1/4) du,
+    k = ln(S0 / K) + r T, phi = heston_char (numerical quadrature)."""
+    import scipy.integrate as si
+    k = math.log(S0 / K) + r * T
+
+    def integrand(u):
+        return (np.exp(1j * u * k) * heston_char(u - 0.5j, T, v0, kappa, eta, sigma, rho)).real / (u * u + 0.25)
+
+    val, _ = si.quad(integrand, 0.0, np.inf, limit=800, epsabs=1e-10, epsrel=1e-10)
+    return S0 - math.sqrt(S0 * K) * math.exp(-0.5 * r * T) / math.pi * val
+
+
 # ----------------------------------------------------------------------------------------
 # Spectral quantities (Lemma 3.1, Theorem 3.1, Theorem 2.2, Lemma 4.1) on tiny grids.
 # ----------------------------------------------------------------------------------------
@@ -490,7 +609,7 @@ def preconditioned_eigs(p, alpha=None):
 def R_matrix(p):
     """R with P_alpha = M - alpha R (Sec. 4): the only non-zero block is Q2 = I + A~/2 in
     block position (1, Nt)."""
-    nt, nx = int(p["nt"]), int(p["nx"])
+    nt, nx = int(p["nt"]), n_space(p)
     _, tau = time_grid(p)
     R = np.zeros((nt * nx, nt * nx))
     R[:nx, (nt - 1) * nx:] = np.eye(nx) + 0.5 * tau * _dense(mean_operator(p))

@@ -659,7 +659,7 @@ __global__ void __launch_bounds__(kGjThreads, 1) k_gj_update_tc(float2* __restri
   }
   // A' (rows i0.., the block's columns): float4 e = (row r, q pair qp) at chunk qp >> 3; the loads of
   // four pieces are issued before any of them is converted
-  constexpr int kBatch = 4;
+  constexpr int kBatch = 8;
   for (int it0 = 0; it0 < 4096 / kGjThreads; it0 += kBatch) {
     float4 v[kBatch];
 #pragma unroll
@@ -695,16 +695,27 @@ __global__ void __launch_bounds__(kGjThreads, 1) k_gj_update_tc(float2* __restri
     const int j0 = jbase + 32 * nt;
     if (j0 >= nx) break;
     if (j0 >= p0 && j0 + 32 <= pe) continue;  // every column of this tile is in the block
-    // B' (the block's rows, columns j0..j0+31): float4 e = (row n = 2 j + t, q pair qp)
-    for (int it = 0; it < 2048 / kGjThreads; ++it) {
+    // B' (the block's rows, columns j0..j0+31): float4 e = (row n = 2 j + t, q pair qp); all loads
+    // of a thread issued before any is used
+    constexpr int kIt = 2048 / kGjThreads;
+    float2 bq[kIt][2];
+#pragma unroll
+    for (int it = 0; it < kIt; ++it) {
       const int e = it * kGjThreads + tid;
       const int n = ((e >> 8) << 3) | (e & 7), qp = (e >> 3) & 31;
-      const int j = j0 + (n >> 1), t = n & 1, q = 2 * qp;
-      float2 b0 = make_float2(0.f, 0.f), b1 = make_float2(0.f, 0.f);
+      const int j = j0 + (n >> 1), q = 2 * qp;
+      bq[it][0] = bq[it][1] = make_float2(0.f, 0.f);
       if (j < nx) {
-        if (q < wp) b0 = A[(size_t)(p0 + q) * nx + j];
-        if (q + 1 < wp) b1 = A[(size_t)(p0 + q + 1) * nx + j];
+        if (q < wp) bq[it][0] = A[(size_t)(p0 + q) * nx + j];
+        if (q + 1 < wp) bq[it][1] = A[(size_t)(p0 + q + 1) * nx + j];
       }
+    }
+#pragma unroll
+    for (int it = 0; it < kIt; ++it) {
+      const int e = it * kGjThreads + tid;
+      const int n = ((e >> 8) << 3) | (e & 7), qp = (e >> 3) & 31;
+      const int t = n & 1;
+      const float2 b0 = bq[it][0], b1 = bq[it][1];
       const float4 v = t == 0 ? make_float4(b0.x, -b0.y, b1.x, -b1.y) : make_float4(b0.y, b0.x, b1.y, b1.x);
       const uint32_t off = (uint32_t)((qp >> 3) * 8192 + (((n >> 3) << 3) + (qp & 7)) * 128 + (n & 7) * 16);
       const float4 hi = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
@@ -731,6 +742,17 @@ __global__ void __launch_bounds__(kGjThreads, 1) k_gj_update_tc(float2* __restri
       }
       commit(mbar);
     }
+    // this thread's 16 entries of C (row i, complex columns j0 + 16 (w >> 2) ..), loaded while the
+    // MMAs run
+    const int i = i0 + 32 * (warp & 3) + lane;
+    const bool row_ok = i < nx && (i < p0 || i >= pe);
+    const int jc = j0 + 16 * (warp >> 2);
+    float2 cv[16];
+#pragma unroll
+    for (int jj = 0; jj < 16; ++jj) {
+      const int j = jc + jj;
+      cv[jj] = (row_ok && j < nx) ? A[(size_t)i * nx + j] : make_float2(0.f, 0.f);
+    }
     // the MMAs of this tile are done (thread 0 waits; the outcome is shared at the barrier)
     __shared__ int done_s;
     if (tid == 0) {
@@ -747,9 +769,7 @@ __global__ void __launch_bounds__(kGjThreads, 1) k_gj_update_tc(float2* __restri
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!ok) break;
     // epilogue: warp w reads TMEM lanes 32 (w & 3) .. (rows i0 + 32 (w & 3) + lane) and columns
-    // 32 (w >> 2) .. (complex columns j0 + 16 (w >> 2) ..)
-    const int i = i0 + 32 * (warp & 3) + lane;
-    const bool row_ok = i < nx && (i < p0 || i >= pe);
+    // 32 (w >> 2) .. (complex columns jc ..)
     {
       const int half = warp >> 2;
       uint32_t v[32];
@@ -767,11 +787,9 @@ __global__ void __launch_bounds__(kGjThreads, 1) k_gj_update_tc(float2* __restri
         float2* dst = A + (size_t)i * nx;
 #pragma unroll
         for (int jj = 0; jj < 16; ++jj) {
-          const int j = j0 + 16 * half + jj;
-          if (j < nx && (j < p0 || j >= pe)) {
-            const float2 c = dst[j];
-            dst[j] = make_float2(c.x - __uint_as_float(v[2 * jj]), c.y - __uint_as_float(v[2 * jj + 1]));
-          }
+          const int j = jc + jj;
+          if (j < nx && (j < p0 || j >= pe))
+            dst[j] = make_float2(cv[jj].x - __uint_as_float(v[2 * jj]), cv[jj].y - __uint_as_float(v[2 * jj + 1]));
         }
       }
     }

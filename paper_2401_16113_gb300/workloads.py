@@ -8,8 +8,9 @@ plain dictionaries and numpy arrays from here.
 A problem is a dict with the keys
 
   op        'bs' (constant-coefficient Black-Scholes in S), 'localvol'
-            (Black-Scholes with sigma(S, t)), or 'riesz' (Riesz fractional
-            operator in log-price x)
+            (Black-Scholes with sigma(S, t)), 'riesz' (Riesz fractional
+            operator in log-price x) or 'heston' (the two-dimensional Heston
+            operator in (s, v), Sec. 5.1)
   payoff    'put' or 'call'
   nx, nt    interior spatial nodes, number of Crank-Nicolson steps
   T, r, K   maturity, rate, strike
@@ -21,6 +22,10 @@ A problem is a dict with the keys
             volatility that depends on time only; the oracle's pins use it, the library
             rejects it)
   beta      'riesz' only: fractional order in (1, 2]
+  nv, kappa, eta, rho, v_max
+            'heston' only: nx = Ns nodes in s, nv = Nv nodes in v, mean reversion,
+            long-run variance, correlation, v-domain [0, v_max]; sigma is the
+            volatility of variance and s_max the s-domain [0, s_max]
   alpha     the free parameter of the alpha-circulant preconditioner (Sec. 3.1)
   precision 'fp64' or 'mixed' (FP32-complex preconditioner inside FP64 FGMRES)
   m, tol    restart length and relative-residual tolerance of FGMRES(m)
@@ -76,6 +81,22 @@ def riesz_sym_1023x512():
     return with_(riesz_1023x512(), r=0.03125)
 
 
+def heston_set1(nt=48, precision="mixed"):
+    """Heston parameter Set I of Sec. 5.1 (European call, S in [0, 800], v in [0, 4]): T 1, K 100,
+    kappa 1.5, eta 0.04, sigma 0.3, r 0.025, rho -0.9, evaluated at S0 100, V0 0.5; the paper's mesh
+    family Nt = Ns = 2 Nv, alpha 1e-3, GMRES(40), tol 1e-9."""
+    return _base(op="heston", payoff="call", nx=nt, nv=nt // 2, nt=nt, T=1.0, K=100.0, r=0.025,
+                 sigma=0.3, kappa=1.5, eta=0.04, rho=-0.9, s_max=800.0, v_max=4.0, S0=100.0, V0=0.5,
+                 alpha=1e-3, precision=precision, m=40, tol=1e-9)
+
+
+def heston_set2(nt=48, precision="mixed"):
+    """Heston parameter Set II of Sec. 5.1: T 3, K 100, kappa 0.6067, eta 0.0707, sigma 0.2928,
+    r 0.03, rho -0.7571, S0 100, V0 0.2; same domain and mesh family as Set I."""
+    return with_(heston_set1(nt, precision), T=3.0, kappa=0.6067, eta=0.0707, sigma=0.2928, r=0.03,
+                 rho=-0.7571, V0=0.2)
+
+
 def batch_instances(n=512, seed=SEED, nx_choices=(127, 255, 511, 1023),
                     nt_choices=(64, 128, 256, 512, 1024), precision="mixed", alpha=1e-3, m=20,
                     tol=1e-8):
@@ -107,4 +128,4 @@ def with_(p, **kw):
 
 
 def unknowns(p):
-    return int(p["nx"]) * int(p["nt"])
+    return int(p["nx"]) * int(p.get("nv", 1)) * int(p["nt"])
