@@ -5,7 +5,8 @@
  * Conventions shared by every entry point
  *  - Space-time vectors are FP64, time-block-major: u[t * nx + i] holds u^{t+1} at the
  *    interior spatial node i (the ordering of the all-at-once unknown in Sec. 2.2),
- *    t = 0..nt-1, i = 0..nx-1. Their length is nx * nt.
+ *    t = 0..nt-1, i = 0..nx-1. Their length is nx * nt (nx * nv * nt for AAO_OP_HESTON, whose
+ *    time level holds nx * nv unknowns).
  *  - Pointers named *_dev are device pointers owned by the caller; the library never
  *    frees caller memory. Pointers named *_host are ordinary (pageable or pinned) host
  *    pointers.
@@ -48,6 +49,17 @@ extern "C" {
                              (r = sigma^2/2, a symmetric operator), by the eigendecomposition
                              tau Abar = Q diag(lambda) Q^T: two products with Q per apply   */
 
+#define AAO_OP_HESTON 3   /* the two-dimensional Heston operator of Sec. 5.1 (Eq. 5.1) in (s, v) on a
+                             uniform grid: s_i = i s_max / nx, i = 1..nx (s = s_max carries the
+                             Neumann condition u_s = 1 through a ghost node), v_j = j v_max / nv,
+                             j = 0..nv-1 (v = 0 carries the boundary equation u_t = kappa eta u_v +
+                             r s u_s - r u with a one-sided second-order u_v; v = v_max the Dirichlet
+                             value u = s), u(0, v) = 0; central differences, the mixed derivative by
+                             the four-point cross stencil; call payoff only. Unknown (i, j) of a
+                             time level at j nx + i - 1. Step (b) by block elimination over the v
+                             levels with dense inverses of the diagonal blocks made at create
+                             (precision AAO_MIXED only) */
+
 #define AAO_PUT 0
 #define AAO_CALL 1
 
@@ -71,6 +83,10 @@ extern "C" {
  *              default the factored method where one bin's staged tables fit in shared memory,
  *              the recomputing one elsewhere; both give P_alpha^{-1} v up to rounding)
  *  stream      cudaStream_t on which all work is issued
+ *  nv, kappa, eta, rho, v_max
+ *              AAO_OP_HESTON only: nodes in v (3..512; nx 3..512 nodes in s), mean reversion,
+ *              long-run variance, correlation of the two Brownian motions, v-domain [0, v_max];
+ *              sigma is then the volatility of the variance. A time level holds nx * nv unknowns.
  */
 #define AAO_FLAG_STEPB_FACTORED 1  /* partition method with per-bin pivot tables made at create */
 #define AAO_FLAG_STEPB_RECOMPUTE 2 /* partition method, pivots recomputed in every apply      */
@@ -78,6 +94,8 @@ typedef struct aao_problem {
   int32_t nx, nt, op, payoff, precision, flags;
   double T, r, K, sigma, s_max, lv_bump, lv_tslope, beta, alpha;
   void* stream;
+  int32_t nv, reserved;
+  double kappa, eta, rho, v_max;
 } aao_problem;
 
 /* FGMRES outcome. iterations counts inner Arnoldi steps (= preconditioned matrix-vector

@@ -17,7 +17,7 @@ from . import build as _build
 
 AAO_OK, AAO_EINVAL, AAO_ECUDA, AAO_ENOMEM = 0, -1, -2, -3
 AAO_NOT_CONVERGED, AAO_BREAKDOWN, AAO_TIMEOUT, AAO_EUNSUPPORTED = -4, -5, -6, -7
-OPS = {"bs": 0, "localvol": 1, "riesz": 2}
+OPS = {"bs": 0, "localvol": 1, "riesz": 2, "heston": 3}
 PAYOFFS = {"put": 0, "call": 1}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 STEPB = {"auto": 0, "factored": 1, "recompute": 2}  # how the tridiagonal step (b) is solved
@@ -39,7 +39,9 @@ class AaoProblem(ctypes.Structure):
                 ("T", ctypes.c_double), ("r", ctypes.c_double), ("K", ctypes.c_double),
                 ("sigma", ctypes.c_double), ("s_max", ctypes.c_double), ("lv_bump", ctypes.c_double),
                 ("lv_tslope", ctypes.c_double), ("beta", ctypes.c_double), ("alpha", ctypes.c_double),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("nv", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("kappa", ctypes.c_double), ("eta", ctypes.c_double), ("rho", ctypes.c_double),
+                ("v_max", ctypes.c_double)]
 
 
 class AaoStats(ctypes.Structure):
@@ -131,6 +133,8 @@ def make_problem(p, stream=0):
     s.T, s.r, s.K, s.sigma, s.s_max = p["T"], p["r"], p["K"], p["sigma"], p["s_max"]
     s.lv_bump, s.lv_tslope, s.beta, s.alpha = p["lv_bump"], p["lv_tslope"], p["beta"], p["alpha"]
     s.flags = STEPB[p.get("step_b", "auto")]
+    s.nv = int(p.get("nv", 1))
+    s.kappa, s.eta, s.rho, s.v_max = (float(p.get(k, 0.0)) for k in ("kappa", "eta", "rho", "v_max"))
     s.stream = int(stream or 0)
     return s
 
@@ -148,7 +152,7 @@ class Handle:
     def __init__(self, ptr, problem):
         self.ptr = ptr
         self.problem = dict(problem)
-        self.n = int(problem["nx"]) * int(problem["nt"])
+        self.n = int(problem["nx"]) * int(problem.get("nv", 1)) * int(problem["nt"])
 
     def close(self):
         if self.ptr:

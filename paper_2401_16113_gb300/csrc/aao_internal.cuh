@@ -269,6 +269,15 @@ struct Handle {
   // TMA tensor maps (CUtensorMap, 128 bytes each) of the tiled Q^T head, tail, Q head, tail
   alignas(64) unsigned char rz_tmap[4 * 128] = {};
 
+  // Heston operator (AAO_OP_HESTON): grid hs_ns x hs_nv (nx = hs_ns * hs_nv unknowns per level);
+  // per unknown the ten stencil coefficients of (tau/2) A (FP64 for the matvec, FP32 for step (b)),
+  // tau f (boundary data), the payoff; step (b) per bin and v level: X_j = D_j^{-1},
+  // G_j = X_j C'_j (j < nv - 1), H_0 = X_0 E_0 (FP32 complex, [j][k][ns][ns])
+  int hs_ns = 0, hs_nv = 0;
+  double *hs_c = nullptr, *hs_tf = nullptr, *hs_u0 = nullptr;
+  float* hs_cf = nullptr;
+  float2 *hs_X = nullptr, *hs_G = nullptr, *hs_H = nullptr;
+
   // FGMRES workspace (grown on demand)
   int ws_m = 0;
   double* V = nullptr;    // (m+1) * n
@@ -296,6 +305,15 @@ inline bool riesz_symmetric(const aao_problem& p) { return p.r - 0.5 * p.sigma *
 // Q^T. False if the QL iteration does not converge.
 bool sym_eig(int n, double* A, double* w);
 int riesz_build(Handle& h);
+// in place: each of the K contiguous n x n complex matrices of M replaced by its inverse (blocked
+// Gauss-Jordan without pivoting, the rank-64 updates on the tensor cores); synchronises the stream
+int gj_invert_batched(cudaStream_t stream, float2* M, int n, int K);
+// the Heston operator: stencil, boundary data and the step (b) block factors; matvec, b, step (b)
+int heston_build(Handle& h);
+int heston_matvec(Handle& h, const void* x, bool x_is_float, double* y, const double* b, const double* V, int nd,
+                  int m);
+int heston_rhs(Handle& h, double* b);
+int heston_solve_bins(Handle& h, void* spec);
 int riesz_matvec(Handle& h, const void* x, bool x_is_float, double* y, const double* b, const double* V, int nd, int m);
 int riesz_rhs(Handle& h, double* b);
 // step (b) of the Riesz operator on the half spectrum spec; *result: the buffer holding z2

@@ -69,7 +69,18 @@ bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 int validate(const aao_problem* p) {
   if (!p) { set_error("aao_create: null problem"); return AAO_EINVAL; }
   if (p->nx < 2 || p->nt < 1) { set_error("aao_create: need nx >= 2 and nt >= 1"); return AAO_EINVAL; }
-  if (p->op != AAO_OP_BS && p->op != AAO_OP_LOCALVOL && p->op != AAO_OP_RIESZ) { set_error("aao_create: unknown op"); return AAO_EINVAL; }
+  if (p->op != AAO_OP_BS && p->op != AAO_OP_LOCALVOL && p->op != AAO_OP_RIESZ && p->op != AAO_OP_HESTON) { set_error("aao_create: unknown op"); return AAO_EINVAL; }
+  if (p->op == AAO_OP_HESTON) {
+    if (p->precision != AAO_MIXED) { set_error("aao_create: the Heston operator is built for precision AAO_MIXED only"); return AAO_EUNSUPPORTED; }
+    if (p->payoff != AAO_CALL) { set_error("aao_create: the Heston boundary conditions of Sec. 5.1 are those of a call"); return AAO_EUNSUPPORTED; }
+    if (p->nx < 3 || p->nx > 512 || p->nv < 3 || p->nv > 512) { set_error("aao_create: Heston needs 3 <= nx, nv <= 512"); return AAO_EUNSUPPORTED; }
+    if (!(p->kappa > 0) || !(p->eta > 0) || !(p->rho >= -1) || !(p->rho <= 1) || !(p->v_max > 0)) {
+      set_error("aao_create: Heston needs kappa, eta, v_max > 0 and -1 <= rho <= 1");
+      return AAO_EINVAL;
+    }
+    const double factors = 2.0 * p->nv * (double)(p->nt / 2 + 1) * p->nx * (double)p->nx * 8.0;
+    if (factors > 48e9) { set_error("aao_create: Heston step-(b) block factors would exceed 48 GB"); return AAO_EUNSUPPORTED; }
+  }
   if (p->op == AAO_OP_RIESZ) {
     if (p->precision != AAO_MIXED) { set_error("aao_create: the Riesz operator is built for precision AAO_MIXED only"); return AAO_EUNSUPPORTED; }
     if (!(p->beta > 1.0) || !(p->beta <= 2.0)) { set_error("aao_create: Riesz order beta must lie in (1, 2]"); return AAO_EINVAL; }
@@ -120,15 +131,15 @@ int aao_create(const aao_problem* p, aao_handle** out) {
   Handle& h = hd->h;
   h.p = *p;
   h.stream = (cudaStream_t)p->stream;
-  h.nx = p->nx;
+  h.nx = p->op == AAO_OP_HESTON ? p->nx * p->nv : p->nx;  // spatial unknowns per time level
   h.nt = p->nt;
   h.K = p->nt / 2 + 1;
   int l = 0;
   while ((1 << l) < p->nt) ++l;
   h.log2n = l;
   if (!is_pow2(p->nt)) mr_plan(p->nt, h.mr);
-  h.pitch = ((p->nx + 63) / 64) * 64;
-  h.n = (size_t)p->nx * p->nt;
+  h.pitch = ((h.nx + 63) / 64) * 64;
+  h.n = (size_t)h.nx * p->nt;
   h.mixed = p->precision == AAO_MIXED;
   int s = build_tables(h);
   if (s == AAO_OK) s = tune_precond(h);

@@ -1,0 +1,528 @@
+// The two-dimensional Heston operator of Sec. 5.1 (Eq. 5.1-5.5) on GB300.
+//
+//   u_t = 1/2 v s^2 u_ss + sigma rho s v u_sv + 1/2 sigma^2 v u_vv + r s u_s + kappa (eta - v) u_v - r u
+//
+// on a uniform grid: s_i = i h_s (i = 1..Ns, h_s = s_max / Ns), v_j = j h_v (j = 0..Nv-1,
+// h_v = v_max / Nv); unknown (i, j) of a time level at p = j Ns + i - 1 (Ns Nv unknowns per level,
+// so the FFT kernels of steps (a) and (c) see Ns Nv spatial columns). Second-order central
+// differences, the mixed derivative by the four-point cross stencil; u(0, v) = 0; u(s, v_max) = s;
+// u_s(s_max, v) = 1 through the ghost value u_{Ns+1} = u_{Ns-1} + 2 h_s; at v = 0 the boundary
+// equation u_t = kappa eta u_v + r s u_s - r u with u_v = (-3 u_0 + 4 u_1 - u_2) / (2 h_v).
+// Every row couples at most the ten offsets (di, dj) in {-1, 0, 1}^2 and (0, 2) (the last only on
+// v = 0). The coefficients of (tau/2) A are built on the host in FP64 and kept per unknown.
+//
+// Kernels:
+//   k_hs_matvec  FP64 y = M x (Eq. 2.2) from the stencil: y_t = (x_t - x_{t-1}) - (tau/2) A (x_t + x_{t-1}),
+//                fused with the restart residual or the first Gram-Schmidt projections, finished
+//                by the last block (the conventions of the other operators' matvecs);
+//   k_hs_rhs     b = xi + tau f (the boundary data are constant in time);
+//   step (b) of Eq. 3.2 by block elimination over the v levels. The shifted matrix of bin k,
+//                S = mu_k I - tau A, is block tridiagonal in j (blocks Ns x Ns: B_j tridiagonal on
+//                the diagonal, A_j and C_j tridiagonal below and above) except for the block E_0
+//                (diagonal) that the one-sided u_v puts at (0, 2). At create, per bin:
+//                D_0 = B_0, D_j = B_j - A_j G_{j-1}, X_j = D_j^{-1} (batched Gauss-Jordan on the tensor
+//                cores, shared with the Riesz operator), G_j = X_j C'_j with C'_1 = C_1 - A_1 H_0 and
+//                C'_j = C_j otherwise, H_0 = X_0 E_0. Per apply (k_hs_solve, one CTA per bin):
+//                w_0 = X_0 r_0, w_j = X_j (r_j - A_j w_{j-1}); x_{Nv-1} = w_{Nv-1},
+//                x_j = w_j - G_j x_{j+1} (j >= 1), x_0 = w_0 - G_0 x_1 - H_0 x_2.
+#include <math.h>
+
+#include <vector>
+
+#include "krylov_dev.cuh"
+
+namespace aao {
+
+namespace {
+
+using namespace kdev;
+
+constexpr int kHsOff = 10;  // stencil offsets, in this order:
+__host__ __device__ constexpr int hs_di(int q) { return q < 9 ? (q % 3) - 1 : 0; }
+__host__ __device__ constexpr int hs_dj(int q) { return q < 9 ? (q / 3) - 1 : 2; }
+
+template <typename T> __device__ __forceinline__ double ldx(const T* p) { return (double)*p; }
+template <> __device__ __forceinline__ double ldx<float>(const float* p) { return widen(*p); }
+
+// y = M x over all (t, p): one thread per unknown (grid-stride). MODE 0: y = M x; MODE 1: y = b - M x
+// and ||y||^2 (restart residual; sigma_0, g set by the last block); MODE 2: y = M x and the
+// projections V_q . y, q < ND.
+template <typename IN, int MODE, int ND>
+__global__ void __launch_bounds__(256) k_hs_matvec(const IN* __restrict__ x, double* __restrict__ y,
+                                                   const double* __restrict__ b, int ns, int nsp, int nt,
+                                                   const double* __restrict__ c, const double* __restrict__ V,
+                                                   size_t vstride, double* __restrict__ part,
+                                                   double* __restrict__ scal, unsigned int* __restrict__ counter,
+                                                   int m) {
+  pdl_sync();
+  constexpr int NA = MODE == 2 ? ND : 1;
+  double acc[NA];
+#pragma unroll
+  for (int q = 0; q < NA; ++q) acc[q] = 0.0;
+  const size_t n = (size_t)nsp * nt;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const int t = (int)(e / nsp), p = (int)(e - (size_t)t * nsp);
+    const IN* xt = x + (size_t)t * nsp;
+    const IN* xm = t > 0 ? xt - nsp : nullptr;
+    double as = 0.0;  // ((tau/2) A s)_p, s = x_t + x_{t-1}
+#pragma unroll
+    for (int q = 0; q < kHsOff; ++q) {
+      const double cq = __ldg(c + (size_t)q * nsp + p);
+      if (cq != 0.0) {
+        const int nb = p + hs_di(q) + hs_dj(q) * ns;
+        if (nb >= 0 && nb < nsp) as = fma(cq, ldx(xt + nb) + (xm ? ldx(xm + nb) : 0.0), as);
+      }
+    }
+    const double x0 = ldx(xt + p), x1 = xm ? ldx(xm + p) : 0.0;
+    double v = (x0 - x1) - as;
+    if (MODE == 1) {
+      v = __ldg(b + e) - v;
+      acc[0] = fma(v, v, acc[0]);
+    }
+    y[e] = v;
+    if (MODE == 2) {
+#pragma unroll
+      for (int q = 0; q < ND; ++q) acc[q] = fma(__ldg(V + (size_t)q * vstride + e), v, acc[q]);
+    }
+  }
+  if constexpr (MODE == 0) return;
+  __shared__ double red[8][NA];
+  {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NA; ++q) {
+      const double v = warp_sum(acc[q]);
+      if (lane == 0) red[warp][q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < NA) {
+      double s = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
+      part[(size_t)blockIdx.x * kPartLd + threadIdx.x] = s;
+    }
+  }
+  __shared__ bool am_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) am_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < NA; ++q) {
+      double s = 0.0;
+      for (unsigned bb = 0; bb < gridDim.x; ++bb) s += __ldcg(part + (size_t)bb * kPartLd + q);
+      if (MODE == 2) {
+        scal[S_D1 + q] = s;
+      } else {
+        scal[S_BETA2] = s;
+        const double beta = sqrt(s);
+        scal[S_SIG] = beta > 0.0 ? 1.0 / beta : 0.0;
+        scal[S_G] = beta;
+        for (int k = 1; k <= m; ++k) scal[S_G + k] = 0.0;
+        scal[S_FLAG] = isfinite(s) ? 0.0 : 1.0;
+      }
+    }
+    *counter = 0u;
+  }
+}
+
+// b_t = tau f + [t = 0] (u0 + (tau/2) A u0)
+__global__ void k_hs_rhs(double* __restrict__ b, int ns, int nsp, int nt, const double* __restrict__ c,
+                         const double* __restrict__ tf, const double* __restrict__ u0) {
+  const size_t n = (size_t)nsp * nt;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const int t = (int)(e / nsp), p = (int)(e - (size_t)t * nsp);
+    double v = tf[p];
+    if (t == 0) {
+      double au = 0.0;
+      for (int q = 0; q < kHsOff; ++q) {
+        const double cq = c[(size_t)q * nsp + p];
+        const int nb = p + hs_di(q) + hs_dj(q) * ns;
+        if (cq != 0.0 && nb >= 0 && nb < nsp) au = fma(cq, u0[nb], au);
+      }
+      v += u0[p] + au;
+    }
+    b[e] = v;
+  }
+}
+
+// ------------------------------------------------------------------------------- step (b): create
+// Blocks of S_k = mu_k I - tau A for level j (rows r, columns c in 0..Ns-1); tau A = 2 (tau/2) A, the
+// stencil coefficient of offset q at unknown (r, j) being hc[q][j Ns + r] (FP32 copy):
+//   B_j[r][r + di] = mu_k [di = 0] - 2 hc[3 + di + 1][..], A_j[r][r + di] = -2 hc[di + 1][..],
+//   C_j[r][r + di] = -2 hc[6 + di + 1][..], E_0[r][r] = -2 hc[9][r].
+__device__ __forceinline__ float hcoef(const float* __restrict__ hc, int nsp, int q, int p) {
+  return -2.f * __ldg(hc + (size_t)q * nsp + p);
+}
+
+// D[k] = B_j - A_j G (G = G_{j-1}[k], null for j = 0), one thread per entry, all bins (blockIdx.y)
+__global__ void k_hs_form_d(float2* __restrict__ D, const float2* __restrict__ G, int ns, int nsp, int j,
+                            const float* __restrict__ hc, const float2* __restrict__ mu) {
+  const int k = blockIdx.y;
+  const size_t nn = (size_t)ns * ns;
+  float2* Dk = D + (size_t)k * nn;
+  const float2* Gk = G ? G + (size_t)k * nn : nullptr;
+  const float2 muk = mu[k];
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / ns), cc = (int)(e - (size_t)r * ns);
+    const int p = j * ns + r;
+    float2 v = make_float2(0.f, 0.f);
+    const int di = cc - r;
+    if (di >= -1 && di <= 1) v.x = hcoef(hc, nsp, 4 + di, p);
+    if (di == 0) { v.x += muk.x; v.y += muk.y; }
+    if (Gk) {
+#pragma unroll
+      for (int d = -1; d <= 1; ++d) {
+        const int m = r + d;
+        if (m < 0 || m >= ns) continue;
+        const float a = hcoef(hc, nsp, 1 + d, p);
+        if (a != 0.f) {
+          const float2 g = Gk[(size_t)m * ns + cc];
+          v.x -= a * g.x;
+          v.y -= a * g.y;
+        }
+      }
+    }
+    Dk[e] = v;
+  }
+}
+
+// G[k] = X[k] C_j (C_j tridiagonal) - (T ? X[k] T[k] : 0), T dense; one thread per entry
+__global__ void k_hs_form_g(float2* __restrict__ G, const float2* __restrict__ X, const float2* __restrict__ T,
+                            int ns, int nsp, int j, const float* __restrict__ hc) {
+  const int k = blockIdx.y;
+  const size_t nn = (size_t)ns * ns;
+  const float2* Xk = X + (size_t)k * nn;
+  const float2* Tk = T ? T + (size_t)k * nn : nullptr;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / ns), cc = (int)(e - (size_t)r * ns);
+    float2 v = make_float2(0.f, 0.f);
+    // (X C)[r][cc] = sum_di X[r][cc - di] C[cc - di][cc], C[m][m + di] = -2 hc[7 + di][(m, j)]
+#pragma unroll
+    for (int d = -1; d <= 1; ++d) {
+      const int m = cc - d;
+      if (m < 0 || m >= ns) continue;
+      const float cm = hcoef(hc, nsp, 7 + d, j * ns + m);
+      if (cm != 0.f) {
+        const float2 x = Xk[(size_t)r * ns + m];
+        v.x += x.x * cm;
+        v.y += x.y * cm;
+      }
+    }
+    if (Tk) {
+      float ax = 0.f, ay = 0.f;
+      for (int m = 0; m < ns; ++m) {
+        const float2 x = Xk[(size_t)r * ns + m], t = Tk[(size_t)m * ns + cc];
+        ax = fmaf(x.x, t.x, fmaf(-x.y, t.y, ax));
+        ay = fmaf(x.x, t.y, fmaf(x.y, t.x, ay));
+      }
+      v.x -= ax;
+      v.y -= ay;
+    }
+    G[(size_t)k * nn + e] = v;
+  }
+}
+
+// H[k] = X_0[k] E_0 (E_0 diagonal), and T[k] = A_1 H[k] (A_1 tridiagonal): the pieces of C'_1
+__global__ void k_hs_form_h(float2* __restrict__ H, const float2* __restrict__ X0, int ns, int nsp,
+                            const float* __restrict__ hc) {
+  const int k = blockIdx.y;
+  const size_t nn = (size_t)ns * ns;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)gridDim.x * blockDim.x) {
+    const int cc = (int)(e % ns);
+    const float ec = hcoef(hc, nsp, 9, cc);
+    const float2 x = X0[(size_t)k * nn + e];
+    H[(size_t)k * nn + e] = make_float2(x.x * ec, x.y * ec);
+  }
+}
+__global__ void k_hs_form_t(float2* __restrict__ T, const float2* __restrict__ H, int ns, int nsp,
+                            const float* __restrict__ hc) {
+  const int k = blockIdx.y;
+  const size_t nn = (size_t)ns * ns;
+  const float2* Hk = H + (size_t)k * nn;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / ns), cc = (int)(e - (size_t)r * ns);
+    const int p = ns + r;  // level j = 1
+    float2 v = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int d = -1; d <= 1; ++d) {
+      const int m = r + d;
+      if (m < 0 || m >= ns) continue;
+      const float a = hcoef(hc, nsp, 1 + d, p);
+      const float2 h = Hk[(size_t)m * ns + cc];
+      v.x += a * h.x;
+      v.y += a * h.y;
+    }
+    T[(size_t)k * nn + e] = v;
+  }
+}
+
+// ------------------------------------------------------------------------------- step (b): apply
+// One CTA per bin (kHsThreads threads, kHsThreads / 32 warps; a warp forms one row of a dense product
+// at a time, lanes over the columns). The bin's row of the half spectrum is the work vector: r_j is
+// replaced by w_j in the forward sweep and w_j by x_j in the backward one. Shared memory: two
+// vectors of Ns complex.
+constexpr int kHsThreads = 256;
+__device__ __forceinline__ float2 dense_row(const float2* __restrict__ Mrow, const float2* __restrict__ vec, int ns,
+                                            int lane) {
+  float ax = 0.f, ay = 0.f;
+  for (int m = lane; m < ns; m += 32) {
+    const float2 a = __ldg(Mrow + m), b = vec[m];
+    ax = fmaf(a.x, b.x, fmaf(-a.y, b.y, ax));
+    ay = fmaf(a.x, b.y, fmaf(a.y, b.x, ay));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ax += __shfl_xor_sync(0xffffffffu, ax, o);
+    ay += __shfl_xor_sync(0xffffffffu, ay, o);
+  }
+  return make_float2(ax, ay);
+}
+
+__global__ void __launch_bounds__(kHsThreads) k_hs_solve(float2* __restrict__ spec, int pitch, int ns, int nv,
+                                                         const float2* __restrict__ X, const float2* __restrict__ G,
+                                                         const float2* __restrict__ H, const float* __restrict__ hc,
+                                                         const float2* __restrict__ il2, int K) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* t1 = reinterpret_cast<float2*>(smraw);
+  float2* t2 = t1 + ns;
+  pdl_sync();
+  const int k = blockIdx.x;
+  const int nsp = ns * nv;
+  const size_t nn = (size_t)ns * ns;
+  float2* row = spec + (size_t)k * pitch;
+  const float2 sk = il2[k];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  // forward: w_j = X_j (r_j - A_j w_{j-1})
+  for (int j = 0; j < nv; ++j) {
+    for (int r = threadIdx.x; r < ns; r += blockDim.x) {
+      const int p = j * ns + r;
+      float2 v = cmul(row[p], sk);
+      if (j > 0) {
+#pragma unroll
+        for (int d = -1; d <= 1; ++d) {
+          const int m = r + d;
+          if (m < 0 || m >= ns) continue;
+          const float a = hcoef(hc, nsp, 1 + d, p);
+          const float2 w = row[(j - 1) * ns + m];
+          v.x -= a * w.x;
+          v.y -= a * w.y;
+        }
+      }
+      t1[r] = v;
+    }
+    __syncthreads();
+    const float2* Xj = X + ((size_t)j * K + k) * nn;
+    for (int r = warp; r < ns; r += nw) {
+      const float2 w = dense_row(Xj + (size_t)r * ns, t1, ns, lane);
+      if (lane == 0) row[j * ns + r] = w;
+    }
+    __syncthreads();
+  }
+  // backward: x_j = w_j - G_j x_{j+1} (- H_0 x_2 for j = 0)
+  for (int j = nv - 2; j >= 0; --j) {
+    for (int r = threadIdx.x; r < ns; r += blockDim.x) {
+      t1[r] = row[(j + 1) * ns + r];
+      if (j == 0) t2[r] = row[2 * ns + r];
+    }
+    __syncthreads();
+    const float2* Gj = G + ((size_t)j * K + k) * nn;
+    const float2* Hk = H + (size_t)k * nn;
+    for (int r = warp; r < ns; r += nw) {
+      float2 s = dense_row(Gj + (size_t)r * ns, t1, ns, lane);
+      if (j == 0) {
+        const float2 s2 = dense_row(Hk + (size_t)r * ns, t2, ns, lane);
+        s.x += s2.x;
+        s.y += s2.y;
+      }
+      if (lane == 0) {
+        const float2 w = row[j * ns + r];
+        row[j * ns + r] = make_float2(w.x - s.x, w.y - s.y);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------- host
+namespace {
+int hs_grid(size_t n) {
+  const size_t g = (n + 255) / 256;
+  return (int)(g < (size_t)kRedBlocks ? g : (size_t)kRedBlocks);
+}
+int hs_grid2(size_t nn) {
+  const size_t g = (nn + 255) / 256;
+  return (int)(g < 256 ? g : 256);
+}
+}  // namespace
+
+int heston_build(Handle& h) {
+  const aao_problem& p = h.p;
+  const int ns = p.nx, nv = p.nv, nsp = ns * nv, K = h.K;
+  h.hs_ns = ns;
+  h.hs_nv = nv;
+  const double hs = p.s_max / ns, hv = p.v_max / nv, tau = h.tau;
+  const double r = p.r, kap = p.kappa, eta = p.eta, sig = p.sigma, rho = p.rho;
+  std::vector<double> c((size_t)kHsOff * nsp, 0.0), f(nsp, 0.0), u0(nsp);
+  // coefficient w of u(ii, jj) in the equation of unknown (i, j) (i, ii 1-based in s)
+  auto add = [&](int i, int j, int ii, int jj, double w) {
+    const int pt = j * ns + i - 1;
+    if (jj == nv) {  // v = v_max: u = s
+      f[pt] += w * ii * hs;
+      return;
+    }
+    if (ii == 0) return;  // s = 0: u = 0
+    if (ii == ns + 1) {   // the ghost beyond s_max: u_{Ns+1} = u_{Ns-1} + 2 h_s
+      f[pt] += w * 2.0 * hs;
+      ii = ns - 1;
+    }
+    const int di = ii - i, dj = jj - j;
+    const int q = dj == 2 ? 9 : (dj + 1) * 3 + (di + 1);
+    c[(size_t)q * nsp + pt] += w;
+  };
+  for (int j = 0; j < nv; ++j) {
+    const double v = hv * j;
+    for (int i = 1; i <= ns; ++i) {
+      const double s = hs * i;
+      u0[j * ns + i - 1] = s > p.K ? s - p.K : 0.0;  // call payoff
+      if (j == 0) {  // u_t = kappa eta u_v + r s u_s - r u, u_v one-sided to second order
+        add(i, 0, i, 0, -3.0 * kap * eta / (2.0 * hv) - r);
+        add(i, 0, i, 1, 4.0 * kap * eta / (2.0 * hv));
+        add(i, 0, i, 2, -kap * eta / (2.0 * hv));
+        add(i, 0, i + 1, 0, r * s / (2.0 * hs));
+        add(i, 0, i - 1, 0, -r * s / (2.0 * hs));
+        continue;
+      }
+      const double dss = 0.5 * v * s * s / (hs * hs), dvv = 0.5 * sig * sig * v / (hv * hv);
+      const double dsv = sig * rho * s * v / (4.0 * hs * hv);
+      const double cs = r * s / (2.0 * hs), cv = kap * (eta - v) / (2.0 * hv);
+      add(i, j, i, j, -2.0 * dss - 2.0 * dvv - r);
+      add(i, j, i + 1, j, dss + cs);
+      add(i, j, i - 1, j, dss - cs);
+      add(i, j, i, j + 1, dvv + cv);
+      add(i, j, i, j - 1, dvv - cv);
+      add(i, j, i + 1, j + 1, dsv);
+      add(i, j, i - 1, j - 1, dsv);
+      add(i, j, i + 1, j - 1, -dsv);
+      add(i, j, i - 1, j + 1, -dsv);
+    }
+  }
+  std::vector<float> cf(c.size());
+  for (size_t e = 0; e < c.size(); ++e) {
+    c[e] *= 0.5 * tau;  // (tau/2) A
+    cf[e] = (float)c[e];
+  }
+  for (int q = 0; q < nsp; ++q) f[q] *= tau;  // tau f
+  auto up = [&](auto** dst, const auto& src) -> int {
+    using T = typename std::decay<decltype(src)>::type::value_type;
+    AAO_TRY_CUDA(cudaMalloc((void**)dst, sizeof(T) * src.size()));
+    AAO_TRY_CUDA(cudaMemcpyAsync(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, h.stream));
+    return AAO_OK;
+  };
+  AAO_TRY(up(&h.hs_c, c));
+  AAO_TRY(up(&h.hs_cf, cf));
+  AAO_TRY(up(&h.hs_tf, f));
+  AAO_TRY(up(&h.hs_u0, u0));
+
+  // step (b): block elimination over the v levels for every bin at once
+  const size_t nn = (size_t)ns * ns, slice = (size_t)K * nn;
+  AAO_TRY_CUDA(cudaMalloc(&h.hs_X, sizeof(float2) * slice * nv));
+  AAO_TRY_CUDA(cudaMalloc(&h.hs_G, sizeof(float2) * slice * (nv - 1)));
+  AAO_TRY_CUDA(cudaMalloc(&h.hs_H, sizeof(float2) * slice));
+  float2* T = nullptr;
+  AAO_TRY_CUDA(cudaMalloc(&T, sizeof(float2) * slice));
+  const dim3 g2(hs_grid2(nn), K);
+  int rc = AAO_OK;
+  for (int j = 0; j < nv && rc == AAO_OK; ++j) {
+    float2* Xj = h.hs_X + (size_t)j * slice;
+    k_hs_form_d<<<g2, 256, 0, h.stream>>>(Xj, j > 0 ? h.hs_G + (size_t)(j - 1) * slice : nullptr, ns, nsp, j, h.hs_cf,
+                                          h.muf);
+    rc = [&]() -> int { AAO_CHECK_LAUNCH(); return AAO_OK; }();
+    if (rc == AAO_OK) rc = gj_invert_batched(h.stream, Xj, ns, K);
+    if (rc != AAO_OK) break;
+    if (j == 0) {
+      k_hs_form_h<<<g2, 256, 0, h.stream>>>(h.hs_H, Xj, ns, nsp, h.hs_cf);
+      rc = [&]() -> int { AAO_CHECK_LAUNCH(); return AAO_OK; }();
+    }
+    if (rc == AAO_OK && j == 1) {
+      k_hs_form_t<<<g2, 256, 0, h.stream>>>(T, h.hs_H, ns, nsp, h.hs_cf);
+      rc = [&]() -> int { AAO_CHECK_LAUNCH(); return AAO_OK; }();
+    }
+    if (rc == AAO_OK && j < nv - 1) {
+      k_hs_form_g<<<g2, 256, 0, h.stream>>>(h.hs_G + (size_t)j * slice, Xj, j == 1 ? T : nullptr, ns, nsp, j,
+                                            h.hs_cf);
+      rc = [&]() -> int { AAO_CHECK_LAUNCH(); return AAO_OK; }();
+    }
+  }
+  cudaStreamSynchronize(h.stream);
+  cudaFree(T);
+  return rc;
+}
+
+int heston_rhs(Handle& h, double* b) {
+  k_hs_rhs<<<hs_grid(h.n), 256, 0, h.stream>>>(b, h.hs_ns, h.nx, h.nt, h.hs_c, h.hs_tf, h.hs_u0);
+  AAO_CHECK_LAUNCH();
+  return AAO_OK;
+}
+
+int heston_matvec(Handle& h, const void* x, bool x_is_float, double* y, const double* b, const double* V, int nd,
+                  int m) {
+  const int grid = hs_grid(h.n);
+  const double nn = (double)h.n;
+  const double bytes = nn * (x_is_float ? 4.0 : 8.0) + nn * 8.0 + (b ? nn * 8.0 : 0.0) + (V ? nn * 8.0 * nd : 0.0) +
+                       8.0 * kHsOff * h.nx;
+  const double flops = nn * (2.0 * kHsOff + 2.0 + (b ? 3.0 : 0.0) + (V ? 2.0 * nd : 0.0));
+  ProfScope ps(AAO_K_MATVEC, h.stream, bytes, flops);
+#define HS(IN, MODE, ND)                                                                                       \
+  AAO_TRY_CUDA(launch_pdl(k_hs_matvec<IN, MODE, ND>, grid, 256, 0, h.stream, (const IN*)x, y, b, h.hs_ns, h.nx, h.nt, \
+                          h.hs_c, V, h.n, h.part, h.scal, h.counter, m))
+  if (V && nd > 0) {
+    if (x_is_float) {
+      switch (nd) {
+        case 1: HS(float, 2, 1); break;
+        case 2: HS(float, 2, 2); break;
+        case 3: HS(float, 2, 3); break;
+        case 4: HS(float, 2, 4); break;
+        case 5: HS(float, 2, 5); break;
+        case 6: HS(float, 2, 6); break;
+        case 7: HS(float, 2, 7); break;
+        default: HS(float, 2, 8); break;
+      }
+    } else {
+      switch (nd) {
+        case 1: HS(double, 2, 1); break;
+        case 2: HS(double, 2, 2); break;
+        case 3: HS(double, 2, 3); break;
+        case 4: HS(double, 2, 4); break;
+        case 5: HS(double, 2, 5); break;
+        case 6: HS(double, 2, 6); break;
+        case 7: HS(double, 2, 7); break;
+        default: HS(double, 2, 8); break;
+      }
+    }
+  } else if (b) {
+    if (x_is_float) HS(float, 1, 0); else HS(double, 1, 0);
+  } else {
+    if (x_is_float) HS(float, 0, 0); else HS(double, 0, 0);
+  }
+#undef HS
+  AAO_CHECK_LAUNCH();
+  return AAO_OK;
+}
+
+int heston_solve_bins(Handle& h, void* spec) {
+  const size_t smem = 2 * sizeof(float2) * (size_t)h.hs_ns;
+  const double nn = (double)h.hs_ns * h.hs_ns;
+  const double bytes = (double)h.K * ((2.0 * h.hs_nv) * nn * 8.0 + 2.0 * h.nx * 8.0);
+  ProfScope ps(AAO_K_TRIDIAG, h.stream, bytes);
+  AAO_TRY_CUDA(launch_pdl(k_hs_solve, h.K, kHsThreads, smem, h.stream, reinterpret_cast<float2*>(spec), h.pitch,
+                          h.hs_ns, h.hs_nv, (const float2*)h.hs_X, (const float2*)h.hs_G, (const float2*)h.hs_H,
+                          (const float*)h.hs_cf, (const float2*)h.il2f, h.K));
+  AAO_CHECK_LAUNCH();
+  return AAO_OK;
+}
+
+}  // namespace aao

@@ -381,7 +381,8 @@ int build_tables(Handle& h) {
   const aao_problem& p = h.p;
   const int nx = h.nx, nt = h.nt, N = nt;
   h.tau = p.T / nt;
-  const bool riesz = p.op == AAO_OP_RIESZ;
+  const bool riesz = p.op == AAO_OP_RIESZ, heston = p.op == AAO_OP_HESTON;
+  const bool tridiag = !riesz && !heston;  // the one-dimensional Black-Scholes operators
   const double hS = p.s_max / (nx + 1);
   h.coef_rows = (p.op == AAO_OP_LOCALVOL) ? nt : 1;
   const size_t ncoef = (size_t)nx * h.coef_rows;
@@ -395,7 +396,7 @@ int build_tables(Handle& h) {
     gS[i] = exp(-l * l);
   }
   double* d_gS = nullptr;
-  if (!riesz) {
+  if (tridiag) {
   AAO_TRY_CUDA(cudaMalloc(&h.mL, sizeof(double) * ncoef));
   AAO_TRY_CUDA(cudaMalloc(&h.mD, sizeof(double) * ncoef));
   AAO_TRY_CUDA(cudaMalloc(&h.mU, sizeof(double) * ncoef));
@@ -417,7 +418,7 @@ int build_tables(Handle& h) {
   AAO_TRY_CUDA(cudaMalloc(&h.gR, sizeof(double) * (nt + 1)));
   AAO_TRY_CUDA(cudaMemcpyAsync(h.gL, gl.data(), sizeof(double) * (nt + 1), cudaMemcpyHostToDevice, h.stream));
   AAO_TRY_CUDA(cudaMemcpyAsync(h.gR, gr.data(), sizeof(double) * (nt + 1), cudaMemcpyHostToDevice, h.stream));
-  }  // !riesz
+  }  // tridiag
 
   // preconditioner operator tau * Abar: time mean of sigma^2 in closed form,
   // mean_k (s0 + b_i c_k)^2 = s0^2 + 2 s0 b_i mean(c) + b_i^2 mean(c^2)
@@ -476,7 +477,7 @@ int build_tables(Handle& h) {
     AAO_TRY_CUDA(cudaMemcpyAsync(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, h.stream));
     return AAO_OK;
   };
-  if (!riesz) {
+  if (tridiag) {
     AAO_TRY(up(&h.pL, pl)); AAO_TRY(up(&h.pD, pd)); AAO_TRY(up(&h.pU, pu));
     AAO_TRY(up(&h.pLf, plf)); AAO_TRY(up(&h.pDf, pdf)); AAO_TRY(up(&h.pUf, puf));
     // step (b) partition: T = 2^k >= 32 threads per bin with at most 16 rows each (up to T = 512),
@@ -533,6 +534,7 @@ int build_tables(Handle& h) {
   AAO_TRY_CUDA(cudaStreamSynchronize(h.stream));
   if (d_gS) cudaFree(d_gS);
   if (riesz) AAO_TRY(riesz_build(h));
+  if (heston) AAO_TRY(heston_build(h));
   return AAO_OK;
 }
 
@@ -541,7 +543,8 @@ void free_handle(Handle& h) {
                   h.muf, h.il2f, h.twf, h.lam, h.ilam, h.lamf, h.ilamf, h.spec, h.V, h.Z, h.w, h.scal, h.part,
                   h.counter, h.rz_chat, h.rz_tw, h.rz_hcol, h.rz_hrow, h.rz_hcl, h.tri, h.Vf, h.tri_fp,
                   h.tri_fv, h.tri_fpcr, h.rz_dk, h.rz_w,
-                  h.rz_part, h.rz_qh, h.rz_ql, h.rz_qth, h.rz_qtl, h.rz_err, h.rz_inv};
+                  h.rz_part, h.rz_qh, h.rz_ql, h.rz_qth, h.rz_qtl, h.rz_err, h.rz_inv, h.hs_c, h.hs_tf,
+                  h.hs_u0, h.hs_cf, h.hs_X, h.hs_G, h.hs_H};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (h.host_scal) cudaFreeHost(h.host_scal);
@@ -598,13 +601,14 @@ int matvec_t(Handle& h, const IN* x, double* y, const double* b, const double* V
 // y = M x; with b: y = b - M x (restart residual); with V (nd <= 8): first Gram-Schmidt pass
 int launch_matvec(Handle& h, const void* x, bool x_is_float, double* y, const double* b, const double* V, int nd,
                   int m, bool with_bnorm, float* yf) {
-  if (h.p.op == AAO_OP_RIESZ) {
+  if (h.p.op == AAO_OP_RIESZ || h.p.op == AAO_OP_HESTON) {
     if (b && with_bnorm) {
       ProfScope ps(AAO_K_OTHER, h.stream, 8.0 * (double)h.n);
       k_dot_self<<<wave_blocks(h, (const void*)k_dot_self, grid_for(h.n)), kThreads, 0, h.stream>>>(
           b, h.n, h.part, h.scal, S_BNORM2, h.counter);
       AAO_CHECK_LAUNCH();
     }
+    if (h.p.op == AAO_OP_HESTON) return heston_matvec(h, x, x_is_float, y, b, V, nd, m);
     return riesz_matvec(h, x, x_is_float, y, b, V, nd, m);
   }
   const double nn = (double)h.n;
@@ -631,6 +635,7 @@ void launch_coef_raw(cudaStream_t s, double* L, double* D, double* U, int nx, in
 
 int launch_rhs(Handle& h, double* b) {
   if (h.p.op == AAO_OP_RIESZ) return riesz_rhs(h, b);
+  if (h.p.op == AAO_OP_HESTON) return heston_rhs(h, b);
   k_rhs<<<grid_for(h.n), kThreads, 0, h.stream>>>(b, h.nx, h.nt, h.mL, h.mD, h.mU, h.coef_rows, h.gL, h.gR,
                                                    h.p.s_max / (h.nx + 1), h.p.K, h.p.payoff);
   AAO_CHECK_LAUNCH();
@@ -719,7 +724,7 @@ int run_fgmres(Handle& h, const double* b, double* x, double tol, int m, int max
   char* Zb = reinterpret_cast<char*>(h.Z);
   // mixed precision: the residual and update kernels also write an FP32 copy of the basis vector
   // that the next preconditioner apply reads (the Riesz matvec does not write one)
-  float* vf = (h.mixed && h.p.op != AAO_OP_RIESZ) ? h.Vf : nullptr;
+  float* vf = (h.mixed && h.p.op != AAO_OP_RIESZ && h.p.op != AAO_OP_HESTON) ? h.Vf : nullptr;
 
   int its = 0, restarts = 0, status = AAO_OK;
   double rel = 0.0, est = 0.0, bnorm = 0.0;

@@ -402,7 +402,10 @@ int run_precond(Handle& h, const double* v, void* z, bool z_is_float, const doub
 
   C* spec_b = spec;  // where step (b) leaves its result for step (c)
   TriRc rc;
-  if (h.p.op == AAO_OP_RIESZ) {
+  if (h.p.op == AAO_OP_HESTON) {
+    // step (b) with the two-dimensional operator: block elimination over the v levels
+    AAO_TRY(heston_solve_bins(h, spec));
+  } else if (h.p.op == AAO_OP_RIESZ) {
     // step (b) with the dense Toeplitz operator: the inverses of the shifted matrices (with
     // drift) or the eigendecomposition (symmetric), both made by aao_create
     void* res = nullptr;
@@ -527,8 +530,10 @@ int tune_precond(Handle& h) {
   const size_t rs = h.mixed ? 4 : 8;
   int dev = 0;
   AAO_TRY_CUDA(cudaGetDevice(&dev));
-  const bool riesz = h.p.op == AAO_OP_RIESZ;
-  const TuneKey key{dev, h.nx, h.nt, h.mixed ? 1 : 0, riesz ? (h.rz_sym ? 2 : 1) : 0, h.p.flags};
+  // the operators whose step (b) is not the tridiagonal solver
+  const bool riesz = h.p.op == AAO_OP_RIESZ || h.p.op == AAO_OP_HESTON;
+  const int opclass = h.p.op == AAO_OP_HESTON ? 3 : (h.p.op == AAO_OP_RIESZ ? (h.rz_sym ? 2 : 1) : 0);
+  const TuneKey key{dev, h.nx, h.nt, h.mixed ? 1 : 0, opclass, h.p.flags};
   TriRc trc;
   TriPart tpart;
   const bool rc_fits = !riesz && tri_rc_layout(h, rs, trc);
@@ -581,7 +586,7 @@ int tune_precond(Handle& h) {
   int rc = AAO_OK;
   // time the form the solver runs: mixed solves read an FP32 copy of the input (the zero bytes of
   // v serve as one)
-  const float* vf = (h.mixed && h.p.op != AAO_OP_RIESZ) ? reinterpret_cast<const float*>(v) : nullptr;
+  const float* vf = (h.mixed && !riesz) ? reinterpret_cast<const float*>(v) : nullptr;
   // widths: the powers of two up to pmax and, for the register FFT (nt >= 128, any width), the
   // widths whose tile count just fills the SMs once or twice (ceil(pairs / (k SMs))), so that no
   // SM is left without a tile

@@ -849,6 +849,52 @@ __global__ void __launch_bounds__(32 * kRzGemvRows) k_rz_gemv(const float2* __re
   if (lane == 0) out[(size_t)k * pitch + i] = make_float2(sx, sy);
 }
 
+}  // namespace
+
+int gj_invert_batched(cudaStream_t stream, float2* M, int n, int K) {
+  float2* piv = nullptr;
+  int* err = nullptr;
+  AAO_TRY_CUDA(cudaMalloc(&piv, sizeof(float2) * (size_t)K * kGW * kGW));
+  AAO_TRY_CUDA(cudaMalloc(&err, sizeof(int)));
+  int rc = AAO_OK;
+  if (cudaMemsetAsync(err, 0, sizeof(int), stream) != cudaSuccess) rc = AAO_ECUDA;
+  const size_t tsm = 2 * sizeof(float2) * kGW * kGW;
+  if (rc == AAO_OK &&
+      (cudaFuncSetAttribute(k_gj_rowscale, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm) != cudaSuccess ||
+       cudaFuncSetAttribute(k_gj_colfix, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm) != cudaSuccess ||
+       cudaFuncSetAttribute(k_gj_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGjSmem) !=
+           cudaSuccess))
+    rc = AAO_ECUDA;
+  const int nbt = (n + kGW - 1) / kGW;
+  const dim3 gup((n + 32 * kGjNT - 1) / (32 * kGjNT), (n + 127) / 128, K);
+  for (int p0 = 0; p0 < n && rc == AAO_OK; p0 += kGW) {
+    const int wp = n - p0 < kGW ? n - p0 : kGW;
+    k_gj_pivot<<<K, 256, 0, stream>>>(M, n, p0, wp, piv);
+    k_gj_rowscale<<<dim3(nbt, K), 256, tsm, stream>>>(M, n, p0, wp, piv);
+    k_gj_update_tc<<<gup, kGjThreads, kGjSmem, stream>>>(M, n, p0, wp, err, tcg::kWaitNs);
+    k_gj_colfix<<<dim3(nbt, K), 256, tsm, stream>>>(M, n, p0, wp, piv);
+    g_launches.fetch_add(3, std::memory_order_relaxed);
+    rc = [&]() -> int { AAO_CHECK_LAUNCH(); return AAO_OK; }();
+  }
+  int e = 0;
+  if (rc == AAO_OK) {
+    if (cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+      rc = AAO_ECUDA;
+  }
+  cudaFree(piv);
+  cudaFree(err);
+  if (rc == AAO_ECUDA) set_error("gauss-jordan inversion: a CUDA call failed");
+  if (rc != AAO_OK) return rc;
+  if (e) {
+    set_error("aao_create: a tensor-core update of the step (b) inverses gave up a bounded wait");
+    return AAO_TIMEOUT;
+  }
+  return AAO_OK;
+}
+
+namespace {
+
 int grid_for(size_t n) {
   size_t g = (n + kThreads - 1) / kThreads;
   return (int)(g < (size_t)kRedBlocks ? g : (size_t)kRedBlocks);
@@ -1066,39 +1112,7 @@ int riesz_build(Handle& h) {
   k_rz_form<<<dim3(256, K), 256, 0, h.stream>>>(h.rz_inv, nx, d_tcol, d_trow, h.muf);
   AAO_CHECK_LAUNCH();
   {
-    float2* piv = nullptr;
-    int* err = nullptr;
-    AAO_TRY_CUDA(cudaMalloc(&piv, sizeof(float2) * (size_t)K * kGW * kGW));
-    AAO_TRY_CUDA(cudaMalloc(&err, sizeof(int)));
-    AAO_TRY_CUDA(cudaMemsetAsync(err, 0, sizeof(int), h.stream));
-    const size_t tsm = 2 * sizeof(float2) * kGW * kGW;
-    AAO_TRY_CUDA(cudaFuncSetAttribute(k_gj_rowscale, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
-    AAO_TRY_CUDA(cudaFuncSetAttribute(k_gj_colfix, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
-    AAO_TRY_CUDA(cudaFuncSetAttribute(k_gj_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGjSmem));
-    const int nbt = (nx + kGW - 1) / kGW;
-    const dim3 gup((nx + 32 * kGjNT - 1) / (32 * kGjNT), (nx + 127) / 128, K);
-    int rc = AAO_OK;
-    for (int p0 = 0; p0 < nx && rc == AAO_OK; p0 += kGW) {
-      const int wp = nx - p0 < kGW ? nx - p0 : kGW;
-      k_gj_pivot<<<K, 256, 0, h.stream>>>(h.rz_inv, nx, p0, wp, piv);
-      k_gj_rowscale<<<dim3(nbt, K), 256, tsm, h.stream>>>(h.rz_inv, nx, p0, wp, piv);
-      k_gj_update_tc<<<gup, kGjThreads, kGjSmem, h.stream>>>(h.rz_inv, nx, p0, wp, err, tcg::kWaitNs);
-      k_gj_colfix<<<dim3(nbt, K), 256, tsm, h.stream>>>(h.rz_inv, nx, p0, wp, piv);
-      g_launches.fetch_add(3, std::memory_order_relaxed);
-      rc = [&]() -> int { AAO_CHECK_LAUNCH(); return AAO_OK; }();
-    }
-    int e = 0;
-    if (rc == AAO_OK) {
-      AAO_TRY_CUDA(cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, h.stream));
-      AAO_TRY_CUDA(cudaStreamSynchronize(h.stream));
-    }
-    cudaFree(piv);
-    cudaFree(err);
-    if (rc != AAO_OK) return rc;
-    if (e) {
-      set_error("aao_create: a tensor-core update of the Riesz inverses gave up a bounded wait");
-      return AAO_TIMEOUT;
-    }
+    AAO_TRY(gj_invert_batched(h.stream, h.rz_inv, nx, K));
     AAO_TRY_CUDA(cudaMalloc(&h.rz_w, sizeof(float2) * (size_t)K * h.pitch));
     AAO_TRY_CUDA(cudaMemsetAsync(h.rz_w, 0, sizeof(float2) * (size_t)K * h.pitch, h.stream));
   }

@@ -37,9 +37,11 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_struct_layout_matches_header():
-    # int32 x 6, double x 9, pointer
-    assert ctypes.sizeof(aao.AaoProblem) == 6 * 4 + 9 * 8 + 8
+    # int32 x 6, double x 9, pointer, then the Heston fields: int32 x 2, double x 4
+    assert ctypes.sizeof(aao.AaoProblem) == 6 * 4 + 9 * 8 + 8 + 2 * 4 + 4 * 8
     assert aao.AaoProblem.alpha.offset == 24 + 8 * 8
+    assert aao.AaoProblem.nv.offset == 24 + 9 * 8 + 8
+    assert aao.AaoProblem.v_max.offset == 24 + 9 * 8 + 8 + 8 + 3 * 8
     assert ctypes.sizeof(aao.AaoStats) == 4 * 4 + 3 * 8
 
 
