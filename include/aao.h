@@ -272,6 +272,13 @@ int aao_fault_inject(aao_handle* h, int mask, double wait_ms);
    converge within 64 sweeps for some eigenvalue). */
 int aao_sym_eig(int n, double* A_host, double* w_host);
 
+/* Bounds-checked build (diagnostics; the paper has no counterpart). A library compiled with
+   -DAAO_CHECK (libaao_check.so) tests the index of every guarded global store in the
+   preconditioner, solver, Riesz and Heston kernels; a failed test skips the store (no fault) and
+   marks its source file. This call synchronises the device and returns how many source files saw a
+   failed test since the last call (0 in the normal build, whose tests compile away). */
+unsigned int aao_check_failures(void);
+
 /* Message of the calling thread's most recent failure ("" if none). */
 const char* aao_last_error(void);
 

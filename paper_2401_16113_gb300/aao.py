@@ -29,7 +29,7 @@ EXPORTS = ["aao_create", "aao_destroy", "aao_rhs", "aao_matvec", "precond_apply"
            "aao_mlp_create", "aao_mlp_destroy", "aao_mlp_params", "aao_mlp_grad", "aao_mlp_adam_step",
            "aao_mlp_train", "aao_mlp_forward", "aao_mlp_normalization", "alpha_mlp_predict",
            "fgmres_solve", "fgmres_solve_host", "aao_last_error", "aao_launch_count",
-           "aao_profile_enable", "aao_profile_read", "aao_sym_eig", "aao_fault_inject"]
+           "aao_profile_enable", "aao_profile_read", "aao_sym_eig", "aao_fault_inject", "aao_check_failures"]
 AAO_INJECT_TC_NO_LOAD = 1
 
 
@@ -101,6 +101,7 @@ def load(path=None):
     lib.alpha_mlp_predict.argtypes = [vp, fp, ctypes.POINTER(dp), ctypes.POINTER(ip)]
     lib.aao_sym_eig.argtypes = [ip, ctypes.POINTER(dp), ctypes.POINTER(dp)]
     lib.aao_fault_inject.argtypes = [vp, ip, dp]
+    lib.aao_check_failures.restype = ctypes.c_uint
     lib.aao_last_error.restype = ctypes.c_char_p
     lib.aao_launch_count.restype = ctypes.c_uint64
     lib.aao_profile_enable.argtypes = [ctypes.c_int]

@@ -43,6 +43,37 @@ extern std::atomic<uint64_t> g_launches;
     if (s_ != AAO_OK) return s_; \
   } while (0)
 
+// ------------------------------------------------------------------ bounds-checked build
+// Built with -DAAO_CHECK (build.build(check=True): _build_check/libaao_check.so), device code tests
+// the index of each global store it guards with AAO_DCHECK(cond): a failed test sets this
+// translation unit's device word and the store is skipped (no fault); aao_check_failures() reads and
+// clears the words of every unit. In the normal build AAO_DCHECK(cond) is the constant true and the
+// tests compile away.
+#ifdef AAO_CHECK
+static __device__ unsigned int g_aao_check = 0u;
+__device__ __forceinline__ bool aao_dcheck(bool ok) {
+  if (!ok) atomicOr(&g_aao_check, 1u);
+  return ok;
+}
+#define AAO_DCHECK(cond) ::aao::aao_dcheck((cond))
+// this unit's word (read and cleared), and the sum over units
+#define AAO_CHECK_WORD_FN(name)                                                        \
+  unsigned int name() {                                                                \
+    unsigned int v = 0u, z = 0u;                                                       \
+    if (cudaMemcpyFromSymbol(&v, g_aao_check, sizeof v) != cudaSuccess) v = 1u;        \
+    cudaMemcpyToSymbol(g_aao_check, &z, sizeof z);                                     \
+    return v;                                                                          \
+  }
+#else
+#define AAO_DCHECK(cond) true
+#define AAO_CHECK_WORD_FN(name) \
+  unsigned int name() { return 0u; }
+#endif
+unsigned int check_word_precond();
+unsigned int check_word_krylov();
+unsigned int check_word_riesz();
+unsigned int check_word_heston();
+
 // ------------------------------------------------------------------ device timing
 // When enabled, every launch inside a ProfScope is bracketed by two CUDA events recorded on
 // the launching stream; aao_profile_read sums their elapsed times per kernel class.

@@ -241,6 +241,11 @@ int aao_sym_eig(int n, double* A_host, double* w_host) {
   return AAO_OK;
 }
 
+unsigned int aao_check_failures(void) {
+  cudaDeviceSynchronize();
+  return check_word_precond() + check_word_krylov() + check_word_riesz() + check_word_heston();
+}
+
 const char* aao_last_error(void) { return t_last_error.c_str(); }
 
 uint64_t aao_launch_count(void) { return g_launches.load(); }

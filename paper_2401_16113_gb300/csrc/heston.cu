@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(256) k_hs_matvec(const IN* __restrict__ x, dou
       v = __ldg(b + e) - v;
       acc[0] = fma(v, v, acc[0]);
     }
-    y[e] = v;
+    if (AAO_DCHECK(e < n)) y[e] = v;
     if (MODE == 2) {
 #pragma unroll
       for (int q = 0; q < ND; ++q) acc[q] = fma(__ldg(V + (size_t)q * vstride + e), v, acc[q]);
@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(kHsThreads) k_hs_solve(float2* __restrict__ sp
     const float2* Xj = X + ((size_t)j * K + k) * nn;
     for (int r = warp; r < ns; r += nw) {
       const float2 w = dense_row(Xj + (size_t)r * ns, t1, ns, lane);
-      if (lane == 0) row[j * ns + r] = w;
+      if (lane == 0 && AAO_DCHECK(j * ns + r < nsp && nsp <= pitch)) row[j * ns + r] = w;
     }
     __syncthreads();
   }
@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(kHsThreads) k_hs_solve(float2* __restrict__ sp
       }
       if (lane == 0) {
         const float2 w = row[j * ns + r];
-        row[j * ns + r] = make_float2(w.x - s.x, w.y - s.y);
+        if (AAO_DCHECK(j * ns + r < nsp)) row[j * ns + r] = make_float2(w.x - s.x, w.y - s.y);
       }
     }
     __syncthreads();
@@ -348,6 +348,8 @@ __global__ void __launch_bounds__(kHsThreads) k_hs_solve(float2* __restrict__ sp
 }  // namespace
 
 // ------------------------------------------------------------------------------- host
+AAO_CHECK_WORD_FN(check_word_heston)
+
 namespace {
 int hs_grid(size_t n) {
   const size_t g = (n + 255) / 256;

@@ -132,6 +132,7 @@ __global__ void __launch_bounds__(kThreads) k_matvec(const IN* __restrict__ x, d
     const int strip = (int)(r / nt);
     const int t0 = (int)(r - (long long)strip * nt);
     const int t1 = (int)((long long)t0 + (r1 - r) < (long long)nt ? (long long)t0 + (r1 - r) : (long long)nt);
+    if (!AAO_DCHECK(t0 >= 0 && t1 <= nt && strip * kMvCols < nx)) break;
     matvec_item<IN, MODE, ND, NA>(x, y, b, nx, t0, t1, strip * kMvCols, L, D, U, rows, V, vstride, acc, yf);
     r += t1 - t0;
   }
@@ -372,6 +373,8 @@ int ensure_workspace(Handle& h, int m) {
 }
 
 }  // namespace
+
+AAO_CHECK_WORD_FN(check_word_krylov)
 
 // ----------------------------------------------------------------------------------------
 // tables

@@ -209,6 +209,7 @@ __global__ void __launch_bounds__(mr_threads<R>(), 2)
     const R h = (R)0.5;
     const int x = x0 + 2 * p;
     C* out = spec + (size_t)k * pitch + x;
+    if (!AAO_DCHECK(k <= N / 2 && x + 1 <= pitch)) continue;
     if (x < nx) out[0] = cmk<C>(h * (zk.x + zn.x), h * (zk.y - zn.y));
     if (x + 1 < nx) out[1] = cmk<C>(h * (zk.y + zn.y), h * (zn.x - zk.x));
   }
@@ -252,7 +253,7 @@ __global__ void __launch_bounds__(mr_threads<R>(), 2)
     if (x < nx) {
       const C y = Y[t * P + (c >> 1)];
       const R val = ((c & 1) ? -y.y : y.x) * __ldg(&ilam[t]);
-      z[(size_t)t * nx + x] = (OUT)val;
+      if (AAO_DCHECK(t < N)) z[(size_t)t * nx + x] = (OUT)val;
     }
   }
 }
@@ -498,6 +499,8 @@ int run_precond(Handle& h, const double* v, void* z, bool z_is_float, const doub
 }
 
 }  // namespace
+
+AAO_CHECK_WORD_FN(check_word_precond)
 
 int launch_precond(Handle& h, const double* v, void* z, bool z_is_float, const double* in_scale, const float* vf) {
   if (h.mixed) return run_precond<float>(h, v, z, z_is_float, in_scale, vf);

@@ -124,6 +124,7 @@ __device__ __forceinline__ void fft_fwd_tile_smem(const IN* __restrict__ v, C_t<
     const C xb = cmk<C>(h * (zk.y + zn.y), h * (zn.x - zk.x));
     const int x = x0 + 2 * p;
     C* out = spec + (size_t)k * pitch + x;
+    if (!AAO_DCHECK(k <= half && x + 1 <= pitch)) continue;
     if (x < nx) out[0] = xa;
     if (x + 1 < nx) out[1] = xb;
   }
@@ -168,7 +169,7 @@ __device__ __forceinline__ void fft_inv_tile_smem(const C_t<R>* __restrict__ spe
     for (int t = tr; t < N; t += tstep) {
       const C y = data[t * P + (c >> 1)];
       const R val = ((c & 1) ? -y.y : y.x) * __ldg(&ilam[t]);
-      dst[(size_t)t * nx] = (OUT)val;
+      if (AAO_DCHECK(t < N)) dst[(size_t)t * nx] = (OUT)val;
     }
   }
 }
@@ -400,7 +401,8 @@ __device__ __forceinline__ void fft_fwd_tile_reg(const IN* __restrict__ v, C_t<R
         const C zn = u == 0 ? a[(8 - r) & 7] : b[7 - r];
         const C xa = cmk<C>(h * (zk.x + zn.x), h * (zk.y - zn.y));
         const C xb = cmk<C>(h * (zk.y + zn.y), h * (zn.x - zk.x));
-        store_pair(spec + (size_t)(ja + r * ns) * pitch + x, xa, xb, ok0, ok1);
+        if (AAO_DCHECK(ja + r * ns <= N / 2 && x + 1 <= pitch))
+          store_pair(spec + (size_t)(ja + r * ns) * pitch + x, xa, xb, ok0, ok1);
       }
     }
 #pragma unroll
@@ -409,7 +411,8 @@ __device__ __forceinline__ void fft_fwd_tile_reg(const IN* __restrict__ v, C_t<R
       const C zn = u == 0 ? b[7 - r] : a[7 - r];
       const C xa = cmk<C>(h * (zk.x + zn.x), h * (zk.y - zn.y));
       const C xb = cmk<C>(h * (zk.y + zn.y), h * (zn.x - zk.x));
-      store_pair(spec + (size_t)(jb + r * ns) * pitch + x, xa, xb, ok0, ok1);
+      if (AAO_DCHECK(jb + r * ns <= N / 2 && x + 1 <= pitch))
+        store_pair(spec + (size_t)(jb + r * ns) * pitch + x, xa, xb, ok0, ok1);
     }
   }
 }
@@ -457,6 +460,7 @@ __device__ __forceinline__ void fft_inv_tile_reg(const C_t<R>* __restrict__ spec
       const R la = __ldg(&ilam[ta]), lb = __ldg(&ilam[tb]);
       OUT* da = z + (size_t)ta * nx + x;
       OUT* db = z + (size_t)tb * nx + x;
+      if (!AAO_DCHECK(ta < N && tb < N)) continue;
       if (ok0) { da[0] = (OUT)(a[r].x * la); db[0] = (OUT)(b[r].x * lb); }
       if (ok1) { da[1] = (OUT)(-a[r].y * la); db[1] = (OUT)(-b[r].y * lb); }
     }
@@ -633,7 +637,7 @@ __device__ __forceinline__ void tridiag_bin(C_t<R>* __restrict__ spec, int nx, i
   if (valid) {
     for (int i = tid; i < nx; i += T) {
       const int L = i / ch, j = i - L * ch;
-      row[i] = dd[L * cs + j];
+      if (AAO_DCHECK(i < pitch)) row[i] = dd[L * cs + j];
     }
   }
 }
@@ -918,7 +922,7 @@ __global__ void __launch_bounds__(512) k_tridiag_part(C_t<R>* __restrict__ spec,
     for (int L = l / ch, j = l - (l / ch) * ch; L < T;) {
       const int i = L * ch + j;
       if (i >= nx) break;
-      row[i] = cmul(sd[L * cs + j], sk);
+      if (AAO_DCHECK(k < K && i < pitch)) row[i] = cmul(sd[L * cs + j], sk);
       j += dj;
       L += dL;
       if (j >= ch) { j -= ch; ++L; }
@@ -1116,7 +1120,7 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1)
     for (int L = l / ch, j = l - (l / ch) * ch; L < T;) {
       const int i = L * ch + j;
       if (i >= nx) break;
-      row[i] = W[L * cs + j];
+      if (AAO_DCHECK(k < K && i < pitch)) row[i] = W[L * cs + j];
       j += dj;
       L += dL;
       if (j >= ch) { j -= ch; ++L; }

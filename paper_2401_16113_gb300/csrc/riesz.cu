@@ -361,7 +361,8 @@ __global__ void __launch_bounds__(160, 1) k_rz_tc(const float2* __restrict__ A, 
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int bin = b0 + 16 * half + j;
-          if (bin < Kb) Ps[(size_t)bin * ldp + n] = make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
+          if (bin < Kb && AAO_DCHECK(n < ldp))
+            Ps[(size_t)bin * ldp + n] = make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
         }
       }
     } else if (tid == 0) {
@@ -788,7 +789,7 @@ __global__ void __launch_bounds__(kGjThreads, 1) k_gj_update_tc(float2* __restri
 #pragma unroll
         for (int jj = 0; jj < 16; ++jj) {
           const int j = jc + jj;
-          if (j < nx && (j < p0 || j >= pe))
+          if (j < nx && (j < p0 || j >= pe) && AAO_DCHECK(i < nx))
             dst[j] = make_float2(cv[jj].x - __uint_as_float(v[2 * jj]), cv[jj].y - __uint_as_float(v[2 * jj + 1]));
         }
       }
@@ -846,10 +847,12 @@ __global__ void __launch_bounds__(32 * kRzGemvRows) k_rz_gemv(const float2* __re
     sx += __shfl_down_sync(0xffffffffu, sx, o);
     sy += __shfl_down_sync(0xffffffffu, sy, o);
   }
-  if (lane == 0) out[(size_t)k * pitch + i] = make_float2(sx, sy);
+  if (lane == 0 && AAO_DCHECK(i < pitch)) out[(size_t)k * pitch + i] = make_float2(sx, sy);
 }
 
 }  // namespace
+
+AAO_CHECK_WORD_FN(check_word_riesz)
 
 int gj_invert_batched(cudaStream_t stream, float2* M, int n, int K) {
   float2* piv = nullptr;

@@ -18,7 +18,7 @@ def declared_functions():
             continue
         src = open(os.path.join(ROOT, "include", hdr)).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-        names += re.findall(r"^\s*(?:int|const char\*|uint64_t|void)\s+\**\s*([A-Za-z_]\w*)\s*\(", src, flags=re.M)
+        names += re.findall(r"^\s*(?:int|const char\*|uint64_t|void|unsigned int)\s+\**\s*([A-Za-z_]\w*)\s*\(", src, flags=re.M)
     return sorted(set(names))
 
 
@@ -98,3 +98,13 @@ def test_product_code_never_references_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src, f
+
+
+@pytest.mark.slow
+def test_checked_build_compiles_and_exports():
+    """The bounds-checked variant (-DAAO_CHECK) builds for sm_103a and exports the same entry points."""
+    from paper_2401_16113_gb300 import build
+    lib = ctypes.CDLL(build.build(check=True))
+    for name in aao.EXPORTS:
+        assert hasattr(lib, name), name
+    lib.aao_check_failures.restype = ctypes.c_uint
