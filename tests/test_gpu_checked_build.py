@@ -14,7 +14,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 SCRIPT = r"""
 import sys
-sys.path.insert(0, %r)
+sys.path.insert(0, ROOT_PATH)
 import numpy as np, torch
 from oracle import aao_oracle as O
 from paper_2401_16113_gb300 import aao, build, workloads as W
@@ -41,7 +41,7 @@ for p in cases:
     assert st["status"] == 0, (p["op"], st)
     h.close()
 print("FAILURES", aao.load().aao_check_failures(), "WORST", worst)
-""" % ROOT
+""".replace("ROOT_PATH", repr(ROOT))
 
 
 def test_checked_build_runs_clean():
