@@ -36,7 +36,72 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and learned-alpha sections")
     ap.add_argument("--train-instances", type=int, default=20000)
+    ap.add_argument("--case", default=None, choices=sorted(CASES),
+                    help="time one workload alone (create, then --steps solves) and print its own JSON line; "
+                         "for profiling single kernels, not the bench line")
     return ap.parse_args()
+
+
+# single workloads for --case: (problem builder, tol, m)
+CASES = {
+    "localvol_2047x2048": lambda W: (W.localvol_2047x2048("mixed"), TOL, 30),
+    "localvol_2047x2048_recompute": lambda W: (W.with_(W.localvol_2047x2048("mixed"), step_b="recompute"), TOL, 30),
+    "localvol_2047x2048_factored": lambda W: (W.with_(W.localvol_2047x2048("mixed"), step_b="factored"), TOL, 30),
+    "riesz_1023x512": lambda W: (W.riesz_1023x512(), TOL, W.riesz_1023x512()["m"]),
+    "riesz_sym_1023x512": lambda W: (W.riesz_sym_1023x512(), TOL, W.riesz_sym_1023x512()["m"]),
+    "heston_set1_nt96": lambda W: (W.heston_set1(96), 1e-9, 40),
+    "heston_set1_nt192": lambda W: (W.heston_set1(192), 1e-9, 40),
+}
+
+
+def run_case(args):
+    """One workload alone: aao_create, the right-hand side, --warmup untimed and --steps timed solves
+    (CUDA events, L2 flushed before each), step (b)'s device time per apply from the library's
+    event timers in one more solve."""
+    import torch
+
+    from paper_2401_16113_gb300 import aao, build as B, workloads as W
+
+    B.build()
+    aao.load()
+    stream = torch.cuda.current_stream()
+    p, tol, m = CASES[args.case](W)
+    n = W.unknowns(p)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    h = aao.aao_create(p)
+    torch.cuda.synchronize()
+    create_s = time.time() - t0
+    b = torch.empty(n, dtype=torch.float64, device="cuda")
+    aao.aao_rhs(h, b)
+    x = torch.zeros_like(b)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        x.zero_()
+        aao.fgmres_solve(h, b, x, tol, m, 300)
+    times, st = [], None
+    for _ in range(args.steps):
+        x.zero_()
+        flush.fill_(1.0)
+        ms, st = _timed(stream, lambda: aao.fgmres_solve(h, b, x, tol, m, 300))
+        times.append(ms)
+    aao.aao_profile_enable(None)
+    x.zero_()
+    aao.fgmres_solve(h, b, x, tol, m, 300)
+    torch.cuda.synchronize()
+    classes = {c: aao.aao_profile_read(c) for c in aao.KERNEL_CLASSES}
+    tri = classes["tridiag"]
+    aao.aao_profile_enable([])
+    h.close()
+    times.sort()
+    ms = times[len(times) // 2] if times else None
+    print(json.dumps({"case": args.case, "unknowns": n, "create_s": create_s, "ms_median": ms,
+                      "value": n / (ms / 1e3) if ms else None, "unit": "unknowns/s", "steps": args.steps,
+                      "iterations": st["iterations"] if st else None,
+                      "rel_residual": st["rel_residual"] if st else None,
+                      "step_b_ms_per_apply": tri[1] / max(tri[0], 1), "step_b_applies": tri[0],
+                      "kernel_ms_per_solve": {c: v[1] for c, v in classes.items() if v[0]},
+                      "launches_per_solve": {c: v[0] for c, v in classes.items() if v[0]}}))
 
 
 def workload():
@@ -806,7 +871,9 @@ def main():
     args = parse()
     if args.steps is None:
         args.steps = 3 if args.impl == "reference" else 200
-    if args.impl == "reference":
+    if args.case is not None:
+        run_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -305,6 +305,7 @@ struct Handle {
   // tau f (boundary data), the payoff; step (b) per bin and v level: X_j = D_j^{-1},
   // G_j = X_j C'_j (j < nv - 1), H_0 = X_0 E_0 (FP32 complex, [j][k][ns][ns])
   int hs_ns = 0, hs_nv = 0;
+  int hs_C = 1;  // CTAs per bin (thread-block cluster) of the step (b) apply
   double *hs_c = nullptr, *hs_tf = nullptr, *hs_u0 = nullptr;
   float* hs_cf = nullptr;
   float2 *hs_X = nullptr, *hs_G = nullptr, *hs_H = nullptr;

@@ -22,12 +22,16 @@
 //                (diagonal) that the one-sided u_v puts at (0, 2). At create, per bin:
 //                D_0 = B_0, D_j = B_j - A_j G_{j-1}, X_j = D_j^{-1} (batched Gauss-Jordan on the tensor
 //                cores, shared with the Riesz operator), G_j = X_j C'_j with C'_1 = C_1 - A_1 H_0 and
-//                C'_j = C_j otherwise, H_0 = X_0 E_0. Per apply (k_hs_solve, one CTA per bin):
+//                C'_j = C_j otherwise, H_0 = X_0 E_0. Per apply (k_hs_solve, one cluster of CTAs per bin):
 //                w_0 = X_0 r_0, w_j = X_j (r_j - A_j w_{j-1}); x_{Nv-1} = w_{Nv-1},
 //                x_j = w_j - G_j x_{j+1} (j >= 1), x_0 = w_0 - G_0 x_1 - H_0 x_2.
 #include <math.h>
 
+#include <algorithm>
+
 #include <vector>
+
+#include <cooperative_groups.h>
 
 #include "krylov_dev.cuh"
 
@@ -36,6 +40,7 @@ namespace aao {
 namespace {
 
 using namespace kdev;
+namespace cg = cooperative_groups;
 
 constexpr int kHsOff = 10;  // stencil offsets, in this order:
 __host__ __device__ constexpr int hs_di(int q) { return q < 9 ? (q % 3) - 1 : 0; }
@@ -44,63 +49,82 @@ __host__ __device__ constexpr int hs_dj(int q) { return q < 9 ? (q / 3) - 1 : 2;
 template <typename T> __device__ __forceinline__ double ldx(const T* p) { return (double)*p; }
 template <> __device__ __forceinline__ double ldx<float>(const float* p) { return widen(*p); }
 
-// y = M x over all (t, p): one thread per unknown (grid-stride). MODE 0: y = M x; MODE 1: y = b - M x
-// and ||y||^2 (restart residual; sigma_0, g set by the last block); MODE 2: y = M x and the
-// projections V_q . y, q < ND.
+// y = M x over all (t, p), by tiles of one time level t and rb v levels (grid-stride over the tiles).
+// A tile first stages s = x_t + x_{t-1} on its rows and one row below and two above (the stencil's
+// reach; rows outside the grid are zero) in shared memory, then each point sums the stencil from
+// there: one FP64 addition per point for s instead of one per point and offset. The sums run over
+// the offsets in the same order as a point-by-point evaluation, so y is the same bit for bit. MODE 0:
+// y = M x; MODE 1: y = b - M x and ||y||^2 (restart residual; sigma_0, g set by the last block);
+// MODE 2: y = M x and the projections V_q . y, q < ND.
 template <typename IN, int MODE, int ND>
 __global__ void __launch_bounds__(256) k_hs_matvec(const IN* __restrict__ x, double* __restrict__ y,
-                                                   const double* __restrict__ b, int ns, int nsp, int nt,
+                                                   const double* __restrict__ b, int ns, int nv, int nt, int rb,
                                                    const double* __restrict__ c, const double* __restrict__ V,
                                                    size_t vstride, double* __restrict__ part,
                                                    double* __restrict__ scal, unsigned int* __restrict__ counter,
                                                    int m) {
+  extern __shared__ double s_sm[];  // (rb + 3) x ns: s on v rows j0 - 1 .. j0 + rb + 1
   pdl_sync();
   constexpr int NA = MODE == 2 ? ND : 1;
   double acc[NA];
 #pragma unroll
   for (int q = 0; q < NA; ++q) acc[q] = 0.0;
-  const size_t n = (size_t)nsp * nt;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    const int t = (int)(e / nsp), p = (int)(e - (size_t)t * nsp);
+  const int nsp = ns * nv;
+  const int nrb = (nv + rb - 1) / rb;
+  const int tiles = nt * nrb;
+  for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int t = tile / nrb, j0 = (tile - t * nrb) * rb;
+    const int j1 = min(nv, j0 + rb);
+    const int hn = (j1 - j0 + 3) * ns;  // staged entries
     const IN* xt = x + (size_t)t * nsp;
     const IN* xm = t > 0 ? xt - nsp : nullptr;
-    double as = 0.0;  // ((tau/2) A s)_p, s = x_t + x_{t-1}
-#pragma unroll
-    for (int q = 0; q < kHsOff; ++q) {
-      const double cq = __ldg(c + (size_t)q * nsp + p);
-      if (cq != 0.0) {
-        const int nb = p + hs_di(q) + hs_dj(q) * ns;
-        if (nb >= 0 && nb < nsp) as = fma(cq, ldx(xt + nb) + (xm ? ldx(xm + nb) : 0.0), as);
+    __syncthreads();  // the previous tile's reads of s_sm are done
+    for (int e = threadIdx.x; e < hn; e += blockDim.x) {
+      const int r = e / ns;
+      const int jj = j0 - 1 + r;
+      double v = 0.0;
+      if (jj >= 0 && jj < nv) {
+        const int p = jj * ns + (e - r * ns);
+        v = ldx(xt + p) + (xm ? ldx(xm + p) : 0.0);
       }
+      s_sm[e] = v;
     }
-    const double x0 = ldx(xt + p), x1 = xm ? ldx(xm + p) : 0.0;
-    double v = (x0 - x1) - as;
-    if (MODE == 1) {
-      v = __ldg(b + e) - v;
-      acc[0] = fma(v, v, acc[0]);
-    }
-    if (AAO_DCHECK(e < n)) y[e] = v;
-    if (MODE == 2) {
+    __syncthreads();
+    const int np = (j1 - j0) * ns;
+    for (int e = threadIdx.x; e < np; e += blockDim.x) {
+      const int p = j0 * ns + e;  // spatial index; its staged entry is e + ns
+      double as = 0.0;            // ((tau/2) A s)_p
+      // Zero coefficients are skipped, tested on the bits of a 64-bit integer load (an FP64
+      // comparison, which the compiler substitutes for a bit test of a double, takes the FP64 pipe). A nonzero coefficient never reaches past the grid (the boundary couplings are zero:
+      // u(0, v) = 0, the ghost node folded into the i - 1 entry, no v - 1 entry on v = 0, u(s, v_max)
+      // in the data), so the staged index is only clamped into the buffer; the offset (0, 2)
+      // appears on the v = 0 row alone.
 #pragma unroll
-      for (int q = 0; q < ND; ++q) acc[q] = fma(__ldg(V + (size_t)q * vstride + e), v, acc[q]);
+      for (int q = 0; q < kHsOff; ++q) {
+        if (q == kHsOff - 1 && p >= ns) break;
+        const long long cb = __ldg(reinterpret_cast<const long long*>(c) + (size_t)q * nsp + p);
+        if ((cb << 1) != 0) {
+          const int ln = min(max(e + ns + hs_di(q) + hs_dj(q) * ns, 0), hn - 1);
+          as = fma(__longlong_as_double(cb), s_sm[ln], as);
+        }
+      }
+      const double x0 = ldx(xt + p), x1 = xm ? ldx(xm + p) : 0.0;
+      double v = (x0 - x1) - as;
+      const size_t ge = (size_t)t * nsp + p;
+      if (MODE == 1) {
+        v = __ldg(b + ge) - v;
+        acc[0] = fma(v, v, acc[0]);
+      }
+      if (AAO_DCHECK(ge < (size_t)nsp * nt)) y[ge] = v;
+      if (MODE == 2) {
+#pragma unroll
+        for (int q = 0; q < ND; ++q) acc[q] = fma(__ldg(V + (size_t)q * vstride + ge), v, acc[q]);
+      }
     }
   }
   if constexpr (MODE == 0) return;
-  __shared__ double red[8][NA];
-  {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int q = 0; q < NA; ++q) {
-      const double v = warp_sum(acc[q]);
-      if (lane == 0) red[warp][q] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < NA) {
-      double s = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
-      part[(size_t)blockIdx.x * kPartLd + threadIdx.x] = s;
-    }
-  }
+  // block partials, then the last block sums them with all its threads (one round trip)
+  block_sums_wide<NA>(acc, NA, part + (size_t)blockIdx.x * kPartLd);
   __shared__ bool am_last;
   __threadfence();
   __syncthreads();
@@ -108,23 +132,18 @@ __global__ void __launch_bounds__(256) k_hs_matvec(const IN* __restrict__ x, dou
   __syncthreads();
   if (!am_last) return;
   __threadfence();
-  if (threadIdx.x == 0) {
-    for (int q = 0; q < NA; ++q) {
-      double s = 0.0;
-      for (unsigned bb = 0; bb < gridDim.x; ++bb) s += __ldcg(part + (size_t)bb * kPartLd + q);
-      if (MODE == 2) {
-        scal[S_D1 + q] = s;
-      } else {
-        scal[S_BETA2] = s;
-        const double beta = sqrt(s);
-        scal[S_SIG] = beta > 0.0 ? 1.0 / beta : 0.0;
-        scal[S_G] = beta;
-        for (int k = 1; k <= m; ++k) scal[S_G + k] = 0.0;
-        scal[S_FLAG] = isfinite(s) ? 0.0 : 1.0;
-      }
+  finish_sums_wide<NA>(part, (int)gridDim.x, NA, [&](int q, double v) {
+    if (MODE == 2) {
+      scal[S_D1 + q] = v;
+    } else {
+      scal[S_BETA2] = v;
+      const double beta = sqrt(v);
+      scal[S_SIG] = beta > 0.0 ? 1.0 / beta : 0.0;
+      scal[S_G] = beta;
+      for (int k = 1; k <= m; ++k) scal[S_G + k] = 0.0;
+      scal[S_FLAG] = isfinite(v) ? 0.0 : 1.0;
     }
-    *counter = 0u;
-  }
+  }, counter);
 }
 
 // b_t = tau f + [t = 0] (u0 + (tau/2) A u0)
@@ -259,25 +278,63 @@ __global__ void k_hs_form_t(float2* __restrict__ T, const float2* __restrict__ H
 }
 
 // ------------------------------------------------------------------------------- step (b): apply
-// One CTA per bin (kHsThreads threads, kHsThreads / 32 warps; a warp forms one row of a dense product
-// at a time, lanes over the columns). The bin's row of the half spectrum is the work vector: r_j is
-// replaced by w_j in the forward sweep and w_j by x_j in the backward one. Shared memory: two
-// vectors of Ns complex.
+// A thread-block cluster of C CTAs per bin (kHsThreads threads each). The sweeps are sequential in j,
+// and each step is one dense Ns x Ns product, so the CTAs of a cluster split its rows: CTA c owns
+// rows [c P, (c + 1) P), P = ceil(Ns / C), and a warp forms two of them at a time (lanes over the
+// columns, four loads in flight per row and lane). Each finished entry is written into every CTA's
+// copy of the vector (distributed shared memory), and one cluster barrier per step publishes it.
+// The copies are double-buffered by the parity of j: a CTA writes step j's vector into slot j & 1
+// while a slower CTA may still read step j - 1's from slot (j - 1) & 1, and step j + 1 reuses that
+// slot only after the barrier of step j, which every CTA reaches after its reads. w_j reaches the
+// bin's spectrum row (global) after that barrier, when no CTA still reads r_j there. Shared
+// memory: the product's input t (Ns complex) and the two slots (2 Ns complex).
 constexpr int kHsThreads = 256;
-__device__ __forceinline__ float2 dense_row(const float2* __restrict__ Mrow, const float2* __restrict__ vec, int ns,
-                                            int lane) {
-  float ax = 0.f, ay = 0.f;
-  for (int m = lane; m < ns; m += 32) {
-    const float2 a = __ldg(Mrow + m), b = vec[m];
-    ax = fmaf(a.x, b.x, fmaf(-a.y, b.y, ax));
-    ay = fmaf(a.x, b.y, fmaf(a.y, b.x, ay));
+constexpr int kHsMaxC = 8;
+
+// y_i = M_i . vec for the two rows M_0, M_1 (row 1 only if live1); every lane gets both sums.
+// Eight loads per row and lane are issued before the first is used (Ns <= 256 in one round).
+__device__ __forceinline__ void dense_rows2(const float2* __restrict__ M0, const float2* __restrict__ M1, bool live1,
+                                            const float2* __restrict__ vec, int ns, int lane, float2& y0, float2& y1) {
+  float ax0 = 0.f, ay0 = 0.f, ax1 = 0.f, ay1 = 0.f;
+  for (int m0 = 0; m0 < ns; m0 += 256) {
+    float2 a0[8], a1[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int m = m0 + 32 * u + lane;
+      a0[u] = m < ns ? __ldg(M0 + m) : make_float2(0.f, 0.f);
+      a1[u] = (live1 && m < ns) ? __ldg(M1 + m) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int m = m0 + 32 * u + lane;
+      const float2 b = m < ns ? vec[m] : make_float2(0.f, 0.f);
+      ax0 = fmaf(a0[u].x, b.x, fmaf(-a0[u].y, b.y, ax0));
+      ay0 = fmaf(a0[u].x, b.y, fmaf(a0[u].y, b.x, ay0));
+      ax1 = fmaf(a1[u].x, b.x, fmaf(-a1[u].y, b.y, ax1));
+      ay1 = fmaf(a1[u].x, b.y, fmaf(a1[u].y, b.x, ay1));
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    ax += __shfl_xor_sync(0xffffffffu, ax, o);
-    ay += __shfl_xor_sync(0xffffffffu, ay, o);
+    ax0 += __shfl_xor_sync(0xffffffffu, ax0, o);
+    ay0 += __shfl_xor_sync(0xffffffffu, ay0, o);
+    ax1 += __shfl_xor_sync(0xffffffffu, ax1, o);
+    ay1 += __shfl_xor_sync(0xffffffffu, ay1, o);
   }
-  return make_float2(ax, ay);
+  y0 = make_float2(ax0, ay0);
+  y1 = make_float2(ax1, ay1);
+}
+
+// Ask the L2 to fetch rows [r0, r1) of the Ns x Ns block M (one bulk prefetch; the start and end are
+// rounded down to 16 bytes, so the range stays inside the block's allocation). A hint only: the
+// next step's loads then find the rows in L2 while this step's barrier chain runs.
+__device__ __forceinline__ void prefetch_rows_l2(const float2* M, int ns, int r0, int r1) {
+  if (r1 <= r0) return;
+  const uintptr_t a = reinterpret_cast<uintptr_t>(M + (size_t)r0 * ns);
+  const uintptr_t e = reinterpret_cast<uintptr_t>(M + (size_t)r1 * ns);
+  const uintptr_t a16 = a & ~(uintptr_t)15, e16 = e & ~(uintptr_t)15;
+  if (e16 <= a16) return;
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a16), "r"((unsigned)(e16 - a16)) : "memory");
 }
 
 __global__ void __launch_bounds__(kHsThreads) k_hs_solve(float2* __restrict__ spec, int pitch, int ns, int nv,
@@ -285,17 +342,28 @@ __global__ void __launch_bounds__(kHsThreads) k_hs_solve(float2* __restrict__ sp
                                                          const float2* __restrict__ H, const float* __restrict__ hc,
                                                          const float2* __restrict__ il2, int K) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  float2* t1 = reinterpret_cast<float2*>(smraw);
-  float2* t2 = t1 + ns;
+  float2* t = reinterpret_cast<float2*>(smraw);
+  float2* slot = t + ns;  // slot[(j & 1) * ns + r]
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks(), c = (int)cl.block_rank();
   pdl_sync();
-  const int k = blockIdx.x;
+  const int k = blockIdx.x / C;
   const int nsp = ns * nv;
   const size_t nn = (size_t)ns * ns;
   float2* row = spec + (size_t)k * pitch;
   const float2 sk = il2[k];
+  const int P = (ns + C - 1) / C;
+  const int r0 = min(ns, c * P), r1 = min(ns, r0 + P);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  float2* peer = lane < C ? cl.map_shared_rank(slot, lane) : nullptr;  // lane q writes CTA q's copy
+  const float2* Hk = H + (size_t)k * nn;
+  if (threadIdx.x == 0) prefetch_rows_l2(X + (size_t)k * nn, ns, r0, r1);
+
   // forward: w_j = X_j (r_j - A_j w_{j-1})
   for (int j = 0; j < nv; ++j) {
+    if (threadIdx.x == 0)  // the next step's block: X_{j+1}, or G_{nv-2} for the first backward step
+      prefetch_rows_l2(j + 1 < nv ? X + ((size_t)(j + 1) * K + k) * nn : G + ((size_t)(nv - 2) * K + k) * nn, ns, r0, r1);
+    const float2* wprev = slot + ((j - 1) & 1) * ns;
     for (int r = threadIdx.x; r < ns; r += blockDim.x) {
       const int p = j * ns + r;
       float2 v = cmul(row[p], sk);
@@ -305,43 +373,71 @@ __global__ void __launch_bounds__(kHsThreads) k_hs_solve(float2* __restrict__ sp
           const int m = r + d;
           if (m < 0 || m >= ns) continue;
           const float a = hcoef(hc, nsp, 1 + d, p);
-          const float2 w = row[(j - 1) * ns + m];
+          const float2 w = wprev[m];
           v.x -= a * w.x;
           v.y -= a * w.y;
         }
       }
-      t1[r] = v;
+      t[r] = v;
     }
     __syncthreads();
     const float2* Xj = X + ((size_t)j * K + k) * nn;
-    for (int r = warp; r < ns; r += nw) {
-      const float2 w = dense_row(Xj + (size_t)r * ns, t1, ns, lane);
-      if (lane == 0 && AAO_DCHECK(j * ns + r < nsp && nsp <= pitch)) row[j * ns + r] = w;
+    const int off = (j & 1) * ns;
+    for (int ra = r0 + warp; ra < r1; ra += 2 * nw) {
+      const int rb = ra + nw;
+      const bool lb = rb < r1;
+      float2 ya, yb;
+      dense_rows2(Xj + (size_t)ra * ns, Xj + (size_t)(lb ? rb : ra) * ns, lb, t, ns, lane, ya, yb);
+      if (peer && AAO_DCHECK(off + ra < 2 * ns)) {
+        peer[off + ra] = ya;
+        if (lb) peer[off + rb] = yb;
+      }
     }
-    __syncthreads();
+    cl.sync();
+    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x)
+      if (AAO_DCHECK(j * ns + r < nsp && nsp <= pitch)) row[j * ns + r] = slot[off + r];
   }
-  // backward: x_j = w_j - G_j x_{j+1} (- H_0 x_2 for j = 0)
+  // backward: x_{nv-1} = w_{nv-1} (in slot (nv - 1) & 1); x_j = w_j - G_j x_{j+1}, and for j = 0
+  // also - H_0 x_2 (x_1 in slot 1, x_2 in slot 0). x_0 is needed by no other row, so it goes to
+  // the spectrum row only.
   for (int j = nv - 2; j >= 0; --j) {
-    for (int r = threadIdx.x; r < ns; r += blockDim.x) {
-      t1[r] = row[(j + 1) * ns + r];
-      if (j == 0) t2[r] = row[2 * ns + r];
+    if (threadIdx.x == 0 && j > 0) {
+      prefetch_rows_l2(G + ((size_t)(j - 1) * K + k) * nn, ns, r0, r1);
+      if (j == 1) prefetch_rows_l2(Hk, ns, r0, r1);
     }
-    __syncthreads();
+    const float2* xnext = slot + ((j + 1) & 1) * ns;
     const float2* Gj = G + ((size_t)j * K + k) * nn;
-    const float2* Hk = H + (size_t)k * nn;
-    for (int r = warp; r < ns; r += nw) {
-      float2 s = dense_row(Gj + (size_t)r * ns, t1, ns, lane);
+    const int off = (j & 1) * ns;
+    for (int ra = r0 + warp; ra < r1; ra += 2 * nw) {
+      const int rb = ra + nw;
+      const bool lb = rb < r1;
+      float2 sa, sb;
+      dense_rows2(Gj + (size_t)ra * ns, Gj + (size_t)(lb ? rb : ra) * ns, lb, xnext, ns, lane, sa, sb);
       if (j == 0) {
-        const float2 s2 = dense_row(Hk + (size_t)r * ns, t2, ns, lane);
-        s.x += s2.x;
-        s.y += s2.y;
+        float2 ha, hb;
+        dense_rows2(Hk + (size_t)ra * ns, Hk + (size_t)(lb ? rb : ra) * ns, lb, slot, ns, lane, ha, hb);
+        sa.x += ha.x;
+        sa.y += ha.y;
+        sb.x += hb.x;
+        sb.y += hb.y;
       }
-      if (lane == 0) {
-        const float2 w = row[j * ns + r];
-        if (AAO_DCHECK(j * ns + r < nsp)) row[j * ns + r] = make_float2(w.x - s.x, w.y - s.y);
+      const float2 wa = row[j * ns + ra];
+      const float2 xa = make_float2(wa.x - sa.x, wa.y - sa.y);
+      float2 xb = make_float2(0.f, 0.f);
+      if (lb) {
+        const float2 wb = row[j * ns + rb];
+        xb = make_float2(wb.x - sb.x, wb.y - sb.y);
+      }
+      if (lane == 0 && AAO_DCHECK(j * ns + ra < nsp)) {
+        row[j * ns + ra] = xa;
+        if (lb) row[j * ns + rb] = xb;
+      }
+      if (j > 0 && peer && AAO_DCHECK(off + ra < 2 * ns)) {
+        peer[off + ra] = xa;
+        if (lb) peer[off + rb] = xb;
       }
     }
-    __syncthreads();
+    if (j > 0) cl.sync();
   }
 }
 
@@ -360,6 +456,8 @@ int hs_grid2(size_t nn) {
   return (int)(g < 256 ? g : 256);
 }
 }  // namespace
+
+int heston_pick_cluster(Handle& h);
 
 int heston_build(Handle& h) {
   const aao_problem& p = h.p;
@@ -461,6 +559,7 @@ int heston_build(Handle& h) {
   }
   cudaStreamSynchronize(h.stream);
   cudaFree(T);
+  if (rc == AAO_OK) rc = heston_pick_cluster(h);
   return rc;
 }
 
@@ -472,14 +571,22 @@ int heston_rhs(Handle& h, double* b) {
 
 int heston_matvec(Handle& h, const void* x, bool x_is_float, double* y, const double* b, const double* V, int nd,
                   int m) {
-  const int grid = hs_grid(h.n);
+  // tiles of rb v levels: at most about 2048 points, and at least kRedBlocks tiles where the grid
+  // allows (small grids otherwise leave SMs idle); an equal number of tiles per block
+  const int ns = h.hs_ns, nv = h.hs_nv;
+  const int per_t = (kRedBlocks + h.nt - 1) / h.nt;  // v-level blocks per time level wanted
+  const int rb = std::max(1, std::min({nv, 2048 / ns, (nv + per_t - 1) / per_t}));
+  const size_t tiles = (size_t)h.nt * ((nv + rb - 1) / rb);
+  const size_t per = (tiles + kRedBlocks - 1) / kRedBlocks;
+  const int grid = (int)((tiles + per - 1) / per);
+  const size_t smem = sizeof(double) * (size_t)(rb + 3) * ns;
   const double nn = (double)h.n;
   const double bytes = nn * (x_is_float ? 4.0 : 8.0) + nn * 8.0 + (b ? nn * 8.0 : 0.0) + (V ? nn * 8.0 * nd : 0.0) +
                        8.0 * kHsOff * h.nx;
-  const double flops = nn * (2.0 * kHsOff + 2.0 + (b ? 3.0 : 0.0) + (V ? 2.0 * nd : 0.0));
+  const double flops = nn * (2.0 * kHsOff + 3.0 + (b ? 3.0 : 0.0) + (V ? 2.0 * nd : 0.0));
   ProfScope ps(AAO_K_MATVEC, h.stream, bytes, flops);
 #define HS(IN, MODE, ND)                                                                                       \
-  AAO_TRY_CUDA(launch_pdl(k_hs_matvec<IN, MODE, ND>, grid, 256, 0, h.stream, (const IN*)x, y, b, h.hs_ns, h.nx, h.nt, \
+  AAO_TRY_CUDA(launch_pdl(k_hs_matvec<IN, MODE, ND>, grid, 256, smem, h.stream, (const IN*)x, y, b, ns, nv, h.nt, rb, \
                           h.hs_c, V, h.n, h.part, h.scal, h.counter, m))
   if (V && nd > 0) {
     if (x_is_float) {
@@ -515,14 +622,59 @@ int heston_matvec(Handle& h, const void* x, bool x_is_float, double* y, const do
   return AAO_OK;
 }
 
+namespace {
+cudaLaunchConfig_t hs_solve_config(const Handle& h, int C, cudaLaunchAttribute* attr) {
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(h.K * C);
+  cfg.blockDim = dim3(kHsThreads);
+  cfg.dynamicSmemBytes = 3 * sizeof(float2) * (size_t)h.hs_ns;
+  cfg.stream = h.stream;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+}  // namespace
+
+// Cluster size of step (b): the time of one apply goes as (waves of clusters) x (rows per CTA), so
+// take C in {1, 2, 4, 8} minimising ceil(K / clusters resident at once) / C; on a tie the smaller C,
+// which needs fewer waves (each wave pays the chain of per-step barriers again).
+int heston_pick_cluster(Handle& h) {
+  int best = 0;
+  double cost = 0.0;
+  for (int C = 1; C <= kHsMaxC; C <<= 1) {
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = hs_solve_config(h, C, attr);
+    cfg.gridDim = dim3(C);
+    int nc = 0;
+    AAO_TRY_CUDA(cudaOccupancyMaxActiveClusters(&nc, (const void*)k_hs_solve, &cfg));
+    if (nc < 1) continue;
+    const double c = (double)((h.K + nc - 1) / nc) / C;
+    if (best == 0 || c < cost) {
+      best = C;
+      cost = c;
+    }
+  }
+  if (best == 0) {
+    set_error("aao_create: no cluster of the Heston step (b) kernel fits on the GPU");
+    return AAO_EUNSUPPORTED;
+  }
+  h.hs_C = best;
+  return AAO_OK;
+}
+
 int heston_solve_bins(Handle& h, void* spec) {
-  const size_t smem = 2 * sizeof(float2) * (size_t)h.hs_ns;
   const double nn = (double)h.hs_ns * h.hs_ns;
   const double bytes = (double)h.K * ((2.0 * h.hs_nv) * nn * 8.0 + 2.0 * h.nx * 8.0);
   ProfScope ps(AAO_K_TRIDIAG, h.stream, bytes);
-  AAO_TRY_CUDA(launch_pdl(k_hs_solve, h.K, kHsThreads, smem, h.stream, reinterpret_cast<float2*>(spec), h.pitch,
-                          h.hs_ns, h.hs_nv, (const float2*)h.hs_X, (const float2*)h.hs_G, (const float2*)h.hs_H,
-                          (const float*)h.hs_cf, (const float2*)h.il2f, h.K));
+  cudaLaunchAttribute attr[1];
+  const cudaLaunchConfig_t cfg = hs_solve_config(h, h.hs_C, attr);
+  AAO_TRY_CUDA(cudaLaunchKernelEx(&cfg, k_hs_solve, reinterpret_cast<float2*>(spec), h.pitch, h.hs_ns, h.hs_nv,
+                                  (const float2*)h.hs_X, (const float2*)h.hs_G, (const float2*)h.hs_H,
+                                  (const float*)h.hs_cf, (const float2*)h.il2f, h.K));
   AAO_CHECK_LAUNCH();
   return AAO_OK;
 }
