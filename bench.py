@@ -50,6 +50,7 @@ CASES = {
     "riesz_1023x512": lambda W: (W.riesz_1023x512(), TOL, W.riesz_1023x512()["m"]),
     "riesz_sym_1023x512": lambda W: (W.riesz_sym_1023x512(), TOL, W.riesz_sym_1023x512()["m"]),
     "heston_set1_nt96": lambda W: (W.heston_set1(96), 1e-9, 40),
+    "heston_set1_nt128": lambda W: (W.heston_set1(128), 1e-9, 40),
     "heston_set1_nt192": lambda W: (W.heston_set1(192), 1e-9, 40),
 }
 
@@ -178,23 +179,42 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------ roofline bits
-def source_sha():
-    h = hashlib.sha256()
+def _includes(path):
+    import re
+    src = open(path, encoding="utf-8", errors="replace").read()
+    return re.findall(r'^\s*#\s*include\s+"([^"]+)"', src, flags=re.M)
+
+
+def source_sha(files=None):
+    """Hash of the named sources of the CUDA library (paths relative to its csrc directory) and of
+    every quoted header they include, transitively: the translation units a kernel is built from.
+    Without names, every file of the directory."""
     cs = os.path.join(ROOT, "paper_2401_16113_gb300", "csrc")
-    for f in sorted(os.listdir(cs)):
-        h.update(open(os.path.join(cs, f), "rb").read())
+    todo = list(files) if files else sorted(os.listdir(cs))
+    seen = []
+    while todo:
+        f = os.path.normpath(os.path.join(cs, todo.pop(0)))
+        if f in seen or not os.path.isfile(f):
+            continue
+        seen.append(f)
+        todo += [os.path.relpath(os.path.join(os.path.dirname(f), i), cs) for i in _includes(f)]
+    h = hashlib.sha256()
+    for f in sorted(seen):
+        h.update(os.path.relpath(f, cs).encode())
+        h.update(open(f, "rb").read())
     return h.hexdigest()[:16]
 
 
 def ncu_traffic(kernel_class):
-    """DRAM bytes per launch from the committed ncu summary, if taken on the current source."""
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current sources of the
+    kernel's translation units (the entry's "sources")."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         d = json.load(open(path))
     except (OSError, ValueError):
         return None
     e = d.get(kernel_class)
-    if not e or e.get("source_sha") != source_sha():
+    if not e or e.get("source_sha") != source_sha(e.get("sources")):
         return None
     return e.get("dram_bytes_per_launch")
 

@@ -292,20 +292,22 @@ constexpr int kHsThreads = 256;
 constexpr int kHsMaxC = 8;
 
 // y_i = M_i . vec for the two rows M_0, M_1 (row 1 only if live1); every lane gets both sums.
-// Eight loads per row and lane are issued before the first is used (Ns <= 256 in one round).
+// U loads per row and lane (U = ceil(Ns / 32) up to 8) are issued before the first is used, so a
+// row of up to 256 columns takes one round and no load slot is masked off for the common widths.
+template <int U>
 __device__ __forceinline__ void dense_rows2(const float2* __restrict__ M0, const float2* __restrict__ M1, bool live1,
                                             const float2* __restrict__ vec, int ns, int lane, float2& y0, float2& y1) {
   float ax0 = 0.f, ay0 = 0.f, ax1 = 0.f, ay1 = 0.f;
-  for (int m0 = 0; m0 < ns; m0 += 256) {
-    float2 a0[8], a1[8];
+  for (int m0 = 0; m0 < ns; m0 += 32 * U) {
+    float2 a0[U], a1[U];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < U; ++u) {
       const int m = m0 + 32 * u + lane;
       a0[u] = m < ns ? __ldg(M0 + m) : make_float2(0.f, 0.f);
       a1[u] = (live1 && m < ns) ? __ldg(M1 + m) : make_float2(0.f, 0.f);
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < U; ++u) {
       const int m = m0 + 32 * u + lane;
       const float2 b = m < ns ? vec[m] : make_float2(0.f, 0.f);
       ax0 = fmaf(a0[u].x, b.x, fmaf(-a0[u].y, b.y, ax0));
@@ -337,6 +339,7 @@ __device__ __forceinline__ void prefetch_rows_l2(const float2* M, int ns, int r0
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a16), "r"((unsigned)(e16 - a16)) : "memory");
 }
 
+template <int U>
 __global__ void __launch_bounds__(kHsThreads) k_hs_solve(float2* __restrict__ spec, int pitch, int ns, int nv,
                                                          const float2* __restrict__ X, const float2* __restrict__ G,
                                                          const float2* __restrict__ H, const float* __restrict__ hc,
@@ -387,7 +390,7 @@ __global__ void __launch_bounds__(kHsThreads) k_hs_solve(float2* __restrict__ sp
       const int rb = ra + nw;
       const bool lb = rb < r1;
       float2 ya, yb;
-      dense_rows2(Xj + (size_t)ra * ns, Xj + (size_t)(lb ? rb : ra) * ns, lb, t, ns, lane, ya, yb);
+      dense_rows2<U>(Xj + (size_t)ra * ns, Xj + (size_t)(lb ? rb : ra) * ns, lb, t, ns, lane, ya, yb);
       if (peer && AAO_DCHECK(off + ra < 2 * ns)) {
         peer[off + ra] = ya;
         if (lb) peer[off + rb] = yb;
@@ -412,10 +415,10 @@ __global__ void __launch_bounds__(kHsThreads) k_hs_solve(float2* __restrict__ sp
       const int rb = ra + nw;
       const bool lb = rb < r1;
       float2 sa, sb;
-      dense_rows2(Gj + (size_t)ra * ns, Gj + (size_t)(lb ? rb : ra) * ns, lb, xnext, ns, lane, sa, sb);
+      dense_rows2<U>(Gj + (size_t)ra * ns, Gj + (size_t)(lb ? rb : ra) * ns, lb, xnext, ns, lane, sa, sb);
       if (j == 0) {
         float2 ha, hb;
-        dense_rows2(Hk + (size_t)ra * ns, Hk + (size_t)(lb ? rb : ra) * ns, lb, slot, ns, lane, ha, hb);
+        dense_rows2<U>(Hk + (size_t)ra * ns, Hk + (size_t)(lb ? rb : ra) * ns, lb, slot, ns, lane, ha, hb);
         sa.x += ha.x;
         sa.y += ha.y;
         sb.x += hb.x;
@@ -623,6 +626,20 @@ int heston_matvec(Handle& h, const void* x, bool x_is_float, double* y, const do
 }
 
 namespace {
+// the instance of k_hs_solve for Ns: U = ceil(Ns / 32) loads per row and lane, at most 8
+const void* hs_solve_kernel(int ns) {
+  switch ((ns + 31) / 32) {
+    case 1: return (const void*)k_hs_solve<1>;
+    case 2: return (const void*)k_hs_solve<2>;
+    case 3: return (const void*)k_hs_solve<3>;
+    case 4: return (const void*)k_hs_solve<4>;
+    case 5: return (const void*)k_hs_solve<5>;
+    case 6: return (const void*)k_hs_solve<6>;
+    case 7: return (const void*)k_hs_solve<7>;
+    default: return (const void*)k_hs_solve<8>;
+  }
+}
+
 cudaLaunchConfig_t hs_solve_config(const Handle& h, int C, cudaLaunchAttribute* attr) {
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = C;
@@ -650,7 +667,7 @@ int heston_pick_cluster(Handle& h) {
     cudaLaunchConfig_t cfg = hs_solve_config(h, C, attr);
     cfg.gridDim = dim3(C);
     int nc = 0;
-    AAO_TRY_CUDA(cudaOccupancyMaxActiveClusters(&nc, (const void*)k_hs_solve, &cfg));
+    AAO_TRY_CUDA(cudaOccupancyMaxActiveClusters(&nc, hs_solve_kernel(h.hs_ns), &cfg));
     if (nc < 1) continue;
     const double c = (double)((h.K + nc - 1) / nc) / C;
     if (best == 0 || c < cost) {
@@ -672,9 +689,9 @@ int heston_solve_bins(Handle& h, void* spec) {
   ProfScope ps(AAO_K_TRIDIAG, h.stream, bytes);
   cudaLaunchAttribute attr[1];
   const cudaLaunchConfig_t cfg = hs_solve_config(h, h.hs_C, attr);
-  AAO_TRY_CUDA(cudaLaunchKernelEx(&cfg, k_hs_solve, reinterpret_cast<float2*>(spec), h.pitch, h.hs_ns, h.hs_nv,
-                                  (const float2*)h.hs_X, (const float2*)h.hs_G, (const float2*)h.hs_H,
-                                  (const float*)h.hs_cf, (const float2*)h.il2f, h.K));
+  void* args[] = {&spec, (void*)&h.pitch, (void*)&h.hs_ns, (void*)&h.hs_nv, (void*)&h.hs_X, (void*)&h.hs_G,
+                  (void*)&h.hs_H, (void*)&h.hs_cf, (void*)&h.il2f, (void*)&h.K};
+  AAO_TRY_CUDA(cudaLaunchKernelExC(&cfg, hs_solve_kernel(h.hs_ns), args));
   AAO_CHECK_LAUNCH();
   return AAO_OK;
 }

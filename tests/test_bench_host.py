@@ -77,8 +77,29 @@ def test_traffic_record_is_used_only_on_its_own_sources(monkeypatch):
     import json
     B = load_bench()
     rec = json.load(open(os.path.join(B.ROOT, "profiles", "ncu_traffic.json")))["matvec"]
-    monkeypatch.setattr(B, "source_sha", lambda: rec["source_sha"])
+    monkeypatch.setattr(B, "source_sha", lambda files=None: rec["source_sha"])
     assert B.ncu_traffic("matvec") == rec["dram_bytes_per_launch"]
-    monkeypatch.setattr(B, "source_sha", lambda: "0" * 16)
+    monkeypatch.setattr(B, "source_sha", lambda files=None: "0" * 16)
     assert B.ncu_traffic("matvec") is None
     assert B.ncu_traffic("no_such_kernel") is None
+
+
+def test_source_hash_covers_a_kernels_translation_unit(monkeypatch, tmp_path):
+    """The traffic record's hash follows the named sources and the headers they include: a change
+    to another source leaves it alone, a change to an included header changes it."""
+    import shutil
+    B = load_bench()
+    root = tmp_path / "repo"
+    shutil.copytree(os.path.join(B.ROOT, "paper_2401_16113_gb300", "csrc"), root / "paper_2401_16113_gb300" / "csrc")
+    shutil.copytree(os.path.join(B.ROOT, "include"), root / "include")
+    monkeypatch.setattr(B, "ROOT", str(root))
+    cs = root / "paper_2401_16113_gb300" / "csrc"
+    h0 = B.source_sha(["krylov.cu"])
+    assert h0 == B.source_sha(["krylov.cu"])
+    (cs / "heston.cu").write_text((cs / "heston.cu").read_text() + "\n// edit\n")
+    assert B.source_sha(["krylov.cu"]) == h0
+    (cs / "aao_internal.cuh").write_text((cs / "aao_internal.cuh").read_text() + "\n// edit\n")
+    h1 = B.source_sha(["krylov.cu"])
+    assert h1 != h0
+    (root / "include" / "aao.h").write_text((root / "include" / "aao.h").read_text() + "\n/* edit */\n")
+    assert B.source_sha(["krylov.cu"]) != h1

@@ -44,7 +44,7 @@ def bound(p):
     return 20.0 * U32 * math.log2(2 * p["nt"]) / p["alpha"]
 
 
-SHAPES = [(3, 3, 2), (8, 4, 8), (13, 5, 12), (40, 20, 16), (64, 32, 32)]
+SHAPES = [(3, 3, 2), (8, 4, 8), (13, 5, 12), (40, 20, 16), (64, 32, 32), (100, 6, 6), (300, 3, 4)]
 
 
 @pytest.mark.parametrize("ns,nv,nt", SHAPES)
