@@ -358,8 +358,11 @@ int tri_factors_t(Handle& h, int lgT) {
   return AAO_OK;
 }
 
+// skip_b: steps (a) and (c) only (the FFT-tile autotuner of the dense operators, whose step (b) does
+// not depend on the tile and would dominate the timing)
 template <typename R>
-int run_precond(Handle& h, const double* v, void* z, bool z_is_float, const double* in_scale, const float* vf) {
+int run_precond(Handle& h, const double* v, void* z, bool z_is_float, const double* in_scale, const float* vf,
+                bool skip_b = false) {
   using C = C_t<R>;
   const int N = h.nt, nx = h.nx;
   const bool mr = h.mr.nst > 0;  // nt not a power of two: the mixed-radix kernels
@@ -403,7 +406,9 @@ int run_precond(Handle& h, const double* v, void* z, bool z_is_float, const doub
 
   C* spec_b = spec;  // where step (b) leaves its result for step (c)
   TriRc rc;
-  if (h.p.op == AAO_OP_HESTON) {
+  if (skip_b) {
+    // timing of steps (a) and (c) alone
+  } else if (h.p.op == AAO_OP_HESTON) {
     // step (b) with the two-dimensional operator: block elimination over the v levels
     AAO_TRY(heston_solve_bins(h, spec));
   } else if (h.p.op == AAO_OP_RIESZ) {
@@ -507,9 +512,6 @@ int launch_precond(Handle& h, const double* v, void* z, bool z_is_float, const d
   return run_precond<double>(h, v, z, z_is_float, in_scale, nullptr);
 }
 
-// FFT tile autotuner: time the whole apply for every admissible tile width 2P (P = 1, 2, 4, ...)
-// on this problem's sizes and keep the fastest. Every tile width computes identical results
-// (each column's transform runs the same operations in the same order); only speed differs.
 int build_tri_factors(Handle& h) {
   if (h.p.flags == AAO_FLAG_STEPB_RECOMPUTE) return AAO_OK;  // the recomputing solver needs none
   const size_t rsize = h.mixed ? sizeof(float) : sizeof(double);
@@ -529,6 +531,11 @@ struct TuneKey {
 std::mutex g_tune_mu;
 std::map<TuneKey, std::pair<int, bool>> g_tune;  // -> (fft_p, tri_rc)
 
+// FFT tile autotuner: time the apply for every admissible tile width 2P (P = 1, 2, 4, ...) on this
+// problem's sizes and keep the fastest: the whole apply for the tridiagonal operators, steps (a)
+// and (c) alone for the dense ones (their step (b) is the same for every tile and would take most
+// of the tuning time). Every tile width computes identical results (each column's transform runs
+// the same operations in the same order); only speed differs.
 int tune_precond(Handle& h) {
   const size_t rs = h.mixed ? 4 : 8;
   int dev = 0;
@@ -606,11 +613,16 @@ int tune_precond(Handle& h) {
   for (size_t ci = 0; ci < cand.size() && rc == AAO_OK; ++ci) {
     const int P = cand[ci];
     h.fft_p = P;
-    rc = launch_precond(h, v, z, h.mixed, nullptr, vf);
+    auto apply = [&]() -> int {
+      if (!riesz) return launch_precond(h, v, z, h.mixed, nullptr, vf);
+      if (h.mixed) return run_precond<float>(h, v, z, h.mixed, nullptr, vf, true);
+      return run_precond<double>(h, v, z, h.mixed, nullptr, nullptr, true);
+    };
+    rc = apply();
     float pbest = 1e30f;
     for (int r = 0; r < 5 && rc == AAO_OK; ++r) {
       cudaEventRecord(e0, h.stream);
-      rc = launch_precond(h, v, z, h.mixed, nullptr, vf);
+      rc = apply();
       cudaEventRecord(e1, h.stream);
       cudaEventSynchronize(e1);
       float ms = 0.f;

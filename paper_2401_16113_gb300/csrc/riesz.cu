@@ -551,6 +551,35 @@ __global__ void __launch_bounds__(256) k_gj_pivot(const float2* __restrict__ M, 
   for (int e = threadIdx.x; e < kGW * kGW; e += blockDim.x) Pk[e] = S[e / kGW][e % kGW];
 }
 
+// Products of two kGW x kGW complex tiles in shared memory, for rowscale and colfix: thread t
+// forms the 4 x 4 block of outputs (rows 4 (t / 16) .., columns 4 (t % 16) ..), so one round of
+// loads (four entries of L's column, two float4 of R's row) feeds 16 complex FMAs.
+// acc[u][v] = sum_c L[(4 (t / 16) + u) kGW + c] R[c kGW + 4 (t % 16) + v], c < cn.
+__device__ __forceinline__ void tile_mm4x4(const float2* __restrict__ L, const float2* __restrict__ R, int cn,
+                                           float2 (&acc)[4][4]) {
+  const int r0 = 4 * (threadIdx.x >> 4), c0 = 4 * (threadIdx.x & 15);
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = make_float2(0.f, 0.f);
+  for (int c = 0; c < cn; ++c) {
+    float2 l[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) l[u] = L[(r0 + u) * kGW + c];
+    const float4 ra = *reinterpret_cast<const float4*>(R + c * kGW + c0);
+    const float4 rb = *reinterpret_cast<const float4*>(R + c * kGW + c0 + 2);
+    const float2 rr[4] = {make_float2(ra.x, ra.y), make_float2(ra.z, ra.w), make_float2(rb.x, rb.y),
+                          make_float2(rb.z, rb.w)};
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        acc[u][v].x = fmaf(l[u].x, rr[v].x, fmaf(-l[u].y, rr[v].y, acc[u][v].x));
+        acc[u][v].y = fmaf(l[u].x, rr[v].y, fmaf(l[u].y, rr[v].x, acc[u][v].y));
+      }
+  }
+}
+
 // A_pj <- P A_pj on column tile blockIdx.x (kGW columns), bin blockIdx.y; the block's own tile is
 // left to k_gj_colfix. Shared memory: P and the tile, 2 kGW^2 complex.
 __global__ void __launch_bounds__(256) k_gj_rowscale(float2* __restrict__ M, int nx, int p0, int wp,
@@ -568,17 +597,16 @@ __global__ void __launch_bounds__(256) k_gj_rowscale(float2* __restrict__ M, int
     Ts[e] = (b < wp && j0 + jj < nx) ? A[(size_t)(p0 + b) * nx + j0 + jj] : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < kGW * kGW; e += blockDim.x) {
-    const int a = e / kGW, jj = e % kGW;
-    if (a >= wp || j0 + jj >= nx) continue;
-    float ax = 0.f, ay = 0.f;
-    for (int b = 0; b < wp; ++b) {
-      const float2 p = Ps[a * kGW + b], t = Ts[b * kGW + jj];
-      ax = fmaf(p.x, t.x, fmaf(-p.y, t.y, ax));
-      ay = fmaf(p.x, t.y, fmaf(p.y, t.x, ay));
+  float2 acc[4][4];
+  tile_mm4x4(Ps, Ts, wp, acc);
+  const int a0 = 4 * (threadIdx.x >> 4), jj0 = 4 * (threadIdx.x & 15);
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int a = a0 + u, jj = jj0 + v;
+      if (a < wp && j0 + jj < nx) A[(size_t)(p0 + a) * nx + j0 + jj] = acc[u][v];
     }
-    A[(size_t)(p0 + a) * nx + j0 + jj] = make_float2(ax, ay);
-  }
 }
 
 // A_ip <- -A_ip P on row tile blockIdx.x (kGW rows), bin blockIdx.y; the block's own tile becomes P.
@@ -603,17 +631,16 @@ __global__ void __launch_bounds__(256) k_gj_colfix(float2* __restrict__ M, int n
     Ts[e] = (i0 + ii < nx && a < wp) ? A[(size_t)(i0 + ii) * nx + p0 + a] : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < kGW * kGW; e += blockDim.x) {
-    const int ii = e / kGW, b = e % kGW;
-    if (i0 + ii >= nx || b >= wp) continue;
-    float ax = 0.f, ay = 0.f;
-    for (int a = 0; a < wp; ++a) {
-      const float2 t = Ts[ii * kGW + a], p = Ps[a * kGW + b];
-      ax = fmaf(t.x, p.x, fmaf(-t.y, p.y, ax));
-      ay = fmaf(t.x, p.y, fmaf(t.y, p.x, ay));
+  float2 acc[4][4];
+  tile_mm4x4(Ts, Ps, wp, acc);
+  const int ii0 = 4 * (threadIdx.x >> 4), b0 = 4 * (threadIdx.x & 15);
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int ii = ii0 + u, b = b0 + v;
+      if (i0 + ii < nx && b < wp) A[(size_t)(i0 + ii) * nx + p0 + b] = make_float2(-acc[u][v].x, -acc[u][v].y);
     }
-    A[(size_t)(i0 + ii) * nx + p0 + b] = make_float2(-ax, -ay);
-  }
 }
 
 // The rank-kGW update A_ij -= sum_q A_iq A_qj (q in the pivot block) on the tensor cores. A CTA
