@@ -519,36 +519,47 @@ __global__ void k_rz_form(float2* __restrict__ M, int nx, const double* __restri
 // columns before colfix, and writes neither.
 constexpr int kGW = 64;
 
-// one bin per CTA (256 threads); P[k] is kGW x kGW row-major, identity beyond wp
-__global__ void __launch_bounds__(256) k_gj_pivot(const float2* __restrict__ M, int nx, int p0, int wp,
-                                                  float2* __restrict__ P) {
+// one bin per CTA of 4 kGW threads; P[k] is kGW x kGW row-major, identity beyond wp. Thread
+// (h, j) = (tid / kGW, tid % kGW) owns column j on the kGW/4 rows h kGW/4 ... Step c: the pivot
+// column is copied (one entry per thread of the first quarter) and row c read, both before the
+// step's first barrier; after it every thread eliminates column c from its rows
+// (S[i][j] -= S[i][c] S[c][j] / S[c][c]; column c itself becomes -S[i][c] / S[c][c]) in one
+// unrolled, branch-free pass, and the owner of row c then stores the scaled row entry
+// S[c][j] / S[c][c] (1 / S[c][c] in column c) over what the pass wrote there. Rows are padded to
+// kGW + 1 entries so that the column copy does not hit one bank.
+constexpr int kGjPivThreads = 4 * kGW;
+__global__ void __launch_bounds__(kGjPivThreads) k_gj_pivot(const float2* __restrict__ M, int nx, int p0, int wp,
+                                                            float2* __restrict__ P) {
+  constexpr int kR = kGW / 4;  // rows per thread
   __shared__ float2 S[kGW][kGW + 1];
   __shared__ float2 col[kGW];
-  const int k = blockIdx.x;
+  const int k = blockIdx.x, j = threadIdx.x % kGW, h = threadIdx.x / kGW;
+  const int i0 = h * kR;
   const float2* A = M + (size_t)k * nx * nx;
-  for (int e = threadIdx.x; e < kGW * kGW; e += blockDim.x) {
-    const int a = e / kGW, b = e % kGW;
-    S[a][b] = (a < wp && b < wp) ? A[(size_t)(p0 + a) * nx + p0 + b] : make_float2(a == b ? 1.f : 0.f, 0.f);
-  }
+#pragma unroll 4
+  for (int a = i0; a < i0 + kR; ++a)
+    S[a][j] = (a < wp && j < wp) ? A[(size_t)(p0 + a) * nx + p0 + j] : make_float2(a == j ? 1.f : 0.f, 0.f);
   __syncthreads();
   for (int c = 0; c < kGW; ++c) {
-    if (threadIdx.x < kGW) col[threadIdx.x] = S[threadIdx.x][c];
+    if (h == 0) col[j] = S[j][c];
+    const float2 scj = S[c][j];  // read by every quarter before the owner of row c rewrites it
     __syncthreads();
     const float2 inv = cinv(col[c]);
-    if (threadIdx.x < kGW) {
-      const int j = threadIdx.x;
-      S[c][j] = j == c ? inv : cmul(S[c][j], inv);
+    const float2 rc = j == c ? inv : cmul(scj, inv);  // row c of the result, column j
+    const bool pc = j == c;
+#pragma unroll
+    for (int u = 0; u < kR; ++u) {
+      const int i = i0 + u;
+      const float2 ci = col[i];
+      const float2 v = pc ? cscale(cmul(ci, inv), -1.f) : csub(S[i][j], cmul(ci, rc));
+      S[i][j] = v;
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < kGW * kGW; e += blockDim.x) {
-      const int i = e / kGW, j = e % kGW;
-      if (i == c) continue;
-      S[i][j] = j == c ? cscale(cmul(col[i], inv), -1.f) : csub(S[i][j], cmul(col[i], S[c][j]));
-    }
+    if (c >= i0 && c < i0 + kR) S[c][j] = rc;
     __syncthreads();
   }
   float2* Pk = P + (size_t)k * kGW * kGW;
-  for (int e = threadIdx.x; e < kGW * kGW; e += blockDim.x) Pk[e] = S[e / kGW][e % kGW];
+#pragma unroll 4
+  for (int a = i0; a < i0 + kR; ++a) Pk[a * kGW + j] = S[a][j];
 }
 
 // Products of two kGW x kGW complex tiles in shared memory, for rowscale and colfix: thread t
@@ -899,7 +910,7 @@ int gj_invert_batched(cudaStream_t stream, float2* M, int n, int K) {
   const dim3 gup((n + 32 * kGjNT - 1) / (32 * kGjNT), (n + 127) / 128, K);
   for (int p0 = 0; p0 < n && rc == AAO_OK; p0 += kGW) {
     const int wp = n - p0 < kGW ? n - p0 : kGW;
-    k_gj_pivot<<<K, 256, 0, stream>>>(M, n, p0, wp, piv);
+    k_gj_pivot<<<K, kGjPivThreads, 0, stream>>>(M, n, p0, wp, piv);
     k_gj_rowscale<<<dim3(nbt, K), 256, tsm, stream>>>(M, n, p0, wp, piv);
     k_gj_update_tc<<<gup, kGjThreads, kGjSmem, stream>>>(M, n, p0, wp, err, tcg::kWaitNs);
     k_gj_colfix<<<dim3(nbt, K), 256, tsm, stream>>>(M, n, p0, wp, piv);
