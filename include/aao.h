@@ -265,11 +265,12 @@ int aao_fault_inject(aao_handle* h, int mask, double wait_ms);
 /* Dense symmetric eigendecomposition on the host, FP64: A = Q diag(w) Q^T. A_host (n*n doubles,
    row-major, symmetric; only its values are used, the upper and lower triangles must agree) is
    overwritten with Q^T (row j = the unit eigenvector of w[j]); w_host receives the n eigenvalues
-   (unsorted). Householder tridiagonalisation, then the implicit-shift QL iteration. This is the
+   (unsorted). Householder tridiagonalisation, then the symmetric QR iteration with the Wilkinson
+   shift (Golub and Van Loan, Matrix Computations, Sec. 8.3). This is the
    setup of the spectral step (b) for a symmetric spatial operator (AAO_OP_RIESZ with
    r = sigma^2/2), exported for tests and for callers with their own symmetric operator. Needs no
-   GPU. Errors: AAO_EINVAL (n < 1 or a NULL pointer), AAO_BREAKDOWN (the QL iteration did not
-   converge within 64 sweeps for some eigenvalue). */
+   GPU. Errors: AAO_EINVAL (n < 1 or a NULL pointer), AAO_BREAKDOWN (the QR iteration did not
+   converge within 64 steps per eigenvalue found). */
 int aao_sym_eig(int n, double* A_host, double* w_host);
 
 /* Bounds-checked build (diagnostics; the paper has no counterpart). A library compiled with

@@ -334,7 +334,7 @@ int build_tri_factors(Handle& h);
 // The Riesz operator has no drift term ((r - sigma^2/2) u_x vanishes): its matrix is symmetric.
 inline bool riesz_symmetric(const aao_problem& p) { return p.r - 0.5 * p.sigma * p.sigma == 0.0; }
 // A = Q diag(w) Q^T for a dense symmetric n x n A (row-major, FP64, host); A is overwritten with
-// Q^T. False if the QL iteration does not converge.
+// Q^T. False if the symmetric QR iteration does not converge.
 bool sym_eig(int n, double* A, double* w);
 int riesz_build(Handle& h);
 // in place: each of the K contiguous n x n complex matrices of M replaced by its inverse (blocked

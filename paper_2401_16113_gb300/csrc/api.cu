@@ -235,7 +235,7 @@ int fgmres_solve_host(aao_handle* hd, const double* b_host, double* x_host, doub
 int aao_sym_eig(int n, double* A_host, double* w_host) {
   if (n < 1 || !A_host || !w_host) { set_error("aao_sym_eig: bad argument"); return AAO_EINVAL; }
   if (!sym_eig(n, A_host, w_host)) {
-    set_error("aao_sym_eig: the QL iteration did not converge");
+    set_error("aao_sym_eig: the symmetric QR iteration did not converge");
     return AAO_BREAKDOWN;
   }
   return AAO_OK;

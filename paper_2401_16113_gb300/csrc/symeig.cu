@@ -30,7 +30,8 @@ namespace {
 
 // A pool of host threads kept spinning for the duration of one decomposition, so that the ~2n
 // parallel regions of the Householder stage cost a wake-up of a few microseconds each. run(n, f)
-// calls f(begin, end) over [0, n) in contiguous chunks, the caller taking the first.
+// calls f(begin, end) over [0, n) in contiguous chunks, the caller taking the first; run_beside
+// leaves the caller free for other work meanwhile.
 class SpinPool {
  public:
   explicit SpinPool(int threads) : nthr_(std::max(1, threads)) {
@@ -46,18 +47,37 @@ class SpinPool {
       f(0, n);
       return;
     }
-    job_ = &f;
-    n_ = n;
-    done_.store(0, std::memory_order_relaxed);
-    gen_.fetch_add(1, std::memory_order_acq_rel);
+    start(n, f, false);
     chunk(0);
-    while (done_.load(std::memory_order_acquire) < nthr_ - 1) std::this_thread::yield();
+    wait();
+  }
+  // f over [0, n) on the pool's other threads while the caller runs g
+  void run_beside(int n, const std::function<void(int, int)>& f, const std::function<void()>& g) {
+    if (nthr_ == 1) {
+      g();
+      f(0, n);
+      return;
+    }
+    start(n, f, true);
+    g();
+    wait();
   }
 
  private:
+  void start(int n, const std::function<void(int, int)>& f, bool beside) {
+    job_ = &f;
+    n_ = n;
+    beside_ = beside;
+    done_.store(0, std::memory_order_relaxed);
+    gen_.fetch_add(1, std::memory_order_acq_rel);
+  }
+  void wait() {
+    while (done_.load(std::memory_order_acquire) < nthr_ - 1) std::this_thread::yield();
+  }
   void chunk(int t) {
-    const int per = (n_ + nthr_ - 1) / nthr_;
-    const int b = t * per, e = std::min(n_, b + per);
+    const int parts = beside_ ? nthr_ - 1 : nthr_, idx = beside_ ? t - 1 : t;
+    const int per = (n_ + parts - 1) / parts;
+    const int b = idx * per, e = std::min(n_, b + per);
     if (b < e) (*job_)(b, e);
   }
   void worker(int t) {
@@ -79,6 +99,7 @@ class SpinPool {
   std::atomic<bool> stop_{false};
   const std::function<void(int, int)>* job_ = nullptr;
   int n_ = 0;
+  bool beside_ = false;
 };
 
 int host_threads(size_t work) {
@@ -209,28 +230,27 @@ bool sym_eig(int n, double* A, double* w) {
   std::vector<double> a, b, beta;
   std::vector<std::vector<double>> refl;
   tridiagonalise(pool, n, A, a, b, refl, beta);
-  std::vector<Rotation> rot;
-  rot.reserve(4 * N * N / 2 + 16);
-  if (!symmetric_qr(n, a, b, rot)) return false;
-
-  // Q = Q1 G_1 G_2 ..., formed row by row: row r of Q1 = e_r^T H_0 ... H_{n-3} (the reflectors in
-  // order; H_k changes entries k+1.. only), then the rotations in order. A block of kRows rows is
-  // held transposed (entry j of the block's row r at j kRows + r), so that each update touches
-  // kRows contiguous values.
-  std::vector<double> Q(N * N);
+  // Q = Q1 G_1 G_2 ..., formed by blocks of kRows rows: row r of Q1 = e_r^T H_0 ... H_{n-3} (the
+  // reflectors in order; H_k changes entries k+1.. only), then the rotations in order. A block is
+  // held transposed (entry j of the block's row r at j kRows + r), so that each update touches kRows
+  // contiguous values. The reflector stage needs no rotation, so it runs on the pool's other threads
+  // while this thread runs the QR iteration.
   constexpr int kRows = 16;
   const int blocks = (n + kRows - 1) / kRows;
-  pool.run(blocks, [&](int b0, int b1) {
-    std::vector<double> qb(N * kRows);
+  std::vector<double> qall((size_t)blocks * N * kRows);
+  std::vector<Rotation> rot;
+  rot.reserve(4 * N * N / 2 + 16);
+  bool converged = true;
+  pool.run_beside(blocks, [&](int b0, int b1) {
     for (int blk = b0; blk < b1; ++blk) {
+      double* qb = qall.data() + (size_t)blk * N * kRows;
       const int r0 = blk * kRows, nr = std::min(n, r0 + kRows) - r0;
-      std::fill(qb.begin(), qb.end(), 0.0);
       for (int r = 0; r < nr; ++r) qb[(size_t)(r0 + r) * kRows + r] = 1.0;
       for (size_t k = 0; k < refl.size(); ++k) {
         if (beta[k] == 0.0) continue;
         const double* v = refl[k].data();
         const int m = (int)refl[k].size();
-        double* q = qb.data() + (k + 1) * kRows;
+        double* q = qb + (k + 1) * kRows;
         double dot[kRows] = {};
         for (int j = 0; j < m; ++j)
           for (int r = 0; r < kRows; ++r) dot[r] += q[(size_t)j * kRows + r] * v[j];
@@ -238,15 +258,38 @@ bool sym_eig(int n, double* A, double* w) {
         for (int j = 0; j < m; ++j)
           for (int r = 0; r < kRows; ++r) q[(size_t)j * kRows + r] -= dot[r] * v[j];
       }
+    }
+  }, [&]() { converged = symmetric_qr(n, a, b, rot); });
+  if (!converged) return false;
+
+  // The rotations of one QR step act on neighbouring planes (k, k+1), (k+1, k+2), ...: the column
+  // that a rotation leaves in plane k+1 is the one the next rotation takes in, so it is carried in
+  // registers along such a chain (and written back when the chain breaks) instead of being stored
+  // and loaded again between the two.
+  std::vector<double> Q(N * N);
+  pool.run(blocks, [&](int b0, int b1) {
+    for (int blk = b0; blk < b1; ++blk) {
+      double* qb = qall.data() + (size_t)blk * N * kRows;
+      const int r0 = blk * kRows, nr = std::min(n, r0 + kRows) - r0;
+      double xv[kRows];
+      int cur = -1;  // the column held in xv
       for (const Rotation& g : rot) {
-        double* x = qb.data() + (size_t)g.k * kRows;
-        double* y = x + kRows;
-        for (int r = 0; r < kRows; ++r) {
-          const double xr = x[r], yr = y[r];
-          x[r] = g.c * xr + g.s * yr;
-          y[r] = g.c * yr - g.s * xr;
+        if (g.k != cur) {
+          if (cur >= 0)
+            for (int r = 0; r < kRows; ++r) qb[(size_t)cur * kRows + r] = xv[r];
+          for (int r = 0; r < kRows; ++r) xv[r] = qb[(size_t)g.k * kRows + r];
         }
+        double* x = qb + (size_t)g.k * kRows;
+        const double* y = x + kRows;
+        for (int r = 0; r < kRows; ++r) {
+          const double xr = xv[r], yr = y[r];
+          x[r] = g.c * xr + g.s * yr;
+          xv[r] = g.c * yr - g.s * xr;
+        }
+        cur = g.k + 1;
       }
+      if (cur >= 0)
+        for (int r = 0; r < kRows; ++r) qb[(size_t)cur * kRows + r] = xv[r];
       for (int r = 0; r < nr; ++r)
         for (size_t j = 0; j < N; ++j) Q[(size_t)(r0 + r) * N + j] = qb[j * kRows + r];
     }

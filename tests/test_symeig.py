@@ -1,5 +1,5 @@
 """The host eigensolver behind the spectral step (b) of a symmetric Riesz operator
-(aao_sym_eig: Householder tridiagonalisation + implicit-shift QL), checked through the C ABI
+(aao_sym_eig: Householder tridiagonalisation + symmetric QR with the Wilkinson shift), checked through the C ABI
 against the defining identities and numpy's LAPACK eigenvalues. CPU only."""
 import numpy as np
 import pytest
