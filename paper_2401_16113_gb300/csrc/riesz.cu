@@ -28,6 +28,7 @@
 #include <string.h>
 
 #include <complex>
+#include <thread>
 #include <vector>
 
 #include <cuda.h>
@@ -983,6 +984,25 @@ int encode_operator_map(void* map, float* tiled, int ldq) {
 }
 }  // namespace
 
+// f(begin, end) over [0, n) on the host's cores (contiguous chunks, the caller taking the first)
+template <typename F>
+void host_parallel(int n, F f) {
+  const unsigned hw = std::thread::hardware_concurrency();
+  const int T = (int)std::max(1u, std::min(hw == 0 ? 1u : hw, 32u));
+  if (T <= 1 || n < 2 * T) {
+    f(0, n);
+    return;
+  }
+  const int per = (n + T - 1) / T;
+  std::vector<std::thread> th;
+  for (int t = 1; t < T; ++t) {
+    const int b = t * per, e = std::min(n, b + per);
+    if (b < e) th.emplace_back([&f, b, e] { f(b, e); });
+  }
+  f(0, std::min(n, per));
+  for (auto& x : th) x.join();
+}
+
 int riesz_build(Handle& h) {
   const aao_problem& p = h.p;
   const int nx = h.nx, nt = h.nt;
@@ -1075,28 +1095,23 @@ int riesz_build(Handle& h) {
       return AAO_BREAKDOWN;
     }
     // Ad holds Q^T. Both orientations in FP32, zero-padded to ldq (a multiple of the products'
-    // column tile, >= the spectrum's pitch)
+    // column tile, >= the spectrum's pitch): q[r][k] = Q[r][k] = Ad[k][r], qt[r][k] = Ad[r][k]
     const int ldq = ((nx + tcg::kM - 1) / tcg::kM) * tcg::kM;
-    std::vector<float> q((size_t)ldq * ldq, 0.f), qt((size_t)ldq * ldq, 0.f);
-    for (int j = 0; j < nx; ++j)
-      for (int x = 0; x < nx; ++x) {
-        const float v = (float)Ad[(size_t)j * nx + x];
-        qt[(size_t)j * ldq + x] = v;
-        q[(size_t)x * ldq + j] = v;
-      }
     // D_k,j = (1/lambda_{2,k}) / (mu_k - lambda_j)
     std::vector<double2> mu(K), il2(K);
     AAO_TRY_CUDA(cudaMemcpyAsync(mu.data(), h.mu, sizeof(double2) * K, cudaMemcpyDeviceToHost, h.stream));
     AAO_TRY_CUDA(cudaMemcpyAsync(il2.data(), h.il2, sizeof(double2) * K, cudaMemcpyDeviceToHost, h.stream));
     AAO_TRY_CUDA(cudaStreamSynchronize(h.stream));
     std::vector<float2> dk((size_t)K * ldq, make_float2(0.f, 0.f));
-    for (int k = 0; k < K; ++k) {
-      const std::complex<double> m(mu[k].x, mu[k].y), s(il2[k].x, il2[k].y);
-      for (int j = 0; j < nx; ++j) {
-        const std::complex<double> v = s / (m - lam[j]);
-        dk[(size_t)k * ldq + j] = make_float2((float)v.real(), (float)v.imag());
+    host_parallel(K, [&](int k0, int k1) {
+      for (int k = k0; k < k1; ++k) {
+        const std::complex<double> m(mu[k].x, mu[k].y), s(il2[k].x, il2[k].y);
+        for (int j = 0; j < nx; ++j) {
+          const std::complex<double> v = s / (m - lam[j]);
+          dk[(size_t)k * ldq + j] = make_float2((float)v.real(), (float)v.imag());
+        }
       }
-    }
+    });
     // TF32 head and tail of Q and Q^T for the tensor-core products (x = hi + lo)
     auto tf32 = [](float x) {
       uint32_t u;
@@ -1111,17 +1126,21 @@ int riesz_build(Handle& h) {
     };
     // stored tiled for the TMA boxes: entry (row r, contraction index k) at float
     // ((r/8 (ldq/4) + k/4) 8 + r%8) 4 + k%4, i.e. 8 x 16-byte core matrices, K groups of a row
-    // group contiguous
-    std::vector<float> qh(q.size()), ql(q.size()), qth(q.size()), qtl(q.size());
-    for (int r = 0; r < ldq; ++r)
-      for (int k = 0; k < ldq; ++k) {
-        const size_t t = ((((size_t)(r >> 3) * (ldq / 4) + (k >> 2)) * 8 + (r & 7)) * 4) + (k & 3);
-        const float a = q[(size_t)r * ldq + k], b = qt[(size_t)r * ldq + k];
-        qh[t] = tf32(a);
-        ql[t] = tf32(a - qh[t]);
-        qth[t] = tf32(b);
-        qtl[t] = tf32(b - qth[t]);
-      }
+    // group contiguous; row groups of 8 are split over the host threads
+    const size_t qn = (size_t)ldq * ldq;
+    std::vector<float> qh(qn), ql(qn), qth(qn), qtl(qn);
+    host_parallel(ldq / 8, [&](int g0, int g1) {
+      for (int r = 8 * g0; r < 8 * g1; ++r)
+        for (int k = 0; k < ldq; ++k) {
+          const size_t t = ((((size_t)(r >> 3) * (ldq / 4) + (k >> 2)) * 8 + (r & 7)) * 4) + (k & 3);
+          const bool in = r < nx && k < nx;
+          const float a = in ? (float)Ad[(size_t)k * nx + r] : 0.f, b = in ? (float)Ad[(size_t)r * nx + k] : 0.f;
+          qh[t] = tf32(a);
+          ql[t] = tf32(a - qh[t]);
+          qth[t] = tf32(b);
+          qtl[t] = tf32(b - qth[t]);
+        }
+    });
     AAO_TRY(up(&h.rz_qh, qh));
     AAO_TRY(up(&h.rz_ql, ql));
     AAO_TRY(up(&h.rz_qth, qth));

@@ -113,58 +113,95 @@ struct Rotation {
   double c, s;  // columns k, k+1 of Q become c q_k + s q_{k+1} and -s q_k + c q_{k+1}
 };
 
+// Householder vector of x (length m): v = x - sub e_0 with sub = -sign(x_0) ||x|| (no cancellation
+// in v_0), beta = 2 / ||v||^2; beta = 0 and sub = x_0 when x = 0.
+void householder(const double* x, int m, std::vector<double>& v, double& sub, double& bk) {
+  v.assign(x, x + m);
+  double s2 = 0.0;
+  for (int i = 0; i < m; ++i) s2 += v[i] * v[i];
+  sub = v[0];
+  bk = 0.0;
+  if (s2 > 0.0) {
+    const double nrm = sqrt(s2);
+    sub = v[0] >= 0.0 ? -nrm : nrm;
+    v[0] -= sub;
+    const double vv = s2 - 2.0 * sub * (v[0] + sub) + sub * sub;  // ||x - sub e_0||^2
+    bk = vv > 0.0 ? 2.0 / vv : 0.0;
+  }
+}
+
 // Householder stage on A (n x n row-major, overwritten). Returns the diagonal a, the off-diagonal
 // b (b[i] couples i and i+1), the reflectors (v_k of length n-k-1) and their beta_k.
+// Step k on the trailing block B (rows and columns k+1..): p = beta B v, w = p - (beta/2)(v^T p) v,
+// B <- B - v w^T - w v^T. The next step's reflector depends only on column k+1 of the updated B,
+// which costs O(m) to form, so it is built first and one pass over B per step both applies the
+// update and accumulates the next step's B v (over the same entries in the same order as a separate
+// pass would).
 void tridiagonalise(SpinPool& pool, int n, double* A, std::vector<double>& a, std::vector<double>& b,
                     std::vector<std::vector<double>>& refl, std::vector<double>& beta) {
   const size_t N = (size_t)n;
   a.assign(N, 0.0);
   b.assign(N > 0 ? N - 1 : 0, 0.0);
-  std::vector<double> p(N), w(N);
-  for (int k = 0; k + 2 < n; ++k) {
-    const int m = n - k - 1;
-    const size_t o = (size_t)k + 1;
-    std::vector<double> v(m);
-    double s2 = 0.0;
-    for (int i = 0; i < m; ++i) {
-      v[i] = A[(o + i) * N + k];
-      s2 += v[i] * v[i];
-    }
-    double sub = v[0], bk = 0.0;
-    if (s2 > 0.0) {
-      // reflect x = column k below the diagonal onto -sign(x_0) ||x|| e_0 (no cancellation in v_0)
-      const double nrm = sqrt(s2);
-      sub = v[0] >= 0.0 ? -nrm : nrm;
-      v[0] -= sub;
-      const double vv = s2 - 2.0 * sub * (v[0] + sub) + sub * sub;  // ||x - sub e_0||^2
-      bk = vv > 0.0 ? 2.0 / vv : 0.0;
-    }
-    if (bk != 0.0) {
-      // p = beta B v, w = p - (beta/2)(v^T p) v, B <- B - v w^T - w v^T on the trailing block
+  std::vector<double> p(N), w(N), col(N);
+  std::vector<double> v, vn;
+  double sub = 0.0, bk = 0.0;
+  if (n >= 3) {
+    const int m = n - 1;
+    for (int i = 0; i < m; ++i) col[i] = A[(size_t)(1 + i) * N];
+    householder(col.data(), m, v, sub, bk);
+    if (bk != 0.0)
       pool.run(m, [&](int r0, int r1) {
         for (int i = r0; i < r1; ++i) {
-          const double* Bi = A + (o + i) * N + o;
+          const double* Bi = A + (size_t)(1 + i) * N + 1;
           double acc = 0.0;
           for (int j = 0; j < m; ++j) acc += Bi[j] * v[j];
           p[i] = bk * acc;
         }
       });
+  }
+  for (int k = 0; k + 2 < n; ++k) {
+    const int m = n - k - 1;
+    const size_t o = (size_t)k + 1;
+    if (bk != 0.0) {
       double vp = 0.0;
       for (int i = 0; i < m; ++i) vp += v[i] * p[i];
       const double h = 0.5 * bk * vp;
       for (int i = 0; i < m; ++i) w[i] = p[i] - h * v[i];
-      pool.run(m, [&](int r0, int r1) {
-        for (int i = r0; i < r1; ++i) {
-          double* Bi = A + (o + i) * N + o;
-          const double vi = v[i], wi = w[i];
-          for (int j = 0; j < m; ++j) Bi[j] -= vi * w[j] + wi * v[j];
-        }
-      });
     }
     a[k] = A[(size_t)k * N + k];
     b[k] = sub;
+    // the next step's reflector, from column k+1 below the diagonal after this step's update
+    const bool next = k + 3 < n;
+    double subn = 0.0, bkn = 0.0;
+    if (next) {
+      for (int i = 1; i < m; ++i) {
+        const double bi = A[(o + i) * N + o];
+        col[i - 1] = bk != 0.0 ? bi - (v[i] * w[0] + w[i] * v[0]) : bi;
+      }
+      householder(col.data(), m - 1, vn, subn, bkn);
+    }
+    const bool upd = bk != 0.0, mv = next && bkn != 0.0;
+    if (upd || mv)
+      pool.run(m, [&](int r0, int r1) {
+        for (int i = r0; i < r1; ++i) {
+          double* Bi = A + (o + i) * N + o;
+          if (upd) {
+            const double vi = v[i], wi = w[i];
+            for (int j = 0; j < m; ++j) Bi[j] -= vi * w[j] + wi * v[j];
+          }
+          if (mv && i >= 1) {
+            double acc = 0.0;
+            for (int j = 1; j < m; ++j) acc += Bi[j] * vn[j - 1];
+            p[i - 1] = bkn * acc;
+          }
+        }
+      });
     refl.push_back(std::move(v));
     beta.push_back(bk);
+    v = std::move(vn);
+    vn.clear();
+    sub = subn;
+    bk = bkn;
   }
   if (n >= 2) {
     a[n - 2] = A[(N - 2) * N + (N - 2)];
