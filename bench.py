@@ -371,6 +371,12 @@ def run_ours(args):
     h = aao.aao_create(p)  # tables, step (b) factors, FFT tile autotuning
     torch.cuda.synchronize()
     setup_s = time.time() - t_setup
+    # a second problem on the same mesh (another alpha): the tile tuning of the first is reused
+    t_setup = time.time()
+    h2 = aao.aao_create(W.with_(p, alpha=2.0 * p["alpha"]))
+    torch.cuda.synchronize()
+    setup_cached_s = time.time() - t_setup
+    h2.close()
     b = torch.empty(n, dtype=torch.float64, device="cuda")
     aao.aao_rhs(h, b)
     x = torch.zeros(n, dtype=torch.float64, device="cuda")
@@ -507,9 +513,11 @@ def run_ours(args):
             "precond_apply": precond_roofline(prof, hbm_peak, n),
             "fp64_plain": {"value": fp64_value, "unit": "unknowns/s", "ms": min(ms64),
                            "iterations": st64["iterations"]},
-            "precond_setup": {"ms": setup_s * 1e3, "what": "aao_create of the timed workload: coefficient and "
-                              "eigenvalue tables, step (b) factors, FFT tile autotuning; once per "
-                              "problem, outside the timed solves"},
+            "precond_setup": {"ms": setup_s * 1e3, "cached_ms": setup_cached_s * 1e3,
+                              "what": "ms: the first aao_create of the timed workload in the process "
+                              "(coefficient and eigenvalue tables, step (b) factors, FFT tile "
+                              "autotuning); cached_ms: a second create on the same mesh with another "
+                              "alpha, which reuses the tuned tile; both outside the timed solves"},
             "e2e": {"value": e2e_val, "unit": "unknowns/s", "h2d_bytes_per_step": 8 * n,
                     "d2h_bytes_per_step": 8 * n}}
     line.update(extras)
