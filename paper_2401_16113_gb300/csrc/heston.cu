@@ -290,6 +290,7 @@ __global__ void k_hs_form_t(float2* __restrict__ T, const float2* __restrict__ H
 // memory: the product's input t (Ns complex) and the two slots (2 Ns complex).
 constexpr int kHsThreads = 256;
 constexpr int kHsMaxC = 8;
+constexpr int kHsPer = 2;  // entries of a level per thread (Ns <= 512)
 
 // y_i = M_i . vec for the two rows M_0, M_1 (row 1 only if live1); every lane gets both sums.
 // U loads per row and lane (U = ceil(Ns / 32) up to 8) are issued before the first is used, so a
@@ -362,20 +363,44 @@ __global__ void __launch_bounds__(kHsThreads) k_hs_solve(float2* __restrict__ sp
   const float2* Hk = H + (size_t)k * nn;
   if (threadIdx.x == 0) prefetch_rows_l2(X + (size_t)k * nn, ns, r0, r1);
 
-  // forward: w_j = X_j (r_j - A_j w_{j-1})
+  // forward: w_j = X_j (r_j - A_j w_{j-1}). For narrow blocks (U <= 4: Ns <= 128, where a step is
+  // latency-bound) each thread's entries of r_{j+1} and of the coupling A_{j+1} (at most kHsPer per
+  // thread) are loaded into registers before step j's cluster barrier: level j+1 of the spectrum row
+  // is written only after step j+1's barrier, so the loads are safe then and the step after the
+  // barrier starts from registers instead of an L2 round trip. Wider blocks load them after the
+  // barrier (the registers would cost the bandwidth-bound product more than the round trip).
+  constexpr bool kPre = U <= 4;
+  float2 rr[kHsPer];
+  float aa[kHsPer][3];
+  auto load_level = [&](int j) {
+#pragma unroll
+    for (int q = 0; q < kHsPer; ++q) {
+      const int r = threadIdx.x + q * kHsThreads, p = j * ns + r;
+      rr[q] = r < ns ? row[p] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int d = -1; d <= 1; ++d) {
+        const int m = r + d;
+        aa[q][d + 1] = (j > 0 && r < ns && m >= 0 && m < ns) ? hcoef(hc, nsp, 1 + d, p) : 0.f;
+      }
+    }
+  };
+  if (kPre) load_level(0);
   for (int j = 0; j < nv; ++j) {
     if (threadIdx.x == 0)  // the next step's block: X_{j+1}, or G_{nv-2} for the first backward step
       prefetch_rows_l2(j + 1 < nv ? X + ((size_t)(j + 1) * K + k) * nn : G + ((size_t)(nv - 2) * K + k) * nn, ns, r0, r1);
+    if (!kPre) load_level(j);
     const float2* wprev = slot + ((j - 1) & 1) * ns;
-    for (int r = threadIdx.x; r < ns; r += blockDim.x) {
-      const int p = j * ns + r;
-      float2 v = cmul(row[p], sk);
+#pragma unroll
+    for (int q = 0; q < kHsPer; ++q) {
+      const int r = threadIdx.x + q * kHsThreads;
+      if (r >= ns) break;
+      float2 v = cmul(rr[q], sk);
       if (j > 0) {
 #pragma unroll
         for (int d = -1; d <= 1; ++d) {
           const int m = r + d;
           if (m < 0 || m >= ns) continue;
-          const float a = hcoef(hc, nsp, 1 + d, p);
+          const float a = aa[q][d + 1];
           const float2 w = wprev[m];
           v.x -= a * w.x;
           v.y -= a * w.y;
@@ -396,6 +421,7 @@ __global__ void __launch_bounds__(kHsThreads) k_hs_solve(float2* __restrict__ sp
         if (lb) peer[off + rb] = yb;
       }
     }
+    if (kPre && j + 1 < nv) load_level(j + 1);
     cl.sync();
     for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x)
       if (AAO_DCHECK(j * ns + r < nsp && nsp <= pitch)) row[j * ns + r] = slot[off + r];
