@@ -79,16 +79,16 @@ def run_case(args):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
         x.zero_()
-        aao.fgmres_solve(h, b, x, tol, m, 300)
+        aao.fgmres_solve_zero(h, b, x, tol, m, 300)
     times, st = [], None
     for _ in range(args.steps):
         x.zero_()
         flush.fill_(1.0)
-        ms, st = _timed(stream, lambda: aao.fgmres_solve(h, b, x, tol, m, 300))
+        ms, st = _timed(stream, lambda: aao.fgmres_solve_zero(h, b, x, tol, m, 300))
         times.append(ms)
     aao.aao_profile_enable(None)
     x.zero_()
-    aao.fgmres_solve(h, b, x, tol, m, 300)
+    aao.fgmres_solve_zero(h, b, x, tol, m, 300)
     torch.cuda.synchronize()
     classes = {c: aao.aao_profile_read(c) for c in aao.KERNEL_CLASSES}
     tri = classes["tridiag"]
@@ -387,7 +387,7 @@ def run_ours(args):
         x.zero_()
         if timed_events is not None:
             timed_events[0].record(stream)
-        st = aao.fgmres_solve(h, b, x, TOL, p["m"], 300)
+        st = aao.fgmres_solve_zero(h, b, x, TOL, p["m"], 300)
         if timed_events is not None:
             timed_events[1].record(stream)
         if st["status"] != 0 or st["rel_residual"] > TOL:
@@ -440,14 +440,14 @@ def run_ours(args):
     b64 = torch.empty(n, dtype=torch.float64, device="cuda")
     aao.aao_rhs(h64, b64)
     x64 = torch.zeros_like(b64)
-    aao.fgmres_solve(h64, b64, x64, TOL, p["m"], 300)  # warm
+    aao.fgmres_solve_zero(h64, b64, x64, TOL, p["m"], 300)  # warm
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ms64 = []
     for _ in range(3):
         flush.fill_(1.0)
         x64.zero_()
         e0.record(stream)
-        st64 = aao.fgmres_solve(h64, b64, x64, TOL, p["m"], 300)
+        st64 = aao.fgmres_solve_zero(h64, b64, x64, TOL, p["m"], 300)
         e1.record(stream)
         torch.cuda.synchronize()
         ms64.append(e0.elapsed_time(e1))
@@ -616,7 +616,7 @@ def run_metric_arms(args, flush, stream):
             torch.cuda.synchronize()
             setup_ms += 1e3 * (time.perf_counter() - c0)
             c0 = time.perf_counter()
-            st = aao.fgmres_solve(h, b, x, TOL, m, 300)
+            st = aao.fgmres_solve_zero(h, b, x, TOL, m, 300)
             solve_ms += 1e3 * (time.perf_counter() - c0)
             if st["status"] != 0 or st["rel_residual"] > TOL:
                 raise RuntimeError(f"{precision} instance {i}: {st}")
@@ -713,12 +713,12 @@ def run_metric_arms(args, flush, stream):
         aao.aao_rhs(h, b)
         torch.cuda.synchronize()
         setup = 1e3 * (time.perf_counter() - c0)
-        st = aao.fgmres_solve(h, b, x, TOL, m, 300)  # warm (workspace allocation)
+        st = aao.fgmres_solve_zero(h, b, x, TOL, m, 300)  # warm (workspace allocation)
         best = None
         for _ in range(3):
             x.zero_()
             flush.fill_(1.0)
-            ms, st = _timed(stream, lambda: aao.fgmres_solve(h, b, x, TOL, m, 300))
+            ms, st = _timed(stream, lambda: aao.fgmres_solve_zero(h, b, x, TOL, m, 300))
             best = ms if best is None else min(best, ms)
         h.close()
         del b, x
@@ -774,21 +774,21 @@ def run_extras(args, flush, stream, main):
         br = torch.empty(nr, dtype=torch.float64, device="cuda")
         aao.aao_rhs(hr, br)
         xr = torch.zeros_like(br)
-        aao.fgmres_solve(hr, br, xr, TOL, rz["m"], 300)
+        aao.fgmres_solve_zero(hr, br, xr, TOL, rz["m"], 300)
         best, st_r = None, None
         for _ in range(3):
             xr.zero_()
             flush.fill_(1.0)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            st_r = aao.fgmres_solve(hr, br, xr, TOL, rz["m"], 300)
+            st_r = aao.fgmres_solve_zero(hr, br, xr, TOL, rz["m"], 300)
             e1.record(stream)
             torch.cuda.synchronize()
             t = e0.elapsed_time(e1)
             best = t if best is None else min(best, t)
         aao.aao_profile_enable(None)
         xr.zero_()
-        aao.fgmres_solve(hr, br, xr, TOL, rz["m"], 300)
+        aao.fgmres_solve_zero(hr, br, xr, TOL, rz["m"], 300)
         torch.cuda.synchronize()
         tri = aao.aao_profile_read("tridiag")
         aao.aao_profile_enable([])
@@ -803,14 +803,14 @@ def run_extras(args, flush, stream, main):
     p1 = W.with_(p, alpha=1.0)
     h1 = aao.aao_create(p1)
     x1 = torch.zeros(n, dtype=torch.float64, device="cuda")
-    aao.fgmres_solve(h1, b, x1, TOL, p["m"], 300)
+    aao.fgmres_solve_zero(h1, b, x1, TOL, p["m"], 300)
     best1, st1 = None, None
     for _ in range(3):
         x1.zero_()
         flush.fill_(1.0)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        st1 = aao.fgmres_solve(h1, b, x1, TOL, p["m"], 300)
+        st1 = aao.fgmres_solve_zero(h1, b, x1, TOL, p["m"], 300)
         e1.record(stream)
         torch.cuda.synchronize()
         t = e0.elapsed_time(e1)
@@ -830,21 +830,21 @@ def run_extras(args, flush, stream, main):
         if b_ is None:
             aao.aao_rhs(hq, bq)
         xq = torch.zeros(nq, dtype=torch.float64, device="cuda")
-        aao.fgmres_solve(hq, bq, xq, TOL, q["m"], 300)
+        aao.fgmres_solve_zero(hq, bq, xq, TOL, q["m"], 300)
         best, stq = None, None
         for _ in range(3):
             xq.zero_()
             flush.fill_(1.0)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            stq = aao.fgmres_solve(hq, bq, xq, TOL, q["m"], 300)
+            stq = aao.fgmres_solve_zero(hq, bq, xq, TOL, q["m"], 300)
             e1.record(stream)
             torch.cuda.synchronize()
             t = e0.elapsed_time(e1)
             best = t if best is None else min(best, t)
         aao.aao_profile_enable(None)
         xq.zero_()
-        aao.fgmres_solve(hq, bq, xq, TOL, q["m"], 300)
+        aao.fgmres_solve_zero(hq, bq, xq, TOL, q["m"], 300)
         torch.cuda.synchronize()
         fw, iv = aao.aao_profile_read("fft_fwd"), aao.aao_profile_read("fft_inv")
         aao.aao_profile_enable([])
@@ -870,12 +870,12 @@ def run_extras(args, flush, stream, main):
         bq = torch.empty(nq, dtype=torch.float64, device="cuda")
         aao.aao_rhs(hq, bq)
         xq = torch.zeros_like(bq)
-        aao.fgmres_solve(hq, bq, xq, 1e-9, 40, 300)
+        aao.fgmres_solve_zero(hq, bq, xq, 1e-9, 40, 300)
         best, stq = None, None
         for _ in range(3):
             xq.zero_()
             flush.fill_(1.0)
-            ms, stq = _timed(stream, lambda: aao.fgmres_solve(hq, bq, xq, 1e-9, 40, 300))
+            ms, stq = _timed(stream, lambda: aao.fgmres_solve_zero(hq, bq, xq, 1e-9, 40, 300))
             best = ms if best is None else min(best, ms)
         i = int(round(q["S0"] * q["nx"] / q["s_max"])) - 1
         j = int(round(q["V0"] * q["nv"] / q["v_max"]))

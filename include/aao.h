@@ -151,7 +151,14 @@ int precond_apply(aao_handle* h, const double* v_dev, double* z_dev);
 int fgmres_solve(aao_handle* h, const double* b_dev, double* x_dev, double tol, int m, int maxit,
                  aao_stats* st);
 
-/* As fgmres_solve with host buffers: copies b_host to the device, solves from a zero
+/* As fgmres_solve from the zero initial guess of the paper's protocol: x_dev is output only (its
+   contents on entry are ignored), and the first residual r_0 = b is formed by one copy of b
+   (with the FP32 copy that a mixed-precision preconditioner reads and ||b||) instead of the
+   matrix-vector product b - M x_0. Same arguments, results and errors as fgmres_solve. */
+int fgmres_solve_zero(aao_handle* h, const double* b_dev, double* x_dev, double tol, int m, int maxit,
+                      aao_stats* st);
+
+/* As fgmres_solve_zero with host buffers: copies b_host to the device, solves from a zero
    initial guess, copies the solution to x_host. Both are nx*nt doubles. */
 int fgmres_solve_host(aao_handle* h, const double* b_host, double* x_host, double tol, int m,
                       int maxit, aao_stats* st);

@@ -28,7 +28,7 @@ EXPORTS = ["aao_create", "aao_destroy", "aao_rhs", "aao_matvec", "precond_apply"
            "aao_batch_create", "aao_batch_rhs", "batch_submit", "aao_batch_set_alpha", "aao_batch_destroy",
            "aao_mlp_create", "aao_mlp_destroy", "aao_mlp_params", "aao_mlp_grad", "aao_mlp_adam_step",
            "aao_mlp_train", "aao_mlp_forward", "aao_mlp_normalization", "alpha_mlp_predict",
-           "fgmres_solve", "fgmres_solve_host", "aao_last_error", "aao_launch_count",
+           "fgmres_solve", "fgmres_solve_zero", "fgmres_solve_host", "aao_last_error", "aao_launch_count",
            "aao_profile_enable", "aao_profile_read", "aao_sym_eig", "aao_fault_inject", "aao_check_failures"]
 AAO_INJECT_TC_NO_LOAD = 1
 
@@ -83,6 +83,7 @@ def load(path=None):
     lib.precond_apply.argtypes = [vp, vp, vp]
     lib.precond_apply_static.argtypes = [ctypes.POINTER(AaoProblem), vp, vp]
     lib.fgmres_solve.argtypes = [vp, vp, vp, dp, ip, ip, ctypes.POINTER(AaoStats)]
+    lib.fgmres_solve_zero.argtypes = [vp, vp, vp, dp, ip, ip, ctypes.POINTER(AaoStats)]
     lib.fgmres_solve_host.argtypes = [vp, vp, vp, dp, ip, ip, ctypes.POINTER(AaoStats)]
     lib.aao_batch_create.argtypes = [ctypes.POINTER(AaoProblem), ip, ip, ctypes.POINTER(vp)]
     lib.aao_batch_rhs.argtypes = [vp, ctypes.POINTER(vp)]
@@ -108,7 +109,7 @@ def load(path=None):
     lib.aao_profile_read.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     for name in ("aao_create", "aao_destroy", "aao_rhs", "aao_matvec", "precond_apply", "precond_apply_static",
-                 "fgmres_solve",
+                 "fgmres_solve", "fgmres_solve_zero",
                  "fgmres_solve_host", "aao_profile_enable", "aao_profile_read", "aao_batch_create",
                  "aao_batch_rhs", "batch_submit", "aao_batch_destroy", "aao_batch_set_alpha", "aao_mlp_create",
                  "aao_mlp_destroy", "aao_mlp_params", "aao_mlp_grad", "aao_mlp_adam_step", "aao_mlp_train",
@@ -227,6 +228,17 @@ def fgmres_solve(h, b, x, tol, m, maxit, raise_on_failure=False):
     st = AaoStats()
     code = load().fgmres_solve(h.ptr, _dev(b, h.n), _dev(x, h.n), float(tol), int(m), int(maxit),
                                ctypes.byref(st))
+    if code in (AAO_OK, AAO_NOT_CONVERGED, AAO_BREAKDOWN) and not raise_on_failure:
+        return st.to_dict()
+    _check(code)
+    return st.to_dict()
+
+
+def fgmres_solve_zero(h, b, x, tol, m, maxit, raise_on_failure=False):
+    """As fgmres_solve from the zero initial guess: x is output only."""
+    st = AaoStats()
+    code = load().fgmres_solve_zero(h.ptr, _dev(b, h.n), _dev(x, h.n), float(tol), int(m), int(maxit),
+                                    ctypes.byref(st))
     if code in (AAO_OK, AAO_NOT_CONVERGED, AAO_BREAKDOWN) and not raise_on_failure:
         return st.to_dict()
     _check(code)

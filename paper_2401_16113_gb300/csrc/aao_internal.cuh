@@ -355,7 +355,9 @@ int riesz_solve_bins(Handle& h, void* spec, void** result);
 int launch_matvec(Handle& h, const void* x, bool x_is_float, double* y, const double* b, const double* V = nullptr,
                   int nd = 0, int m = 0, bool with_bnorm = false, float* yf = nullptr);
 int launch_rhs(Handle& h, double* b);
-int run_fgmres(Handle& h, const double* b, double* x, double tol, int m, int maxit, aao_stats* st);
+// zero_guess: x is output only and the solve starts from x_0 = 0 (the first residual is b)
+int run_fgmres(Handle& h, const double* b, double* x, double tol, int m, int maxit, aao_stats* st,
+               bool zero_guess = false);
 void free_handle(Handle& h);
 
 }  // namespace aao

@@ -208,6 +208,13 @@ int fgmres_solve(aao_handle* hd, const double* b, double* x, double tol, int m, 
   return run_fgmres(hd->h, b, x, tol, m, maxit, st);
 }
 
+int fgmres_solve_zero(aao_handle* hd, const double* b, double* x, double tol, int m, int maxit, aao_stats* st) {
+  NvtxRange nv("fgmres_solve_zero");
+  if (!hd || !b || !x) { set_error("fgmres_solve_zero: null argument"); return AAO_EINVAL; }
+  if (m < 1 || m > 64 || maxit < 1 || !(tol > 0)) { set_error("fgmres_solve_zero: need 1 <= m <= 64, maxit >= 1, tol > 0"); return AAO_EINVAL; }
+  return run_fgmres(hd->h, b, x, tol, m, maxit, st, true);
+}
+
 int fgmres_solve_host(aao_handle* hd, const double* b_host, double* x_host, double tol, int m, int maxit,
                       aao_stats* st) {
   NvtxRange nv("fgmres_solve_host");
@@ -219,8 +226,7 @@ int fgmres_solve_host(aao_handle* hd, const double* b_host, double* x_host, doub
   AAO_TRY_CUDA(cudaMallocAsync(&b, bytes, h.stream));
   AAO_TRY_CUDA(cudaMallocAsync(&x, bytes, h.stream));
   AAO_TRY_CUDA(cudaMemcpyAsync(b, b_host, bytes, cudaMemcpyHostToDevice, h.stream));
-  AAO_TRY_CUDA(cudaMemsetAsync(x, 0, bytes, h.stream));
-  int s = run_fgmres(h, b, x, tol, m, maxit, st);
+  int s = run_fgmres(h, b, x, tol, m, maxit, st, true);
   cudaError_t e = cudaMemcpyAsync(x_host, x, bytes, cudaMemcpyDeviceToHost, h.stream);
   cudaFreeAsync(b, h.stream);
   cudaFreeAsync(x, h.stream);

@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(kThreads) k_update(double* __restrict__ w, con
 // triangular system itself); Z_i = P^{-1} v_i for the normalised basis vectors v_i
 template <typename ZT>
 __global__ void __launch_bounds__(kThreads) k_xupdate(double* __restrict__ x, const ZT* __restrict__ Z, int jd,
-                                                      size_t n, const double* __restrict__ scal) {
+                                                      size_t n, const double* __restrict__ scal, int fresh) {
   pdl_sync();
   __shared__ double ys[128];
   if (threadIdx.x == 0) {
@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(kThreads) k_xupdate(double* __restrict__ x, co
   size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   // two elements per step, loads first
   for (; e + stride < n; e += 2 * stride) {
-    double va = x[e], vb = x[e + stride];
+    double va = fresh ? 0.0 : x[e], vb = fresh ? 0.0 : x[e + stride];
     int i = 0;
     for (; i + 2 <= jd; i += 2) {
       const double z0 = ld(Z + (size_t)i * n + e), z1 = ld(Z + (size_t)(i + 1) * n + e);
@@ -310,10 +310,38 @@ __global__ void __launch_bounds__(kThreads) k_xupdate(double* __restrict__ x, co
     x[e + stride] = vb;
   }
   for (; e < n; e += stride) {
-    double v = x[e];
+    double v = fresh ? 0.0 : x[e];
     for (int i = 0; i < jd; ++i) v = fma(ys[i], ld(Z + (size_t)i * n + e), v);
     x[e] = v;
   }
+}
+
+// The first restart residual from the zero initial guess, r = b: V_0 <- b (and its FP32 copy vf
+// when the preconditioner reads one), ||b||^2 into both BETA2 and BNORM2, and sigma_0 = 1/beta,
+// g = (beta, 0, ..., 0) and the finiteness flag as the residual matvec sets them.
+__global__ void __launch_bounds__(kThreads) k_first_zero(const double* __restrict__ b, double* __restrict__ V0,
+                                                         float* __restrict__ vf, size_t n, double* part,
+                                                         double* __restrict__ scal, unsigned int* __restrict__ counter,
+                                                         int m) {
+  pdl_sync();
+  double acc[1] = {0.0};
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const double a = __ldg(b + e);
+    if (AAO_DCHECK(e < n)) V0[e] = a;
+    if (vf) vf[e] = narrow(a);
+    acc[0] = fma(a, a, acc[0]);
+  }
+  block_sums_wide<1>(acc, 1, part + (size_t)blockIdx.x * kPartLd);
+  if (!last_block(counter, gridDim.x)) return;
+  finish_sums_wide<1>(part, gridDim.x, 1, [&](int, double v) {
+    scal[S_BETA2] = v;
+    scal[S_BNORM2] = v;
+    const double beta = sqrt(v);
+    scal[S_SIG] = beta > 0.0 ? 1.0 / beta : 0.0;
+    scal[S_G] = beta;
+    for (int k = 1; k <= m; ++k) scal[S_G + k] = 0.0;
+    scal[S_FLAG] = isfinite(v) ? 0.0 : 1.0;
+  }, counter);
 }
 
 // scal[slot] = v . v
@@ -717,7 +745,7 @@ int update(Handle& h, double* w, int j, int pass, float* vf) {
 
 }  // namespace
 
-int run_fgmres(Handle& h, const double* b, double* x, double tol, int m, int maxit, aao_stats* st) {
+int run_fgmres(Handle& h, const double* b, double* x, double tol, int m, int maxit, aao_stats* st, bool zero_guess) {
   const auto t0 = std::chrono::steady_clock::now();
   const uint64_t l0 = g_launches.load();
   AAO_TRY(ensure_workspace(h, m));
@@ -731,13 +759,22 @@ int run_fgmres(Handle& h, const double* b, double* x, double tol, int m, int max
 
   int its = 0, restarts = 0, status = AAO_OK;
   double rel = 0.0, est = 0.0, bnorm = 0.0;
+  bool x_fresh = zero_guess;  // x holds nothing yet and stands for zero
   // the error word of the tensor-core step (b) reports this solve only
   if (h.rz_err) AAO_TRY_CUDA(cudaMemsetAsync(h.rz_err, 0, sizeof(int), h.stream));
   for (bool first = true;; first = false) {
     NvtxRange nv_cycle("fgmres_cycle");
     // restart residual r = b - M x, written as the raw first basis vector V_0 (the first one also
-    // forms ||b||^2)
-    AAO_TRY(launch_matvec(h, x, false, h.V, b, nullptr, 0, m, first, vf));
+    // forms ||b||^2); from a zero guess the first one is b itself, and x is not read: the first
+    // solution update writes it (x_fresh), or it is zeroed if the solve ends before one
+    if (first && zero_guess) {
+      ProfScope ps(AAO_K_OTHER, h.stream, (double)n * (16.0 + (vf ? 4.0 : 0.0)));
+      AAO_TRY_CUDA(launch_pdl(k_first_zero, wave_blocks(h, (const void*)k_first_zero, g), kThreads, 0, h.stream, b,
+                              h.V, vf, n, h.part, h.scal, h.counter, m));
+      AAO_CHECK_LAUNCH();
+    } else {
+      AAO_TRY(launch_matvec(h, x, false, h.V, b, nullptr, 0, m, first, vf));
+    }
     AAO_TRY(read_scalars(h, S_BETA2, 2));  // BETA2, BNORM2
     if (first) {
       bnorm = sqrt(h.host_scal[1]);
@@ -789,15 +826,17 @@ int run_fgmres(Handle& h, const double* b, double* x, double tol, int m, int max
         ProfScope ps(AAO_K_OTHER, h.stream, (double)n * (16.0 + zsz * jd));
         if (h.mixed)
           AAO_TRY_CUDA(launch_pdl(k_xupdate<float>, wave_blocks(h, (const void*)k_xupdate<float>, g), kThreads, 0,
-                                  h.stream, x, (const float*)h.Z, jd, n, h.scal));
+                                  h.stream, x, (const float*)h.Z, jd, n, h.scal, x_fresh ? 1 : 0));
         else
           AAO_TRY_CUDA(launch_pdl(k_xupdate<double>, wave_blocks(h, (const void*)k_xupdate<double>, g), kThreads, 0,
-                                  h.stream, x, (const double*)h.Z, jd, n, h.scal));
+                                  h.stream, x, (const double*)h.Z, jd, n, h.scal, x_fresh ? 1 : 0));
+        x_fresh = false;
       }
       AAO_CHECK_LAUNCH();
       ++restarts;
     }
   }
+  if (x_fresh) AAO_TRY_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, h.stream));
   if (h.rz_err) {
     // a tensor-core product of the spectral step (b) whose bounded wait gave up (its output was
     // skipped): report it rather than the solve's status

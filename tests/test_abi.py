@@ -88,6 +88,7 @@ def test_null_arguments_rejected(lib):
     assert lib.aao_matvec(None, None, None) == aao.AAO_EINVAL
     assert lib.precond_apply(None, None, None) == aao.AAO_EINVAL
     assert lib.fgmres_solve(None, None, None, 1e-8, 10, 10, None) == aao.AAO_EINVAL
+    assert lib.fgmres_solve_zero(None, None, None, 1e-8, 10, 10, None) == aao.AAO_EINVAL
     assert lib.aao_destroy(None) == aao.AAO_OK
 
 

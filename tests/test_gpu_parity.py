@@ -228,13 +228,37 @@ def test_fgmres_host_variant_matches_device(aao):
     n = W.unknowns(p)
     b = torch.empty(n, dtype=torch.float64, device="cuda")
     aao.aao_rhs(h, b)
-    x = torch.zeros(n, dtype=torch.float64, device="cuda")
-    st = aao.fgmres_solve(h, b, x, 1e-9, 20, 100)
+    x = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+    st = aao.fgmres_solve_zero(h, b, x, 1e-9, 20, 100)
     bh = host(b).copy()
     xh = np.zeros(n)
     st2 = aao.fgmres_solve_host(h, bh, xh, 1e-9, 20, 100)
     assert st2["iterations"] == st["iterations"]
     assert np.array_equal(xh, host(x))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_fgmres_zero_guess_entry_point(aao, precision):
+    """fgmres_solve_zero ignores what x holds on entry (NaN here) and reaches the solution of
+    fgmres_solve from x = 0 in the same number of iterations; the first residual is b itself, so the
+    two differ only in the rounding order of ||b||."""
+    cases = [W.with_(BS, nx=127, nt=128, precision=precision, alpha=1e-3),
+             W.with_(LV, nx=255, nt=256, precision=precision, alpha=1e-3)]
+    if precision == "mixed":
+        cases += [W.with_(W.riesz_1023x512(), nx=127, nt=64), W.heston_set1(16)]
+    for p in cases:
+        h = aao.aao_create(p)
+        n = W.unknowns(p)
+        b = torch.empty(n, dtype=torch.float64, device="cuda")
+        aao.aao_rhs(h, b)
+        x0 = torch.zeros_like(b)
+        st0 = aao.fgmres_solve(h, b, x0, 1e-9, 30, 200)
+        xz = torch.full_like(b, float("nan"))
+        stz = aao.fgmres_solve_zero(h, b, xz, 1e-9, 30, 200)
+        assert stz["status"] == 0 and st0["status"] == 0, (stz, st0)
+        assert stz["iterations"] == st0["iterations"], (p["op"], stz, st0)
+        assert rel(host(xz), host(x0)) <= 1e-9, p["op"]
+        h.close()
 
 
 def test_fgmres_restart_small_m(aao):
