@@ -197,7 +197,8 @@ int precond_apply_static(const aao_problem* p, const double* v_dev, double* z_de
 typedef struct aao_batch aao_batch;
 
 /* Build tables and workspace for n problems (all precision AAO_MIXED, op AAO_OP_BS or
-   AAO_OP_LOCALVOL, 2 <= nt <= 4096 a power of two, 2 <= nx <= 4096) with restart length
+   AAO_OP_LOCALVOL, 2 <= nt <= 4096 with prime factors 2, 3, 5 and 7 only (a power of two takes
+   the register FFT tile, any other nt the mixed-radix one), 2 <= nx <= 4096) with restart length
    1 <= m <= 40. The FFT column tile of each nt class is autotuned here. Work is ordered after
    ps[0].stream. Errors: AAO_EINVAL (names the first bad problem), AAO_ENOMEM, AAO_ECUDA. */
 int aao_batch_create(const aao_problem* ps, int n, int m, aao_batch** bt);

@@ -42,6 +42,7 @@ constexpr int kMaxC = 8;       // largest cluster (CTAs per instance)
 
 struct BatchInst {
   int nx, nt, log2n, K, pitch, P, tgrp, ch, cs, rows, m, pad;
+  MrPlan mr;  // stages of the mixed-radix transform (nst = 0: nt is a power of two)
   size_t n;
   const double* b;
   double* x;
@@ -121,13 +122,33 @@ __device__ __noinline__ void cl_matvec_proj(const BatchInst& I, Ctx c, const flo
   cluster_sums<ND>(acc, ND, psm, out);
 }
 
-// P_alpha^{-1} (scale * v) -> z (FP32), Eq. 3.2 with Remark 1; tiles and bins split by rank
+// the twiddle table of the mixed-radix tiles, after their two P x nt buffers
+__device__ __forceinline__ float2* cl_mr_twiddles(const BatchInst& I, unsigned char* smem) {
+  float2* stw = reinterpret_cast<float2*>(smem) + 2 * (size_t)I.P * I.nt;
+  for (int m = threadIdx.x; m < I.nt; m += blockDim.x) stw[m] = I.tw[m];
+  return stw;  // made visible by the first barrier of the tile
+}
+
+// P_alpha^{-1} (scale * v) -> z (FP32), Eq. 3.2 with Remark 1; tiles and bins split by rank. nt
+// a power of two: the register or shared-memory tiles; otherwise the mixed-radix tiles (two
+// buffers of P x nt and the twiddle table in shared memory).
 __device__ __noinline__ void cl_precond(const BatchInst& I, Ctx c, const double* v, float scale, float* z,
                                         unsigned char* smem) {
   const int W = 2 * I.P;
-  for (int x0 = c.rank * W; x0 < I.nx; x0 += c.C * W) {
-    fft_fwd_tile<float>(v, I.spec, I.nx, I.nt, I.log2n, I.P, I.pitch, I.lam, I.tw, scale, x0, smem);
-    __syncthreads();
+  if (I.mr.nst > 0) {
+    const int lp = __ffs(I.P) - 1;
+    float2* b0 = reinterpret_cast<float2*>(smem);
+    const float2* stw = cl_mr_twiddles(I, smem);
+    for (int x0 = c.rank * W; x0 < I.nx; x0 += c.C * W) {
+      fft_fwd_mr_tile<float, double, kBT>(v, I.spec, I.nx, I.nt, I.mr, lp, I.pitch, I.lam, scale, x0, b0,
+                                          b0 + (size_t)I.P * I.nt, stw);
+      __syncthreads();
+    }
+  } else {
+    for (int x0 = c.rank * W; x0 < I.nx; x0 += c.C * W) {
+      fft_fwd_tile<float>(v, I.spec, I.nx, I.nt, I.log2n, I.P, I.pitch, I.lam, I.tw, scale, x0, smem);
+      __syncthreads();
+    }
   }
   cluster_sync();
   const int G = kBT / I.tgrp;
@@ -146,9 +167,20 @@ __device__ __noinline__ void cl_precond(const BatchInst& I, Ctx c, const double*
     __syncthreads();
   }
   cluster_sync();
-  for (int x0 = c.rank * W; x0 < I.nx; x0 += c.C * W) {
-    fft_inv_tile<float, float>(I.spec, z, I.nx, I.nt, I.log2n, I.P, I.pitch, I.ilam, I.tw, x0, smem);
-    __syncthreads();
+  if (I.mr.nst > 0) {
+    const int lp = __ffs(I.P) - 1;
+    float2* b0 = reinterpret_cast<float2*>(smem);
+    const float2* stw = cl_mr_twiddles(I, smem);
+    for (int x0 = c.rank * W; x0 < I.nx; x0 += c.C * W) {
+      fft_inv_mr_tile<float, float, kBT>(I.spec, z, I.nx, I.nt, I.mr, lp, I.pitch, I.ilam, x0, b0,
+                                         b0 + (size_t)I.P * I.nt, stw);
+      __syncthreads();
+    }
+  } else {
+    for (int x0 = c.rank * W; x0 < I.nx; x0 += c.C * W) {
+      fft_inv_tile<float, float>(I.spec, z, I.nx, I.nt, I.log2n, I.P, I.pitch, I.ilam, I.tw, x0, smem);
+      __syncthreads();
+    }
   }
   cluster_sync();
 }
@@ -364,6 +396,13 @@ int tile_P(int nt, int cap) {
   return P;
 }
 
+// the largest FFT tile of an nt class within the batch kernel's shared memory: P nt <= 16 kBT
+// complex for the power-of-two tiles, 2 P nt <= 16 kBT for the mixed-radix ones (two buffers)
+int tile_P_max(int nt) {
+  const bool pow2 = (nt & (nt - 1)) == 0;
+  return tile_P(nt, pow2 ? 16 * kBT : 8 * kBT);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- host side
@@ -501,7 +540,7 @@ int tune_tiles(Batch& B) {
   for (auto& kv : cls) {
     const int nt = kv.first;
     const std::vector<int>& ids = kv.second;
-    const int pmax = tile_P(nt, 16 * kBT);
+    const int pmax = tile_P_max(nt);
     int bestP = pmax;
     float best = 1e30f;
     for (int P = pmax; P >= 1 && P >= pmax / 4 && rc == AAO_OK; P >>= 1) {
@@ -589,14 +628,15 @@ extern "C" int aao_batch_create(const aao_problem* ps, int n, int m, aao_batch**
   if (m < 1 || m > kMaxM) { set_error("aao_batch_create: need 1 <= m <= 40"); return AAO_EINVAL; }
   for (int i = 0; i < n; ++i) {
     const aao_problem& p = ps[i];
-    const bool pow2 = p.nt > 0 && (p.nt & (p.nt - 1)) == 0;
-    if ((p.op != AAO_OP_BS && p.op != AAO_OP_LOCALVOL) || p.precision != AAO_MIXED || !pow2 || p.nt < 2 ||
+    MrPlan pl;
+    const bool radix_ok = p.nt > 0 && mr_plan(p.nt, pl);  // prime factors 2, 3, 5 and 7 only
+    if ((p.op != AAO_OP_BS && p.op != AAO_OP_LOCALVOL) || p.precision != AAO_MIXED || !radix_ok || p.nt < 2 ||
         p.nt > 4096 || p.nx < 2 || p.nx > 4096 || !(p.T > 0) || !(p.K > 0) || !(p.sigma > 0) || !(p.s_max > 0) ||
         !(p.r >= 0) || !(p.alpha > 0) || !(p.alpha <= 1) || (p.payoff != AAO_PUT && p.payoff != AAO_CALL)) {
       char buf[200];
       snprintf(buf, sizeof buf,
                "aao_batch_create: problem %d unsupported (mixed precision, op BS or LOCALVOL, "
-               "2 <= nt <= 4096 a power of two, 2 <= nx <= 4096, valid parameters)", i);
+               "2 <= nt <= 4096 with prime factors 2, 3, 5, 7 only, 2 <= nx <= 4096, valid parameters)", i);
       set_error(buf);
       return AAO_EINVAL;
     }
@@ -664,7 +704,9 @@ extern "C" int aao_batch_create(const aao_problem* ps, int n, int m, aao_batch**
     I.ch = (nx + I.tgrp - 1) / I.tgrp;
     if (I.ch < 2) I.ch = 2;
     I.cs = (I.ch & 1) ? I.ch + 2 : I.ch + 1;
-    I.P = tile_P(nt, 16 * kBT);
+    I.P = tile_P_max(nt);
+    if (!(nt & (nt - 1))) I.mr.nst = 0;
+    else mr_plan(nt, I.mr);
   }
   const size_t tail = o;
   size_t dsz = al(sizeof(BatchInst) * n) + al(sizeof(int) * n) + 256 + al(sizeof(aao_stats) * n);

@@ -85,134 +85,23 @@ int default_tile(int nx, int N, size_t rsize) {
 }
 
 // ------------------------------------------------------------ mixed-radix FFT along t
-// For nt not a power of two (prime factors 2, 3, 5, 7): the same steps (a) and (c) as
-// k_fft_fwd / k_fft_inv (two real columns per complex column, Lambda_alpha fused, bins
-// 0..nt/2 written frequency-major), the transform a shared-memory Stockham recursion over
-// the stages of MrPlan (radix 8, 4, 2, 3, 5, 7), out of place between two buffers of P
-// columns x N.
-// A stage of radix Q with Ns = the product of the earlier radices: butterfly j < N/Q of column
-// p reads elements j + q N/Q (q < Q), twiddles element q by w^(q (j mod Ns)), w = exp(-2 pi i /
-// (Ns Q)), takes their Q-point DFT and writes output m to (j / Ns) Ns Q + (j mod Ns) + m Ns.
-// Twiddle indices into tw[m] = exp(-2 pi i m / N): q (j mod Ns) N / (Ns Q) < N.
-// P = 2^lp columns per tile; j / Ns by a multiply-high with ceil(2^32 / Ns), exact for
-// j < 2^14 and Ns <= 2^13 (j < N/2 <= 4096 here).
-template <typename R> __host__ __device__ constexpr int mr_threads() { return sizeof(R) == 4 ? 512 : 256; }
-
-template <typename C, int Q>
-__device__ __forceinline__ void mr_stage(const C* __restrict__ in, C* __restrict__ out, int N, int lp, int Ns,
-                                         const C* __restrict__ tw) {
-  const int P = 1 << lp;
-  const int L = N / Q, ts = N / (Ns * Q);
-  const unsigned mag = Ns > 1 ? (unsigned)((0x100000000ull + (unsigned)Ns - 1) / (unsigned)Ns) : 0u;
-  C w[Q];  // Q-th roots of unity exp(-2 pi i s / Q)
-#pragma unroll
-  for (int s = 0; s < Q; ++s) w[s] = tw[s * L];
-  for (int e = threadIdx.x; e < L * P; e += blockDim.x) {
-    const int j = e >> lp, p = e & (P - 1);
-    const int jq = mag ? (int)__umulhi((unsigned)j, mag) : j;  // j / Ns
-    const int k = j - jq * Ns;
-    C a[Q];
-#pragma unroll
-    for (int q = 0; q < Q; ++q) a[q] = in[(j + q * L) * P + p];
-    if (k > 0) {
-#pragma unroll
-      for (int q = 1; q < Q; ++q) a[q] = cmul(a[q], tw[q * k * ts]);
-    }
-    C o[Q];
-    if constexpr (Q == 8) {
-      dft8(a);
-#pragma unroll
-      for (int m = 0; m < 8; ++m) o[m] = a[m];
-    } else if constexpr (Q == 4) {
-      dft4(a[0], a[1], a[2], a[3]);
-#pragma unroll
-      for (int m = 0; m < 4; ++m) o[m] = a[m];
-    } else if constexpr (Q == 2) {
-      o[0] = cadd(a[0], a[1]);
-      o[1] = csub(a[0], a[1]);
-    } else {
-      // the Q-point DFT by its definition: o_m = sum_q a_q w^(q m mod Q)
-#pragma unroll
-      for (int m = 0; m < Q; ++m) {
-        C acc = a[0];
-#pragma unroll
-        for (int q = 1; q < Q; ++q) acc = cadd(acc, cmul(a[q], w[(q * m) % Q]));
-        o[m] = acc;
-      }
-    }
-    const int base = jq * Ns * Q + k;
-#pragma unroll
-    for (int m = 0; m < Q; ++m) out[(base + m * Ns) * P + p] = o[m];
-  }
-}
-
-// forward DFT of the P columns in b0 (tw: the twiddle table in shared memory); returns the
-// buffer that holds the result
-template <typename C>
-__device__ C* mr_fft(C* b0, C* b1, int N, int lp, const MrPlan& pl, const C* __restrict__ tw) {
-  C* in = b0;
-  C* out = b1;
-  int Ns = 1;
-  for (int s = 0; s < pl.nst; ++s) {
-    const int Q = pl.rad[s];
-    switch (Q) {
-      case 2: mr_stage<C, 2>(in, out, N, lp, Ns, tw); break;
-      case 3: mr_stage<C, 3>(in, out, N, lp, Ns, tw); break;
-      case 4: mr_stage<C, 4>(in, out, N, lp, Ns, tw); break;
-      case 5: mr_stage<C, 5>(in, out, N, lp, Ns, tw); break;
-      case 7: mr_stage<C, 7>(in, out, N, lp, Ns, tw); break;
-      default: mr_stage<C, 8>(in, out, N, lp, Ns, tw); break;
-    }
-    __syncthreads();
-    Ns *= Q;
-    C* t = in;
-    in = out;
-    out = t;
-  }
-  return in;
-}
-
-// Both kernels are launched with mr_threads<R>() threads (their strided loops assume it).
+// For nt not a power of two (prime factors 2, 3, 5, 7): steps (a) and (c) by the mixed-radix
+// column tiles of precond_dev.cuh (fft_fwd_mr_tile / fft_inv_mr_tile), one tile per CTA.
+// Both kernels are launched with mr_threads<R>() threads (the tiles' strided loops assume it).
 template <typename R, typename IN>
 __global__ void __launch_bounds__(mr_threads<R>(), 2)
     k_fft_fwd_mr(const IN* __restrict__ v, C_t<R>* __restrict__ spec, int nx, int N, MrPlan pl, int lp, int pitch,
                  const R* __restrict__ lam, const C_t<R>* __restrict__ tw, const double* __restrict__ in_scale) {
   using C = C_t<R>;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int P = 1 << lp, W = 2 * P;
+  const int P = 1 << lp;
   C* b0 = reinterpret_cast<C*>(smraw);
   C* b1 = b0 + (size_t)P * N;
   C* stw = b1 + (size_t)P * N;  // twiddle table copy (N complex)
-  R* flat = reinterpret_cast<R*>(smraw);
   for (int m = threadIdx.x; m < N; m += blockDim.x) stw[m] = __ldg(&tw[m]);
   pdl_sync();
   const R sc = in_scale ? to_r<R>(*in_scale) : (R)1;
-  const int x0 = blockIdx.x * W;
-  // real column c of the tile is the real (c even) or imaginary (c odd) part of complex column c/2;
-  // unrolled so that a thread's global loads are in flight together
-  constexpr int NT = mr_threads<R>();
-#pragma unroll 8
-  for (int e = threadIdx.x; e < N * W; e += NT) {
-    const int t = e >> (lp + 1), c = e & (W - 1), x = x0 + c;
-    R val = (R)0;
-    if (x < nx) val = in_r<R>(__ldg(v + (size_t)t * nx + x)) * (__ldg(&lam[t]) * sc);
-    flat[e] = val;
-  }
-  __syncthreads();
-  const C* Z = mr_fft(b0, b1, N, lp, pl, stw);
-  // bins 0..N/2 of the two real columns: X_a = (Z_k + conj Z_{N-k}) / 2, X_b = (Z_k - conj Z_{N-k}) / 2i
-  const int K = N / 2 + 1;
-  for (int e = threadIdx.x; e < K * P; e += blockDim.x) {
-    const int k = e >> lp, p = e & (P - 1);
-    const C zk = Z[k * P + p];
-    const C zn = Z[(k == 0 ? 0 : N - k) * P + p];
-    const R h = (R)0.5;
-    const int x = x0 + 2 * p;
-    C* out = spec + (size_t)k * pitch + x;
-    if (!AAO_DCHECK(k <= N / 2 && x + 1 <= pitch)) continue;
-    if (x < nx) out[0] = cmk<C>(h * (zk.x + zn.x), h * (zk.y - zn.y));
-    if (x + 1 < nx) out[1] = cmk<C>(h * (zk.y + zn.y), h * (zn.x - zk.x));
-  }
+  fft_fwd_mr_tile<R, IN, mr_threads<R>()>(v, spec, nx, N, pl, lp, pitch, lam, sc, blockIdx.x * 2 * P, b0, b1, stw);
 }
 
 template <typename R, typename OUT>
@@ -221,41 +110,13 @@ __global__ void __launch_bounds__(mr_threads<R>(), 2)
                  const R* __restrict__ ilam, const C_t<R>* __restrict__ tw) {
   using C = C_t<R>;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int P = 1 << lp, W = 2 * P;
+  const int P = 1 << lp;
   C* b0 = reinterpret_cast<C*>(smraw);
   C* b1 = b0 + (size_t)P * N;
   C* stw = b1 + (size_t)P * N;  // twiddle table copy (N complex)
   for (int m = threadIdx.x; m < N; m += blockDim.x) stw[m] = __ldg(&tw[m]);
   pdl_sync();
-  const int x0 = blockIdx.x * W;
-  const int K = N / 2 + 1;
-  // Z_k = A_k + i B_k for all k from the half spectra (A_{N-k} = conj A_k), stored conjugated:
-  // the inverse DFT is the conjugate of the forward DFT of the conjugate
-  constexpr int NT = mr_threads<R>();
-#pragma unroll 4
-  for (int e = threadIdx.x; e < K * P; e += NT) {
-    const int k = e >> lp, p = e & (P - 1);
-    const int x = x0 + 2 * p;
-    const C* in = spec + (size_t)k * pitch + x;
-    C A = cmk<C>(0, 0), B = cmk<C>(0, 0);
-    if (x < nx) A = in[0];
-    if (x + 1 < nx) B = in[1];
-    const bool self = (k == 0) || (2 * k == N);  // DC and (N even) Nyquist bins of a real signal
-    if (self) { A.y = 0; B.y = 0; }
-    b0[k * P + p] = cmk<C>(A.x - B.y, -(A.y + B.x));
-    if (!self) b0[(N - k) * P + p] = cmk<C>(A.x + B.y, A.y - B.x);
-  }
-  __syncthreads();
-  const C* Y = mr_fft(b0, b1, N, lp, pl, stw);
-#pragma unroll 4
-  for (int e = threadIdx.x; e < N * W; e += NT) {
-    const int t = e >> (lp + 1), c = e & (W - 1), x = x0 + c;
-    if (x < nx) {
-      const C y = Y[t * P + (c >> 1)];
-      const R val = ((c & 1) ? -y.y : y.x) * __ldg(&ilam[t]);
-      if (AAO_DCHECK(t < N)) z[(size_t)t * nx + x] = (OUT)val;
-    }
-  }
+  fft_inv_mr_tile<R, OUT, mr_threads<R>()>(spec, z, nx, N, pl, lp, pitch, ilam, blockIdx.x * 2 * P, b0, b1, stw);
 }
 
 // tile of the mixed-radix kernels: the largest power of two P <= 16 with both buffers and the

@@ -149,3 +149,39 @@ def test_batch_distribution_512_instances(aao):
         b_ref = O.assemble_b(p)
         assert np.linalg.norm(b_ref - O.assemble_M(p) @ x) <= 1.01e-8 * np.linalg.norm(b_ref)
     bt.close()
+
+
+def test_batch_mixed_radix_nt_matches_oracle_and_single_instance(aao):
+    """Instances whose nt is not a power of two (prime factors 2, 3, 5, 7) take the mixed-radix FFT
+    tiles inside the persistent kernel; mixed with power-of-two instances in one batch, each
+    solution is the AaO solution (oracle residual, sequential CN) and agrees with the
+    single-instance solver, which takes the stand-alone mixed-radix kernels."""
+    ps = W.batch_instances(12, seed=23, nx_choices=(31, 63, 127), nt_choices=(12, 48, 96, 160, 210, 64), m=20)
+    assert any(p["nt"] & (p["nt"] - 1) for p in ps)
+    bt = aao.aao_batch_create(ps, 20)
+    bs, xs = vectors(bt), vectors(bt)
+    aao.aao_batch_rhs(bt, bs)
+    st = aao.batch_submit(bt, bs, xs, 1e-10, 200)
+    torch.cuda.synchronize()
+    for i, p in enumerate(ps):
+        assert st[i]["status"] == 0 and st[i]["rel_residual"] <= 1e-10, (i, p["nt"], st[i])
+        b_ref = O.assemble_b(p)
+        x = xs[i].cpu().numpy()
+        M = O.assemble_M(p)
+        assert np.linalg.norm(b_ref - M @ x) <= 1.01e-10 * np.linalg.norm(b_ref), (i, p["nt"])
+        U = O.sequential_cn(p)
+        assert np.abs(x - U.ravel()).max() <= 1e-7 * np.abs(U).max(), (i, p["nt"])
+        h = aao.aao_create(p)
+        x1 = torch.zeros_like(xs[i])
+        s1 = aao.fgmres_solve(h, bs[i], x1, 1e-10, 20, 200)
+        assert abs(s1["iterations"] - st[i]["iterations"]) <= 1, (p["nt"], s1, st[i])
+        h.close()
+    bt.close()
+
+
+def test_batch_rejects_nt_with_a_prime_factor_above_7(aao):
+    ps = W.batch_instances(3, seed=5, nx_choices=(31,), nt_choices=(16,), m=20)
+    ps[1] = W.with_(ps[1], nt=22)
+    with pytest.raises(aao.AaoError) as e:
+        aao.aao_batch_create(ps, 20)
+    assert e.value.code == aao.AAO_EINVAL
