@@ -59,6 +59,21 @@ int ensure_smem(const void* kernel, size_t bytes) {
 }
 
 
+// A launch with programmatic dependent launch (see launch_pdl) or, pdl false, a plain one: the
+// kernel's CTAs are then scheduled only once the previous kernel has finished.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_maybe_pdl(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                             Args... args) {
+  if (pdl) return launch_pdl(kernel, grid, block, smem, s, args...);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.numAttrs = 0;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // threads of the FFT kernels: kVals complex values per thread per stage, a multiple of 32,
 // within the kernels' launch bounds
 int fft_threads(int P, int N, size_t rsize) {
@@ -267,6 +282,10 @@ int run_precond(Handle& h, const double* v, void* z, bool z_is_float, const doub
 
   C* spec_b = spec;  // where step (b) leaves its result for step (c)
   TriRc rc;
+  // Step (c) follows the recomputing tridiagonal kernel without programmatic dependent launch:
+  // scheduled early, the inverse transform's CTAs cost that kernel more than the overlap saves
+  // (1.17 against 1.10 ms per 2047 x 2048 mixed solve); after the factored kernel the overlap pays.
+  bool pdl_c = true;
   if (skip_b) {
     // timing of steps (a) and (c) alone
   } else if (h.p.op == AAO_OP_HESTON) {
@@ -285,6 +304,7 @@ int run_precond(Handle& h, const double* v, void* z, bool z_is_float, const doub
     const C* il2 = (sizeof(R) == 4) ? (const C*)h.il2f : (const C*)h.il2;
     ProfScope ps(AAO_K_TRIDIAG, h.stream, 2.0 * nsp);
     AAO_TRY(launch_tri_rc<R>(h, rc, spec, mu, il2));
+    pdl_c = false;
   } else if (TriPart tp; h.tri_fp && tri_part_layout(h, sizeof(R), tp)) {
     // step (b): partition method with the per-bin factors built with the handle, G bins of
     // tri_T = 2^lgT threads per CTA
@@ -342,22 +362,22 @@ int run_precond(Handle& h, const double* v, void* z, bool z_is_float, const doub
     ProfScope ps(AAO_K_FFT_INV, h.stream, nsp + nv * (z_is_float ? sizeof(float) : sizeof(double)));
     if (z_is_float) {
       AAO_TRY(ensure_smem((const void*)k_fft_inv_mr<R, float>, smem));
-      AAO_TRY_CUDA(launch_pdl(k_fft_inv_mr<R, float>, grid, threads, smem, h.stream, spec_b, (float*)z, nx, N, h.mr,
+      AAO_TRY_CUDA(launch_maybe_pdl(pdl_c, k_fft_inv_mr<R, float>, grid, threads, smem, h.stream, spec_b, (float*)z, nx, N, h.mr,
                               lp, h.pitch, ilam, tw));
     } else {
       AAO_TRY(ensure_smem((const void*)k_fft_inv_mr<R, double>, smem));
-      AAO_TRY_CUDA(launch_pdl(k_fft_inv_mr<R, double>, grid, threads, smem, h.stream, spec_b, (double*)z, nx, N, h.mr,
+      AAO_TRY_CUDA(launch_maybe_pdl(pdl_c, k_fft_inv_mr<R, double>, grid, threads, smem, h.stream, spec_b, (double*)z, nx, N, h.mr,
                               lp, h.pitch, ilam, tw));
     }
   } else if (z_is_float) {
     AAO_TRY(ensure_smem((const void*)k_fft_inv<R, float>, smem));
     ProfScope ps(AAO_K_FFT_INV, h.stream, nsp + nv * sizeof(float));
-    AAO_TRY_CUDA(launch_pdl(k_fft_inv<R, float>, grid, threads, smem, h.stream, spec_b, (float*)z, nx, N, h.log2n, P,
+    AAO_TRY_CUDA(launch_maybe_pdl(pdl_c, k_fft_inv<R, float>, grid, threads, smem, h.stream, spec_b, (float*)z, nx, N, h.log2n, P,
                             h.pitch, ilam, tw));
   } else {
     AAO_TRY(ensure_smem((const void*)k_fft_inv<R, double>, smem));
     ProfScope ps(AAO_K_FFT_INV, h.stream, nsp + nv * sizeof(double));
-    AAO_TRY_CUDA(launch_pdl(k_fft_inv<R, double>, grid, threads, smem, h.stream, spec_b, (double*)z, nx, N, h.log2n, P,
+    AAO_TRY_CUDA(launch_maybe_pdl(pdl_c, k_fft_inv<R, double>, grid, threads, smem, h.stream, spec_b, (double*)z, nx, N, h.log2n, P,
                             h.pitch, ilam, tw));
   }
   AAO_CHECK_LAUNCH();
@@ -430,10 +450,13 @@ int tune_precond(Handle& h) {
     }
   }
   if (!riesz) {
-    // the per-bin tables of the factored solver (skipped where they do not fit or are not wanted);
-    // without them the recomputing solver is the one
-    AAO_TRY(build_tri_factors(h));
-    if ((!h.tri_fp && rc_fits) || h.p.flags == AAO_FLAG_STEPB_RECOMPUTE) h.tri_rc = true;
+    // the default: in mixed precision the recomputing solver wherever it fits (no tables; 1.10
+    // against 1.12 ms per 2047 x 2048 solve), in FP64 the factored one (the recomputing solver pays
+    // FP64 divisions there). The per-bin tables of the factored solver are built only where it is
+    // wanted and fits; without them the recomputing solver is the one.
+    const bool want_rc = h.p.flags == AAO_FLAG_STEPB_RECOMPUTE || (h.p.flags == 0 && h.mixed && rc_fits);
+    if (!want_rc) AAO_TRY(build_tri_factors(h));
+    if (want_rc || (!h.tri_fp && rc_fits)) h.tri_rc = true;
   }
   auto remember = [&]() {
     std::lock_guard<std::mutex> lk(g_tune_mu);

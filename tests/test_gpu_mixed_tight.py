@@ -11,14 +11,17 @@ u = 2^-24, C = 20. On the early levels this is up to 1/alpha times tighter than 
 and it has to hold on every level separately instead of on their sum, so an error on a few early or
 middle levels (a wrong power in the FP32 Lambda table, a slightly wrong input vector) fails it
 where the norm-wise bound passes. On the last level the two agree up to the norm of that level, so
-an error confined to the final levels is held only to the plain bound. Measured on the GPU (constants in units of u log2(2 nt)): 0.1 to 1.8 up to
-300 x 256, 11 at 2047 x 2048 (the shifted tridiagonal systems are worse conditioned there).
+an error confined to the final levels is held only to the plain bound. Measured on the GPU (constants in units of u log2(2 nt)): 0.1 to 1.9 up to
+300 x 256, 2.5 at 1023 x 1024, 11 at 2047 x 2048 (the shifted tridiagonal systems are worse
+conditioned there).
 
 The solver's FP32-copy path: inside fgmres_solve the residual and update kernels write an FP32 copy
 of each basis vector and the next apply reads it instead of the FP64 vector, a path the C entry
 point precond_apply does not take. One restart cycle of FGMRES(1) from a zero guess returns
 x_1 = y z_0 with z_0 = P_alpha^{-1} (b / ||b||) computed through that copy, so x_1 / y is compared
-with the oracle's P_alpha^{-1} b under the same level-by-level bound.
+with the oracle's P_alpha^{-1} b under the same level-by-level bound (y fitted with the level
+weights: an unweighted fit takes its scale from the amplified late levels and carries their error
+into the early ones). Both tridiagonal solvers of step (b) meet it with the same constants.
 """
 import math
 
@@ -113,7 +116,10 @@ def test_solver_fp32_copy_path_matches_oracle(aao, nx, nt):
         assert st["iterations"] == 1, st
         x1, bh = host(x), host(b)
         ref = O.precond_fft(p, bh)
-        y = float(np.dot(x1, ref) / np.dot(ref, ref))  # x_1 = y P^{-1} b
+        # x_1 = y P^{-1} b; y is fitted with the level weights alpha^(t/nt), so that the late levels,
+        # whose rounding errors step (c) amplifies, do not set the scale of the early ones
+        w = np.repeat(p["alpha"] ** (np.arange(nt) / nt), nx)
+        y = float(np.dot(w * x1, w * ref) / np.dot(w * ref, w * ref))
         assert y != 0.0
         e = level_error(p, bh, x1 / y, ref)
         assert e <= C, (p["op"], p["payoff"], e)
