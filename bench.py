@@ -48,6 +48,8 @@ CASES = {
     "localvol_2047x2048_recompute": lambda W: (W.with_(W.localvol_2047x2048("mixed"), step_b="recompute"), TOL, 30),
     "localvol_2047x2048_factored": lambda W: (W.with_(W.localvol_2047x2048("mixed"), step_b="factored"), TOL, 30),
     "localvol_2047x1536": lambda W: (W.with_(W.localvol_2047x2048("mixed"), nt=1536), TOL, 30),
+    "localvol_2047x1536_factored": lambda W: (W.with_(W.localvol_2047x2048("mixed"), nt=1536, step_b="factored"),
+                                              TOL, 30),
     "riesz_1023x512": lambda W: (W.riesz_1023x512(), TOL, W.riesz_1023x512()["m"]),
     "riesz_sym_1023x512": lambda W: (W.riesz_sym_1023x512(), TOL, W.riesz_sym_1023x512()["m"]),
     "heston_set1_nt96": lambda W: (W.heston_set1(96), 1e-9, 40),
