@@ -80,9 +80,9 @@ extern "C" {
  *  alpha       the free parameter of P_alpha (Eq. 3.1), 0 < alpha < 1 (alpha = 1 allowed:
  *              the classical block-circulant preconditioner P_1)
  *  flags       0, or one AAO_FLAG_STEPB_* to fix how the tridiagonal step (b) is solved (by
- *              default, AAO_MIXED: the recomputing method where one bin fits in shared memory;
- *              AAO_FP64: the factored method where one bin's staged tables fit; each falls back
- *              to the other; both give P_alpha^{-1} v up to rounding)
+ *              default, AAO_MIXED with nt a power of two: the recomputing method where one bin
+ *              fits in shared memory; otherwise the factored method where one bin's staged tables
+ *              fit; each falls back to the other; both give P_alpha^{-1} v up to rounding)
  *  stream      cudaStream_t on which all work is issued
  *  nv, kappa, eta, rho, v_max
  *              AAO_OP_HESTON only: nodes in v (3..512; nx 3..512 nodes in s), mean reversion,

@@ -282,9 +282,10 @@ int run_precond(Handle& h, const double* v, void* z, bool z_is_float, const doub
 
   C* spec_b = spec;  // where step (b) leaves its result for step (c)
   TriRc rc;
-  // Step (c) follows the recomputing tridiagonal kernel without programmatic dependent launch:
-  // scheduled early, the inverse transform's CTAs cost that kernel more than the overlap saves
-  // (1.17 against 1.10 ms per 2047 x 2048 mixed solve); after the factored kernel the overlap pays.
+  // Step (c) by the register tiles follows the recomputing tridiagonal kernel without programmatic
+  // dependent launch: scheduled early, the inverse transform's CTAs cost that kernel more than the
+  // overlap saves (1.17 against 1.10 ms per 2047 x 2048 mixed solve). After the factored kernel, and
+  // for the mixed-radix tiles after either, the overlap pays.
   bool pdl_c = true;
   if (skip_b) {
     // timing of steps (a) and (c) alone
@@ -362,11 +363,11 @@ int run_precond(Handle& h, const double* v, void* z, bool z_is_float, const doub
     ProfScope ps(AAO_K_FFT_INV, h.stream, nsp + nv * (z_is_float ? sizeof(float) : sizeof(double)));
     if (z_is_float) {
       AAO_TRY(ensure_smem((const void*)k_fft_inv_mr<R, float>, smem));
-      AAO_TRY_CUDA(launch_maybe_pdl(pdl_c, k_fft_inv_mr<R, float>, grid, threads, smem, h.stream, spec_b, (float*)z, nx, N, h.mr,
+      AAO_TRY_CUDA(launch_maybe_pdl(true, k_fft_inv_mr<R, float>, grid, threads, smem, h.stream, spec_b, (float*)z, nx, N, h.mr,
                               lp, h.pitch, ilam, tw));
     } else {
       AAO_TRY(ensure_smem((const void*)k_fft_inv_mr<R, double>, smem));
-      AAO_TRY_CUDA(launch_maybe_pdl(pdl_c, k_fft_inv_mr<R, double>, grid, threads, smem, h.stream, spec_b, (double*)z, nx, N, h.mr,
+      AAO_TRY_CUDA(launch_maybe_pdl(true, k_fft_inv_mr<R, double>, grid, threads, smem, h.stream, spec_b, (double*)z, nx, N, h.mr,
                               lp, h.pitch, ilam, tw));
     }
   } else if (z_is_float) {
@@ -450,11 +451,13 @@ int tune_precond(Handle& h) {
     }
   }
   if (!riesz) {
-    // the default: in mixed precision the recomputing solver wherever it fits (no tables; 1.10
-    // against 1.12 ms per 2047 x 2048 solve), in FP64 the factored one (the recomputing solver pays
-    // FP64 divisions there). The per-bin tables of the factored solver are built only where it is
+    // the default: in mixed precision with nt a power of two the recomputing solver wherever it
+    // fits (no tables; 1.092 against 1.105 ms per 2047 x 2048 solve); otherwise the factored one
+    // (FP64: the recomputing solver pays FP64 divisions; mixed radix: 1.075 against 1.053 ms per
+    // 2047 x 1536 solve). The per-bin tables of the factored solver are built only where it is
     // wanted and fits; without them the recomputing solver is the one.
-    const bool want_rc = h.p.flags == AAO_FLAG_STEPB_RECOMPUTE || (h.p.flags == 0 && h.mixed && rc_fits);
+    const bool want_rc = h.p.flags == AAO_FLAG_STEPB_RECOMPUTE ||
+                         (h.p.flags == 0 && h.mixed && h.mr.nst == 0 && rc_fits);
     if (!want_rc) AAO_TRY(build_tri_factors(h));
     if (want_rc || (!h.tri_fp && rc_fits)) h.tri_rc = true;
   }
