@@ -11,9 +11,9 @@ u = 2^-24, C = 20. On the early levels this is up to 1/alpha times tighter than 
 and it has to hold on every level separately instead of on their sum, so an error on a few early or
 middle levels (a wrong power in the FP32 Lambda table, a slightly wrong input vector) fails it
 where the norm-wise bound passes. On the last level the two agree up to the norm of that level, so
-an error confined to the final levels is held only to the plain bound. Measured on the GPU (constants in units of u log2(2 nt)): 0.1 to 1.9 up to
-300 x 256, 2.5 at 1023 x 1024, 11 at 2047 x 2048 (the shifted tridiagonal systems are worse
-conditioned there).
+an error confined to the final levels is held only to the plain bound. Measured on the GPU
+(constants in units of u log2(2 nt)): 0.1 to 1.9 up to 300 x 256, 2.5 at 1023 x 1024, 11 at
+2047 x 2048 (the shifted tridiagonal systems are worse conditioned there).
 
 The solver's FP32-copy path: inside fgmres_solve the residual and update kernels write an FP32 copy
 of each basis vector and the next apply reads it instead of the FP64 vector, a path the C entry
