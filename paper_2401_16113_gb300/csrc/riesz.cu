@@ -656,7 +656,7 @@ __global__ void __launch_bounds__(256) k_gj_colfix(float2* __restrict__ M, int n
 }
 
 // The rank-kGW update A_ij -= sum_q A_iq A_qj (q in the pivot block) on the tensor cores. A CTA
-// owns 128 rows (i0 ..) and kGjNT column tiles of 32 complex columns (j0 ..); per column tile one
+// owns 128 rows (i0 ..) and NT column tiles of 32 complex columns (j0 ..); per column tile one
 // accumulation D (128 x 64 FP32 in TMEM) = A' B'^T with the complex product embedded in a real one
 // along the contraction index kappa = 2q + s:
 //   A'[r][2q] = Re A_iq, A'[r][2q+1] = Im A_iq;
@@ -670,20 +670,20 @@ __global__ void __launch_bounds__(256) k_gj_colfix(float2* __restrict__ M, int n
 // Rows and columns inside the pivot block, and beyond nx, are not written. The wait for the MMAs
 // is bounded by wait_ns; on a timeout the CTA sets *err, waits (bounded) once more so that no MMA is
 // pending, frees TMEM and returns without writing.
-constexpr int kGjNT = 4;
 constexpr uint32_t kGjA = 4 * 16384u, kGjB = 4 * 8192u;  // one operand (hi or lo), bytes
 constexpr uint32_t kGjSmem = 2 * kGjA + 2 * kGjB + 64 + 1024;
 constexpr int kGjThreads = 256;
+template <int NT>
 __global__ void __launch_bounds__(kGjThreads, 1) k_gj_update_tc(float2* __restrict__ M, int nx, int p0, int wp,
                                                                 int* __restrict__ err, unsigned long long wait_ns) {
   using namespace tcg;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int k = blockIdx.z, i0 = blockIdx.y * 128, jbase = blockIdx.x * 32 * kGjNT;
+  const int k = blockIdx.z, i0 = blockIdx.y * 128, jbase = blockIdx.x * 32 * NT;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   float2* A = M + (size_t)k * nx * nx;
   const int pe = p0 + wp;
   // nothing to write: all rows in the pivot block (cannot happen for 128 rows) or all columns in it
-  if (jbase >= p0 && jbase + 32 * kGjNT <= pe) return;
+  if (jbase >= p0 && jbase + 32 * NT <= pe) return;
   const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(smraw);
   const uint32_t base = (s0 + 1023u) & ~1023u;
   unsigned char* gbase = smraw + (base - s0);
@@ -731,7 +731,7 @@ __global__ void __launch_bounds__(kGjThreads, 1) k_gj_update_tc(float2* __restri
   const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(gbase + 2 * kGjA + 2 * kGjB + 8);
   bool ok = true;
   int phase = 0;  // commits issued so far: the mbarrier phase of the next one
-  for (int nt = 0; nt < kGjNT && ok; ++nt) {
+  for (int nt = 0; nt < NT && ok; ++nt) {
     const int j0 = jbase + 32 * nt;
     if (j0 >= nx) break;
     if (j0 >= p0 && j0 + 32 <= pe) continue;  // every column of this tile is in the block
@@ -904,16 +904,25 @@ int gj_invert_batched(cudaStream_t stream, float2* M, int n, int K) {
   if (rc == AAO_OK &&
       (cudaFuncSetAttribute(k_gj_rowscale, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm) != cudaSuccess ||
        cudaFuncSetAttribute(k_gj_colfix, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm) != cudaSuccess ||
-       cudaFuncSetAttribute(k_gj_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGjSmem) !=
+       cudaFuncSetAttribute(k_gj_update_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGjSmem) !=
+           cudaSuccess ||
+       cudaFuncSetAttribute(k_gj_update_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGjSmem) !=
            cudaSuccess))
     rc = AAO_ECUDA;
   const int nbt = (n + kGW - 1) / kGW;
-  const dim3 gup((n + 32 * kGjNT - 1) / (32 * kGjNT), (n + 127) / 128, K);
+  // column tiles per CTA of the update: 16 for wide matrices (the staged pivot columns A' serve
+  // more tiles: 55 -> 51 ms for the 257 inverses of order 1023), 4 for narrow ones, which would
+  // otherwise leave too few CTAs (the Heston blocks of order 192: 52 against 53 ms)
+  const int NT = n >= 512 ? 16 : 4;
+  const dim3 gup((n + 32 * NT - 1) / (32 * NT), (n + 127) / 128, K);
   for (int p0 = 0; p0 < n && rc == AAO_OK; p0 += kGW) {
     const int wp = n - p0 < kGW ? n - p0 : kGW;
     k_gj_pivot<<<K, kGjPivThreads, 0, stream>>>(M, n, p0, wp, piv);
     k_gj_rowscale<<<dim3(nbt, K), 256, tsm, stream>>>(M, n, p0, wp, piv);
-    k_gj_update_tc<<<gup, kGjThreads, kGjSmem, stream>>>(M, n, p0, wp, err, tcg::kWaitNs);
+    if (NT == 16)
+      k_gj_update_tc<16><<<gup, kGjThreads, kGjSmem, stream>>>(M, n, p0, wp, err, tcg::kWaitNs);
+    else
+      k_gj_update_tc<4><<<gup, kGjThreads, kGjSmem, stream>>>(M, n, p0, wp, err, tcg::kWaitNs);
     k_gj_colfix<<<dim3(nbt, K), 256, tsm, stream>>>(M, n, p0, wp, piv);
     g_launches.fetch_add(3, std::memory_order_relaxed);
     rc = [&]() -> int { AAO_CHECK_LAUNCH(); return AAO_OK; }();
@@ -1028,7 +1037,7 @@ int riesz_build(Handle& h) {
     if (i >= 1) run += g[i];
     cl[i] = c0 * (-0.5 * g[0] - run) + (i == 0 ? -dr : 0.0);
   }
-  // circulant embedding of length N2 >= 2 nx - 1 and its spectrum (direct DFT in FP64)
+  // circulant embedding of length N2 >= 2 nx - 1 and its spectrum (radix-2 FFT in FP64)
   int l2 = 0;
   while ((1 << l2) < 2 * nx - 1) ++l2;
   const int n2 = 1 << l2;
@@ -1045,16 +1054,32 @@ int riesz_build(Handle& h) {
   }
   std::vector<double2> chat(n2), tw2(n2);
   const double sc = 0.5 * h.tau / n2;
-  for (int f = 0; f < n2; ++f) {
-    double re = 0.0, im = 0.0;
+  {
+    // chat[f] = sc sum_q cc[q] exp(-2 pi i f q / N2): iterative radix-2 decimation in time, inputs
+    // in bit-reversed order, twiddles exp(-2 pi i j / len) = (cs, sn)[j N2 / len]
+    std::vector<double> re(n2), im(n2, 0.0);
     for (int q = 0; q < n2; ++q) {
-      if (cc[q] == 0.0) continue;
-      const int idx = (int)(((long long)f * q) % n2);
-      re += cc[q] * cs[idx];
-      im += cc[q] * sn[idx];
+      int rq = 0;
+      for (int b = 0; b < l2; ++b) rq |= ((q >> b) & 1) << (l2 - 1 - b);
+      re[rq] = cc[q];
     }
-    chat[f] = make_double2(re * sc, im * sc);
-    tw2[f] = make_double2(cs[f], sn[f]);
+    for (int len = 2; len <= n2; len <<= 1) {
+      const int half = len >> 1, step = n2 / len;
+      for (int i0 = 0; i0 < n2; i0 += len)
+        for (int j = 0; j < half; ++j) {
+          const double wr = cs[j * step], wi = sn[j * step];
+          const int a = i0 + j, b = a + half;
+          const double tr = wr * re[b] - wi * im[b], ti = wr * im[b] + wi * re[b];
+          re[b] = re[a] - tr;
+          im[b] = im[a] - ti;
+          re[a] += tr;
+          im[a] += ti;
+        }
+    }
+    for (int f = 0; f < n2; ++f) {
+      chat[f] = make_double2(re[f] * sc, im[f] * sc);
+      tw2[f] = make_double2(cs[f], sn[f]);
+    }
   }
   std::vector<double> hcol(nx), hrow(nx), hcl(nx), tcol(nx), trow(nx);
   for (int k = 0; k < nx; ++k) {
