@@ -79,18 +79,22 @@ __global__ void __launch_bounds__(256) k_rz_cgemm_sum(const float2* __restrict__
 // hi*hi + hi*lo + lo*hi (the lo*lo term is below FP32 rounding): FP32 accuracy. Q's split is
 // made at create; the half spectrum's when it is staged. Operand tiles use the K-major layout
 // without swizzling: 8-row x 16-byte core matrices, adjacent along K 128 bytes apart and along
-// the rows 1024 bytes apart (32 contraction entries per staged chunk). Two chunks are staged
-// alternately; the MMAs of one run while the threads stage the next, a tcgen05.commit per chunk
-// arriving on that buffer's mbarrier. Every wait is bounded in time (the global nanosecond
+// the rows 1024 bytes apart (32 contraction entries per staged chunk). Chunks are staged into
+// tcg::kStages buffers in turn (with more than one, the MMAs of a chunk run while the threads
+// stage the next), a tcgen05.commit per chunk arriving on that buffer's mbarrier. Every wait is bounded in time (the global nanosecond
 // timer): when one gives up, the CTA raises a shared abort flag, the producer stops issuing, the
 // TMA loads and the MMAs already issued are waited for (bounded as well), and only then is TMEM
 // freed; the kernel records an error code and skips its output (the solve then reports
 // AAO_TIMEOUT instead of hanging).
 namespace tcg {
-constexpr int kM = 128, kN = 64, kKC = 32, kBins = kN / 2, kSeg = 4;  // kSeg contraction segments
+// One staged chunk per CTA and 8 contraction segments (576 CTAs of 48 KB, four per SM, so that the
+// chunks of different CTAs overlap): 43 us per apply at 1023 x 512 against 45 us with two chunks in
+// flight per CTA and 4 segments (288 CTAs of 96 KB, two per SM)
+constexpr int kM = 128, kN = 64, kKC = 32, kBins = kN / 2, kSeg = 8;  // kSeg contraction segments
+constexpr int kStages = 1;                                     // staged chunks in flight per CTA
 constexpr uint32_t kAop = kM * kKC * 4, kBop = kN * kKC * 4;  // bytes of one operand tile
 constexpr uint32_t kStage = 2 * kAop + 2 * kBop;               // hi and lo of both operands
-constexpr uint32_t kSmem = 2 * kStage + 64 + 1024;             // two stages, barriers, alignment
+constexpr uint32_t kSmem = kStages * kStage + 16 * kStages + 16 + 1024;  // stages, barriers, alignment
 constexpr unsigned long long kWaitNs = 2000000000ull;          // 2 s: far above any legitimate wait
 
 // A staged operand tile (rows x 32 contraction entries, K-major, no swizzling) keeps entry
@@ -174,7 +178,7 @@ __device__ __forceinline__ bool staging_all(bool v) {
 // (fault injection for tests of the timeout path) makes the producer issue no load, so that the
 // first wait for an operator tile runs out with nothing in flight.
 // Warps 0-3 stage the spectrum tiles and write the output (thread 0 issues the MMAs); warp 4 is
-// the TMA producer of the operator tiles, running ahead as far as the two buffers allow. Per
+// the TMA producer of the operator tiles, running ahead as far as the kStages buffers allow. Per
 // buffer: `full` completes when both operator tiles have landed (transaction count), `empty`
 // when the MMAs that read the buffer have finished (tcgen05.commit).
 // Timeout path: the thread whose wait gives up raises the shared abort flag; every other wait
@@ -183,7 +187,7 @@ __device__ __forceinline__ bool staging_all(bool v) {
 // phase of the last chunk it committed (a commit covers all earlier MMAs of the thread), so that
 // no copy into this CTA's shared memory and no MMA is pending when TMEM is freed and the CTA
 // exits. These drain waits ignore the flag and are bounded by wait_ns too.
-__global__ void __launch_bounds__(160, 1) k_rz_tc(const float2* __restrict__ A, int lda,
+__global__ void __launch_bounds__(160, 4) k_rz_tc(const float2* __restrict__ A, int lda,
                                                   const __grid_constant__ CUtensorMap thi,
                                                   const __grid_constant__ CUtensorMap tlo, float2* __restrict__ P,
                                                   int ldp, int Kb, int Mseg, int* __restrict__ err,
@@ -195,8 +199,9 @@ __global__ void __launch_bounds__(160, 1) k_rz_tc(const float2* __restrict__ A, 
   const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(smraw);
   const uint32_t base = (s0 + 1023u) & ~1023u;  // 1024-aligned operand tiles
   unsigned char* gbase = smraw + (base - s0);
-  const uint32_t bars = base + 2 * kStage;  // full[2] at +0, +8; empty[2] at +16, +24; TMEM slot +32
-  const uint32_t full0 = bars, empty0 = bars + 16, slot = bars + 32;
+  constexpr int S = kStages;
+  const uint32_t bars = base + S * kStage;  // full[S] at +0, empty[S] at +8 S, TMEM slot at +16 S
+  const uint32_t full0 = bars, empty0 = bars + 8 * S, slot = bars + 16 * S;
   const int tid = threadIdx.x, warp = tid >> 5;
   const int n0 = blockIdx.x * kM, b0 = blockIdx.y * kBins, seg = blockIdx.z;
   const int mbeg = seg * Mseg, nch = Mseg / kKC;
@@ -207,7 +212,7 @@ __global__ void __launch_bounds__(160, 1) k_rz_tc(const float2* __restrict__ A, 
 
   if (tid == 0) {
     abort_flag = 0;
-    for (int i = 0; i < 4; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bars + 8 * i) : "memory");
+    for (int i = 0; i < 2 * S; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bars + 8 * i) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -216,17 +221,17 @@ __global__ void __launch_bounds__(160, 1) k_rz_tc(const float2* __restrict__ A, 
   }
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(gbase + 2 * kStage + 32);
+  const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(gbase + S * kStage + 16 * S);
 
   bool ok = true;
   if (warp == 4) {
-    // producer: chunk c into buffer c & 1 once the MMAs of chunk c - 2 have released it
+    // producer: chunk c into buffer c % S once the MMAs of chunk c - S have released it
     if ((tid & 31) == 0) {
       int issued = 0;
       for (int c = 0; c < nch && !inject; ++c) {
-        const int buf = c & 1;
+        const int buf = c % S;
         if (abort_flag) break;
-        if (c >= 2 && !wait_parity(empty0 + 8 * buf, ((c - 2) >> 1) & 1, wait_ns, &abort_flag)) {
+        if (c >= S && !wait_parity(empty0 + 8 * buf, ((c - S) / S) & 1, wait_ns, &abort_flag)) {
           if (!abort_flag) { ok = false; raise_abort(); }
           break;
         }
@@ -239,8 +244,8 @@ __global__ void __launch_bounds__(160, 1) k_rz_tc(const float2* __restrict__ A, 
         issued = c + 1;
       }
       // drain: the last load issued into each buffer has landed (none newer shares its phase)
-      for (int c = issued - 2 > 0 ? issued - 2 : 0; c < issued; ++c)
-        if (!wait_parity(full0 + 8 * (c & 1), (c >> 1) & 1, wait_ns)) ok = false;
+      for (int c = issued - S > 0 ? issued - S : 0; c < issued; ++c)
+        if (!wait_parity(full0 + 8 * (c % S), (c / S) & 1, wait_ns)) ok = false;
       if (!ok) atomicExch(err, 1);
     }
     __syncwarp();  // the producer lane rejoins its warp before the final barrier
@@ -264,13 +269,13 @@ __global__ void __launch_bounds__(160, 1) k_rz_tc(const float2* __restrict__ A, 
     int committed = 0;  // chunks whose MMAs thread 0 has committed
     if (nch > 0) fetch_z(mbeg);
     for (int c = 0; c < nch; ++c) {
-      const int buf = c & 1;
+      const int buf = c % S;
       const uint32_t st = base + buf * kStage;
       unsigned char* gst = gbase + buf * kStage;
-      if (c >= 2) {
+      if (c >= S) {
         bool freed = true;
         if (tid == 0) {
-          freed = wait_parity(empty0 + 8 * buf, ((c - 2) >> 1) & 1, wait_ns, &abort_flag);
+          freed = wait_parity(empty0 + 8 * buf, ((c - S) / S) & 1, wait_ns, &abort_flag);
           if (!freed && !abort_flag) raise_abort();
         }
         __syncwarp();
@@ -305,7 +310,7 @@ __global__ void __launch_bounds__(160, 1) k_rz_tc(const float2* __restrict__ A, 
       // the operator tiles have landed (thread 0 waits; the outcome is shared at the barrier)
       bool landed = true;
       if (tid == 0) {
-        landed = wait_parity(full0 + 8 * buf, (c >> 1) & 1, wait_ns, &abort_flag);
+        landed = wait_parity(full0 + 8 * buf, (c / S) & 1, wait_ns, &abort_flag);
         if (!landed && !abort_flag) raise_abort();
       }
       __syncwarp();
@@ -332,14 +337,14 @@ __global__ void __launch_bounds__(160, 1) k_rz_tc(const float2* __restrict__ A, 
       bool done = true;
       if (tid == 0) {
         const int last = nch - 1;
-        done = wait_parity(empty0 + 8 * (last & 1), (last >> 1) & 1, wait_ns, &abort_flag);
+        done = wait_parity(empty0 + 8 * (last % S), (last / S) & 1, wait_ns, &abort_flag);
         if (!done && !abort_flag) raise_abort();
       }
       __syncwarp();
       ok = staging_all(done);
     } else if (!ok && tid == 0 && committed > 0) {
       const int last = committed - 1;
-      (void)wait_parity(empty0 + 8 * (last & 1), (last >> 1) & 1, wait_ns);
+      (void)wait_parity(empty0 + 8 * (last % S), (last / S) & 1, wait_ns);
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
