@@ -461,10 +461,23 @@ __global__ void __launch_bounds__(256) k_rz_matvec(const IN* __restrict__ x, dou
   __syncthreads();
   if (!am_last) return;
   __threadfence();
+  // the last block sums the partials with all its threads (one round trip), then thread 0 writes
+  __shared__ double fin[8][NA];
+  {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NA; ++q) {
+      double s = 0.0;
+      for (unsigned bb = threadIdx.x; bb < gridDim.x; bb += blockDim.x) s += __ldcg(part + (size_t)bb * kPartLd + q);
+      s = warp_sum(s);
+      if (lane == 0) fin[warp][q] = s;
+    }
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     for (int q = 0; q < NA; ++q) {
       double s = 0.0;
-      for (unsigned bb = 0; bb < gridDim.x; ++bb) s += __ldcg(part + (size_t)bb * kPartLd + q);
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += fin[w][q];
       if (MODE == 2) {
         scal[S_D1 + q] = s;
       } else {
