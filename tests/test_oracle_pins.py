@@ -207,6 +207,27 @@ def test_riesz_weights_beta2_is_three_point_laplacian():
     assert abs(g15[0] + 2 * g15[1:].sum()) < 2e-3
 
 
+@pytest.mark.parametrize("beta", [1.2, 1.5, 1.8])
+def test_riesz_weights_converge_to_the_closed_form_riesz_derivative(beta):
+    """The fractional centred difference -h^-beta sum_k g_k f(x - k h) (the weights and scaling of
+    the Riesz operator, Eq. 1.2) converges at second order to the Riesz derivative
+    -(-d^2/dx^2)^(beta/2) f. For the Lorentzian f = 1/(1 + x^2), whose Fourier transform is
+    pi exp(-|xi|), the derivative has the closed form -Gamma(beta + 1) Re[(1 - i x)^-(beta + 1)]
+    (f'' at beta = 2). A wrong sign, scale or exponent in the weights fails this at any beta."""
+    f = lambda x: 1.0 / (1.0 + x * x)
+    for x0 in (0.0, 0.7):
+        exact = -math.gamma(beta + 1.0) * ((1.0 - 1j * x0) ** (-(beta + 1.0))).real
+        errs = []
+        for h in (0.1, 0.05):
+            M = int(round(400.0 / h))  # the sum's tail beyond M h is below 1e-7
+            g = O.riesz_weights(beta, M + 1)
+            k = np.arange(-M, M + 1)
+            approx = -h ** (-beta) * np.sum(g[np.abs(k)] * f(x0 - k * h))
+            errs.append(abs(approx - exact))
+        assert errs[1] <= 4e-3 * math.gamma(beta + 1.0), (beta, x0, errs, exact)  # the derivative's scale
+        assert 3.8 <= errs[0] / errs[1] <= 4.2, (beta, x0, errs)
+
+
 def test_riesz_beta2_is_log_price_bs():
     """At beta = 2 the Riesz problem is Black-Scholes in x = ln S; compare with the closed form."""
     q = W.with_(W.riesz_1023x512(), beta=2.0, nx=255, nt=128)
