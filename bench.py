@@ -431,11 +431,8 @@ def run_ours(args):
     ms = sum(e0.elapsed_time(e1) for e0, e1 in evs) / args.steps
     dn, dms, dbytes, dflops = aao.aao_profile_read(dominant)
     aao.aao_profile_enable([])
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * n / (ms / 1e3)
+    ms = max_over_ranks(ms, "cuda")
+    value = whole_job_rate(world, n, ms / 1e3)
 
     # plain FP64 single-instance solve of the same workload (the metric's comparison)
     p64 = W.with_(p, precision="fp64")
@@ -470,7 +467,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         aao.fgmres_solve_host(h, bn, xn, TOL, p["m"], 300)
         e2e.append(time.perf_counter() - t0)
-    e2e_val = world * n / (sum(e2e) / len(e2e))
+    e2e_val = whole_job_rate(world, n, max_over_ranks(sum(e2e) / len(e2e), "cuda"))
 
     extras = {}
     if not args.no_extras:
@@ -555,6 +552,24 @@ def run_ours(args):
     h.close()
     if dist:
         tdist.destroy_process_group()
+
+
+def max_over_ranks(x, device):
+    """The largest of the ranks' values of x, on every rank (x itself without a process group or
+    with one rank): the job's time is its slowest rank's."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()) or tdist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank, seconds):
+    """Units per second of the whole job: every rank processes units_per_rank in the (slowest
+    rank's) time seconds."""
+    return world * units_per_rank / seconds
 
 
 def _note(what, t0):
