@@ -223,8 +223,8 @@ def ncu_traffic(kernel_class):
 
 
 def precond_roofline(prof, hbm_peak, unknowns):
-    """The preconditioner apply (its three kernel classes) as one unit, counted by the survey's
-    algorithmic bytes: 16 B per unknown (v read and z written once in FP64), over its device time
+    """The preconditioner apply (its three kernel classes) as one unit, counted by its algorithmic
+    bytes: 16 B per unknown (v read and z written once in FP64), over its device time
     per apply inside the solve. Beside it: the same time against the bytes the solve's applies
     actually move at their ends (FP32 copy of v in, FP32 z out: 8 B per unknown) and against the
     kernels' argument sizes (both exchanges of the half spectrum and any per-bin factor tables
