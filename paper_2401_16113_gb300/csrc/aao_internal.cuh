@@ -287,9 +287,12 @@ struct Handle {
   // z2_k = Q diag(D_k) Q^T z1_k with D_k,j = (1/lambda_{2,k}) / (mu_k - lambda_j)
   bool rz_sym = false;
   float2* rz_dk = nullptr;  // D, [k][j] (FP32 complex)
-  float2* rz_w = nullptr;   // D o (Q^T z1) per bin, K x rz_ldq complex
+  float2* rz_w = nullptr;   // the result of step (b) per bin, K x pitch complex (with drift)
   float2* rz_part = nullptr;  // partial products of the contraction segments
   int rz_ldq = 0;           // leading dimension of Q, Q^T, D and the workspaces
+  int rz_kpad = 0;          // bins padded to whole 32-bin tiles of the tensor-core products
+  int rz_nseg = 1;          // contraction segments of each tensor-core product
+  float *rz_bh = nullptr, *rz_bl = nullptr;  // their complex operand, TF32 head and tail, tiled
   // TF32 head and tail (x = hi + lo) of Q (rows x, entries j) and of Q^T (rows j, entries x):
   // the tensor-core operands, zero-padded to rz_ldq and stored in 8 x 16-byte core-matrix tiles
   float *rz_qh = nullptr, *rz_ql = nullptr;
@@ -297,8 +300,9 @@ struct Handle {
   int* rz_err = nullptr;    // set by a tensor-core product whose bounded wait gave up
   unsigned long long rz_wait_ns = 2000000000ull;  // bound of each wait in those products
   int rz_inject = 0;        // fault injection (aao_fault_inject): the products issue no operator load
-  // TMA tensor maps (CUtensorMap, 128 bytes each) of the tiled Q^T head, tail, Q head, tail
-  alignas(64) unsigned char rz_tmap[4 * 128] = {};
+  // TMA tensor maps (CUtensorMap, 128 bytes each) of the tiled Q^T head, tail, Q head, tail and of
+  // the complex operand's head and tail
+  alignas(64) unsigned char rz_tmap[6 * 128] = {};
 
   // Heston operator (AAO_OP_HESTON): grid hs_ns x hs_nv (nx = hs_ns * hs_nv unknowns per level);
   // per unknown the ten stencil coefficients of (tau/2) A (FP64 for the matvec, FP32 for step (b)),

@@ -574,7 +574,7 @@ void free_handle(Handle& h) {
                   h.muf, h.il2f, h.twf, h.lam, h.ilam, h.lamf, h.ilamf, h.spec, h.V, h.Z, h.w, h.scal, h.part,
                   h.counter, h.rz_chat, h.rz_tw, h.rz_hcol, h.rz_hrow, h.rz_hcl, h.tri, h.Vf, h.tri_fp,
                   h.tri_fv, h.tri_fpcr, h.rz_dk, h.rz_w,
-                  h.rz_part, h.rz_qh, h.rz_ql, h.rz_qth, h.rz_qtl, h.rz_err, h.rz_inv, h.hs_c, h.hs_tf,
+                  h.rz_part, h.rz_qh, h.rz_ql, h.rz_qth, h.rz_qtl, h.rz_bh, h.rz_bl, h.rz_err, h.rz_inv, h.hs_c, h.hs_tf,
                   h.hs_u0, h.hs_cf, h.hs_X, h.hs_G, h.hs_H};
   for (void* b : bufs)
     if (b) cudaFree(b);

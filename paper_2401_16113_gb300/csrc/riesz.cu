@@ -23,7 +23,8 @@
 //   k_rz_tc      step (b) when the operator is symmetric (no drift): with tau Abar = Q diag(lambda) Q^T
 //                (eigendecomposition at aao_create), z2_k = Q diag(D_k) Q^T z1_k for every bin is two
 //                products of the K x Nx complex half spectrum with the real Nx x Nx matrix Q, on the
-//                tensor cores (3xTF32); k_rz_cgemm_sum adds their contraction segments in order.
+//                tensor cores (3xTF32). k_rz_split makes each product's complex operand (TF32 head
+//                and tail, tiled for TMA); k_rz_cgemm_sum adds the last contraction segments in order.
 #include <math.h>
 #include <string.h>
 
@@ -77,24 +78,24 @@ __global__ void __launch_bounds__(256) k_rz_cgemm_sum(const float2* __restrict__
 // bits, and step (c) multiplies errors by up to 1/alpha, so each operand is split into a TF32
 // head and a TF32 tail (x = hi + lo) and three products are accumulated,
 // hi*hi + hi*lo + lo*hi (the lo*lo term is below FP32 rounding): FP32 accuracy. Q's split is
-// made at create; the half spectrum's when it is staged. Operand tiles use the K-major layout
-// without swizzling: 8-row x 16-byte core matrices, adjacent along K 128 bytes apart and along
-// the rows 1024 bytes apart (32 contraction entries per staged chunk). Chunks are staged into
-// tcg::kStages buffers in turn (with more than one, the MMAs of a chunk run while the threads
-// stage the next), a tcgen05.commit per chunk arriving on that buffer's mbarrier. Every wait is bounded in time (the global nanosecond
-// timer): when one gives up, the CTA raises a shared abort flag, the producer stops issuing, the
-// TMA loads and the MMAs already issued are waited for (bounded as well), and only then is TMEM
-// freed; the kernel records an error code and skips its output (the solve then reports
-// AAO_TIMEOUT instead of hanging).
+// made at create; the complex operand's by k_rz_split, which writes it in the same tiled layout
+// (row 2 bin + c), so that both operands reach shared memory by TMA. Operand tiles use the
+// K-major layout without swizzling: 8-row x 16-byte core matrices, adjacent along K 128 bytes
+// apart and along the rows 1024 bytes apart (32 contraction entries per chunk). A producer warp
+// streams the chunks into S buffers; one thread issues the MMAs of each chunk as soon as it has
+// landed and releases the buffer with a tcgen05.commit. Every wait is bounded in time (the global
+// nanosecond timer): when one gives up, the CTA raises a shared abort flag, the producer stops
+// issuing, the TMA loads and the MMAs already issued are waited for (bounded as well), and only
+// then is TMEM freed; the kernel records an error code and skips its output (the solve then
+// reports AAO_TIMEOUT instead of hanging).
 namespace tcg {
-// One staged chunk per CTA and 8 contraction segments (576 CTAs of 48 KB, four per SM, so that the
-// chunks of different CTAs overlap): 43 us per apply at 1023 x 512 against 45 us with two chunks in
-// flight per CTA and 4 segments (288 CTAs of 96 KB, two per SM)
-constexpr int kM = 128, kN = 64, kKC = 32, kBins = kN / 2, kSeg = 8;  // kSeg contraction segments
-constexpr int kStages = 1;                                     // staged chunks in flight per CTA
+constexpr int kM = 128, kN = 64, kKC = 32, kBins = kN / 2;
+constexpr int kSegMax = 8;                                     // contraction segments, at most
+constexpr int kStages = 3;  // chunk buffers per CTA (144 KB: one CTA per SM, the producer 3 chunks ahead)
 constexpr uint32_t kAop = kM * kKC * 4, kBop = kN * kKC * 4;  // bytes of one operand tile
 constexpr uint32_t kStage = 2 * kAop + 2 * kBop;               // hi and lo of both operands
-constexpr uint32_t kSmem = kStages * kStage + 16 * kStages + 16 + 1024;  // stages, barriers, alignment
+// dynamic shared memory of k_rz_tc<S>: S stages, 2 S + 1 mbarriers and the TMEM slot, alignment
+constexpr uint32_t smem_bytes(int S) { return (uint32_t)S * kStage + 16u * S + 16u + 1024u; }
 constexpr unsigned long long kWaitNs = 2000000000ull;          // 2 s: far above any legitimate wait
 
 // A staged operand tile (rows x 32 contraction entries, K-major, no swizzling) keeps entry
@@ -151,16 +152,16 @@ __device__ __forceinline__ bool wait_parity(uint32_t mbar, uint32_t parity, unsi
 }
 }  // namespace tcg
 
-// TMA load of one 16 KB operator tile: a box of 256 floats (8 core matrices of one row group) x 16
-// row groups from the tiled operator (see the tensor map made at create), completing on mbar
+// TMA load of one operand tile: a box of 256 floats (8 core matrices of one row group) x `rows / 8`
+// row groups from a tiled operand (see the tensor maps made at create), completing on mbar
 __device__ __forceinline__ void tma_tile(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t mbar) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
       ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar)
       : "memory");
 }
-// all 128 staging threads: true iff every one of them passes true (named barrier 1)
-__device__ __forceinline__ bool staging_all(bool v) {
+// all 128 threads of warps 0-3: true iff every one of them passes true (named barrier 1)
+__device__ __forceinline__ bool warps03_all(bool v) {
   uint32_t r;
   asm volatile(
       "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.and.pred q, 1, 128, p;\n\t"
@@ -171,49 +172,107 @@ __device__ __forceinline__ bool staging_all(bool v) {
   return r != 0;
 }
 
-// P[seg][k][n] for k < Kb (see above). A: complex rows of pitch lda; thi / tlo: tensor maps of the
-// operator's head and tail, stored tiled at create (row group rg, K group kg, row r, entry q at
-// float ((rg (ldo/4) + kg) 8 + r) 4 + q); segment seg = blockIdx.z covers [seg Mseg, (seg+1) Mseg),
-// Mseg a multiple of 32. err: set to 1 if a wait gave up. wait_ns bounds every wait; inject != 0
-// (fault injection for tests of the timeout path) makes the producer issue no load, so that the
-// first wait for an operator tile runs out with nothing in flight.
-// Warps 0-3 stage the spectrum tiles and write the output (thread 0 issues the MMAs); warp 4 is
-// the TMA producer of the operator tiles, running ahead as far as the kStages buffers allow. Per
-// buffer: `full` completes when both operator tiles have landed (transaction count), `empty`
-// when the MMAs that read the buffer have finished (tcgen05.commit).
+// The complex operand of a tensor-core product, B[2 bin + c][m] (c = re, im) for bin < Kpad and
+// m < L, written as TF32 head and tail in the tiled layout of the operands: entry (row r, m) at
+// float ((r/8 (L/4) + m/4) 8 + r%8) 4 + m%4. B[bin][m] = D[bin][m] sum_{s < nseg} P[s][bin][m]
+// (the segments added in order; no D factor when D is null) for bin < Kb and m < ncols, zero
+// elsewhere. One thread per (bin, group of 4 m): four lanes fill one 128-byte core matrix.
+__global__ void __launch_bounds__(256) k_rz_split(const float2* __restrict__ P, int ldp, size_t plane, int nseg,
+                                                  int Kb, int ncols, const float2* __restrict__ D, int ldd,
+                                                  float* __restrict__ Bh, float* __restrict__ Bl, int L, int Kpad) {
+  pdl_sync();
+  const int ng = L >> 2;
+  const size_t total = (size_t)Kpad * ng;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t t = e >> 2;  // (row group, K group) = (t / ng, t % ng)
+    const int b = (int)(e & 3);
+    const int kg = (int)(t % ng), bin = 4 * (int)(t / ng) + b, m0 = 4 * kg;
+    float4 re = make_float4(0.f, 0.f, 0.f, 0.f), im = re;
+    if (bin < Kb && m0 < ncols) {
+      const float4* src = reinterpret_cast<const float4*>(P + (size_t)bin * ldp + m0);
+      float4 u = __ldg(src), w = __ldg(src + 1);
+      for (int s = 1; s < nseg; ++s) {
+        const float4* q = reinterpret_cast<const float4*>(P + s * plane + (size_t)bin * ldp + m0);
+        const float4 u2 = __ldg(q), w2 = __ldg(q + 1);
+        u.x += u2.x; u.y += u2.y; u.z += u2.z; u.w += u2.w;
+        w.x += w2.x; w.y += w2.y; w.z += w2.z; w.w += w2.w;
+      }
+      if (D) {
+        const float4* dp = reinterpret_cast<const float4*>(D + (size_t)bin * ldd + m0);
+        const float4 d0 = __ldg(dp), d1 = __ldg(dp + 1);
+        u = make_float4(u.x * d0.x - u.y * d0.y, u.x * d0.y + u.y * d0.x, u.z * d0.z - u.w * d0.w,
+                        u.z * d0.w + u.w * d0.z);
+        w = make_float4(w.x * d1.x - w.y * d1.y, w.x * d1.y + w.y * d1.x, w.z * d1.z - w.w * d1.w,
+                        w.z * d1.w + w.w * d1.z);
+      }
+      re = make_float4(u.x, u.z, w.x, w.z);
+      im = make_float4(u.y, u.w, w.y, w.w);
+    }
+    const float4 rh = make_float4(tcg::tf32_rna(re.x), tcg::tf32_rna(re.y), tcg::tf32_rna(re.z), tcg::tf32_rna(re.w));
+    const float4 ih = make_float4(tcg::tf32_rna(im.x), tcg::tf32_rna(im.y), tcg::tf32_rna(im.z), tcg::tf32_rna(im.w));
+    const size_t o = (t * 8 + 2 * b) * 4;  // row 2 b (re) of the core matrix; row 2 b + 1 (im) follows
+    *reinterpret_cast<float4*>(Bh + o) = rh;
+    *reinterpret_cast<float4*>(Bh + o + 4) = ih;
+    *reinterpret_cast<float4*>(Bl + o) = make_float4(tcg::tf32_rna(re.x - rh.x), tcg::tf32_rna(re.y - rh.y),
+                                                     tcg::tf32_rna(re.z - rh.z), tcg::tf32_rna(re.w - rh.w));
+    *reinterpret_cast<float4*>(Bl + o + 4) = make_float4(tcg::tf32_rna(im.x - ih.x), tcg::tf32_rna(im.y - ih.y),
+                                                         tcg::tf32_rna(im.z - ih.z), tcg::tf32_rna(im.w - ih.w));
+  }
+}
+
+// P[seg][k][n] for k < Kb (see above). ahi / alo: tensor maps of the real operator's head and tail
+// (rows n, stored tiled at create); bhi / blo: those of the complex operand made by k_rz_split
+// (rows 2 bin + c, padded to a multiple of 32 bins). Segment seg = blockIdx.z covers contraction
+// entries [seg Mseg, (seg+1) Mseg), Mseg a multiple of 32. err: set to 1 if a wait gave up. wait_ns
+// bounds every wait; inject != 0 (fault injection for tests of the timeout path) makes the
+// producer issue no load, so that the first wait for a chunk runs out with nothing in flight.
+// Warp 4 is the TMA producer, running ahead as far as the S buffers allow; thread 0 issues the
+// MMAs; warps 0-3 then move the accumulator out of TMEM. Per buffer: `full` completes when the
+// four tiles of a chunk have landed (transaction count), `empty` when the MMAs that read the
+// buffer have finished (tcgen05.commit); `done` when all MMAs of the CTA have.
 // Timeout path: the thread whose wait gives up raises the shared abort flag; every other wait
 // returns at once when it sees the flag. The producer then issues nothing more and waits for the
-// `full` phases of the last load it issued into each buffer, and thread 0 waits for the `empty`
-// phase of the last chunk it committed (a commit covers all earlier MMAs of the thread), so that
-// no copy into this CTA's shared memory and no MMA is pending when TMEM is freed and the CTA
-// exits. These drain waits ignore the flag and are bounded by wait_ns too.
-__global__ void __launch_bounds__(160, 4) k_rz_tc(const float2* __restrict__ A, int lda,
-                                                  const __grid_constant__ CUtensorMap thi,
-                                                  const __grid_constant__ CUtensorMap tlo, float2* __restrict__ P,
-                                                  int ldp, int Kb, int Mseg, int* __restrict__ err,
-                                                  unsigned long long wait_ns, int inject) {
+// `full` phases of the last load it issued into each buffer, and thread 0 commits what it issued
+// to `done` and waits for it, so that no copy into this CTA's shared memory and no MMA is pending
+// when TMEM is freed and the CTA exits. These drain waits ignore the flag and are bounded by
+// wait_ns too.
+template <int S>
+__global__ void __launch_bounds__(160) k_rz_tc(const __grid_constant__ CUtensorMap ahi,
+                                               const __grid_constant__ CUtensorMap alo,
+                                               const __grid_constant__ CUtensorMap bhi,
+                                               const __grid_constant__ CUtensorMap blo, float2* __restrict__ P,
+                                               int ldp, int Kb, int Mseg, int* __restrict__ err,
+                                               unsigned long long wait_ns, int inject) {
   using namespace tcg;
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ volatile int abort_flag;
-  pdl_sync();
   const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(smraw);
   const uint32_t base = (s0 + 1023u) & ~1023u;  // 1024-aligned operand tiles
   unsigned char* gbase = smraw + (base - s0);
-  constexpr int S = kStages;
-  const uint32_t bars = base + S * kStage;  // full[S] at +0, empty[S] at +8 S, TMEM slot at +16 S
-  const uint32_t full0 = bars, empty0 = bars + 8 * S, slot = bars + 16 * S;
+  // full[S] at +0, empty[S] at +8 S, done at +16 S, TMEM slot at +16 S + 8
+  const uint32_t bars = base + S * kStage;
+  const uint32_t full0 = bars, empty0 = bars + 8 * S, done = bars + 16 * S, slot = done + 8;
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int n0 = blockIdx.x * kM, b0 = blockIdx.y * kBins, seg = blockIdx.z;
-  const int mbeg = seg * Mseg, nch = Mseg / kKC;
+  const int n0 = blockIdx.x * kM, b0 = blockIdx.y * kBins;
+  const int nch = Mseg / kKC, c0 = blockIdx.z * nch;  // chunks of this segment: [c0, c0 + nch)
   auto raise_abort = [&]() {
     abort_flag = 1;
     __threadfence_block();
   };
 
+  // set-up that reads nothing the previous kernel writes, before the wait for it (programmatic
+  // dependent launch): barriers, the TMEM columns, the tensor maps (kernel parameters)
   if (tid == 0) {
     abort_flag = 0;
-    for (int i = 0; i < 2 * S; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bars + 8 * i) : "memory");
+    for (int i = 0; i < 2 * S + 1; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bars + 8 * i) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (tid == 128) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&ahi)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&alo)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&bhi)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&blo)) : "memory");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(kN) : "memory");
@@ -221,12 +280,13 @@ __global__ void __launch_bounds__(160, 4) k_rz_tc(const float2* __restrict__ A, 
   }
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(gbase + S * kStage + 16 * S);
+  const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(gbase + (slot - base));
+  pdl_sync();
 
-  bool ok = true;
   if (warp == 4) {
     // producer: chunk c into buffer c % S once the MMAs of chunk c - S have released it
     if ((tid & 31) == 0) {
+      bool ok = true;
       int issued = 0;
       for (int c = 0; c < nch && !inject; ++c) {
         const int buf = c % S;
@@ -235,12 +295,13 @@ __global__ void __launch_bounds__(160, 4) k_rz_tc(const float2* __restrict__ A, 
           if (!abort_flag) { ok = false; raise_abort(); }
           break;
         }
-        const uint32_t st = base + buf * kStage;
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full0 + 8 * buf), "r"(2 * kAop)
-                     : "memory");
-        const int x = ((mbeg + c * kKC) / kKC) * 256, y = n0 / 8;
-        tma_tile(st, &thi, x, y, full0 + 8 * buf);
-        tma_tile(st + kAop, &tlo, x, y, full0 + 8 * buf);
+        const uint32_t st = base + buf * kStage, fb = full0 + 8 * buf;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(kStage) : "memory");
+        const int x = (c0 + c) * 256;
+        tma_tile(st, &ahi, x, n0 / 8, fb);
+        tma_tile(st + kAop, &alo, x, n0 / 8, fb);
+        tma_tile(st + 2 * kAop, &bhi, x, b0 / 4, fb);
+        tma_tile(st + 2 * kAop + kBop, &blo, x, b0 / 4, fb);
         issued = c + 1;
       }
       // drain: the last load issued into each buffer has landed (none newer shares its phase)
@@ -250,107 +311,45 @@ __global__ void __launch_bounds__(160, 4) k_rz_tc(const float2* __restrict__ A, 
     }
     __syncwarp();  // the producer lane rejoins its warp before the final barrier
   } else {
-    // spectrum piece i of this thread: core matrix cm = e >> 3 (row group: bins 4 (cm >> 3) ..,
-    // K group cm & 7), lane pair (b, t) = ((e & 7) >> 1, e & 1) of bin 4 (cm >> 3) + b. Lane t loads
-    // the complex at K entries 4 (cm & 7) + 2 t + {0, 1}; the pair swaps halves with a shuffle, so
-    // that each lane holds the bin's four entries and writes one whole 16-byte core-matrix row,
-    // row 2 b + t (re for t = 0, im for t = 1) and then row 2 b + 1 - t: eight lanes fill one
-    // 128-byte core matrix per store (no bank conflicts)
-    float4 zv[4];
-    auto fetch_z = [&](int m0) {
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int e = tid + 128 * i, cm = e >> 3, l8 = e & 7;
-        const int bin = b0 + 4 * (cm >> 3) + (l8 >> 1), x = 4 * (cm & 7) + 2 * (l8 & 1);
-        zv[i] = bin < Kb ? __ldg(reinterpret_cast<const float4*>(A + (size_t)bin * lda + m0 + x))
-                         : make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-    };
-    int committed = 0;  // chunks whose MMAs thread 0 has committed
-    if (nch > 0) fetch_z(mbeg);
-    for (int c = 0; c < nch; ++c) {
-      const int buf = c % S;
-      const uint32_t st = base + buf * kStage;
-      unsigned char* gst = gbase + buf * kStage;
-      if (c >= S) {
-        bool freed = true;
-        if (tid == 0) {
-          freed = wait_parity(empty0 + 8 * buf, ((c - S) / S) & 1, wait_ns, &abort_flag);
-          if (!freed && !abort_flag) raise_abort();
+    bool mma_ok = true;
+    if (tid == 0) {
+      int committed = 0;
+      for (int c = 0; c < nch; ++c) {
+        const int buf = c % S;
+        if (!wait_parity(full0 + 8 * buf, (c / S) & 1, wait_ns, &abort_flag)) {
+          if (!abort_flag) raise_abort();
+          break;
         }
-        __syncwarp();
-        ok = staging_all(freed);
-        if (!ok) break;
-      }
-      float4 v[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) v[i] = zv[i];
-      if (c + 1 < nch) fetch_z(mbeg + (c + 1) * kKC);
-      unsigned char* bh = gst + 2 * kAop;
-      unsigned char* bl = bh + kBop;
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int e = tid + 128 * i, cm = e >> 3, l8 = e & 7, b = l8 >> 1, t = l8 & 1;
-        const float4 u = make_float4(__shfl_xor_sync(0xffffffffu, v[i].x, 1), __shfl_xor_sync(0xffffffffu, v[i].y, 1),
-                                     __shfl_xor_sync(0xffffffffu, v[i].z, 1), __shfl_xor_sync(0xffffffffu, v[i].w, 1));
-        const float4 lo2 = t ? u : v[i], hi2 = t ? v[i] : u;  // K entries 0, 1 and 2, 3 of the group
-        const float4 re = make_float4(lo2.x, lo2.z, hi2.x, hi2.z), im = make_float4(lo2.y, lo2.w, hi2.y, hi2.w);
-        const float4 first = t ? im : re, second = t ? re : im;
-        const uint32_t off1 = (uint32_t)(cm * 128 + (2 * b + t) * 16), off2 = (uint32_t)(cm * 128 + (2 * b + 1 - t) * 16);
-        const float4 h1 = make_float4(tf32_rna(first.x), tf32_rna(first.y), tf32_rna(first.z), tf32_rna(first.w));
-        const float4 h2 = make_float4(tf32_rna(second.x), tf32_rna(second.y), tf32_rna(second.z), tf32_rna(second.w));
-        *reinterpret_cast<float4*>(bh + off1) = h1;
-        *reinterpret_cast<float4*>(bh + off2) = h2;
-        *reinterpret_cast<float4*>(bl + off1) = make_float4(tf32_rna(first.x - h1.x), tf32_rna(first.y - h1.y),
-                                                            tf32_rna(first.z - h1.z), tf32_rna(first.w - h1.w));
-        *reinterpret_cast<float4*>(bl + off2) = make_float4(tf32_rna(second.x - h2.x), tf32_rna(second.y - h2.y),
-                                                            tf32_rna(second.z - h2.z), tf32_rna(second.w - h2.w));
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      // the operator tiles have landed (thread 0 waits; the outcome is shared at the barrier)
-      bool landed = true;
-      if (tid == 0) {
-        landed = wait_parity(full0 + 8 * buf, (c / S) & 1, wait_ns, &abort_flag);
-        if (!landed && !abort_flag) raise_abort();
-      }
-      __syncwarp();
-      ok = staging_all(landed);
-      if (!ok) break;
-      if (tid == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t st = base + buf * kStage;
 #pragma unroll
         for (int ks = 0; ks < kKC / 8; ++ks) {
           const uint32_t ko = ks * 256;  // two core matrices along K per MMA
           const uint64_t ah = sdesc(st + ko), al = sdesc(st + kAop + ko);
-          const uint64_t bh2 = sdesc(st + 2 * kAop + ko), bl2 = sdesc(st + 2 * kAop + kBop + ko);
-          mma(tmem, ah, bh2, (c > 0 || ks > 0) ? 1u : 0u);
-          mma(tmem, ah, bl2, 1u);
-          mma(tmem, al, bh2, 1u);
+          const uint64_t bh = sdesc(st + 2 * kAop + ko), bl = sdesc(st + 2 * kAop + kBop + ko);
+          mma(tmem, ah, bh, (c > 0 || ks > 0) ? 1u : 0u);
+          mma(tmem, ah, bl, 1u);
+          mma(tmem, al, bh, 1u);
         }
         commit(empty0 + 8 * buf);
         committed = c + 1;
       }
-      __syncwarp();
-    }
-    // all MMAs finished: the last commit's phase (on the timeout path a drain that ignores the flag)
-    if (ok && nch > 0) {
-      bool done = true;
-      if (tid == 0) {
-        const int last = nch - 1;
-        done = wait_parity(empty0 + 8 * (last % S), (last / S) & 1, wait_ns, &abort_flag);
-        if (!done && !abort_flag) raise_abort();
+      // all MMAs issued by this thread finished (on the timeout path as well: a drain that
+      // ignores the flag)
+      if (committed > 0) {
+        commit(done);
+        if (!wait_parity(done, 0, wait_ns)) committed = -1;
       }
-      __syncwarp();
-      ok = staging_all(done);
-    } else if (!ok && tid == 0 && committed > 0) {
-      const int last = committed - 1;
-      (void)wait_parity(empty0 + 8 * (last % S), (last / S) & 1, wait_ns);
+      mma_ok = committed == nch;
+      if (!mma_ok && !abort_flag) raise_abort();
     }
+    __syncwarp();
+    const bool ok = warps03_all(mma_ok);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
       // warp w reads TMEM lanes 32 w .. 32 w + 31 (output columns n0 + 32 w + lane), 64 columns
       const int n = n0 + 32 * warp + (tid & 31);
-      float2* Ps = P + (size_t)seg * Kb * ldp;
+      float2* Ps = P + (size_t)blockIdx.z * Kb * ldp;
 #pragma unroll
       for (int half = 0; half < 2; ++half) {
         uint32_t v[32];
@@ -990,21 +989,23 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 // the 2-D map over a tiled operator: rows of ldq * 8 floats (one row group: ldq / 4 core
 // matrices of 8 rows x 4 entries), ldq / 8 row groups; boxes of 256 floats x 16 row groups
-int encode_operator_map(void* map, float* tiled, int ldq) {
+// tensor map of an operand stored tiled (see k_rz_tc): `rows` rows of L contraction entries, as
+// L * 8 floats per 8-row group; one TMA box is 32 entries (8 core matrices) x box_rows rows
+int encode_tiled_map(void* map, float* tiled, int L, int rows, int box_rows) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) {
     set_error("aao_create: cuTensorMapEncodeTiled is not available");
     return AAO_ECUDA;
   }
-  const cuuint64_t dims[2] = {(cuuint64_t)ldq * 8, (cuuint64_t)ldq / 8};
-  const cuuint64_t strides[1] = {(cuuint64_t)ldq * 8 * sizeof(float)};
-  const cuuint32_t box[2] = {256, 16};
+  const cuuint64_t dims[2] = {(cuuint64_t)L * 8, (cuuint64_t)rows / 8};
+  const cuuint64_t strides[1] = {(cuuint64_t)L * 8 * sizeof(float)};
+  const cuuint32_t box[2] = {256, (cuuint32_t)box_rows / 8};
   const cuuint32_t estr[2] = {1, 1};
   const CUresult r = enc(reinterpret_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, tiled, dims, strides,
                          box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
-    set_error("aao_create: cuTensorMapEncodeTiled failed for the spectral operator");
+    set_error("aao_create: cuTensorMapEncodeTiled failed for an operand of the spectral step");
     return AAO_ECUDA;
   }
   return AAO_OK;
@@ -1188,20 +1189,41 @@ int riesz_build(Handle& h) {
     AAO_TRY(up(&h.rz_ql, ql));
     AAO_TRY(up(&h.rz_qth, qth));
     AAO_TRY(up(&h.rz_qtl, qtl));
-    AAO_TRY(encode_operator_map(h.rz_tmap + 0 * 128, h.rz_qth, ldq));
-    AAO_TRY(encode_operator_map(h.rz_tmap + 1 * 128, h.rz_qtl, ldq));
-    AAO_TRY(encode_operator_map(h.rz_tmap + 2 * 128, h.rz_qh, ldq));
-    AAO_TRY(encode_operator_map(h.rz_tmap + 3 * 128, h.rz_ql, ldq));
+    // the complex operand of the products (TF32 head and tail, tiled, 2 Kpad rows)
+    const int Kpad = ((K + tcg::kBins - 1) / tcg::kBins) * tcg::kBins;
+    const size_t nb = (size_t)2 * Kpad * ldq;
+    AAO_TRY_CUDA(cudaMalloc(&h.rz_bh, sizeof(float) * nb));
+    AAO_TRY_CUDA(cudaMalloc(&h.rz_bl, sizeof(float) * nb));
+    AAO_TRY_CUDA(cudaMemsetAsync(h.rz_bh, 0, sizeof(float) * nb, h.stream));
+    AAO_TRY_CUDA(cudaMemsetAsync(h.rz_bl, 0, sizeof(float) * nb, h.stream));
+    AAO_TRY(encode_tiled_map(h.rz_tmap + 0 * 128, h.rz_qth, ldq, ldq, tcg::kM));
+    AAO_TRY(encode_tiled_map(h.rz_tmap + 1 * 128, h.rz_qtl, ldq, ldq, tcg::kM));
+    AAO_TRY(encode_tiled_map(h.rz_tmap + 2 * 128, h.rz_qh, ldq, ldq, tcg::kM));
+    AAO_TRY(encode_tiled_map(h.rz_tmap + 3 * 128, h.rz_ql, ldq, ldq, tcg::kM));
+    AAO_TRY(encode_tiled_map(h.rz_tmap + 4 * 128, h.rz_bh, ldq, 2 * Kpad, tcg::kN));
+    AAO_TRY(encode_tiled_map(h.rz_tmap + 5 * 128, h.rz_bl, ldq, 2 * Kpad, tcg::kN));
     AAO_TRY_CUDA(cudaMalloc(&h.rz_err, sizeof(int)));
     AAO_TRY_CUDA(cudaMemsetAsync(h.rz_err, 0, sizeof(int), h.stream));
-    AAO_TRY_CUDA(cudaFuncSetAttribute(k_rz_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tcg::kSmem));
+    const uint32_t tc_smem = tcg::smem_bytes(tcg::kStages);
+    AAO_TRY_CUDA(cudaFuncSetAttribute(k_rz_tc<tcg::kStages>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem));
+    // contraction segments: the fewest (a power of two dividing the ldq / 32 chunks, at most
+    // kSegMax) whose grid fills 90% of the resident CTA slots
+    int per_sm = 0, sms = h.sms;
+    AAO_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rz_tc<tcg::kStages>, 160, tc_smem));
+    if (sms <= 0) {
+      int dev = 0;
+      AAO_TRY_CUDA(cudaGetDevice(&dev));
+      AAO_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    const long slots = (long)(per_sm > 0 ? per_sm : 1) * sms, ctas = (long)(ldq / tcg::kM) * (Kpad / tcg::kBins);
+    int nseg = 1;
+    while (2 * nseg <= tcg::kSegMax && (ldq / tcg::kKC) % (2 * nseg) == 0 && 10 * ctas * nseg < 9 * slots) nseg *= 2;
+    h.rz_nseg = nseg;
+    h.rz_kpad = Kpad;
     AAO_TRY(up(&h.rz_dk, dk));
-    AAO_TRY_CUDA(cudaMalloc(&h.rz_w, sizeof(float2) * (size_t)K * ldq));
-    AAO_TRY_CUDA(cudaMalloc(&h.rz_part, sizeof(float2) * (size_t)tcg::kSeg * K * ldq));
+    AAO_TRY_CUDA(cudaMalloc(&h.rz_part, sizeof(float2) * (size_t)nseg * K * ldq));
     h.rz_ldq = ldq;
-    // the padding columns of the spectrum and of the workspace stay zero: every kernel writes
-    // columns < nx only, or zeros
-    AAO_TRY_CUDA(cudaMemsetAsync(h.rz_w, 0, sizeof(float2) * (size_t)K * ldq, h.stream));
+    // the padding columns of the spectrum stay zero: every kernel writes columns < nx only, or zeros
     AAO_TRY_CUDA(cudaMemsetAsync(h.spec, 0, sizeof(float2) * (size_t)K * h.pitch, h.stream));
     AAO_TRY_CUDA(cudaStreamSynchronize(h.stream));
     h.rz_sym = true;
@@ -1292,25 +1314,27 @@ int riesz_solve_bins(Handle& h, void* spec, void** result) {
   *result = spec;
   if (h.rz_sym) {
     // W = (Z1 Q) o D, then Z2 = W Q^T (rows: bins; the half spectrum is [k][x]) on the tensor
-    // cores, each product in tcg::kSeg contraction segments added in order
-    const int ldq = h.rz_ldq;
+    // cores: k_rz_split tiles and splits the complex operand (for the second product it also adds
+    // the first one's contraction segments in order and multiplies by D), k_rz_tc forms the
+    // segments' partial products, k_rz_cgemm_sum adds the second product's
+    const int ldq = h.rz_ldq, Kpad = h.rz_kpad, nseg = h.rz_nseg;
     const double nq = (double)ldq * ldq;
     ProfScope ps(AAO_K_TRIDIAG, h.stream, 2.0 * (nq * 8.0 + 2.0 * (double)h.K * ldq * 8.0));
-    // segments: as many as keep whole 32-entry chunks (the contraction lengths are multiples of 64)
-    auto segs = [](int mp) { return mp % (tcg::kKC * tcg::kSeg) == 0 ? tcg::kSeg : (mp % (2 * tcg::kKC) == 0 ? 2 : 1); };
-    const int s1 = segs(h.pitch), s2 = segs(ldq);
-    const dim3 g1(ldq / tcg::kM, (h.K + tcg::kBins - 1) / tcg::kBins, s1);
-    const dim3 g2(ldq / tcg::kM, (h.K + tcg::kBins - 1) / tcg::kBins, s2);
+    const dim3 g(ldq / tcg::kM, Kpad / tcg::kBins, nseg);
+    const uint32_t smem = tcg::smem_bytes(tcg::kStages);
+    const int bgrid = (int)(((size_t)Kpad * (ldq / 4) + 255) / 256);
     const int sgrid = (int)((((size_t)h.K * ldq / 2) + 255) / 256);
-    CUtensorMap m[4];
+    CUtensorMap m[6];
     memcpy(m, h.rz_tmap, sizeof m);
-    AAO_TRY_CUDA(launch_pdl(k_rz_tc, g1, 160, tcg::kSmem, h.stream, (const float2*)spec, h.pitch, m[0], m[1],
-                            h.rz_part, ldq, h.K, h.pitch / s1, h.rz_err, h.rz_wait_ns, h.rz_inject));
-    AAO_TRY_CUDA(launch_pdl(k_rz_cgemm_sum, sgrid, 256, 0, h.stream, (const float2*)h.rz_part, ldq, h.K, ldq, s1,
-                            h.rz_w, ldq, (const float2*)h.rz_dk, ldq));
-    AAO_TRY_CUDA(launch_pdl(k_rz_tc, g2, 160, tcg::kSmem, h.stream, (const float2*)h.rz_w, ldq, m[2], m[3],
-                            h.rz_part, ldq, h.K, ldq / s2, h.rz_err, h.rz_wait_ns, h.rz_inject));
-    AAO_TRY_CUDA(launch_pdl(k_rz_cgemm_sum, sgrid, 256, 0, h.stream, (const float2*)h.rz_part, ldq, h.K, h.pitch, s2,
+    AAO_TRY_CUDA(launch_pdl(k_rz_split, bgrid, 256, 0, h.stream, (const float2*)spec, h.pitch, (size_t)0, 1, h.K,
+                            h.pitch, (const float2*)nullptr, 0, h.rz_bh, h.rz_bl, ldq, Kpad));
+    AAO_TRY_CUDA(launch_pdl(k_rz_tc<tcg::kStages>, g, 160, smem, h.stream, m[0], m[1], m[4], m[5], h.rz_part, ldq, h.K,
+                            ldq / nseg, h.rz_err, h.rz_wait_ns, h.rz_inject));
+    AAO_TRY_CUDA(launch_pdl(k_rz_split, bgrid, 256, 0, h.stream, (const float2*)h.rz_part, ldq, (size_t)h.K * ldq, nseg,
+                            h.K, ldq, (const float2*)h.rz_dk, ldq, h.rz_bh, h.rz_bl, ldq, Kpad));
+    AAO_TRY_CUDA(launch_pdl(k_rz_tc<tcg::kStages>, g, 160, smem, h.stream, m[2], m[3], m[4], m[5], h.rz_part, ldq, h.K,
+                            ldq / nseg, h.rz_err, h.rz_wait_ns, h.rz_inject));
+    AAO_TRY_CUDA(launch_pdl(k_rz_cgemm_sum, sgrid, 256, 0, h.stream, (const float2*)h.rz_part, ldq, h.K, h.pitch, nseg,
                             (float2*)spec, h.pitch, (const float2*)nullptr, ldq));
     AAO_CHECK_LAUNCH();
     return AAO_OK;
