@@ -116,6 +116,11 @@ int validate(const aao_problem* p) {
 
 struct aao_handle {
   aao::Handle h;
+  // device copies of b and x for fgmres_solve_host, made at its first call and kept until
+  // aao_destroy (an allocation per call would map fresh pages each time: the default memory pool
+  // releases freed memory at every synchronisation)
+  double* host_b = nullptr;
+  double* host_x = nullptr;
 };
 
 using namespace aao;
@@ -155,6 +160,8 @@ int aao_create(const aao_problem* p, aao_handle** out) {
 int aao_destroy(aao_handle* hd) {
   if (!hd) return AAO_OK;
   cudaStreamSynchronize(hd->h.stream);
+  if (hd->host_b) cudaFree(hd->host_b);
+  if (hd->host_x) cudaFree(hd->host_x);
   free_handle(hd->h);
   delete hd;
   return AAO_OK;
@@ -222,14 +229,12 @@ int fgmres_solve_host(aao_handle* hd, const double* b_host, double* x_host, doub
   if (m < 1 || m > 64 || maxit < 1 || !(tol > 0)) { set_error("fgmres_solve_host: need 1 <= m <= 64, maxit >= 1, tol > 0"); return AAO_EINVAL; }
   Handle& h = hd->h;
   const size_t bytes = sizeof(double) * h.n;
-  double *b = nullptr, *x = nullptr;
-  AAO_TRY_CUDA(cudaMallocAsync(&b, bytes, h.stream));
-  AAO_TRY_CUDA(cudaMallocAsync(&x, bytes, h.stream));
+  if (!hd->host_b) AAO_TRY_CUDA(cudaMalloc(&hd->host_b, bytes));
+  if (!hd->host_x) AAO_TRY_CUDA(cudaMalloc(&hd->host_x, bytes));
+  double *b = hd->host_b, *x = hd->host_x;
   AAO_TRY_CUDA(cudaMemcpyAsync(b, b_host, bytes, cudaMemcpyHostToDevice, h.stream));
   int s = run_fgmres(h, b, x, tol, m, maxit, st, true);
   cudaError_t e = cudaMemcpyAsync(x_host, x, bytes, cudaMemcpyDeviceToHost, h.stream);
-  cudaFreeAsync(b, h.stream);
-  cudaFreeAsync(x, h.stream);
   cudaError_t e2 = cudaStreamSynchronize(h.stream);
   if (e != cudaSuccess || e2 != cudaSuccess) {
     set_error(std::string("fgmres_solve_host: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
