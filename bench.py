@@ -188,10 +188,37 @@ def _includes(path):
     return re.findall(r'^\s*#\s*include\s+"([^"]+)"', src, flags=re.M)
 
 
+def _code(text):
+    """A C/C++/CUDA source without its comments, indentation and blank lines: what the compiler
+    sees of it (string and character literals kept as written)."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and text[j] != c and text[j] != "\n":
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    lines = (ln.strip() for ln in "".join(out).split("\n"))
+    return "\n".join(ln for ln in lines if ln)
+
+
 def source_sha(files=None):
     """Hash of the named sources of the CUDA library (paths relative to its csrc directory) and of
     every quoted header they include, transitively: the translation units a kernel is built from.
-    Without names, every file of the directory."""
+    Comments, indentation and blank lines do not count (an edit of the documentation leaves the
+    compiled kernel and its counters as they were). Without names, every file of the directory."""
     cs = os.path.join(ROOT, "paper_2401_16113_gb300", "csrc")
     todo = list(files) if files else sorted(os.listdir(cs))
     seen = []
@@ -204,7 +231,7 @@ def source_sha(files=None):
     h = hashlib.sha256()
     for f in sorted(seen):
         h.update(os.path.relpath(f, cs).encode())
-        h.update(open(f, "rb").read())
+        h.update(_code(open(f, encoding="utf-8", errors="replace").read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -160,7 +160,9 @@ int fgmres_solve_zero(aao_handle* h, const double* b_dev, double* x_dev, double 
                       aao_stats* st);
 
 /* As fgmres_solve_zero with host buffers: copies b_host to the device, solves from a zero
-   initial guess, copies the solution to x_host. Both are nx*nt doubles. */
+   initial guess, copies the solution to x_host. Both are nx*nt doubles, owned by the caller
+   (pinned host memory gives the fastest copies). The handle keeps its two device copies of them
+   from the first call until aao_destroy (16 * nx*nt bytes). */
 int fgmres_solve_host(aao_handle* h, const double* b_host, double* x_host, double tol, int m,
                       int maxit, aao_stats* st);
 

@@ -85,8 +85,9 @@ def test_traffic_record_is_used_only_on_its_own_sources(monkeypatch):
 
 
 def test_source_hash_covers_a_kernels_translation_unit(monkeypatch, tmp_path):
-    """The traffic record's hash follows the named sources and the headers they include: a change
-    to another source leaves it alone, a change to an included header changes it."""
+    """The traffic record's hash follows the code of the named sources and of the headers they
+    include: a change to another source leaves it alone, a change of code in an included header
+    changes it, and an edit of comments or blank lines alone does not."""
     import shutil
     B = load_bench()
     root = tmp_path / "repo"
@@ -96,10 +97,12 @@ def test_source_hash_covers_a_kernels_translation_unit(monkeypatch, tmp_path):
     cs = root / "paper_2401_16113_gb300" / "csrc"
     h0 = B.source_sha(["krylov.cu"])
     assert h0 == B.source_sha(["krylov.cu"])
-    (cs / "heston.cu").write_text((cs / "heston.cu").read_text() + "\n// edit\n")
+    (cs / "heston.cu").write_text((cs / "heston.cu").read_text() + "\nint edit_marker;\n")
     assert B.source_sha(["krylov.cu"]) == h0
-    (cs / "aao_internal.cuh").write_text((cs / "aao_internal.cuh").read_text() + "\n// edit\n")
+    (cs / "krylov.cu").write_text((cs / "krylov.cu").read_text() + "\n// a comment\n\n/* and another */\n")
+    assert B.source_sha(["krylov.cu"]) == h0
+    (cs / "aao_internal.cuh").write_text((cs / "aao_internal.cuh").read_text() + "\nint edit_marker;\n")
     h1 = B.source_sha(["krylov.cu"])
     assert h1 != h0
-    (root / "include" / "aao.h").write_text((root / "include" / "aao.h").read_text() + "\n/* edit */\n")
+    (root / "include" / "aao.h").write_text((root / "include" / "aao.h").read_text() + "\n#define AAO_EDIT 1\n")
     assert B.source_sha(["krylov.cu"]) != h1
