@@ -23,6 +23,9 @@ Readings of points the paper leaves open (each one also listed in the design not
   * Heston operator (Sec. 5.1): central differences on a uniform (s, v) grid, the s = S_max
     Neumann condition through a ghost node, the v = 0 boundary equation with a one-sided
     second-order u_v.
+  * SABR operator (Sec. 5.2, Eq. 5.7): the Heston grid and s- and V_max-boundary conditions;
+    only r = 0 (parameter Sets III and IV), where D(t) = 1 and A is constant in time; at v = 0
+    the boundary equation u_t = r s u_s - r u is then u_t = 0.
 Parity pins for every function live in tests/test_oracle_*.py.
 """
 from __future__ import annotations
@@ -50,9 +53,14 @@ def spatial_grid(p):
     return h * np.arange(1, nx + 1), h
 
 
+def is_2d(p):
+    """The two-dimensional operators in (s, v): Heston (Sec. 5.1) and SABR (Sec. 5.2)."""
+    return p["op"] in ("heston", "sabr")
+
+
 def n_space(p):
-    """Spatial unknowns per time level: Nx, or Ns Nv for the two-dimensional Heston operator."""
-    return int(p["nx"]) * (int(p["nv"]) if p["op"] == "heston" else 1)
+    """Spatial unknowns per time level: Nx, or Ns Nv for the two-dimensional operators."""
+    return int(p["nx"]) * (int(p["nv"]) if is_2d(p) else 1)
 
 
 def time_grid(p):
@@ -194,6 +202,58 @@ def heston_matrix(p):
     return A, f
 
 
+def sabr_matrix(p):
+    """The SABR operator of Eq. 5.7 with r = 0 (so D(t) = e^{-rt} = 1 and A does not depend on t):
+    u_t = 1/2 v^2 s^(2 beta) u_ss + rho sigma s^beta v^2 u_sv + 1/2 sigma^2 v^2 u_vv, on the grid of
+    heston_grid with the boundary conditions shared with Heston (Sec. 5.2): u(0, v) = 0,
+    u(s, V_max) = s, u_s(S_max, v) = 1 through a ghost node u_{Ns+1} = u_{Ns-1} + 2 h_s; at v = 0 the
+    boundary equation u_t = r s u_s - r u, which is u_t = 0 for r = 0 (an all-zero row of A).
+    Central differences, u_sv by the four-point cross stencil. Returns the sparse A and f
+    (u' = A u + f)."""
+    if p["r"] != 0.0:
+        raise NotImplementedError("the SABR operator is built for r = 0 only (Sets III and IV)")
+    ns, nv = int(p["nx"]), int(p["nv"])
+    S, V, hs, hv = heston_grid(p)
+    beta, sig, rho = p["beta"], p["sigma"], p["rho"]
+    rows, cols, vals = [], [], []
+    f = np.zeros(ns * nv)
+
+    def add(i, j, ii, jj, c):
+        """coefficient c of u(ii, jj) in the equation of unknown (i, j), i, ii 1-based in s"""
+        row = j * ns + (i - 1)
+        if jj == nv:                       # v = V_max: u = s
+            f[row] += c * ii * hs
+        elif ii == 0:                      # s = 0: u = 0
+            pass
+        elif ii == ns + 1:                 # ghost beyond S_max
+            add(i, j, ns - 1, jj, c)
+            f[row] += c * 2.0 * hs
+        else:
+            rows.append(row)
+            cols.append(jj * ns + (ii - 1))
+            vals.append(c)
+
+    for j in range(1, nv):                 # j = 0: u_t = 0, nothing to add
+        v = V[j]
+        for i in range(1, ns + 1):
+            s_ = S[i - 1]
+            ass = 0.5 * v * v * s_ ** (2 * beta) / hs ** 2
+            avv = 0.5 * sig * sig * v * v / hv ** 2
+            asv = rho * sig * s_ ** beta * v * v / (4 * hs * hv)
+            add(i, j, i, j, -2 * ass - 2 * avv)
+            add(i, j, i + 1, j, ass)
+            add(i, j, i - 1, j, ass)
+            add(i, j, i, j + 1, avv)
+            add(i, j, i, j - 1, avv)
+            add(i, j, i + 1, j + 1, asv)
+            add(i, j, i - 1, j - 1, asv)
+            add(i, j, i + 1, j - 1, -asv)
+            add(i, j, i - 1, j + 1, -asv)
+    A = sp.csr_matrix((vals, (rows, cols)), shape=(ns * nv, ns * nv))
+    A.sum_duplicates()
+    return A, f
+
+
 def operator_at(p, t):
     """A(t) as a dense matrix, plus the coefficients through which the left/right Dirichlet
     values enter the first/last interior rows. op 'matrix' takes a user matrix p['A']
@@ -201,8 +261,8 @@ def operator_at(p, t):
     if p["op"] == "matrix":
         A = np.asarray(p["A"], dtype=np.float64)
         return A, np.zeros(A.shape[0]), np.zeros(A.shape[0])
-    if p["op"] == "heston":
-        A, f = heston_matrix(p)
+    if is_2d(p):
+        A, f = heston_matrix(p) if p["op"] == "heston" else sabr_matrix(p)
         return A, f, np.zeros(A.shape[0])
     if p["op"] == "riesz":
         A, left_ext, left_drift = riesz_matrix(p)
@@ -222,8 +282,8 @@ def boundary_values(p, t):
     """Dirichlet values (g_L(t), g_R(t)) in time-to-maturity t."""
     if p["op"] == "matrix":
         return 0.0, 0.0
-    if p["op"] == "heston":
-        return 1.0, 0.0  # time-independent data, carried by the vector f of heston_matrix
+    if is_2d(p):
+        return 1.0, 0.0  # time-independent data, carried by the vector f of heston/sabr_matrix
     disc = p["K"] * math.exp(-p["r"] * t)
     if p["op"] == "riesz":
         return disc - math.exp(-p["s_max"]), 0.0
@@ -236,9 +296,9 @@ def payoff(p):
     """u_0: the option payoff at the interior nodes (Eq. 1.1, u(., 0) = u_0)."""
     if p["op"] == "matrix":
         return np.asarray(p.get("u0", np.ones(int(p["nx"]))), dtype=np.float64)
-    if p["op"] == "heston":
+    if is_2d(p):
         S, _, _, _ = heston_grid(p)
-        return np.tile(np.maximum(S - p["K"], 0.0), int(p["nv"]))  # call, Eq. 5.2
+        return np.tile(np.maximum(S - p["K"], 0.0), int(p["nv"]))  # call, Eq. 5.2 (both operators)
     x, _ = spatial_grid(p)
     if p["op"] == "riesz":
         return np.maximum(p["K"] - np.exp(x), 0.0)

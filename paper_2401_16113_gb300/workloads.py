@@ -9,8 +9,9 @@ A problem is a dict with the keys
 
   op        'bs' (constant-coefficient Black-Scholes in S), 'localvol'
             (Black-Scholes with sigma(S, t)), 'riesz' (Riesz fractional
-            operator in log-price x) or 'heston' (the two-dimensional Heston
-            operator in (s, v), Sec. 5.1)
+            operator in log-price x), 'heston' (the two-dimensional Heston
+            operator in (s, v), Sec. 5.1) or 'sabr' (the two-dimensional SABR operator of
+            Sec. 5.2 with r = 0, on the same (s, v) grid)
   payoff    'put' or 'call'
   nx, nt    interior spatial nodes, number of Crank-Nicolson steps
   T, r, K   maturity, rate, strike
@@ -21,11 +22,12 @@ A problem is a dict with the keys
   lv_shape  optional, 'gauss' (the bump above, the default) or 'flat' (bump shape 1: a
             volatility that depends on time only; the oracle's pins use it, the library
             rejects it)
-  beta      'riesz' only: fractional order in (1, 2]
+  beta      'riesz': fractional order in (1, 2]; 'sabr': the CEV exponent of s
   nv, kappa, eta, rho, v_max
-            'heston' only: nx = Ns nodes in s, nv = Nv nodes in v, mean reversion,
-            long-run variance, correlation, v-domain [0, v_max]; sigma is the
-            volatility of variance and s_max the s-domain [0, s_max]
+            'heston' and 'sabr': nx = Ns nodes in s, nv = Nv nodes in v, mean reversion
+            and long-run variance (Heston only), correlation, v-domain [0, v_max]; sigma
+            is the volatility of the variance (of the volatility for SABR) and s_max the
+            s-domain [0, s_max]
   alpha     the free parameter of the alpha-circulant preconditioner (Sec. 3.1)
   precision 'fp64' or 'mixed' (FP32-complex preconditioner inside FP64 FGMRES)
   m, tol    restart length and relative-residual tolerance of FGMRES(m)
@@ -95,6 +97,22 @@ def heston_set2(nt=48, precision="mixed"):
     r 0.03, rho -0.7571, S0 100, V0 0.2; same domain and mesh family as Set I."""
     return with_(heston_set1(nt, precision), T=3.0, kappa=0.6067, eta=0.0707, sigma=0.2928, r=0.03,
                  rho=-0.7571, V0=0.2)
+
+
+def sabr_set3(nt=48, precision="mixed"):
+    """SABR parameter Set III of Sec. 5.2 (European call, s in [0, 24], v in [0, 3]): T 2, beta 0.5,
+    sigma 0.4, r 0, rho 0, K = S0 = 0.5, V0 0.5; the mesh family Nt = Ns = 2 Nv of Table 3, alpha
+    1e-3, GMRES(40), tol 1e-9."""
+    return _base(op="sabr", payoff="call", nx=nt, nv=nt // 2, nt=nt, T=2.0, K=0.5, r=0.0, sigma=0.4,
+                 beta=0.5, rho=0.0, kappa=0.0, eta=0.0, s_max=24.0, v_max=3.0, S0=0.5, V0=0.5,
+                 alpha=1e-3, precision=precision, m=40, tol=1e-9)
+
+
+def sabr_set4(nt=48, precision="mixed"):
+    """SABR parameter Set IV of Sec. 5.2: s in [0, 4], v in [0, 2], T 10, beta 0.5, sigma 0.8, r 0,
+    rho -0.6, K = S0 = 0.07, V0 0.4; the same mesh family."""
+    return with_(sabr_set3(nt, precision), s_max=4.0, v_max=2.0, T=10.0, sigma=0.8, rho=-0.6, K=0.07,
+                 S0=0.07, V0=0.4)
 
 
 def batch_instances(n=512, seed=SEED, nx_choices=(127, 255, 511, 1023),
