@@ -55,6 +55,8 @@ CASES = {
     "heston_set1_nt96": lambda W: (W.heston_set1(96), 1e-9, 40),
     "heston_set1_nt128": lambda W: (W.heston_set1(128), 1e-9, 40),
     "heston_set1_nt192": lambda W: (W.heston_set1(192), 1e-9, 40),
+    "sabr_set3_nt192": lambda W: (W.sabr_set3(192), 1e-9, 40),
+    "sabr_set4_nt192": lambda W: (W.sabr_set4(192), 1e-9, 40),
 }
 
 
@@ -902,11 +904,12 @@ def run_extras(args, flush, stream, main):
                           "nt_1536": fft_profile(W.with_(p, nt=1536)),
                           "nt_2048": fft_profile(p, b)}
 
-    # the two-dimensional Heston operator (Sec. 5.1, Table 1 Set I, uniform mesh Nt = Ns = 2 Nv,
-    # alpha 1e-3, FGMRES(40), tol 1e-9): iterations, time and the price at (S0, V0) (a grid node here;
-    # its error against the paper's Table 1 is checked by the parity tests)
-    def heston_line(nt):
-        q = W.heston_set1(nt)
+    # the two-dimensional operators (Heston: Sec. 5.1, Table 1 Set I; SABR: Sec. 5.2, Table 3 Sets III
+    # and IV; uniform mesh Nt = Ns = 2 Nv, alpha 1e-3, FGMRES(40), tol 1e-9): iterations, time and the
+    # price at (S0, V0) where that point is a grid node (its error against the paper's tables is
+    # checked by the parity tests)
+    def line_2d(make, nt):
+        q = make(nt)
         t0 = time.time()
         hq = aao.aao_create(q)
         torch.cuda.synchronize()
@@ -922,9 +925,10 @@ def run_extras(args, flush, stream, main):
             flush.fill_(1.0)
             ms, stq = _timed(stream, lambda: aao.fgmres_solve_zero(hq, bq, xq, 1e-9, 40, 300))
             best = ms if best is None else min(best, ms)
-        i = int(round(q["S0"] * q["nx"] / q["s_max"])) - 1
-        j = int(round(q["V0"] * q["nv"] / q["v_max"]))
-        price = float(xq.view(nt, q["nv"], q["nx"])[-1, j, i].item())
+        gi, gj = q["S0"] * q["nx"] / q["s_max"], q["V0"] * q["nv"] / q["v_max"]
+        price = None
+        if abs(gi - round(gi)) < 1e-9 and abs(gj - round(gj)) < 1e-9:
+            price = float(xq.view(nt, q["nv"], q["nx"])[-1, int(round(gj)), int(round(gi)) - 1].item())
         hq.close()
         return {"nt": nt, "ns": q["nx"], "nv": q["nv"], "unknowns": nq, "ms": best, "value": nq / (best / 1e3),
                 "unit": "unknowns/s", "iterations": stq["iterations"], "rel_residual": stq["rel_residual"],
@@ -932,7 +936,11 @@ def run_extras(args, flush, stream, main):
 
     out["heston"] = {"workload": "heston_set1_uniform", "note": "the paper's Table 1 (Set I, P_alpha, MATLAB on "
                      "an i9-13900K): 4 iterations, 0.51 s at Nt 96 and 5.52 s at Nt 192 (context only)",
-                     "nt_96": heston_line(96), "nt_192": heston_line(192)}
+                     "nt_96": line_2d(W.heston_set1, 96), "nt_192": line_2d(W.heston_set1, 192)}
+    out["sabr"] = {"workload": "sabr_uniform", "note": "the paper's Table 3 (P_alpha, MATLAB on an i9-13900K): "
+                   "4 iterations; Set III 0.38 s at Nt 96 and 3.11 s at Nt 192, Set IV 0.40 s and 3.68 s (context "
+                   "only)", "set3_nt_96": line_2d(W.sabr_set3, 96), "set3_nt_192": line_2d(W.sabr_set3, 192),
+                   "set4_nt_192": line_2d(W.sabr_set4, 192)}
 
     riesz_solve(W.riesz_1023x512(), "riesz", "explicit inverses of the shifted matrices (2.15 GB) read per apply")
     riesz_solve(W.riesz_sym_1023x512(), "riesz_sym",

@@ -59,6 +59,12 @@ extern "C" {
                              time level at j nx + i - 1. Step (b) by block elimination over the v
                              levels with dense inverses of the diagonal blocks made at create
                              (precision AAO_MIXED only) */
+#define AAO_OP_SABR 4     /* the two-dimensional SABR operator of Sec. 5.2 (Eq. 5.7) with r = 0
+                             (D(t) = 1, so A is constant in time; r != 0 returns
+                             AAO_EUNSUPPORTED): u_t = 1/2 v^2 s^(2 beta) u_ss + rho sigma s^beta v^2
+                             u_sv + 1/2 sigma^2 v^2 u_vv on the grid, boundary conditions, unknown
+                             order and step (b) of AAO_OP_HESTON; at v = 0 the boundary equation
+                             u_t = r s u_s - r u, i.e. u_t = 0 (kappa and eta unused) */
 
 #define AAO_PUT 0
 #define AAO_CALL 1
@@ -85,9 +91,11 @@ extern "C" {
  *              fit; each falls back to the other; both give P_alpha^{-1} v up to rounding)
  *  stream      cudaStream_t on which all work is issued
  *  nv, kappa, eta, rho, v_max
- *              AAO_OP_HESTON only: nodes in v (3..512; nx 3..512 nodes in s), mean reversion,
- *              long-run variance, correlation of the two Brownian motions, v-domain [0, v_max];
- *              sigma is then the volatility of the variance. A time level holds nx * nv unknowns.
+ *              AAO_OP_HESTON and AAO_OP_SABR: nodes in v (3..512; nx 3..512 nodes in s), mean
+ *              reversion and long-run variance (Heston only), correlation of the two Brownian
+ *              motions, v-domain [0, v_max]; sigma is then the volatility of the variance
+ *              (Heston) or of the volatility (SABR), and beta the SABR exponent of s (0..1).
+ *              A time level holds nx * nv unknowns.
  */
 #define AAO_FLAG_STEPB_FACTORED 1  /* partition method with per-bin pivot tables made at create */
 #define AAO_FLAG_STEPB_RECOMPUTE 2 /* partition method, pivots recomputed in every apply      */

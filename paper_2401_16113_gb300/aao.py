@@ -17,7 +17,7 @@ from . import build as _build
 
 AAO_OK, AAO_EINVAL, AAO_ECUDA, AAO_ENOMEM = 0, -1, -2, -3
 AAO_NOT_CONVERGED, AAO_BREAKDOWN, AAO_TIMEOUT, AAO_EUNSUPPORTED = -4, -5, -6, -7
-OPS = {"bs": 0, "localvol": 1, "riesz": 2, "heston": 3}
+OPS = {"bs": 0, "localvol": 1, "riesz": 2, "heston": 3, "sabr": 4}
 PAYOFFS = {"put": 0, "call": 1}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 STEPB = {"auto": 0, "factored": 1, "recompute": 2}  # how the tridiagonal step (b) is solved

@@ -304,7 +304,8 @@ struct Handle {
   // the complex operand's head and tail
   alignas(64) unsigned char rz_tmap[6 * 128] = {};
 
-  // Heston operator (AAO_OP_HESTON): grid hs_ns x hs_nv (nx = hs_ns * hs_nv unknowns per level);
+  // Heston and SABR operators (AAO_OP_HESTON, AAO_OP_SABR): grid hs_ns x hs_nv (nx = hs_ns * hs_nv
+  // unknowns per level);
   // per unknown the ten stencil coefficients of (tau/2) A (FP64 for the matvec, FP32 for step (b)),
   // tau f (boundary data), the payoff; step (b) per bin and v level: X_j = D_j^{-1},
   // G_j = X_j C'_j (j < nv - 1), H_0 = X_0 E_0 (FP32 complex, [j][k][ns][ns])
@@ -336,6 +337,8 @@ int tune_precond(Handle& h);
 // factors of the partitioned tridiagonal solves of step (b) (needs tri, mu/muf)
 int build_tri_factors(Handle& h);
 // The Riesz operator has no drift term ((r - sigma^2/2) u_x vanishes): its matrix is symmetric.
+// the two-dimensional operators in (s, v), which share the grid, the stencil matvec and step (b)
+inline bool op_2d(int op) { return op == AAO_OP_HESTON || op == AAO_OP_SABR; }
 inline bool riesz_symmetric(const aao_problem& p) { return p.r - 0.5 * p.sigma * p.sigma == 0.0; }
 // A = Q diag(w) Q^T for a dense symmetric n x n A (row-major, FP64, host); A is overwritten with
 // Q^T. False if the symmetric QR iteration does not converge.

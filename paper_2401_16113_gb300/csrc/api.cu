@@ -69,14 +69,26 @@ bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 int validate(const aao_problem* p) {
   if (!p) { set_error("aao_create: null problem"); return AAO_EINVAL; }
   if (p->nx < 2 || p->nt < 1) { set_error("aao_create: need nx >= 2 and nt >= 1"); return AAO_EINVAL; }
-  if (p->op != AAO_OP_BS && p->op != AAO_OP_LOCALVOL && p->op != AAO_OP_RIESZ && p->op != AAO_OP_HESTON) { set_error("aao_create: unknown op"); return AAO_EINVAL; }
-  if (p->op == AAO_OP_HESTON) {
-    if (p->precision != AAO_MIXED) { set_error("aao_create: the Heston operator is built for precision AAO_MIXED only"); return AAO_EUNSUPPORTED; }
-    if (p->payoff != AAO_CALL) { set_error("aao_create: the Heston boundary conditions of Sec. 5.1 are those of a call"); return AAO_EUNSUPPORTED; }
-    if (p->nx < 3 || p->nx > 512 || p->nv < 3 || p->nv > 512) { set_error("aao_create: Heston needs 3 <= nx, nv <= 512"); return AAO_EUNSUPPORTED; }
-    if (!(p->kappa > 0) || !(p->eta > 0) || !(p->rho >= -1) || !(p->rho <= 1) || !(p->v_max > 0)) {
-      set_error("aao_create: Heston needs kappa, eta, v_max > 0 and -1 <= rho <= 1");
+  if (p->op != AAO_OP_BS && p->op != AAO_OP_LOCALVOL && p->op != AAO_OP_RIESZ && !op_2d(p->op)) { set_error("aao_create: unknown op"); return AAO_EINVAL; }
+  if (op_2d(p->op)) {
+    if (p->precision != AAO_MIXED) { set_error("aao_create: the Heston and SABR operators are built for precision AAO_MIXED only"); return AAO_EUNSUPPORTED; }
+    if (p->payoff != AAO_CALL) { set_error("aao_create: the Heston and SABR boundary conditions of Sec. 5.1-5.2 are those of a call"); return AAO_EUNSUPPORTED; }
+    if (p->nx < 3 || p->nx > 512 || p->nv < 3 || p->nv > 512) { set_error("aao_create: Heston and SABR need 3 <= nx, nv <= 512"); return AAO_EUNSUPPORTED; }
+    if (!(p->rho >= -1) || !(p->rho <= 1) || !(p->v_max > 0) || !(p->sigma >= 0)) {
+      set_error("aao_create: Heston and SABR need v_max > 0, sigma >= 0 and -1 <= rho <= 1");
       return AAO_EINVAL;
+    }
+    if (p->op == AAO_OP_HESTON && (!(p->kappa > 0) || !(p->eta > 0))) {
+      set_error("aao_create: Heston needs kappa, eta > 0");
+      return AAO_EINVAL;
+    }
+    if (p->op == AAO_OP_SABR && !(p->beta >= 0.0 && p->beta <= 1.0)) {
+      set_error("aao_create: SABR needs 0 <= beta <= 1");
+      return AAO_EINVAL;
+    }
+    if (p->op == AAO_OP_SABR && p->r != 0.0) {
+      set_error("aao_create: SABR with r != 0 has a time-dependent operator (Eq. 5.7, D(t) = e^{-rt}); only r = 0 is built");
+      return AAO_EUNSUPPORTED;
     }
     const double factors = 2.0 * p->nv * (double)(p->nt / 2 + 1) * p->nx * (double)p->nx * 8.0;
     if (factors > 48e9) { set_error("aao_create: Heston step-(b) block factors would exceed 48 GB"); return AAO_EUNSUPPORTED; }
@@ -136,7 +148,7 @@ int aao_create(const aao_problem* p, aao_handle** out) {
   Handle& h = hd->h;
   h.p = *p;
   h.stream = (cudaStream_t)p->stream;
-  h.nx = p->op == AAO_OP_HESTON ? p->nx * p->nv : p->nx;  // spatial unknowns per time level
+  h.nx = op_2d(p->op) ? p->nx * p->nv : p->nx;  // spatial unknowns per time level
   h.nt = p->nt;
   h.K = p->nt / 2 + 1;
   int l = 0;

@@ -2,6 +2,13 @@
 //
 //   u_t = 1/2 v s^2 u_ss + sigma rho s v u_sv + 1/2 sigma^2 v u_vv + r s u_s + kappa (eta - v) u_v - r u
 //
+// and, on the same grid with the same boundary conditions and the same kernels, the SABR operator of
+// Sec. 5.2 (Eq. 5.7) with r = 0 (D(t) = 1):
+//
+//   u_t = 1/2 v^2 s^(2 beta) u_ss + rho sigma s^beta v^2 u_sv + 1/2 sigma^2 v^2 u_vv,
+//
+// whose boundary equation at v = 0, u_t = r s u_s - r u, is u_t = 0 (an all-zero row of A).
+//
 // on a uniform grid: s_i = i h_s (i = 1..Ns, h_s = s_max / Ns), v_j = j h_v (j = 0..Nv-1,
 // h_v = v_max / Nv); unknown (i, j) of a time level at p = j Ns + i - 1 (Ns Nv unknowns per level,
 // so the FFT kernels of steps (a) and (c) see Ns Nv spatial columns). Second-order central
@@ -495,6 +502,7 @@ int heston_build(Handle& h) {
   h.hs_nv = nv;
   const double hs = p.s_max / ns, hv = p.v_max / nv, tau = h.tau;
   const double r = p.r, kap = p.kappa, eta = p.eta, sig = p.sigma, rho = p.rho;
+  const bool sabr = p.op == AAO_OP_SABR;  // r = 0 (checked at create)
   std::vector<double> c((size_t)kHsOff * nsp, 0.0), f(nsp, 0.0), u0(nsp);
   // coefficient w of u(ii, jj) in the equation of unknown (i, j) (i, ii 1-based in s)
   auto add = [&](int i, int j, int ii, int jj, double w) {
@@ -517,6 +525,7 @@ int heston_build(Handle& h) {
     for (int i = 1; i <= ns; ++i) {
       const double s = hs * i;
       u0[j * ns + i - 1] = s > p.K ? s - p.K : 0.0;  // call payoff
+      if (j == 0 && sabr) continue;  // u_t = r s u_s - r u = 0
       if (j == 0) {  // u_t = kappa eta u_v + r s u_s - r u, u_v one-sided to second order
         add(i, 0, i, 0, -3.0 * kap * eta / (2.0 * hv) - r);
         add(i, 0, i, 1, 4.0 * kap * eta / (2.0 * hv));
@@ -525,9 +534,21 @@ int heston_build(Handle& h) {
         add(i, 0, i - 1, 0, -r * s / (2.0 * hs));
         continue;
       }
-      const double dss = 0.5 * v * s * s / (hs * hs), dvv = 0.5 * sig * sig * v / (hv * hv);
-      const double dsv = sig * rho * s * v / (4.0 * hs * hv);
-      const double cs = r * s / (2.0 * hs), cv = kap * (eta - v) / (2.0 * hv);
+      double dss, dvv, dsv, cs, cv;
+      if (sabr) {
+        const double sb = pow(s, p.beta);  // s^beta; s^(2 beta) = sb^2
+        dss = 0.5 * v * v * sb * sb / (hs * hs);
+        dvv = 0.5 * sig * sig * v * v / (hv * hv);
+        dsv = rho * sig * sb * v * v / (4.0 * hs * hv);
+        cs = 0.0;
+        cv = 0.0;
+      } else {
+        dss = 0.5 * v * s * s / (hs * hs);
+        dvv = 0.5 * sig * sig * v / (hv * hv);
+        dsv = sig * rho * s * v / (4.0 * hs * hv);
+        cs = r * s / (2.0 * hs);
+        cv = kap * (eta - v) / (2.0 * hv);
+      }
       add(i, j, i, j, -2.0 * dss - 2.0 * dvv - r);
       add(i, j, i + 1, j, dss + cs);
       add(i, j, i - 1, j, dss - cs);

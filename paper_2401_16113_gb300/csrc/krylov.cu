@@ -412,7 +412,7 @@ int build_tables(Handle& h) {
   const aao_problem& p = h.p;
   const int nx = h.nx, nt = h.nt, N = nt;
   h.tau = p.T / nt;
-  const bool riesz = p.op == AAO_OP_RIESZ, heston = p.op == AAO_OP_HESTON;
+  const bool riesz = p.op == AAO_OP_RIESZ, heston = op_2d(p.op);
   const bool tridiag = !riesz && !heston;  // the one-dimensional Black-Scholes operators
   const double hS = p.s_max / (nx + 1);
   h.coef_rows = (p.op == AAO_OP_LOCALVOL) ? nt : 1;
@@ -632,14 +632,14 @@ int matvec_t(Handle& h, const IN* x, double* y, const double* b, const double* V
 // y = M x; with b: y = b - M x (restart residual); with V (nd <= 8): first Gram-Schmidt pass
 int launch_matvec(Handle& h, const void* x, bool x_is_float, double* y, const double* b, const double* V, int nd,
                   int m, bool with_bnorm, float* yf) {
-  if (h.p.op == AAO_OP_RIESZ || h.p.op == AAO_OP_HESTON) {
+  if (h.p.op == AAO_OP_RIESZ || op_2d(h.p.op)) {
     if (b && with_bnorm) {
       ProfScope ps(AAO_K_OTHER, h.stream, 8.0 * (double)h.n);
       k_dot_self<<<wave_blocks(h, (const void*)k_dot_self, grid_for(h.n)), kThreads, 0, h.stream>>>(
           b, h.n, h.part, h.scal, S_BNORM2, h.counter);
       AAO_CHECK_LAUNCH();
     }
-    if (h.p.op == AAO_OP_HESTON) return heston_matvec(h, x, x_is_float, y, b, V, nd, m);
+    if (op_2d(h.p.op)) return heston_matvec(h, x, x_is_float, y, b, V, nd, m);
     return riesz_matvec(h, x, x_is_float, y, b, V, nd, m);
   }
   const double nn = (double)h.n;
@@ -666,7 +666,7 @@ void launch_coef_raw(cudaStream_t s, double* L, double* D, double* U, int nx, in
 
 int launch_rhs(Handle& h, double* b) {
   if (h.p.op == AAO_OP_RIESZ) return riesz_rhs(h, b);
-  if (h.p.op == AAO_OP_HESTON) return heston_rhs(h, b);
+  if (op_2d(h.p.op)) return heston_rhs(h, b);
   k_rhs<<<grid_for(h.n), kThreads, 0, h.stream>>>(b, h.nx, h.nt, h.mL, h.mD, h.mU, h.coef_rows, h.gL, h.gR,
                                                    h.p.s_max / (h.nx + 1), h.p.K, h.p.payoff);
   AAO_CHECK_LAUNCH();
@@ -755,7 +755,7 @@ int run_fgmres(Handle& h, const double* b, double* x, double tol, int m, int max
   char* Zb = reinterpret_cast<char*>(h.Z);
   // mixed precision: the residual and update kernels also write an FP32 copy of the basis vector
   // that the next preconditioner apply reads (the Riesz matvec does not write one)
-  float* vf = (h.mixed && h.p.op != AAO_OP_RIESZ && h.p.op != AAO_OP_HESTON) ? h.Vf : nullptr;
+  float* vf = (h.mixed && h.p.op != AAO_OP_RIESZ && !op_2d(h.p.op)) ? h.Vf : nullptr;
 
   int its = 0, restarts = 0, status = AAO_OK;
   double rel = 0.0, est = 0.0, bnorm = 0.0;

@@ -289,7 +289,7 @@ int run_precond(Handle& h, const double* v, void* z, bool z_is_float, const doub
   bool pdl_c = true;
   if (skip_b) {
     // timing of steps (a) and (c) alone
-  } else if (h.p.op == AAO_OP_HESTON) {
+  } else if (op_2d(h.p.op)) {
     // step (b) with the two-dimensional operator: block elimination over the v levels
     AAO_TRY(heston_solve_bins(h, spec));
   } else if (h.p.op == AAO_OP_RIESZ) {
@@ -423,8 +423,8 @@ int tune_precond(Handle& h) {
   int dev = 0;
   AAO_TRY_CUDA(cudaGetDevice(&dev));
   // the operators whose step (b) is not the tridiagonal solver
-  const bool riesz = h.p.op == AAO_OP_RIESZ || h.p.op == AAO_OP_HESTON;
-  const int opclass = h.p.op == AAO_OP_HESTON ? 3 : (h.p.op == AAO_OP_RIESZ ? (h.rz_sym ? 2 : 1) : 0);
+  const bool riesz = h.p.op == AAO_OP_RIESZ || op_2d(h.p.op);
+  const int opclass = op_2d(h.p.op) ? 3 : (h.p.op == AAO_OP_RIESZ ? (h.rz_sym ? 2 : 1) : 0);
   const TuneKey key{dev, h.nx, h.nt, h.mixed ? 1 : 0, opclass, h.p.flags};
   TriRc trc;
   TriPart tpart;

@@ -1,0 +1,155 @@
+"""The two-dimensional SABR operator (Sec. 5.2, Eq. 5.7 with r = 0) through the C ABI against the FP64
+oracle: the right-hand side and the matrix-vector product of Eq. 2.2, the preconditioner apply of
+Eq. 3.2 with the block-elimination step (b) it shares with the Heston operator (the FP32 bound of
+the other parity tests; the brute-force dense inverse on a tiny grid), and the mixed-precision
+FGMRES(40) solve to 1e-9. The solve takes the oracle's iteration count, equals sequential
+Crank-Nicolson, and its prices on the Nt = 48 and 96 meshes imply one reference price through the
+errors printed in Table 3. With alpha = 1 the zero-frequency shifted block is singular (the v = 0
+rows of A vanish) and the solve reports the breakdown that Table 3 marks for P_1."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import aao_oracle as O
+from paper_2401_16113_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "sabr_table3.txt")
+SETS = {3: W.sabr_set3, 4: W.sabr_set4}
+
+
+@pytest.fixture(scope="module")
+def aao():
+    from paper_2401_16113_gb300 import aao as A, build
+    build.build()
+    A.load()
+    return A
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def bound(p):
+    return 20.0 * U32 * math.log2(2 * p["nt"]) / p["alpha"]
+
+
+SHAPES = [(3, 3, 2), (8, 4, 8), (13, 5, 12), (40, 20, 16), (64, 32, 32), (100, 6, 6)]
+
+
+@pytest.mark.parametrize("ns,nv,nt", SHAPES)
+def test_sabr_rhs_and_matvec_match_oracle(aao, ns, nv, nt):
+    for base in (W.sabr_set3(), W.sabr_set4()):
+        p = W.with_(base, nx=ns, nv=nv, nt=nt)
+        n = W.unknowns(p)
+        h = aao.aao_create(p)
+        b = torch.empty(n, dtype=torch.float64, device="cuda")
+        aao.aao_rhs(h, b)
+        bref = O.assemble_b(p)
+        assert np.abs(host(b) - bref).max() <= 1e-13 * np.abs(bref).max()
+        x = W.random_vector(n, seed=ns + nt)
+        y = torch.empty(n, dtype=torch.float64, device="cuda")
+        aao.aao_matvec(h, dev(x), y)
+        yref = O.matvec(p, x)
+        assert np.abs(host(y) - yref).max() <= 1e-12 * np.abs(yref).max()
+        h.close()
+
+
+@pytest.mark.parametrize("ns,nv,nt", SHAPES)
+@pytest.mark.parametrize("alpha", [1e-2, 1e-3])
+def test_sabr_precond_matches_oracle(aao, ns, nv, nt, alpha):
+    for base in (W.sabr_set3(), W.sabr_set4()):
+        p = W.with_(base, nx=ns, nv=nv, nt=nt, alpha=alpha)
+        n = W.unknowns(p)
+        h = aao.aao_create(p)
+        v = W.random_vector(n, seed=2 * ns + nt)
+        z = torch.empty(n, dtype=torch.float64, device="cuda")
+        aao.precond_apply(h, dev(v), z)
+        assert rel(host(z), O.precond_fft(p, v)) <= bound(p)
+        h.close()
+
+
+def test_sabr_precond_tiny_matches_dense_inverse(aao):
+    p = W.with_(W.sabr_set4(), nx=6, nv=4, nt=6)
+    n = W.unknowns(p)
+    h = aao.aao_create(p)
+    v = W.random_vector(n, seed=5)
+    z = torch.empty(n, dtype=torch.float64, device="cuda")
+    aao.precond_apply(h, dev(v), z)
+    assert rel(host(z), O.precond_dense(p, v)) <= bound(p)
+    h.close()
+
+
+def price_at(p, last):
+    """Bilinear interpolation at (S0, V0), the boundary values u(0, v) = 0 and u(s, V_max) = s
+    included (the Set IV point lies between s = 0 and the first node)."""
+    ns, nv = int(p["nx"]), int(p["nv"])
+    _, _, hs, hv = O.heston_grid(p)
+    G = np.zeros((nv + 1, ns + 1))
+    G[:nv, 1:] = last.reshape(nv, ns)
+    G[nv, :] = hs * np.arange(ns + 1)
+    x, y = p["S0"] / hs, p["V0"] / hv
+    i0, j0 = min(int(math.floor(x)), ns - 1), min(int(math.floor(y)), nv - 1)
+    fx, fy = x - i0, y - j0
+    return ((1 - fx) * (1 - fy) * G[j0, i0] + fx * (1 - fy) * G[j0, i0 + 1] + (1 - fx) * fy * G[j0 + 1, i0]
+            + fx * fy * G[j0 + 1, i0 + 1])
+
+
+def solve(aao, p):
+    n = W.unknowns(p)
+    h = aao.aao_create(p)
+    b = torch.empty(n, dtype=torch.float64, device="cuda")
+    aao.aao_rhs(h, b)
+    x = torch.zeros_like(b)
+    st = aao.fgmres_solve(h, b, x, 1e-9, 40, 200)
+    h.close()
+    return st, host(x)
+
+
+@pytest.mark.parametrize("set_", [3, 4])
+def test_sabr_solve_matches_cn_iterations_and_table3(aao, set_):
+    prices = {}
+    for nt in (16, 48, 96):
+        p = SETS[set_](nt)
+        st, xs = solve(aao, p)
+        assert st["status"] == 0 and st["rel_residual"] <= 1e-9, st
+        U = O.sequential_cn(p)
+        assert np.abs(xs - U.ravel()).max() <= 1e-7 * np.abs(U).max()
+        if nt == 16:
+            _, info = O.solve(p, tol=1e-9, m=40, maxit=200)
+            assert abs(st["iterations"] - info["its"]) <= 1, (st["iterations"], info["its"])
+        assert st["iterations"] <= 5  # the paper: 4 on every mesh
+        prices[nt] = price_at(p, xs.reshape(nt, -1)[-1])
+    rows = {int(nt): err for s, nt, err in np.loadtxt(GOLDEN, ndmin=2) if int(s) == set_}
+    spread = min(abs(prices[48] / (1 + side * rows[48]) - prices[96] / (1 + side * rows[96]))
+                 / (prices[96] / (1 + side * rows[96])) for side in (-1.0, 1.0))
+    assert spread <= 1.2e-4, spread
+
+
+def test_sabr_P_1_is_singular_and_the_solve_reports_it(aao):
+    p = W.with_(W.sabr_set3(16), alpha=1.0)
+    st, _ = solve(aao, p)
+    assert st["status"] == aao.AAO_BREAKDOWN, st
+
+
+def test_sabr_rejects_what_is_not_built(aao):
+    for bad, code in ((dict(r=0.03), aao.AAO_EUNSUPPORTED), (dict(precision="fp64"), aao.AAO_EUNSUPPORTED),
+                      (dict(payoff="put"), aao.AAO_EUNSUPPORTED), (dict(beta=1.5), aao.AAO_EINVAL),
+                      (dict(rho=1.5), aao.AAO_EINVAL)):
+        with pytest.raises(aao.AaoError) as e:
+            aao.aao_create(W.with_(W.sabr_set3(16), **bad))
+        assert e.value.code == code
