@@ -23,9 +23,12 @@ Readings of points the paper leaves open (each one also listed in the design not
   * Heston operator (Sec. 5.1): central differences on a uniform (s, v) grid, the s = S_max
     Neumann condition through a ghost node, the v = 0 boundary equation with a one-sided
     second-order u_v.
-  * SABR operator (Sec. 5.2, Eq. 5.7): the Heston grid and s- and V_max-boundary conditions;
-    only r = 0 (parameter Sets III and IV), where D(t) = 1 and A is constant in time; at v = 0
-    the boundary equation u_t = r s u_s - r u is then u_t = 0.
+  * SABR operator (Sec. 5.2, Eq. 5.7): the Heston grid and s- and V_max-boundary conditions, at
+    v = 0 the boundary equation u_t = r s u_s - r u (u_t = 0 for r = 0, parameter Sets III and
+    IV). For r != 0 (Set V) the operator is Eq. 5.7 itself, each term with its own power of
+    D(t) = e^{-rt}, at t_{k+1/2} in block row k; the preconditioner uses its time mean, as for
+    the local volatility. (Sec. 5.2 motivates the preconditioner with the form L(t) = d(t) L; the
+    errors printed in Table 4 fit Eq. 5.7 and not that form.)
 Parity pins for every function live in tests/test_oracle_*.py.
 """
 from __future__ import annotations
@@ -56,6 +59,11 @@ def spatial_grid(p):
 def is_2d(p):
     """The two-dimensional operators in (s, v): Heston (Sec. 5.1) and SABR (Sec. 5.2)."""
     return p["op"] in ("heston", "sabr")
+
+
+def time_dependent(p):
+    """Operators whose A depends on t: local volatility, and SABR with r != 0 (D(t) = e^{-rt})."""
+    return p["op"] == "localvol" or (p["op"] == "sabr" and p["r"] != 0.0)
 
 
 def n_space(p):
@@ -202,19 +210,20 @@ def heston_matrix(p):
     return A, f
 
 
-def sabr_matrix(p):
-    """The SABR operator of Eq. 5.7 with r = 0 (so D(t) = e^{-rt} = 1 and A does not depend on t):
-    u_t = 1/2 v^2 s^(2 beta) u_ss + rho sigma s^beta v^2 u_sv + 1/2 sigma^2 v^2 u_vv, on the grid of
-    heston_grid with the boundary conditions shared with Heston (Sec. 5.2): u(0, v) = 0,
-    u(s, V_max) = s, u_s(S_max, v) = 1 through a ghost node u_{Ns+1} = u_{Ns-1} + 2 h_s; at v = 0 the
-    boundary equation u_t = r s u_s - r u, which is u_t = 0 for r = 0 (an all-zero row of A).
+def sabr_matrix(p, t=0.0):
+    """The SABR operator of Eq. 5.7 at time t (time to maturity), D = e^{-rt}:
+    u_t = 1/2 v^2 s^(2 beta) D^(2(1-beta)) u_ss + rho sigma s^beta D^(1-beta) v^2 u_sv
+          + 1/2 sigma^2 v^2 u_vv + r s u_s - r u,
+    on the grid of heston_grid with the boundary conditions shared with Heston (Sec. 5.2):
+    u(0, v) = 0, u(s, V_max) = s, u_s(S_max, v) = 1 through a ghost node u_{Ns+1} = u_{Ns-1} + 2 h_s;
+    at v = 0 the boundary equation u_t = r s u_s - r u (central u_s), an all-zero row for r = 0.
     Central differences, u_sv by the four-point cross stencil. Returns the sparse A and f
     (u' = A u + f)."""
-    if p["r"] != 0.0:
-        raise NotImplementedError("the SABR operator is built for r = 0 only (Sets III and IV)")
     ns, nv = int(p["nx"]), int(p["nv"])
     S, V, hs, hv = heston_grid(p)
-    beta, sig, rho = p["beta"], p["sigma"], p["rho"]
+    beta, sig, rho, r = p["beta"], p["sigma"], p["rho"], p["r"]
+    D = math.exp(-r * t)
+    gss, gsv = D ** (2.0 * (1.0 - beta)), D ** (1.0 - beta)
     rows, cols, vals = [], [], []
     f = np.zeros(ns * nv)
 
@@ -233,16 +242,23 @@ def sabr_matrix(p):
             cols.append(jj * ns + (ii - 1))
             vals.append(c)
 
-    for j in range(1, nv):                 # j = 0: u_t = 0, nothing to add
+    for j in range(nv):
         v = V[j]
         for i in range(1, ns + 1):
             s_ = S[i - 1]
-            ass = 0.5 * v * v * s_ ** (2 * beta) / hs ** 2
+            bs = r * s_ / (2 * hs)
+            if j == 0:                     # u_t = r s u_s - r u (nothing to add for r = 0)
+                if r != 0.0:
+                    add(i, j, i, j, -r)
+                    add(i, j, i + 1, j, bs)
+                    add(i, j, i - 1, j, -bs)
+                continue
+            ass = 0.5 * v * v * s_ ** (2 * beta) * gss / hs ** 2
             avv = 0.5 * sig * sig * v * v / hv ** 2
-            asv = rho * sig * s_ ** beta * v * v / (4 * hs * hv)
-            add(i, j, i, j, -2 * ass - 2 * avv)
-            add(i, j, i + 1, j, ass)
-            add(i, j, i - 1, j, ass)
+            asv = rho * sig * s_ ** beta * gsv * v * v / (4 * hs * hv)
+            add(i, j, i, j, -2 * ass - 2 * avv - r)
+            add(i, j, i + 1, j, ass + bs)
+            add(i, j, i - 1, j, ass - bs)
             add(i, j, i, j + 1, avv)
             add(i, j, i, j - 1, avv)
             add(i, j, i + 1, j + 1, asv)
@@ -262,7 +278,7 @@ def operator_at(p, t):
         A = np.asarray(p["A"], dtype=np.float64)
         return A, np.zeros(A.shape[0]), np.zeros(A.shape[0])
     if is_2d(p):
-        A, f = heston_matrix(p) if p["op"] == "heston" else sabr_matrix(p)
+        A, f = heston_matrix(p) if p["op"] == "heston" else sabr_matrix(p, t)
         return A, f, np.zeros(A.shape[0])
     if p["op"] == "riesz":
         A, left_ext, left_drift = riesz_matrix(p)
@@ -364,7 +380,7 @@ def sequential_cn(p):
         A, _, _ = step_operator(p, k)
         I = _eye_like(A)
         rhs = (I + 0.5 * tau * A) @ u + tau * forcing(p, k)
-        if not sp.issparse(A) and p["op"] != "localvol":
+        if not sp.issparse(A) and not time_dependent(p):
             # constant dense A: the same matrix I - tau/2 A at every step, factored once
             if lu is None:
                 lu = sla.lu_factor(I - 0.5 * tau * A)
@@ -381,7 +397,7 @@ def assemble_M(p):
     nt, nx = int(p["nt"]), n_space(p)
     _, tau = time_grid(p)
     I = sp.identity(nx, format="csr")
-    if p["op"] != "localvol":
+    if not time_dependent(p):
         At = sp.csr_matrix(tau * step_operator(p, 0)[0])
         B1 = sp.diags([np.ones(nt), -np.ones(nt - 1)], [0, -1], shape=(nt, nt))
         B2 = 0.5 * sp.diags([np.ones(nt), np.ones(nt - 1)], [0, -1], shape=(nt, nt))
@@ -446,7 +462,7 @@ def alpha_circulants(nt, alpha):
 def mean_operator(p):
     """A-bar used by the preconditioner: A itself for constant coefficients; the mean of
     A(t_{k+1/2}) over k for time-dependent ones (generalising d-bar of Sec. 5.3)."""
-    if p["op"] != "localvol":
+    if not time_dependent(p):
         return step_operator(p, 0)[0]
     nt = int(p["nt"])
     acc = step_operator(p, 0)[0]

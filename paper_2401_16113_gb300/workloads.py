@@ -11,7 +11,7 @@ A problem is a dict with the keys
             (Black-Scholes with sigma(S, t)), 'riesz' (Riesz fractional
             operator in log-price x), 'heston' (the two-dimensional Heston
             operator in (s, v), Sec. 5.1) or 'sabr' (the two-dimensional SABR operator of
-            Sec. 5.2 with r = 0, on the same (s, v) grid)
+            Sec. 5.2, on the same (s, v) grid)
   payoff    'put' or 'call'
   nx, nt    interior spatial nodes, number of Crank-Nicolson steps
   T, r, K   maturity, rate, strike
@@ -113,6 +113,14 @@ def sabr_set4(nt=48, precision="mixed"):
     rho -0.6, K = S0 = 0.07, V0 0.4; the same mesh family."""
     return with_(sabr_set3(nt, precision), s_max=4.0, v_max=2.0, T=10.0, sigma=0.8, rho=-0.6, K=0.07,
                  S0=0.07, V0=0.4)
+
+
+def sabr_set5(nt=48, precision="mixed"):
+    """SABR parameter Set V of Sec. 5.2 (Table 4), with a nonzero rate, so that the operator of
+    Eq. 5.7 depends on time through D(t) = e^{-rt}: s in [0, 23], v in [0, 3], T 2, beta 0.45,
+    sigma 0.4, r 0.03, rho -0.65, K = S0 = 0.5, V0 0.2; the same mesh family and solver."""
+    return with_(sabr_set3(nt, precision), s_max=23.0, v_max=3.0, T=2.0, beta=0.45, sigma=0.4, r=0.03,
+                 rho=-0.65, K=0.5, S0=0.5, V0=0.2)
 
 
 def batch_instances(n=512, seed=SEED, nx_choices=(127, 255, 511, 1023),

@@ -12,6 +12,11 @@
     (lambda_1,0 = 0) is singular: P_1 is singular while P_alpha (alpha < 1) is not.
   * Right-preconditioned FGMRES(40) to 1e-9 with P_alpha: the same few iterations on every mesh
     (the paper: 4) and the AaO solution equal to sequential CN.
+  * Set V (r = 0.03, Table 4): the operator of Eq. 5.7 depends on time, each term through its own
+    power of D(t) = e^{-rt}. With it the Nt = 48 and 96 rows of Table 4 imply one reference price
+    (to 5e-5). The form L(t) = d(t) L, which Sec. 5.2 uses to derive the preconditioner, spreads it
+    35-fold and is caught. P_alpha built on the time mean of A takes the same few iterations on every
+    mesh (the paper: 6), P_1 many more (the paper: 100 and up).
 """
 import math
 import os
@@ -23,7 +28,8 @@ from oracle import aao_oracle as O
 from paper_2401_16113_gb300 import workloads as W
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "sabr_table3.txt")
-SETS = {3: W.sabr_set3, 4: W.sabr_set4}
+GOLDEN4 = os.path.join(os.path.dirname(__file__), "golden", "sabr_table4.txt")
+SETS = {3: W.sabr_set3, 4: W.sabr_set4, 5: W.sabr_set5}
 
 
 def price_at(p, U_last):
@@ -44,11 +50,8 @@ def price_at(p, U_last):
 def implied_references(rows, make):
     """For each side (price below or above the reference), the reference price that each row's
     printed error implies."""
-    out = {}
-    for side in (-1.0, 1.0):
-        out[side] = [price_at(make(int(nt)), O.sequential_cn(make(int(nt)))[-1]) / (1.0 + side * err)
-                     for _, nt, err in rows]
-    return out
+    prices = [price_at(make(int(nt)), O.sequential_cn(make(int(nt)))[-1]) for _, nt, _ in rows]
+    return {side: [pr / (1.0 + side * err) for pr, (_, _, err) in zip(prices, rows)] for side in (-1.0, 1.0)}
 
 
 def spread(refs):
@@ -125,3 +128,60 @@ def test_sabr_iterations_are_mesh_independent_and_solution_is_cn():
             assert np.abs(x - U.ravel()).max() <= 1e-8 * np.abs(U).max()
             its.append(info["its"])
         assert max(its) <= 4 and max(its) - min(its) <= 1, its  # the paper: 4 on every mesh
+
+
+@pytest.mark.slow
+def test_sabr_set5_meshes_imply_one_reference_price():
+    rows = np.loadtxt(GOLDEN4, ndmin=2)
+    assert spread(implied_references(rows, W.sabr_set5)) <= AGREE
+
+
+@pytest.mark.slow
+def test_the_scalar_time_factor_form_does_not_fit_table4(monkeypatch):
+    """L(t) = d(t) L with L the operator at t = 0 (the simplification Sec. 5.2 uses to derive the
+    preconditioner), planted in place of Eq. 5.7: Table 4's rows then disagree (measured 1.7e-3)."""
+    exact = O.sabr_matrix
+
+    def scalar_form(p, t=0.0):
+        A0, f0 = exact(p, 0.0)
+        d = math.exp(-p["r"] * t)
+        return d * A0, d * f0
+
+    monkeypatch.setattr(O, "sabr_matrix", scalar_form)
+    rows = np.loadtxt(GOLDEN4, ndmin=2)
+    assert spread(implied_references(rows, W.sabr_set5)) > 10 * AGREE
+
+
+def test_sabr_with_rate_is_time_dependent_and_reduces_at_t0():
+    p = W.with_(W.sabr_set5(8), nx=8, nv=4, nt=4)
+    assert O.time_dependent(p) and not O.time_dependent(W.sabr_set3(8))
+    A0, _ = O.sabr_matrix(p, 0.0)
+    A1, _ = O.sabr_matrix(p, 1.0)
+    S, V, hs, hv = O.heston_grid(p)
+    i, j = 4, 2
+    row = j * 8 + (i - 1)
+    s, v, b, r = S[i - 1], V[j], p["beta"], p["r"]
+    D = math.exp(-r)
+    # the u_ss entry scales by D^(2(1-beta)), the u_sv entry by D^(1-beta), the u_vv entry not at all
+    ss0 = 0.5 * v * v * s ** (2 * b) / hs ** 2
+    assert math.isclose(A0[row, row + 1], ss0 + r * s / (2 * hs), rel_tol=1e-13)
+    assert math.isclose(A1[row, row + 1], ss0 * D ** (2 * (1 - b)) + r * s / (2 * hs), rel_tol=1e-13)
+    assert math.isclose(A1[row, row + 9] / A0[row, row + 9], D ** (1 - b), rel_tol=1e-13)
+    assert math.isclose(A1[row, row + 8], A0[row, row + 8], rel_tol=1e-15)
+    # the v = 0 row: u_t = r s u_s - r u
+    assert math.isclose(A1[0, 0], -r, rel_tol=1e-15) and math.isclose(A1[1, 2], r * S[1] / (2 * hs), rel_tol=1e-13)
+
+
+@pytest.mark.slow
+def test_sabr_set5_iterations_and_solution():
+    its = []
+    for nt in (16, 32):
+        p = W.sabr_set5(nt)
+        x, info = O.solve(p, tol=1e-9, m=40, maxit=300)
+        assert info["converged"]
+        U = O.sequential_cn(p)
+        assert np.abs(x - U.ravel()).max() <= 1e-8 * np.abs(U).max()
+        its.append(info["its"])
+    assert max(its) <= 6 and max(its) - min(its) <= 1, its  # the paper: 6 on every mesh
+    _, info1 = O.solve(W.with_(W.sabr_set5(16), alpha=1.0), tol=1e-9, m=40, maxit=300)
+    assert info1["converged"] and info1["its"] >= 5 * max(its), (info1["its"], its)
