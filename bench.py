@@ -57,6 +57,7 @@ CASES = {
     "heston_set1_nt192": lambda W: (W.heston_set1(192), 1e-9, 40),
     "sabr_set3_nt192": lambda W: (W.sabr_set3(192), 1e-9, 40),
     "sabr_set4_nt192": lambda W: (W.sabr_set4(192), 1e-9, 40),
+    "sabr_set5_nt192": lambda W: (W.sabr_set5(192), 1e-9, 40),
 }
 
 
@@ -938,9 +939,10 @@ def run_extras(args, flush, stream, main):
                      "an i9-13900K): 4 iterations, 0.51 s at Nt 96 and 5.52 s at Nt 192 (context only)",
                      "nt_96": line_2d(W.heston_set1, 96), "nt_192": line_2d(W.heston_set1, 192)}
     out["sabr"] = {"workload": "sabr_uniform", "note": "the paper's Table 3 (P_alpha, MATLAB on an i9-13900K): "
-                   "4 iterations; Set III 0.38 s at Nt 96 and 3.11 s at Nt 192, Set IV 0.40 s and 3.68 s (context "
-                   "only)", "set3_nt_96": line_2d(W.sabr_set3, 96), "set3_nt_192": line_2d(W.sabr_set3, 192),
-                   "set4_nt_192": line_2d(W.sabr_set4, 192)}
+                   "4 iterations; Set III 0.38 s at Nt 96 and 3.11 s at Nt 192, Set IV 0.40 s and 3.68 s; Table 4, "
+                   "Set V (r = 0.03, time-dependent operator): 6 iterations, 6.24 s at Nt 192 (context only)",
+                   "set3_nt_96": line_2d(W.sabr_set3, 96), "set3_nt_192": line_2d(W.sabr_set3, 192),
+                   "set4_nt_192": line_2d(W.sabr_set4, 192), "set5_nt_192": line_2d(W.sabr_set5, 192)}
 
     riesz_solve(W.riesz_1023x512(), "riesz", "explicit inverses of the shifted matrices (2.15 GB) read per apply")
     riesz_solve(W.riesz_sym_1023x512(), "riesz_sym",

@@ -59,12 +59,13 @@ extern "C" {
                              time level at j nx + i - 1. Step (b) by block elimination over the v
                              levels with dense inverses of the diagonal blocks made at create
                              (precision AAO_MIXED only) */
-#define AAO_OP_SABR 4     /* the two-dimensional SABR operator of Sec. 5.2 (Eq. 5.7) with r = 0
-                             (D(t) = 1, so A is constant in time; r != 0 returns
-                             AAO_EUNSUPPORTED): u_t = 1/2 v^2 s^(2 beta) u_ss + rho sigma s^beta v^2
-                             u_sv + 1/2 sigma^2 v^2 u_vv on the grid, boundary conditions, unknown
-                             order and step (b) of AAO_OP_HESTON; at v = 0 the boundary equation
-                             u_t = r s u_s - r u, i.e. u_t = 0 (kappa and eta unused) */
+#define AAO_OP_SABR 4     /* the two-dimensional SABR operator of Sec. 5.2 (Eq. 5.7):
+                             u_t = 1/2 v^2 s^(2 beta) D^(2(1-beta)) u_ss + rho sigma s^beta D^(1-beta)
+                             v^2 u_sv + 1/2 sigma^2 v^2 u_vv + r s u_s - r u, D(t) = e^{-rt}, on the
+                             grid, boundary conditions, unknown order and step (b) of AAO_OP_HESTON;
+                             at v = 0 the boundary equation u_t = r s u_s - r u (u_t = 0 for r = 0;
+                             kappa and eta unused). For r != 0 row k of the AaO system uses A at
+                             t_{k+1/2} (Eq. 5.8) and step (b) the time mean of those matrices */
 
 #define AAO_PUT 0
 #define AAO_CALL 1

@@ -86,10 +86,6 @@ int validate(const aao_problem* p) {
       set_error("aao_create: SABR needs 0 <= beta <= 1");
       return AAO_EINVAL;
     }
-    if (p->op == AAO_OP_SABR && p->r != 0.0) {
-      set_error("aao_create: SABR with r != 0 has a time-dependent operator (Eq. 5.7, D(t) = e^{-rt}); only r = 0 is built");
-      return AAO_EUNSUPPORTED;
-    }
     const double factors = 2.0 * p->nv * (double)(p->nt / 2 + 1) * p->nx * (double)p->nx * 8.0;
     if (factors > 48e9) { set_error("aao_create: Heston step-(b) block factors would exceed 48 GB"); return AAO_EUNSUPPORTED; }
   }

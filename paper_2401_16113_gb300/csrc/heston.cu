@@ -3,11 +3,15 @@
 //   u_t = 1/2 v s^2 u_ss + sigma rho s v u_sv + 1/2 sigma^2 v u_vv + r s u_s + kappa (eta - v) u_v - r u
 //
 // and, on the same grid with the same boundary conditions and the same kernels, the SABR operator of
-// Sec. 5.2 (Eq. 5.7) with r = 0 (D(t) = 1):
+// Sec. 5.2 (Eq. 5.7), D(t) = e^{-rt}:
 //
-//   u_t = 1/2 v^2 s^(2 beta) u_ss + rho sigma s^beta v^2 u_sv + 1/2 sigma^2 v^2 u_vv,
+//   u_t = 1/2 v^2 s^(2 beta) D^(2(1-beta)) u_ss + rho sigma s^beta D^(1-beta) v^2 u_sv
+//         + 1/2 sigma^2 v^2 u_vv + r s u_s - r u,
 //
-// whose boundary equation at v = 0, u_t = r s u_s - r u, is u_t = 0 (an all-zero row of A).
+// with the boundary equation u_t = r s u_s - r u at v = 0 (an all-zero row of A for r = 0). For
+// r != 0 the operator depends on time: row k of the AaO system (Eq. 5.8) takes it at t_{k+1/2} (its
+// coefficients as three sets, scaled per time level by 1, D^(2(1-beta)) and D^(1-beta)), and step (b)
+// takes the time mean of those matrices.
 //
 // on a uniform grid: s_i = i h_s (i = 1..Ns, h_s = s_max / Ns), v_j = j h_v (j = 0..Nv-1,
 // h_v = v_max / Nv); unknown (i, j) of a time level at p = j Ns + i - 1 (Ns Nv unknowns per level,
@@ -22,7 +26,7 @@
 //   k_hs_matvec  FP64 y = M x (Eq. 2.2) from the stencil: y_t = (x_t - x_{t-1}) - (tau/2) A (x_t + x_{t-1}),
 //                fused with the restart residual or the first Gram-Schmidt projections, finished
 //                by the last block (the conventions of the other operators' matvecs);
-//   k_hs_rhs     b = xi + tau f (the boundary data are constant in time);
+//   k_hs_rhs     b = xi + tau f (f at t_{k+1/2}: constant in time but for SABR with r != 0);
 //   step (b) of Eq. 3.2 by block elimination over the v levels. The shifted matrix of bin k,
 //                S = mu_k I - tau A, is block tridiagonal in j (blocks Ns x Ns: B_j tridiagonal on
 //                the diagonal, A_j and C_j tridiagonal below and above) except for the block E_0
@@ -53,6 +57,9 @@ constexpr int kHsOff = 10;  // stencil offsets, in this order:
 __host__ __device__ constexpr int hs_di(int q) { return q < 9 ? (q % 3) - 1 : 0; }
 __host__ __device__ constexpr int hs_dj(int q) { return q < 9 ? (q / 3) - 1 : 2; }
 
+// SABR with a nonzero rate: Eq. 5.7 depends on time through D(t) = e^{-rt} (three coefficient sets)
+bool hs_time_dependent(const aao_problem& p) { return p.op == AAO_OP_SABR && p.r != 0.0; }
+
 template <typename T> __device__ __forceinline__ double ldx(const T* p) { return (double)*p; }
 template <> __device__ __forceinline__ double ldx<float>(const float* p) { return widen(*p); }
 
@@ -62,11 +69,15 @@ template <> __device__ __forceinline__ double ldx<float>(const float* p) { retur
 // there: one FP64 addition per point for s instead of one per point and offset. The sums run over
 // the offsets in the same order as a point-by-point evaluation, so y is the same bit for bit. MODE 0:
 // y = M x; MODE 1: y = b - M x and ||y||^2 (restart residual; sigma_0, g set by the last block);
-// MODE 2: y = M x and the projections V_q . y, q < ND.
-template <typename IN, int MODE, int ND>
+// MODE 2: y = M x and the projections V_q . y, q < ND. TD (SABR with r != 0): the coefficient of
+// offset q at time level t is c0 + g2[t] c1 + g1[t] c2 from the three sets of c (each kHsOff x nsp),
+// g = (g2[0..nt), g1[0..nt)); every offset is summed (no zero test: a zero coefficient multiplies a
+// staged value inside the buffer).
+template <typename IN, int MODE, int ND, bool TD>
 __global__ void __launch_bounds__(256) k_hs_matvec(const IN* __restrict__ x, double* __restrict__ y,
                                                    const double* __restrict__ b, int ns, int nv, int nt, int rb,
-                                                   const double* __restrict__ c, const double* __restrict__ V,
+                                                   const double* __restrict__ c, const double* __restrict__ g,
+                                                   const double* __restrict__ V,
                                                    size_t vstride, double* __restrict__ part,
                                                    double* __restrict__ scal, unsigned int* __restrict__ counter,
                                                    int m) {
@@ -82,6 +93,11 @@ __global__ void __launch_bounds__(256) k_hs_matvec(const IN* __restrict__ x, dou
   for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int t = tile / nrb, j0 = (tile - t * nrb) * rb;
     const int j1 = min(nv, j0 + rb);
+    double g2 = 1.0, g1 = 1.0;
+    if constexpr (TD) {
+      g2 = __ldg(g + t);
+      g1 = __ldg(g + nt + t);
+    }
     const int hn = (j1 - j0 + 3) * ns;  // staged entries
     const IN* xt = x + (size_t)t * nsp;
     const IN* xm = t > 0 ? xt - nsp : nullptr;
@@ -109,10 +125,17 @@ __global__ void __launch_bounds__(256) k_hs_matvec(const IN* __restrict__ x, dou
 #pragma unroll
       for (int q = 0; q < kHsOff; ++q) {
         if (q == kHsOff - 1 && p >= ns) break;
-        const long long cb = __ldg(reinterpret_cast<const long long*>(c) + (size_t)q * nsp + p);
-        if ((cb << 1) != 0) {
+        if constexpr (TD) {
+          const size_t o = (size_t)q * nsp + p, cs = (size_t)kHsOff * nsp;
+          const double cq = fma(g2, __ldg(c + cs + o), fma(g1, __ldg(c + 2 * cs + o), __ldg(c + o)));
           const int ln = min(max(e + ns + hs_di(q) + hs_dj(q) * ns, 0), hn - 1);
-          as = fma(__longlong_as_double(cb), s_sm[ln], as);
+          as = fma(cq, s_sm[ln], as);
+        } else {
+          const long long cb = __ldg(reinterpret_cast<const long long*>(c) + (size_t)q * nsp + p);
+          if ((cb << 1) != 0) {
+            const int ln = min(max(e + ns + hs_di(q) + hs_dj(q) * ns, 0), hn - 1);
+            as = fma(__longlong_as_double(cb), s_sm[ln], as);
+          }
         }
       }
       const double x0 = ldx(xt + p), x1 = xm ? ldx(xm + p) : 0.0;
@@ -153,17 +176,21 @@ __global__ void __launch_bounds__(256) k_hs_matvec(const IN* __restrict__ x, dou
   }, counter);
 }
 
-// b_t = tau f + [t = 0] (u0 + (tau/2) A u0)
+// b_t = tau f + [t = 0] (u0 + (tau/2) A u0); with g (time-dependent SABR, the three sets of c and of
+// tf as in k_hs_matvec) both at t_{t+1/2}: tau f = tf0 + g2[t] tf1 + g1[t] tf2, and A at t_{1/2}
 __global__ void k_hs_rhs(double* __restrict__ b, int ns, int nsp, int nt, const double* __restrict__ c,
-                         const double* __restrict__ tf, const double* __restrict__ u0) {
-  const size_t n = (size_t)nsp * nt;
+                         const double* __restrict__ tf, const double* __restrict__ u0,
+                         const double* __restrict__ g) {
+  const size_t n = (size_t)nsp * nt, cs = (size_t)kHsOff * nsp;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     const int t = (int)(e / nsp), p = (int)(e - (size_t)t * nsp);
     double v = tf[p];
+    if (g) v = fma(g[t], tf[nsp + p], fma(g[nt + t], tf[2 * (size_t)nsp + p], v));
     if (t == 0) {
       double au = 0.0;
       for (int q = 0; q < kHsOff; ++q) {
-        const double cq = c[(size_t)q * nsp + p];
+        double cq = c[(size_t)q * nsp + p];
+        if (g) cq = fma(g[0], c[cs + (size_t)q * nsp + p], fma(g[nt], c[2 * cs + (size_t)q * nsp + p], cq));
         const int nb = p + hs_di(q) + hs_dj(q) * ns;
         if (cq != 0.0 && nb >= 0 && nb < nsp) au = fma(cq, u0[nb], au);
       }
@@ -502,30 +529,66 @@ int heston_build(Handle& h) {
   h.hs_nv = nv;
   const double hs = p.s_max / ns, hv = p.v_max / nv, tau = h.tau;
   const double r = p.r, kap = p.kappa, eta = p.eta, sig = p.sigma, rho = p.rho;
-  const bool sabr = p.op == AAO_OP_SABR;  // r = 0 (checked at create)
-  std::vector<double> c((size_t)kHsOff * nsp, 0.0), f(nsp, 0.0), u0(nsp);
+  const bool sabr = p.op == AAO_OP_SABR;
+  // SABR with r != 0: Eq. 5.7 depends on time through D(t) = e^{-rt}; its coefficients are kept as
+  // three sets, the terms without D (set 0), the u_ss term at D = 1 (set 1, times D^(2(1-beta)))
+  // and the u_sv term at D = 1 (set 2, times D^(1-beta))
+  const bool td = hs_time_dependent(p);
+  const int nset = td ? 3 : 1;
+  const size_t cset = (size_t)kHsOff * nsp;  // one coefficient set
+  std::vector<double> c(nset * cset, 0.0), f((size_t)nset * nsp + (td ? 2 * (size_t)h.nt : 0), 0.0), u0(nsp);
+  int set = 0;  // the set that add() writes
   // coefficient w of u(ii, jj) in the equation of unknown (i, j) (i, ii 1-based in s)
   auto add = [&](int i, int j, int ii, int jj, double w) {
     const int pt = j * ns + i - 1;
     if (jj == nv) {  // v = v_max: u = s
-      f[pt] += w * ii * hs;
+      f[(size_t)set * nsp + pt] += w * ii * hs;
       return;
     }
     if (ii == 0) return;  // s = 0: u = 0
     if (ii == ns + 1) {   // the ghost beyond s_max: u_{Ns+1} = u_{Ns-1} + 2 h_s
-      f[pt] += w * 2.0 * hs;
+      f[(size_t)set * nsp + pt] += w * 2.0 * hs;
       ii = ns - 1;
     }
     const int di = ii - i, dj = jj - j;
     const int q = dj == 2 ? 9 : (dj + 1) * 3 + (di + 1);
-    c[(size_t)q * nsp + pt] += w;
+    c[set * cset + (size_t)q * nsp + pt] += w;
   };
   for (int j = 0; j < nv; ++j) {
     const double v = hv * j;
     for (int i = 1; i <= ns; ++i) {
       const double s = hs * i;
       u0[j * ns + i - 1] = s > p.K ? s - p.K : 0.0;  // call payoff
-      if (j == 0 && sabr) continue;  // u_t = r s u_s - r u = 0
+      if (j == 0 && sabr) {  // u_t = r s u_s - r u (nothing for r = 0)
+        if (r != 0.0) {
+          add(i, 0, i, 0, -r);
+          add(i, 0, i + 1, 0, r * s / (2.0 * hs));
+          add(i, 0, i - 1, 0, -r * s / (2.0 * hs));
+        }
+        continue;
+      }
+      if (td) {  // the three sets of Eq. 5.7's interior row
+        const double sb = pow(s, p.beta);
+        const double dss = 0.5 * v * v * sb * sb / (hs * hs), dvv = 0.5 * sig * sig * v * v / (hv * hv);
+        const double dsv = rho * sig * sb * v * v / (4.0 * hs * hv), cs1 = r * s / (2.0 * hs);
+        set = 0;
+        add(i, j, i, j, -2.0 * dvv - r);
+        add(i, j, i + 1, j, cs1);
+        add(i, j, i - 1, j, -cs1);
+        add(i, j, i, j + 1, dvv);
+        add(i, j, i, j - 1, dvv);
+        set = 1;
+        add(i, j, i, j, -2.0 * dss);
+        add(i, j, i + 1, j, dss);
+        add(i, j, i - 1, j, dss);
+        set = 2;
+        add(i, j, i + 1, j + 1, dsv);
+        add(i, j, i - 1, j - 1, dsv);
+        add(i, j, i + 1, j - 1, -dsv);
+        add(i, j, i - 1, j + 1, -dsv);
+        set = 0;
+        continue;
+      }
       if (j == 0) {  // u_t = kappa eta u_v + r s u_s - r u, u_v one-sided to second order
         add(i, 0, i, 0, -3.0 * kap * eta / (2.0 * hv) - r);
         add(i, 0, i, 1, 4.0 * kap * eta / (2.0 * hv));
@@ -560,12 +623,28 @@ int heston_build(Handle& h) {
       add(i, j, i - 1, j + 1, -dsv);
     }
   }
-  std::vector<float> cf(c.size());
-  for (size_t e = 0; e < c.size(); ++e) {
-    c[e] *= 0.5 * tau;  // (tau/2) A
-    cf[e] = (float)c[e];
+  for (size_t e = 0; e < c.size(); ++e) c[e] *= 0.5 * tau;  // (tau/2) A
+  for (size_t q = 0; q < (size_t)nset * nsp; ++q) f[q] *= tau;  // tau f
+  // step (b) takes the time mean of A(t_{k+1/2}) (for constant coefficients A itself): the sets
+  // weighted by the means of their factors, in FP32
+  double m2 = 1.0, m1 = 1.0;
+  if (td) {
+    // per time level k the factors g2 = D^(2(1-beta)), g1 = D^(1-beta), D = e^{-r t_{k+1/2}}, kept
+    // after the three boundary vectors
+    double* g = f.data() + (size_t)3 * nsp;
+    m2 = m1 = 0.0;
+    for (int k = 0; k < h.nt; ++k) {
+      const double D = exp(-r * tau * (k + 0.5));
+      g[k] = pow(D, 2.0 * (1.0 - p.beta));
+      g[h.nt + k] = pow(D, 1.0 - p.beta);
+      m2 += g[k];
+      m1 += g[h.nt + k];
+    }
+    m2 /= h.nt;
+    m1 /= h.nt;
   }
-  for (int q = 0; q < nsp; ++q) f[q] *= tau;  // tau f
+  std::vector<float> cf(cset);
+  for (size_t e = 0; e < cset; ++e) cf[e] = (float)(td ? c[e] + m2 * c[cset + e] + m1 * c[2 * cset + e] : c[e]);
   auto up = [&](auto** dst, const auto& src) -> int {
     using T = typename std::decay<decltype(src)>::type::value_type;
     AAO_TRY_CUDA(cudaMalloc((void**)dst, sizeof(T) * src.size()));
@@ -614,7 +693,8 @@ int heston_build(Handle& h) {
 }
 
 int heston_rhs(Handle& h, double* b) {
-  k_hs_rhs<<<hs_grid(h.n), 256, 0, h.stream>>>(b, h.hs_ns, h.nx, h.nt, h.hs_c, h.hs_tf, h.hs_u0);
+  const double* g = hs_time_dependent(h.p) ? h.hs_tf + (size_t)3 * h.nx : nullptr;
+  k_hs_rhs<<<hs_grid(h.n), 256, 0, h.stream>>>(b, h.hs_ns, h.nx, h.nt, h.hs_c, h.hs_tf, h.hs_u0, g);
   AAO_CHECK_LAUNCH();
   return AAO_OK;
 }
@@ -631,13 +711,21 @@ int heston_matvec(Handle& h, const void* x, bool x_is_float, double* y, const do
   const int grid = (int)((tiles + per - 1) / per);
   const size_t smem = sizeof(double) * (size_t)(rb + 3) * ns;
   const double nn = (double)h.n;
+  const bool td = hs_time_dependent(h.p);
+  const double* g = td ? h.hs_tf + (size_t)3 * h.nx : nullptr;
   const double bytes = nn * (x_is_float ? 4.0 : 8.0) + nn * 8.0 + (b ? nn * 8.0 : 0.0) + (V ? nn * 8.0 * nd : 0.0) +
-                       8.0 * kHsOff * h.nx;
+                       8.0 * kHsOff * h.nx * (td ? 3 : 1);
   const double flops = nn * (2.0 * kHsOff + 3.0 + (b ? 3.0 : 0.0) + (V ? 2.0 * nd : 0.0));
   ProfScope ps(AAO_K_MATVEC, h.stream, bytes, flops);
 #define HS(IN, MODE, ND)                                                                                       \
-  AAO_TRY_CUDA(launch_pdl(k_hs_matvec<IN, MODE, ND>, grid, 256, smem, h.stream, (const IN*)x, y, b, ns, nv, h.nt, rb, \
-                          h.hs_c, V, h.n, h.part, h.scal, h.counter, m))
+  do {                                                                                                         \
+    if (td)                                                                                                    \
+      AAO_TRY_CUDA(launch_pdl(k_hs_matvec<IN, MODE, ND, true>, grid, 256, smem, h.stream, (const IN*)x, y, b, ns, \
+                              nv, h.nt, rb, h.hs_c, g, V, h.n, h.part, h.scal, h.counter, m));                  \
+    else                                                                                                       \
+      AAO_TRY_CUDA(launch_pdl(k_hs_matvec<IN, MODE, ND, false>, grid, 256, smem, h.stream, (const IN*)x, y, b, ns, \
+                              nv, h.nt, rb, h.hs_c, g, V, h.n, h.part, h.scal, h.counter, m));                  \
+  } while (0)
   if (V && nd > 0) {
     if (x_is_float) {
       switch (nd) {
