@@ -134,8 +134,10 @@ int aao_destroy(aao_handle* h);
    Dirichlet data averaged over t_k and t_{k+1}. b_dev: nx*nt doubles, device. */
 int aao_rhs(aao_handle* h, double* b_dev);
 
-/* y_dev <- M x_dev with M = B1 (x) I - B2 (x) A~ (Eq. 2.2; Eq. 5.8 form for AAO_OP_LOCALVOL).
-   x_dev, y_dev: nx*nt doubles, device, must not alias. */
+/* y_dev <- M x_dev with M = B1 (x) I - B2 (x) A~ (Eq. 2.2; the Eq. 5.8 form, A at t_{k+1/2} in block
+   row k, for AAO_OP_LOCALVOL and for AAO_OP_SABR with r != 0).
+   x_dev, y_dev: nx*nt doubles (nx*nv*nt for the two-dimensional operators), device, must not
+   alias. */
 int aao_matvec(aao_handle* h, const double* x_dev, double* y_dev);
 
 /* z_dev <- P_alpha^{-1} v_dev by the three steps of Eq. 3.2 with the conjugate-pair saving
@@ -183,8 +185,9 @@ int fgmres_solve_host(aao_handle* h, const double* b_host, double* x_host, doubl
    descriptor directly and keeps every table and the half spectrum in one static device array of
    32 MiB (reserved on each GPU that loads the library until the process exits); it calls no
    cudaMalloc or cudaFree.
-    - Operators: AAO_OP_BS and AAO_OP_LOCALVOL. AAO_OP_RIESZ returns AAO_EUNSUPPORTED: its step
-      (b) needs the dense inverses or the eigendecomposition that aao_create builds.
+    - Operators: AAO_OP_BS and AAO_OP_LOCALVOL. AAO_OP_RIESZ, AAO_OP_HESTON and AAO_OP_SABR return
+      AAO_EUNSUPPORTED: their step (b) needs the dense inverses, the eigendecomposition or the
+      block factors that aao_create builds.
     - Size limit: the half spectrum plus tables must fit in 32 MiB, roughly
       (nt/2+1) * 64*ceil(nx/64) * 8 bytes (mixed) or * 16 bytes (FP64) plus O(nt + nx);
       e.g. nx 2047, nt 2048 fits in mixed precision. Larger problems return AAO_EINVAL
