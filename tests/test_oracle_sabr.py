@@ -185,3 +185,28 @@ def test_sabr_set5_iterations_and_solution():
     assert max(its) <= 6 and max(its) - min(its) <= 1, its  # the paper: 6 on every mesh
     _, info1 = O.solve(W.with_(W.sabr_set5(16), alpha=1.0), tol=1e-9, m=40, maxit=300)
     assert info1["converged"] and info1["its"] >= 5 * max(its), (info1["its"], its)
+
+
+@pytest.mark.parametrize("alpha", [1e-1, 1e-3])
+@pytest.mark.parametrize("make", [W.sabr_set3, W.sabr_set4], ids=["set3", "set4"])
+def test_sabr_lemma31_eigenvalues(alpha, make):
+    """Lemma 3.1 on the SABR matrix (r = 0): (Nt - 1) N eigenvalues of P_alpha^{-1} M equal 1, the
+    other N are 1 / (1 - alpha q(l)^Nt) with q(l) = (1 + l/2) / (1 - l/2) for the eigenvalues l of
+    tau A. The zero eigenvalues of A (the v = 0 rows) give q = 1 and the value 1 / (1 - alpha)."""
+    p = W.with_(make(8), nx=6, nv=4, nt=6, alpha=alpha)
+    N, nt = 24, 6
+    A, _ = O.sabr_matrix(p)
+    _, tau = O.time_grid(p)
+    lam = np.linalg.eigvals(tau * A.toarray())
+    q = (1 + lam / 2) / (1 - lam / 2)
+    zf = 1.0 / (1.0 - alpha * q ** nt)
+    assert np.sum(np.abs(lam) < 1e-12) >= 6  # one zero row per s node on v = 0
+    z = O.preconditioned_eigs(p)
+    order = np.argsort(np.abs(z - 1))
+    unit, rest = z[order[:(nt - 1) * N]], z[order[(nt - 1) * N:]]
+    assert np.abs(unit - 1).max() < 1e-8
+    for w in zf:
+        k = int(np.argmin(np.abs(rest - w)))
+        assert abs(rest[k] - w) < 1e-8
+        rest = np.delete(rest, k)
+    assert np.sum(np.abs(zf - 1 / (1 - alpha)) < 1e-10) >= 6
